@@ -1,0 +1,220 @@
+"""Python handle on the FP64 CPU oracle (oracle/npxo.c) -- test infrastructure only.
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg import this module.  It
+shares no code with the CUDA library; it reads the same seeded inputs (a SceneBatch of float32 /
+int32 arrays) and keeps its own double-precision state.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnpxo.so")
+SOURCES = [os.path.join(HERE, "npxo.c")]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C11, no FMA contraction so that x86 and Arm agree)."""
+    newest = max(os.path.getmtime(p) for p in SOURCES + [os.path.join(HERE, "npxo.h")])
+    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
+        return LIB_PATH
+    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fPIC", "-shared",
+           "-o", tmp, *SOURCES, "-lm", "-lpthread"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class _Model(C.Structure):
+    _fields_ = [
+        ("n_scenes", C.c_int), ("dt", C.c_double), ("gravity", C.c_double * 3), ("K", C.c_int),
+        ("omega_c", C.c_double), ("zeta", C.c_double),
+        ("link_off", C.c_void_p), ("point_off", C.c_void_p),
+        ("p0", C.c_void_p), ("m", C.c_void_p), ("plink", C.c_void_p),
+        ("parent", C.c_void_p), ("anchor", C.c_void_p), ("axis", C.c_void_p),
+        ("lo", C.c_void_p), ("hi", C.c_void_p), ("sensor", C.c_void_p),
+        ("mu", C.c_void_p), ("hmap", C.c_void_p),
+        ("heightmaps", C.c_void_p), ("hm_nx", C.c_int), ("hm_ny", C.c_int),
+        ("hm_scale", C.c_double), ("hm_origin", C.c_double * 2),
+        ("act_mode", C.c_int), ("act_params", C.c_void_p),
+    ]
+
+
+class _State(C.Structure):
+    _fields_ = [("c", C.c_void_p), ("q", C.c_void_p), ("v", C.c_void_p), ("L", C.c_void_p),
+                ("theta", C.c_void_p), ("kappa", C.c_void_p), ("sensors", C.c_void_p),
+                ("status", C.c_void_p)]
+
+
+class Counts(C.Structure):
+    _fields_ = [("scene_steps", C.c_ulonglong), ("points", C.c_ulonglong),
+                ("contacts", C.c_ulonglong), ("friction_pts", C.c_ulonglong),
+                ("ticks", C.c_ulonglong), ("tick_points", C.c_ulonglong)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        P = C.c_void_p
+        _lib.npxo_init.argtypes = [P, P, P, P, P, P, P]
+        _lib.npxo_step.argtypes = [P, P, C.c_int, C.c_int, C.c_int, C.c_longlong, P]
+        _lib.npxo_step_mt.argtypes = [P, P, C.c_int, C.c_longlong, C.c_int, P]
+        _lib.npxo_points_world.argtypes = [P, P, C.c_int, P]
+        _lib.npxo_mass_props.argtypes = [P, P, C.c_int, P, P, P]
+        _lib.npxo_link_frames.argtypes = [P, P, C.c_int, P]
+        _lib.npxo_target.argtypes = [P, C.c_int, C.c_int, C.c_longlong]
+        _lib.npxo_target.restype = C.c_double
+        _lib.npxo_lut.argtypes = [P, C.c_int, C.c_double, C.c_double, P]
+        _lib.npxo_friction_ls.argtypes = [C.c_int, P, P, P, P]
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def friction_ls(src_xy: np.ndarray, e_xy: np.ndarray):
+    """The oracle's solution of Eqs. 4-6: (t, a3) of the centred problem."""
+    s = np.ascontiguousarray(src_xy, np.float64)
+    e = np.ascontiguousarray(e_xy, np.float64)
+    t = np.zeros(2)
+    a3 = np.zeros(1)
+    lib().npxo_friction_ls(len(s), _ptr(s), _ptr(e), _ptr(t), _ptr(a3))
+    return t, float(a3[0])
+
+
+class Oracle:
+    """FP64 state of every scene of a SceneBatch, advanced by the C oracle."""
+
+    def __init__(self, batch, threads: int = 1):
+        self.batch = b = batch
+        self.threads = threads
+        S, P, J = b.n_scenes, b.n_points, b.n_joints
+        self._keep = [np.ascontiguousarray(a) for a in
+                      (b.link_off, b.point_off, b.p0, b.m, b.plink, b.parent, b.anchor, b.axis,
+                       b.lo, b.hi, b.sensor, b.mu, b.hmap)]
+        (lo_, po_, p0, m, pl, par, anc, ax, lo, hi, sen, mu, hm) = self._keep
+        maps = None if b.heightmaps is None else np.ascontiguousarray(b.heightmaps, np.float32)
+        act = np.ascontiguousarray(b.act_params if b.act_params is not None
+                                   else np.zeros((J, 4), np.float32), np.float32)
+        self._keep += [maps, act]
+        self.model = _Model(
+            n_scenes=S, dt=b.dt, gravity=(C.c_double * 3)(*b.gravity), K=b.joint_update_steps,
+            omega_c=b.contact_omega, zeta=b.contact_zeta,
+            link_off=_ptr(lo_), point_off=_ptr(po_), p0=_ptr(p0), m=_ptr(m), plink=_ptr(pl),
+            parent=_ptr(par), anchor=_ptr(anc), axis=_ptr(ax), lo=_ptr(lo), hi=_ptr(hi),
+            sensor=_ptr(sen), mu=_ptr(mu), hmap=_ptr(hm), heightmaps=_ptr(maps),
+            hm_nx=0 if maps is None else maps.shape[2], hm_ny=0 if maps is None else maps.shape[1],
+            hm_scale=b.hm_scale, hm_origin=(C.c_double * 2)(*b.hm_origin),
+            act_mode=b.act_mode, act_params=_ptr(act))
+        self.c = np.zeros((S, 3))
+        self.q = np.zeros((S, 4))
+        self.v = np.zeros((S, 3))
+        self.L = np.zeros((S, 3))
+        self.theta = np.zeros(J)
+        self.kappa = np.zeros(P, np.uint8)
+        self.sensors = np.zeros(S, np.uint32)
+        self.status = np.zeros(S, np.uint32)
+        self.state = _State(*[_ptr(a) for a in (self.c, self.q, self.v, self.L, self.theta,
+                                                 self.kappa, self.sensors, self.status)])
+        self.n = 0
+        rc = lib().npxo_init(C.byref(self.model), _ptr(b.origin), _ptr(b.quat), _ptr(b.vel),
+                             _ptr(b.omega), _ptr(np.ascontiguousarray(b.theta0, np.float32)),
+                             C.byref(self.state))
+        if rc:
+            raise ValueError(f"oracle rejected the scene batch (rc={rc})")
+
+    def step(self, n_steps: int, threads: int | None = None) -> dict:
+        cnt = Counts()
+        th = self.threads if threads is None else threads
+        if th > 1:
+            rc = lib().npxo_step_mt(C.byref(self.model), C.byref(self.state), n_steps, self.n, th,
+                                    C.byref(cnt))
+        else:
+            rc = lib().npxo_step(C.byref(self.model), C.byref(self.state), 0, self.batch.n_scenes,
+                                 n_steps, self.n, C.byref(cnt))
+        if rc:
+            raise RuntimeError(f"oracle step failed (rc={rc})")
+        self.n += n_steps
+        return cnt.as_dict()
+
+    # -- views
+    def omega(self) -> np.ndarray:
+        """World angular velocity of every scene, from L and the current shape."""
+        out = np.zeros((self.batch.n_scenes, 3))
+        for s in range(self.batch.n_scenes):
+            g, Ib, M = self.mass_props(s)
+            R = quat_matrix(self.q[s])
+            out[s] = R @ np.linalg.solve(Ib, R.T @ self.L[s])
+        return out
+
+    def points_world(self, s: int) -> np.ndarray:
+        b = self.batch
+        out = np.zeros((int(b.point_off[s + 1] - b.point_off[s]), 3))
+        lib().npxo_points_world(C.byref(self.model), C.byref(self.state), s, _ptr(out))
+        return out
+
+    def mass_props(self, s: int):
+        g = np.zeros(3)
+        Ib = np.zeros(9)
+        M = np.zeros(1)
+        lib().npxo_mass_props(C.byref(self.model), C.byref(self.state), s, _ptr(g), _ptr(Ib),
+                              _ptr(M))
+        return g, Ib.reshape(3, 3), float(M[0])
+
+    def link_frames(self, s: int):
+        b = self.batch
+        nl = int(b.link_off[s + 1] - b.link_off[s])
+        out = np.zeros((nl, 12))
+        lib().npxo_link_frames(C.byref(self.model), C.byref(self.state), s, _ptr(out))
+        return out[:, :9].reshape(nl, 3, 3), out[:, 9:]
+
+    def target(self, s: int, j: int, n: int) -> float:
+        return lib().npxo_target(C.byref(self.model), s, j, n)
+
+    def lut(self, s: int, x: float, y: float) -> float:
+        h = np.zeros(1)
+        lib().npxo_lut(C.byref(self.model), s, x, y, _ptr(h))
+        return float(h[0])
+
+    def copy_state_from(self, other: "Oracle"):
+        for a, b_ in ((self.c, other.c), (self.q, other.q), (self.v, other.v), (self.L, other.L),
+                      (self.theta, other.theta), (self.kappa, other.kappa),
+                      (self.sensors, other.sensors), (self.status, other.status)):
+            a[...] = b_
+        self.n = other.n
+
+
+def quat_matrix(q) -> np.ndarray:
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def time_oracle(batch, n_steps: int, threads: int) -> dict:
+    """Wall-clock throughput of the oracle on `batch` for n_steps (CPU baseline)."""
+    o = Oracle(batch, threads=threads)
+    t0 = time.perf_counter()
+    cnt = o.step(n_steps)
+    dt = time.perf_counter() - t0
+    return {"seconds": dt, "scene_steps": cnt["scene_steps"], "counts": cnt,
+            "scene_steps_per_s": cnt["scene_steps"] / dt if dt > 0 else float("nan")}
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv))
