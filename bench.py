@@ -1,0 +1,294 @@
+"""Benchmark: hexapod scene-steps per second on one GB300 (and N replicas under torchrun).
+
+Workload: 4,096 independent 18-DoF hexapods (352 mass points each, flat ground, mu = 0.8,
+dt = 1 ms, joints re-targeted every 80 steps to seeded sinusoids).  One benchmark step is one
+npx_world_step(1000) call: 1 s of simulated time for every scene, i.e. 4.096e6 scene-steps.
+The default 10 timed steps are the workload's 10 s of simulated time.
+
+Timing: CUDA events on the world's stream around every step; between timed steps a 256 MiB
+buffer is written to flush the 129 MB L2 (not timed).  `value` is whole-job throughput with the
+state resident in HBM; `e2e` is the same metric through the public C-ABI with host buffers:
+every step uploads the full dynamic state from pinned host memory, steps, and reads the sensors
+back.  The roofline object reports the step kernel's algorithmic FP32 flops (event counts of the
+CPU oracle on a sample of the same workload times a fixed per-event flop model) per launch over
+its measured launch time, against the FP32 FMA peak of the part.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SCENES = 4096
+CHUNK = 1000
+WORKLOAD = "hexapod_18dof_4096_scenes_flat_dt1ms_K80"
+METRIC = "hexapod scene-steps/s on 1 GB300 (plain vs surrogate at stated error) + % roofline"
+UNIT = "scene-steps/s"
+
+# FP32 peak of a GB300 (152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.07 GHz max SM clock)
+SMS, FP32_LANES, MAX_SM_GHZ = 152, 128, 2.07
+FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_GHZ / 1e3
+
+# Algorithmic flops per oracle event (an FMA counts 2): flat-ground z test per point; contact
+# point (x, y, point velocity, penalty force, wrench); friction point (two positions, slip, seven
+# least-squares sums); joint-update point (forward kinematics twice for the mass properties,
+# once for the offsets, ten moment sums); fixed per-scene work (rotation matrices, angular
+# velocity twice, integration, exponential map, normalisation, friction solve, momentum and
+# orientation corrections).
+FLOPS_PER = {"points": 7, "contacts": 27, "friction_pts": 42, "tick_points": 115,
+             "scene_steps": 320}
+
+
+def algorithmic_flops(counts: dict) -> float:
+    return float(sum(FLOPS_PER[k] * counts[k] for k in FLOPS_PER))
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_sample(batch, n_scenes: int, n_steps: int, threads: int) -> dict:
+    """The FP64 CPU oracle as it stands on a bounded sample of the workload."""
+    from oracle.oracle import time_oracle
+    sub = batch.subset(np.arange(n_scenes))
+    r = time_oracle(sub, n_steps, threads)
+    return r
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle on the host cores, same workload and metric."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2411_05799_gb300 import scenes
+    from oracle.oracle import build as build_oracle
+    build_oracle()
+    threads = os.cpu_count() or 1
+    batch = scenes.hexapod_batch(N_SCENES)
+    n_sc, n_st = 256, 500                  # a bounded sample of the 4,096-scene, 1,000-step step
+    for _ in range(args.warmup):
+        cpu_oracle_sample(batch, n_sc, 50, threads)
+    vals = []
+    t_total = 0.0
+    for _ in range(args.steps):
+        r = cpu_oracle_sample(batch, n_sc, n_st, threads)
+        vals.append(r["scene_steps_per_s"])
+        t_total += r["seconds"]
+    value = float(np.mean(vals))
+    ms_per_step = N_SCENES * CHUNK / value * 1e3
+    sample = f"{n_sc} of {N_SCENES} hexapods x {n_st} of {CHUNK} steps per benchmark step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "scenes": N_SCENES,
+                                            "steps_per_bench_step": CHUNK, "dt": 1e-3, "K": 80},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    from paper_2411_05799_gb300 import scenes
+    from paper_2411_05799_gb300.build import build
+    from paper_2411_05799_gb300.npx import World
+
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        build()
+    if dist:
+        dist.barrier()
+    stream = torch.cuda.Stream(device=dev)
+    batch = scenes.hexapod_batch(N_SCENES)
+    world = World.from_batch(batch, stream=stream.cuda_stream, device=local)
+    tune = world.autotune(200)
+    world.configure(chunk_steps=CHUNK)
+    info = world.info()
+    # initial state of the workload, kept in pinned host memory for the end-to-end leg
+    init = world.read()
+    init_kappa = world.contacts()
+    init_step = init["step"]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def l2_flush():
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+
+    for _ in range(args.warmup):
+        world.step(CHUNK)
+    world.sync()
+    l2_flush()
+    torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local)
+    launches0 = world.info()["kernel_launches"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        world.step(CHUNK)
+        ev[i][1].record(stream)
+        l2_flush()
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    per_step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(per_step_ms))
+    launches = world.info()["kernel_launches"] - launches0
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    status = world.read()["status"]
+
+    # ---- end to end through the C-ABI with host buffers
+    e2e_steps = max(1, min(args.steps, 5))
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy()
+           for k, v in (("cog", init["cog"]), ("quat", init["quat"]), ("vel", init["vel"]),
+                        ("angmom", init["angmom"]), ("theta", init["theta"]),
+                        ("kappa", init_kappa))}
+    h2d = sum(v.nbytes for v in pin.values()) + 8
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(e2e_steps):
+        world.write_state(pin["cog"], pin["quat"], pin["vel"], pin["angmom"], pin["theta"],
+                          pin["kappa"], init_step)
+        world.step(CHUNK)
+        last = world.read()
+    e2e_s = time.perf_counter() - t0
+    d2h = sum(v.nbytes for v in last.values() if isinstance(v, np.ndarray)) + 8
+    e2e_val = ws * N_SCENES * CHUNK * e2e_steps / e2e_s
+
+    value = ws * N_SCENES * CHUNK * args.steps / (total_ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "scenes_per_gpu": N_SCENES,
+                       "steps_per_bench_step": CHUNK, "dt": 1e-3, "K": 80,
+                       "parallelism": f"replicas{ws}", "l2": "flushed between timed steps (256 MiB write)",
+                       "lanes_per_scene": info["lanes_per_scene"],
+                       "warps_per_block": info["warps_per_block"], "blocks": info["blocks"],
+                       "frozen_scenes": int((status != 0).sum())},
+            "gpu_launches": int(2 * launches),
+            "clocks": clk,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "steps": e2e_steps}}
+
+    if rank == 0:
+        # algorithmic flops per scene-step from the oracle's event counts on a sample
+        n_sc, n_st = 1024, 1000
+        threads = os.cpu_count() or 1
+        r = cpu_oracle_sample(batch, n_sc, n_st, threads)
+        flops_per_ss = algorithmic_flops(r["counts"]) / r["counts"]["scene_steps"]
+        launch_ms = total_ms / max(1, launches)
+        achieved = flops_per_ss * N_SCENES * CHUNK / (launch_ms / 1e3) / 1e12
+        line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                            "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                            "traffic": None, "kernel": "step_kernel",
+                            "flops_per_scene_step": flops_per_ss,
+                            "peak_note": "FP32 FMA peak from unit counts and max SM clock"}
+        line["cpu_baseline"] = {"value": r["scene_steps_per_s"], "unit": UNIT, "cores": threads,
+                                "kind": "oracle",
+                                "sample": f"{n_sc} of {N_SCENES} hexapods x {n_st} steps (FP64)"}
+        print(json.dumps(line), flush=True)
+    world.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,187 @@
+/* npx.h -- C-ABI of the GB300 batched NeoPhysIx scene-step library (libnpx.so).
+ *
+ * A world holds many independent scenes; each scene is one robot made of links of mass points
+ * (NeoPhysIx Sec. III-A) joined by hinges (Sec. III-B, Appendix "createJoint").  One call of
+ * npx_world_step(w, n) advances every scene by n fixed steps on the GPU.  Each step:
+ *   1. every K steps, joint-angle determination: each hinge jumps to its clamped target and the
+ *      robot's shape is recomputed while it stays one rigid body (Sec. III-B);
+ *   2. point-cloud collision: every mass point looks up the ground height under it in a height
+ *      map (x, y scaled by the map's scale and floored to integer cells, Sec. III-A);
+ *   3. a penalty normal force per point in contact, summed into the body wrench;
+ *   4. semi-implicit Euler integration of the CoG and the angular momentum;
+ *   5. friction estimation: the least-squares rigid correction of Eqs. 1-6 (Sec. III-C) over the
+ *      points in contact in both steps, capped by the maximum static friction;
+ *   6. foot-contact sensors.
+ *
+ * Conventions: SI units, z up, quaternions (w, x, y, z).  All arrays passed to the library are
+ * HOST pointers unless a name says "device"; the library copies them during the call and never
+ * keeps them.  Every function returns NPX_OK (0) or a negative NPX_E* code; npx_last_error()
+ * then describes the failure (thread-local).  A world is not thread-safe: one caller thread at
+ * a time.  Work is queued on the world's CUDA stream; functions that return data synchronise
+ * that stream.
+ */
+#ifndef NPX_H
+#define NPX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NPX_OK 0
+#define NPX_EINVAL (-1)   /* bad argument (null pointer, index out of range, bad geometry) */
+#define NPX_ENOMEM (-2)   /* host or device allocation failed */
+#define NPX_ESTATE (-3)   /* call out of order (e.g. adding bodies after finalize) */
+#define NPX_ECUDA (-4)    /* a CUDA runtime call failed */
+#define NPX_ETIMEOUT (-5) /* a bounded device wait gave up */
+#define NPX_ERANGE (-6)   /* a size exceeds what the library supports */
+
+#define NPX_ACT_HOLD 0     /* joints keep their angles; no joint updates */
+#define NPX_ACT_SINUSOID 1 /* target = bias + A sin(2 pi f t + phi), set every K steps */
+
+#define NPX_MAX_LINKS 64         /* links per scene */
+#define NPX_MAX_POINTS 2048      /* mass points per scene */
+#define NPX_MAX_SENSORS 32       /* contact sensors per scene (one bit each) */
+
+typedef struct npx_world npx_world;
+
+/* World-wide parameters.  The height maps (Sec. III-A) are hm_count maps of hm_ny x hm_nx
+ * float heights [m], row-major (row = y cell), cell (0,0) at world (hm_origin[0], hm_origin[1]),
+ * hm_scale cells per metre (the paper's factor 10 gives 0.1 m cells).  A point at (x, y) reads
+ * cell (floor((x - ox) * scale), floor((y - oy) * scale)) clamped to the map.  hm_count = 0
+ * means flat ground z = 0 for every scene. */
+typedef struct {
+    int n_scenes;            /* number of scenes (>= 1) */
+    float dt;                /* step [s] (> 0) */
+    float gravity[3];        /* [m/s^2] */
+    int joint_update_steps;  /* K: joints updated on steps n with n % K == 0 (Sec. III-B); >= 1 */
+    float contact_omega;     /* per-point penalty natural frequency w_c [rad/s]: k = m w_c^2 */
+    float contact_zeta;      /* per-point damping ratio: c = 2 zeta m w_c */
+    int hm_count, hm_nx, hm_ny;
+    float hm_scale;
+    float hm_origin[2];
+    const float *hm_data;    /* host, hm_count * hm_ny * hm_nx floats, or NULL when hm_count = 0 */
+    void *stream;            /* cudaStream_t to queue work on; NULL = the legacy default stream */
+    int device;              /* CUDA device ordinal */
+} npx_world_desc;
+
+/* Batched construction: scenes [first, first + count) in one call, structure of arrays.
+ * Per scene s (0-based within the batch): links link_off[s] .. link_off[s+1]-1 and points
+ * point_off[s] .. point_off[s+1]-1 of the arrays below.  Scene-local link 0 is the root; link
+ * k >= 1 hangs from parent[k] < k by a hinge (scene-local joint k-1) through anchor[k] along
+ * axis[k] (construction frame = the parent's frame with all angles zero, Appendix "createJoint"),
+ * limited to [lo[k], hi[k]] rad.  sensor[k] >= 0 puts the link's points on contact sensor bit
+ * sensor[k].  Points: construction-frame position p0 (xyz), mass m [kg] (> 0), scene-local link
+ * plink.  mu[s] is the scene's friction coefficient, hmap[s] its height map (-1 = flat z = 0). */
+typedef struct {
+    int first, count;
+    const int *link_off, *point_off;              /* [count + 1] */
+    const int *parent;                            /* [n_links] */
+    const float *anchor, *axis;                   /* [n_links * 3] */
+    const float *lo, *hi;                         /* [n_links] */
+    const int *sensor;                            /* [n_links] */
+    const float *p0, *m;                          /* [n_points * 3], [n_points] */
+    const int *plink;                             /* [n_points] */
+    const float *mu;                              /* [count] */
+    const int *hmap;                              /* [count] or NULL (all flat / map 0) */
+} npx_scene_batch;
+
+/* State and sensor read-out, all host arrays, any may be NULL. */
+typedef struct {
+    float *cog;        /* [S*3] world CoG */
+    float *quat;       /* [S*4] orientation of the construction (root-link) frame */
+    float *vel;        /* [S*3] CoG velocity */
+    float *omega;      /* [S*3] world angular velocity */
+    float *angmom;     /* [S*3] world angular momentum about the CoG */
+    float *theta;      /* [J]   joint angles, scene-major (joint j of scene s at joint_off(s)+j) */
+    uint32_t *contacts;/* [S]   contact-sensor bits of the last step */
+    uint32_t *status;  /* [S]   0 = ok; bit 0 non-finite state, bit 1 out of range (scene frozen) */
+    int64_t *step;     /* [1]   global step counter n */
+} npx_sensors;
+
+/* --- lifetime ------------------------------------------------------------------------- */
+int npx_world_create(const npx_world_desc *desc, npx_world **out);
+int npx_world_destroy(npx_world *w);
+const char *npx_last_error(void);
+
+/* --- construction, the paper's robot API (Sec. IV, Appendix) --------------------------- */
+/* createPoint/createBox/...: a body is a cloud of n mass points (construction frame) of masses
+ * mass[i], or of total_mass spread evenly when mass == NULL.  Returns the scene-local body id. */
+int npx_body_add_pointcloud(npx_world *w, int scene, const float *xyz, const float *mass,
+                            float total_mass, int n, int *out_body);
+/* connectBodies: glue body2 rigidly to body1 (same link). */
+int npx_body_connect(npx_world *w, int scene, int body1, int body2);
+/* createJoint: hinge between the links of body1 (parent side) and body2, anchor in the
+ * construction frame of body1, axis direction (normalised by the library), limits [lo, hi]. */
+int npx_joint_add(npx_world *w, int scene, int body1, int body2, const float anchor[3],
+                  const float axis[3], float lo, float hi, int *out_joint);
+/* foot-contact sensor: bit `bit` is set when any point of the body's link touches the ground */
+int npx_sensor_add(npx_world *w, int scene, int body, int bit);
+int npx_scene_set_friction(npx_world *w, int scene, float mu);
+int npx_scene_set_heightmap(npx_world *w, int scene, int hm);
+/* copy scene src's construction into scenes [first_dst, first_dst + count) */
+int npx_scene_clone(npx_world *w, int src, int first_dst, int count);
+/* batched construction of many scenes at once (see npx_scene_batch) */
+int npx_scenes_add(npx_world *w, const npx_scene_batch *b);
+/* finalizeConstruction: checks every scene, packs the structure-of-arrays device layout,
+ * uploads it.  All scenes must be defined.  Initial state: every scene at its construction pose
+ * (origin 0, identity orientation, angles 0), at rest. */
+int npx_world_finalize(npx_world *w);
+
+/* --- state ------------------------------------------------------------------------------ */
+/* Set every scene's pose and motion: construction-frame origin [S*3] and orientation [S*4]
+ * (the paper's moveBody/rotateBody applied to the whole robot), CoG velocity [S*3], world
+ * angular velocity [S*3], joint angles [J] (NULL keeps them).  Contact history is cleared. */
+int npx_state_set(npx_world *w, const float *origin, const float *quat, const float *vel,
+                  const float *omega, const float *theta);
+/* Overwrite the whole dynamic state: CoG [S*3], orientation [S*4], CoG velocity [S*3], world
+ * angular momentum about the CoG [S*3], joint angles [J], contact flags of the previous step per
+ * mass point [P] (NULL clears them; 1 = in contact), and the global step counter n (which fixes
+ * the joint-update phase n % K and the actuator phase).  Status words are cleared. */
+int npx_state_write(npx_world *w, const float *cog, const float *quat, const float *vel,
+                    const float *angmom, const float *theta, const uint8_t *contact_prev,
+                    int64_t step);
+/* Per mass point contact flag of the last step [P] (1 = in contact), scene-major. */
+int npx_contacts_read(npx_world *w, uint8_t *contact, size_t n);
+/* Actuators: NPX_ACT_HOLD (params ignored) or NPX_ACT_SINUSOID with params [J*4] =
+ * (amplitude rad, frequency Hz, phase rad, bias rad) per joint.  The phase advances by
+ * round(f dt 2^32) / 2^32 turns per step (exact over any horizon). */
+int npx_actuator_set(npx_world *w, int mode, const float *params);
+/* Advance all scenes n >= 0 steps (asynchronous on the world's stream). */
+int npx_world_step(npx_world *w, int n);
+/* Wait for queued work; reports a latched error of an earlier asynchronous call. */
+int npx_world_sync(npx_world *w);
+int npx_sensors_read(npx_world *w, npx_sensors *out);
+/* World positions of one scene's mass points [n*3] (n = its point count) */
+int npx_points_read(npx_world *w, int scene, float *xyz, int n);
+
+/* --- checkpoint --------------------------------------------------------------------------- */
+/* Serialise the dynamic state (state, angles, contact history, sensors, status, step counter)
+ * into blob.  Call with blob == NULL to get the size. */
+int npx_state_export(npx_world *w, void *blob, size_t *size);
+int npx_state_import(npx_world *w, const void *blob, size_t size);
+
+/* --- introspection and tuning -------------------------------------------------------------- */
+typedef struct {
+    int n_scenes, n_links, n_joints, n_points, max_points, max_links;
+    int lanes_per_scene, warps_per_block, blocks, chunk_steps;
+    int64_t step;
+    int64_t kernel_launches;    /* step-kernel launches so far */
+} npx_world_info;
+int npx_world_info_get(npx_world *w, npx_world_info *out);
+/* Launch shape of the step kernel: lanes per scene (8, 16 or 32), warps per block (1..16),
+ * resident blocks (0 = as many as fit), steps per kernel launch (chunk).  0 keeps a value. */
+int npx_world_configure(npx_world *w, int lanes_per_scene, int warps_per_block, int blocks,
+                        int chunk_steps);
+/* Time the step kernel over the feasible launch shapes on a copy of the state (n_steps each)
+ * and keep the fastest; the world's state is unchanged.  Writes the chosen shape to *out. */
+int npx_world_autotune(npx_world *w, int n_steps, npx_world_info *out);
+/* Capture world_step's chunk sequence in CUDA graphs (1, default) or launch directly (0). */
+int npx_world_use_graphs(npx_world *w, int on);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

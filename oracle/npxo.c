@@ -21,9 +21,14 @@
  *  - Friction (Sec. III-C): over the points in contact in both this and the previous step, the
  *    least-squares rigid map of Eq. 3 takes the points' positions after the step onto their
  *    positions before it; a3 ~ sin(alpha) (text below Eq. 6) is applied as an exact rotation by
- *    asin(a3) about the contact centroid.  The part caused by the joint motion is applied whole
- *    (the motors are strong enough, Sec. III-B); the part caused by the dynamics is scaled down so
- *    that its impulse never exceeds mu * (total normal force) * dt (the maximum static friction).
+ *    asin(a3) about the contact centroid.  Two such maps are solved: one for the slip caused by
+ *    the joint motion (source: the points after the joint update, target: the step-start
+ *    points), applied whole because the motors are strong enough (Sec. III-B), and one for the
+ *    slip caused by the dynamics (source: the integrated points, target: the points before
+ *    integration), scaled down so that its impulse never exceeds mu * (total normal force) * dt
+ *    (the maximum static friction).  The CoG takes the scaled dynamic map, then the kinematic
+ *    map; its velocity changes by the scaled dynamic displacement over dt, and the angular
+ *    momentum by the yaw rate of the scaled dynamic rotation.
  */
 #include "npxo.h"
 
@@ -282,6 +287,27 @@ int npxo_friction_ls(int n, const double *s, const double *e, double *t, double 
     return 0;
 }
 
+/* centroid of n horizontal points and their spread sum |s - centroid|^2 */
+static void centroid_spread(int n, const double *s, double *sb, double *S2) {
+    sb[0] = sb[1] = 0.0;
+    for (int i = 0; i < n; ++i) { sb[0] += s[2 * i]; sb[1] += s[2 * i + 1]; }
+    sb[0] /= n; sb[1] /= n;
+    *S2 = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double dx = s[2 * i] - sb[0], dy = s[2 * i + 1] - sb[1];
+        *S2 += dx * dx + dy * dy;
+    }
+}
+
+/* the planar rigid map x -> centre + t + Rz(alpha) (x - centre) applied to the point x */
+static void rigid_map_2d(const double centre[2], double tx, double ty, double alpha,
+                         const double x[2], double out[2]) {
+    double dx = x[0] - centre[0], dy = x[1] - centre[1];
+    double ca = cos(alpha), sa = sin(alpha);
+    out[0] = centre[0] + tx + ca * dx - sa * dy;
+    out[1] = centre[1] + ty + sa * dx + ca * dy;
+}
+
 /* ------------------------------------------------------------------ one step of one scene */
 
 static void scene_step(const npxo_model *M, npxo_state *st, int s, scene_ws *w, long long n,
@@ -367,66 +393,67 @@ static void scene_step(const npxo_model *M, npxo_state *st, int s, scene_ws *w, 
     double cn[3] = {cs[0], cs[1], cs[2]}, vn[3] = {vs[0], vs[1], vs[2]}, Ln[3] = {Ls[0], Ls[1], Ls[2]};
     double qn[4] = {qs[0], qs[1], qs[2], qs[3]};
     int nC = 0;
-    for (int i = 0; i < np; ++i) {
-        if (!(st->kappa[w->p0 + i] && w->kap[i])) continue;
-        double rw[3];
-        mat_vec(Rs, w->r + 3 * i, rw);
-        ls_s[2 * nC] = cs[0] + rw[0];
-        ls_s[2 * nC + 1] = cs[1] + rw[1];
-        nC++;
-    }
+    for (int i = 0; i < np; ++i) nC += st->kappa[w->p0 + i] && w->kap[i];
     if (nC >= 1) {
         cnt->friction_pts += (unsigned long long)nC;
-        double tD[2], a3D, tK[2] = {0, 0}, a3K = 0.0;
-        /* dynamic slip: back from the integrated positions to the positions before integration */
+        /* dynamic slip: the map taking the integrated positions back onto the positions before
+         * integration */
+        double tD[2], a3D, sD[2], S2D;
         int k = 0;
         for (int i = 0; i < np; ++i) {
             if (!(st->kappa[w->p0 + i] && w->kap[i])) continue;
+            double rw[3];
+            mat_vec(Rs, w->r + 3 * i, rw);
+            ls_s[2 * k] = cs[0] + rw[0];
+            ls_s[2 * k + 1] = cs[1] + rw[1];
             ls_e[2 * k] = w->xp[3 * i] - ls_s[2 * k];
             ls_e[2 * k + 1] = w->xp[3 * i + 1] - ls_s[2 * k + 1];
             k++;
         }
         npxo_friction_ls(nC, ls_s, ls_e, tD, &a3D);
-        if (tick) { /* kinematic slip: back from the moved joints to the step-start positions */
+        centroid_spread(nC, ls_s, sD, &S2D);
+        /* kinematic slip (joint-update steps): the map taking the points moved by the joints
+         * back onto their step-start positions */
+        double tK[2] = {0, 0}, a3K = 0.0, sK[2] = {0, 0}, S2K = 0.0;
+        if (tick) {
             k = 0;
             for (int i = 0; i < np; ++i) {
                 if (!(st->kappa[w->p0 + i] && w->kap[i])) continue;
+                ls_s[2 * k] = w->xp[3 * i];
+                ls_s[2 * k + 1] = w->xp[3 * i + 1];
                 ls_e[2 * k] = w->x0[3 * i] - w->xp[3 * i];
                 ls_e[2 * k + 1] = w->x0[3 * i + 1] - w->xp[3 * i + 1];
                 k++;
             }
             npxo_friction_ls(nC, ls_s, ls_e, tK, &a3K);
-        }
-        double sb[2] = {0, 0}, S2 = 0.0;
-        for (int i = 0; i < nC; ++i) { sb[0] += ls_s[2 * i]; sb[1] += ls_s[2 * i + 1]; }
-        sb[0] /= nC; sb[1] /= nC;
-        for (int i = 0; i < nC; ++i) {
-            double dx = ls_s[2 * i] - sb[0], dy = ls_s[2 * i + 1] - sb[1];
-            S2 += dx * dx + dy * dy;
+            centroid_spread(nC, ls_s, sK, &S2K);
         }
         double aD = asin(a3D < -1 ? -1 : (a3D > 1 ? 1 : a3D));
         double aK = asin(a3K < -1 ? -1 : (a3K > 1 ? 1 : a3K));
-        /* maximum static friction: impulse needed to undo the dynamic slip vs mu * FN * dt */
+        /* maximum static friction: the impulse that undoes the dynamic slip is at most
+         * mu * FN * dt; beyond that the dynamic correction is scaled down */
         double sh = sin(0.5 * aD);
-        double u2 = tD[0] * tD[0] + tD[1] * tD[1] + 4.0 * sh * sh * S2 / nC;
+        double u2 = tD[0] * tD[0] + tD[1] * tD[1] + 4.0 * sh * sh * S2D / nC;
         double Jreq = w->Mtot * sqrt(u2) / dt;
         double Jmax = (double)M->mu[s] * dt * FN;
         double sc = (Jreq <= Jmax) ? 1.0 : Jmax / Jreq;
-        double Tx = tK[0] + sc * tD[0], Ty = tK[1] + sc * tD[1], A = aK + sc * aD;
-        double dx = cs[0] - sb[0], dy = cs[1] - sb[1];
-        double cA = cos(A), sA = sin(A), cD = cos(aD), sD = sin(aD);
-        cn[0] = sb[0] + Tx + cA * dx - sA * dy;
-        cn[1] = sb[1] + Ty + sA * dx + cA * dy;
-        double dcx = tD[0] + (cD - 1.0) * dx - sD * dy;
-        double dcy = tD[1] + sD * dx + (cD - 1.0) * dy;
-        vn[0] = vs[0] + sc * dcx / dt;
-        vn[1] = vs[1] + sc * dcy / dt;
+        /* CoG: first the scaled dynamic map about its centroid, then the kinematic map */
+        double y[2], x2[2];
+        rigid_map_2d(sD, sc * tD[0], sc * tD[1], sc * aD, cs, y);
+        rigid_map_2d(sK, tK[0], tK[1], aK, y, x2);
+        cn[0] = x2[0];
+        cn[1] = x2[1];
+        double yD[2];
+        rigid_map_2d(sD, tD[0], tD[1], aD, cs, yD);
+        vn[0] = vs[0] + sc * (yD[0] - cs[0]) / dt;
+        vn[1] = vs[1] + sc * (yD[1] - cs[1]) / dt;
         double Rst[9], Iw[9], ez[3] = {0, 0, 1}, Iz[3];
         mat_transpose(Rs, Rst);
         mat_mul(Rs, w->Ib, tmp);
         mat_mul(tmp, Rst, Iw);
         mat_vec(Iw, ez, Iz);
         for (int k2 = 0; k2 < 3; ++k2) Ln[k2] = Ls[k2] + (sc * aD / dt) * Iz[k2];
+        double A = aK + sc * aD;
         double qz[4] = {cos(0.5 * A), 0.0, 0.0, sin(0.5 * A)};
         quat_mul(qz, qs, qn);
     }

@@ -1,0 +1,68 @@
+// npx_internal.h -- device data layout shared by the host library (npx_world.cpp) and the
+// kernels (npx_step.cu).  Not part of the public C-ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace npx {
+
+// One link of a scene (48 bytes): hinge anchor and unit axis in the parent's construction frame
+// (NeoPhysIx Appendix, createJoint), joint limits, parent link (scene-local, -1 for the root),
+// contact-sensor bit (-1 none) and depth in the link tree (root 0).
+struct LinkDev {
+    float ax, ay, az, lo;
+    float ux, uy, uz, hi;
+    int parent, sensor, depth, pad;
+};
+
+// Dynamic state, structure of arrays: component k of scene s at st[k * S + s].
+enum { ST_CX = 0, ST_CY, ST_CZ, ST_QW, ST_QX, ST_QY, ST_QZ, ST_VX, ST_VY, ST_VZ,
+       ST_LX, ST_LY, ST_LZ, ST_N };
+
+struct WorldDev {
+    int S, P, L, J;
+    const int *link_off, *point_off;      // [S+1]
+    const float4 *p0m;                    // [P] construction position (xyz) and mass (w)
+    const uint8_t *plink;                 // [P] scene-local link of each point
+    const LinkDev *links;                 // [L]
+    const float *mu;                      // [S]
+    const int *hmap;                      // [S] height map per scene, -1 = flat z = 0
+    const float *hm;                      // [H * ny * nx]
+    int hm_nx, hm_ny;
+    float hm_scale, hm_ox, hm_oy;
+    float dt, gx, gy, gz;
+    int K;
+    float kw2, kc;                        // penalty: w_c^2 and 2 zeta w_c
+    int act_mode;
+    const float4 *act;                    // [J] amplitude, frequency, phase, bias
+    const uint32_t *act_nu;               // [J] phase increment, 2^-32 turns per step
+    // dynamic state
+    float *st;                            // [ST_N * S]
+    float *theta;                         // [J]
+    uint8_t *kappa;                       // [P] contact flag of the last step
+    float *ref;                           // [2 * S] centring reference of the friction sums
+    float *omega;                         // [3 * S] angular velocity (output)
+    uint32_t *sensors, *status;           // [S]
+    // schedule
+    const int *order;                     // [S] scenes, most points first
+    int max_points, max_links;
+    const long long *step;                // device step counter n
+    unsigned int *queue;                  // work-queue counter (reset before each launch)
+};
+
+struct LaunchCfg {
+    int lps;      // lanes per scene: 8, 16 or 32
+    int wpb;      // warps per block
+    int blocks;   // grid size
+};
+
+size_t step_smem_bytes(const WorldDev &W, int lps, int wpb);
+int step_blocks_per_sm(const WorldDev &W, int lps, int wpb, cudaError_t *err);
+cudaError_t launch_step(const WorldDev &W, const LaunchCfg &cfg, int n_steps, cudaStream_t st);
+cudaError_t launch_advance(long long *d_step, int n, cudaStream_t st);
+cudaError_t launch_init(const WorldDev &W, const float *d_origin, const float *d_quat,
+                        const float *d_vel, const float *d_omega, cudaStream_t st);
+cudaError_t launch_refresh(const WorldDev &W, cudaStream_t st);
+cudaError_t launch_points(const WorldDev &W, int scene, float *d_out, cudaStream_t st);
+
+}  // namespace npx

@@ -1,0 +1,778 @@
+// npx_step.cu -- the fused NeoPhysIx scene-step kernel for GB300 (sm_103a) and its helpers.
+//
+// Execution model.  A group of LPS lanes (8, 16 or 32) of one warp owns one scene; a warp owns
+// 32/LPS scenes.  Warps are persistent: each takes the next group of scenes from a global work
+// counter (scenes ordered by decreasing point count), runs them through all n steps of the
+// launch with their state in registers, writes them back and takes the next group.  Every
+// reduction is a warp-synchronous xor-butterfly restricted to the group, so a scene never waits
+// on a block-wide barrier and every lane of a group ends with bit-identical sums (and therefore
+// bit-identical replicated scene state).
+//
+// Per scene the lanes hold, in shared memory, the point offsets r_i from the CoG in the shape
+// frame together with the point masses (float4 per point), the link frames of the forward
+// kinematics and the joint angles.  Contact history (one bit per point) lives in a 64-bit
+// register per lane: point i belongs to lane i % LPS, bit i / LPS.
+//
+// The step (NeoPhysIx Sec. III; the readings of the paper that fix what it leaves open are the
+// same as the CPU oracle's):
+//   joint update (Sec. III-B, every K steps): clamped sinusoid targets, forward kinematics along
+//     the link tree, new CoG and inertia; world CoG, root orientation and angular momentum kept;
+//   collision (Sec. III-A): every point reads the ground height under it (flat, or a height map
+//     indexed by floor((x - ox) * scale)); penalty force m (w_c^2 d - 2 zeta w_c vz) >= 0;
+//   semi-implicit Euler of the CoG velocity and world angular momentum, exponential map of the
+//     orientation;
+//   friction (Sec. III-C, Eqs. 1-6): least squares over the points in contact in both steps,
+//     solved in centred form (identical to the paper's 3x3 normal equations), a3 applied as a
+//     rotation by asin(a3) about the contact centroid, dynamic part capped by mu * FN * dt.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "npx_internal.h"
+
+namespace npx {
+
+#define FULL_MASK 0xffffffffu
+
+// ------------------------------------------------------------------------ group reductions
+
+template <int LPS, int N>
+__device__ __forceinline__ void gsum(float (&v)[N]) {
+#pragma unroll
+    for (int o = LPS / 2; o > 0; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] += __shfl_xor_sync(FULL_MASK, v[i], o);
+    }
+}
+
+template <int LPS>
+__device__ __forceinline__ uint32_t gor(uint32_t v) {
+#pragma unroll
+    for (int o = LPS / 2; o > 0; o >>= 1) v |= __shfl_xor_sync(FULL_MASK, v, o);
+    return v;
+}
+
+// ------------------------------------------------------------------------ small linear algebra
+
+struct Sym {  // symmetric 3x3
+    float xx, yy, zz, xy, xz, yz;
+};
+
+__device__ __forceinline__ void sym_mul(const Sym &a, const float x[3], float y[3]) {
+    y[0] = a.xx * x[0] + a.xy * x[1] + a.xz * x[2];
+    y[1] = a.xy * x[0] + a.yy * x[1] + a.yz * x[2];
+    y[2] = a.xz * x[0] + a.yz * x[1] + a.zz * x[2];
+}
+
+__device__ __forceinline__ Sym sym_inv(const Sym &a) {
+    float c00 = a.yy * a.zz - a.yz * a.yz;
+    float c01 = a.xz * a.yz - a.xy * a.zz;
+    float c02 = a.xy * a.yz - a.xz * a.yy;
+    float det = a.xx * c00 + a.xy * c01 + a.xz * c02;
+    float id = 1.0f / det;
+    Sym r;
+    r.xx = c00 * id;
+    r.xy = c01 * id;
+    r.xz = c02 * id;
+    r.yy = (a.xx * a.zz - a.xz * a.xz) * id;
+    r.yz = (a.xy * a.xz - a.xx * a.yz) * id;
+    r.zz = (a.xx * a.yy - a.xy * a.xy) * id;
+    return r;
+}
+
+// rotation matrix (row-major) of the unit quaternion (w, x, y, z)
+__device__ __forceinline__ void quat_mat(const float q[4], float R[9]) {
+    float w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+__device__ __forceinline__ void mat_vec(const float R[9], const float x[3], float y[3]) {
+    y[0] = R[0] * x[0] + R[1] * x[1] + R[2] * x[2];
+    y[1] = R[3] * x[0] + R[4] * x[1] + R[5] * x[2];
+    y[2] = R[6] * x[0] + R[7] * x[1] + R[8] * x[2];
+}
+
+__device__ __forceinline__ void mat_tvec(const float R[9], const float x[3], float y[3]) {
+    y[0] = R[0] * x[0] + R[3] * x[1] + R[6] * x[2];
+    y[1] = R[1] * x[0] + R[4] * x[1] + R[7] * x[2];
+    y[2] = R[2] * x[0] + R[5] * x[1] + R[8] * x[2];
+}
+
+// world-frame tensor applied to x: R S R^T x
+__device__ __forceinline__ void world_sym(const float R[9], const Sym &S, const float x[3], float y[3]) {
+    float a[3], b[3];
+    mat_tvec(R, x, a);
+    sym_mul(S, a, b);
+    mat_vec(R, b, y);
+}
+
+__device__ __forceinline__ void quat_mul(const float a[4], const float b[4], float c[4]) {
+    float t0 = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    float t1 = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    float t2 = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    float t3 = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+    c[0] = t0; c[1] = t1; c[2] = t2; c[3] = t3;
+}
+
+// ------------------------------------------------------------------------ shared-memory slots
+
+// Per scene: float4 pts[max_points] | float frames[12 * max_links] | float theta[max_links]
+__host__ __device__ inline int slot_bytes(int max_points, int max_links) {
+    int b = 16 * max_points + 48 * max_links + 4 * max_links;
+    return (b + 15) & ~15;
+}
+
+// ------------------------------------------------------------------------ kinematics (Sec. III-B)
+
+// Link frames (rotation Q row-major, translation T) taking construction coordinates of each link
+// to the shape frame (root link fixed).  A link's frame is its parent's frame followed by the
+// hinge rotation by theta about the unit axis through the anchor.  Lanes build the local hinge
+// transforms in parallel, then compose them one tree level at a time.
+template <int LPS>
+__device__ void link_frames(const WorldDev &W, int l0, int nl, const float *th, float *fr, int gl) {
+    for (int l = gl; l < nl; l += LPS) {
+        float *F = fr + 12 * l;
+        if (l == 0) {
+            F[0] = 1.f; F[1] = 0.f; F[2] = 0.f; F[3] = 0.f; F[4] = 1.f; F[5] = 0.f;
+            F[6] = 0.f; F[7] = 0.f; F[8] = 1.f; F[9] = 0.f; F[10] = 0.f; F[11] = 0.f;
+            continue;
+        }
+        const LinkDev lk = W.links[l0 + l];
+        float s, c;
+        sincosf(th[l - 1], &s, &c);
+        const float k = 1.f - c, ux = lk.ux, uy = lk.uy, uz = lk.uz;
+        float Rj[9] = {c + k * ux * ux, k * ux * uy - s * uz, k * ux * uz + s * uy,
+                       k * uy * ux + s * uz, c + k * uy * uy, k * uy * uz - s * ux,
+                       k * uz * ux - s * uy, k * uz * uy + s * ux, c + k * uz * uz};
+        const float a[3] = {lk.ax, lk.ay, lk.az};
+        float Ra[3];
+        mat_vec(Rj, a, Ra);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) F[i] = Rj[i];
+        F[9] = a[0] - Ra[0]; F[10] = a[1] - Ra[1]; F[11] = a[2] - Ra[2];
+    }
+    __syncwarp();
+    // level d >= 2: F_l = F_parent o F_l (parents at level d-1 are final)
+    for (int d = 2;; ++d) {
+        bool any = false;
+        for (int l = gl; l < nl; l += LPS) {
+            const LinkDev lk = W.links[l0 + l];
+            if (lk.depth != d) continue;
+            any = true;
+            const float *P = fr + 12 * lk.parent;
+            float *F = fr + 12 * l;
+            float Q[9], T[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    Q[3 * i + j] = P[3 * i] * F[j] + P[3 * i + 1] * F[3 + j] + P[3 * i + 2] * F[6 + j];
+                T[i] = P[3 * i] * F[9] + P[3 * i + 1] * F[10] + P[3 * i + 2] * F[11] + P[9 + i];
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) F[i] = Q[i];
+            F[9] = T[0]; F[10] = T[1]; F[11] = T[2];
+        }
+        __syncwarp();
+        if (!__any_sync(FULL_MASK, any)) break;
+    }
+}
+
+__device__ __forceinline__ void fk_point(const float *fr, float4 a, int l, float p[3]) {
+    const float *F = fr + 12 * l;
+    p[0] = F[0] * a.x + F[1] * a.y + F[2] * a.z + F[9];
+    p[1] = F[3] * a.x + F[4] * a.y + F[5] * a.z + F[10];
+    p[2] = F[6] * a.x + F[7] * a.y + F[8] * a.z + F[11];
+}
+
+struct Shape {
+    float M, g[3];
+    Sym Ib, Ii;
+};
+
+// Mass properties of the posed point cloud (Sec. III-A: the mass points give CoG and momentum),
+// accumulated about a reference point close to the CoG so that the FP32 sums do not cancel.
+template <int LPS>
+__device__ void mass_props(const WorldDev &W, int p0, int np, const float *fr, int gl,
+                           const float ref[3], Shape &sh) {
+    float a[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int i = gl; i < np; i += LPS) {
+        const float4 q = W.p0m[p0 + i];
+        float p[3];
+        fk_point(fr, q, W.plink[p0 + i], p);
+        const float dx = p[0] - ref[0], dy = p[1] - ref[1], dz = p[2] - ref[2], m = q.w;
+        a[0] += m;
+        a[1] += m * dx; a[2] += m * dy; a[3] += m * dz;
+        a[4] += m * dx * dx; a[5] += m * dy * dy; a[6] += m * dz * dz;
+        a[7] += m * dx * dy; a[8] += m * dx * dz; a[9] += m * dy * dz;
+    }
+    gsum<LPS, 10>(a);
+    const float M = a[0], dx = a[1] / M, dy = a[2] / M, dz = a[3] / M;
+    sh.M = M;
+    sh.g[0] = ref[0] + dx; sh.g[1] = ref[1] + dy; sh.g[2] = ref[2] + dz;
+    // inertia about the CoG = about the reference minus the parallel-axis term
+    sh.Ib.xx = (a[5] + a[6]) - M * (dy * dy + dz * dz);
+    sh.Ib.yy = (a[4] + a[6]) - M * (dx * dx + dz * dz);
+    sh.Ib.zz = (a[4] + a[5]) - M * (dx * dx + dy * dy);
+    sh.Ib.xy = -a[7] + M * dx * dy;
+    sh.Ib.xz = -a[8] + M * dx * dz;
+    sh.Ib.yz = -a[9] + M * dy * dz;
+    sh.Ii = sym_inv(sh.Ib);
+}
+
+// Frames and mass properties as a pure function of the joint angles: the CoG from sums about the
+// construction origin, then the inertia from sums about that CoG.  Being a function of theta
+// alone makes the result independent of where a launch (chunk) starts.
+template <int LPS>
+__device__ void shape_props(const WorldDev &W, int p0, int np, int l0, int nl, const float *th,
+                            float *fr, int gl, Shape &sh) {
+    link_frames<LPS>(W, l0, nl, th, fr, gl);
+    const float zero[3] = {0.f, 0.f, 0.f};
+    mass_props<LPS>(W, p0, np, fr, gl, zero, sh);
+    const float g0[3] = {sh.g[0], sh.g[1], sh.g[2]};
+    mass_props<LPS>(W, p0, np, fr, gl, g0, sh);
+}
+
+// Full shape set-up from the current joint angles: frames, mass properties, r_i in smem.
+template <int LPS>
+__device__ void shape_setup(const WorldDev &W, int p0, int np, int l0, int nl, const float *th,
+                            float *fr, float4 *pts, int gl, Shape &sh) {
+    shape_props<LPS>(W, p0, np, l0, nl, th, fr, gl, sh);
+    for (int i = gl; i < np; i += LPS) {
+        const float4 q = W.p0m[p0 + i];
+        float p[3];
+        fk_point(fr, q, W.plink[p0 + i], p);
+        pts[i] = make_float4(p[0] - sh.g[0], p[1] - sh.g[1], p[2] - sh.g[2], q.w);
+    }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------------------ ground (Sec. III-A)
+
+template <bool FLAT>
+__device__ __forceinline__ float ground(const WorldDev &W, int hm, float x, float y) {
+    if (FLAT || hm < 0) return 0.f;
+    const float fx = __fmul_rn(__fsub_rn(x, W.hm_ox), W.hm_scale);
+    const float fy = __fmul_rn(__fsub_rn(y, W.hm_oy), W.hm_scale);
+    int ix = __float2int_rd(fx), iy = __float2int_rd(fy);
+    ix = min(max(ix, 0), W.hm_nx - 1);
+    iy = min(max(iy, 0), W.hm_ny - 1);
+    return __ldg(W.hm + ((size_t)hm * W.hm_ny + iy) * W.hm_nx + ix);
+}
+
+// ------------------------------------------------------------------------ actuators (Sec. III-B)
+
+__device__ __forceinline__ float joint_target(const WorldDev &W, int j, long long n) {
+    const float4 a = W.act[j];
+    const uint32_t u = W.act_nu[j] * (uint32_t)(unsigned long long)n;   // phase mod 1 turn, exact
+    const float turns = __uint2float_rn(u) * 2.3283064365386963e-10f;
+    return a.w + a.x * sinf(fmaf(6.2831853071795865f, turns, a.z));
+}
+
+// ------------------------------------------------------------------------ one scene, n steps
+
+template <int LPS, bool FLAT>
+__device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *fr, float *th,
+                          int n_steps, long long step0) {
+    const bool valid = s >= 0;
+    int p0 = 0, np = 0, l0 = 0, nl = 1;
+    if (valid) {
+        p0 = W.point_off[s]; np = W.point_off[s + 1] - p0;
+        l0 = W.link_off[s]; nl = W.link_off[s + 1] - l0;
+    }
+    const int j0 = l0 - (valid ? s : 0), nj = nl - 1;
+    // ---- load
+    float c[3], q[4], v[3], L[3], off[2];
+    uint32_t status = 1u;
+    float mu = 0.f;
+    int hm = -1;
+    if (valid) {
+        const int S = W.S;
+        c[0] = W.st[ST_CX * S + s]; c[1] = W.st[ST_CY * S + s]; c[2] = W.st[ST_CZ * S + s];
+        q[0] = W.st[ST_QW * S + s]; q[1] = W.st[ST_QX * S + s]; q[2] = W.st[ST_QY * S + s];
+        q[3] = W.st[ST_QZ * S + s];
+        v[0] = W.st[ST_VX * S + s]; v[1] = W.st[ST_VY * S + s]; v[2] = W.st[ST_VZ * S + s];
+        L[0] = W.st[ST_LX * S + s]; L[1] = W.st[ST_LY * S + s]; L[2] = W.st[ST_LZ * S + s];
+        off[0] = W.ref[s]; off[1] = W.ref[S + s];
+        status = W.status[s];
+        mu = W.mu[s];
+        hm = FLAT ? -1 : W.hmap[s];
+    } else {
+        c[0] = c[1] = c[2] = 0.f; q[0] = 1.f; q[1] = q[2] = q[3] = 0.f;
+        v[0] = v[1] = v[2] = 0.f; L[0] = L[1] = L[2] = 0.f; off[0] = off[1] = 0.f;
+    }
+    for (int j = gl; j < nj; j += LPS) th[j] = W.theta[j0 + j];
+    uint64_t kprev = 0;
+    for (int k = 0, i = gl; i < np; ++k, i += LPS)
+        if (W.kappa[p0 + i]) kprev |= 1ull << k;
+    __syncwarp();
+    Shape sh;
+    shape_setup<LPS>(W, p0, np, l0, nl, th, fr, pts, gl, sh);
+
+    const float dt = W.dt, kw2 = W.kw2, kc = W.kc;
+    const bool actuated = W.act_mode != 0;
+    int ph = (int)(step0 % (long long)W.K);
+    for (int t = 0; t < n_steps; ++t) {
+        const long long n = step0 + t;
+        const bool tick = actuated && ph == 0;
+        ph = (ph + 1 == W.K) ? 0 : ph + 1;
+        float R[9];
+        quat_mat(q, R);
+
+        // -- joint-angle determination: new angles, frames and mass properties
+        if (tick) {
+            if (status == 0u) {   // a frozen scene keeps its angles
+                for (int j = gl; j < nj; j += LPS) {
+                    const LinkDev lk = W.links[l0 + j + 1];
+                    th[j] = fminf(fmaxf(joint_target(W, j0 + j, n), lk.lo), lk.hi);
+                }
+            }
+            __syncwarp();
+            shape_props<LPS>(W, p0, np, l0, nl, th, fr, gl, sh);
+        }
+
+        float om[3];
+        world_sym(R, sh.Ii, L, om);
+
+        // -- collision and normal forces (pass 1); on joint-update steps also the new offsets
+        //    and the sums of the kinematic least squares
+        uint64_t know = 0;
+        float red[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (!tick) {
+            for (int k = 0, i = gl; i < np; ++k, i += LPS) {
+                const float4 r = pts[i];
+                const float rz = R[6] * r.x + R[7] * r.y + R[8] * r.z;
+                const float z = c[2] + rz;
+                float rx = 0.f, ry = 0.f, h = 0.f;
+                if (!FLAT) {
+                    rx = R[0] * r.x + R[1] * r.y + R[2] * r.z;
+                    ry = R[3] * r.x + R[4] * r.y + R[5] * r.z;
+                    h = ground<FLAT>(W, hm, c[0] + rx, c[1] + ry);
+                }
+                if (z < h) {
+                    know |= 1ull << k;
+                    if (FLAT) {
+                        rx = R[0] * r.x + R[1] * r.y + R[2] * r.z;
+                        ry = R[3] * r.x + R[4] * r.y + R[5] * r.z;
+                    }
+                    const float vz = v[2] + (om[0] * ry - om[1] * rx);
+                    const float F = fmaxf(0.f, r.w * (kw2 * (h - z) - kc * vz));
+                    red[0] += F;
+                    red[1] += ry * F;
+                    red[2] -= rx * F;
+                }
+            }
+            float r3[3] = {red[0], red[1], red[2]};
+            gsum<LPS, 3>(r3);
+            red[0] = r3[0]; red[1] = r3[1]; red[2] = r3[2];
+        } else {
+            for (int k = 0, i = gl; i < np; ++k, i += LPS) {
+                const float4 a = W.p0m[p0 + i];
+                float p[3];
+                fk_point(fr, a, W.plink[p0 + i], p);
+                const float4 ro = pts[i];
+                const float rn[3] = {p[0] - sh.g[0], p[1] - sh.g[1], p[2] - sh.g[2]};
+                pts[i] = make_float4(rn[0], rn[1], rn[2], a.w);
+                float rho[3];
+                mat_vec(R, rn, rho);
+                const float z = c[2] + rho[2];
+                const float h = ground<FLAT>(W, hm, c[0] + rho[0], c[1] + rho[1]);
+                if (z < h) {
+                    know |= 1ull << k;
+                    const float vz = v[2] + (om[0] * rho[1] - om[1] * rho[0]);
+                    const float F = fmaxf(0.f, a.w * (kw2 * (h - z) - kc * vz));
+                    red[0] += F;
+                    red[1] += rho[1] * F;
+                    red[2] -= rho[0] * F;
+                    if ((kprev >> k) & 1ull) {
+                        // kinematic slip back to the step-start position: R (r_old - r_new)
+                        const float ex = R[0] * (ro.x - rn[0]) + R[1] * (ro.y - rn[1]) + R[2] * (ro.z - rn[2]);
+                        const float ey = R[3] * (ro.x - rn[0]) + R[4] * (ro.y - rn[1]) + R[5] * (ro.z - rn[2]);
+                        const float sx = rho[0] - off[0], sy = rho[1] - off[1];
+                        red[3] += sx; red[4] += sy; red[5] += sx * sx + sy * sy;
+                        red[6] += ex; red[7] += ey; red[8] += sx * ey - sy * ex;
+                    }
+                }
+            }
+            __syncwarp();
+            gsum<LPS, 9>(red);
+        }
+        const float FN = red[0];
+
+        // -- semi-implicit Euler
+        float vs[3], Ls[3], cs[3], qs[4], oms[3], Rs[9];
+        const float iM = 1.0f / sh.M;
+        vs[0] = v[0] + dt * W.gx;
+        vs[1] = v[1] + dt * W.gy;
+        vs[2] = v[2] + dt * (W.gz + FN * iM);
+        Ls[0] = L[0] + dt * red[1];
+        Ls[1] = L[1] + dt * red[2];
+        Ls[2] = L[2];
+        world_sym(R, sh.Ii, Ls, oms);
+        cs[0] = c[0] + dt * vs[0]; cs[1] = c[1] + dt * vs[1]; cs[2] = c[2] + dt * vs[2];
+        {
+            const float px = dt * oms[0], py = dt * oms[1], pz = dt * oms[2];
+            const float a = sqrtf(px * px + py * py + pz * pz);
+            float dq[4] = {1.f, 0.f, 0.f, 0.f};
+            if (a > 0.f) {
+                float sn, cn;
+                sincosf(0.5f * a, &sn, &cn);
+                const float f = sn / a;
+                dq[0] = cn; dq[1] = f * px; dq[2] = f * py; dq[3] = f * pz;
+            }
+            quat_mul(dq, q, qs);
+            const float inv = rsqrtf(qs[0] * qs[0] + qs[1] * qs[1] + qs[2] * qs[2] + qs[3] * qs[3]);
+            qs[0] *= inv; qs[1] *= inv; qs[2] *= inv; qs[3] *= inv;
+        }
+        quat_mat(qs, Rs);
+
+        // -- friction (pass 2 over the points in contact in both steps)
+        float f7[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        {
+            const float dcx = c[0] - cs[0], dcy = c[1] - cs[1];
+            uint64_t cm = kprev & know;
+            while (cm) {
+                const int k = __ffsll((long long)cm) - 1;
+                cm &= cm - 1;
+                const float4 r = pts[gl + k * LPS];
+                const float rhx = R[0] * r.x + R[1] * r.y + R[2] * r.z;
+                const float rhy = R[3] * r.x + R[4] * r.y + R[5] * r.z;
+                const float rsx = Rs[0] * r.x + Rs[1] * r.y + Rs[2] * r.z;
+                const float rsy = Rs[3] * r.x + Rs[4] * r.y + Rs[5] * r.z;
+                const float sx = rsx - off[0], sy = rsy - off[1];
+                const float ex = dcx + rhx - rsx, ey = dcy + rhy - rsy;
+                f7[0] += 1.f;
+                f7[1] += sx; f7[2] += sy; f7[3] += sx * sx + sy * sy;
+                f7[4] += ex; f7[5] += ey; f7[6] += sx * ey - sy * ex;
+            }
+            gsum<LPS, 7>(f7);
+        }
+        float cn[3] = {cs[0], cs[1], cs[2]}, vn[3] = {vs[0], vs[1], vs[2]};
+        float Ln[3] = {Ls[0], Ls[1], Ls[2]}, qn[4] = {qs[0], qs[1], qs[2], qs[3]};
+        float offn[2] = {off[0], off[1]};
+        const float nC = f7[0];
+        if (nC >= 1.f) {
+            const float in = 1.0f / nC;
+            // dynamic least squares, centred on the contact centroid
+            const float sbx = f7[1] * in, sby = f7[2] * in;
+            const float S2 = f7[3] - nC * (sbx * sbx + sby * sby);
+            const float tDx = f7[4] * in, tDy = f7[5] * in;
+            const float X = f7[6] - (sbx * f7[5] - sby * f7[4]);
+            float a3 = (nC >= 2.f && S2 > 1e-12f) ? X / S2 : 0.f;
+            a3 = fminf(fmaxf(a3, -1.f), 1.f);
+            const float cD = sqrtf(fmaxf(0.f, 1.f - a3 * a3));
+            const float cm1 = -a3 * a3 / (1.f + cD);                  // cos(alpha_D) - 1
+            const float dDx = -(off[0] + sbx), dDy = -(off[1] + sby);  // CoG minus centroid
+            const float DDx = tDx + cm1 * dDx - a3 * dDy;               // uncapped CoG shift
+            const float DDy = tDy + a3 * dDx + cm1 * dDy;
+            // maximum static friction (Coulomb cap on the impulse that undoes the slip)
+            const float sh2 = a3 * a3 / (2.f * (1.f + cD));              // sin^2(alpha_D / 2)
+            const float u2 = tDx * tDx + tDy * tDy + 4.f * sh2 * S2 * in;
+            const float Jreq = sh.M * sqrtf(u2) / dt;
+            const float Jmax = mu * dt * FN;
+            const float sc = (Jreq <= Jmax) ? 1.f : Jmax / Jreq;
+            const float aD = asinf(a3);
+            float s1, c1;
+            sincosf(0.5f * sc * aD, &s1, &c1);
+            const float sin1 = 2.f * s1 * c1, cm1s = -2.f * s1 * s1;
+            float dx1 = sc * tDx + cm1s * dDx - sin1 * dDy;
+            float dy1 = sc * tDy + sin1 * dDx + cm1s * dDy;
+            float A = sc * aD;
+            if (tick) {
+                // kinematic least squares from the pass-1 sums (same contact set)
+                const float kbx = red[3] * in, kby = red[4] * in;
+                const float S2K = red[5] - nC * (kbx * kbx + kby * kby);
+                const float tKx = red[6] * in, tKy = red[7] * in;
+                const float XK = red[8] - (kbx * red[7] - kby * red[6]);
+                float a3K = (nC >= 2.f && S2K > 1e-12f) ? XK / S2K : 0.f;
+                a3K = fminf(fmaxf(a3K, -1.f), 1.f);
+                const float aK = asinf(a3K);
+                float s2, c2;
+                sincosf(0.5f * aK, &s2, &c2);
+                const float sin2 = 2.f * s2 * c2, cm2 = -2.f * s2 * s2;
+                // centroid of the moved points is c + off + kb; CoG after the dynamic map
+                const float dKx = (cs[0] - c[0]) + dx1 - (off[0] + kbx);
+                const float dKy = (cs[1] - c[1]) + dy1 - (off[1] + kby);
+                dx1 += tKx + cm2 * dKx - sin2 * dKy;
+                dy1 += tKy + sin2 * dKx + cm2 * dKy;
+                A += aK;
+            }
+            cn[0] = cs[0] + dx1;
+            cn[1] = cs[1] + dy1;
+            vn[0] = vs[0] + sc * DDx / dt;
+            vn[1] = vs[1] + sc * DDy / dt;
+            const float ez[3] = {0.f, 0.f, 1.f};
+            float Iz[3];
+            world_sym(Rs, sh.Ib, ez, Iz);
+            const float w = sc * aD / dt;
+            Ln[0] = Ls[0] + w * Iz[0]; Ln[1] = Ls[1] + w * Iz[1]; Ln[2] = Ls[2] + w * Iz[2];
+            float sa, ca;
+            sincosf(0.5f * A, &sa, &ca);
+            const float qz[4] = {ca, 0.f, 0.f, sa};
+            quat_mul(qz, qs, qn);
+            offn[0] = off[0] + sbx;
+            offn[1] = off[1] + sby;
+        }
+
+        // -- freeze a scene whose state is no longer finite or has left any sane range
+        if (status == 0u) {
+            bool fin = true;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) fin = fin && isfinite(cn[i]) && isfinite(vn[i]) && isfinite(Ln[i]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) fin = fin && isfinite(qn[i]);
+            if (!fin) {
+                status |= 1u;
+            } else if (fabsf(vn[0]) > 1e3f || fabsf(vn[1]) > 1e3f || fabsf(vn[2]) > 1e3f ||
+                       fabsf(cn[0]) > 1e6f || fabsf(cn[1]) > 1e6f || fabsf(cn[2]) > 1e6f) {
+                status |= 2u;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) { c[i] = cn[i]; v[i] = vn[i]; L[i] = Ln[i]; }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) q[i] = qn[i];
+                off[0] = offn[0]; off[1] = offn[1];
+                kprev = know;
+            }
+        }
+    }
+
+    // ---- write back (contact sensors from the last step's contacts)
+    uint32_t sens = 0;
+    for (int k = 0, i = gl; i < np; ++k, i += LPS) {
+        const uint8_t kb = (uint8_t)((kprev >> k) & 1ull);
+        W.kappa[p0 + i] = kb;
+        if (kb) {
+            const int sid = W.links[l0 + W.plink[p0 + i]].sensor;
+            if (sid >= 0 && sid < 32) sens |= 1u << sid;
+        }
+    }
+    sens = gor<LPS>(sens);
+    for (int j = gl; j < nj; j += LPS) W.theta[j0 + j] = th[j];
+    if (valid && gl == 0) {
+        const int S = W.S;
+        W.st[ST_CX * S + s] = c[0]; W.st[ST_CY * S + s] = c[1]; W.st[ST_CZ * S + s] = c[2];
+        W.st[ST_QW * S + s] = q[0]; W.st[ST_QX * S + s] = q[1]; W.st[ST_QY * S + s] = q[2];
+        W.st[ST_QZ * S + s] = q[3];
+        W.st[ST_VX * S + s] = v[0]; W.st[ST_VY * S + s] = v[1]; W.st[ST_VZ * S + s] = v[2];
+        W.st[ST_LX * S + s] = L[0]; W.st[ST_LY * S + s] = L[1]; W.st[ST_LZ * S + s] = L[2];
+        W.ref[s] = off[0]; W.ref[S + s] = off[1];
+        float R[9], om[3];
+        quat_mat(q, R);
+        world_sym(R, sh.Ii, L, om);
+        W.omega[s] = om[0]; W.omega[S + s] = om[1]; W.omega[2 * S + s] = om[2];
+        W.sensors[s] = sens;
+        W.status[s] = status;
+    }
+    __syncwarp();
+}
+
+template <int LPS, bool FLAT>
+__global__ void __launch_bounds__(512) step_kernel(WorldDev W, int n_steps, int sbytes) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int G = 32 / LPS;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane / LPS, gl = lane % LPS;
+    unsigned char *slot = smem + (size_t)(warp * G + g) * sbytes;
+    float4 *pts = reinterpret_cast<float4 *>(slot);
+    float *fr = reinterpret_cast<float *>(slot + 16 * W.max_points);
+    float *th = fr + 12 * W.max_links;
+    const long long step0 = *W.step;
+    const int n_items = (W.S + G - 1) / G;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = (int)atomicAdd(W.queue, 1u);
+        item = __shfl_sync(FULL_MASK, item, 0);
+        if (item >= n_items) break;
+        const int idx = item * G + g;
+        const int s = idx < W.S ? W.order[idx] : -1;
+        run_scene<LPS, FLAT>(W, s, gl, pts, fr, th, n_steps, step0);
+    }
+}
+
+__global__ void advance_kernel(long long *step, int n) { *step += n; }
+
+// ------------------------------------------------------------------------ state set-up and probes
+
+// One warp per scene: joint angles already in W.theta; origin/quat/vel/omega are the caller's
+// arrays (AoS, [S*3] / [S*4]).  CoG = origin + R g, L = R Ib R^T omega, contact history cleared.
+__global__ void __launch_bounds__(128) init_kernel(WorldDev W, const float *origin, const float *quat,
+                                                   const float *vel, const float *omega, int sbytes) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int s = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (s >= W.S) return;   // warp-uniform
+    unsigned char *slot = smem + (size_t)warp * sbytes;
+    float4 *pts = reinterpret_cast<float4 *>(slot);
+    float *fr = reinterpret_cast<float *>(slot + 16 * W.max_points);
+    float *th = fr + 12 * W.max_links;
+    const int p0 = W.point_off[s], np = W.point_off[s + 1] - p0;
+    const int l0 = W.link_off[s], nl = W.link_off[s + 1] - l0, j0 = l0 - s;
+    for (int j = lane; j < nl - 1; j += 32) th[j] = W.theta[j0 + j];
+    __syncwarp();
+    Shape sh;
+    shape_setup<32>(W, p0, np, l0, nl, th, fr, pts, lane, sh);
+    for (int i = lane; i < np; i += 32) W.kappa[p0 + i] = 0;
+    if (lane == 0) {
+        float q[4] = {quat[4 * s], quat[4 * s + 1], quat[4 * s + 2], quat[4 * s + 3]};
+        const float inv = 1.0f / sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        q[0] *= inv; q[1] *= inv; q[2] *= inv; q[3] *= inv;
+        float R[9], Rg[3], L[3];
+        quat_mat(q, R);
+        mat_vec(R, sh.g, Rg);
+        const float w[3] = {omega[3 * s], omega[3 * s + 1], omega[3 * s + 2]};
+        world_sym(R, sh.Ib, w, L);
+        const int S = W.S;
+        W.st[ST_CX * S + s] = origin[3 * s] + Rg[0];
+        W.st[ST_CY * S + s] = origin[3 * s + 1] + Rg[1];
+        W.st[ST_CZ * S + s] = origin[3 * s + 2] + Rg[2];
+        W.st[ST_QW * S + s] = q[0]; W.st[ST_QX * S + s] = q[1];
+        W.st[ST_QY * S + s] = q[2]; W.st[ST_QZ * S + s] = q[3];
+        W.st[ST_VX * S + s] = vel[3 * s]; W.st[ST_VY * S + s] = vel[3 * s + 1];
+        W.st[ST_VZ * S + s] = vel[3 * s + 2];
+        W.st[ST_LX * S + s] = L[0]; W.st[ST_LY * S + s] = L[1]; W.st[ST_LZ * S + s] = L[2];
+        W.ref[s] = 0.f; W.ref[S + s] = 0.f;
+        W.omega[s] = w[0]; W.omega[S + s] = w[1]; W.omega[2 * S + s] = w[2];
+        W.sensors[s] = 0u;
+        W.status[s] = 0u;
+    }
+}
+
+// Angular velocity of every scene from its state (one warp per scene), after a raw state write.
+__global__ void __launch_bounds__(128) refresh_kernel(WorldDev W, int sbytes) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int s = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (s >= W.S) return;   // warp-uniform
+    unsigned char *slot = smem + (size_t)warp * sbytes;
+    float4 *pts = reinterpret_cast<float4 *>(slot);
+    float *fr = reinterpret_cast<float *>(slot + 16 * W.max_points);
+    float *th = fr + 12 * W.max_links;
+    const int p0 = W.point_off[s], np = W.point_off[s + 1] - p0;
+    const int l0 = W.link_off[s], nl = W.link_off[s + 1] - l0, j0 = l0 - s;
+    for (int j = lane; j < nl - 1; j += 32) th[j] = W.theta[j0 + j];
+    __syncwarp();
+    Shape sh;
+    shape_setup<32>(W, p0, np, l0, nl, th, fr, pts, lane, sh);
+    if (lane == 0) {
+        const int S = W.S;
+        const float q[4] = {W.st[ST_QW * S + s], W.st[ST_QX * S + s], W.st[ST_QY * S + s],
+                            W.st[ST_QZ * S + s]};
+        const float L[3] = {W.st[ST_LX * S + s], W.st[ST_LY * S + s], W.st[ST_LZ * S + s]};
+        float R[9], om[3];
+        quat_mat(q, R);
+        world_sym(R, sh.Ii, L, om);
+        W.omega[s] = om[0]; W.omega[S + s] = om[1]; W.omega[2 * S + s] = om[2];
+    }
+}
+
+// World positions x_i = c + R r_i of one scene's points (one warp).
+__global__ void __launch_bounds__(32) points_kernel(WorldDev W, int s, float *out, int sbytes) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x;
+    float4 *pts = reinterpret_cast<float4 *>(smem);
+    float *fr = reinterpret_cast<float *>(smem + 16 * W.max_points);
+    float *th = fr + 12 * W.max_links;
+    const int p0 = W.point_off[s], np = W.point_off[s + 1] - p0;
+    const int l0 = W.link_off[s], nl = W.link_off[s + 1] - l0, j0 = l0 - s;
+    for (int j = lane; j < nl - 1; j += 32) th[j] = W.theta[j0 + j];
+    __syncwarp();
+    Shape sh;
+    shape_setup<32>(W, p0, np, l0, nl, th, fr, pts, lane, sh);
+    const int S = W.S;
+    const float c[3] = {W.st[ST_CX * S + s], W.st[ST_CY * S + s], W.st[ST_CZ * S + s]};
+    const float q[4] = {W.st[ST_QW * S + s], W.st[ST_QX * S + s], W.st[ST_QY * S + s],
+                        W.st[ST_QZ * S + s]};
+    float R[9];
+    quat_mat(q, R);
+    for (int i = lane; i < np; i += 32) {
+        const float4 r = pts[i];
+        const float rr[3] = {r.x, r.y, r.z};
+        float x[3];
+        mat_vec(R, rr, x);
+        out[3 * i] = c[0] + x[0]; out[3 * i + 1] = c[1] + x[1]; out[3 * i + 2] = c[2] + x[2];
+    }
+}
+
+// ------------------------------------------------------------------------ host-side launchers
+
+size_t step_smem_bytes(const WorldDev &W, int lps, int wpb) {
+    return (size_t)wpb * (32 / lps) * slot_bytes(W.max_points, W.max_links);
+}
+
+template <int LPS, bool FLAT>
+static void *step_fn() { return (void *)step_kernel<LPS, FLAT>; }
+
+static void *pick_step(int lps, bool flat) {
+    switch (lps) {
+        case 8: return flat ? step_fn<8, true>() : step_fn<8, false>();
+        case 16: return flat ? step_fn<16, true>() : step_fn<16, false>();
+        case 32: return flat ? step_fn<32, true>() : step_fn<32, false>();
+        default: return nullptr;
+    }
+}
+
+int step_blocks_per_sm(const WorldDev &W, int lps, int wpb, cudaError_t *err) {
+    void *fn = pick_step(lps, W.hm == nullptr);
+    *err = cudaSuccess;
+    if (!fn) { *err = cudaErrorInvalidValue; return 0; }
+    const size_t smem = step_smem_bytes(W, lps, wpb);
+    *err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (*err != cudaSuccess) return 0;
+    int nb = 0;
+    *err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, wpb * 32, smem);
+    return nb;
+}
+
+cudaError_t launch_step(const WorldDev &W, const LaunchCfg &cfg, int n_steps, cudaStream_t st) {
+    void *fn = pick_step(cfg.lps, W.hm == nullptr);
+    if (!fn || cfg.wpb < 1 || cfg.wpb > 16 || cfg.blocks < 1) return cudaErrorInvalidValue;
+    // the kernel's shared-memory limit was raised by step_blocks_per_sm for this shape
+    const size_t smem = step_smem_bytes(W, cfg.lps, cfg.wpb);
+    cudaError_t e = cudaMemsetAsync(W.queue, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    int sb = slot_bytes(W.max_points, W.max_links);
+    WorldDev w = W;
+    void *args[] = {&w, &n_steps, &sb};
+    return cudaLaunchKernel(fn, dim3(cfg.blocks), dim3(cfg.wpb * 32), args, smem, st);
+}
+
+cudaError_t launch_advance(long long *d_step, int n, cudaStream_t st) {
+    advance_kernel<<<1, 1, 0, st>>>(d_step, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(const WorldDev &W, const float *d_origin, const float *d_quat,
+                        const float *d_vel, const float *d_omega, cudaStream_t st) {
+    const int wpb = 4;
+    const int sb = slot_bytes(W.max_points, W.max_links);
+    const size_t smem = (size_t)wpb * sb;
+    cudaError_t e = cudaFuncSetAttribute((void *)init_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    init_kernel<<<(W.S + wpb - 1) / wpb, wpb * 32, smem, st>>>(W, d_origin, d_quat, d_vel, d_omega, sb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refresh(const WorldDev &W, cudaStream_t st) {
+    const int wpb = 4;
+    const int sb = slot_bytes(W.max_points, W.max_links);
+    const size_t smem = (size_t)wpb * sb;
+    cudaError_t e = cudaFuncSetAttribute((void *)refresh_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    refresh_kernel<<<(W.S + wpb - 1) / wpb, wpb * 32, smem, st>>>(W, sb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_points(const WorldDev &W, int scene, float *d_out, cudaStream_t st) {
+    const int sb = slot_bytes(W.max_points, W.max_links);
+    cudaError_t e = cudaFuncSetAttribute((void *)points_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+    if (e != cudaSuccess) return e;
+    points_kernel<<<1, 32, sb, st>>>(W, scene, d_out, sb);
+    return cudaGetLastError();
+}
+
+}  // namespace npx

@@ -1,0 +1,906 @@
+// npx_world.cpp -- host side of libnpx: the C-ABI of include/npx.h.
+//
+// Construction follows the paper's robot API (NeoPhysIx Sec. IV and Appendix: bodies made of
+// mass points, connectBodies, createJoint, finalizeConstruction); npx_scenes_add is the batched
+// equivalent for many scenes at once.  finalize packs every scene into the structure-of-arrays
+// device layout of npx_internal.h and orders the scenes by point count for the persistent step
+// kernel.  Stepping queues chunks of the step kernel on the world's stream, captured once per
+// step count into a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/npx.h"
+#include "npx_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(call)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(NPX_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                            \
+    } while (0)
+
+struct Body {
+    std::vector<float> xyz, m;
+    int sensor = -1;
+};
+
+struct JointDef {
+    int b1, b2;
+    float anchor[3], axis[3], lo, hi;
+};
+
+// A scene built body by body (the paper's API); converted to a Flat scene at finalize.
+struct Build {
+    std::vector<Body> bodies;
+    std::vector<std::pair<int, int>> glue;
+    std::vector<JointDef> joints;
+};
+
+// A scene in link form: link 0 root, link k hangs from parent[k] < k by joint k-1.
+struct Flat {
+    std::vector<int> parent, sensor;
+    std::vector<float> anchor, axis, lo, hi;
+    std::vector<float> p0, m;
+    std::vector<int> plink;
+};
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t n = 0;
+};
+
+}  // namespace
+
+struct npx_world {
+    npx_world_desc desc{};
+    cudaStream_t stream = nullptr;
+    int device = 0, n_sm = 0;
+    // construction
+    std::vector<Build> builds;
+    std::vector<Flat> flats;
+    std::vector<uint8_t> kind;          // 0 undefined, 1 build, 2 flat
+    std::vector<float> mu;
+    std::vector<int> hmap;
+    std::vector<float> hm_host;         // height maps until finalize uploads them
+    bool finalized = false;
+    // packed sizes
+    int S = 0, P = 0, L = 0, J = 0, max_points = 0, max_links = 0;
+    std::vector<int> link_off, point_off;
+    // device
+    std::vector<DevBuf> bufs;
+    npx::WorldDev W{};
+    long long *d_step = nullptr;
+    float *d_stage = nullptr;           // state_set staging [13 * S]
+    float *d_points = nullptr;          // points_read staging [3 * max_points]
+    long long step = 0;
+    // launch shape
+    npx::LaunchCfg cfg{32, 4, 0};
+    int chunk = 1000;
+    bool graphs = true;
+    std::map<int, cudaGraphExec_t> graph_cache;
+    long long launches = 0;
+    int act_mode = NPX_ACT_HOLD;
+};
+
+namespace {
+
+template <class T>
+int dev_alloc(npx_world *w, T **out, size_t count) {
+    void *p = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return fail(NPX_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    w->bufs.push_back({p, bytes});
+    *out = static_cast<T *>(p);
+    return NPX_OK;
+}
+
+int check_world(npx_world *w) {
+    if (!w) return fail(NPX_EINVAL, "null world");
+    return NPX_OK;
+}
+
+int check_building(npx_world *w, int scene) {
+    if (int rc = check_world(w)) return rc;
+    if (w->finalized) return fail(NPX_ESTATE, "world already finalized");
+    if (scene < 0 || scene >= w->desc.n_scenes) return fail(NPX_EINVAL, "scene %d out of range", scene);
+    return NPX_OK;
+}
+
+int check_ready(npx_world *w) {
+    if (int rc = check_world(w)) return rc;
+    if (!w->finalized) return fail(NPX_ESTATE, "world not finalized");
+    return NPX_OK;
+}
+
+Build &build_of(npx_world *w, int scene) {
+    if (w->kind[scene] != 1) {
+        w->builds[scene] = Build{};
+        w->flats[scene] = Flat{};
+        w->kind[scene] = 1;
+    }
+    return w->builds[scene];
+}
+
+int find_root(std::vector<int> &par, int x) {
+    while (par[x] != x) x = par[x] = par[par[x]];
+    return x;
+}
+
+// Turn a body-by-body scene into link form: links = groups of glued bodies; the root link holds
+// body 0; joints orient the link tree away from it (body1 on the parent side).
+int build_to_flat(const Build &b, int scene, Flat &f) {
+    const int nb = (int)b.bodies.size();
+    if (nb == 0) return fail(NPX_EINVAL, "scene %d has no bodies", scene);
+    std::vector<int> uf(nb);
+    std::iota(uf.begin(), uf.end(), 0);
+    for (auto &g : b.glue) uf[find_root(uf, g.second)] = find_root(uf, g.first);
+    std::vector<int> comp(nb, -1), comp_root;
+    for (int i = 0; i < nb; ++i) {
+        int r = find_root(uf, i);
+        if (comp[r] < 0) { comp[r] = (int)comp_root.size(); comp_root.push_back(r); }
+        comp[i] = comp[r];
+    }
+    const int nc = (int)comp_root.size();
+    if ((int)b.joints.size() != nc - 1)
+        return fail(NPX_EINVAL, "scene %d: %d links need %d joints, got %zu", scene, nc, nc - 1,
+                    b.joints.size());
+    // breadth-first order from the root link
+    std::vector<int> order{comp[0]}, link_of(nc, -1), pj(nc, -1);
+    link_of[comp[0]] = 0;
+    for (size_t h = 0; h < order.size(); ++h) {
+        for (int j = 0; j < (int)b.joints.size(); ++j) {
+            const JointDef &jd = b.joints[j];
+            int c1 = comp[jd.b1], c2 = comp[jd.b2];
+            if (c1 != order[h]) continue;
+            if (link_of[c2] >= 0)
+                return fail(NPX_EINVAL, "scene %d: joint %d closes a loop", scene, j);
+            link_of[c2] = (int)order.size();
+            pj[link_of[c2]] = j;
+            order.push_back(c2);
+        }
+    }
+    if ((int)order.size() != nc)
+        return fail(NPX_EINVAL, "scene %d: joints do not connect every link to the root "
+                                "(body1 must be on the root side)", scene);
+    f = Flat{};
+    f.parent.assign(nc, -1);
+    f.sensor.assign(nc, -1);
+    f.anchor.assign(3 * nc, 0.f);
+    f.axis.assign(3 * nc, 0.f);
+    f.lo.assign(nc, 0.f);
+    f.hi.assign(nc, 0.f);
+    for (int k = 1; k < nc; ++k) {
+        const JointDef &jd = b.joints[pj[k]];
+        f.parent[k] = link_of[comp[jd.b1]];
+        for (int a = 0; a < 3; ++a) { f.anchor[3 * k + a] = jd.anchor[a]; f.axis[3 * k + a] = jd.axis[a]; }
+        f.lo[k] = jd.lo;
+        f.hi[k] = jd.hi;
+    }
+    for (int k = 0; k < nc; ++k) {
+        for (int i = 0; i < nb; ++i) {
+            if (comp[i] != order[k]) continue;
+            const Body &bd = b.bodies[i];
+            if (bd.sensor >= 0) f.sensor[k] = bd.sensor;
+            for (size_t p = 0; p < bd.m.size(); ++p) {
+                f.p0.insert(f.p0.end(), bd.xyz.begin() + 3 * p, bd.xyz.begin() + 3 * p + 3);
+                f.m.push_back(bd.m[p]);
+                f.plink.push_back(k);
+            }
+        }
+    }
+    return NPX_OK;
+}
+
+int check_flat(const Flat &f, int scene) {
+    const int nl = (int)f.parent.size(), np = (int)f.m.size();
+    if (nl < 1 || nl > NPX_MAX_LINKS) return fail(NPX_ERANGE, "scene %d: %d links (1..%d)", scene, nl, NPX_MAX_LINKS);
+    if (np < 1 || np > NPX_MAX_POINTS) return fail(NPX_ERANGE, "scene %d: %d points (1..%d)", scene, np, NPX_MAX_POINTS);
+    if (f.parent[0] != -1) return fail(NPX_EINVAL, "scene %d: link 0 must be the root", scene);
+    for (int k = 1; k < nl; ++k) {
+        if (f.parent[k] < 0 || f.parent[k] >= k) return fail(NPX_EINVAL, "scene %d: link %d parent %d not in [0,%d)", scene, k, f.parent[k], k);
+        double n2 = 0;
+        for (int a = 0; a < 3; ++a) n2 += (double)f.axis[3 * k + a] * f.axis[3 * k + a];
+        if (!(n2 > 0.0) || !std::isfinite(n2)) return fail(NPX_EINVAL, "scene %d: link %d has a zero axis", scene, k);
+        if (!(f.lo[k] <= f.hi[k])) return fail(NPX_EINVAL, "scene %d: link %d limits lo > hi", scene, k);
+    }
+    for (int k = 0; k < nl; ++k)
+        if (f.sensor[k] >= NPX_MAX_SENSORS) return fail(NPX_ERANGE, "scene %d: sensor bit %d >= %d", scene, f.sensor[k], NPX_MAX_SENSORS);
+    for (int i = 0; i < np; ++i) {
+        if (!(f.m[i] > 0.f) || !std::isfinite(f.m[i])) return fail(NPX_EINVAL, "scene %d: point %d mass must be > 0", scene, i);
+        if (f.plink[i] < 0 || f.plink[i] >= nl) return fail(NPX_EINVAL, "scene %d: point %d link out of range", scene, i);
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(f.p0[3 * i + a])) return fail(NPX_EINVAL, "scene %d: point %d not finite", scene, i);
+    }
+    return NPX_OK;
+}
+
+npx::LaunchCfg clamp_cfg(npx_world *w, npx::LaunchCfg c, int *rc) {
+    *rc = NPX_OK;
+    if (w->max_points > 64 * c.lps) {
+        *rc = fail(NPX_ERANGE, "%d points per scene exceed 64 per lane at %d lanes per scene",
+                   w->max_points, c.lps);
+        return c;
+    }
+    cudaError_t e;
+    int nb = npx::step_blocks_per_sm(w->W, c.lps, c.wpb, &e);
+    if (e != cudaSuccess) { *rc = fail(NPX_ECUDA, "occupancy query: %s", cudaGetErrorString(e)); return c; }
+    if (nb < 1) { *rc = fail(NPX_ERANGE, "launch shape lps=%d wpb=%d does not fit on an SM", c.lps, c.wpb); return c; }
+    const int per_block = c.wpb * (32 / c.lps);
+    const int need = (w->S + per_block - 1) / per_block;
+    const int full = nb * w->n_sm;
+    if (c.blocks <= 0 || c.blocks > full) c.blocks = full;
+    c.blocks = std::max(1, std::min(c.blocks, need));
+    return c;
+}
+
+void clear_graphs(npx_world *w) {
+    for (auto &kv : w->graph_cache) cudaGraphExecDestroy(kv.second);
+    w->graph_cache.clear();
+}
+
+int enqueue_steps(npx_world *w, int n) {
+    for (int done = 0; done < n;) {
+        const int nc = std::min(w->chunk, n - done);
+        CUDA_TRY(npx::launch_step(w->W, w->cfg, nc, w->stream));
+        CUDA_TRY(npx::launch_advance(w->d_step, nc, w->stream));
+        done += nc;
+    }
+    return NPX_OK;
+}
+
+struct BlobLayout {
+    size_t st, theta, ref, omega, kappa, sensors, status, end;
+};
+
+BlobLayout blob_layout(const npx_world *w) {
+    BlobLayout b;
+    b.st = 64;
+    b.theta = b.st + sizeof(float) * (size_t)npx::ST_N * w->S;
+    b.ref = b.theta + sizeof(float) * (size_t)w->J;
+    b.omega = b.ref + sizeof(float) * 2 * (size_t)w->S;
+    b.sensors = b.omega + sizeof(float) * 3 * (size_t)w->S;
+    b.status = b.sensors + sizeof(uint32_t) * (size_t)w->S;
+    b.kappa = b.status + sizeof(uint32_t) * (size_t)w->S;
+    b.end = b.kappa + (size_t)w->P;
+    return b;
+}
+
+const uint64_t kBlobMagic = 0x315850584e504e47ull;
+
+}  // namespace
+
+extern "C" {
+
+const char *npx_last_error(void) { return g_err.c_str(); }
+
+int npx_world_create(const npx_world_desc *d, npx_world **out) {
+    if (!d || !out) return fail(NPX_EINVAL, "null argument");
+    *out = nullptr;
+    if (d->n_scenes < 1) return fail(NPX_EINVAL, "n_scenes must be >= 1");
+    if (!(d->dt > 0.f) || !std::isfinite(d->dt)) return fail(NPX_EINVAL, "dt must be > 0");
+    if (d->joint_update_steps < 1) return fail(NPX_EINVAL, "joint_update_steps must be >= 1");
+    if (!(d->contact_omega > 0.f) || !(d->contact_zeta >= 0.f))
+        return fail(NPX_EINVAL, "contact_omega must be > 0 and contact_zeta >= 0");
+    if (d->hm_count < 0) return fail(NPX_EINVAL, "hm_count < 0");
+    if (d->hm_count > 0 && (!d->hm_data || d->hm_nx < 1 || d->hm_ny < 1 || !(d->hm_scale > 0.f)))
+        return fail(NPX_EINVAL, "height maps need data, nx, ny >= 1 and scale > 0");
+    if (d->device < 0) return fail(NPX_EINVAL, "device %d out of range", d->device);
+    npx_world *w = new (std::nothrow) npx_world();
+    if (!w) return fail(NPX_ENOMEM, "out of host memory");
+    w->desc = *d;
+    w->desc.hm_data = nullptr;
+    w->device = d->device;
+    w->stream = static_cast<cudaStream_t>(d->stream);
+    const int S = d->n_scenes;
+    w->builds.resize(S);
+    w->flats.resize(S);
+    w->kind.assign(S, 0);
+    w->mu.assign(S, 0.5f);
+    w->hmap.assign(S, d->hm_count > 0 ? 0 : -1);
+    // the caller's height maps are copied now and uploaded at finalize
+    if (d->hm_count > 0)
+        w->hm_host.assign(d->hm_data, d->hm_data + (size_t)d->hm_count * d->hm_ny * d->hm_nx);
+    *out = w;
+    return NPX_OK;
+}
+
+int npx_world_destroy(npx_world *w) {
+    if (!w) return NPX_OK;
+    if (!w->bufs.empty()) {
+        cudaSetDevice(w->device);
+        if (w->finalized) cudaStreamSynchronize(w->stream);
+        clear_graphs(w);
+        for (auto &b : w->bufs) cudaFree(b.p);
+    }
+    delete w;
+    return NPX_OK;
+}
+
+int npx_body_add_pointcloud(npx_world *w, int scene, const float *xyz, const float *mass,
+                            float total_mass, int n, int *out_body) {
+    if (int rc = check_building(w, scene)) return rc;
+    if (!xyz || n < 1) return fail(NPX_EINVAL, "need n >= 1 points");
+    if (!mass && !(total_mass > 0.f)) return fail(NPX_EINVAL, "total_mass must be > 0");
+    Build &b = build_of(w, scene);
+    Body bd;
+    bd.xyz.assign(xyz, xyz + 3 * (size_t)n);
+    if (mass) bd.m.assign(mass, mass + n);
+    else bd.m.assign(n, total_mass / (float)n);
+    b.bodies.push_back(std::move(bd));
+    if (out_body) *out_body = (int)b.bodies.size() - 1;
+    return NPX_OK;
+}
+
+int npx_body_connect(npx_world *w, int scene, int body1, int body2) {
+    if (int rc = check_building(w, scene)) return rc;
+    if (w->kind[scene] != 1) return fail(NPX_ESTATE, "scene %d has no bodies", scene);
+    Build &b = w->builds[scene];
+    const int nb = (int)b.bodies.size();
+    if (body1 < 0 || body1 >= nb || body2 < 0 || body2 >= nb) return fail(NPX_EINVAL, "body id out of range");
+    b.glue.push_back({body1, body2});
+    return NPX_OK;
+}
+
+int npx_joint_add(npx_world *w, int scene, int body1, int body2, const float anchor[3],
+                  const float axis[3], float lo, float hi, int *out_joint) {
+    if (int rc = check_building(w, scene)) return rc;
+    if (w->kind[scene] != 1) return fail(NPX_ESTATE, "scene %d has no bodies", scene);
+    if (!anchor || !axis) return fail(NPX_EINVAL, "null anchor or axis");
+    Build &b = w->builds[scene];
+    const int nb = (int)b.bodies.size();
+    if (body1 < 0 || body1 >= nb || body2 < 0 || body2 >= nb || body1 == body2)
+        return fail(NPX_EINVAL, "body id out of range");
+    if (!(lo <= hi)) return fail(NPX_EINVAL, "joint limits lo > hi");
+    JointDef j{body1, body2, {anchor[0], anchor[1], anchor[2]}, {axis[0], axis[1], axis[2]}, lo, hi};
+    b.joints.push_back(j);
+    if (out_joint) *out_joint = (int)b.joints.size() - 1;
+    return NPX_OK;
+}
+
+int npx_sensor_add(npx_world *w, int scene, int body, int bit) {
+    if (int rc = check_building(w, scene)) return rc;
+    if (w->kind[scene] != 1) return fail(NPX_ESTATE, "scene %d has no bodies", scene);
+    Build &b = w->builds[scene];
+    if (body < 0 || body >= (int)b.bodies.size()) return fail(NPX_EINVAL, "body id out of range");
+    if (bit < 0 || bit >= NPX_MAX_SENSORS) return fail(NPX_ERANGE, "sensor bit %d out of range", bit);
+    b.bodies[body].sensor = bit;
+    return NPX_OK;
+}
+
+int npx_scene_set_friction(npx_world *w, int scene, float mu) {
+    if (int rc = check_building(w, scene)) return rc;
+    if (!(mu >= 0.f) || !std::isfinite(mu)) return fail(NPX_EINVAL, "mu must be >= 0");
+    w->mu[scene] = mu;
+    return NPX_OK;
+}
+
+int npx_scene_set_heightmap(npx_world *w, int scene, int hm) {
+    if (int rc = check_building(w, scene)) return rc;
+    if (hm < -1 || hm >= w->desc.hm_count) return fail(NPX_EINVAL, "height map %d out of range", hm);
+    w->hmap[scene] = hm;
+    return NPX_OK;
+}
+
+int npx_scene_clone(npx_world *w, int src, int first_dst, int count) {
+    if (int rc = check_building(w, src)) return rc;
+    if (count < 0 || first_dst < 0 || (long long)first_dst + count > w->desc.n_scenes)
+        return fail(NPX_EINVAL, "clone range out of bounds");
+    if (w->kind[src] == 0) return fail(NPX_ESTATE, "scene %d is not defined", src);
+    for (int d = first_dst; d < first_dst + count; ++d) {
+        if (d == src) continue;
+        w->kind[d] = w->kind[src];
+        if (w->kind[src] == 1) w->builds[d] = w->builds[src];
+        else w->flats[d] = w->flats[src];
+        w->mu[d] = w->mu[src];
+        w->hmap[d] = w->hmap[src];
+    }
+    return NPX_OK;
+}
+
+int npx_scenes_add(npx_world *w, const npx_scene_batch *b) {
+    if (int rc = check_world(w)) return rc;
+    if (w->finalized) return fail(NPX_ESTATE, "world already finalized");
+    if (!b || !b->link_off || !b->point_off || !b->parent || !b->anchor || !b->axis || !b->lo ||
+        !b->hi || !b->sensor || !b->p0 || !b->m || !b->plink || !b->mu)
+        return fail(NPX_EINVAL, "null array in scene batch");
+    if (b->count < 0 || b->first < 0 || (long long)b->first + b->count > w->desc.n_scenes)
+        return fail(NPX_EINVAL, "scene range [%d, %d) out of bounds", b->first, b->first + b->count);
+    if (b->link_off[0] != 0 || b->point_off[0] != 0) return fail(NPX_EINVAL, "offsets must start at 0");
+    for (int s = 0; s < b->count; ++s) {
+        const int l0 = b->link_off[s], l1 = b->link_off[s + 1];
+        const int p0 = b->point_off[s], p1 = b->point_off[s + 1];
+        if (l1 <= l0 || p1 <= p0) return fail(NPX_EINVAL, "scene %d: empty links or points", b->first + s);
+        const int sc = b->first + s;
+        Flat f;
+        f.parent.assign(b->parent + l0, b->parent + l1);
+        f.sensor.assign(b->sensor + l0, b->sensor + l1);
+        f.anchor.assign(b->anchor + 3 * (size_t)l0, b->anchor + 3 * (size_t)l1);
+        f.axis.assign(b->axis + 3 * (size_t)l0, b->axis + 3 * (size_t)l1);
+        f.lo.assign(b->lo + l0, b->lo + l1);
+        f.hi.assign(b->hi + l0, b->hi + l1);
+        f.p0.assign(b->p0 + 3 * (size_t)p0, b->p0 + 3 * (size_t)p1);
+        f.m.assign(b->m + p0, b->m + p1);
+        f.plink.assign(b->plink + p0, b->plink + p1);
+        if (int rc = check_flat(f, sc)) return rc;
+        w->flats[sc] = std::move(f);
+        w->builds[sc] = Build{};
+        w->kind[sc] = 2;
+        if (!(b->mu[s] >= 0.f) || !std::isfinite(b->mu[s])) return fail(NPX_EINVAL, "scene %d: mu must be >= 0", sc);
+        w->mu[sc] = b->mu[s];
+        const int hm = b->hmap ? b->hmap[s] : (w->desc.hm_count > 0 ? 0 : -1);
+        if (hm < -1 || hm >= w->desc.hm_count) return fail(NPX_EINVAL, "scene %d: height map %d out of range", sc, hm);
+        w->hmap[sc] = hm;
+    }
+    return NPX_OK;
+}
+
+int npx_world_finalize(npx_world *w) {
+    if (int rc = check_world(w)) return rc;
+    if (w->finalized) return fail(NPX_ESTATE, "world already finalized");
+    const int S = w->desc.n_scenes;
+    for (int s = 0; s < S; ++s) {
+        if (w->kind[s] == 0) return fail(NPX_ESTATE, "scene %d is not defined", s);
+        if (w->kind[s] == 1) {
+            if (int rc = build_to_flat(w->builds[s], s, w->flats[s])) return rc;
+            if (int rc = check_flat(w->flats[s], s)) return rc;
+            w->builds[s] = Build{};
+            w->kind[s] = 2;
+        }
+    }
+    // ---- pack
+    w->S = S;
+    w->link_off.assign(S + 1, 0);
+    w->point_off.assign(S + 1, 0);
+    for (int s = 0; s < S; ++s) {
+        w->link_off[s + 1] = w->link_off[s] + (int)w->flats[s].parent.size();
+        w->point_off[s + 1] = w->point_off[s] + (int)w->flats[s].m.size();
+        w->max_links = std::max(w->max_links, (int)w->flats[s].parent.size());
+        w->max_points = std::max(w->max_points, (int)w->flats[s].m.size());
+    }
+    w->L = w->link_off[S];
+    w->P = w->point_off[S];
+    w->J = w->L - S;
+    std::vector<npx::LinkDev> links(w->L);
+    std::vector<float4> p0m(w->P);
+    std::vector<uint8_t> plink(w->P);
+    for (int s = 0; s < S; ++s) {
+        const Flat &f = w->flats[s];
+        const int l0 = w->link_off[s], p0 = w->point_off[s], nl = (int)f.parent.size();
+        std::vector<int> depth(nl, 0);
+        for (int k = 0; k < nl; ++k) {
+            npx::LinkDev &ld = links[l0 + k];
+            if (k > 0) depth[k] = depth[f.parent[k]] + 1;
+            double ux = f.axis[3 * k], uy = f.axis[3 * k + 1], uz = f.axis[3 * k + 2];
+            double un = std::sqrt(ux * ux + uy * uy + uz * uz);
+            if (k == 0) { ux = 0; uy = 0; uz = 1; un = 1; }
+            ld = {f.anchor[3 * k], f.anchor[3 * k + 1], f.anchor[3 * k + 2], f.lo[k],
+                  (float)(ux / un), (float)(uy / un), (float)(uz / un), f.hi[k],
+                  f.parent[k], f.sensor[k], depth[k], 0};
+        }
+        for (size_t i = 0; i < f.m.size(); ++i) {
+            p0m[p0 + i] = make_float4(f.p0[3 * i], f.p0[3 * i + 1], f.p0[3 * i + 2], f.m[i]);
+            plink[p0 + i] = (uint8_t)f.plink[i];
+        }
+    }
+    // persistent schedule: most points first (longest jobs start first)
+    std::vector<int> order(S);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return w->point_off[a + 1] - w->point_off[a] > w->point_off[b + 1] - w->point_off[b];
+    });
+    // ---- device
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev < 1) return fail(NPX_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    if (w->device >= ndev) return fail(NPX_EINVAL, "device %d out of range (%d devices)", w->device, ndev);
+    CUDA_TRY(cudaSetDevice(w->device));
+    CUDA_TRY(cudaDeviceGetAttribute(&w->n_sm, cudaDevAttrMultiProcessorCount, w->device));
+    npx::WorldDev &W = w->W;
+    if (!w->hm_host.empty()) {
+        float *hm = nullptr;
+        if (int rc = dev_alloc(w, &hm, w->hm_host.size())) return rc;
+        CUDA_TRY(cudaMemcpy(hm, w->hm_host.data(), w->hm_host.size() * sizeof(float), cudaMemcpyHostToDevice));
+        W.hm = hm;
+        w->hm_host.clear();
+        w->hm_host.shrink_to_fit();
+    }
+    W.S = S; W.P = w->P; W.L = w->L; W.J = w->J;
+    int *d_lo, *d_po, *d_hmap, *d_order;
+    float4 *d_p0m, *d_act;
+    uint8_t *d_plink, *d_kappa;
+    npx::LinkDev *d_links;
+    float *d_mu, *d_st, *d_theta, *d_ref, *d_omega;
+    uint32_t *d_nu, *d_sens, *d_status;
+    unsigned int *d_queue;
+    int rc = 0;
+    if ((rc = dev_alloc(w, &d_lo, S + 1)) || (rc = dev_alloc(w, &d_po, S + 1)) ||
+        (rc = dev_alloc(w, &d_hmap, S)) || (rc = dev_alloc(w, &d_order, S)) ||
+        (rc = dev_alloc(w, &d_p0m, w->P)) || (rc = dev_alloc(w, &d_plink, w->P)) ||
+        (rc = dev_alloc(w, &d_links, w->L)) || (rc = dev_alloc(w, &d_mu, S)) ||
+        (rc = dev_alloc(w, &d_act, w->J)) || (rc = dev_alloc(w, &d_nu, w->J)) ||
+        (rc = dev_alloc(w, &d_st, (size_t)npx::ST_N * S)) || (rc = dev_alloc(w, &d_theta, w->J)) ||
+        (rc = dev_alloc(w, &d_kappa, w->P)) || (rc = dev_alloc(w, &d_ref, 2 * (size_t)S)) ||
+        (rc = dev_alloc(w, &d_omega, 3 * (size_t)S)) || (rc = dev_alloc(w, &d_sens, S)) ||
+        (rc = dev_alloc(w, &d_status, S)) || (rc = dev_alloc(w, &d_queue, 1)) ||
+        (rc = dev_alloc(w, &w->d_step, 1)) || (rc = dev_alloc(w, &w->d_stage, 13 * (size_t)S)) ||
+        (rc = dev_alloc(w, &w->d_points, 3 * (size_t)w->max_points)))
+        return rc;
+    CUDA_TRY(cudaMemcpy(d_lo, w->link_off.data(), sizeof(int) * (S + 1), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_po, w->point_off.data(), sizeof(int) * (S + 1), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_hmap, w->hmap.data(), sizeof(int) * S, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_order, order.data(), sizeof(int) * S, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_p0m, p0m.data(), sizeof(float4) * w->P, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_plink, plink.data(), w->P, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_links, links.data(), sizeof(npx::LinkDev) * w->L, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_mu, w->mu.data(), sizeof(float) * S, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemset(d_act, 0, sizeof(float4) * std::max(w->J, 1)));
+    CUDA_TRY(cudaMemset(d_nu, 0, sizeof(uint32_t) * std::max(w->J, 1)));
+    CUDA_TRY(cudaMemset(d_theta, 0, sizeof(float) * std::max(w->J, 1)));
+    CUDA_TRY(cudaMemset(w->d_step, 0, sizeof(long long)));
+    W.link_off = d_lo; W.point_off = d_po; W.p0m = d_p0m; W.plink = d_plink; W.links = d_links;
+    W.mu = d_mu; W.hmap = d_hmap;
+    W.hm_nx = w->desc.hm_nx; W.hm_ny = w->desc.hm_ny;
+    W.hm_scale = w->desc.hm_scale; W.hm_ox = w->desc.hm_origin[0]; W.hm_oy = w->desc.hm_origin[1];
+    W.dt = w->desc.dt;
+    W.gx = w->desc.gravity[0]; W.gy = w->desc.gravity[1]; W.gz = w->desc.gravity[2];
+    W.K = w->desc.joint_update_steps;
+    W.kw2 = w->desc.contact_omega * w->desc.contact_omega;
+    W.kc = 2.f * w->desc.contact_zeta * w->desc.contact_omega;
+    W.act_mode = NPX_ACT_HOLD;
+    W.act = d_act; W.act_nu = d_nu;
+    W.st = d_st; W.theta = d_theta; W.kappa = d_kappa; W.ref = d_ref; W.omega = d_omega;
+    W.sensors = d_sens; W.status = d_status;
+    W.order = d_order; W.max_points = w->max_points; W.max_links = w->max_links;
+    W.step = w->d_step; W.queue = d_queue;
+    w->finalized = true;
+    w->flats.clear();
+    w->flats.shrink_to_fit();
+    w->builds.clear();
+    w->builds.shrink_to_fit();
+    // default launch shape: widest group that holds the largest scene
+    int lps = 8;
+    while (lps < 32 && w->max_points > 64 * lps) lps *= 2;
+    if (w->max_points > 64 * 32) return fail(NPX_ERANGE, "scene too large");
+    if (lps < 16) lps = 16;
+    int rc2;
+    npx::LaunchCfg c = clamp_cfg(w, {lps, 4, 0}, &rc2);
+    if (rc2) return rc2;
+    w->cfg = c;
+    // construction pose, at rest
+    std::vector<float> zero(3 * (size_t)S, 0.f), quat(4 * (size_t)S, 0.f);
+    for (int s = 0; s < S; ++s) quat[4 * s] = 1.f;
+    return npx_state_set(w, zero.data(), quat.data(), zero.data(), zero.data(), nullptr);
+}
+
+int npx_state_set(npx_world *w, const float *origin, const float *quat, const float *vel,
+                  const float *omega, const float *theta) {
+    if (int rc = check_ready(w)) return rc;
+    if (!origin || !quat || !vel || !omega) return fail(NPX_EINVAL, "null state array");
+    CUDA_TRY(cudaSetDevice(w->device));
+    const size_t S = w->S;
+    float *d = w->d_stage;
+    CUDA_TRY(cudaMemcpyAsync(d, origin, 3 * S * sizeof(float), cudaMemcpyHostToDevice, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(d + 3 * S, quat, 4 * S * sizeof(float), cudaMemcpyHostToDevice, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(d + 7 * S, vel, 3 * S * sizeof(float), cudaMemcpyHostToDevice, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(d + 10 * S, omega, 3 * S * sizeof(float), cudaMemcpyHostToDevice, w->stream));
+    if (theta && w->J > 0)
+        CUDA_TRY(cudaMemcpyAsync(w->W.theta, theta, w->J * sizeof(float), cudaMemcpyHostToDevice, w->stream));
+    CUDA_TRY(npx::launch_init(w->W, d, d + 3 * S, d + 7 * S, d + 10 * S, w->stream));
+    CUDA_TRY(cudaStreamSynchronize(w->stream));
+    return NPX_OK;
+}
+
+int npx_state_write(npx_world *w, const float *cog, const float *quat, const float *vel,
+                    const float *angmom, const float *theta, const uint8_t *contact_prev,
+                    int64_t step) {
+    if (int rc = check_ready(w)) return rc;
+    if (!cog || !quat || !vel || !angmom) return fail(NPX_EINVAL, "null state array");
+    if (step < 0) return fail(NPX_EINVAL, "step must be >= 0");
+    CUDA_TRY(cudaSetDevice(w->device));
+    const size_t S = w->S;
+    std::vector<float> st((size_t)npx::ST_N * S);
+    for (size_t s = 0; s < S; ++s) {
+        for (int k = 0; k < 3; ++k) {
+            st[(npx::ST_CX + k) * S + s] = cog[3 * s + k];
+            st[(npx::ST_VX + k) * S + s] = vel[3 * s + k];
+            st[(npx::ST_LX + k) * S + s] = angmom[3 * s + k];
+        }
+        for (int k = 0; k < 4; ++k) st[(npx::ST_QW + k) * S + s] = quat[4 * s + k];
+    }
+    CUDA_TRY(cudaMemcpyAsync(w->W.st, st.data(), st.size() * sizeof(float), cudaMemcpyHostToDevice, w->stream));
+    if (theta && w->J > 0)
+        CUDA_TRY(cudaMemcpyAsync(w->W.theta, theta, w->J * sizeof(float), cudaMemcpyHostToDevice, w->stream));
+    if (contact_prev) CUDA_TRY(cudaMemcpyAsync(w->W.kappa, contact_prev, w->P, cudaMemcpyHostToDevice, w->stream));
+    else CUDA_TRY(cudaMemsetAsync(w->W.kappa, 0, w->P, w->stream));
+    CUDA_TRY(cudaMemsetAsync(w->W.ref, 0, 2 * S * sizeof(float), w->stream));
+    CUDA_TRY(cudaMemsetAsync(w->W.status, 0, S * sizeof(uint32_t), w->stream));
+    const long long st64 = step;
+    CUDA_TRY(cudaMemcpyAsync(w->d_step, &st64, sizeof st64, cudaMemcpyHostToDevice, w->stream));
+    CUDA_TRY(npx::launch_refresh(w->W, w->stream));
+    CUDA_TRY(cudaStreamSynchronize(w->stream));
+    w->step = step;
+    return NPX_OK;
+}
+
+int npx_contacts_read(npx_world *w, uint8_t *contact, size_t n) {
+    if (int rc = check_ready(w)) return rc;
+    if (!contact || n < (size_t)w->P) return fail(NPX_EINVAL, "buffer holds %zu flags, world has %d points", n, w->P);
+    CUDA_TRY(cudaSetDevice(w->device));
+    CUDA_TRY(cudaMemcpyAsync(contact, w->W.kappa, w->P, cudaMemcpyDeviceToHost, w->stream));
+    CUDA_TRY(cudaStreamSynchronize(w->stream));
+    return NPX_OK;
+}
+
+int npx_actuator_set(npx_world *w, int mode, const float *params) {
+    if (int rc = check_ready(w)) return rc;
+    if (mode != NPX_ACT_HOLD && mode != NPX_ACT_SINUSOID) return fail(NPX_EINVAL, "unknown actuator mode %d", mode);
+    CUDA_TRY(cudaSetDevice(w->device));
+    if (mode == NPX_ACT_SINUSOID && w->J > 0) {
+        if (!params) return fail(NPX_EINVAL, "sinusoid mode needs params");
+        std::vector<float4> act(w->J);
+        std::vector<uint32_t> nu(w->J);
+        for (int j = 0; j < w->J; ++j) {
+            const float *p = params + 4 * (size_t)j;
+            for (int a = 0; a < 4; ++a)
+                if (!std::isfinite(p[a])) return fail(NPX_EINVAL, "joint %d: non-finite actuator parameter", j);
+            act[j] = make_float4(p[0], p[1], p[2], p[3]);
+            // phase increment per step in 2^-32 turns: round(f dt 2^32) modulo 2^32
+            nu[j] = (uint32_t)(int64_t)std::llround((double)p[1] * (double)w->desc.dt * 4294967296.0);
+        }
+        CUDA_TRY(cudaMemcpyAsync((void *)w->W.act, act.data(), sizeof(float4) * w->J, cudaMemcpyHostToDevice, w->stream));
+        CUDA_TRY(cudaMemcpyAsync((void *)w->W.act_nu, nu.data(), sizeof(uint32_t) * w->J, cudaMemcpyHostToDevice, w->stream));
+        CUDA_TRY(cudaStreamSynchronize(w->stream));
+    }
+    w->act_mode = mode;
+    w->W.act_mode = mode;
+    clear_graphs(w);    // kernel arguments changed
+    return NPX_OK;
+}
+
+int npx_world_step(npx_world *w, int n) {
+    if (int rc = check_ready(w)) return rc;
+    if (n < 0) return fail(NPX_EINVAL, "n must be >= 0");
+    if (n == 0) return NPX_OK;
+    CUDA_TRY(cudaSetDevice(w->device));
+    const int nchunks = (n + w->chunk - 1) / w->chunk;
+    if (w->graphs) {
+        auto it = w->graph_cache.find(n);
+        if (it == w->graph_cache.end()) {
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ge = nullptr;
+            CUDA_TRY(cudaStreamBeginCapture(w->stream, cudaStreamCaptureModeThreadLocal));
+            int rc = enqueue_steps(w, n);
+            cudaError_t e = cudaStreamEndCapture(w->stream, &g);
+            if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+            if (e != cudaSuccess) return fail(NPX_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return fail(NPX_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+            if (w->graph_cache.size() >= 8) clear_graphs(w);
+            it = w->graph_cache.emplace(n, ge).first;
+        }
+        CUDA_TRY(cudaGraphLaunch(it->second, w->stream));
+    } else {
+        if (int rc = enqueue_steps(w, n)) return rc;
+    }
+    w->launches += nchunks;
+    w->step += n;
+    return NPX_OK;
+}
+
+int npx_world_sync(npx_world *w) {
+    if (int rc = check_ready(w)) return rc;
+    CUDA_TRY(cudaSetDevice(w->device));
+    CUDA_TRY(cudaStreamSynchronize(w->stream));
+    return NPX_OK;
+}
+
+int npx_sensors_read(npx_world *w, npx_sensors *o) {
+    if (int rc = check_ready(w)) return rc;
+    if (!o) return fail(NPX_EINVAL, "null sensors");
+    CUDA_TRY(cudaSetDevice(w->device));
+    const size_t S = w->S;
+    std::vector<float> st((size_t)npx::ST_N * S), om(3 * S);
+    CUDA_TRY(cudaMemcpyAsync(st.data(), w->W.st, st.size() * sizeof(float), cudaMemcpyDeviceToHost, w->stream));
+    if (o->omega) CUDA_TRY(cudaMemcpyAsync(om.data(), w->W.omega, om.size() * sizeof(float), cudaMemcpyDeviceToHost, w->stream));
+    if (o->theta && w->J > 0) CUDA_TRY(cudaMemcpyAsync(o->theta, w->W.theta, w->J * sizeof(float), cudaMemcpyDeviceToHost, w->stream));
+    if (o->contacts) CUDA_TRY(cudaMemcpyAsync(o->contacts, w->W.sensors, S * sizeof(uint32_t), cudaMemcpyDeviceToHost, w->stream));
+    if (o->status) CUDA_TRY(cudaMemcpyAsync(o->status, w->W.status, S * sizeof(uint32_t), cudaMemcpyDeviceToHost, w->stream));
+    CUDA_TRY(cudaStreamSynchronize(w->stream));
+    for (size_t s = 0; s < S; ++s) {
+        if (o->cog) for (int k = 0; k < 3; ++k) o->cog[3 * s + k] = st[(npx::ST_CX + k) * S + s];
+        if (o->quat) for (int k = 0; k < 4; ++k) o->quat[4 * s + k] = st[(npx::ST_QW + k) * S + s];
+        if (o->vel) for (int k = 0; k < 3; ++k) o->vel[3 * s + k] = st[(npx::ST_VX + k) * S + s];
+        if (o->angmom) for (int k = 0; k < 3; ++k) o->angmom[3 * s + k] = st[(npx::ST_LX + k) * S + s];
+        if (o->omega) for (int k = 0; k < 3; ++k) o->omega[3 * s + k] = om[k * S + s];
+    }
+    if (o->step) *o->step = w->step;
+    return NPX_OK;
+}
+
+int npx_points_read(npx_world *w, int scene, float *xyz, int n) {
+    if (int rc = check_ready(w)) return rc;
+    if (scene < 0 || scene >= w->S) return fail(NPX_EINVAL, "scene %d out of range", scene);
+    const int np = w->point_off[scene + 1] - w->point_off[scene];
+    if (!xyz || n < np) return fail(NPX_EINVAL, "buffer holds %d points, scene has %d", n, np);
+    CUDA_TRY(cudaSetDevice(w->device));
+    CUDA_TRY(npx::launch_points(w->W, scene, w->d_points, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(xyz, w->d_points, 3 * (size_t)np * sizeof(float), cudaMemcpyDeviceToHost, w->stream));
+    CUDA_TRY(cudaStreamSynchronize(w->stream));
+    return NPX_OK;
+}
+
+int npx_state_export(npx_world *w, void *blob, size_t *size) {
+    if (int rc = check_ready(w)) return rc;
+    if (!size) return fail(NPX_EINVAL, "null size");
+    const BlobLayout b = blob_layout(w);
+    if (!blob) { *size = b.end; return NPX_OK; }
+    if (*size < b.end) return fail(NPX_EINVAL, "blob needs %zu bytes", b.end);
+    CUDA_TRY(cudaSetDevice(w->device));
+    char *p = static_cast<char *>(blob);
+    const uint64_t hdr[8] = {kBlobMagic, (uint64_t)w->S, (uint64_t)w->P, (uint64_t)w->J,
+                             (uint64_t)w->step, 0, 0, 0};
+    memcpy(p, hdr, sizeof hdr);
+    const size_t S = w->S;
+    CUDA_TRY(cudaMemcpyAsync(p + b.st, w->W.st, sizeof(float) * npx::ST_N * S, cudaMemcpyDeviceToHost, w->stream));
+    if (w->J) CUDA_TRY(cudaMemcpyAsync(p + b.theta, w->W.theta, sizeof(float) * w->J, cudaMemcpyDeviceToHost, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(p + b.ref, w->W.ref, sizeof(float) * 2 * S, cudaMemcpyDeviceToHost, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(p + b.omega, w->W.omega, sizeof(float) * 3 * S, cudaMemcpyDeviceToHost, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(p + b.sensors, w->W.sensors, sizeof(uint32_t) * S, cudaMemcpyDeviceToHost, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(p + b.status, w->W.status, sizeof(uint32_t) * S, cudaMemcpyDeviceToHost, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(p + b.kappa, w->W.kappa, w->P, cudaMemcpyDeviceToHost, w->stream));
+    CUDA_TRY(cudaStreamSynchronize(w->stream));
+    *size = b.end;
+    return NPX_OK;
+}
+
+int npx_state_import(npx_world *w, const void *blob, size_t size) {
+    if (int rc = check_ready(w)) return rc;
+    const BlobLayout b = blob_layout(w);
+    if (!blob || size < b.end) return fail(NPX_EINVAL, "blob too small (%zu < %zu)", size, b.end);
+    uint64_t hdr[8];
+    memcpy(hdr, blob, sizeof hdr);
+    if (hdr[0] != kBlobMagic || hdr[1] != (uint64_t)w->S || hdr[2] != (uint64_t)w->P || hdr[3] != (uint64_t)w->J)
+        return fail(NPX_EINVAL, "blob does not match this world");
+    CUDA_TRY(cudaSetDevice(w->device));
+    const char *p = static_cast<const char *>(blob);
+    const size_t S = w->S;
+    CUDA_TRY(cudaMemcpyAsync(w->W.st, p + b.st, sizeof(float) * npx::ST_N * S, cudaMemcpyHostToDevice, w->stream));
+    if (w->J) CUDA_TRY(cudaMemcpyAsync(w->W.theta, p + b.theta, sizeof(float) * w->J, cudaMemcpyHostToDevice, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(w->W.ref, p + b.ref, sizeof(float) * 2 * S, cudaMemcpyHostToDevice, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(w->W.omega, p + b.omega, sizeof(float) * 3 * S, cudaMemcpyHostToDevice, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(w->W.sensors, p + b.sensors, sizeof(uint32_t) * S, cudaMemcpyHostToDevice, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(w->W.status, p + b.status, sizeof(uint32_t) * S, cudaMemcpyHostToDevice, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(w->W.kappa, p + b.kappa, w->P, cudaMemcpyHostToDevice, w->stream));
+    const long long st = (long long)hdr[4];
+    CUDA_TRY(cudaMemcpyAsync(w->d_step, &st, sizeof st, cudaMemcpyHostToDevice, w->stream));
+    CUDA_TRY(cudaStreamSynchronize(w->stream));
+    w->step = st;
+    return NPX_OK;
+}
+
+int npx_world_info_get(npx_world *w, npx_world_info *o) {
+    if (int rc = check_ready(w)) return rc;
+    if (!o) return fail(NPX_EINVAL, "null info");
+    o->n_scenes = w->S; o->n_links = w->L; o->n_joints = w->J; o->n_points = w->P;
+    o->max_points = w->max_points; o->max_links = w->max_links;
+    o->lanes_per_scene = w->cfg.lps; o->warps_per_block = w->cfg.wpb; o->blocks = w->cfg.blocks;
+    o->chunk_steps = w->chunk; o->step = w->step; o->kernel_launches = w->launches;
+    return NPX_OK;
+}
+
+int npx_world_configure(npx_world *w, int lps, int wpb, int blocks, int chunk) {
+    if (int rc = check_ready(w)) return rc;
+    CUDA_TRY(cudaSetDevice(w->device));
+    npx::LaunchCfg c = w->cfg;
+    if (lps) {
+        if (lps != 8 && lps != 16 && lps != 32) return fail(NPX_EINVAL, "lanes per scene must be 8, 16 or 32");
+        c.lps = lps;
+    }
+    if (wpb) {
+        if (wpb < 1 || wpb > 16) return fail(NPX_EINVAL, "warps per block must be 1..16");
+        c.wpb = wpb;
+    }
+    c.blocks = blocks > 0 ? blocks : (lps || wpb ? 0 : c.blocks);
+    if (chunk < 0) return fail(NPX_EINVAL, "chunk must be >= 0");
+    int rc;
+    c = clamp_cfg(w, c, &rc);
+    if (rc) return rc;
+    w->cfg = c;
+    if (chunk) w->chunk = chunk;
+    clear_graphs(w);
+    return NPX_OK;
+}
+
+int npx_world_use_graphs(npx_world *w, int on) {
+    if (int rc = check_world(w)) return rc;
+    w->graphs = on != 0;
+    clear_graphs(w);
+    return NPX_OK;
+}
+
+int npx_world_autotune(npx_world *w, int n_steps, npx_world_info *out) {
+    if (int rc = check_ready(w)) return rc;
+    if (n_steps < 1) return fail(NPX_EINVAL, "n_steps must be >= 1");
+    CUDA_TRY(cudaSetDevice(w->device));
+    CUDA_TRY(cudaStreamSynchronize(w->stream));
+    // snapshot the dynamic state so the trial runs leave it untouched
+    std::vector<char> blob;
+    size_t bytes = 0;
+    if (int rc = npx_state_export(w, nullptr, &bytes)) return rc;
+    blob.resize(bytes);
+    if (int rc = npx_state_export(w, blob.data(), &bytes)) return rc;
+    const npx::LaunchCfg saved = w->cfg;
+    npx::LaunchCfg best = saved;
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    const int lps_list[3] = {8, 16, 32};
+    const int wpb_list[4] = {2, 4, 8, 16};
+    int rc_out = NPX_OK;
+    for (int lps : lps_list) {
+        if (w->max_points > 64 * lps) continue;
+        for (int wpb : wpb_list) {
+            int rc;
+            npx::LaunchCfg c = clamp_cfg(w, {lps, wpb, 0}, &rc);
+            if (rc) { g_err.clear(); continue; }
+            w->cfg = c;
+            float ms = 0.f;
+            bool ok = true;
+            for (int rep = 0; rep < 2 && ok; ++rep) {   // first run warms up
+                if (npx_state_import(w, blob.data(), bytes)) { ok = false; break; }
+                cudaEventRecord(e0, w->stream);
+                for (int done = 0; done < n_steps && ok;) {
+                    const int nc = std::min(w->chunk, n_steps - done);
+                    ok = npx::launch_step(w->W, w->cfg, nc, w->stream) == cudaSuccess &&
+                         npx::launch_advance(w->d_step, nc, w->stream) == cudaSuccess;
+                    done += nc;
+                }
+                cudaEventRecord(e1, w->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (ok && ms < best_ms) { best_ms = ms; best = c; }
+            if (!ok) { rc_out = fail(NPX_ECUDA, "autotune trial lps=%d wpb=%d failed: %s", lps, wpb, cudaGetErrorString(cudaGetLastError())); break; }
+        }
+        if (rc_out) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int rc_cfg;
+    w->cfg = clamp_cfg(w, rc_out ? saved : best, &rc_cfg);   // re-arms the kernel's smem limit
+    clear_graphs(w);
+    if (rc_cfg && !rc_out) rc_out = rc_cfg;
+    if (int rc = npx_state_import(w, blob.data(), bytes)) return rc;
+    if (rc_out) return rc_out;
+    if (out) return npx_world_info_get(w, out);
+    return NPX_OK;
+}
+
+}  // extern "C"

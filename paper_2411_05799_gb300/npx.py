@@ -1,0 +1,314 @@
+"""Thin Python binding of libnpx (include/npx.h): argument marshalling only.
+
+Every step of the simulation runs in the CUDA library; this module converts numpy arrays to the
+C-ABI's pointers and back.  There is no CPU fallback: if the compiled library is missing or no
+GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnpx.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "npx.h")
+
+NPX_OK = 0
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ESTATE", -4: "ECUDA", -5: "ETIMEOUT", -6: "ERANGE"}
+ACT_HOLD = 0
+ACT_SINUSOID = 1
+
+
+class NpxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class WorldDesc(C.Structure):
+    _fields_ = [("n_scenes", C.c_int), ("dt", C.c_float), ("gravity", C.c_float * 3),
+                ("joint_update_steps", C.c_int), ("contact_omega", C.c_float),
+                ("contact_zeta", C.c_float), ("hm_count", C.c_int), ("hm_nx", C.c_int),
+                ("hm_ny", C.c_int), ("hm_scale", C.c_float), ("hm_origin", C.c_float * 2),
+                ("hm_data", C.c_void_p), ("stream", C.c_void_p), ("device", C.c_int)]
+
+
+class SceneBatchC(C.Structure):
+    _fields_ = [("first", C.c_int), ("count", C.c_int), ("link_off", C.c_void_p),
+                ("point_off", C.c_void_p), ("parent", C.c_void_p), ("anchor", C.c_void_p),
+                ("axis", C.c_void_p), ("lo", C.c_void_p), ("hi", C.c_void_p),
+                ("sensor", C.c_void_p), ("p0", C.c_void_p), ("m", C.c_void_p),
+                ("plink", C.c_void_p), ("mu", C.c_void_p), ("hmap", C.c_void_p)]
+
+
+class Sensors(C.Structure):
+    _fields_ = [("cog", C.c_void_p), ("quat", C.c_void_p), ("vel", C.c_void_p),
+                ("omega", C.c_void_p), ("angmom", C.c_void_p), ("theta", C.c_void_p),
+                ("contacts", C.c_void_p), ("status", C.c_void_p), ("step", C.c_void_p)]
+
+
+class WorldInfo(C.Structure):
+    _fields_ = [("n_scenes", C.c_int), ("n_links", C.c_int), ("n_joints", C.c_int),
+                ("n_points", C.c_int), ("max_points", C.c_int), ("max_links", C.c_int),
+                ("lanes_per_scene", C.c_int), ("warps_per_block", C.c_int), ("blocks", C.c_int),
+                ("chunk_steps", C.c_int), ("step", C.c_int64), ("kernel_launches", C.c_int64)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+P = C.c_void_p
+I = C.c_int
+F = C.c_float
+_SIGS = {
+    "npx_world_create": [P, P],
+    "npx_world_destroy": [P],
+    "npx_body_add_pointcloud": [P, I, P, P, F, I, P],
+    "npx_body_connect": [P, I, I, I],
+    "npx_joint_add": [P, I, I, I, P, P, F, F, P],
+    "npx_sensor_add": [P, I, I, I],
+    "npx_scene_set_friction": [P, I, F],
+    "npx_scene_set_heightmap": [P, I, I],
+    "npx_scene_clone": [P, I, I, I],
+    "npx_scenes_add": [P, P],
+    "npx_world_finalize": [P],
+    "npx_state_set": [P, P, P, P, P, P],
+    "npx_actuator_set": [P, I, P],
+    "npx_state_write": [P, P, P, P, P, P, P, C.c_int64],
+    "npx_contacts_read": [P, P, C.c_size_t],
+    "npx_world_step": [P, I],
+    "npx_world_sync": [P],
+    "npx_sensors_read": [P, P],
+    "npx_points_read": [P, I, P, I],
+    "npx_state_export": [P, P, P],
+    "npx_state_import": [P, P, C.c_size_t],
+    "npx_world_info_get": [P, P],
+    "npx_world_configure": [P, I, I, I, I],
+    "npx_world_autotune": [P, I, P],
+    "npx_world_use_graphs": [P, I],
+}
+
+_lib = None
+
+
+def header_functions() -> list[str]:
+    """Names of every function the public header declares."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*(npx_\w+)\s*\(", text, re.M)))
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libnpx.so (build it first with paper_2411_05799_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libnpx.so not built at {path}; run paper_2411_05799_gb300/build.py")
+    lib = C.CDLL(path)
+    for name, args in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    lib.npx_last_error.argtypes = []
+    lib.npx_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != NPX_OK:
+        raise NpxError(rc, _lib.npx_last_error().decode())
+    return rc
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+class World:
+    """A world of independent scenes on one GPU (a handle on npx_world)."""
+
+    def __init__(self, n_scenes, dt=1e-3, gravity=(0.0, 0.0, -9.81), joint_update_steps=80,
+                 contact_omega=300.0, contact_zeta=1.0, heightmaps=None, hm_scale=10.0,
+                 hm_origin=(0.0, 0.0), stream=None, device=0):
+        lib = load()
+        self._h = P()
+        maps = None if heightmaps is None else _f32(heightmaps)
+        d = WorldDesc(n_scenes=n_scenes, dt=dt, gravity=(F * 3)(*gravity),
+                      joint_update_steps=joint_update_steps, contact_omega=contact_omega,
+                      contact_zeta=contact_zeta,
+                      hm_count=0 if maps is None else maps.shape[0],
+                      hm_nx=0 if maps is None else maps.shape[2],
+                      hm_ny=0 if maps is None else maps.shape[1], hm_scale=hm_scale,
+                      hm_origin=(F * 2)(*hm_origin), hm_data=_p(maps), stream=stream,
+                      device=device)
+        _check(lib.npx_world_create(C.byref(d), C.byref(self._h)))
+        self.n_scenes = n_scenes
+        self._info = None
+
+    @classmethod
+    def from_batch(cls, batch, stream=None, device=0, configure=None) -> "World":
+        """World built from a SceneBatch: bulk construction, finalize, initial state, actuators."""
+        b = batch
+        w = cls(b.n_scenes, dt=b.dt, gravity=b.gravity, joint_update_steps=b.joint_update_steps,
+                contact_omega=b.contact_omega, contact_zeta=b.contact_zeta,
+                heightmaps=b.heightmaps, hm_scale=b.hm_scale, hm_origin=b.hm_origin,
+                stream=stream, device=device)
+        w.add_scenes(b)
+        w.finalize()
+        if configure:
+            w.configure(**configure)
+        w.set_state(b.origin, b.quat, b.vel, b.omega, b.theta0)
+        w.set_actuators(b.act_mode, b.act_params)
+        return w
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.npx_world_destroy(self._h)
+            self._h = P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- construction
+    def add_scenes(self, b, first=0):
+        keep = [_i32(b.link_off), _i32(b.point_off), _i32(b.parent), _f32(b.anchor),
+                _f32(b.axis), _f32(b.lo), _f32(b.hi), _i32(b.sensor), _f32(b.p0), _f32(b.m),
+                _i32(b.plink), _f32(b.mu), _i32(b.hmap)]
+        sb = SceneBatchC(first, b.n_scenes, *[_p(a) for a in keep])
+        _check(_lib.npx_scenes_add(self._h, C.byref(sb)))
+
+    def add_body(self, scene, xyz, mass=None, total_mass=1.0) -> int:
+        xyz = _f32(xyz).reshape(-1, 3)
+        m = None if mass is None else _f32(mass)
+        out = C.c_int()
+        _check(_lib.npx_body_add_pointcloud(self._h, scene, _p(xyz), _p(m), total_mass,
+                                            len(xyz), C.byref(out)))
+        return out.value
+
+    def connect(self, scene, b1, b2):
+        _check(_lib.npx_body_connect(self._h, scene, b1, b2))
+
+    def add_joint(self, scene, b1, b2, anchor, axis, lo, hi) -> int:
+        a, u = _f32(anchor), _f32(axis)
+        out = C.c_int()
+        _check(_lib.npx_joint_add(self._h, scene, b1, b2, _p(a), _p(u), lo, hi, C.byref(out)))
+        return out.value
+
+    def add_sensor(self, scene, body, bit):
+        _check(_lib.npx_sensor_add(self._h, scene, body, bit))
+
+    def set_friction(self, scene, mu):
+        _check(_lib.npx_scene_set_friction(self._h, scene, mu))
+
+    def set_heightmap(self, scene, hm):
+        _check(_lib.npx_scene_set_heightmap(self._h, scene, hm))
+
+    def clone(self, src, first, count):
+        _check(_lib.npx_scene_clone(self._h, src, first, count))
+
+    def finalize(self):
+        _check(_lib.npx_world_finalize(self._h))
+        self._info = self.info()
+
+    # -- state
+    def set_state(self, origin, quat, vel, omega, theta=None):
+        S = self.n_scenes
+        o, q, v, w = (_f32(origin).reshape(S, 3), _f32(quat).reshape(S, 4),
+                      _f32(vel).reshape(S, 3), _f32(omega).reshape(S, 3))
+        th = None if theta is None else _f32(theta)
+        _check(_lib.npx_state_set(self._h, _p(o), _p(q), _p(v), _p(w), _p(th)))
+
+    def write_state(self, cog, quat, vel, angmom, theta=None, contact_prev=None, step=0):
+        S = self.n_scenes
+        c, q, v, L = (_f32(cog).reshape(S, 3), _f32(quat).reshape(S, 4),
+                      _f32(vel).reshape(S, 3), _f32(angmom).reshape(S, 3))
+        th = None if theta is None else _f32(theta)
+        k = None if contact_prev is None else np.ascontiguousarray(contact_prev, np.uint8)
+        _check(_lib.npx_state_write(self._h, _p(c), _p(q), _p(v), _p(L), _p(th), _p(k),
+                                    int(step)))
+
+    def contacts(self) -> np.ndarray:
+        out = np.zeros(self._info["n_points"], np.uint8)
+        _check(_lib.npx_contacts_read(self._h, _p(out), out.size))
+        return out
+
+    def set_actuators(self, mode, params=None):
+        p = None if params is None else _f32(params)
+        _check(_lib.npx_actuator_set(self._h, mode, _p(p)))
+
+    def step(self, n: int):
+        _check(_lib.npx_world_step(self._h, int(n)))
+
+    def sync(self):
+        _check(_lib.npx_world_sync(self._h))
+
+    def read(self) -> dict:
+        S, J = self.n_scenes, self._info["n_joints"]
+        out = {"cog": np.zeros((S, 3), np.float32), "quat": np.zeros((S, 4), np.float32),
+               "vel": np.zeros((S, 3), np.float32), "omega": np.zeros((S, 3), np.float32),
+               "angmom": np.zeros((S, 3), np.float32), "theta": np.zeros(J, np.float32),
+               "contacts": np.zeros(S, np.uint32), "status": np.zeros(S, np.uint32),
+               "step": np.zeros(1, np.int64)}
+        s = Sensors(*[_p(out[k]) for k in ("cog", "quat", "vel", "omega", "angmom", "theta",
+                                           "contacts", "status", "step")])
+        _check(_lib.npx_sensors_read(self._h, C.byref(s)))
+        out["step"] = int(out["step"][0])
+        return out
+
+    def points(self, scene: int) -> np.ndarray:
+        n = self._info["max_points"]
+        buf = np.zeros((n, 3), np.float32)
+        _check(_lib.npx_points_read(self._h, scene, _p(buf), n))
+        return buf
+
+    def export_state(self) -> bytes:
+        size = C.c_size_t()
+        _check(_lib.npx_state_export(self._h, None, C.byref(size)))
+        buf = C.create_string_buffer(size.value)
+        _check(_lib.npx_state_export(self._h, buf, C.byref(size)))
+        return buf.raw[:size.value]
+
+    def import_state(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        _check(_lib.npx_state_import(self._h, buf, len(blob)))
+
+    # -- tuning
+    def info(self) -> dict:
+        i = WorldInfo()
+        _check(_lib.npx_world_info_get(self._h, C.byref(i)))
+        return i.as_dict()
+
+    def configure(self, lanes_per_scene=0, warps_per_block=0, blocks=0, chunk_steps=0):
+        _check(_lib.npx_world_configure(self._h, lanes_per_scene, warps_per_block, blocks,
+                                        chunk_steps))
+        self._info = self.info()
+
+    def autotune(self, n_steps=200) -> dict:
+        i = WorldInfo()
+        _check(_lib.npx_world_autotune(self._h, n_steps, C.byref(i)))
+        self._info = i.as_dict()
+        return self._info
+
+    def use_graphs(self, on: bool):
+        _check(_lib.npx_world_use_graphs(self._h, 1 if on else 0))

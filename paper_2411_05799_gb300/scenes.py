@@ -232,6 +232,10 @@ def _assemble(robots, mu, origin, quat, vel, omega, act_params, name, dt=1e-3, K
         link_off.append(link_off[-1] + len(links))
         point_off.append(point_off[-1] + sum(len(p) for p in pts))
     J = link_off[-1] - S
+    r32 = lambda x: float(np.float32(x))      # world parameters are single precision inputs
+    dt, hm_scale = r32(dt), r32(hm_scale)
+    gravity = tuple(r32(g) for g in gravity)
+    hm_origin = tuple(r32(o) for o in hm_origin)
     f32 = lambda a: np.ascontiguousarray(np.asarray(a, np.float32))
     i32 = lambda a: np.ascontiguousarray(np.asarray(a, np.int32))
     return SceneBatch(
@@ -365,13 +369,14 @@ def cpg_batch(n_scenes: int = 16384, seed_key: int = 0, n_cells=128, cell=0.05) 
     origin[:, 2] = hmax - FOOT_Z + 0.01
     return base.with_(act_params=act.reshape(-1, 4).astype(np.float32),
                       origin=origin.astype(np.float32), heightmaps=maps,
-                      hmap=np.arange(S, dtype=np.int32), hm_scale=1.0 / cell,
-                      hm_origin=(-half, -half))
+                      hmap=np.arange(S, dtype=np.int32), hm_scale=float(np.float32(1.0 / cell)),
+                      hm_origin=(float(np.float32(-half)), float(np.float32(-half))))
 
 
 def tilted_gravity(batch: SceneBatch, theta: float, g: float = 9.81) -> SceneBatch:
     """An incline of angle theta realised by tilting gravity about the y axis on flat ground."""
-    return batch.with_(gravity=(g * math.sin(theta), 0.0, -g * math.cos(theta)))
+    return batch.with_(gravity=(float(np.float32(g * math.sin(theta))), 0.0,
+                                float(np.float32(-g * math.cos(theta)))))
 
 
 def block_batch(n_scenes=1, mu=0.5, extent=(0.2, 0.2, 0.1), counts=(3, 3, 2), mass=1.0,

@@ -22,12 +22,12 @@ def test_free_fall_closed_form():
     b = b.with_(origin=np.array([[0.3, -0.2, 100.0]], np.float32))
     o = Oracle(b)
     c0, v0 = o.c[0].copy(), o.v[0].copy()
-    dt = b.dt
+    dt, g = b.dt, -b.gravity[2]
     for n in (1, 7, 100, 1000, 3000):
         o2 = Oracle(b)
         o2.step(n)
-        zc = c0[2] + n * dt * v0[2] - G * dt * dt * n * (n + 1) / 2
-        vz = v0[2] - G * n * dt
+        zc = c0[2] + n * dt * v0[2] - g * dt * dt * n * (n + 1) / 2
+        vz = v0[2] - g * n * dt
         assert abs(o2.c[0, 2] - zc) < 1e-11 * max(1.0, abs(zc))
         assert abs(o2.v[0, 2] - vz) < 1e-12 * max(1.0, abs(vz))
         np.testing.assert_allclose(o2.c[0, :2], c0[:2] + n * dt * v0[:2], rtol=0, atol=1e-12)
@@ -38,12 +38,12 @@ def test_modified_energy_and_angular_momentum_invariant():
     b = scenes.single_body()
     b = b.with_(origin=np.array([[0.0, 0.0, 50.0]], np.float32))
     o = Oracle(b)
-    M = 1.0
+    M, g = 1.0, -b.gravity[2]
     L0 = o.L[0].copy()
-    E0 = 0.5 * M * o.v[0] @ o.v[0] + M * G * o.c[0, 2] - 0.5 * M * G * b.dt * o.v[0, 2]
+    E0 = 0.5 * M * o.v[0] @ o.v[0] + M * g * o.c[0, 2] - 0.5 * M * g * b.dt * o.v[0, 2]
     for _ in range(20):
         o.step(100)
-        E = 0.5 * M * o.v[0] @ o.v[0] + M * G * o.c[0, 2] - 0.5 * M * G * b.dt * o.v[0, 2]
+        E = 0.5 * M * o.v[0] @ o.v[0] + M * g * o.c[0, 2] - 0.5 * M * g * b.dt * o.v[0, 2]
         assert abs(E - E0) < 1e-9 * abs(E0)
         np.testing.assert_array_equal(o.L[0], L0)                # no torque: L exactly constant
         assert abs(np.linalg.norm(o.q[0]) - 1.0) < 1e-14
@@ -248,7 +248,8 @@ def test_block_rests_on_plane():
     o = Oracle(b)
     o.step(1000)
     w2 = b.contact_omega ** 2
-    d = 1.0 * G / (9 * (1.0 / 18) * w2)
+    m_pt = float(np.float32(1.0 / 18))
+    d = 18 * m_pt * -b.gravity[2] / (9 * m_pt * w2)
     assert abs(o.c[0, 2] - (0.05 - d)) < 1e-9
     assert np.abs(o.v[0]).max() < 1e-6
     np.testing.assert_allclose(o.c[0, :2], 0.0, atol=1e-12)
@@ -330,7 +331,8 @@ def test_incline_sticks_below_friction_angle():
 def test_incline_slips_with_coulomb_acceleration(theta_deg, mu):
     theta = math.radians(theta_deg)
     xs, vs, b = _incline_run(theta, mu)
-    want = G * (math.sin(theta) - mu * math.cos(theta))
+    gx, gz = b.gravity[0], -b.gravity[2]
+    want = gx - float(np.float32(mu)) * gz
     acc = (vs[-1] - vs[100]) / ((len(vs) - 1 - 100) * 10 * b.dt)
     assert abs(acc - want) < 1e-3 * want
 
