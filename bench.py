@@ -276,8 +276,33 @@ def run_gpu(args):
     return 0
 
 
+def run_profile(args):
+    """A few step-kernel launches of `--chunk` steps on the benchmark workload in a fixed launch
+    shape, for ncu captures (prints no benchmark line)."""
+    import torch
+    from paper_2411_05799_gb300 import scenes
+    from paper_2411_05799_gb300.build import build
+    from paper_2411_05799_gb300.npx import World
+    build()
+    torch.cuda.set_device(0)
+    world = World.from_batch(scenes.hexapod_batch(N_SCENES),
+                             configure=dict(lanes_per_scene=args.lps, warps_per_block=args.wpb,
+                                            chunk_steps=args.chunk))
+    for _ in range(3):
+        world.step(args.chunk)
+    world.sync()
+    print(json.dumps({"profile": True, **world.info(),
+                      "status_nonzero": int((world.read()["status"] != 0).sum())}))
+    world.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--profile", action="store_true", help="ncu driver: 3 launches, no bench line")
+    ap.add_argument("--lps", type=int, default=16)
+    ap.add_argument("--wpb", type=int, default=16)
+    ap.add_argument("--chunk", type=int, default=100)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
@@ -285,6 +310,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.profile:
+        return run_profile(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -63,7 +63,8 @@ typedef struct {
     float hm_scale;
     float hm_origin[2];
     const float *hm_data;    /* host, hm_count * hm_ny * hm_nx floats, or NULL when hm_count = 0 */
-    void *stream;            /* cudaStream_t to queue work on; NULL = the legacy default stream */
+    void *stream;            /* cudaStream_t to queue work on (not the legacy default stream,
+                                which cannot be captured); NULL = a stream the world creates */
     int device;              /* CUDA device ordinal */
 } npx_world_desc;
 

@@ -40,6 +40,7 @@
 
 #define NPXO_ACT_HOLD 0
 #define NPXO_PI 3.14159265358979323846
+#define NPXO_POINT_RADIUS 1e-3
 
 /* ------------------------------------------------------------------ 3-vectors and 3x3 matrices */
 
@@ -229,7 +230,10 @@ static void shape_update(const npxo_model *M, const npxo_state *st, scene_ws *w)
     }
     w->Mtot = Mt;
     for (int k = 0; k < 3; ++k) w->g[k] = mp[k] / Mt;
+    /* every mass point is a solid sphere of radius NPXO_POINT_RADIUS (2/5 m r^2 about any axis),
+     * so that a single point or a line of points has an invertible inertia */
     memset(w->Ib, 0, sizeof w->Ib);
+    for (int a = 0; a < 3; ++a) w->Ib[4 * a] = 0.4 * Mt * NPXO_POINT_RADIUS * NPXO_POINT_RADIUS;
     for (int i = 0; i < w->np; ++i) {
         double *r = w->r + 3 * i, m = M->m[w->p0 + i];
         for (int k = 0; k < 3; ++k) r[k] -= w->g[k];

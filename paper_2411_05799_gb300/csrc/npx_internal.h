@@ -40,7 +40,6 @@ struct WorldDev {
     float *st;                            // [ST_N * S]
     float *theta;                         // [J]
     uint8_t *kappa;                       // [P] contact flag of the last step
-    float *ref;                           // [2 * S] centring reference of the friction sums
     float *omega;                         // [3 * S] angular velocity (output)
     uint32_t *sensors, *status;           // [S]
     // schedule

@@ -33,6 +33,8 @@ namespace npx {
 
 #define FULL_MASK 0xffffffffu
 
+constexpr float POINT_RADIUS = 1e-3f;   // m, see mass_props
+
 // ------------------------------------------------------------------------ group reductions
 
 template <int LPS, int N>
@@ -215,6 +217,10 @@ __device__ void mass_props(const WorldDev &W, int p0, int np, const float *fr, i
     sh.Ib.xx = (a[5] + a[6]) - M * (dy * dy + dz * dz);
     sh.Ib.yy = (a[4] + a[6]) - M * (dx * dx + dz * dz);
     sh.Ib.zz = (a[4] + a[5]) - M * (dx * dx + dy * dy);
+    // every mass point is a solid sphere of radius POINT_RADIUS (2/5 m r^2 about any axis), so
+    // a single point or a line of points still has an invertible inertia
+    const float ps = 0.4f * M * POINT_RADIUS * POINT_RADIUS;
+    sh.Ib.xx += ps; sh.Ib.yy += ps; sh.Ib.zz += ps;
     sh.Ib.xy = -a[7] + M * dx * dy;
     sh.Ib.xz = -a[8] + M * dx * dz;
     sh.Ib.yz = -a[9] + M * dy * dz;
@@ -283,7 +289,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
     }
     const int j0 = l0 - (valid ? s : 0), nj = nl - 1;
     // ---- load
-    float c[3], q[4], v[3], L[3], off[2];
+    float c[3], q[4], v[3], L[3];
     uint32_t status = 1u;
     float mu = 0.f;
     int hm = -1;
@@ -294,13 +300,12 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         q[3] = W.st[ST_QZ * S + s];
         v[0] = W.st[ST_VX * S + s]; v[1] = W.st[ST_VY * S + s]; v[2] = W.st[ST_VZ * S + s];
         L[0] = W.st[ST_LX * S + s]; L[1] = W.st[ST_LY * S + s]; L[2] = W.st[ST_LZ * S + s];
-        off[0] = W.ref[s]; off[1] = W.ref[S + s];
         status = W.status[s];
         mu = W.mu[s];
         hm = FLAT ? -1 : W.hmap[s];
     } else {
         c[0] = c[1] = c[2] = 0.f; q[0] = 1.f; q[1] = q[2] = q[3] = 0.f;
-        v[0] = v[1] = v[2] = 0.f; L[0] = L[1] = L[2] = 0.f; off[0] = off[1] = 0.f;
+        v[0] = v[1] = v[2] = 0.f; L[0] = L[1] = L[2] = 0.f;
     }
     for (int j = gl; j < nj; j += LPS) th[j] = W.theta[j0 + j];
     uint64_t kprev = 0;
@@ -320,7 +325,9 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         float R[9];
         quat_mat(q, R);
 
-        // -- joint-angle determination: new angles, frames and mass properties
+        // -- joint-angle determination: new angles, frames and mass properties.  The new
+        //    offsets r_new are evaluated on the fly from the frames; smem keeps r_old until
+        //    the end of the step.
         if (tick) {
             if (status == 0u) {   // a frozen scene keeps its angles
                 for (int j = gl; j < nj; j += LPS) {
@@ -331,73 +338,45 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             __syncwarp();
             shape_props<LPS>(W, p0, np, l0, nl, th, fr, gl, sh);
         }
+        // offsets used this step: r_new on joint-update steps, else the stored ones
+        auto offset = [&](int i) -> float4 {
+            if (!tick) return pts[i];
+            const float4 a = W.p0m[p0 + i];
+            float p[3];
+            fk_point(fr, a, W.plink[p0 + i], p);
+            return make_float4(p[0] - sh.g[0], p[1] - sh.g[1], p[2] - sh.g[2], a.w);
+        };
 
         float om[3];
         world_sym(R, sh.Ii, L, om);
 
-        // -- collision and normal forces (pass 1); on joint-update steps also the new offsets
-        //    and the sums of the kinematic least squares
+        // -- pass 1: collision against the ground and penalty normal forces
         uint64_t know = 0;
-        float red[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (!tick) {
-            for (int k = 0, i = gl; i < np; ++k, i += LPS) {
-                const float4 r = pts[i];
-                const float rz = R[6] * r.x + R[7] * r.y + R[8] * r.z;
-                const float z = c[2] + rz;
-                float rx = 0.f, ry = 0.f, h = 0.f;
-                if (!FLAT) {
+        float red[3] = {0.f, 0.f, 0.f};
+        for (int k = 0, i = gl; i < np; ++k, i += LPS) {
+            const float4 r = offset(i);
+            const float rz = R[6] * r.x + R[7] * r.y + R[8] * r.z;
+            const float z = c[2] + rz;
+            float rx = 0.f, ry = 0.f, h = 0.f;
+            if (!FLAT) {
+                rx = R[0] * r.x + R[1] * r.y + R[2] * r.z;
+                ry = R[3] * r.x + R[4] * r.y + R[5] * r.z;
+                h = ground<FLAT>(W, hm, c[0] + rx, c[1] + ry);
+            }
+            if (z < h) {
+                know |= 1ull << k;
+                if (FLAT) {
                     rx = R[0] * r.x + R[1] * r.y + R[2] * r.z;
                     ry = R[3] * r.x + R[4] * r.y + R[5] * r.z;
-                    h = ground<FLAT>(W, hm, c[0] + rx, c[1] + ry);
                 }
-                if (z < h) {
-                    know |= 1ull << k;
-                    if (FLAT) {
-                        rx = R[0] * r.x + R[1] * r.y + R[2] * r.z;
-                        ry = R[3] * r.x + R[4] * r.y + R[5] * r.z;
-                    }
-                    const float vz = v[2] + (om[0] * ry - om[1] * rx);
-                    const float F = fmaxf(0.f, r.w * (kw2 * (h - z) - kc * vz));
-                    red[0] += F;
-                    red[1] += ry * F;
-                    red[2] -= rx * F;
-                }
+                const float vz = v[2] + (om[0] * ry - om[1] * rx);
+                const float F = fmaxf(0.f, r.w * (kw2 * (h - z) - kc * vz));
+                red[0] += F;
+                red[1] += ry * F;
+                red[2] -= rx * F;
             }
-            float r3[3] = {red[0], red[1], red[2]};
-            gsum<LPS, 3>(r3);
-            red[0] = r3[0]; red[1] = r3[1]; red[2] = r3[2];
-        } else {
-            for (int k = 0, i = gl; i < np; ++k, i += LPS) {
-                const float4 a = W.p0m[p0 + i];
-                float p[3];
-                fk_point(fr, a, W.plink[p0 + i], p);
-                const float4 ro = pts[i];
-                const float rn[3] = {p[0] - sh.g[0], p[1] - sh.g[1], p[2] - sh.g[2]};
-                pts[i] = make_float4(rn[0], rn[1], rn[2], a.w);
-                float rho[3];
-                mat_vec(R, rn, rho);
-                const float z = c[2] + rho[2];
-                const float h = ground<FLAT>(W, hm, c[0] + rho[0], c[1] + rho[1]);
-                if (z < h) {
-                    know |= 1ull << k;
-                    const float vz = v[2] + (om[0] * rho[1] - om[1] * rho[0]);
-                    const float F = fmaxf(0.f, a.w * (kw2 * (h - z) - kc * vz));
-                    red[0] += F;
-                    red[1] += rho[1] * F;
-                    red[2] -= rho[0] * F;
-                    if ((kprev >> k) & 1ull) {
-                        // kinematic slip back to the step-start position: R (r_old - r_new)
-                        const float ex = R[0] * (ro.x - rn[0]) + R[1] * (ro.y - rn[1]) + R[2] * (ro.z - rn[2]);
-                        const float ey = R[3] * (ro.x - rn[0]) + R[4] * (ro.y - rn[1]) + R[5] * (ro.z - rn[2]);
-                        const float sx = rho[0] - off[0], sy = rho[1] - off[1];
-                        red[3] += sx; red[4] += sy; red[5] += sx * sx + sy * sy;
-                        red[6] += ex; red[7] += ey; red[8] += sx * ey - sy * ex;
-                    }
-                }
-            }
-            __syncwarp();
-            gsum<LPS, 9>(red);
         }
+        gsum<LPS, 3>(red);
         const float FN = red[0];
 
         // -- semi-implicit Euler
@@ -411,63 +390,105 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         Ls[2] = L[2];
         world_sym(R, sh.Ii, Ls, oms);
         cs[0] = c[0] + dt * vs[0]; cs[1] = c[1] + dt * vs[1]; cs[2] = c[2] + dt * vs[2];
+        // rotation increment dR = exp([u]x), u = dt w*: q* = dq (x) q, and D = dR - 1 =
+        // a [u]x + b [u]x^2 (a = sin|u| / |u|, b = (1 - cos|u|) / |u|^2) gives the points'
+        // rotational displacement D (R r) without the cancellation of R* r - R r
+        float Dm[6];   // rows 0 and 1 of D (only horizontal displacements are needed)
         {
             const float px = dt * oms[0], py = dt * oms[1], pz = dt * oms[2];
-            const float a = sqrtf(px * px + py * py + pz * pz);
+            const float a2 = px * px + py * py + pz * pz;
+            const float a = sqrtf(a2);
             float dq[4] = {1.f, 0.f, 0.f, 0.f};
+            float fa = 1.f, fb = 0.5f;
             if (a > 0.f) {
                 float sn, cn;
                 sincosf(0.5f * a, &sn, &cn);
                 const float f = sn / a;
                 dq[0] = cn; dq[1] = f * px; dq[2] = f * py; dq[3] = f * pz;
+                fa = 2.f * f * cn;
+                fb = 2.f * f * f;
             }
+            // [u]x^2 = u u^T - |u|^2 1
+            Dm[0] = fb * (px * px - a2); Dm[1] = -fa * pz + fb * px * py; Dm[2] = fa * py + fb * px * pz;
+            Dm[3] = fa * pz + fb * py * px; Dm[4] = fb * (py * py - a2); Dm[5] = -fa * px + fb * py * pz;
             quat_mul(dq, q, qs);
             const float inv = rsqrtf(qs[0] * qs[0] + qs[1] * qs[1] + qs[2] * qs[2] + qs[3] * qs[3]);
             qs[0] *= inv; qs[1] *= inv; qs[2] *= inv; qs[3] *= inv;
         }
         quat_mat(qs, Rs);
 
-        // -- friction (pass 2 over the points in contact in both steps)
-        float f7[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        // -- friction over the points in contact in both steps (Sec. III-C).  Pass 2a finds
+        //    the contact centroid of the integrated points (relative to c*); pass 2b sums the
+        //    least-squares terms about it, so the FP32 sums never cancel.
+        const uint64_t cmask = kprev & know;
+        float f3[3] = {0.f, 0.f, 0.f};
+        for (uint64_t cm = cmask; cm; cm &= cm - 1) {
+            const int k = __ffsll((long long)cm) - 1;
+            const float4 r = offset(gl + k * LPS);
+            const float rh[3] = {R[0] * r.x + R[1] * r.y + R[2] * r.z,
+                                 R[3] * r.x + R[4] * r.y + R[5] * r.z,
+                                 R[6] * r.x + R[7] * r.y + R[8] * r.z};
+            f3[0] += 1.f;
+            f3[1] += rh[0] + (Dm[0] * rh[0] + Dm[1] * rh[1] + Dm[2] * rh[2]);
+            f3[2] += rh[1] + (Dm[3] * rh[0] + Dm[4] * rh[1] + Dm[5] * rh[2]);
+        }
+        gsum<LPS, 3>(f3);
+        const float nC = f3[0];
+        const float in = nC > 0.f ? 1.0f / nC : 0.f;
+        const float gx = f3[1] * in, gy = f3[2] * in;      // centroid minus c*
+        // dynamic: S2, sum e, sum s x e; kinematic (joint-update steps): sum sigma, S2, sum e,
+        // sum sigma x e, with sigma the moved point minus c minus (gx, gy)
+        float f10[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         {
-            const float dcx = c[0] - cs[0], dcy = c[1] - cs[1];
-            uint64_t cm = kprev & know;
-            while (cm) {
+            const float dcx = -dt * vs[0], dcy = -dt * vs[1];
+            for (uint64_t cm = cmask; cm; cm &= cm - 1) {
                 const int k = __ffsll((long long)cm) - 1;
-                cm &= cm - 1;
-                const float4 r = pts[gl + k * LPS];
-                const float rhx = R[0] * r.x + R[1] * r.y + R[2] * r.z;
-                const float rhy = R[3] * r.x + R[4] * r.y + R[5] * r.z;
-                const float rsx = Rs[0] * r.x + Rs[1] * r.y + Rs[2] * r.z;
-                const float rsy = Rs[3] * r.x + Rs[4] * r.y + Rs[5] * r.z;
-                const float sx = rsx - off[0], sy = rsy - off[1];
-                const float ex = dcx + rhx - rsx, ey = dcy + rhy - rsy;
-                f7[0] += 1.f;
-                f7[1] += sx; f7[2] += sy; f7[3] += sx * sx + sy * sy;
-                f7[4] += ex; f7[5] += ey; f7[6] += sx * ey - sy * ex;
+                const int i = gl + k * LPS;
+                const float4 r = offset(i);
+                const float rh[3] = {R[0] * r.x + R[1] * r.y + R[2] * r.z,
+                                     R[3] * r.x + R[4] * r.y + R[5] * r.z,
+                                     R[6] * r.x + R[7] * r.y + R[8] * r.z};
+                const float ddx = Dm[0] * rh[0] + Dm[1] * rh[1] + Dm[2] * rh[2];
+                const float ddy = Dm[3] * rh[0] + Dm[4] * rh[1] + Dm[5] * rh[2];
+                // dynamic slip back to the pre-integration position: e = -dt v* - D (R r)
+                const float sx = (rh[0] - gx) + ddx, sy = (rh[1] - gy) + ddy;
+                const float ex = dcx - ddx, ey = dcy - ddy;
+                f10[0] += sx * sx + sy * sy;
+                f10[1] += ex; f10[2] += ey; f10[3] += sx * ey - sy * ex;
+                if (tick) {
+                    // kinematic slip back to the step-start position: R (r_old - r_new)
+                    const float4 ro = pts[i];
+                    const float d[3] = {ro.x - r.x, ro.y - r.y, ro.z - r.z};
+                    const float kx = R[0] * d[0] + R[1] * d[1] + R[2] * d[2];
+                    const float ky = R[3] * d[0] + R[4] * d[1] + R[5] * d[2];
+                    const float ux = rh[0] - gx, uy = rh[1] - gy;
+                    f10[4] += ux; f10[5] += uy; f10[6] += ux * ux + uy * uy;
+                    f10[7] += kx; f10[8] += ky; f10[9] += ux * ky - uy * kx;
+                }
             }
-            gsum<LPS, 7>(f7);
+            if (tick) gsum<LPS, 10>(f10);
+            else {
+                float f4[4] = {f10[0], f10[1], f10[2], f10[3]};
+                gsum<LPS, 4>(f4);
+                f10[0] = f4[0]; f10[1] = f4[1]; f10[2] = f4[2]; f10[3] = f4[3];
+            }
         }
         float cn[3] = {cs[0], cs[1], cs[2]}, vn[3] = {vs[0], vs[1], vs[2]};
         float Ln[3] = {Ls[0], Ls[1], Ls[2]}, qn[4] = {qs[0], qs[1], qs[2], qs[3]};
-        float offn[2] = {off[0], off[1]};
-        const float nC = f7[0];
         if (nC >= 1.f) {
-            const float in = 1.0f / nC;
-            // dynamic least squares, centred on the contact centroid
-            const float sbx = f7[1] * in, sby = f7[2] * in;
-            const float S2 = f7[3] - nC * (sbx * sbx + sby * sby);
-            const float tDx = f7[4] * in, tDy = f7[5] * in;
-            const float X = f7[6] - (sbx * f7[5] - sby * f7[4]);
+            // dynamic least squares about the contact centroid
+            const float S2 = f10[0];
+            const float tDx = f10[1] * in, tDy = f10[2] * in;
+            const float X = f10[3];
             float a3 = (nC >= 2.f && S2 > 1e-12f) ? X / S2 : 0.f;
             a3 = fminf(fmaxf(a3, -1.f), 1.f);
             const float cD = sqrtf(fmaxf(0.f, 1.f - a3 * a3));
             const float cm1 = -a3 * a3 / (1.f + cD);                  // cos(alpha_D) - 1
-            const float dDx = -(off[0] + sbx), dDy = -(off[1] + sby);  // CoG minus centroid
-            const float DDx = tDx + cm1 * dDx - a3 * dDy;               // uncapped CoG shift
+            const float dDx = -gx, dDy = -gy;                         // CoG minus centroid
+            const float DDx = tDx + cm1 * dDx - a3 * dDy;             // uncapped CoG shift
             const float DDy = tDy + a3 * dDx + cm1 * dDy;
             // maximum static friction (Coulomb cap on the impulse that undoes the slip)
-            const float sh2 = a3 * a3 / (2.f * (1.f + cD));              // sin^2(alpha_D / 2)
+            const float sh2 = a3 * a3 / (2.f * (1.f + cD));            // sin^2(alpha_D / 2)
             const float u2 = tDx * tDx + tDy * tDy + 4.f * sh2 * S2 * in;
             const float Jreq = sh.M * sqrtf(u2) / dt;
             const float Jmax = mu * dt * FN;
@@ -480,20 +501,20 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             float dy1 = sc * tDy + sin1 * dDx + cm1s * dDy;
             float A = sc * aD;
             if (tick) {
-                // kinematic least squares from the pass-1 sums (same contact set)
-                const float kbx = red[3] * in, kby = red[4] * in;
-                const float S2K = red[5] - nC * (kbx * kbx + kby * kby);
-                const float tKx = red[6] * in, tKy = red[7] * in;
-                const float XK = red[8] - (kbx * red[7] - kby * red[6]);
+                // kinematic least squares about the centroid of the moved points
+                const float kbx = f10[4] * in, kby = f10[5] * in;
+                const float S2K = f10[6] - nC * (kbx * kbx + kby * kby);
+                const float tKx = f10[7] * in, tKy = f10[8] * in;
+                const float XK = f10[9] - (kbx * f10[8] - kby * f10[7]);
                 float a3K = (nC >= 2.f && S2K > 1e-12f) ? XK / S2K : 0.f;
                 a3K = fminf(fmaxf(a3K, -1.f), 1.f);
                 const float aK = asinf(a3K);
                 float s2, c2;
                 sincosf(0.5f * aK, &s2, &c2);
                 const float sin2 = 2.f * s2 * c2, cm2 = -2.f * s2 * s2;
-                // centroid of the moved points is c + off + kb; CoG after the dynamic map
-                const float dKx = (cs[0] - c[0]) + dx1 - (off[0] + kbx);
-                const float dKy = (cs[1] - c[1]) + dy1 - (off[1] + kby);
+                // moved-point centroid is c + (gx, gy) + kb; CoG after the dynamic map is cs + d1
+                const float dKx = (cs[0] - c[0]) + dx1 - (gx + kbx);
+                const float dKy = (cs[1] - c[1]) + dy1 - (gy + kby);
                 dx1 += tKx + cm2 * dKx - sin2 * dKy;
                 dy1 += tKy + sin2 * dKx + cm2 * dKy;
                 A += aK;
@@ -511,8 +532,11 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             sincosf(0.5f * A, &sa, &ca);
             const float qz[4] = {ca, 0.f, 0.f, sa};
             quat_mul(qz, qs, qn);
-            offn[0] = off[0] + sbx;
-            offn[1] = off[1] + sby;
+        }
+        // joint-update steps: the new offsets replace the old ones
+        if (tick) {
+            for (int i = gl; i < np; i += LPS) pts[i] = offset(i);
+            __syncwarp();
         }
 
         // -- freeze a scene whose state is no longer finite or has left any sane range
@@ -532,7 +556,6 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
                 for (int i = 0; i < 3; ++i) { c[i] = cn[i]; v[i] = vn[i]; L[i] = Ln[i]; }
 #pragma unroll
                 for (int i = 0; i < 4; ++i) q[i] = qn[i];
-                off[0] = offn[0]; off[1] = offn[1];
                 kprev = know;
             }
         }
@@ -557,7 +580,6 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         W.st[ST_QZ * S + s] = q[3];
         W.st[ST_VX * S + s] = v[0]; W.st[ST_VY * S + s] = v[1]; W.st[ST_VZ * S + s] = v[2];
         W.st[ST_LX * S + s] = L[0]; W.st[ST_LY * S + s] = L[1]; W.st[ST_LZ * S + s] = L[2];
-        W.ref[s] = off[0]; W.ref[S + s] = off[1];
         float R[9], om[3];
         quat_mat(q, R);
         world_sym(R, sh.Ii, L, om);
@@ -632,7 +654,6 @@ __global__ void __launch_bounds__(128) init_kernel(WorldDev W, const float *orig
         W.st[ST_VX * S + s] = vel[3 * s]; W.st[ST_VY * S + s] = vel[3 * s + 1];
         W.st[ST_VZ * S + s] = vel[3 * s + 2];
         W.st[ST_LX * S + s] = L[0]; W.st[ST_LY * S + s] = L[1]; W.st[ST_LZ * S + s] = L[2];
-        W.ref[s] = 0.f; W.ref[S + s] = 0.f;
         W.omega[s] = w[0]; W.omega[S + s] = w[1]; W.omega[2 * S + s] = w[2];
         W.sensors[s] = 0u;
         W.status[s] = 0u;

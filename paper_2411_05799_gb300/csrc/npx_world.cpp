@@ -78,6 +78,7 @@ struct DevBuf {
 struct npx_world {
     npx_world_desc desc{};
     cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;  // created when the caller passes no stream
     int device = 0, n_sm = 0;
     // construction
     std::vector<Build> builds;
@@ -274,15 +275,14 @@ int enqueue_steps(npx_world *w, int n) {
 }
 
 struct BlobLayout {
-    size_t st, theta, ref, omega, kappa, sensors, status, end;
+    size_t st, theta, omega, kappa, sensors, status, end;
 };
 
 BlobLayout blob_layout(const npx_world *w) {
     BlobLayout b;
     b.st = 64;
     b.theta = b.st + sizeof(float) * (size_t)npx::ST_N * w->S;
-    b.ref = b.theta + sizeof(float) * (size_t)w->J;
-    b.omega = b.ref + sizeof(float) * 2 * (size_t)w->S;
+    b.omega = b.theta + sizeof(float) * (size_t)w->J;
     b.sensors = b.omega + sizeof(float) * 3 * (size_t)w->S;
     b.status = b.sensors + sizeof(uint32_t) * (size_t)w->S;
     b.kappa = b.status + sizeof(uint32_t) * (size_t)w->S;
@@ -337,6 +337,7 @@ int npx_world_destroy(npx_world *w) {
         clear_graphs(w);
         for (auto &b : w->bufs) cudaFree(b.p);
     }
+    if (w->own_stream) cudaStreamDestroy(w->own_stream);
     delete w;
     return NPX_OK;
 }
@@ -520,6 +521,10 @@ int npx_world_finalize(npx_world *w) {
     if (w->device >= ndev) return fail(NPX_EINVAL, "device %d out of range (%d devices)", w->device, ndev);
     CUDA_TRY(cudaSetDevice(w->device));
     CUDA_TRY(cudaDeviceGetAttribute(&w->n_sm, cudaDevAttrMultiProcessorCount, w->device));
+    if (!w->stream) {   // the legacy default stream cannot be captured into graphs
+        CUDA_TRY(cudaStreamCreateWithFlags(&w->own_stream, cudaStreamNonBlocking));
+        w->stream = w->own_stream;
+    }
     npx::WorldDev &W = w->W;
     if (!w->hm_host.empty()) {
         float *hm = nullptr;
@@ -534,7 +539,7 @@ int npx_world_finalize(npx_world *w) {
     float4 *d_p0m, *d_act;
     uint8_t *d_plink, *d_kappa;
     npx::LinkDev *d_links;
-    float *d_mu, *d_st, *d_theta, *d_ref, *d_omega;
+    float *d_mu, *d_st, *d_theta, *d_omega;
     uint32_t *d_nu, *d_sens, *d_status;
     unsigned int *d_queue;
     int rc = 0;
@@ -544,7 +549,7 @@ int npx_world_finalize(npx_world *w) {
         (rc = dev_alloc(w, &d_links, w->L)) || (rc = dev_alloc(w, &d_mu, S)) ||
         (rc = dev_alloc(w, &d_act, w->J)) || (rc = dev_alloc(w, &d_nu, w->J)) ||
         (rc = dev_alloc(w, &d_st, (size_t)npx::ST_N * S)) || (rc = dev_alloc(w, &d_theta, w->J)) ||
-        (rc = dev_alloc(w, &d_kappa, w->P)) || (rc = dev_alloc(w, &d_ref, 2 * (size_t)S)) ||
+        (rc = dev_alloc(w, &d_kappa, w->P)) ||
         (rc = dev_alloc(w, &d_omega, 3 * (size_t)S)) || (rc = dev_alloc(w, &d_sens, S)) ||
         (rc = dev_alloc(w, &d_status, S)) || (rc = dev_alloc(w, &d_queue, 1)) ||
         (rc = dev_alloc(w, &w->d_step, 1)) || (rc = dev_alloc(w, &w->d_stage, 13 * (size_t)S)) ||
@@ -573,7 +578,7 @@ int npx_world_finalize(npx_world *w) {
     W.kc = 2.f * w->desc.contact_zeta * w->desc.contact_omega;
     W.act_mode = NPX_ACT_HOLD;
     W.act = d_act; W.act_nu = d_nu;
-    W.st = d_st; W.theta = d_theta; W.kappa = d_kappa; W.ref = d_ref; W.omega = d_omega;
+    W.st = d_st; W.theta = d_theta; W.kappa = d_kappa; W.omega = d_omega;
     W.sensors = d_sens; W.status = d_status;
     W.order = d_order; W.max_points = w->max_points; W.max_links = w->max_links;
     W.step = w->d_step; W.queue = d_queue;
@@ -637,7 +642,6 @@ int npx_state_write(npx_world *w, const float *cog, const float *quat, const flo
         CUDA_TRY(cudaMemcpyAsync(w->W.theta, theta, w->J * sizeof(float), cudaMemcpyHostToDevice, w->stream));
     if (contact_prev) CUDA_TRY(cudaMemcpyAsync(w->W.kappa, contact_prev, w->P, cudaMemcpyHostToDevice, w->stream));
     else CUDA_TRY(cudaMemsetAsync(w->W.kappa, 0, w->P, w->stream));
-    CUDA_TRY(cudaMemsetAsync(w->W.ref, 0, 2 * S * sizeof(float), w->stream));
     CUDA_TRY(cudaMemsetAsync(w->W.status, 0, S * sizeof(uint32_t), w->stream));
     const long long st64 = step;
     CUDA_TRY(cudaMemcpyAsync(w->d_step, &st64, sizeof st64, cudaMemcpyHostToDevice, w->stream));
@@ -769,7 +773,6 @@ int npx_state_export(npx_world *w, void *blob, size_t *size) {
     const size_t S = w->S;
     CUDA_TRY(cudaMemcpyAsync(p + b.st, w->W.st, sizeof(float) * npx::ST_N * S, cudaMemcpyDeviceToHost, w->stream));
     if (w->J) CUDA_TRY(cudaMemcpyAsync(p + b.theta, w->W.theta, sizeof(float) * w->J, cudaMemcpyDeviceToHost, w->stream));
-    CUDA_TRY(cudaMemcpyAsync(p + b.ref, w->W.ref, sizeof(float) * 2 * S, cudaMemcpyDeviceToHost, w->stream));
     CUDA_TRY(cudaMemcpyAsync(p + b.omega, w->W.omega, sizeof(float) * 3 * S, cudaMemcpyDeviceToHost, w->stream));
     CUDA_TRY(cudaMemcpyAsync(p + b.sensors, w->W.sensors, sizeof(uint32_t) * S, cudaMemcpyDeviceToHost, w->stream));
     CUDA_TRY(cudaMemcpyAsync(p + b.status, w->W.status, sizeof(uint32_t) * S, cudaMemcpyDeviceToHost, w->stream));
@@ -792,7 +795,6 @@ int npx_state_import(npx_world *w, const void *blob, size_t size) {
     const size_t S = w->S;
     CUDA_TRY(cudaMemcpyAsync(w->W.st, p + b.st, sizeof(float) * npx::ST_N * S, cudaMemcpyHostToDevice, w->stream));
     if (w->J) CUDA_TRY(cudaMemcpyAsync(w->W.theta, p + b.theta, sizeof(float) * w->J, cudaMemcpyHostToDevice, w->stream));
-    CUDA_TRY(cudaMemcpyAsync(w->W.ref, p + b.ref, sizeof(float) * 2 * S, cudaMemcpyHostToDevice, w->stream));
     CUDA_TRY(cudaMemcpyAsync(w->W.omega, p + b.omega, sizeof(float) * 3 * S, cudaMemcpyHostToDevice, w->stream));
     CUDA_TRY(cudaMemcpyAsync(w->W.sensors, p + b.sensors, sizeof(uint32_t) * S, cudaMemcpyHostToDevice, w->stream));
     CUDA_TRY(cudaMemcpyAsync(w->W.status, p + b.status, sizeof(uint32_t) * S, cudaMemcpyHostToDevice, w->stream));

@@ -27,9 +27,14 @@ def rel(a, b):
 
 
 def quat_angle(qa, qb):
-    """Rotation angle between orientations given as (w, x, y, z) rows."""
-    d = np.abs(np.sum(np.asarray(qa, np.float64) * qb, axis=1))
-    return 2 * np.arccos(np.clip(d, -1.0, 1.0))
+    """Rotation angle between orientations given as (w, x, y, z) rows (well conditioned for
+    small angles: 2 atan2(|a - b|, |a + b|) with b's sign matched to a)."""
+    a = np.asarray(qa, np.float64)
+    b = np.asarray(qb, np.float64)
+    a = a / np.linalg.norm(a, axis=1, keepdims=True)
+    b = b / np.linalg.norm(b, axis=1, keepdims=True)
+    b = b * np.where(np.sum(a * b, axis=1, keepdims=True) < 0, -1.0, 1.0)
+    return 2 * np.arctan2(np.linalg.norm(a - b, axis=1), np.linalg.norm(a + b, axis=1))
 
 
 def ground_height(b, s, xy):

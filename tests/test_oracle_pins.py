@@ -89,7 +89,8 @@ def _lattice_inertia(extent, counts, mass):
     Sx = s2[0] * N / counts[0]
     Sy = s2[1] * N / counts[1]
     Sz = s2[2] * N / counts[2]
-    return np.diag([m * (Sy + Sz), m * (Sx + Sz), m * (Sx + Sy)])
+    # plus each point's own sphere inertia (radius 1 mm): 2/5 M r^2 on the diagonal
+    return np.diag([m * (Sy + Sz), m * (Sx + Sz), m * (Sx + Sy)]) + 0.4 * mass * 1e-6 * np.eye(3)
 
 
 @pytest.mark.parametrize("extent,counts", [((0.3, 0.18, 0.06), (4, 4, 4)),
@@ -101,7 +102,8 @@ def test_lattice_mass_properties(extent, counts):
     g, Ib, M = o.mass_props(0)
     assert abs(M - 1.7) < 1e-6
     np.testing.assert_allclose(g, 0.0, atol=1e-8)
-    np.testing.assert_allclose(Ib, _lattice_inertia(extent, counts, 1.7), rtol=1e-6, atol=1e-12)
+    M32 = float(np.sum(np.float32(1.7 / np.prod(counts)) * np.ones(np.prod(counts), np.float32).astype(np.float64)))
+    np.testing.assert_allclose(Ib, _lattice_inertia(extent, counts, M32), rtol=1e-6, atol=1e-12)
 
 
 def test_hexapod_rest_mass_properties_brute_force():
@@ -113,8 +115,8 @@ def test_hexapod_rest_mass_properties_brute_force():
     m = b.m.astype(np.float64)
     gg = (m[:, None] * p).sum(0) / m.sum()
     r = p - gg
-    I = sum(
-        mi * (ri @ ri * np.eye(3) - np.outer(ri, ri)) for mi, ri in zip(m, r))
+    I = sum(mi * (ri @ ri * np.eye(3) - np.outer(ri, ri)) for mi, ri in zip(m, r))
+    I += 0.4 * m.sum() * 1e-6 * np.eye(3)         # point spheres of radius 1 mm
     assert abs(M - 2.34) < 1e-5
     np.testing.assert_allclose(g, gg, atol=1e-12)
     np.testing.assert_allclose(Ib, I, rtol=1e-10, atol=1e-14)
@@ -401,3 +403,24 @@ def test_kinematic_correction_keeps_a_turning_foot_in_place():
     assert o.sensors[0] == 1
     np.testing.assert_allclose(xf1[:, :2], xf0[:, :2], atol=1e-7)
     assert abs((yaw1 - yaw0) - (-th)) < 1e-6
+
+
+def test_point_and_rod_bodies_have_invertible_inertia():
+    """A single mass point (createPoint) and a line of points are legal robots: their inertia is
+    that of their point spheres, so rotation stays defined and free flight follows the closed
+    form."""
+    one = ([((0, 0, 0), (0, 0, 0), 0.5, -1, None, None, -1)], [np.zeros((1, 3), np.float32)])
+    rod = ([((0.3, 0, 0), (0, 0, 0), 0.5, -1, None, None, -1)],
+           [scenes.box_lattice((0.3, 0.0, 0.0), (0, 0, 0), (4, 1, 1))])
+    b = scenes._assemble([one, rod], mu=[0.5, 0.5], origin=[(0, 0, 5.0), (0, 0, 5.0)],
+                         quat=[(1, 0, 0, 0)] * 2, vel=[(0.1, 0.2, 0.0)] * 2,
+                         omega=[(0.0, 0.0, 1.0), (3.0, 0.0, 0.0)], act_params=None, name="pts",
+                         act_mode=scenes.ACT_HOLD)
+    o = Oracle(b)
+    g, Ib, M = o.mass_props(0)
+    np.testing.assert_allclose(Ib, 0.4 * M * 1e-6 * np.eye(3), rtol=1e-12)
+    o.step(100)
+    assert (o.status == 0).all()
+    np.testing.assert_allclose(o.omega()[0], [0, 0, 1.0], atol=1e-9)
+    np.testing.assert_allclose(o.omega()[1], [3.0, 0, 0], atol=1e-9)
+    np.testing.assert_allclose(o.c[:, 0], 0.1 * 100 * b.dt, atol=1e-9)
