@@ -40,6 +40,7 @@ struct WorldDev {
     float *st;                            // [ST_N * S]
     float *theta;                         // [J]
     uint8_t *kappa;                       // [P] contact flag of the last step
+    float *ref;                           // [3 * S] centring reference of the friction moments
     float *omega;                         // [3 * S] angular velocity (output)
     uint32_t *sensors, *status;           // [S]
     // schedule

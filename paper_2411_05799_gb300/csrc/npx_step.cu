@@ -117,6 +117,28 @@ __device__ __forceinline__ void quat_mul(const float a[4], const float b[4], flo
     c[0] = t0; c[1] = t1; c[2] = t2; c[3] = t3;
 }
 
+// Small-angle sine/cosine and arcsine.  Inside |x| <= 1/16 the Taylor polynomials below are
+// exact to single precision (first omitted terms x^7/5040, x^8/40320 and 35 x^9/1152 are below
+// 1e-12); outside it the library functions are used.  Per-step rotation increments and friction
+// corrections are almost always tiny, so this removes the range reduction from the hot path.
+__device__ __forceinline__ void sincos_small(float x, float *s, float *c) {
+    if (fabsf(x) <= 0.0625f) {
+        const float x2 = x * x;
+        *s = x * fmaf(x2, fmaf(x2, 1.f / 120.f, -1.f / 6.f), 1.f);
+        *c = fmaf(x2, fmaf(x2, fmaf(x2, -1.f / 720.f, 1.f / 24.f), -0.5f), 1.f);
+    } else {
+        sincosf(x, s, c);
+    }
+}
+
+__device__ __forceinline__ float asin_small(float x) {
+    if (fabsf(x) <= 0.0625f) {
+        const float x2 = x * x;
+        return x * fmaf(x2, fmaf(x2, fmaf(x2, 5.f / 112.f, 3.f / 40.f), 1.f / 6.f), 1.f);
+    }
+    return asinf(x);
+}
+
 // ------------------------------------------------------------------------ shared-memory slots
 
 // Per scene: float4 pts[max_points] | float frames[12 * max_links] | float theta[max_links]
@@ -290,6 +312,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
     const int j0 = l0 - (valid ? s : 0), nj = nl - 1;
     // ---- load
     float c[3], q[4], v[3], L[3];
+    float o[3] = {0.f, 0.f, 0.f};   // centring reference of the friction moments (numerical only)
     uint32_t status = 1u;
     float mu = 0.f;
     int hm = -1;
@@ -300,6 +323,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         q[3] = W.st[ST_QZ * S + s];
         v[0] = W.st[ST_VX * S + s]; v[1] = W.st[ST_VY * S + s]; v[2] = W.st[ST_VZ * S + s];
         L[0] = W.st[ST_LX * S + s]; L[1] = W.st[ST_LY * S + s]; L[2] = W.st[ST_LZ * S + s];
+        o[0] = W.ref[s]; o[1] = W.ref[S + s]; o[2] = W.ref[2 * S + s];
         status = W.status[s];
         mu = W.mu[s];
         hm = FLAT ? -1 : W.hmap[s];
@@ -315,7 +339,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
     Shape sh;
     shape_setup<LPS>(W, p0, np, l0, nl, th, fr, pts, gl, sh);
 
-    const float dt = W.dt, kw2 = W.kw2, kc = W.kc;
+    const float dt = W.dt, idt = 1.0f / W.dt, kw2 = W.kw2, kc = W.kc;
     const bool actuated = W.act_mode != 0;
     int ph = (int)(step0 % (long long)W.K);
     for (int t = 0; t < n_steps; ++t) {
@@ -350,10 +374,16 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         float om[3];
         world_sym(R, sh.Ii, L, om);
 
-        // -- pass 1: collision against the ground and penalty normal forces
+        // -- pass 1: collision against the ground and penalty normal forces.  For the points in
+        //    contact in both steps (the friction set C, Sec. III-C) it also sums the count, first
+        //    and second moments of rho = R r about the reference point o (last step's centroid):
+        //    every term of the dynamic least squares is a function of these (see below).
         uint64_t know = 0;
-        float red[3] = {0.f, 0.f, 0.f};
-        for (int k = 0, i = gl; i < np; ++k, i += LPS) {
+        float red[13] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const int nk = gl < np ? (np - gl + LPS - 1) / LPS : 0;   // this lane's points
+#pragma unroll 4
+        for (int k = 0; k < nk; ++k) {
+            const int i = gl + k * LPS;
             const float4 r = offset(i);
             const float rz = R[6] * r.x + R[7] * r.y + R[8] * r.z;
             const float z = c[2] + rz;
@@ -374,13 +404,20 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
                 red[0] += F;
                 red[1] += ry * F;
                 red[2] -= rx * F;
+                if ((kprev >> k) & 1ull) {
+                    const float dx = rx - o[0], dy = ry - o[1], dz = rz - o[2];
+                    red[3] += 1.f;
+                    red[4] += dx; red[5] += dy; red[6] += dz;
+                    red[7] += dx * dx; red[8] += dy * dy; red[9] += dz * dz;
+                    red[10] += dx * dy; red[11] += dx * dz; red[12] += dy * dz;
+                }
             }
         }
-        gsum<LPS, 3>(red);
+        gsum<LPS, 13>(red);
         const float FN = red[0];
 
         // -- semi-implicit Euler
-        float vs[3], Ls[3], cs[3], qs[4], oms[3], Rs[9];
+        float vs[3], Ls[3], cs[3], qs[4], oms[3];
         const float iM = 1.0f / sh.M;
         vs[0] = v[0] + dt * W.gx;
         vs[1] = v[1] + dt * W.gy;
@@ -390,9 +427,9 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         Ls[2] = L[2];
         world_sym(R, sh.Ii, Ls, oms);
         cs[0] = c[0] + dt * vs[0]; cs[1] = c[1] + dt * vs[1]; cs[2] = c[2] + dt * vs[2];
-        // rotation increment dR = exp([u]x), u = dt w*: q* = dq (x) q, and D = dR - 1 =
-        // a [u]x + b [u]x^2 (a = sin|u| / |u|, b = (1 - cos|u|) / |u|^2) gives the points'
-        // rotational displacement D (R r) without the cancellation of R* r - R r
+        // rotation increment dR = exp([u]x), u = dt w*: q* = dq (x) q and R* = dR R, so a point's
+        // offset moves from rho to (1 + D) rho with D = dR - 1 = a [u]x + b [u]x^2
+        // (a = sin|u| / |u|, b = (1 - cos|u|) / |u|^2), free of the cancellation in R* r - R r
         float Dm[6];   // rows 0 and 1 of D (only horizontal displacements are needed)
         {
             const float px = dt * oms[0], py = dt * oms[1], pz = dt * oms[2];
@@ -402,7 +439,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             float fa = 1.f, fb = 0.5f;
             if (a > 0.f) {
                 float sn, cn;
-                sincosf(0.5f * a, &sn, &cn);
+                sincos_small(0.5f * a, &sn, &cn);
                 const float f = sn / a;
                 dq[0] = cn; dq[1] = f * px; dq[2] = f * py; dq[3] = f * pz;
                 fa = 2.f * f * cn;
@@ -415,121 +452,107 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             const float inv = rsqrtf(qs[0] * qs[0] + qs[1] * qs[1] + qs[2] * qs[2] + qs[3] * qs[3]);
             qs[0] *= inv; qs[1] *= inv; qs[2] *= inv; qs[3] *= inv;
         }
-        quat_mat(qs, Rs);
 
-        // -- friction over the points in contact in both steps (Sec. III-C).  Pass 2a finds
-        //    the contact centroid of the integrated points (relative to c*); pass 2b sums the
-        //    least-squares terms about it, so the FP32 sums never cancel.
-        const uint64_t cmask = kprev & know;
-        float f3[3] = {0.f, 0.f, 0.f};
-        for (uint64_t cm = cmask; cm; cm &= cm - 1) {
-            const int k = __ffsll((long long)cm) - 1;
-            const float4 r = offset(gl + k * LPS);
-            const float rh[3] = {R[0] * r.x + R[1] * r.y + R[2] * r.z,
-                                 R[3] * r.x + R[4] * r.y + R[5] * r.z,
-                                 R[6] * r.x + R[7] * r.y + R[8] * r.z};
-            f3[0] += 1.f;
-            f3[1] += rh[0] + (Dm[0] * rh[0] + Dm[1] * rh[1] + Dm[2] * rh[2]);
-            f3[2] += rh[1] + (Dm[3] * rh[0] + Dm[4] * rh[1] + Dm[5] * rh[2]);
-        }
-        gsum<LPS, 3>(f3);
-        const float nC = f3[0];
+        // -- friction (Sec. III-C, Eqs. 1-6) over C.  With d_i = rho_i - centroid and
+        //    M2 = sum d d^T, the integrated sources are s_i = [(1 + D) rho_i]_xy and the slips
+        //    e_i = -dt v*_xy - [D rho_i]_xy, so about the source centroid
+        //      S2 = a_x^T M2 a_x + a_y^T M2 a_y,  sum s~ x e = -(a_x^T M2 b_y - a_y^T M2 b_x),
+        //      mean e = -dt v*_xy - [D centroid]_xy
+        //    with a_x, a_y the x, y rows of (1 + D) and b_x, b_y those of D.
+        const float nC = red[3];
         const float in = nC > 0.f ? 1.0f / nC : 0.f;
-        const float gx = f3[1] * in, gy = f3[2] * in;      // centroid minus c*
-        // dynamic: S2, sum e, sum s x e; kinematic (joint-update steps): sum sigma, S2, sum e,
-        // sum sigma x e, with sigma the moved point minus c minus (gx, gy)
-        float f10[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        {
-            const float dcx = -dt * vs[0], dcy = -dt * vs[1];
-            for (uint64_t cm = cmask; cm; cm &= cm - 1) {
+        const float dlx = red[4] * in, dly = red[5] * in, dlz = red[6] * in;
+        const float gb[3] = {o[0] + dlx, o[1] + dly, o[2] + dlz};   // centroid of rho over C
+        float cn[3] = {cs[0], cs[1], cs[2]}, vn[3] = {vs[0], vs[1], vs[2]};
+        float Ln[3] = {Ls[0], Ls[1], Ls[2]}, qn[4] = {qs[0], qs[1], qs[2], qs[3]};
+        // kinematic least squares (joint-update steps): a second pass over C about the exact
+        // centroid of the moved points, slip R (r_old - r_new) back to the step start
+        float f6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (tick) {
+            for (uint64_t cm = kprev & know; cm; cm &= cm - 1) {
                 const int k = __ffsll((long long)cm) - 1;
                 const int i = gl + k * LPS;
                 const float4 r = offset(i);
-                const float rh[3] = {R[0] * r.x + R[1] * r.y + R[2] * r.z,
-                                     R[3] * r.x + R[4] * r.y + R[5] * r.z,
-                                     R[6] * r.x + R[7] * r.y + R[8] * r.z};
-                const float ddx = Dm[0] * rh[0] + Dm[1] * rh[1] + Dm[2] * rh[2];
-                const float ddy = Dm[3] * rh[0] + Dm[4] * rh[1] + Dm[5] * rh[2];
-                // dynamic slip back to the pre-integration position: e = -dt v* - D (R r)
-                const float sx = (rh[0] - gx) + ddx, sy = (rh[1] - gy) + ddy;
-                const float ex = dcx - ddx, ey = dcy - ddy;
-                f10[0] += sx * sx + sy * sy;
-                f10[1] += ex; f10[2] += ey; f10[3] += sx * ey - sy * ex;
-                if (tick) {
-                    // kinematic slip back to the step-start position: R (r_old - r_new)
-                    const float4 ro = pts[i];
-                    const float d[3] = {ro.x - r.x, ro.y - r.y, ro.z - r.z};
-                    const float kx = R[0] * d[0] + R[1] * d[1] + R[2] * d[2];
-                    const float ky = R[3] * d[0] + R[4] * d[1] + R[5] * d[2];
-                    const float ux = rh[0] - gx, uy = rh[1] - gy;
-                    f10[4] += ux; f10[5] += uy; f10[6] += ux * ux + uy * uy;
-                    f10[7] += kx; f10[8] += ky; f10[9] += ux * ky - uy * kx;
-                }
+                const float4 ro = pts[i];
+                const float ux = (R[0] * r.x + R[1] * r.y + R[2] * r.z) - gb[0];
+                const float uy = (R[3] * r.x + R[4] * r.y + R[5] * r.z) - gb[1];
+                const float d[3] = {ro.x - r.x, ro.y - r.y, ro.z - r.z};
+                const float kx = R[0] * d[0] + R[1] * d[1] + R[2] * d[2];
+                const float ky = R[3] * d[0] + R[4] * d[1] + R[5] * d[2];
+                f6[0] += ux; f6[1] += uy; f6[2] += ux * ux + uy * uy;
+                f6[3] += kx; f6[4] += ky; f6[5] += ux * ky - uy * kx;
             }
-            if (tick) gsum<LPS, 10>(f10);
-            else {
-                float f4[4] = {f10[0], f10[1], f10[2], f10[3]};
-                gsum<LPS, 4>(f4);
-                f10[0] = f4[0]; f10[1] = f4[1]; f10[2] = f4[2]; f10[3] = f4[3];
-            }
+            gsum<LPS, 6>(f6);
         }
-        float cn[3] = {cs[0], cs[1], cs[2]}, vn[3] = {vs[0], vs[1], vs[2]};
-        float Ln[3] = {Ls[0], Ls[1], Ls[2]}, qn[4] = {qs[0], qs[1], qs[2], qs[3]};
         if (nC >= 1.f) {
-            // dynamic least squares about the contact centroid
-            const float S2 = f10[0];
-            const float tDx = f10[1] * in, tDy = f10[2] * in;
-            const float X = f10[3];
+            const Sym M2 = {red[7] - nC * dlx * dlx, red[8] - nC * dly * dly,
+                            red[9] - nC * dlz * dlz, red[10] - nC * dlx * dly,
+                            red[11] - nC * dlx * dlz, red[12] - nC * dly * dlz};
+            const float ax[3] = {1.f + Dm[0], Dm[1], Dm[2]}, ay[3] = {Dm[3], 1.f + Dm[4], Dm[5]};
+            const float bx[3] = {Dm[0], Dm[1], Dm[2]}, by[3] = {Dm[3], Dm[4], Dm[5]};
+            float Max[3], May[3];
+            sym_mul(M2, ax, Max);
+            sym_mul(M2, ay, May);
+            const float S2 = ax[0] * Max[0] + ax[1] * Max[1] + ax[2] * Max[2] +
+                             ay[0] * May[0] + ay[1] * May[1] + ay[2] * May[2];
+            const float X = -((Max[0] * by[0] + Max[1] * by[1] + Max[2] * by[2]) -
+                              (May[0] * bx[0] + May[1] * bx[1] + May[2] * bx[2]));
+            const float sbx = ax[0] * gb[0] + ax[1] * gb[1] + ax[2] * gb[2];  // source centroid - c*
+            const float sby = ay[0] * gb[0] + ay[1] * gb[1] + ay[2] * gb[2];
+            const float tDx = -dt * vs[0] - (bx[0] * gb[0] + bx[1] * gb[1] + bx[2] * gb[2]);
+            const float tDy = -dt * vs[1] - (by[0] * gb[0] + by[1] * gb[1] + by[2] * gb[2]);
             float a3 = (nC >= 2.f && S2 > 1e-12f) ? X / S2 : 0.f;
             a3 = fminf(fmaxf(a3, -1.f), 1.f);
             const float cD = sqrtf(fmaxf(0.f, 1.f - a3 * a3));
             const float cm1 = -a3 * a3 / (1.f + cD);                  // cos(alpha_D) - 1
-            const float dDx = -gx, dDy = -gy;                         // CoG minus centroid
+            const float dDx = -sbx, dDy = -sby;                       // CoG minus centroid
             const float DDx = tDx + cm1 * dDx - a3 * dDy;             // uncapped CoG shift
             const float DDy = tDy + a3 * dDx + cm1 * dDy;
             // maximum static friction (Coulomb cap on the impulse that undoes the slip)
             const float sh2 = a3 * a3 / (2.f * (1.f + cD));            // sin^2(alpha_D / 2)
             const float u2 = tDx * tDx + tDy * tDy + 4.f * sh2 * S2 * in;
-            const float Jreq = sh.M * sqrtf(u2) / dt;
+            const float Jreq = sh.M * sqrtf(u2) * idt;
             const float Jmax = mu * dt * FN;
-            const float sc = (Jreq <= Jmax) ? 1.f : Jmax / Jreq;
-            const float aD = asinf(a3);
+            const float sc = (Jreq <= Jmax) ? 1.f : __fdividef(Jmax, Jreq);
+            const float aD = asin_small(a3);
             float s1, c1;
-            sincosf(0.5f * sc * aD, &s1, &c1);
+            sincos_small(0.5f * sc * aD, &s1, &c1);
             const float sin1 = 2.f * s1 * c1, cm1s = -2.f * s1 * s1;
             float dx1 = sc * tDx + cm1s * dDx - sin1 * dDy;
             float dy1 = sc * tDy + sin1 * dDx + cm1s * dDy;
             float A = sc * aD;
             if (tick) {
-                // kinematic least squares about the centroid of the moved points
-                const float kbx = f10[4] * in, kby = f10[5] * in;
-                const float S2K = f10[6] - nC * (kbx * kbx + kby * kby);
-                const float tKx = f10[7] * in, tKy = f10[8] * in;
-                const float XK = f10[9] - (kbx * f10[8] - kby * f10[7]);
+                const float kbx = f6[0] * in, kby = f6[1] * in;
+                const float S2K = f6[2] - nC * (kbx * kbx + kby * kby);
+                const float tKx = f6[3] * in, tKy = f6[4] * in;
+                const float XK = f6[5] - (kbx * f6[4] - kby * f6[3]);
                 float a3K = (nC >= 2.f && S2K > 1e-12f) ? XK / S2K : 0.f;
                 a3K = fminf(fmaxf(a3K, -1.f), 1.f);
-                const float aK = asinf(a3K);
+                const float aK = asin_small(a3K);
                 float s2, c2;
-                sincosf(0.5f * aK, &s2, &c2);
+                sincos_small(0.5f * aK, &s2, &c2);
                 const float sin2 = 2.f * s2 * c2, cm2 = -2.f * s2 * s2;
-                // moved-point centroid is c + (gx, gy) + kb; CoG after the dynamic map is cs + d1
-                const float dKx = (cs[0] - c[0]) + dx1 - (gx + kbx);
-                const float dKy = (cs[1] - c[1]) + dy1 - (gy + kby);
+                // moved-point centroid is c + gb + kb; CoG after the dynamic map is cs + d1
+                const float dKx = (cs[0] - c[0]) + dx1 - (gb[0] + kbx);
+                const float dKy = (cs[1] - c[1]) + dy1 - (gb[1] + kby);
                 dx1 += tKx + cm2 * dKx - sin2 * dKy;
                 dy1 += tKy + sin2 * dKx + cm2 * dKy;
                 A += aK;
             }
             cn[0] = cs[0] + dx1;
             cn[1] = cs[1] + dy1;
-            vn[0] = vs[0] + sc * DDx / dt;
-            vn[1] = vs[1] + sc * DDy / dt;
+            vn[0] = vs[0] + sc * DDx * idt;
+            vn[1] = vs[1] + sc * DDy * idt;
+            // angular momentum of the yaw correction: (sc alpha_D / dt) R* Ib R*^T z
+            float Rs[9];
+            quat_mat(qs, Rs);
             const float ez[3] = {0.f, 0.f, 1.f};
             float Iz[3];
             world_sym(Rs, sh.Ib, ez, Iz);
-            const float w = sc * aD / dt;
+            const float w = sc * aD * idt;
             Ln[0] = Ls[0] + w * Iz[0]; Ln[1] = Ls[1] + w * Iz[1]; Ln[2] = Ls[2] + w * Iz[2];
             float sa, ca;
-            sincosf(0.5f * A, &sa, &ca);
+            sincos_small(0.5f * A, &sa, &ca);
             const float qz[4] = {ca, 0.f, 0.f, sa};
             quat_mul(qz, qs, qn);
         }
@@ -541,11 +564,11 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
 
         // -- freeze a scene whose state is no longer finite or has left any sane range
         if (status == 0u) {
-            bool fin = true;
-#pragma unroll
-            for (int i = 0; i < 3; ++i) fin = fin && isfinite(cn[i]) && isfinite(vn[i]) && isfinite(Ln[i]);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) fin = fin && isfinite(qn[i]);
+            // any NaN or infinity makes the sum non-finite (all terms are bounded below 1e6
+            // in magnitude when finite, so the sum itself cannot overflow)
+            const float chk = cn[0] + cn[1] + cn[2] + vn[0] + vn[1] + vn[2] + Ln[0] + Ln[1] +
+                              Ln[2] + qn[0] + qn[1] + qn[2] + qn[3];
+            const bool fin = isfinite(chk);
             if (!fin) {
                 status |= 1u;
             } else if (fabsf(vn[0]) > 1e3f || fabsf(vn[1]) > 1e3f || fabsf(vn[2]) > 1e3f ||
@@ -557,6 +580,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
 #pragma unroll
                 for (int i = 0; i < 4; ++i) q[i] = qn[i];
                 kprev = know;
+                if (nC >= 1.f) { o[0] = gb[0]; o[1] = gb[1]; o[2] = gb[2]; }
             }
         }
     }
@@ -584,6 +608,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         quat_mat(q, R);
         world_sym(R, sh.Ii, L, om);
         W.omega[s] = om[0]; W.omega[S + s] = om[1]; W.omega[2 * S + s] = om[2];
+        W.ref[s] = o[0]; W.ref[S + s] = o[1]; W.ref[2 * S + s] = o[2];
         W.sensors[s] = sens;
         W.status[s] = status;
     }
@@ -655,6 +680,7 @@ __global__ void __launch_bounds__(128) init_kernel(WorldDev W, const float *orig
         W.st[ST_VZ * S + s] = vel[3 * s + 2];
         W.st[ST_LX * S + s] = L[0]; W.st[ST_LY * S + s] = L[1]; W.st[ST_LZ * S + s] = L[2];
         W.omega[s] = w[0]; W.omega[S + s] = w[1]; W.omega[2 * S + s] = w[2];
+        W.ref[s] = 0.f; W.ref[S + s] = 0.f; W.ref[2 * S + s] = 0.f;
         W.sensors[s] = 0u;
         W.status[s] = 0u;
     }

@@ -275,14 +275,15 @@ int enqueue_steps(npx_world *w, int n) {
 }
 
 struct BlobLayout {
-    size_t st, theta, omega, kappa, sensors, status, end;
+    size_t st, theta, ref, omega, kappa, sensors, status, end;
 };
 
 BlobLayout blob_layout(const npx_world *w) {
     BlobLayout b;
     b.st = 64;
     b.theta = b.st + sizeof(float) * (size_t)npx::ST_N * w->S;
-    b.omega = b.theta + sizeof(float) * (size_t)w->J;
+    b.ref = b.theta + sizeof(float) * (size_t)w->J;
+    b.omega = b.ref + sizeof(float) * 3 * (size_t)w->S;
     b.sensors = b.omega + sizeof(float) * 3 * (size_t)w->S;
     b.status = b.sensors + sizeof(uint32_t) * (size_t)w->S;
     b.kappa = b.status + sizeof(uint32_t) * (size_t)w->S;
@@ -539,7 +540,7 @@ int npx_world_finalize(npx_world *w) {
     float4 *d_p0m, *d_act;
     uint8_t *d_plink, *d_kappa;
     npx::LinkDev *d_links;
-    float *d_mu, *d_st, *d_theta, *d_omega;
+    float *d_mu, *d_st, *d_theta, *d_ref, *d_omega;
     uint32_t *d_nu, *d_sens, *d_status;
     unsigned int *d_queue;
     int rc = 0;
@@ -549,7 +550,7 @@ int npx_world_finalize(npx_world *w) {
         (rc = dev_alloc(w, &d_links, w->L)) || (rc = dev_alloc(w, &d_mu, S)) ||
         (rc = dev_alloc(w, &d_act, w->J)) || (rc = dev_alloc(w, &d_nu, w->J)) ||
         (rc = dev_alloc(w, &d_st, (size_t)npx::ST_N * S)) || (rc = dev_alloc(w, &d_theta, w->J)) ||
-        (rc = dev_alloc(w, &d_kappa, w->P)) ||
+        (rc = dev_alloc(w, &d_kappa, w->P)) || (rc = dev_alloc(w, &d_ref, 3 * (size_t)S)) ||
         (rc = dev_alloc(w, &d_omega, 3 * (size_t)S)) || (rc = dev_alloc(w, &d_sens, S)) ||
         (rc = dev_alloc(w, &d_status, S)) || (rc = dev_alloc(w, &d_queue, 1)) ||
         (rc = dev_alloc(w, &w->d_step, 1)) || (rc = dev_alloc(w, &w->d_stage, 13 * (size_t)S)) ||
@@ -578,7 +579,7 @@ int npx_world_finalize(npx_world *w) {
     W.kc = 2.f * w->desc.contact_zeta * w->desc.contact_omega;
     W.act_mode = NPX_ACT_HOLD;
     W.act = d_act; W.act_nu = d_nu;
-    W.st = d_st; W.theta = d_theta; W.kappa = d_kappa; W.omega = d_omega;
+    W.st = d_st; W.theta = d_theta; W.kappa = d_kappa; W.ref = d_ref; W.omega = d_omega;
     W.sensors = d_sens; W.status = d_status;
     W.order = d_order; W.max_points = w->max_points; W.max_links = w->max_links;
     W.step = w->d_step; W.queue = d_queue;
@@ -643,6 +644,7 @@ int npx_state_write(npx_world *w, const float *cog, const float *quat, const flo
     if (contact_prev) CUDA_TRY(cudaMemcpyAsync(w->W.kappa, contact_prev, w->P, cudaMemcpyHostToDevice, w->stream));
     else CUDA_TRY(cudaMemsetAsync(w->W.kappa, 0, w->P, w->stream));
     CUDA_TRY(cudaMemsetAsync(w->W.status, 0, S * sizeof(uint32_t), w->stream));
+    CUDA_TRY(cudaMemsetAsync(w->W.ref, 0, 3 * S * sizeof(float), w->stream));
     const long long st64 = step;
     CUDA_TRY(cudaMemcpyAsync(w->d_step, &st64, sizeof st64, cudaMemcpyHostToDevice, w->stream));
     CUDA_TRY(npx::launch_refresh(w->W, w->stream));
@@ -773,6 +775,7 @@ int npx_state_export(npx_world *w, void *blob, size_t *size) {
     const size_t S = w->S;
     CUDA_TRY(cudaMemcpyAsync(p + b.st, w->W.st, sizeof(float) * npx::ST_N * S, cudaMemcpyDeviceToHost, w->stream));
     if (w->J) CUDA_TRY(cudaMemcpyAsync(p + b.theta, w->W.theta, sizeof(float) * w->J, cudaMemcpyDeviceToHost, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(p + b.ref, w->W.ref, sizeof(float) * 3 * S, cudaMemcpyDeviceToHost, w->stream));
     CUDA_TRY(cudaMemcpyAsync(p + b.omega, w->W.omega, sizeof(float) * 3 * S, cudaMemcpyDeviceToHost, w->stream));
     CUDA_TRY(cudaMemcpyAsync(p + b.sensors, w->W.sensors, sizeof(uint32_t) * S, cudaMemcpyDeviceToHost, w->stream));
     CUDA_TRY(cudaMemcpyAsync(p + b.status, w->W.status, sizeof(uint32_t) * S, cudaMemcpyDeviceToHost, w->stream));
@@ -795,6 +798,7 @@ int npx_state_import(npx_world *w, const void *blob, size_t size) {
     const size_t S = w->S;
     CUDA_TRY(cudaMemcpyAsync(w->W.st, p + b.st, sizeof(float) * npx::ST_N * S, cudaMemcpyHostToDevice, w->stream));
     if (w->J) CUDA_TRY(cudaMemcpyAsync(w->W.theta, p + b.theta, sizeof(float) * w->J, cudaMemcpyHostToDevice, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(w->W.ref, p + b.ref, sizeof(float) * 3 * S, cudaMemcpyHostToDevice, w->stream));
     CUDA_TRY(cudaMemcpyAsync(w->W.omega, p + b.omega, sizeof(float) * 3 * S, cudaMemcpyHostToDevice, w->stream));
     CUDA_TRY(cudaMemcpyAsync(w->W.sensors, p + b.sensors, sizeof(uint32_t) * S, cudaMemcpyHostToDevice, w->stream));
     CUDA_TRY(cudaMemcpyAsync(w->W.status, p + b.status, sizeof(uint32_t) * S, cudaMemcpyHostToDevice, w->stream));
@@ -864,10 +868,20 @@ int npx_world_autotune(npx_world *w, int n_steps, npx_world_info *out) {
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
     const int lps_list[3] = {8, 16, 32};
-    const int wpb_list[4] = {2, 4, 8, 16};
     int rc_out = NPX_OK;
     for (int lps : lps_list) {
         if (w->max_points > 64 * lps) continue;
+        // fixed block sizes plus the "balanced" ones that spread the scenes evenly over all SMs
+        // with 1, 2 or 3 resident blocks per SM
+        std::vector<int> wpb_list = {2, 4, 8, 16};
+        const int G = 32 / lps;
+        for (int k = 1; k <= 3; ++k) {
+            const long long per = (long long)w->n_sm * G * k;
+            const int wb = (int)((w->S + per - 1) / per);
+            if (wb >= 1 && wb <= 16 &&
+                std::find(wpb_list.begin(), wpb_list.end(), wb) == wpb_list.end())
+                wpb_list.push_back(wb);
+        }
         for (int wpb : wpb_list) {
             int rc;
             npx::LaunchCfg c = clamp_cfg(w, {lps, wpb, 0}, &rc);
