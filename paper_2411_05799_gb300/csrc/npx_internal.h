@@ -24,10 +24,12 @@ struct WorldDev {
     const int *link_off, *point_off;      // [S+1]
     const float4 *p0m;                    // [P] construction position (xyz) and mass (w)
     const uint8_t *plink;                 // [P] scene-local link of each point
+    const float *gref;                    // [3 * S] rest-pose CoG (centring reference of sums)
     const LinkDev *links;                 // [L]
     const float *mu;                      // [S]
     const int *hmap;                      // [S] height map per scene, -1 = flat z = 0
     const float *hm;                      // [H * ny * nx]
+    const float *hm_max;                  // [H] highest cell of each map
     int hm_nx, hm_ny;
     float hm_scale, hm_ox, hm_oy;
     float dt, gx, gy, gz;
@@ -40,7 +42,6 @@ struct WorldDev {
     float *st;                            // [ST_N * S]
     float *theta;                         // [J]
     uint8_t *kappa;                       // [P] contact flag of the last step
-    float *ref;                           // [3 * S] centring reference of the friction moments
     float *omega;                         // [3 * S] angular velocity (output)
     uint32_t *sensors, *status;           // [S]
     // schedule

@@ -33,7 +33,7 @@ namespace npx {
 
 #define FULL_MASK 0xffffffffu
 
-constexpr float POINT_RADIUS = 1e-3f;   // m, see mass_props
+constexpr float POINT_RADIUS = 1e-3f;   // m, see shape_update
 
 // ------------------------------------------------------------------------ group reductions
 
@@ -43,6 +43,50 @@ __device__ __forceinline__ void gsum(float (&v)[N]) {
     for (int o = LPS / 2; o > 0; o >>= 1) {
 #pragma unroll
         for (int i = 0; i < N; ++i) v[i] += __shfl_xor_sync(FULL_MASK, v[i], o);
+    }
+}
+
+// Count, mean and second central moment (symmetric 3x3: xx yy zz xy xz yz) of a point set,
+// merged across the group with Chan's pairwise formula.  The merge is written symmetrically in
+// its two operands (the partner's sign of the mean difference cancels in the outer product), so
+// every lane ends with bit-identical moments.
+struct Moments {
+    float n, m[3], M[6];
+};
+
+__device__ __forceinline__ void moments_add(Moments &a, const float x[3]) {
+    const float n1 = a.n + 1.f, f = 1.f / n1, w = a.n * f;
+    const float d0 = x[0] - a.m[0], d1 = x[1] - a.m[1], d2 = x[2] - a.m[2];
+    a.m[0] += d0 * f; a.m[1] += d1 * f; a.m[2] += d2 * f;
+    a.M[0] += w * d0 * d0; a.M[1] += w * d1 * d1; a.M[2] += w * d2 * d2;
+    a.M[3] += w * d0 * d1; a.M[4] += w * d0 * d2; a.M[5] += w * d1 * d2;
+    a.n = n1;
+}
+
+template <int LPS>
+__device__ __forceinline__ void moments_reduce(Moments &a) {
+#pragma unroll
+    for (int o = LPS / 2; o > 0; o >>= 1) {
+        Moments b;
+        b.n = __shfl_xor_sync(FULL_MASK, a.n, o);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) b.m[i] = __shfl_xor_sync(FULL_MASK, a.m[i], o);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) b.M[i] = __shfl_xor_sync(FULL_MASK, a.M[i], o);
+        const float n = a.n + b.n;
+        const float inv = n > 0.f ? 1.f / n : 0.f;
+        const float w = a.n * b.n * inv;
+        const float d0 = b.m[0] - a.m[0], d1 = b.m[1] - a.m[1], d2 = b.m[2] - a.m[2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)   // no FMA contraction: keep the merge symmetric
+            a.m[i] = (__fmul_rn(a.n, a.m[i]) + __fmul_rn(b.n, b.m[i])) * inv;
+        a.M[0] = (a.M[0] + b.M[0]) + w * (d0 * d0);
+        a.M[1] = (a.M[1] + b.M[1]) + w * (d1 * d1);
+        a.M[2] = (a.M[2] + b.M[2]) + w * (d2 * d2);
+        a.M[3] = (a.M[3] + b.M[3]) + w * (d0 * d1);
+        a.M[4] = (a.M[4] + b.M[4]) + w * (d0 * d2);
+        a.M[5] = (a.M[5] + b.M[5]) + w * (d1 * d2);
+        a.n = n;
     }
 }
 
@@ -121,13 +165,16 @@ __device__ __forceinline__ void quat_mul(const float a[4], const float b[4], flo
 // exact to single precision (first omitted terms x^7/5040, x^8/40320 and 35 x^9/1152 are below
 // 1e-12); outside it the library functions are used.  Per-step rotation increments and friction
 // corrections are almost always tiny, so this removes the range reduction from the hot path.
+__device__ __noinline__ void sincos_large(float x, float *s, float *c) { sincosf(x, s, c); }
+__device__ __noinline__ float asin_large(float x) { return asinf(x); }
+
 __device__ __forceinline__ void sincos_small(float x, float *s, float *c) {
     if (fabsf(x) <= 0.0625f) {
         const float x2 = x * x;
         *s = x * fmaf(x2, fmaf(x2, 1.f / 120.f, -1.f / 6.f), 1.f);
         *c = fmaf(x2, fmaf(x2, fmaf(x2, -1.f / 720.f, 1.f / 24.f), -0.5f), 1.f);
     } else {
-        sincosf(x, s, c);
+        sincos_large(x, s, c);
     }
 }
 
@@ -136,15 +183,51 @@ __device__ __forceinline__ float asin_small(float x) {
         const float x2 = x * x;
         return x * fmaf(x2, fmaf(x2, fmaf(x2, 5.f / 112.f, 3.f / 40.f), 1.f / 6.f), 1.f);
     }
-    return asinf(x);
+    return asin_large(x);
 }
 
 // ------------------------------------------------------------------------ shared-memory slots
 
-// Per scene: float4 pts[max_points] | float frames[12 * max_links] | float theta[max_links]
-__host__ __device__ inline int slot_bytes(int max_points, int max_links) {
-    int b = 16 * max_points + 48 * max_links + 4 * max_links;
-    return (b + 15) & ~15;
+// Per scene: float4 pts[max_points] | float frames[12 * max_links] | float theta[max_links] |
+// float theta_old[max_links] | float4 tile bounds[2 * ceil(max_points / lps)]
+__host__ __device__ inline int tiles_offset(int max_points, int max_links) {
+    return (16 * max_points + 56 * max_links + 15) & ~15;
+}
+__host__ __device__ inline int slot_bytes(int max_points, int max_links, int lps) {
+    return tiles_offset(max_points, max_links) + 32 * ((max_points + lps - 1) / lps);
+}
+
+// Bounding boxes for skipping points that cannot touch the ground.  Tile t holds points
+// [t*LPS, (t+1)*LPS) of a scene (stored in ascending construction-frame height); tb[2t], tb[2t+1]
+// are the min / max corners of the offsets r of every point in tiles t, t+1, ..., so that
+// c_z + min over that box of (R r)_z bounds from below the height of all remaining points.
+template <int LPS>
+__device__ __noinline__ void tile_bounds(const float4 *pts, int np, float4 *tb, int gl) {
+    const int nt = (np + LPS - 1) / LPS;
+    for (int t = gl; t < nt; t += LPS) {
+        float4 lo = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+        float4 hi = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
+        const int e = min(np, (t + 1) * LPS);
+        for (int i = t * LPS; i < e; ++i) {
+            const float4 r = pts[i];
+            lo.x = fminf(lo.x, r.x); lo.y = fminf(lo.y, r.y); lo.z = fminf(lo.z, r.z);
+            hi.x = fmaxf(hi.x, r.x); hi.y = fmaxf(hi.y, r.y); hi.z = fmaxf(hi.z, r.z);
+        }
+        tb[2 * t] = lo;
+        tb[2 * t + 1] = hi;
+    }
+    __syncwarp();
+    if (gl == 0) {
+        for (int t = nt - 2; t >= 0; --t) {
+            float4 lo = tb[2 * t], hi = tb[2 * t + 1];
+            const float4 l2 = tb[2 * t + 2], h2 = tb[2 * t + 3];
+            lo.x = fminf(lo.x, l2.x); lo.y = fminf(lo.y, l2.y); lo.z = fminf(lo.z, l2.z);
+            hi.x = fmaxf(hi.x, h2.x); hi.y = fmaxf(hi.y, h2.y); hi.z = fmaxf(hi.z, h2.z);
+            tb[2 * t] = lo;
+            tb[2 * t + 1] = hi;
+        }
+    }
+    __syncwarp();
 }
 
 // ------------------------------------------------------------------------ kinematics (Sec. III-B)
@@ -154,7 +237,7 @@ __host__ __device__ inline int slot_bytes(int max_points, int max_links) {
 // hinge rotation by theta about the unit axis through the anchor.  Lanes build the local hinge
 // transforms in parallel, then compose them one tree level at a time.
 template <int LPS>
-__device__ void link_frames(const WorldDev &W, int l0, int nl, const float *th, float *fr, int gl) {
+__device__ __noinline__ void link_frames(const WorldDev &W, int l0, int nl, const float *th, float *fr, int gl) {
     for (int l = gl; l < nl; l += LPS) {
         float *F = fr + 12 * l;
         if (l == 0) {
@@ -215,17 +298,26 @@ struct Shape {
     Sym Ib, Ii;
 };
 
-// Mass properties of the posed point cloud (Sec. III-A: the mass points give CoG and momentum),
-// accumulated about a reference point close to the CoG so that the FP32 sums do not cancel.
+// Posed shape as a pure function of the joint angles (Sec. III-A: the mass points give the CoG
+// and the momentum; Sec. III-B: the segments move rigidly with their joints): link frames, one
+// forward-kinematics pass that stores each point relative to the scene's rest CoG gref and sums
+// the mass moments about it, then the CoG, the inertia about the CoG (parallel-axis theorem; gref
+// is close to the CoG, so the FP32 sums do not cancel) and a recentring of the stored offsets.
+// Being a function of theta alone, the result does not depend on where a launch (chunk) starts.
 template <int LPS>
-__device__ void mass_props(const WorldDev &W, int p0, int np, const float *fr, int gl,
-                           const float ref[3], Shape &sh) {
+__device__ __noinline__ void shape_update(const WorldDev &W, int s, int p0, int np, int l0, int nl,
+                                          const float *th, float *fr, float4 *pts, int gl,
+                                          Shape &sh) {
+    link_frames<LPS>(W, l0, nl, th, fr, gl);
+    const float gref[3] = {W.gref[3 * s], W.gref[3 * s + 1], W.gref[3 * s + 2]};
     float a[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
     for (int i = gl; i < np; i += LPS) {
         const float4 q = W.p0m[p0 + i];
         float p[3];
         fk_point(fr, q, W.plink[p0 + i], p);
-        const float dx = p[0] - ref[0], dy = p[1] - ref[1], dz = p[2] - ref[2], m = q.w;
+        const float dx = p[0] - gref[0], dy = p[1] - gref[1], dz = p[2] - gref[2], m = q.w;
+        pts[i] = make_float4(dx, dy, dz, m);
         a[0] += m;
         a[1] += m * dx; a[2] += m * dy; a[3] += m * dz;
         a[4] += m * dx * dx; a[5] += m * dy * dy; a[6] += m * dz * dz;
@@ -234,44 +326,22 @@ __device__ void mass_props(const WorldDev &W, int p0, int np, const float *fr, i
     gsum<LPS, 10>(a);
     const float M = a[0], dx = a[1] / M, dy = a[2] / M, dz = a[3] / M;
     sh.M = M;
-    sh.g[0] = ref[0] + dx; sh.g[1] = ref[1] + dy; sh.g[2] = ref[2] + dz;
-    // inertia about the CoG = about the reference minus the parallel-axis term
-    sh.Ib.xx = (a[5] + a[6]) - M * (dy * dy + dz * dz);
-    sh.Ib.yy = (a[4] + a[6]) - M * (dx * dx + dz * dz);
-    sh.Ib.zz = (a[4] + a[5]) - M * (dx * dx + dy * dy);
-    // every mass point is a solid sphere of radius POINT_RADIUS (2/5 m r^2 about any axis), so
-    // a single point or a line of points still has an invertible inertia
+    sh.g[0] = gref[0] + dx; sh.g[1] = gref[1] + dy; sh.g[2] = gref[2] + dz;
+    // inertia about the CoG = about gref minus the parallel-axis term; every mass point is also a
+    // solid sphere of radius POINT_RADIUS (2/5 m r^2 about any axis), so that a single point or a
+    // line of points still has an invertible inertia
     const float ps = 0.4f * M * POINT_RADIUS * POINT_RADIUS;
-    sh.Ib.xx += ps; sh.Ib.yy += ps; sh.Ib.zz += ps;
+    sh.Ib.xx = (a[5] + a[6]) - M * (dy * dy + dz * dz) + ps;
+    sh.Ib.yy = (a[4] + a[6]) - M * (dx * dx + dz * dz) + ps;
+    sh.Ib.zz = (a[4] + a[5]) - M * (dx * dx + dy * dy) + ps;
     sh.Ib.xy = -a[7] + M * dx * dy;
     sh.Ib.xz = -a[8] + M * dx * dz;
     sh.Ib.yz = -a[9] + M * dy * dz;
     sh.Ii = sym_inv(sh.Ib);
-}
-
-// Frames and mass properties as a pure function of the joint angles: the CoG from sums about the
-// construction origin, then the inertia from sums about that CoG.  Being a function of theta
-// alone makes the result independent of where a launch (chunk) starts.
-template <int LPS>
-__device__ void shape_props(const WorldDev &W, int p0, int np, int l0, int nl, const float *th,
-                            float *fr, int gl, Shape &sh) {
-    link_frames<LPS>(W, l0, nl, th, fr, gl);
-    const float zero[3] = {0.f, 0.f, 0.f};
-    mass_props<LPS>(W, p0, np, fr, gl, zero, sh);
-    const float g0[3] = {sh.g[0], sh.g[1], sh.g[2]};
-    mass_props<LPS>(W, p0, np, fr, gl, g0, sh);
-}
-
-// Full shape set-up from the current joint angles: frames, mass properties, r_i in smem.
-template <int LPS>
-__device__ void shape_setup(const WorldDev &W, int p0, int np, int l0, int nl, const float *th,
-                            float *fr, float4 *pts, int gl, Shape &sh) {
-    shape_props<LPS>(W, p0, np, l0, nl, th, fr, gl, sh);
     for (int i = gl; i < np; i += LPS) {
-        const float4 q = W.p0m[p0 + i];
-        float p[3];
-        fk_point(fr, q, W.plink[p0 + i], p);
-        pts[i] = make_float4(p[0] - sh.g[0], p[1] - sh.g[1], p[2] - sh.g[2], q.w);
+        float4 r = pts[i];
+        r.x -= dx; r.y -= dy; r.z -= dz;
+        pts[i] = r;
     }
     __syncwarp();
 }
@@ -302,7 +372,7 @@ __device__ __forceinline__ float joint_target(const WorldDev &W, int j, long lon
 
 template <int LPS, bool FLAT>
 __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *fr, float *th,
-                          int n_steps, long long step0) {
+                          float *th_old, float4 *tb, int n_steps, long long step0) {
     const bool valid = s >= 0;
     int p0 = 0, np = 0, l0 = 0, nl = 1;
     if (valid) {
@@ -312,7 +382,6 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
     const int j0 = l0 - (valid ? s : 0), nj = nl - 1;
     // ---- load
     float c[3], q[4], v[3], L[3];
-    float o[3] = {0.f, 0.f, 0.f};   // centring reference of the friction moments (numerical only)
     uint32_t status = 1u;
     float mu = 0.f;
     int hm = -1;
@@ -323,7 +392,6 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         q[3] = W.st[ST_QZ * S + s];
         v[0] = W.st[ST_VX * S + s]; v[1] = W.st[ST_VY * S + s]; v[2] = W.st[ST_VZ * S + s];
         L[0] = W.st[ST_LX * S + s]; L[1] = W.st[ST_LY * S + s]; L[2] = W.st[ST_LZ * S + s];
-        o[0] = W.ref[s]; o[1] = W.ref[S + s]; o[2] = W.ref[2 * S + s];
         status = W.status[s];
         mu = W.mu[s];
         hm = FLAT ? -1 : W.hmap[s];
@@ -337,7 +405,11 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         if (W.kappa[p0 + i]) kprev |= 1ull << k;
     __syncwarp();
     Shape sh;
-    shape_setup<LPS>(W, p0, np, l0, nl, th, fr, pts, gl, sh);
+    shape_update<LPS>(W, valid ? s : 0, p0, np, l0, nl, th, fr, pts, gl, sh);
+    tile_bounds<LPS>(pts, np, tb, gl);
+    // highest ground a point can meet (plus a margin for the rounding of the bound)
+    const float hmax = (FLAT || hm < 0 ? 0.f : W.hm_max[hm]) + 1e-5f;
+    const int ntiles = (np + LPS - 1) / LPS;
 
     const float dt = W.dt, idt = 1.0f / W.dt, kw2 = W.kw2, kc = W.kc;
     const bool actuated = W.act_mode != 0;
@@ -349,27 +421,21 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         float R[9];
         quat_mat(q, R);
 
-        // -- joint-angle determination: new angles, frames and mass properties.  The new
-        //    offsets r_new are evaluated on the fly from the frames; smem keeps r_old until
-        //    the end of the step.
+        // -- joint-angle determination: new angles, frames, mass properties and offsets; the
+        //    old angles and CoG are kept for the kinematic slip of the contact points
+        float gold[3] = {sh.g[0], sh.g[1], sh.g[2]};
         if (tick) {
-            if (status == 0u) {   // a frozen scene keeps its angles
-                for (int j = gl; j < nj; j += LPS) {
+            for (int j = gl; j < nj; j += LPS) {
+                th_old[j] = th[j];
+                if (status == 0u) {   // a frozen scene keeps its angles
                     const LinkDev lk = W.links[l0 + j + 1];
                     th[j] = fminf(fmaxf(joint_target(W, j0 + j, n), lk.lo), lk.hi);
                 }
             }
             __syncwarp();
-            shape_props<LPS>(W, p0, np, l0, nl, th, fr, gl, sh);
+            shape_update<LPS>(W, valid ? s : 0, p0, np, l0, nl, th, fr, pts, gl, sh);
+            tile_bounds<LPS>(pts, np, tb, gl);
         }
-        // offsets used this step: r_new on joint-update steps, else the stored ones
-        auto offset = [&](int i) -> float4 {
-            if (!tick) return pts[i];
-            const float4 a = W.p0m[p0 + i];
-            float p[3];
-            fk_point(fr, a, W.plink[p0 + i], p);
-            return make_float4(p[0] - sh.g[0], p[1] - sh.g[1], p[2] - sh.g[2], a.w);
-        };
 
         float om[3];
         world_sym(R, sh.Ii, L, om);
@@ -379,12 +445,18 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         //    and second moments of rho = R r about the reference point o (last step's centroid):
         //    every term of the dynamic least squares is a function of these (see below).
         uint64_t know = 0;
-        float red[13] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        const int nk = gl < np ? (np - gl + LPS - 1) / LPS : 0;   // this lane's points
-#pragma unroll 4
-        for (int k = 0; k < nk; ++k) {
+        float red[3] = {0.f, 0.f, 0.f};
+        Moments mc = {0.f, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}};
+        for (int k = 0; k < ntiles; ++k) {
+            {   // stop once every remaining point is provably above the ground
+                const float4 lo = tb[2 * k], hi = tb[2 * k + 1];
+                const float zb = c[2] + fminf(R[6] * lo.x, R[6] * hi.x) +
+                                 fminf(R[7] * lo.y, R[7] * hi.y) + fminf(R[8] * lo.z, R[8] * hi.z);
+                if (zb > hmax) break;
+            }
             const int i = gl + k * LPS;
-            const float4 r = offset(i);
+            if (i >= np) continue;
+            const float4 r = pts[i];
             const float rz = R[6] * r.x + R[7] * r.y + R[8] * r.z;
             const float z = c[2] + rz;
             float rx = 0.f, ry = 0.f, h = 0.f;
@@ -405,15 +477,13 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
                 red[1] += ry * F;
                 red[2] -= rx * F;
                 if ((kprev >> k) & 1ull) {
-                    const float dx = rx - o[0], dy = ry - o[1], dz = rz - o[2];
-                    red[3] += 1.f;
-                    red[4] += dx; red[5] += dy; red[6] += dz;
-                    red[7] += dx * dx; red[8] += dy * dy; red[9] += dz * dz;
-                    red[10] += dx * dy; red[11] += dx * dz; red[12] += dy * dz;
+                    const float rho[3] = {rx, ry, rz};
+                    moments_add(mc, rho);
                 }
             }
         }
-        gsum<LPS, 13>(red);
+        gsum<LPS, 3>(red);
+        moments_reduce<LPS>(mc);
         const float FN = red[0];
 
         // -- semi-implicit Euler
@@ -459,21 +529,25 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         //      S2 = a_x^T M2 a_x + a_y^T M2 a_y,  sum s~ x e = -(a_x^T M2 b_y - a_y^T M2 b_x),
         //      mean e = -dt v*_xy - [D centroid]_xy
         //    with a_x, a_y the x, y rows of (1 + D) and b_x, b_y those of D.
-        const float nC = red[3];
+        const float nC = mc.n;
         const float in = nC > 0.f ? 1.0f / nC : 0.f;
-        const float dlx = red[4] * in, dly = red[5] * in, dlz = red[6] * in;
-        const float gb[3] = {o[0] + dlx, o[1] + dly, o[2] + dlz};   // centroid of rho over C
+        const float gb[3] = {mc.m[0], mc.m[1], mc.m[2]};   // centroid of rho over C
         float cn[3] = {cs[0], cs[1], cs[2]}, vn[3] = {vs[0], vs[1], vs[2]};
         float Ln[3] = {Ls[0], Ls[1], Ls[2]}, qn[4] = {qs[0], qs[1], qs[2], qs[3]};
         // kinematic least squares (joint-update steps): a second pass over C about the exact
         // centroid of the moved points, slip R (r_old - r_new) back to the step start
         float f6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (tick) {
+            // old frames again (the new ones are no longer needed this step)
+            link_frames<LPS>(W, l0, nl, th_old, fr, gl);
             for (uint64_t cm = kprev & know; cm; cm &= cm - 1) {
                 const int k = __ffsll((long long)cm) - 1;
                 const int i = gl + k * LPS;
-                const float4 r = offset(i);
-                const float4 ro = pts[i];
+                const float4 r = pts[i];
+                const float4 a0 = W.p0m[p0 + i];
+                float po[3];
+                fk_point(fr, a0, W.plink[p0 + i], po);
+                const float4 ro = make_float4(po[0] - gold[0], po[1] - gold[1], po[2] - gold[2], 0.f);
                 const float ux = (R[0] * r.x + R[1] * r.y + R[2] * r.z) - gb[0];
                 const float uy = (R[3] * r.x + R[4] * r.y + R[5] * r.z) - gb[1];
                 const float d[3] = {ro.x - r.x, ro.y - r.y, ro.z - r.z};
@@ -485,9 +559,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             gsum<LPS, 6>(f6);
         }
         if (nC >= 1.f) {
-            const Sym M2 = {red[7] - nC * dlx * dlx, red[8] - nC * dly * dly,
-                            red[9] - nC * dlz * dlz, red[10] - nC * dlx * dly,
-                            red[11] - nC * dlx * dlz, red[12] - nC * dly * dlz};
+            const Sym M2 = {mc.M[0], mc.M[1], mc.M[2], mc.M[3], mc.M[4], mc.M[5]};
             const float ax[3] = {1.f + Dm[0], Dm[1], Dm[2]}, ay[3] = {Dm[3], 1.f + Dm[4], Dm[5]};
             const float bx[3] = {Dm[0], Dm[1], Dm[2]}, by[3] = {Dm[3], Dm[4], Dm[5]};
             float Max[3], May[3];
@@ -556,11 +628,6 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             const float qz[4] = {ca, 0.f, 0.f, sa};
             quat_mul(qz, qs, qn);
         }
-        // joint-update steps: the new offsets replace the old ones
-        if (tick) {
-            for (int i = gl; i < np; i += LPS) pts[i] = offset(i);
-            __syncwarp();
-        }
 
         // -- freeze a scene whose state is no longer finite or has left any sane range
         if (status == 0u) {
@@ -580,7 +647,6 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
 #pragma unroll
                 for (int i = 0; i < 4; ++i) q[i] = qn[i];
                 kprev = know;
-                if (nC >= 1.f) { o[0] = gb[0]; o[1] = gb[1]; o[2] = gb[2]; }
             }
         }
     }
@@ -608,7 +674,6 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         quat_mat(q, R);
         world_sym(R, sh.Ii, L, om);
         W.omega[s] = om[0]; W.omega[S + s] = om[1]; W.omega[2 * S + s] = om[2];
-        W.ref[s] = o[0]; W.ref[S + s] = o[1]; W.ref[2 * S + s] = o[2];
         W.sensors[s] = sens;
         W.status[s] = status;
     }
@@ -625,6 +690,8 @@ __global__ void __launch_bounds__(512) step_kernel(WorldDev W, int n_steps, int 
     float4 *pts = reinterpret_cast<float4 *>(slot);
     float *fr = reinterpret_cast<float *>(slot + 16 * W.max_points);
     float *th = fr + 12 * W.max_links;
+    float *th_old = th + W.max_links;
+    float4 *tb = reinterpret_cast<float4 *>(slot + tiles_offset(W.max_points, W.max_links));
     const long long step0 = *W.step;
     const int n_items = (W.S + G - 1) / G;
     for (;;) {
@@ -634,7 +701,7 @@ __global__ void __launch_bounds__(512) step_kernel(WorldDev W, int n_steps, int 
         if (item >= n_items) break;
         const int idx = item * G + g;
         const int s = idx < W.S ? W.order[idx] : -1;
-        run_scene<LPS, FLAT>(W, s, gl, pts, fr, th, n_steps, step0);
+        run_scene<LPS, FLAT>(W, s, gl, pts, fr, th, th_old, tb, n_steps, step0);
     }
 }
 
@@ -659,7 +726,7 @@ __global__ void __launch_bounds__(128) init_kernel(WorldDev W, const float *orig
     for (int j = lane; j < nl - 1; j += 32) th[j] = W.theta[j0 + j];
     __syncwarp();
     Shape sh;
-    shape_setup<32>(W, p0, np, l0, nl, th, fr, pts, lane, sh);
+    shape_update<32>(W, s, p0, np, l0, nl, th, fr, pts, lane, sh);
     for (int i = lane; i < np; i += 32) W.kappa[p0 + i] = 0;
     if (lane == 0) {
         float q[4] = {quat[4 * s], quat[4 * s + 1], quat[4 * s + 2], quat[4 * s + 3]};
@@ -680,7 +747,6 @@ __global__ void __launch_bounds__(128) init_kernel(WorldDev W, const float *orig
         W.st[ST_VZ * S + s] = vel[3 * s + 2];
         W.st[ST_LX * S + s] = L[0]; W.st[ST_LY * S + s] = L[1]; W.st[ST_LZ * S + s] = L[2];
         W.omega[s] = w[0]; W.omega[S + s] = w[1]; W.omega[2 * S + s] = w[2];
-        W.ref[s] = 0.f; W.ref[S + s] = 0.f; W.ref[2 * S + s] = 0.f;
         W.sensors[s] = 0u;
         W.status[s] = 0u;
     }
@@ -701,7 +767,7 @@ __global__ void __launch_bounds__(128) refresh_kernel(WorldDev W, int sbytes) {
     for (int j = lane; j < nl - 1; j += 32) th[j] = W.theta[j0 + j];
     __syncwarp();
     Shape sh;
-    shape_setup<32>(W, p0, np, l0, nl, th, fr, pts, lane, sh);
+    shape_update<32>(W, s, p0, np, l0, nl, th, fr, pts, lane, sh);
     if (lane == 0) {
         const int S = W.S;
         const float q[4] = {W.st[ST_QW * S + s], W.st[ST_QX * S + s], W.st[ST_QY * S + s],
@@ -726,7 +792,7 @@ __global__ void __launch_bounds__(32) points_kernel(WorldDev W, int s, float *ou
     for (int j = lane; j < nl - 1; j += 32) th[j] = W.theta[j0 + j];
     __syncwarp();
     Shape sh;
-    shape_setup<32>(W, p0, np, l0, nl, th, fr, pts, lane, sh);
+    shape_update<32>(W, s, p0, np, l0, nl, th, fr, pts, lane, sh);
     const int S = W.S;
     const float c[3] = {W.st[ST_CX * S + s], W.st[ST_CY * S + s], W.st[ST_CZ * S + s]};
     const float q[4] = {W.st[ST_QW * S + s], W.st[ST_QX * S + s], W.st[ST_QY * S + s],
@@ -745,7 +811,7 @@ __global__ void __launch_bounds__(32) points_kernel(WorldDev W, int s, float *ou
 // ------------------------------------------------------------------------ host-side launchers
 
 size_t step_smem_bytes(const WorldDev &W, int lps, int wpb) {
-    return (size_t)wpb * (32 / lps) * slot_bytes(W.max_points, W.max_links);
+    return (size_t)wpb * (32 / lps) * slot_bytes(W.max_points, W.max_links, lps);
 }
 
 template <int LPS, bool FLAT>
@@ -779,7 +845,7 @@ cudaError_t launch_step(const WorldDev &W, const LaunchCfg &cfg, int n_steps, cu
     const size_t smem = step_smem_bytes(W, cfg.lps, cfg.wpb);
     cudaError_t e = cudaMemsetAsync(W.queue, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    int sb = slot_bytes(W.max_points, W.max_links);
+    int sb = slot_bytes(W.max_points, W.max_links, cfg.lps);
     WorldDev w = W;
     void *args[] = {&w, &n_steps, &sb};
     return cudaLaunchKernel(fn, dim3(cfg.blocks), dim3(cfg.wpb * 32), args, smem, st);
@@ -793,7 +859,7 @@ cudaError_t launch_advance(long long *d_step, int n, cudaStream_t st) {
 cudaError_t launch_init(const WorldDev &W, const float *d_origin, const float *d_quat,
                         const float *d_vel, const float *d_omega, cudaStream_t st) {
     const int wpb = 4;
-    const int sb = slot_bytes(W.max_points, W.max_links);
+    const int sb = slot_bytes(W.max_points, W.max_links, 32);
     const size_t smem = (size_t)wpb * sb;
     cudaError_t e = cudaFuncSetAttribute((void *)init_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -804,7 +870,7 @@ cudaError_t launch_init(const WorldDev &W, const float *d_origin, const float *d
 
 cudaError_t launch_refresh(const WorldDev &W, cudaStream_t st) {
     const int wpb = 4;
-    const int sb = slot_bytes(W.max_points, W.max_links);
+    const int sb = slot_bytes(W.max_points, W.max_links, 32);
     const size_t smem = (size_t)wpb * sb;
     cudaError_t e = cudaFuncSetAttribute((void *)refresh_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -814,7 +880,7 @@ cudaError_t launch_refresh(const WorldDev &W, cudaStream_t st) {
 }
 
 cudaError_t launch_points(const WorldDev &W, int scene, float *d_out, cudaStream_t st) {
-    const int sb = slot_bytes(W.max_points, W.max_links);
+    const int sb = slot_bytes(W.max_points, W.max_links, 32);
     cudaError_t e = cudaFuncSetAttribute((void *)points_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
     if (e != cudaSuccess) return e;

@@ -91,6 +91,9 @@ struct npx_world {
     // packed sizes
     int S = 0, P = 0, L = 0, J = 0, max_points = 0, max_links = 0;
     std::vector<int> link_off, point_off;
+    // points are stored per scene in ascending construction-frame height; perm maps a stored
+    // (global) point index to the caller's index
+    std::vector<int> perm;
     // device
     std::vector<DevBuf> bufs;
     npx::WorldDev W{};
@@ -275,15 +278,14 @@ int enqueue_steps(npx_world *w, int n) {
 }
 
 struct BlobLayout {
-    size_t st, theta, ref, omega, kappa, sensors, status, end;
+    size_t st, theta, omega, kappa, sensors, status, end;
 };
 
 BlobLayout blob_layout(const npx_world *w) {
     BlobLayout b;
     b.st = 64;
     b.theta = b.st + sizeof(float) * (size_t)npx::ST_N * w->S;
-    b.ref = b.theta + sizeof(float) * (size_t)w->J;
-    b.omega = b.ref + sizeof(float) * 3 * (size_t)w->S;
+    b.omega = b.theta + sizeof(float) * (size_t)w->J;
     b.sensors = b.omega + sizeof(float) * 3 * (size_t)w->S;
     b.status = b.sensors + sizeof(uint32_t) * (size_t)w->S;
     b.kappa = b.status + sizeof(uint32_t) * (size_t)w->S;
@@ -488,6 +490,10 @@ int npx_world_finalize(npx_world *w) {
     w->P = w->point_off[S];
     w->J = w->L - S;
     std::vector<npx::LinkDev> links(w->L);
+    w->perm.assign(w->P, 0);
+    // rest-pose CoG of each scene: the kernels sum mass moments about it (a numerical reference
+    // only; the results do not depend on it beyond rounding)
+    std::vector<float> gref(3 * (size_t)S);
     std::vector<float4> p0m(w->P);
     std::vector<uint8_t> plink(w->P);
     for (int s = 0; s < S; ++s) {
@@ -504,9 +510,23 @@ int npx_world_finalize(npx_world *w) {
                   (float)(ux / un), (float)(uy / un), (float)(uz / un), f.hi[k],
                   f.parent[k], f.sensor[k], depth[k], 0};
         }
+        {
+            double m = 0, g[3] = {0, 0, 0};
+            for (size_t i = 0; i < f.m.size(); ++i) {
+                m += f.m[i];
+                for (int k = 0; k < 3; ++k) g[k] += (double)f.m[i] * f.p0[3 * i + k];
+            }
+            for (int k = 0; k < 3; ++k) gref[3 * s + k] = (float)(g[k] / m);
+        }
+        // lowest points first: the step kernel stops scanning once the rest is above ground
+        std::vector<int> ord(f.m.size());
+        std::iota(ord.begin(), ord.end(), 0);
+        std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return f.p0[3 * a + 2] < f.p0[3 * b + 2]; });
         for (size_t i = 0; i < f.m.size(); ++i) {
-            p0m[p0 + i] = make_float4(f.p0[3 * i], f.p0[3 * i + 1], f.p0[3 * i + 2], f.m[i]);
-            plink[p0 + i] = (uint8_t)f.plink[i];
+            const int u = ord[i];
+            p0m[p0 + i] = make_float4(f.p0[3 * u], f.p0[3 * u + 1], f.p0[3 * u + 2], f.m[u]);
+            plink[p0 + i] = (uint8_t)f.plink[u];
+            w->perm[p0 + i] = p0 + u;
         }
     }
     // persistent schedule: most points first (longest jobs start first)
@@ -528,19 +548,27 @@ int npx_world_finalize(npx_world *w) {
     }
     npx::WorldDev &W = w->W;
     if (!w->hm_host.empty()) {
-        float *hm = nullptr;
+        float *hm = nullptr, *hmx = nullptr;
         if (int rc = dev_alloc(w, &hm, w->hm_host.size())) return rc;
         CUDA_TRY(cudaMemcpy(hm, w->hm_host.data(), w->hm_host.size() * sizeof(float), cudaMemcpyHostToDevice));
+        const size_t cells = (size_t)w->desc.hm_nx * w->desc.hm_ny;
+        std::vector<float> mx(w->desc.hm_count);
+        for (int h = 0; h < w->desc.hm_count; ++h)
+            mx[h] = *std::max_element(w->hm_host.begin() + h * cells, w->hm_host.begin() + (h + 1) * cells);
+        if (int rc = dev_alloc(w, &hmx, mx.size())) return rc;
+        CUDA_TRY(cudaMemcpy(hmx, mx.data(), mx.size() * sizeof(float), cudaMemcpyHostToDevice));
         W.hm = hm;
+        W.hm_max = hmx;
         w->hm_host.clear();
         w->hm_host.shrink_to_fit();
     }
     W.S = S; W.P = w->P; W.L = w->L; W.J = w->J;
     int *d_lo, *d_po, *d_hmap, *d_order;
+    float *d_gref;
     float4 *d_p0m, *d_act;
     uint8_t *d_plink, *d_kappa;
     npx::LinkDev *d_links;
-    float *d_mu, *d_st, *d_theta, *d_ref, *d_omega;
+    float *d_mu, *d_st, *d_theta, *d_omega;
     uint32_t *d_nu, *d_sens, *d_status;
     unsigned int *d_queue;
     int rc = 0;
@@ -550,7 +578,7 @@ int npx_world_finalize(npx_world *w) {
         (rc = dev_alloc(w, &d_links, w->L)) || (rc = dev_alloc(w, &d_mu, S)) ||
         (rc = dev_alloc(w, &d_act, w->J)) || (rc = dev_alloc(w, &d_nu, w->J)) ||
         (rc = dev_alloc(w, &d_st, (size_t)npx::ST_N * S)) || (rc = dev_alloc(w, &d_theta, w->J)) ||
-        (rc = dev_alloc(w, &d_kappa, w->P)) || (rc = dev_alloc(w, &d_ref, 3 * (size_t)S)) ||
+        (rc = dev_alloc(w, &d_kappa, w->P)) || (rc = dev_alloc(w, &d_gref, 3 * (size_t)S)) ||
         (rc = dev_alloc(w, &d_omega, 3 * (size_t)S)) || (rc = dev_alloc(w, &d_sens, S)) ||
         (rc = dev_alloc(w, &d_status, S)) || (rc = dev_alloc(w, &d_queue, 1)) ||
         (rc = dev_alloc(w, &w->d_step, 1)) || (rc = dev_alloc(w, &w->d_stage, 13 * (size_t)S)) ||
@@ -564,11 +592,13 @@ int npx_world_finalize(npx_world *w) {
     CUDA_TRY(cudaMemcpy(d_plink, plink.data(), w->P, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(d_links, links.data(), sizeof(npx::LinkDev) * w->L, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(d_mu, w->mu.data(), sizeof(float) * S, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_gref, gref.data(), sizeof(float) * 3 * S, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemset(d_act, 0, sizeof(float4) * std::max(w->J, 1)));
     CUDA_TRY(cudaMemset(d_nu, 0, sizeof(uint32_t) * std::max(w->J, 1)));
     CUDA_TRY(cudaMemset(d_theta, 0, sizeof(float) * std::max(w->J, 1)));
     CUDA_TRY(cudaMemset(w->d_step, 0, sizeof(long long)));
     W.link_off = d_lo; W.point_off = d_po; W.p0m = d_p0m; W.plink = d_plink; W.links = d_links;
+    W.gref = d_gref;
     W.mu = d_mu; W.hmap = d_hmap;
     W.hm_nx = w->desc.hm_nx; W.hm_ny = w->desc.hm_ny;
     W.hm_scale = w->desc.hm_scale; W.hm_ox = w->desc.hm_origin[0]; W.hm_oy = w->desc.hm_origin[1];
@@ -579,7 +609,7 @@ int npx_world_finalize(npx_world *w) {
     W.kc = 2.f * w->desc.contact_zeta * w->desc.contact_omega;
     W.act_mode = NPX_ACT_HOLD;
     W.act = d_act; W.act_nu = d_nu;
-    W.st = d_st; W.theta = d_theta; W.kappa = d_kappa; W.ref = d_ref; W.omega = d_omega;
+    W.st = d_st; W.theta = d_theta; W.kappa = d_kappa; W.omega = d_omega;
     W.sensors = d_sens; W.status = d_status;
     W.order = d_order; W.max_points = w->max_points; W.max_links = w->max_links;
     W.step = w->d_step; W.queue = d_queue;
@@ -641,10 +671,15 @@ int npx_state_write(npx_world *w, const float *cog, const float *quat, const flo
     CUDA_TRY(cudaMemcpyAsync(w->W.st, st.data(), st.size() * sizeof(float), cudaMemcpyHostToDevice, w->stream));
     if (theta && w->J > 0)
         CUDA_TRY(cudaMemcpyAsync(w->W.theta, theta, w->J * sizeof(float), cudaMemcpyHostToDevice, w->stream));
-    if (contact_prev) CUDA_TRY(cudaMemcpyAsync(w->W.kappa, contact_prev, w->P, cudaMemcpyHostToDevice, w->stream));
-    else CUDA_TRY(cudaMemsetAsync(w->W.kappa, 0, w->P, w->stream));
+    std::vector<uint8_t> kap;
+    if (contact_prev) {
+        kap.resize(w->P);
+        for (int i = 0; i < w->P; ++i) kap[i] = contact_prev[w->perm[i]] ? 1 : 0;
+        CUDA_TRY(cudaMemcpyAsync(w->W.kappa, kap.data(), w->P, cudaMemcpyHostToDevice, w->stream));
+    } else {
+        CUDA_TRY(cudaMemsetAsync(w->W.kappa, 0, w->P, w->stream));
+    }
     CUDA_TRY(cudaMemsetAsync(w->W.status, 0, S * sizeof(uint32_t), w->stream));
-    CUDA_TRY(cudaMemsetAsync(w->W.ref, 0, 3 * S * sizeof(float), w->stream));
     const long long st64 = step;
     CUDA_TRY(cudaMemcpyAsync(w->d_step, &st64, sizeof st64, cudaMemcpyHostToDevice, w->stream));
     CUDA_TRY(npx::launch_refresh(w->W, w->stream));
@@ -657,8 +692,10 @@ int npx_contacts_read(npx_world *w, uint8_t *contact, size_t n) {
     if (int rc = check_ready(w)) return rc;
     if (!contact || n < (size_t)w->P) return fail(NPX_EINVAL, "buffer holds %zu flags, world has %d points", n, w->P);
     CUDA_TRY(cudaSetDevice(w->device));
-    CUDA_TRY(cudaMemcpyAsync(contact, w->W.kappa, w->P, cudaMemcpyDeviceToHost, w->stream));
+    std::vector<uint8_t> kap(w->P);
+    CUDA_TRY(cudaMemcpyAsync(kap.data(), w->W.kappa, w->P, cudaMemcpyDeviceToHost, w->stream));
     CUDA_TRY(cudaStreamSynchronize(w->stream));
+    for (int i = 0; i < w->P; ++i) contact[w->perm[i]] = kap[i];
     return NPX_OK;
 }
 
@@ -755,9 +792,15 @@ int npx_points_read(npx_world *w, int scene, float *xyz, int n) {
     const int np = w->point_off[scene + 1] - w->point_off[scene];
     if (!xyz || n < np) return fail(NPX_EINVAL, "buffer holds %d points, scene has %d", n, np);
     CUDA_TRY(cudaSetDevice(w->device));
+    std::vector<float> tmp(3 * (size_t)np);
     CUDA_TRY(npx::launch_points(w->W, scene, w->d_points, w->stream));
-    CUDA_TRY(cudaMemcpyAsync(xyz, w->d_points, 3 * (size_t)np * sizeof(float), cudaMemcpyDeviceToHost, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(tmp.data(), w->d_points, tmp.size() * sizeof(float), cudaMemcpyDeviceToHost, w->stream));
     CUDA_TRY(cudaStreamSynchronize(w->stream));
+    const int p0 = w->point_off[scene];
+    for (int i = 0; i < np; ++i) {
+        const int u = w->perm[p0 + i] - p0;
+        for (int k = 0; k < 3; ++k) xyz[3 * u + k] = tmp[3 * i + k];
+    }
     return NPX_OK;
 }
 
@@ -775,7 +818,6 @@ int npx_state_export(npx_world *w, void *blob, size_t *size) {
     const size_t S = w->S;
     CUDA_TRY(cudaMemcpyAsync(p + b.st, w->W.st, sizeof(float) * npx::ST_N * S, cudaMemcpyDeviceToHost, w->stream));
     if (w->J) CUDA_TRY(cudaMemcpyAsync(p + b.theta, w->W.theta, sizeof(float) * w->J, cudaMemcpyDeviceToHost, w->stream));
-    CUDA_TRY(cudaMemcpyAsync(p + b.ref, w->W.ref, sizeof(float) * 3 * S, cudaMemcpyDeviceToHost, w->stream));
     CUDA_TRY(cudaMemcpyAsync(p + b.omega, w->W.omega, sizeof(float) * 3 * S, cudaMemcpyDeviceToHost, w->stream));
     CUDA_TRY(cudaMemcpyAsync(p + b.sensors, w->W.sensors, sizeof(uint32_t) * S, cudaMemcpyDeviceToHost, w->stream));
     CUDA_TRY(cudaMemcpyAsync(p + b.status, w->W.status, sizeof(uint32_t) * S, cudaMemcpyDeviceToHost, w->stream));
@@ -798,7 +840,6 @@ int npx_state_import(npx_world *w, const void *blob, size_t size) {
     const size_t S = w->S;
     CUDA_TRY(cudaMemcpyAsync(w->W.st, p + b.st, sizeof(float) * npx::ST_N * S, cudaMemcpyHostToDevice, w->stream));
     if (w->J) CUDA_TRY(cudaMemcpyAsync(w->W.theta, p + b.theta, sizeof(float) * w->J, cudaMemcpyHostToDevice, w->stream));
-    CUDA_TRY(cudaMemcpyAsync(w->W.ref, p + b.ref, sizeof(float) * 3 * S, cudaMemcpyHostToDevice, w->stream));
     CUDA_TRY(cudaMemcpyAsync(w->W.omega, p + b.omega, sizeof(float) * 3 * S, cudaMemcpyHostToDevice, w->stream));
     CUDA_TRY(cudaMemcpyAsync(w->W.sensors, p + b.sensors, sizeof(uint32_t) * S, cudaMemcpyHostToDevice, w->stream));
     CUDA_TRY(cudaMemcpyAsync(w->W.status, p + b.status, sizeof(uint32_t) * S, cudaMemcpyHostToDevice, w->stream));

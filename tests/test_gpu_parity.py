@@ -284,7 +284,7 @@ def test_zero_steps_and_chunking_and_graphs_are_bit_exact():
 def test_launch_shapes_agree():
     b = scenes.hexapod_batch(96, seed_key=6)
     outs = []
-    for lps, wpb in ((8, 2), (16, 4), (32, 8), (16, 16)):
+    for lps, wpb in ((8, 2), (16, 4), (32, 8), (16, 8)):
         w = World.from_batch(b, configure=dict(lanes_per_scene=lps, warps_per_block=wpb))
         w.step(120)
         outs.append(w.read())
