@@ -55,7 +55,7 @@ struct Moments {
 };
 
 __device__ __forceinline__ void moments_add(Moments &a, const float x[3]) {
-    const float n1 = a.n + 1.f, f = 1.f / n1, w = a.n * f;
+    const float n1 = a.n + 1.f, f = __frcp_rn(n1), w = a.n * f;
     const float d0 = x[0] - a.m[0], d1 = x[1] - a.m[1], d2 = x[2] - a.m[2];
     a.m[0] += d0 * f; a.m[1] += d1 * f; a.m[2] += d2 * f;
     a.M[0] += w * d0 * d0; a.M[1] += w * d1 * d1; a.M[2] += w * d2 * d2;
@@ -64,9 +64,11 @@ __device__ __forceinline__ void moments_add(Moments &a, const float x[3]) {
 }
 
 template <int LPS>
-__device__ __forceinline__ void moments_reduce(Moments &a) {
+__device__ __forceinline__ void moments_reduce(Moments &a, float (&f)[3]) {
 #pragma unroll
     for (int o = LPS / 2; o > 0; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) f[i] += __shfl_xor_sync(FULL_MASK, f[i], o);
         Moments b;
         b.n = __shfl_xor_sync(FULL_MASK, a.n, o);
 #pragma unroll
@@ -74,7 +76,7 @@ __device__ __forceinline__ void moments_reduce(Moments &a) {
 #pragma unroll
         for (int i = 0; i < 6; ++i) b.M[i] = __shfl_xor_sync(FULL_MASK, a.M[i], o);
         const float n = a.n + b.n;
-        const float inv = n > 0.f ? 1.f / n : 0.f;
+        const float inv = n > 0.f ? __frcp_rn(n) : 0.f;
         const float w = a.n * b.n * inv;
         const float d0 = b.m[0] - a.m[0], d1 = b.m[1] - a.m[1], d2 = b.m[2] - a.m[2];
 #pragma unroll
@@ -198,11 +200,12 @@ __host__ __device__ inline int slot_bytes(int max_points, int max_links, int lps
 }
 
 // Bounding boxes for skipping points that cannot touch the ground.  Tile t holds points
-// [t*LPS, (t+1)*LPS) of a scene (stored in ascending construction-frame height); tb[2t], tb[2t+1]
-// are the min / max corners of the offsets r of every point in tiles t, t+1, ..., so that
-// c_z + min over that box of (R r)_z bounds from below the height of all remaining points.
+// [t*LPS, (t+1)*LPS) of a scene (stored in ascending construction-frame height, so that a tile
+// gathers points of similar height); tb[2t], tb[2t+1] are the min / max corners of the offsets r
+// of its points, and c_z + min over that box of (R r)_z bounds their heights from below.
 template <int LPS>
 __device__ __noinline__ void tile_bounds(const float4 *pts, int np, float4 *tb, int gl) {
+    __syncwarp();
     const int nt = (np + LPS - 1) / LPS;
     for (int t = gl; t < nt; t += LPS) {
         float4 lo = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
@@ -217,17 +220,29 @@ __device__ __noinline__ void tile_bounds(const float4 *pts, int np, float4 *tb, 
         tb[2 * t + 1] = hi;
     }
     __syncwarp();
-    if (gl == 0) {
-        for (int t = nt - 2; t >= 0; --t) {
-            float4 lo = tb[2 * t], hi = tb[2 * t + 1];
-            const float4 l2 = tb[2 * t + 2], h2 = tb[2 * t + 3];
-            lo.x = fminf(lo.x, l2.x); lo.y = fminf(lo.y, l2.y); lo.z = fminf(lo.z, l2.z);
-            hi.x = fmaxf(hi.x, h2.x); hi.y = fmaxf(hi.y, h2.y); hi.z = fmaxf(hi.z, h2.z);
-            tb[2 * t] = lo;
-            tb[2 * t + 1] = hi;
+}
+
+// Tiles that may hold a point at or below the highest ground hmax: every lane tests the boxes of
+// its tiles (t = gl, gl + LPS, ...) and a ballot gathers the group's answers into a mask.
+template <int LPS>
+__device__ __forceinline__ uint64_t tiles_near_ground(const float4 *tb, int ntiles, int ntiles_warp,
+                                                      const float R[9], float cz, float hmax, int gl) {
+    uint64_t mask = 0;
+    const int g = (threadIdx.x & 31) / LPS;
+    for (int t0 = 0; t0 < ntiles_warp; t0 += LPS) {   // warp-uniform trip count
+        const int t = t0 + gl;
+        bool near = false;
+        if (t < ntiles) {
+            const float4 lo = tb[2 * t], hi = tb[2 * t + 1];
+            const float zb = cz + fminf(R[6] * lo.x, R[6] * hi.x) + fminf(R[7] * lo.y, R[7] * hi.y) +
+                             fminf(R[8] * lo.z, R[8] * hi.z);
+            near = zb <= hmax;
         }
+        const uint32_t bal = __ballot_sync(FULL_MASK, near);
+        const uint64_t mine = (bal >> (g * LPS)) & (LPS == 32 ? 0xffffffffu : ((1u << LPS) - 1u));
+        mask |= mine << t0;
     }
-    __syncwarp();
+    return mask;
 }
 
 // ------------------------------------------------------------------------ kinematics (Sec. III-B)
@@ -410,6 +425,9 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
     // highest ground a point can meet (plus a margin for the rounding of the bound)
     const float hmax = (FLAT || hm < 0 ? 0.f : W.hm_max[hm]) + 1e-5f;
     const int ntiles = (np + LPS - 1) / LPS;
+    int ntiles_warp = ntiles;   // the warp's largest tile count (uniform loop bound)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ntiles_warp = max(ntiles_warp, __shfl_xor_sync(FULL_MASK, ntiles_warp, o));
 
     const float dt = W.dt, idt = 1.0f / W.dt, kw2 = W.kw2, kc = W.kc;
     const bool actuated = W.act_mode != 0;
@@ -447,13 +465,9 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         uint64_t know = 0;
         float red[3] = {0.f, 0.f, 0.f};
         Moments mc = {0.f, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}};
-        for (int k = 0; k < ntiles; ++k) {
-            {   // stop once every remaining point is provably above the ground
-                const float4 lo = tb[2 * k], hi = tb[2 * k + 1];
-                const float zb = c[2] + fminf(R[6] * lo.x, R[6] * hi.x) +
-                                 fminf(R[7] * lo.y, R[7] * hi.y) + fminf(R[8] * lo.z, R[8] * hi.z);
-                if (zb > hmax) break;
-            }
+        for (uint64_t tm = tiles_near_ground<LPS>(tb, ntiles, ntiles_warp, R, c[2], hmax, gl); tm;
+             tm &= tm - 1) {
+            const int k = __ffsll((long long)tm) - 1;
             const int i = gl + k * LPS;
             if (i >= np) continue;
             const float4 r = pts[i];
@@ -482,8 +496,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
                 }
             }
         }
-        gsum<LPS, 3>(red);
-        moments_reduce<LPS>(mc);
+        moments_reduce<LPS>(mc, red);
         const float FN = red[0];
 
         // -- semi-implicit Euler
@@ -573,7 +586,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             const float sby = ay[0] * gb[0] + ay[1] * gb[1] + ay[2] * gb[2];
             const float tDx = -dt * vs[0] - (bx[0] * gb[0] + bx[1] * gb[1] + bx[2] * gb[2]);
             const float tDy = -dt * vs[1] - (by[0] * gb[0] + by[1] * gb[1] + by[2] * gb[2]);
-            float a3 = (nC >= 2.f && S2 > 1e-12f) ? X / S2 : 0.f;
+            float a3 = (nC >= 2.f && S2 > 1e-12f) ? __fdividef(X, S2) : 0.f;
             a3 = fminf(fmaxf(a3, -1.f), 1.f);
             const float cD = sqrtf(fmaxf(0.f, 1.f - a3 * a3));
             const float cm1 = -a3 * a3 / (1.f + cD);                  // cos(alpha_D) - 1
