@@ -182,6 +182,61 @@ int npx_world_autotune(npx_world *w, int n_steps, npx_world_info *out);
 /* Capture world_step's chunk sequence in CUDA graphs (1, default) or launch directly (0). */
 int npx_world_use_graphs(npx_world *w, int on);
 
+/* --- stepping without any allocation ------------------------------------------------------ */
+/* The paper has no counterpart of this call; it serves callers that must not allocate device
+ * memory while they run: code that records its work into a CUDA graph (cudaMalloc is not allowed
+ * during stream capture), real-time loops that forbid allocation after start-up, frameworks that
+ * hand out all device memory from their own pool.  They allocate the arrays below once, their own
+ * way, and npx_step_noalloc steps them without allocating anything.  Its scratch memory (work-
+ * queue counter, step counter, scene schedule) is a static device array of the library that every
+ * GPU which loads the library keeps until the process exits; its size limits a call to
+ * NPX_NOALLOC_MAX_SCENES scenes (larger worlds are rejected with NPX_ERANGE).  All calls share
+ * that array: calls whose work overlaps on the GPU (on different streams, or from different
+ * threads) race on it and must be serialised by the caller.  The first call on a device looks up
+ * the array's device address (a one-time set-up per device, done with that device current);
+ * make that first call before capturing a stream.
+ *
+ * All pointers are DEVICE pointers to arrays the caller owns, in the layout a finalized world
+ * uses internally (scene-major, points of each scene in ascending construction-frame height):
+ *   link_off, point_off [S+1]; p0m [P*4] construction position xyz and mass; plink [P] link of
+ *   each point; links [L] 48-byte records {anchor xyz, lo, unit axis xyz, hi (floats), parent,
+ *   sensor bit, depth in the link tree, 0 (ints)}; gref [S*3] rest-pose CoG; mu [S]; hmap [S]
+ *   (-1 flat); hm [maps*ny*nx] and hm_max [maps] (NULL when there are no maps); act / act_nu
+ *   [J*4] / [J] actuator parameters and phase increments round(f dt 2^32);
+ *   state [13*S] structure of arrays (component k of scene s at k*S+s: CoG xyz, quaternion
+ *   wxyz, velocity xyz, angular momentum xyz); theta [J]; contact [P] flags of the last step;
+ *   omega [S*3 as 3 rows of S]; sensors, status [S].
+ * step is the global step index of the first step (it fixes the joint-update phase); the caller
+ * keeps the counter, the world is at step + n_steps afterwards.  The call is asynchronous on
+ * stream (a cudaStream_t, NULL = legacy default stream); state, theta, contact, omega, sensors
+ * and status are read and written in place. */
+#define NPX_NOALLOC_MAX_SCENES 65536
+typedef struct {
+    int n_scenes, max_points, max_links;
+    const int *link_off, *point_off;
+    const float *p0m;
+    const uint8_t *plink;
+    const void *links;
+    const float *gref, *mu;
+    const int *hmap;
+    const float *hm, *hm_max;
+    int hm_nx, hm_ny;
+    float hm_scale, hm_origin[2];
+    float dt, gravity[3];
+    int joint_update_steps;
+    float contact_omega, contact_zeta;
+    int act_mode;
+    const float *act;
+    const uint32_t *act_nu;
+    float *state, *theta;
+    uint8_t *contact;
+    float *omega;
+    uint32_t *sensors, *status;
+    int64_t step;
+    int lanes_per_scene, warps_per_block;
+} npx_device_world;
+int npx_step_noalloc(const npx_device_world *world, int n_steps, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,6 +64,8 @@ cudaError_t launch_advance(long long *d_step, int n, cudaStream_t st);
 cudaError_t launch_init(const WorldDev &W, const float *d_origin, const float *d_quat,
                         const float *d_vel, const float *d_omega, cudaStream_t st);
 cudaError_t launch_refresh(const WorldDev &W, cudaStream_t st);
+// records msg as the thread's npx_last_error() text and returns code
+int set_last_error(int code, const char *msg);
 cudaError_t launch_points(const WorldDev &W, int scene, float *d_out, cudaStream_t st);
 
 }  // namespace npx

@@ -297,6 +297,11 @@ const uint64_t kBlobMagic = 0x315850584e504e47ull;
 
 }  // namespace
 
+int npx::set_last_error(int code, const char *msg) {
+    g_err = msg;
+    return code;
+}
+
 extern "C" {
 
 const char *npx_last_error(void) { return g_err.c_str(); }

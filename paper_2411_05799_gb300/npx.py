@@ -60,6 +60,28 @@ class WorldInfo(C.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+class DeviceWorld(C.Structure):
+    """npx_device_world: device pointers to caller-owned arrays for npx_step_noalloc."""
+    _fields_ = [("n_scenes", C.c_int), ("max_points", C.c_int), ("max_links", C.c_int),
+                ("link_off", C.c_void_p), ("point_off", C.c_void_p), ("p0m", C.c_void_p),
+                ("plink", C.c_void_p), ("links", C.c_void_p), ("gref", C.c_void_p),
+                ("mu", C.c_void_p), ("hmap", C.c_void_p), ("hm", C.c_void_p),
+                ("hm_max", C.c_void_p), ("hm_nx", C.c_int), ("hm_ny", C.c_int),
+                ("hm_scale", C.c_float), ("hm_origin", C.c_float * 2), ("dt", C.c_float),
+                ("gravity", C.c_float * 3), ("joint_update_steps", C.c_int),
+                ("contact_omega", C.c_float), ("contact_zeta", C.c_float), ("act_mode", C.c_int),
+                ("act", C.c_void_p), ("act_nu", C.c_void_p), ("state", C.c_void_p),
+                ("theta", C.c_void_p), ("contact", C.c_void_p), ("omega", C.c_void_p),
+                ("sensors", C.c_void_p), ("status", C.c_void_p), ("step", C.c_int64),
+                ("lanes_per_scene", C.c_int), ("warps_per_block", C.c_int)]
+
+
+def step_noalloc(device_world: DeviceWorld, n_steps: int, stream=None):
+    """npx_step_noalloc: step caller-owned device arrays without any allocation."""
+    load()
+    _check(_lib.npx_step_noalloc(C.byref(device_world), int(n_steps), stream))
+
+
 P = C.c_void_p
 I = C.c_int
 F = C.c_float
@@ -89,6 +111,7 @@ _SIGS = {
     "npx_world_configure": [P, I, I, I, I],
     "npx_world_autotune": [P, I, P],
     "npx_world_use_graphs": [P, I],
+    "npx_step_noalloc": [P, I, P],
 }
 
 _lib = None
