@@ -120,6 +120,34 @@ def cpu_oracle_sample(batch, n_scenes: int, n_steps: int, threads: int) -> dict:
     return r
 
 
+def other_workloads(World, scenes, stream, device) -> dict:
+    """Scene-steps/s of 1,000-step launches on the uneven mixed batch and the rough-terrain
+    batch (state resident in HBM, CUDA events, one warm-up launch each)."""
+    import torch
+    out = {}
+    for name, make in (("uneven_mix_65536_scenes", lambda: scenes.uneven_batch(65536)),
+                       ("hexapod_rough_terrain_16384_scenes", lambda: scenes.cpg_batch(16384))):
+        b = make()
+        w = World.from_batch(b, stream=stream.cuda_stream, device=device)
+        w.autotune(100)
+        w.configure(chunk_steps=CHUNK)
+        w.step(CHUNK)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        w.step(2 * CHUNK)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        info = w.info()
+        out[name] = {"value": b.n_scenes * 2 * CHUNK / (ms / 1e3), "unit": UNIT, "steps": 2 * CHUNK,
+                     "ms": ms, "points": b.n_points, "lanes_per_scene": info["lanes_per_scene"],
+                     "warps_per_block": info["warps_per_block"],
+                     "frozen_scenes": int((w.read()["status"] != 0).sum())}
+        w.close()
+        del b
+    return out
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle on the host cores, same workload and metric."""
     ws, rank, _ = dist_env()
@@ -252,6 +280,11 @@ def run_gpu(args):
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "steps": e2e_steps}}
 
+    # ---- the other batched workloads: throughput of the same step on the uneven 65,536-scene
+    # mix and on 16,384 hexapods walking on rough height fields (informational)
+    if rank == 0 and not args.no_extra:
+        line["other_workloads"] = other_workloads(World, scenes, stream, local)
+
     if rank == 0:
         # algorithmic flops per scene-step from the oracle's event counts on a sample
         n_sc, n_st = 1024, 1000
@@ -303,6 +336,7 @@ def main():
     ap.add_argument("--lps", type=int, default=16)
     ap.add_argument("--wpb", type=int, default=16)
     ap.add_argument("--chunk", type=int, default=100)
+    ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)

@@ -282,8 +282,28 @@ def legged_batch(n_scenes: int, n_legs=6, seed_key: int = 0, mu=0.8, lattice=Tru
     robots = []
     links = _robot_links(n_legs)
     if lattice:
+        # identical robots: assemble one and tile its arrays
         pts = [box_lattice(e, c, _lattice_counts(e)) for e, c, *_ in links]
-        robots = [(links, pts)] * n_scenes
+        one = _assemble([(links, pts)], mu=[0.0], origin=np.zeros((1, 3)), quat=[(1, 0, 0, 0)],
+                        vel=np.zeros((1, 3)), omega=np.zeros((1, 3)), act_params=None, K=K,
+                        name="template")
+        S, nl, npt = n_scenes, len(links), one.n_points
+        J = (nl - 1) * S
+        mu_arr = np.full(S, mu) if np.isscalar(mu) else np.asarray(mu)
+        act = _sinusoid_params(rng, J, amp_max, fmin, fmax)
+        return one.with_(
+            link_off=(np.arange(S + 1) * nl).astype(np.int32),
+            point_off=(np.arange(S + 1) * npt).astype(np.int32),
+            p0=np.tile(one.p0, (S, 1)), m=np.tile(one.m, S), plink=np.tile(one.plink, S),
+            parent=np.tile(one.parent, S), anchor=np.tile(one.anchor, (S, 1)),
+            axis=np.tile(one.axis, (S, 1)), lo=np.tile(one.lo, S), hi=np.tile(one.hi, S),
+            sensor=np.tile(one.sensor, S), mu=mu_arr.astype(np.float32),
+            hmap=-np.ones(S, np.int32),
+            origin=np.tile(np.float32([0.0, 0.0, -FOOT_Z + 0.01]), (S, 1)),
+            quat=np.tile(np.float32([1.0, 0.0, 0.0, 0.0]), (S, 1)),
+            vel=np.zeros((S, 3), np.float32), omega=np.zeros((S, 3), np.float32),
+            theta0=np.zeros(J, np.float32), act_mode=ACT_SINUSOID,
+            act_params=act.astype(np.float32), name=name or f"legged{n_legs}x{n_scenes}")
     else:
         for _ in range(n_scenes):
             pts = [box_uniform(rng, e, c, int(rng.integers(pts_range[0], pts_range[1] + 1)))
@@ -307,37 +327,70 @@ def hexapod_batch(n_scenes: int = 4096, seed_key: int = 0, K: int = 80) -> Scene
     return legged_batch(n_scenes, 6, seed_key, mu=0.8, K=K, name=f"hexapod_{n_scenes}")
 
 
+def _robots_vectorized(rng, legs_per_scene, pts_lo=8, pts_hi=64):
+    """Flat arrays for scenes of legged robots with U{pts_lo..pts_hi} points per link, uniform in
+    each link's box (vectorised over all scenes)."""
+    templates = {n: _robot_links(n) for n in np.unique(legs_per_scene)}
+    tl = [templates[n] for n in legs_per_scene]
+    nl = np.array([len(t) for t in tl], np.int64)
+    ext = np.concatenate([[l[0] for l in t] for t in tl]).reshape(-1, 3)
+    ctr = np.concatenate([[l[1] for l in t] for t in tl]).reshape(-1, 3)
+    lmass = np.concatenate([[l[2] for l in t] for t in tl])
+    parent = np.concatenate([[l[3] for l in t] for t in tl]).astype(np.int32)
+    anchor = np.concatenate([[l[4] if l[4] is not None else (0, 0, 0) for l in t] for t in tl]).reshape(-1, 3)
+    axis = np.concatenate([[l[5] if l[5] is not None else (0, 0, 1) for l in t] for t in tl]).reshape(-1, 3)
+    sensor = np.concatenate([[l[6] for l in t] for t in tl]).astype(np.int32)
+    counts = rng.integers(pts_lo, pts_hi + 1, len(parent))
+    u = rng.random((int(counts.sum()), 3))
+    p0 = (np.repeat(ctr, counts, 0) + (u - 0.5) * np.repeat(ext, counts, 0)).astype(np.float32)
+    m = np.repeat(lmass / counts, counts).astype(np.float32)
+    link_off = np.concatenate([[0], np.cumsum(nl)]).astype(np.int32)
+    scene_of_link = np.repeat(np.arange(len(nl)), nl)
+    local = (np.arange(len(parent)) - link_off[scene_of_link]).astype(np.int32)
+    plink = np.repeat(local, counts).astype(np.int32)
+    pts_per_scene = np.add.reduceat(counts, link_off[:-1])
+    point_off = np.concatenate([[0], np.cumsum(pts_per_scene)]).astype(np.int32)
+    root = parent < 0
+    lo = np.where(root, 0.0, -LIMIT).astype(np.float32)
+    hi = np.where(root, 0.0, LIMIT).astype(np.float32)
+    return dict(link_off=link_off, point_off=point_off, p0=p0, m=m, plink=plink, parent=parent,
+                anchor=anchor.astype(np.float32), axis=axis.astype(np.float32), lo=lo, hi=hi,
+                sensor=sensor)
+
+
 def uneven_batch(n_scenes: int = 65536, seed_key: int = 0) -> SceneBatch:
     """Mixed batch: hexapods (19 links) / quadrupeds (13 links) / bipeds (7 links) in seeded
     50/30/20 proportions, 8..64 points per link uniform in the link box, mu ~ U(0.3, 1.0)."""
     rng = _rng(3, seed_key)
     kinds = rng.choice([6, 4, 2], size=n_scenes, p=[0.5, 0.3, 0.2])
     mu = rng.uniform(0.3, 1.0, n_scenes)
-    robots = []
-    for legs in kinds:
-        links = _robot_links(int(legs))
-        pts = [box_uniform(rng, e, c, int(rng.integers(8, 65))) for e, c, *_ in links]
-        robots.append((links, pts))
+    arr = _robots_vectorized(rng, kinds)
     S = n_scenes
-    J = sum(len(r[0]) - 1 for r in robots)
+    J = int(arr["link_off"][-1]) - S
     act = _sinusoid_params(rng, J)
-    origin = np.tile([0.0, 0.0, -FOOT_Z + 0.01], (S, 1))
-    b = _assemble(robots, mu=mu, origin=origin, quat=np.tile([1.0, 0, 0, 0], (S, 1)),
-                  vel=np.zeros((S, 3)), omega=np.zeros((S, 3)), act_params=act,
-                  name=f"uneven_{n_scenes}", meta={"legs": kinds.astype(np.int32)})
-    return b
+    r32 = lambda x: float(np.float32(x))
+    return SceneBatch(
+        dt=r32(1e-3), gravity=(0.0, 0.0, r32(-9.81)), joint_update_steps=80, contact_omega=300.0,
+        contact_zeta=1.0, **arr, mu=mu.astype(np.float32), hmap=-np.ones(S, np.int32),
+        origin=np.tile(np.float32([0.0, 0.0, -FOOT_Z + 0.01]), (S, 1)),
+        quat=np.tile(np.float32([1.0, 0, 0, 0]), (S, 1)), vel=np.zeros((S, 3), np.float32),
+        omega=np.zeros((S, 3), np.float32), theta0=np.zeros(J, np.float32),
+        act_mode=ACT_SINUSOID, act_params=act.astype(np.float32), name=f"uneven_{n_scenes}",
+        meta={"legs": kinds.astype(np.int32)})
 
 
 def rough_heightfields(rng, n_maps, n=128, cell=0.05, sigma_cells=2.0, std=0.02):
     """Per-scene n x n FP32 height fields: N(0,1) noise, periodic Gaussian blur (sigma in cells),
     rescaled to the given standard deviation [m]."""
-    k = np.fft.fftfreq(n)
-    g = np.exp(-2 * (math.pi * sigma_cells) ** 2 * (k[:, None] ** 2 + k[None, :] ** 2))
+    import scipy.fft as sfft
+    ky = np.fft.fftfreq(n)
+    kx = np.fft.rfftfreq(n)
+    g = np.exp(-2 * (math.pi * sigma_cells) ** 2 * (ky[:, None] ** 2 + kx[None, :] ** 2))
     out = np.empty((n_maps, n, n), np.float32)
-    chunk = 512
+    chunk = 1024
     for i in range(0, n_maps, chunk):
-        z = rng.standard_normal((min(chunk, n_maps - i), n, n))
-        z = np.fft.ifft2(np.fft.fft2(z) * g).real
+        z = rng.standard_normal((min(chunk, n_maps - i), n, n), dtype=np.float32)
+        z = sfft.irfft2(sfft.rfft2(z, workers=-1) * g, s=(n, n), workers=-1)
         z /= z.std(axis=(1, 2), keepdims=True)
         out[i:i + len(z)] = (z * std).astype(np.float32)
     return out

@@ -64,6 +64,20 @@ def test_single_body_per_step():
                         max_near_frac=0.3)
 
 
+def test_rough_terrain_cpg_per_step():
+    """Hexapods with per-leg CPG targets on 128 x 128 rough height fields (5 cm cells)."""
+    b = scenes.cpg_batch(32, seed_key=2)
+    w = World.from_batch(b)
+    _assert_step_parity(w, Oracle(b, threads=THREADS), [0, 1, 80, 81, 300, 801, 1600],
+                        max_near_frac=0.2)
+
+
+def test_rough_terrain_200_step_window():
+    dc, da, r, o = _window(scenes.cpg_batch(64, seed_key=3), 500)
+    assert ((dc <= 1e-3) & (da <= 1e-3)).mean() >= 0.9
+    assert np.median(dc) < 1e-5
+
+
 def _window(b, n0, horizon=200, lps=0):
     o = Oracle(b, threads=THREADS)
     o.step(n0, threads=THREADS)
