@@ -14,7 +14,8 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnpx.so")
-HEADER = os.path.join(os.path.dirname(HERE), "include", "npx.h")
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
+HEADER = os.path.join(INCLUDE, "npx.h")
 
 NPX_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ESTATE", -4: "ECUDA", -5: "ETIMEOUT", -6: "ERANGE"}
@@ -82,6 +83,23 @@ def step_noalloc(device_world: DeviceWorld, n_steps: int, stream=None):
     _check(_lib.npx_step_noalloc(C.byref(device_world), int(n_steps), stream))
 
 
+EPI_BIAS, EPI_BIAS_GELU, EPI_F32, EPI_DGELU = 0, 1, 2, 3
+
+
+class GemmEpilogue(C.Structure):
+    """npx_gemm_epilogue (include/npx_mlp.h)."""
+    _fields_ = [("mode", C.c_int), ("bias", C.c_void_p), ("out", C.c_void_p), ("ldo", C.c_int),
+                ("outT", C.c_void_p), ("ldt", C.c_int), ("outf", C.c_void_p), ("ldf", C.c_int),
+                ("split_stride", C.c_longlong), ("zsave", C.c_void_p), ("ldz", C.c_int),
+                ("zin", C.c_void_p), ("ldzi", C.c_int)]
+
+
+def gemm_bf16(A, B, M, N, K, epilogue: GemmEpilogue, err, splits=1, stream=None):
+    """npx_gemm_bf16: C = A B^T on the tensor cores (device pointers as integers)."""
+    load()
+    _check(_lib.npx_gemm_bf16(A, B, M, N, K, splits, C.byref(epilogue), err, stream))
+
+
 P = C.c_void_p
 I = C.c_int
 F = C.c_float
@@ -112,15 +130,20 @@ _SIGS = {
     "npx_world_autotune": [P, I, P],
     "npx_world_use_graphs": [P, I],
     "npx_step_noalloc": [P, I, P],
+    "npx_gemm_bf16": [P, P, I, I, I, I, P, P, P],
 }
 
 _lib = None
 
 
 def header_functions() -> list[str]:
-    """Names of every function the public header declares."""
-    text = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*(npx_\w+)\s*\(", text, re.M)))
+    """Names of every function the public headers (include/*.h) declare."""
+    names = set()
+    for h in sorted(os.listdir(INCLUDE)):
+        if h.endswith(".h"):
+            text = open(os.path.join(INCLUDE, h)).read()
+            names |= set(re.findall(r"^\s*(?:int|const char \*)\s*(npx_\w+)\s*\(", text, re.M))
+    return sorted(names)
 
 
 def load(path: str = LIB_PATH) -> C.CDLL:
