@@ -51,6 +51,42 @@ typedef struct {
 int npx_gemm_bf16(const void *A, const void *B, int M, int N, int K, int splits,
                   const npx_gemm_epilogue *epilogue, int *err, void *stream);
 
+/* --- the surrogate network --------------------------------------------------------------
+ * y = W_L gelu(... gelu(W_1 x + b_1) ...) + b_L with n_hidden_layers GELU layers of width
+ * n_hidden (exact GELU, z Phi(z)), trained on the mean over the batch of the squared error summed
+ * over outputs, with Adam.  Master weights, gradients and Adam moments are FP32; the GEMMs read
+ * BF16 copies of the weights and BF16 activations and accumulate in FP32.  Inputs are zero-padded
+ * to a multiple of 128 features and outputs to a multiple of 128 (the padding never reaches the
+ * caller).  x, t, y below are DEVICE arrays, row-major, rows = samples; M (rows per call) must be
+ * a multiple of 128 and at most max_batch.  Calls are asynchronous on the network's stream unless
+ * they return host data. */
+typedef struct npx_mlp npx_mlp;
+
+typedef struct {
+    int n_in, n_hidden, n_hidden_layers, n_out;
+    int max_batch;
+    float lr, beta1, beta2, eps;     /* Adam */
+    unsigned long long seed;         /* He-normal initial weights, zero biases */
+    void *stream;                    /* cudaStream_t; NULL = a stream the network creates */
+} npx_mlp_desc;
+
+int npx_mlp_create(const npx_mlp_desc *desc, npx_mlp **out);
+int npx_mlp_destroy(npx_mlp *net);
+/* Host FP32 parameters, layer by layer: W_l [n_out_l x n_in_l] row-major, b_l [n_out_l]
+ * (unpadded sizes), concatenated in layer order (W_1, b_1, W_2, b_2, ...). */
+int npx_mlp_params_set(npx_mlp *net, const float *params, size_t n);
+int npx_mlp_params_get(npx_mlp *net, float *params, size_t n);
+size_t npx_mlp_param_count(const npx_mlp *net);
+/* y [M x n_out] = network(x [M x n_in]) */
+int npx_mlp_forward(npx_mlp *net, const float *x, float *y, int M);
+/* Gradients of the loss on (x, t) into the network's gradient buffers; *loss (device float)
+ * receives the batch loss. */
+int npx_mlp_backward(npx_mlp *net, const float *x, const float *t, int M, float *loss);
+/* Host FP32 copy of the last gradients, same layout as the parameters. */
+int npx_mlp_grads_get(npx_mlp *net, float *grads, size_t n);
+/* One Adam step with the last gradients. */
+int npx_mlp_adam_step(npx_mlp *net);
+
 #ifdef __cplusplus
 }
 #endif

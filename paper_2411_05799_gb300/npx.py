@@ -131,6 +131,14 @@ _SIGS = {
     "npx_world_use_graphs": [P, I],
     "npx_step_noalloc": [P, I, P],
     "npx_gemm_bf16": [P, P, I, I, I, I, P, P, P],
+    "npx_mlp_create": [P, P],
+    "npx_mlp_destroy": [P],
+    "npx_mlp_params_set": [P, P, C.c_size_t],
+    "npx_mlp_params_get": [P, P, C.c_size_t],
+    "npx_mlp_grads_get": [P, P, C.c_size_t],
+    "npx_mlp_forward": [P, P, P, I],
+    "npx_mlp_backward": [P, P, P, I, P],
+    "npx_mlp_adam_step": [P],
 }
 
 _lib = None
@@ -142,7 +150,7 @@ def header_functions() -> list[str]:
     for h in sorted(os.listdir(INCLUDE)):
         if h.endswith(".h"):
             text = open(os.path.join(INCLUDE, h)).read()
-            names |= set(re.findall(r"^\s*(?:int|const char \*)\s*(npx_\w+)\s*\(", text, re.M))
+            names |= set(re.findall(r"^\s*(?:int|size_t|const char \*)\s*(npx_\w+)\s*\(", text, re.M))
     return sorted(names)
 
 
@@ -160,6 +168,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         fn.restype = C.c_int
     lib.npx_last_error.argtypes = []
     lib.npx_last_error.restype = C.c_char_p
+    lib.npx_mlp_param_count.argtypes = [P]
+    lib.npx_mlp_param_count.restype = C.c_size_t
     _lib = lib
     return lib
 
@@ -358,3 +368,72 @@ class World:
 
     def use_graphs(self, on: bool):
         _check(_lib.npx_world_use_graphs(self._h, 1 if on else 0))
+
+
+class MLPDesc(C.Structure):
+    _fields_ = [("n_in", C.c_int), ("n_hidden", C.c_int), ("n_hidden_layers", C.c_int),
+                ("n_out", C.c_int), ("max_batch", C.c_int), ("lr", C.c_float),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("seed", C.c_ulonglong), ("stream", C.c_void_p)]
+
+
+class MLP:
+    """The surrogate network (npx_mlp): tensor-core forward, backward and Adam.  Arrays passed
+    to forward/backward are device pointers (integers, e.g. torch tensors' data_ptr())."""
+
+    def __init__(self, n_in, n_out, n_hidden=512, n_hidden_layers=4, max_batch=8192, lr=1e-3,
+                 beta1=0.9, beta2=0.999, eps=1e-8, seed=0, stream=None):
+        lib = load()
+        self._h = P()
+        d = MLPDesc(n_in, n_hidden, n_hidden_layers, n_out, max_batch, lr, beta1, beta2, eps,
+                    seed, stream)
+        _check(lib.npx_mlp_create(C.byref(d), C.byref(self._h)))
+        self.n_in, self.n_out = n_in, n_out
+        self.sizes = [n_in] + [n_hidden] * n_hidden_layers + [n_out]
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.npx_mlp_destroy(self._h)
+            self._h = P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_params(self) -> int:
+        return int(_lib.npx_mlp_param_count(self._h))
+
+    def set_params(self, Ws, bs):
+        flat = np.concatenate([np.concatenate([np.asarray(W, np.float32).ravel(),
+                                               np.asarray(b, np.float32).ravel()])
+                               for W, b in zip(Ws, bs)]).astype(np.float32)
+        _check(_lib.npx_mlp_params_set(self._h, _p(flat), flat.size))
+
+    def _unflat(self, flat):
+        Ws, bs, off = [], [], 0
+        for fi, fo in zip(self.sizes[:-1], self.sizes[1:]):
+            Ws.append(flat[off:off + fi * fo].reshape(fo, fi)); off += fi * fo
+            bs.append(flat[off:off + fo]); off += fo
+        return Ws, bs
+
+    def get_params(self):
+        flat = np.zeros(self.n_params, np.float32)
+        _check(_lib.npx_mlp_params_get(self._h, _p(flat), flat.size))
+        return self._unflat(flat)
+
+    def get_grads(self):
+        flat = np.zeros(self.n_params, np.float32)
+        _check(_lib.npx_mlp_grads_get(self._h, _p(flat), flat.size))
+        return self._unflat(flat)
+
+    def forward(self, x_ptr, y_ptr, M):
+        _check(_lib.npx_mlp_forward(self._h, x_ptr, y_ptr, M))
+
+    def backward(self, x_ptr, t_ptr, M, loss_ptr):
+        _check(_lib.npx_mlp_backward(self._h, x_ptr, t_ptr, M, loss_ptr))
+
+    def adam_step(self):
+        _check(_lib.npx_mlp_adam_step(self._h))

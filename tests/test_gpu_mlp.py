@@ -1,0 +1,103 @@
+"""The surrogate network on the tensor cores (BF16 operands, FP32 accumulation) against the FP64
+oracle of oracle/mlp.py: forward outputs, loss and every layer's gradients within BF16 bounds,
+Adam's first step, and training that actually fits."""
+import numpy as np
+import pytest
+
+from oracle import mlp as ref
+from paper_2411_05799_gb300 import npx
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+SIZES = [271, 512, 512, 512, 512, 247]
+
+
+def _rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _setup(M=256, seed=0):
+    rng = np.random.default_rng(seed)
+    Ws, bs = ref.init_params(SIZES, seed=seed)
+    bs = [rng.normal(0, 0.05, b.shape) for b in bs]
+    x = rng.normal(0, 1, (M, SIZES[0])).astype(np.float32)
+    t = rng.normal(0, 1, (M, SIZES[-1])).astype(np.float32)
+    net = npx.MLP(SIZES[0], SIZES[-1], max_batch=M, lr=1e-3,
+                  stream=torch.cuda.current_stream().cuda_stream)
+    net.set_params([W.astype(np.float32) for W in Ws], [b.astype(np.float32) for b in bs])
+    Ws = [W.astype(np.float32).astype(np.float64) for W in Ws]     # the values the GPU holds
+    bs = [b.astype(np.float32).astype(np.float64) for b in bs]
+    return net, Ws, bs, x, t
+
+
+def test_params_round_trip():
+    net, Ws, bs, x, t = _setup()
+    W2, b2 = net.get_params()
+    for a, b in zip(W2 + b2, Ws + bs):
+        np.testing.assert_array_equal(a, b.astype(np.float32))
+
+
+def test_forward_matches_fp64_oracle():
+    net, Ws, bs, x, t = _setup()
+    M = len(x)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.zeros(M, SIZES[-1], device="cuda")
+    net.forward(xd.data_ptr(), yd.data_ptr(), M)
+    torch.cuda.synchronize()
+    y_ref, _ = ref.forward(Ws, bs, x.astype(np.float64))
+    assert _rel(yd.cpu().numpy(), y_ref) < 2e-2
+
+
+def test_gradients_match_fp64_oracle():
+    net, Ws, bs, x, t = _setup()
+    M = len(x)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    loss = torch.zeros(1, device="cuda")
+    net.backward(xd.data_ptr(), td.data_ptr(), M, loss.data_ptr())
+    dW, db = net.get_grads()
+    y, cache = ref.forward(Ws, bs, x.astype(np.float64))
+    rW, rb = ref.backward(Ws, bs, cache, y, t.astype(np.float64))
+    assert abs(float(loss.item()) - ref.mse(y, t)) < 2e-2 * ref.mse(y, t)
+    for l in range(len(rW)):
+        assert _rel(dW[l], rW[l]) < 5e-2, (l, _rel(dW[l], rW[l]))
+        assert _rel(db[l], rb[l]) < 5e-2, (l, _rel(db[l], rb[l]))
+        cos = np.sum(dW[l] * rW[l]) / (np.linalg.norm(dW[l]) * np.linalg.norm(rW[l]))
+        assert cos > 0.998, (l, cos)
+
+
+def test_adam_first_step_moves_each_weight_by_the_learning_rate():
+    net, Ws, bs, x, t = _setup()
+    M = len(x)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    loss = torch.zeros(1, device="cuda")
+    W0, b0 = net.get_params()
+    net.backward(xd.data_ptr(), td.data_ptr(), M, loss.data_ptr())
+    g, gb = net.get_grads()
+    net.adam_step()
+    W1, b1 = net.get_params()
+    for l in range(len(W0)):
+        want = W0[l] - 1e-3 * g[l] / (np.abs(g[l]) + 1e-8)
+        np.testing.assert_allclose(W1[l], want, rtol=0, atol=2e-6)
+
+
+def test_training_fits_a_smooth_map():
+    """Fit t = sin(x A) B on random inputs: the loss falls by more than 20x in 300 steps."""
+    M = 1024
+    rng = np.random.default_rng(7)
+    A = rng.normal(0, 0.2, (SIZES[0], 16))
+    B = rng.normal(0, 1.0, (16, SIZES[-1]))
+    x = rng.normal(0, 1, (M, SIZES[0])).astype(np.float32)
+    t = (np.sin(x @ A) @ B).astype(np.float32)
+    net = npx.MLP(SIZES[0], SIZES[-1], max_batch=M, lr=1e-3, seed=3,
+                  stream=torch.cuda.current_stream().cuda_stream)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    loss = torch.zeros(1, device="cuda")
+    losses = []
+    for it in range(300):
+        net.backward(xd.data_ptr(), td.data_ptr(), M, loss.data_ptr())
+        net.adam_step()
+        if it % 50 == 0 or it == 299:
+            losses.append(float(loss.item()))
+    assert losses[-1] < losses[0] / 20, losses
