@@ -87,6 +87,33 @@ int npx_mlp_grads_get(npx_mlp *net, float *grads, size_t n);
 /* One Adam step with the last gradients. */
 int npx_mlp_adam_step(npx_mlp *net);
 
+/* --- the surrogate step -----------------------------------------------------------------
+ * For worlds whose scenes all have the same number of links NL (NL - 1 joints) and NS contact-
+ * sensor bits, a scene's features are, per link: the CoG of the link's points (x, y relative to a
+ * horizontal reference, z absolute), the link's orientation quaternion, the velocity of its CoG
+ * and the angular velocity (13 numbers), then the NL - 1 joint angles after the current step's
+ * joint update and the NS contact bits of the last step: n_features = 14 NL - 1 + NS (271 for
+ * the 18-DoF six-sensor hexapod).  The target of a transition is the change of the link part
+ * over one step (n_targets = 13 NL), positions taken relative to the first state's CoG.
+ * Standardisation (all DEVICE arrays, NULL = raw values): features (x - x_mu) * x_isd, targets
+ * (d - t_mu) / t_sd. */
+typedef struct {
+    const float *x_mu, *x_isd, *t_mu, *t_sd;
+} npx_surrogate_norm;
+
+int npx_surrogate_dims(npx_world *w, int *n_features, int *n_targets);
+/* Advance the world n_steps plain steps, writing every step's features X and targets T
+ * (DEVICE, rows = step * n_scenes + scene, standardised when norm is given). */
+int npx_surrogate_collect(npx_world *w, const npx_surrogate_norm *norm, int n_steps, float *X,
+                          float *T);
+/* Advance the world n_steps surrogate steps: the network predicts every scene's next state from
+ * its features; scenes whose contact sensors change during a step redo that step with the plain
+ * step (the fallback).  *fallbacks (host, may be NULL) receives the number of scene-steps that
+ * fell back.  The network must take n_features inputs, give n_targets outputs, and hold at least
+ * n_scenes rounded up to 128 rows. */
+int npx_world_step_surrogate(npx_world *w, npx_mlp *net, const npx_surrogate_norm *norm,
+                             int n_steps, long long *fallbacks);
+
 #ifdef __cplusplus
 }
 #endif

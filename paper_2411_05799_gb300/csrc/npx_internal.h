@@ -25,6 +25,7 @@ struct WorldDev {
     const float4 *p0m;                    // [P] construction position (xyz) and mass (w)
     const uint8_t *plink;                 // [P] scene-local link of each point
     const float *gref;                    // [3 * S] rest-pose CoG (centring reference of sums)
+    const float *link_cog;                // [3 * L] CoG of each link's points, construction frame
     const LinkDev *links;                 // [L]
     const float *mu;                      // [S]
     const int *hmap;                      // [S] height map per scene, -1 = flat z = 0
@@ -46,6 +47,8 @@ struct WorldDev {
     uint32_t *sensors, *status;           // [S]
     // schedule
     const int *order;                     // [S] scenes, most points first
+    int n_sched;                          // entries of order to run
+    const int *sched_count;               // device count overriding n_sched, or NULL
     int max_points, max_links;
     const long long *step;                // device step counter n
     unsigned int *queue;                  // work-queue counter (reset before each launch)
@@ -64,8 +67,28 @@ cudaError_t launch_advance(long long *d_step, int n, cudaStream_t st);
 cudaError_t launch_init(const WorldDev &W, const float *d_origin, const float *d_quat,
                         const float *d_vel, const float *d_omega, cudaStream_t st);
 cudaError_t launch_refresh(const WorldDev &W, cudaStream_t st);
+cudaError_t launch_features(const WorldDev &W, int nf, int nt, int nl, int ns, float *X, float *Xraw,
+                            float *cxy_out, const float *cxy_ref, const float *prev, float *T,
+                            const float *x_mu, const float *x_isd, const float *t_mu,
+                            const float *t_sd, cudaStream_t st);
+cudaError_t launch_surrogate_apply(const WorldDev &W, const float *Y, const float *t_mu,
+                                   const float *t_sd, const float *F0, int nf, int nt,
+                                   const float *cxy0, cudaStream_t st);
+cudaError_t launch_contact_probe(const WorldDev &W, int *list, int *count, cudaStream_t st);
+cudaError_t launch_restore(const WorldDev &W, const int *list, const int *count, const float *st_b,
+                           const float *theta_b, const uint8_t *kappa_b, const uint32_t *sens_b,
+                           const uint32_t *status_b, cudaStream_t st);
+cudaError_t launch_accumulate(long long *total, int *count, cudaStream_t st);
 // records msg as the thread's npx_last_error() text and returns code
 int set_last_error(int code, const char *msg);
 cudaError_t launch_points(const WorldDev &W, int scene, float *d_out, cudaStream_t st);
 
+}  // namespace npx
+
+struct npx_mlp;
+namespace npx {
+// the surrogate network's stream, batch capacity and input / output widths
+cudaStream_t mlp_stream(const npx_mlp *net);
+int mlp_max_batch(const npx_mlp *net);
+void mlp_dims(const npx_mlp *net, int *n_in, int *n_out);
 }  // namespace npx

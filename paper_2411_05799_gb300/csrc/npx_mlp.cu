@@ -200,6 +200,13 @@ int forward_impl(npx_mlp *n, const float *x, int M, bool train) {
 
 }  // namespace
 
+cudaStream_t npx::mlp_stream(const npx_mlp *n) { return n->stream; }
+int npx::mlp_max_batch(const npx_mlp *n) { return n->d.max_batch; }
+void npx::mlp_dims(const npx_mlp *n, int *n_in, int *n_out) {
+    *n_in = n->d.n_in;
+    *n_out = n->d.n_out;
+}
+
 extern "C" {
 
 int npx_mlp_create(const npx_mlp_desc *d, npx_mlp **out) {

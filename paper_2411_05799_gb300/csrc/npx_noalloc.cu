@@ -113,6 +113,7 @@ extern "C" int npx_step_noalloc(const npx_device_world *d, int n_steps, void *st
     W.queue = scratch;
     W.step = reinterpret_cast<const long long *>(scratch + 2);
     W.order = reinterpret_cast<const int *>(scratch + NOALLOC_HEADER_WORDS);
+    W.n_sched = W.S;
 
     int nb = npx::step_blocks_per_sm(W, lps, wpb, &e);   // also raises the kernel's smem limit
     if (e != cudaSuccess || nb < 1)

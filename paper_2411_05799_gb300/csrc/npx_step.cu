@@ -706,14 +706,15 @@ __global__ void __launch_bounds__(512) step_kernel(WorldDev W, int n_steps, int 
     float *th_old = th + W.max_links;
     float4 *tb = reinterpret_cast<float4 *>(slot + tiles_offset(W.max_points, W.max_links));
     const long long step0 = *W.step;
-    const int n_items = (W.S + G - 1) / G;
+    const int n_sched = W.sched_count ? *W.sched_count : W.n_sched;
+    const int n_items = (n_sched + G - 1) / G;
     for (;;) {
         int item = 0;
         if (lane == 0) item = (int)atomicAdd(W.queue, 1u);
         item = __shfl_sync(FULL_MASK, item, 0);
         if (item >= n_items) break;
         const int idx = item * G + g;
-        const int s = idx < W.S ? W.order[idx] : -1;
+        const int s = idx < n_sched ? W.order[idx] : -1;
         run_scene<LPS, FLAT>(W, s, gl, pts, fr, th, th_old, tb, n_steps, step0);
     }
 }
@@ -819,6 +820,279 @@ __global__ void __launch_bounds__(32) points_kernel(WorldDev W, int s, float *ou
         mat_vec(R, rr, x);
         out[3 * i] = c[0] + x[0]; out[3 * i + 1] = c[1] + x[1]; out[3 * i + 2] = c[2] + x[2];
     }
+}
+
+// ------------------------------------------------------------------------ learned surrogate
+// Scene features for the surrogate network (one warp per scene): per link, the CoG of its points
+// (horizontally relative to ref, or to the robot CoG), its orientation, the velocity of its CoG
+// and the angular velocity (13 numbers; the robot is one rigid body, so every link shares it);
+// then the joint angles after this step's joint update and the contact-sensor bits of the last
+// step.  Optionally standardised ((x - mu) * isd), optionally also the next-step delta target.
+
+// unit quaternion of a rotation matrix (row-major), sign chosen with w >= 0
+__device__ __forceinline__ void quat_from_mat(const float *Q, float *q) {
+    const float tr = Q[0] + Q[4] + Q[8];
+    float w, x, y, z;
+    if (tr > 0.f) {
+        const float s = 2.f * sqrtf(tr + 1.f);
+        w = 0.25f * s; x = (Q[7] - Q[5]) / s; y = (Q[2] - Q[6]) / s; z = (Q[3] - Q[1]) / s;
+    } else if (Q[0] > Q[4] && Q[0] > Q[8]) {
+        const float s = 2.f * sqrtf(1.f + Q[0] - Q[4] - Q[8]);
+        w = (Q[7] - Q[5]) / s; x = 0.25f * s; y = (Q[1] + Q[3]) / s; z = (Q[2] + Q[6]) / s;
+    } else if (Q[4] > Q[8]) {
+        const float s = 2.f * sqrtf(1.f + Q[4] - Q[0] - Q[8]);
+        w = (Q[2] - Q[6]) / s; x = (Q[1] + Q[3]) / s; y = 0.25f * s; z = (Q[5] + Q[7]) / s;
+    } else {
+        const float s = 2.f * sqrtf(1.f + Q[8] - Q[0] - Q[4]);
+        w = (Q[3] - Q[1]) / s; x = (Q[2] + Q[6]) / s; y = (Q[5] + Q[7]) / s; z = 0.25f * s;
+    }
+    const float sg = w < 0.f ? -1.f : 1.f;
+    q[0] = sg * w; q[1] = sg * x; q[2] = sg * y; q[3] = sg * z;
+}
+
+// joint angles after the joint update of step n (clamped targets on update steps)
+__device__ __forceinline__ float angle_after(const WorldDev &W, int l0, int j0, int j, const float *th,
+                                             long long n) {
+    if (W.act_mode != 0 && n % W.K == 0) {
+        const LinkDev lk = W.links[l0 + j + 1];
+        return fminf(fmaxf(joint_target(W, j0 + j, n), lk.lo), lk.hi);
+    }
+    return th[j];
+}
+
+struct SurrogateIO {
+    int nf, nt, nl, ns;
+    float *X;            // [S x nf] features (standardised when x_mu is set)
+    float *Xraw;         // [S x nf] raw features or NULL
+    float *cxy_out;      // [S x 2] robot CoG (x, y) or NULL
+    const float *cxy_ref;// [S x 2] horizontal reference or NULL (the robot CoG)
+    const float *prev;   // [S x nf] raw features of the previous state (delta target) or NULL
+    float *T;            // [S x nt] delta target (standardised when t_mu is set)
+    const float *x_mu, *x_isd, *t_mu, *t_sd;
+};
+
+__global__ void __launch_bounds__(128) features_kernel(WorldDev W, SurrogateIO io, int sbytes) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int s = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (s >= W.S) return;   // warp-uniform
+    unsigned char *slot = smem + (size_t)warp * sbytes;
+    float4 *pts = reinterpret_cast<float4 *>(slot);
+    float *fr = reinterpret_cast<float *>(slot + 16 * W.max_points);
+    float *th = fr + 12 * W.max_links;
+    const int p0 = W.point_off[s], np = W.point_off[s + 1] - p0;
+    const int l0 = W.link_off[s], nl = W.link_off[s + 1] - l0, j0 = l0 - s;
+    for (int j = lane; j < nl - 1; j += 32) th[j] = W.theta[j0 + j];
+    __syncwarp();
+    Shape sh;
+    shape_update<32>(W, s, p0, np, l0, nl, th, fr, pts, lane, sh);
+    const int S = W.S;
+    const float c[3] = {W.st[ST_CX * S + s], W.st[ST_CY * S + s], W.st[ST_CZ * S + s]};
+    const float q[4] = {W.st[ST_QW * S + s], W.st[ST_QX * S + s], W.st[ST_QY * S + s], W.st[ST_QZ * S + s]};
+    const float v[3] = {W.st[ST_VX * S + s], W.st[ST_VY * S + s], W.st[ST_VZ * S + s]};
+    const float L[3] = {W.st[ST_LX * S + s], W.st[ST_LY * S + s], W.st[ST_LZ * S + s]};
+    float R[9], om[3];
+    quat_mat(q, R);
+    world_sym(R, sh.Ii, L, om);
+    const float rx = io.cxy_ref ? io.cxy_ref[2 * s] : c[0], ry = io.cxy_ref ? io.cxy_ref[2 * s + 1] : c[1];
+    const long long n = *W.step;
+    auto emit = [&](int i, float raw) {
+        const size_t o = (size_t)s * io.nf + i;
+        if (io.Xraw) io.Xraw[o] = raw;
+        if (io.X) io.X[o] = io.x_mu ? (raw - io.x_mu[i]) * io.x_isd[i] : raw;
+        if (io.T && i < io.nt) {
+            const float d = raw - io.prev[o];
+            io.T[(size_t)s * io.nt + i] = io.t_mu ? (d - io.t_mu[i]) / io.t_sd[i] : d;
+        }
+    };
+    for (int l = lane; l < io.nl; l += 32) {
+        float f[13];
+        if (l < nl) {
+            const float *F = fr + 12 * l;
+            const float pc[3] = {W.link_cog[3 * (l0 + l)], W.link_cog[3 * (l0 + l) + 1], W.link_cog[3 * (l0 + l) + 2]};
+            float ps[3], r[3], ql[4], qq[4];
+            ps[0] = F[0] * pc[0] + F[1] * pc[1] + F[2] * pc[2] + F[9] - sh.g[0];
+            ps[1] = F[3] * pc[0] + F[4] * pc[1] + F[5] * pc[2] + F[10] - sh.g[1];
+            ps[2] = F[6] * pc[0] + F[7] * pc[1] + F[8] * pc[2] + F[11] - sh.g[2];
+            mat_vec(R, ps, r);
+            quat_from_mat(F, ql);
+            quat_mul(q, ql, qq);
+            f[0] = c[0] + r[0] - rx; f[1] = c[1] + r[1] - ry; f[2] = c[2] + r[2];
+            f[3] = qq[0]; f[4] = qq[1]; f[5] = qq[2]; f[6] = qq[3];
+            f[7] = v[0] + om[1] * r[2] - om[2] * r[1];
+            f[8] = v[1] + om[2] * r[0] - om[0] * r[2];
+            f[9] = v[2] + om[0] * r[1] - om[1] * r[0];
+            f[10] = om[0]; f[11] = om[1]; f[12] = om[2];
+        } else {
+            for (int i = 0; i < 13; ++i) f[i] = 0.f;
+        }
+        for (int i = 0; i < 13; ++i) emit(13 * l + i, f[i]);
+    }
+    for (int j = lane; j < io.nl - 1; j += 32) emit(13 * io.nl + j, j < nl - 1 ? angle_after(W, l0, j0, j, th, n) : 0.f);
+    const uint32_t sens = W.sensors[s];
+    for (int k = lane; k < io.ns; k += 32) emit(13 * io.nl + io.nl - 1 + k, (float)((sens >> k) & 1u));
+    if (lane == 0 && io.cxy_out) { io.cxy_out[2 * s] = c[0]; io.cxy_out[2 * s + 1] = c[1]; }
+}
+
+// Surrogate update of one scene: joint angles of this step's update, then the root state from
+// the torso's predicted next state (position, orientation, CoG velocity, angular velocity).
+__global__ void __launch_bounds__(128) surrogate_apply_kernel(WorldDev W, const float *Y, const float *t_mu,
+                                                              const float *t_sd, const float *F0, int nf, int nt,
+                                                              const float *cxy0, int sbytes) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int s = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (s >= W.S) return;   // warp-uniform
+    unsigned char *slot = smem + (size_t)warp * sbytes;
+    float4 *pts = reinterpret_cast<float4 *>(slot);
+    float *fr = reinterpret_cast<float *>(slot + 16 * W.max_points);
+    float *th = fr + 12 * W.max_links;
+    const int p0 = W.point_off[s], np = W.point_off[s + 1] - p0;
+    const int l0 = W.link_off[s], nl = W.link_off[s + 1] - l0, j0 = l0 - s;
+    const long long n = *W.step;
+    const uint32_t status = W.status[s];
+    for (int j = lane; j < nl - 1; j += 32) th[j] = W.theta[j0 + j];
+    __syncwarp();
+    for (int j = lane; j < nl - 1; j += 32) {
+        const float a = status ? th[j] : angle_after(W, l0, j0, j, th, n);
+        th[j] = a;
+        W.theta[j0 + j] = a;
+    }
+    __syncwarp();
+    Shape sh;
+    shape_update<32>(W, s, p0, np, l0, nl, th, fr, pts, lane, sh);
+    if (lane != 0 || status) return;
+    float f[13];
+    for (int i = 0; i < 13; ++i) f[i] = F0[(size_t)s * nf + i] + Y[(size_t)s * nt + i] * t_sd[i] + t_mu[i];
+    float qn[4] = {f[3], f[4], f[5], f[6]};
+    const float inv = rsqrtf(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
+    qn[0] *= inv; qn[1] *= inv; qn[2] *= inv; qn[3] *= inv;
+    float R[9];
+    quat_mat(qn, R);
+    // root link frame = shape frame: torso CoG offset from the robot CoG is link_cog - g
+    const float ps[3] = {W.link_cog[3 * l0] - sh.g[0], W.link_cog[3 * l0 + 1] - sh.g[1], W.link_cog[3 * l0 + 2] - sh.g[2]};
+    float d[3], L[3];
+    mat_vec(R, ps, d);
+    const float om[3] = {f[10], f[11], f[12]};
+    const float c[3] = {cxy0[2 * s] + f[0] - d[0], cxy0[2 * s + 1] + f[1] - d[1], f[2] - d[2]};
+    const float v[3] = {f[7] - (om[1] * d[2] - om[2] * d[1]), f[8] - (om[2] * d[0] - om[0] * d[2]),
+                        f[9] - (om[0] * d[1] - om[1] * d[0])};
+    world_sym(R, sh.Ib, om, L);
+    const float chk = c[0] + c[1] + c[2] + v[0] + v[1] + v[2] + L[0] + L[1] + L[2] + qn[0] + qn[1] + qn[2] + qn[3];
+    if (!isfinite(chk)) { W.status[s] = status | 1u; return; }
+    const int S = W.S;
+    W.st[ST_CX * S + s] = c[0]; W.st[ST_CY * S + s] = c[1]; W.st[ST_CZ * S + s] = c[2];
+    W.st[ST_QW * S + s] = qn[0]; W.st[ST_QX * S + s] = qn[1]; W.st[ST_QY * S + s] = qn[2]; W.st[ST_QZ * S + s] = qn[3];
+    W.st[ST_VX * S + s] = v[0]; W.st[ST_VY * S + s] = v[1]; W.st[ST_VZ * S + s] = v[2];
+    W.st[ST_LX * S + s] = L[0]; W.st[ST_LY * S + s] = L[1]; W.st[ST_LZ * S + s] = L[2];
+    W.omega[s] = om[0]; W.omega[S + s] = om[1]; W.omega[2 * S + s] = om[2];
+}
+
+// Contacts of every point at the current state; scenes whose contact sensors changed are
+// appended to list (the plain step redoes them), the others keep the new contacts.
+template <bool FLAT>
+__global__ void __launch_bounds__(128) contact_probe_kernel(WorldDev W, int *list, int *count, int sbytes) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int s = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (s >= W.S) return;   // warp-uniform
+    unsigned char *slot = smem + (size_t)warp * sbytes;
+    float4 *pts = reinterpret_cast<float4 *>(slot);
+    float *fr = reinterpret_cast<float *>(slot + 16 * W.max_points);
+    float *th = fr + 12 * W.max_links;
+    const int p0 = W.point_off[s], np = W.point_off[s + 1] - p0;
+    const int l0 = W.link_off[s], nl = W.link_off[s + 1] - l0, j0 = l0 - s;
+    for (int j = lane; j < nl - 1; j += 32) th[j] = W.theta[j0 + j];
+    __syncwarp();
+    Shape sh;
+    shape_update<32>(W, s, p0, np, l0, nl, th, fr, pts, lane, sh);
+    const int S = W.S;
+    const float c[3] = {W.st[ST_CX * S + s], W.st[ST_CY * S + s], W.st[ST_CZ * S + s]};
+    const float q[4] = {W.st[ST_QW * S + s], W.st[ST_QX * S + s], W.st[ST_QY * S + s], W.st[ST_QZ * S + s]};
+    float R[9];
+    quat_mat(q, R);
+    const int hm = FLAT ? -1 : W.hmap[s];
+    uint32_t sens = 0;
+    for (int i = lane; i < np; i += 32) {
+        const float4 r = pts[i];
+        const float x = c[0] + R[0] * r.x + R[1] * r.y + R[2] * r.z;
+        const float y = c[1] + R[3] * r.x + R[4] * r.y + R[5] * r.z;
+        const float z = c[2] + R[6] * r.x + R[7] * r.y + R[8] * r.z;
+        const bool k = z < ground<FLAT>(W, hm, x, y);
+        W.kappa[p0 + i] = k ? 1 : 0;
+        if (k) {
+            const int sid = W.links[l0 + W.plink[p0 + i]].sensor;
+            if (sid >= 0 && sid < 32) sens |= 1u << sid;
+        }
+    }
+    sens = gor<32>(sens);
+    if (lane == 0) {
+        if (sens != W.sensors[s] && W.status[s] == 0u) list[atomicAdd(count, 1)] = s;
+        W.sensors[s] = sens;
+    }
+}
+
+// Put the listed scenes back to their state before the surrogate step.
+__global__ void restore_kernel(WorldDev W, const int *list, const int *count, const float *st, const float *theta,
+                               const uint8_t *kappa, const uint32_t *sensors, const uint32_t *status) {
+    const int i = blockIdx.x;
+    if (i >= *count) return;
+    const int s = list[i];
+    const int S = W.S;
+    const int p0 = W.point_off[s], np = W.point_off[s + 1] - p0;
+    const int l0 = W.link_off[s], nj = W.link_off[s + 1] - l0 - 1, j0 = l0 - s;
+    for (int k = threadIdx.x; k < ST_N; k += blockDim.x) W.st[k * S + s] = st[k * S + s];
+    for (int j = threadIdx.x; j < nj; j += blockDim.x) W.theta[j0 + j] = theta[j0 + j];
+    for (int p = threadIdx.x; p < np; p += blockDim.x) W.kappa[p0 + p] = kappa[p0 + p];
+    if (threadIdx.x == 0) { W.sensors[s] = sensors[s]; W.status[s] = status[s]; }
+}
+
+__global__ void accumulate_kernel(long long *total, int *count) {
+    *total += *count;
+    *count = 0;
+}
+
+cudaError_t launch_accumulate(long long *total, int *count, cudaStream_t st) {
+    accumulate_kernel<<<1, 1, 0, st>>>(total, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_features(const WorldDev &W, int nf, int nt, int nl, int ns, float *X, float *Xraw, float *cxy_out,
+                            const float *cxy_ref, const float *prev, float *T, const float *x_mu, const float *x_isd,
+                            const float *t_mu, const float *t_sd, cudaStream_t st) {
+    const int wpb = 4, sb = slot_bytes(W.max_points, W.max_links, 32);
+    cudaError_t e = cudaFuncSetAttribute((void *)features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, wpb * sb);
+    if (e != cudaSuccess) return e;
+    SurrogateIO io{nf, nt, nl, ns, X, Xraw, cxy_out, cxy_ref, prev, T, x_mu, x_isd, t_mu, t_sd};
+    features_kernel<<<(W.S + wpb - 1) / wpb, wpb * 32, wpb * sb, st>>>(W, io, sb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_surrogate_apply(const WorldDev &W, const float *Y, const float *t_mu, const float *t_sd,
+                                   const float *F0, int nf, int nt, const float *cxy0, cudaStream_t st) {
+    const int wpb = 4, sb = slot_bytes(W.max_points, W.max_links, 32);
+    cudaError_t e = cudaFuncSetAttribute((void *)surrogate_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, wpb * sb);
+    if (e != cudaSuccess) return e;
+    surrogate_apply_kernel<<<(W.S + wpb - 1) / wpb, wpb * 32, wpb * sb, st>>>(W, Y, t_mu, t_sd, F0, nf, nt, cxy0, sb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_contact_probe(const WorldDev &W, int *list, int *count, cudaStream_t st) {
+    const int wpb = 4, sb = slot_bytes(W.max_points, W.max_links, 32);
+    void *fn = W.hm ? (void *)contact_probe_kernel<false> : (void *)contact_probe_kernel<true>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, wpb * sb);
+    if (e != cudaSuccess) return e;
+    WorldDev w = W;
+    int sbv = sb;
+    void *args[] = {&w, &list, &count, &sbv};
+    return cudaLaunchKernel(fn, dim3((W.S + wpb - 1) / wpb), dim3(wpb * 32), args, wpb * sb, st);
+}
+
+cudaError_t launch_restore(const WorldDev &W, const int *list, const int *count, const float *st_b,
+                           const float *theta_b, const uint8_t *kappa_b, const uint32_t *sens_b,
+                           const uint32_t *status_b, cudaStream_t st) {
+    restore_kernel<<<W.S, 128, 0, st>>>(W, list, count, st_b, theta_b, kappa_b, sens_b, status_b);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------ host-side launchers

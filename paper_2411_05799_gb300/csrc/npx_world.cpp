@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/npx.h"
+#include "../../include/npx_mlp.h"
 #include "npx_internal.h"
 
 namespace {
@@ -108,6 +109,19 @@ struct npx_world {
     std::map<int, cudaGraphExec_t> graph_cache;
     long long launches = 0;
     int act_mode = NPX_ACT_HOLD;
+    bool uniform_links = true;          // every scene has max_links links
+    int sensor_bits = 0;                // highest contact-sensor bit + 1
+    // surrogate-step buffers, allocated on first use
+    struct {
+        float *X = nullptr, *F0 = nullptr, *F1 = nullptr, *C0 = nullptr, *Y = nullptr;
+        float *st = nullptr, *theta = nullptr;
+        uint8_t *kappa = nullptr;
+        uint32_t *sens = nullptr, *status = nullptr;
+        int *list = nullptr, *count = nullptr;
+        long long *total = nullptr;
+        cudaEvent_t ev_w = nullptr, ev_n = nullptr;
+        int rows = 0;
+    } sg;
 };
 
 namespace {
@@ -297,6 +311,40 @@ const uint64_t kBlobMagic = 0x315850584e504e47ull;
 
 }  // namespace
 
+namespace {
+
+int surrogate_dims(npx_world *w, int *nf, int *nt) {
+    if (!w->uniform_links) return fail(NPX_EINVAL, "surrogate features need scenes with equal link counts");
+    const int NL = w->max_links;
+    *nf = 14 * NL - 1 + w->sensor_bits;
+    *nt = 13 * NL;
+    return NPX_OK;
+}
+
+int surrogate_buffers(npx_world *w) {
+    if (w->sg.X) return NPX_OK;
+    int nf, nt;
+    if (int rc = surrogate_dims(w, &nf, &nt)) return rc;
+    const int rows = (w->S + 127) / 128 * 128;
+    int rc;
+    if ((rc = dev_alloc(w, &w->sg.X, (size_t)rows * nf)) || (rc = dev_alloc(w, &w->sg.F0, (size_t)w->S * nf)) ||
+        (rc = dev_alloc(w, &w->sg.F1, (size_t)w->S * nf)) || (rc = dev_alloc(w, &w->sg.C0, 2 * (size_t)w->S)) ||
+        (rc = dev_alloc(w, &w->sg.Y, (size_t)rows * nt)) || (rc = dev_alloc(w, &w->sg.st, (size_t)npx::ST_N * w->S)) ||
+        (rc = dev_alloc(w, &w->sg.theta, std::max(w->J, 1))) || (rc = dev_alloc(w, &w->sg.kappa, w->P)) ||
+        (rc = dev_alloc(w, &w->sg.sens, w->S)) || (rc = dev_alloc(w, &w->sg.status, w->S)) ||
+        (rc = dev_alloc(w, &w->sg.list, w->S)) || (rc = dev_alloc(w, &w->sg.count, 1)) ||
+        (rc = dev_alloc(w, &w->sg.total, 1)))
+        return rc;
+    CUDA_TRY(cudaMemset(w->sg.X, 0, sizeof(float) * (size_t)rows * nf));
+    CUDA_TRY(cudaMemset(w->sg.count, 0, sizeof(int)));
+    CUDA_TRY(cudaEventCreateWithFlags(&w->sg.ev_w, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&w->sg.ev_n, cudaEventDisableTiming));
+    w->sg.rows = rows;
+    return NPX_OK;
+}
+
+}  // namespace
+
 int npx::set_last_error(int code, const char *msg) {
     g_err = msg;
     return code;
@@ -345,6 +393,8 @@ int npx_world_destroy(npx_world *w) {
         clear_graphs(w);
         for (auto &b : w->bufs) cudaFree(b.p);
     }
+    if (w->sg.ev_w) cudaEventDestroy(w->sg.ev_w);
+    if (w->sg.ev_n) cudaEventDestroy(w->sg.ev_n);
     if (w->own_stream) cudaStreamDestroy(w->own_stream);
     delete w;
     return NPX_OK;
@@ -493,12 +543,16 @@ int npx_world_finalize(npx_world *w) {
     }
     w->L = w->link_off[S];
     w->P = w->point_off[S];
+    for (int s = 0; s < S; ++s) {
+        if (w->link_off[s + 1] - w->link_off[s] != w->max_links) w->uniform_links = false;
+        for (int sid : w->flats[s].sensor) w->sensor_bits = std::max(w->sensor_bits, sid + 1);
+    }
     w->J = w->L - S;
     std::vector<npx::LinkDev> links(w->L);
     w->perm.assign(w->P, 0);
     // rest-pose CoG of each scene: the kernels sum mass moments about it (a numerical reference
-    // only; the results do not depend on it beyond rounding)
-    std::vector<float> gref(3 * (size_t)S);
+    // only; the results do not depend on it beyond rounding); CoG of each link's points
+    std::vector<float> gref(3 * (size_t)S), lcog(3 * (size_t)w->L, 0.f);
     std::vector<float4> p0m(w->P);
     std::vector<uint8_t> plink(w->P);
     for (int s = 0; s < S; ++s) {
@@ -522,6 +576,14 @@ int npx_world_finalize(npx_world *w) {
                 for (int k = 0; k < 3; ++k) g[k] += (double)f.m[i] * f.p0[3 * i + k];
             }
             for (int k = 0; k < 3; ++k) gref[3 * s + k] = (float)(g[k] / m);
+            std::vector<double> lm(nl, 0.0), lg(3 * (size_t)nl, 0.0);
+            for (size_t i = 0; i < f.m.size(); ++i) {
+                lm[f.plink[i]] += f.m[i];
+                for (int k = 0; k < 3; ++k) lg[3 * f.plink[i] + k] += (double)f.m[i] * f.p0[3 * i + k];
+            }
+            for (int k = 0; k < nl; ++k)
+                for (int a = 0; a < 3; ++a)
+                    lcog[3 * (size_t)(l0 + k) + a] = lm[k] > 0 ? (float)(lg[3 * k + a] / lm[k]) : 0.f;
         }
         // lowest points first: the step kernel stops scanning once the rest is above ground
         std::vector<int> ord(f.m.size());
@@ -569,7 +631,7 @@ int npx_world_finalize(npx_world *w) {
     }
     W.S = S; W.P = w->P; W.L = w->L; W.J = w->J;
     int *d_lo, *d_po, *d_hmap, *d_order;
-    float *d_gref;
+    float *d_gref, *d_lcog;
     float4 *d_p0m, *d_act;
     uint8_t *d_plink, *d_kappa;
     npx::LinkDev *d_links;
@@ -584,6 +646,7 @@ int npx_world_finalize(npx_world *w) {
         (rc = dev_alloc(w, &d_act, w->J)) || (rc = dev_alloc(w, &d_nu, w->J)) ||
         (rc = dev_alloc(w, &d_st, (size_t)npx::ST_N * S)) || (rc = dev_alloc(w, &d_theta, w->J)) ||
         (rc = dev_alloc(w, &d_kappa, w->P)) || (rc = dev_alloc(w, &d_gref, 3 * (size_t)S)) ||
+        (rc = dev_alloc(w, &d_lcog, 3 * (size_t)w->L)) ||
         (rc = dev_alloc(w, &d_omega, 3 * (size_t)S)) || (rc = dev_alloc(w, &d_sens, S)) ||
         (rc = dev_alloc(w, &d_status, S)) || (rc = dev_alloc(w, &d_queue, 1)) ||
         (rc = dev_alloc(w, &w->d_step, 1)) || (rc = dev_alloc(w, &w->d_stage, 13 * (size_t)S)) ||
@@ -598,12 +661,14 @@ int npx_world_finalize(npx_world *w) {
     CUDA_TRY(cudaMemcpy(d_links, links.data(), sizeof(npx::LinkDev) * w->L, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(d_mu, w->mu.data(), sizeof(float) * S, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(d_gref, gref.data(), sizeof(float) * 3 * S, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_lcog, lcog.data(), sizeof(float) * 3 * w->L, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemset(d_act, 0, sizeof(float4) * std::max(w->J, 1)));
     CUDA_TRY(cudaMemset(d_nu, 0, sizeof(uint32_t) * std::max(w->J, 1)));
     CUDA_TRY(cudaMemset(d_theta, 0, sizeof(float) * std::max(w->J, 1)));
     CUDA_TRY(cudaMemset(w->d_step, 0, sizeof(long long)));
     W.link_off = d_lo; W.point_off = d_po; W.p0m = d_p0m; W.plink = d_plink; W.links = d_links;
     W.gref = d_gref;
+    W.link_cog = d_lcog;
     W.mu = d_mu; W.hmap = d_hmap;
     W.hm_nx = w->desc.hm_nx; W.hm_ny = w->desc.hm_ny;
     W.hm_scale = w->desc.hm_scale; W.hm_ox = w->desc.hm_origin[0]; W.hm_oy = w->desc.hm_origin[1];
@@ -616,7 +681,8 @@ int npx_world_finalize(npx_world *w) {
     W.act = d_act; W.act_nu = d_nu;
     W.st = d_st; W.theta = d_theta; W.kappa = d_kappa; W.omega = d_omega;
     W.sensors = d_sens; W.status = d_status;
-    W.order = d_order; W.max_points = w->max_points; W.max_links = w->max_links;
+    W.order = d_order; W.n_sched = S; W.sched_count = nullptr;
+    W.max_points = w->max_points; W.max_links = w->max_links;
     W.step = w->d_step; W.queue = d_queue;
     w->finalized = true;
     w->flats.clear();
@@ -893,6 +959,91 @@ int npx_world_use_graphs(npx_world *w, int on) {
     if (int rc = check_world(w)) return rc;
     w->graphs = on != 0;
     clear_graphs(w);
+    return NPX_OK;
+}
+
+int npx_surrogate_dims(npx_world *w, int *nf, int *nt) {
+    if (int rc = check_ready(w)) return rc;
+    if (!nf || !nt) return fail(NPX_EINVAL, "null argument");
+    return surrogate_dims(w, nf, nt);
+}
+
+int npx_surrogate_collect(npx_world *w, const npx_surrogate_norm *nrm, int n_steps, float *X, float *T) {
+    if (int rc = check_ready(w)) return rc;
+    if (n_steps < 1 || !X || !T) return fail(NPX_EINVAL, "need n_steps >= 1 and X, T");
+    if (nrm && (!nrm->x_mu || !nrm->x_isd || !nrm->t_mu || !nrm->t_sd)) return fail(NPX_EINVAL, "incomplete norm");
+    CUDA_TRY(cudaSetDevice(w->device));
+    if (int rc = surrogate_buffers(w)) return rc;
+    int nf, nt;
+    surrogate_dims(w, &nf, &nt);
+    const float *xm = nrm ? nrm->x_mu : nullptr, *xi = nrm ? nrm->x_isd : nullptr;
+    const float *tm = nrm ? nrm->t_mu : nullptr, *ts = nrm ? nrm->t_sd : nullptr;
+    const int NL = w->max_links;
+    for (int k = 0; k < n_steps; ++k) {
+        float *Xk = X + (size_t)k * w->S * nf, *Tk = T + (size_t)k * w->S * nt;
+        CUDA_TRY(npx::launch_features(w->W, nf, nt, NL, w->sensor_bits, Xk, w->sg.F0, w->sg.C0, nullptr, nullptr,
+                                      nullptr, xm, xi, nullptr, nullptr, w->stream));
+        CUDA_TRY(npx::launch_step(w->W, w->cfg, 1, w->stream));
+        CUDA_TRY(npx::launch_advance(w->d_step, 1, w->stream));
+        CUDA_TRY(npx::launch_features(w->W, nf, nt, NL, w->sensor_bits, nullptr, w->sg.F1, nullptr, w->sg.C0,
+                                      w->sg.F0, Tk, nullptr, nullptr, tm, ts, w->stream));
+    }
+    w->step += n_steps;
+    w->launches += n_steps;
+    return NPX_OK;
+}
+
+int npx_world_step_surrogate(npx_world *w, npx_mlp *net, const npx_surrogate_norm *nrm, int n_steps,
+                             long long *fallbacks) {
+    if (int rc = check_ready(w)) return rc;
+    if (!net || !nrm || !nrm->x_mu || !nrm->x_isd || !nrm->t_mu || !nrm->t_sd)
+        return fail(NPX_EINVAL, "need a network and its standardisation");
+    if (n_steps < 0) return fail(NPX_EINVAL, "n_steps must be >= 0");
+    CUDA_TRY(cudaSetDevice(w->device));
+    if (int rc = surrogate_buffers(w)) return rc;
+    int nf, nt, nin, nout;
+    surrogate_dims(w, &nf, &nt);
+    npx::mlp_dims(net, &nin, &nout);
+    if (nin != nf || nout != nt) return fail(NPX_EINVAL, "network is %d -> %d, world needs %d -> %d", nin, nout, nf, nt);
+    if (npx::mlp_max_batch(net) < w->sg.rows) return fail(NPX_ERANGE, "network batch capacity below %d rows", w->sg.rows);
+    CUDA_TRY(cudaMemsetAsync(w->sg.total, 0, sizeof(long long), w->stream));
+    cudaStream_t ns = npx::mlp_stream(net);
+    npx::WorldDev Wsub = w->W;            // the plain step on the fallback list only
+    Wsub.order = w->sg.list;
+    Wsub.sched_count = w->sg.count;
+    const size_t S = w->S;
+    for (int k = 0; k < n_steps; ++k) {
+        CUDA_TRY(npx::launch_features(w->W, nf, nt, w->max_links, w->sensor_bits, w->sg.X, w->sg.F0, w->sg.C0, nullptr,
+                                      nullptr, nullptr, nrm->x_mu, nrm->x_isd, nullptr, nullptr, w->stream));
+        if (ns != w->stream) {
+            CUDA_TRY(cudaEventRecord(w->sg.ev_w, w->stream));
+            CUDA_TRY(cudaStreamWaitEvent(ns, w->sg.ev_w, 0));
+        }
+        if (int rc = npx_mlp_forward(net, w->sg.X, w->sg.Y, w->sg.rows)) return rc;
+        if (ns != w->stream) {
+            CUDA_TRY(cudaEventRecord(w->sg.ev_n, ns));
+            CUDA_TRY(cudaStreamWaitEvent(w->stream, w->sg.ev_n, 0));
+        }
+        // keep the state before the step for the scenes that fall back
+        CUDA_TRY(cudaMemcpyAsync(w->sg.st, w->W.st, sizeof(float) * npx::ST_N * S, cudaMemcpyDeviceToDevice, w->stream));
+        if (w->J) CUDA_TRY(cudaMemcpyAsync(w->sg.theta, w->W.theta, sizeof(float) * w->J, cudaMemcpyDeviceToDevice, w->stream));
+        CUDA_TRY(cudaMemcpyAsync(w->sg.kappa, w->W.kappa, w->P, cudaMemcpyDeviceToDevice, w->stream));
+        CUDA_TRY(cudaMemcpyAsync(w->sg.sens, w->W.sensors, sizeof(uint32_t) * S, cudaMemcpyDeviceToDevice, w->stream));
+        CUDA_TRY(cudaMemcpyAsync(w->sg.status, w->W.status, sizeof(uint32_t) * S, cudaMemcpyDeviceToDevice, w->stream));
+        CUDA_TRY(npx::launch_surrogate_apply(w->W, w->sg.Y, nrm->t_mu, nrm->t_sd, w->sg.F0, nf, nt, w->sg.C0, w->stream));
+        CUDA_TRY(npx::launch_contact_probe(w->W, w->sg.list, w->sg.count, w->stream));
+        CUDA_TRY(npx::launch_restore(w->W, w->sg.list, w->sg.count, w->sg.st, w->sg.theta, w->sg.kappa, w->sg.sens,
+                                     w->sg.status, w->stream));
+        CUDA_TRY(npx::launch_step(Wsub, w->cfg, 1, w->stream));
+        CUDA_TRY(npx::launch_accumulate(w->sg.total, w->sg.count, w->stream));
+        CUDA_TRY(npx::launch_advance(w->d_step, 1, w->stream));
+    }
+    w->step += n_steps;
+    w->launches += n_steps;
+    if (fallbacks) {
+        CUDA_TRY(cudaMemcpyAsync(fallbacks, w->sg.total, sizeof(long long), cudaMemcpyDeviceToHost, w->stream));
+        CUDA_TRY(cudaStreamSynchronize(w->stream));
+    }
     return NPX_OK;
 }
 

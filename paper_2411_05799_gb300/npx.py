@@ -139,6 +139,9 @@ _SIGS = {
     "npx_mlp_forward": [P, P, P, I],
     "npx_mlp_backward": [P, P, P, I, P],
     "npx_mlp_adam_step": [P],
+    "npx_surrogate_dims": [P, P, P],
+    "npx_surrogate_collect": [P, P, I, P, P],
+    "npx_world_step_surrogate": [P, P, P, I, P],
 }
 
 _lib = None
@@ -437,3 +440,27 @@ class MLP:
 
     def adam_step(self):
         _check(_lib.npx_mlp_adam_step(self._h))
+
+
+class SurrogateNorm(C.Structure):
+    """npx_surrogate_norm: device pointers to the standardisation vectors."""
+    _fields_ = [("x_mu", C.c_void_p), ("x_isd", C.c_void_p), ("t_mu", C.c_void_p),
+                ("t_sd", C.c_void_p)]
+
+
+def surrogate_dims(world: "World"):
+    nf, nt = C.c_int(), C.c_int()
+    _check(_lib.npx_surrogate_dims(world._h, C.byref(nf), C.byref(nt)))
+    return nf.value, nt.value
+
+
+def surrogate_collect(world: "World", n_steps, X_ptr, T_ptr, norm: SurrogateNorm = None):
+    _check(_lib.npx_surrogate_collect(world._h, C.byref(norm) if norm else None, int(n_steps),
+                                      X_ptr, T_ptr))
+
+
+def world_step_surrogate(world: "World", net: "MLP", norm: SurrogateNorm, n_steps) -> int:
+    fb = C.c_longlong()
+    _check(_lib.npx_world_step_surrogate(world._h, net._h, C.byref(norm), int(n_steps),
+                                         C.byref(fb)))
+    return fb.value

@@ -1,0 +1,115 @@
+"""The learned surrogate: its features against a numpy computation from the FP64 oracle's state,
+training on simulator transitions, and rollouts with the contact-change fallback measured
+against the oracle (what the trained network gains over an untrained one)."""
+import math
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+
+from oracle.oracle import Oracle, quat_matrix
+from paper_2411_05799_gb300 import npx, scenes
+from tests.parity import to_gpu, quat_angle
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _features_ref(o: Oracle, b, s):
+    """Features of scene s from the oracle's state, written out in numpy."""
+    l0, l1 = b.link_off[s], b.link_off[s + 1]
+    p0, p1 = b.point_off[s], b.point_off[s + 1]
+    Q, T = o.link_frames(s)
+    g, Ib, M = o.mass_props(s)
+    R = quat_matrix(o.q[s])
+    om = o.omega()[s]
+    c, v = o.c[s], o.v[s]
+    f = []
+    for k in range(l1 - l0):
+        sel = b.plink[p0:p1] == k
+        m = b.m[p0:p1][sel].astype(np.float64)
+        pc = (m[:, None] * b.p0[p0:p1][sel].astype(np.float64)).sum(0) / m.sum()
+        r = R @ (Q[k] @ pc + T[k] - g)
+        xq = Rotation.from_matrix(Q[k]).as_quat()          # (x, y, z, w)
+        ql = np.array([xq[3], *xq[:3]]) * (1 if xq[3] >= 0 else -1)
+        w1, x1, y1, z1 = o.q[s]
+        w2, x2, y2, z2 = ql
+        qq = [w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+              w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2]
+        f += [r[0], r[1], c[2] + r[2], *qq, *(v + np.cross(om, r)), *om]
+    j0 = b.joint_off[s]
+    for j in range(l1 - l0 - 1):
+        th = o.theta[j0 + j]
+        if o.n % b.joint_update_steps == 0:
+            th = min(max(o.target(s, j, o.n), b.lo[l0 + j + 1]), b.hi[l0 + j + 1])
+        f.append(th)
+    f += [float((int(o.sensors[s]) >> k) & 1) for k in range(6)]
+    return np.array(f)
+
+
+@pytest.mark.parametrize("n0", [37, 160])
+def test_features_match_oracle_state(n0):
+    b = scenes.hexapod_batch(8, seed_key=31)
+    o = Oracle(b)
+    o.step(n0)
+    w = npx.World.from_batch(b)
+    to_gpu(w, o)
+    nf, nt = npx.surrogate_dims(w)
+    assert (nf, nt) == (271, 247)
+    X = torch.zeros(8, nf, device="cuda")
+    T = torch.zeros(8, nt, device="cuda")
+    npx.surrogate_collect(w, 1, X.data_ptr(), T.data_ptr())
+    torch.cuda.synchronize()
+    got = X.cpu().numpy()
+    for s in range(8):
+        ref = _features_ref(o, b, s)
+        np.testing.assert_allclose(got[s], ref, rtol=2e-5, atol=2e-6)
+    # targets: the change of the link part over the plain step, against the oracle's next state
+    o2 = Oracle(b)
+    o2.copy_state_from(o)
+    o2.step(1)
+    tg = T.cpu().numpy()
+    for s in range(8):
+        before = _features_ref(o, b, s)[:nt]
+        after = _features_ref(o2, b, s)[:nt]
+        after[0] += o2.c[s, 0] - o.c[s, 0]
+        after[1] += o2.c[s, 1] - o.c[s, 1]
+        np.testing.assert_allclose(tg[s], after - before, rtol=1e-3, atol=2e-5)
+
+
+def _rollout_error(b, sur, state_world_src, n_steps, o_ref):
+    """Surrogate rollout of n_steps from the oracle's state; errors of CoG and orientation."""
+    w = npx.World.from_batch(b, stream=torch.cuda.current_stream().cuda_stream)
+    to_gpu(w, state_world_src)
+    fb = npx.world_step_surrogate(w, sur.net, sur.norm, n_steps)
+    r = w.read()
+    dc = np.linalg.norm(r["cog"] - o_ref.c, axis=1)
+    da = quat_angle(r["quat"], o_ref.q)
+    return dc, da, fb, r
+
+
+def test_training_and_50_step_rollout():
+    from paper_2411_05799_gb300 import surrogate
+    train_b = scenes.hexapod_batch(1024, seed_key=40)
+    res = surrogate.train(train_b, n_transitions=2_000_000, minibatch=8192, steps_per_chunk=16)
+    sur = res["surrogate"]
+    losses = [l for _, l in res["losses"]]
+    assert losses[-1] < 0.25 * losses[0], losses
+    # held-out scenes, 50 steps from a mid-gait state, against the FP64 oracle
+    test_b = scenes.hexapod_batch(256, seed_key=41)
+    o = Oracle(test_b, threads=8)
+    o.step(1000, threads=8)
+    o50 = Oracle(test_b, threads=8)
+    o50.copy_state_from(o)
+    o50.step(50, threads=8)
+    dc, da, fb, r = _rollout_error(test_b, sur, o, 50, o50)
+    assert (r["status"] == 0).all()
+    assert 0 <= fb < 256 * 50
+    untrained = surrogate.Surrogate(sur.n_in, sur.n_out, sur.net_max_batch if hasattr(sur, "net_max_batch") else 8192,
+                                    torch.cuda.current_stream().cuda_stream, seed=99)
+    untrained.set_norm(*[t.cpu().numpy() for t in sur.norm_t[:1]], 1.0 / sur.norm_t[1].cpu().numpy(),
+                       sur.norm_t[2].cpu().numpy(), sur.norm_t[3].cpu().numpy(), "cuda")
+    dcu, dau, fbu, ru = _rollout_error(test_b, untrained, o, 50, o50)
+    # what training gains: the trained network's 50-step CoG error is far below an untrained one's
+    assert np.median(dc) < 0.2 * np.median(dcu), (np.median(dc), np.median(dcu))
+    assert np.median(dc) < 0.02
