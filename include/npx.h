@@ -140,7 +140,8 @@ int npx_state_set(npx_world *w, const float *origin, const float *quat, const fl
 /* Overwrite the whole dynamic state: CoG [S*3], orientation [S*4], CoG velocity [S*3], world
  * angular momentum about the CoG [S*3], joint angles [J], contact flags of the previous step per
  * mass point [P] (NULL clears them; 1 = in contact), and the global step counter n (which fixes
- * the joint-update phase n % K and the actuator phase).  Status words are cleared. */
+ * the joint-update phase n % K and the actuator phase).  Status words are cleared; the contact
+ * sensors are recomputed from contact_prev. */
 int npx_state_write(npx_world *w, const float *cog, const float *quat, const float *vel,
                     const float *angmom, const float *theta, const uint8_t *contact_prev,
                     int64_t step);

@@ -86,6 +86,8 @@ int npx_mlp_backward(npx_mlp *net, const float *x, const float *t, int M, float 
 int npx_mlp_grads_get(npx_mlp *net, float *grads, size_t n);
 /* One Adam step with the last gradients. */
 int npx_mlp_adam_step(npx_mlp *net);
+/* Learning rate of the following Adam steps (a schedule sets it between steps); lr > 0. */
+int npx_mlp_set_lr(npx_mlp *net, float lr);
 
 /* --- the surrogate step -----------------------------------------------------------------
  * For worlds whose scenes all have the same number of links NL (NL - 1 joints) and NS contact-
@@ -102,13 +104,15 @@ typedef struct {
 } npx_surrogate_norm;
 
 int npx_surrogate_dims(npx_world *w, int *n_features, int *n_targets);
-/* Advance the world n_steps plain steps, writing every step's features X and targets T
- * (DEVICE, rows = step * n_scenes + scene, standardised when norm is given). */
+/* Advance the world with the plain step until n_steps steps have been recorded, writing each
+ * recorded step's features X and targets T (DEVICE, rows = step * n_scenes + scene, standardised
+ * when norm is given).  Joint-update steps (n % K == 0) are stepped but not recorded: the
+ * surrogate never takes them. */
 int npx_surrogate_collect(npx_world *w, const npx_surrogate_norm *norm, int n_steps, float *X,
                           float *T);
-/* Advance the world n_steps surrogate steps: the network predicts every scene's next state from
- * its features; scenes whose contact sensors change during a step redo that step with the plain
- * step (the fallback).  *fallbacks (host, may be NULL) receives the number of scene-steps that
+/* Advance the world n_steps steps with the surrogate: the network predicts every scene's next
+ * state from its features; scenes whose contact sensors change during a step redo that step with
+ * the plain step (the fallback), and joint-update steps (n % K == 0) are plain for every scene.  *fallbacks (host, may be NULL) receives the number of scene-steps that
  * fell back.  The network must take n_features inputs, give n_targets outputs, and hold at least
  * n_scenes rounded up to 128 rows. */
 int npx_world_step_surrogate(npx_world *w, npx_mlp *net, const npx_surrogate_norm *norm,

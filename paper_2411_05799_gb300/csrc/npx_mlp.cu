@@ -400,4 +400,11 @@ int npx_mlp_adam_step(npx_mlp *n) {
     return NPX_OK;
 }
 
+int npx_mlp_set_lr(npx_mlp *n, float lr) {
+    if (!n) return npx::set_last_error(NPX_EINVAL, "null network");
+    if (!(lr > 0.f) || !std::isfinite(lr)) return npx::set_last_error(NPX_EINVAL, "learning rate must be positive");
+    n->d.lr = lr;
+    return NPX_OK;
+}
+
 }  // extern "C"

@@ -782,6 +782,13 @@ __global__ void __launch_bounds__(128) refresh_kernel(WorldDev W, int sbytes) {
     __syncwarp();
     Shape sh;
     shape_update<32>(W, s, p0, np, l0, nl, th, fr, pts, lane, sh);
+    uint32_t sens = 0;   // contact sensors of the written contact flags
+    for (int i = lane; i < np; i += 32) {
+        if (!W.kappa[p0 + i]) continue;
+        const int sid = W.links[l0 + W.plink[p0 + i]].sensor;
+        if (sid >= 0 && sid < 32) sens |= 1u << sid;
+    }
+    sens = gor<32>(sens);
     if (lane == 0) {
         const int S = W.S;
         const float q[4] = {W.st[ST_QW * S + s], W.st[ST_QX * S + s], W.st[ST_QY * S + s],
@@ -791,6 +798,7 @@ __global__ void __launch_bounds__(128) refresh_kernel(WorldDev W, int sbytes) {
         quat_mat(q, R);
         world_sym(R, sh.Ii, L, om);
         W.omega[s] = om[0]; W.omega[S + s] = om[1]; W.omega[2 * S + s] = om[2];
+        W.sensors[s] = sens;
     }
 }
 

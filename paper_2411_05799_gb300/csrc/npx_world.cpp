@@ -979,7 +979,15 @@ int npx_surrogate_collect(npx_world *w, const npx_surrogate_norm *nrm, int n_ste
     const float *xm = nrm ? nrm->x_mu : nullptr, *xi = nrm ? nrm->x_isd : nullptr;
     const float *tm = nrm ? nrm->t_mu : nullptr, *ts = nrm ? nrm->t_sd : nullptr;
     const int NL = w->max_links;
-    for (int k = 0; k < n_steps; ++k) {
+    const bool actuated = w->act_mode != NPX_ACT_HOLD;
+    for (int k = 0; k < n_steps;) {
+        if (actuated && w->step % w->desc.joint_update_steps == 0) {   // joint updates stay plain
+            CUDA_TRY(npx::launch_step(w->W, w->cfg, 1, w->stream));
+            CUDA_TRY(npx::launch_advance(w->d_step, 1, w->stream));
+            w->step += 1;
+            w->launches += 1;
+            continue;
+        }
         float *Xk = X + (size_t)k * w->S * nf, *Tk = T + (size_t)k * w->S * nt;
         CUDA_TRY(npx::launch_features(w->W, nf, nt, NL, w->sensor_bits, Xk, w->sg.F0, w->sg.C0, nullptr, nullptr,
                                       nullptr, xm, xi, nullptr, nullptr, w->stream));
@@ -987,9 +995,10 @@ int npx_surrogate_collect(npx_world *w, const npx_surrogate_norm *nrm, int n_ste
         CUDA_TRY(npx::launch_advance(w->d_step, 1, w->stream));
         CUDA_TRY(npx::launch_features(w->W, nf, nt, NL, w->sensor_bits, nullptr, w->sg.F1, nullptr, w->sg.C0,
                                       w->sg.F0, Tk, nullptr, nullptr, tm, ts, w->stream));
+        w->step += 1;
+        w->launches += 1;
+        ++k;
     }
-    w->step += n_steps;
-    w->launches += n_steps;
     return NPX_OK;
 }
 
@@ -1012,7 +1021,14 @@ int npx_world_step_surrogate(npx_world *w, npx_mlp *net, const npx_surrogate_nor
     Wsub.order = w->sg.list;
     Wsub.sched_count = w->sg.count;
     const size_t S = w->S;
+    const bool actuated = w->act_mode != NPX_ACT_HOLD;
     for (int k = 0; k < n_steps; ++k) {
+        if (actuated && (w->step + k) % w->desc.joint_update_steps == 0) {
+            // joint-update steps (Sec. III-B) are taken by the plain step for every scene
+            CUDA_TRY(npx::launch_step(w->W, w->cfg, 1, w->stream));
+            CUDA_TRY(npx::launch_advance(w->d_step, 1, w->stream));
+            continue;
+        }
         CUDA_TRY(npx::launch_features(w->W, nf, nt, w->max_links, w->sensor_bits, w->sg.X, w->sg.F0, w->sg.C0, nullptr,
                                       nullptr, nullptr, nrm->x_mu, nrm->x_isd, nullptr, nullptr, w->stream));
         if (ns != w->stream) {

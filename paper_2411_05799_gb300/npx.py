@@ -139,6 +139,7 @@ _SIGS = {
     "npx_mlp_forward": [P, P, P, I],
     "npx_mlp_backward": [P, P, P, I, P],
     "npx_mlp_adam_step": [P],
+    "npx_mlp_set_lr": [P, F],
     "npx_surrogate_dims": [P, P, P],
     "npx_surrogate_collect": [P, P, I, P, P],
     "npx_world_step_surrogate": [P, P, P, I, P],
@@ -440,6 +441,9 @@ class MLP:
 
     def adam_step(self):
         _check(_lib.npx_mlp_adam_step(self._h))
+
+    def set_lr(self, lr: float):
+        _check(_lib.npx_mlp_set_lr(self._h, float(lr)))
 
 
 class SurrogateNorm(C.Structure):

@@ -10,6 +10,16 @@ from paper_2411_05799_gb300 import npx
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
+
+@pytest.fixture(autouse=True)
+def _own_stream():
+    """Each test runs on a torch stream of its own: on the legacy default stream (handle 0) the
+    library would create a stream of its own that torch's reads do not wait for."""
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        yield
+    s.synchronize()
+
 SIZES = [271, 512, 512, 512, 512, 247]
 
 

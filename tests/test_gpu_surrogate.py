@@ -15,6 +15,16 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
+@pytest.fixture(autouse=True)
+def _own_stream():
+    """Each test runs on a torch stream of its own: on the legacy default stream (handle 0) the
+    library would create a stream of its own that torch's reads do not wait for."""
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        yield
+    s.synchronize()
+
+
 def _features_ref(o: Oracle, b, s):
     """Features of scene s from the oracle's state, written out in numpy."""
     l0, l1 = b.link_off[s], b.link_off[s + 1]
@@ -47,7 +57,7 @@ def _features_ref(o: Oracle, b, s):
     return np.array(f)
 
 
-@pytest.mark.parametrize("n0", [37, 160])
+@pytest.mark.parametrize("n0", [37, 161])
 def test_features_match_oracle_state(n0):
     b = scenes.hexapod_batch(8, seed_key=31)
     o = Oracle(b)
@@ -72,8 +82,8 @@ def test_features_match_oracle_state(n0):
     for s in range(8):
         before = _features_ref(o, b, s)[:nt]
         after = _features_ref(o2, b, s)[:nt]
-        after[0] += o2.c[s, 0] - o.c[s, 0]
-        after[1] += o2.c[s, 1] - o.c[s, 1]
+        after[0::13][:19] += o2.c[s, 0] - o.c[s, 0]     # every link relative to the first CoG
+        after[1::13][:19] += o2.c[s, 1] - o.c[s, 1]
         np.testing.assert_allclose(tg[s], after - before, rtol=1e-3, atol=2e-5)
 
 
@@ -90,11 +100,15 @@ def _rollout_error(b, sur, state_world_src, n_steps, o_ref):
 
 def test_training_and_50_step_rollout():
     from paper_2411_05799_gb300 import surrogate
-    train_b = scenes.hexapod_batch(1024, seed_key=40)
-    res = surrogate.train(train_b, n_transitions=2_000_000, minibatch=8192, steps_per_chunk=16)
+    train_b = scenes.hexapod_batch(4096, seed_key=40)
+    res = surrogate.train(train_b, n_transitions=20_000_000, minibatch=8192, steps_per_chunk=16,
+                          passes=2, lr=1e-3)
     sur = res["surrogate"]
-    losses = [l for _, l in res["losses"]]
-    assert losses[-1] < 0.25 * losses[0], losses
+    u = res["unexplained"]
+    # held-out loss (rows the network has not been trained on) against the zero predictor's
+    assert np.isfinite(u).all()
+    assert u[-5:].mean() < 0.25, u[-5:]
+    assert u[-5:].mean() < 0.1 * u[0], (u[0], u[-5:])
     # held-out scenes, 50 steps from a mid-gait state, against the FP64 oracle
     test_b = scenes.hexapod_batch(256, seed_key=41)
     o = Oracle(test_b, threads=8)
@@ -105,11 +119,8 @@ def test_training_and_50_step_rollout():
     dc, da, fb, r = _rollout_error(test_b, sur, o, 50, o50)
     assert (r["status"] == 0).all()
     assert 0 <= fb < 256 * 50
-    untrained = surrogate.Surrogate(sur.n_in, sur.n_out, sur.net_max_batch if hasattr(sur, "net_max_batch") else 8192,
-                                    torch.cuda.current_stream().cuda_stream, seed=99)
-    untrained.set_norm(*[t.cpu().numpy() for t in sur.norm_t[:1]], 1.0 / sur.norm_t[1].cpu().numpy(),
-                       sur.norm_t[2].cpu().numpy(), sur.norm_t[3].cpu().numpy(), "cuda")
-    dcu, dau, fbu, ru = _rollout_error(test_b, untrained, o, 50, o50)
+    dcu, dau, fbu, ru = _rollout_error(test_b, sur.untrained_copy(), o, 50, o50)
     # what training gains: the trained network's 50-step CoG error is far below an untrained one's
     assert np.median(dc) < 0.2 * np.median(dcu), (np.median(dc), np.median(dcu))
-    assert np.median(dc) < 0.02
+    assert np.median(dc) < 5e-3, np.median(dc)
+    assert np.median(da) < 0.2 * np.median(dau), (np.median(da), np.median(dau))
