@@ -31,7 +31,9 @@ extern "C" {
  *   out  [M x ldo] BF16 row-major;  outT [N x ldt] BF16 (the transpose of y);
  *   outf [M x ldf] FP32 row-major (for NPX_EPI_F32: split s at outf + s * split_stride);
  *   zsave [M x ldz] BF16 pre-activations (NPX_EPI_BIAS_GELU); zin [M x ldzi] BF16 (DGELU);
- *   bias [N] FP32 or NULL. */
+ *   bias [N] FP32 or NULL.
+ * bias, out, zsave, zin and outf start on 16-byte boundaries and their row strides (ld * element
+ * size, and split_stride * 4) are multiples of 16 bytes; outT is 2-byte aligned. */
 typedef struct {
     int mode;
     const float *bias;

@@ -2,13 +2,17 @@
 // for the learned surrogate: C[M x N] = A[M x K] . B[N x K]^T, both operands K-major (row-major
 // with K contiguous), FP32 accumulation in tensor memory, fused epilogues.
 //
-// One CTA computes a 128 x BN tile.  Thread 0 streams 128 x 64 and BN x 64 operand tiles with TMA
-// (128-byte swizzle, the layout the UMMA shared-memory descriptors describe) through a STAGES-deep
-// ring of shared-memory buffers and issues one tcgen05.mma (M = 128, N = BN, K = 16) per 32-byte
-// step of each 64-wide K block; tcgen05.commit on an mbarrier hands each buffer back to the TMA.
-// The four warps then read the accumulator out of tensor memory (warp w owns rows 32w .. 32w+31)
-// and apply the epilogue.  Every wait is bounded: a stalled barrier sets an error flag, the
-// kernel drains the copies it started, frees its tensor memory and returns.
+// A persistent, warp-specialised kernel: each CTA (one per SM) walks tiles of 128 x BN (and, for
+// split K, one K range) in a static round-robin.  Warp 0 streams 128 x 64 and BN x 64 operand
+// tiles with TMA (128-byte swizzle, the layout the UMMA shared-memory descriptors describe)
+// through a STAGES-deep ring of shared-memory buffers; warp 1 issues one tcgen05.mma (M = 128,
+// N = BN, K = 16) per 32-byte step of each 64-wide K block into one of two accumulators in tensor
+// memory (2 x BN columns) and hands each ring buffer back with tcgen05.commit; sixteen epilogue warps
+// read the other accumulator out (warp w owns TMEM lanes 32 (w % 4) .. + 31 and a quarter of
+// the columns), apply the epilogue and release it, so a tile's epilogue overlaps the next tile's
+// MMAs.  Every wait is bounded and also gives up once another role has failed: the failing role
+// sets an error flag, the kernel drains the copies it started, waits for its MMAs, frees its
+// tensor memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -20,7 +24,7 @@
 namespace npx {
 namespace gemm {
 
-constexpr int BM = 128, BK = 64, STAGES = 4, THREADS = 128;
+constexpr int BM = 128, BK = 64, STAGES = 4, EPI_WARPS = 16, THREADS = 32 * (2 + EPI_WARPS);
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s per barrier wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -54,13 +58,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *b, uint32_t parity) {
     return ok != 0;
 }
 
-// bounded wait: false after WAIT_NS without the phase completing
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
+// bounded wait: false after WAIT_NS without the phase completing, or (when abort is given) as
+// soon as another role has raised the abort flag
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, const volatile int *abort = nullptr) {
     if (mbar_try_wait(b, parity)) return true;
     const unsigned long long t0 = global_ns();
-    while (!mbar_try_wait(b, parity))
+    while (!mbar_try_wait(b, parity)) {
+        if (abort && *abort) return false;
         if (global_ns() - t0 > WAIT_NS) return false;
+    }
     return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
@@ -119,15 +130,90 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad(float z) {
-    return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.3989422804014327f * expf(-0.5f * z * z);
+// Standard normal CDF Phi(z) = (1 + erf(z / sqrt 2)) / 2, with erf from the rational
+// approximation of Abramowitz & Stegun, Handbook of Mathematical Functions, formula 7.1.26
+// (|error| <= 1.5e-7, far below the BF16 rounding of the outputs).  e = exp(-z^2 / 2), which the
+// approximation needs anyway, is also the Gaussian factor of GELU'.
+__device__ __forceinline__ float norm_cdf(float z, float &e) {
+    const float x = fabsf(z) * 0.70710678118654752f;
+    const float t = __fdividef(1.f, fmaf(0.3275911f, x, 1.f));
+    e = __expf(-x * x);
+    const float p = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
+                             0.254829592f);
+    const float tail = 0.5f * p * e;   // (1 - erf(x)) / 2
+    return z >= 0.f ? 1.f - tail : tail;
+}
+__device__ __forceinline__ float gelu(float z) {
+    float e;
+    return z * norm_cdf(z, e);
+}
+__device__ __forceinline__ float gelu_grad(float z) {   // Phi(z) + z phi(z)
+    float e;
+    const float c = norm_cdf(z, e);
+    return fmaf(z * 0.3989422804014327f, e, c);
+}
+
+__device__ __forceinline__ void store_bf16x16(__nv_bfloat16 *o, const float (&v)[16]) {
+    uint4 u[2];
+    uint32_t *w = reinterpret_cast<uint32_t *>(u);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        w[i] = *reinterpret_cast<const uint32_t *>(&h);
+    }
+    reinterpret_cast<uint4 *>(o)[0] = u[0];
+    reinterpret_cast<uint4 *>(o)[1] = u[1];
+}
+
+// the epilogue of 16 accumulator values of one row: v = acc[row, col .. col + 15]
+__device__ __forceinline__ void epilogue16(const npx_gemm_epilogue &ep, float (&v)[16], int row, int col, int split) {
+    if (ep.mode == NPX_EPI_F32) {
+        float4 *o = reinterpret_cast<float4 *>(ep.outf + (size_t)split * ep.split_stride + (size_t)row * ep.ldf + col);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        return;
+    }
+    if (ep.bias) {
+        const float4 *bb = reinterpret_cast<const float4 *>(ep.bias + col);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float4 b = bb[i];
+            v[4 * i] += b.x; v[4 * i + 1] += b.y; v[4 * i + 2] += b.z; v[4 * i + 3] += b.w;
+        }
+    }
+    if (ep.mode == NPX_EPI_BIAS_GELU) {
+        if (ep.zsave) store_bf16x16(static_cast<__nv_bfloat16 *>(ep.zsave) + (size_t)row * ep.ldz + col, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = gelu(v[i]);
+    } else if (ep.mode == NPX_EPI_DGELU) {
+        const uint4 *zp = reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(ep.zin) + (size_t)row * ep.ldzi + col);
+        uint4 u[2] = {zp[0], zp[1]};
+        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(u);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float2 z = __bfloat1622float2(h[i]);
+            v[2 * i] *= gelu_grad(z.x);
+            v[2 * i + 1] *= gelu_grad(z.y);
+        }
+    }
+    if (ep.outf) {
+        float4 *o = reinterpret_cast<float4 *>(ep.outf + (size_t)row * ep.ldf + col);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    }
+    if (ep.out) store_bf16x16(static_cast<__nv_bfloat16 *>(ep.out) + (size_t)row * ep.ldo + col, v);
+    if (ep.outT) {
+        // lanes hold consecutive rows: each store instruction writes 64 contiguous bytes
+        __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(ep.outT) + (size_t)col * ep.ldt + row;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) o[(size_t)i * ep.ldt] = __float2bfloat16_rn(v[i]);
+    }
 }
 
 template <int BN>
 __global__ void __launch_bounds__(THREADS, 1)
 gemm_tn_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int M, int N,
-               int k_per_split, npx_gemm_epilogue ep, int *err) {
+               int k_per_split, int splits, npx_gemm_epilogue ep, int *err) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
@@ -135,26 +221,37 @@ gemm_tn_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ C
     uint8_t *sB = smem + STAGES * A_BYTES;
     uint64_t *full = reinterpret_cast<uint64_t *>(sB + STAGES * B_BYTES);
     uint64_t *empty = full + STAGES;
-    uint64_t *done = empty + STAGES;
+    uint64_t *tfull = empty + STAGES;     // accumulator b ready for the epilogue
+    uint64_t *tempty = tfull + 2;         // accumulator b drained by the epilogue
+    uint64_t *done = tempty + 2;          // every MMA of this CTA complete
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    int *issued = reinterpret_cast<int *>(tmem_slot + 2);      // k-blocks whose copies were started
+    int *consumed = reinterpret_cast<int *>(tmem_slot + 3);    // k-blocks whose copies were waited for
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-    const int kbeg = blockIdx.z * k_per_split;
+    const int tiles_m = M / BM, tiles_n = N / BN, total = tiles_m * tiles_n * splits;
     const int nk = k_per_split / BK;
 
-    if (warp == 0) {   // whole warp: allocate BN accumulator columns of tensor memory
+    if (warp == 1) {   // whole warp: allocate two accumulators of BN columns
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"((uint32_t)BN)
+                     "r"((uint32_t)(2 * BN))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (threadIdx.x == 32) {
+    if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], EPI_WARPS);
+        }
         mbar_init(done, 1);
+        *abort = 0;
+        *issued = 0;
+        *consumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc_fence_before();
@@ -162,101 +259,112 @@ gemm_tn_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ C
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    __shared__ int s_ok;
-    if (threadIdx.x == 0) {
-        const uint32_t idesc = idesc_bf16(BM, BN);
-        bool ok = true;
-        int issued = 0;   // k-blocks whose TMA was started
-        auto issue = [&](int kb) {
-            const int s = kb % STAGES;
-            mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-            tma_load_2d(sA + s * A_BYTES, &ta, kbeg + kb * BK, m0, &full[s]);
-            tma_load_2d(sB + s * B_BYTES, &tb, kbeg + kb * BK, n0, &full[s]);
-            ++issued;
-        };
-        for (int kb = 0; kb < nk && kb < STAGES; ++kb) issue(kb);
-        int consumed = 0;
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % STAGES;
-            const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
-            if (!mbar_wait(&full[s], ph)) { ok = false; break; }
-            ++consumed;
-            tc_fence_after();
-            const uint64_t da = sdesc_k_sw128(smem_u32(sA + s * A_BYTES));
-            const uint64_t db = sdesc_k_sw128(smem_u32(sB + s * B_BYTES));
-#pragma unroll
-            for (int k = 0; k < BK / 16; ++k)   // 32 bytes along K per instruction
-                umma_bf16(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), idesc, (kb | k) != 0);
-            umma_commit(&empty[s]);
-            if (kb + STAGES < nk) {
-                if (!mbar_wait(&empty[s], ph)) { ok = false; break; }
-                issue(kb + STAGES);
+    if (warp == 0) {
+        // ---- TMA producer
+        if (lane == 0) {
+            int g = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                const int split = t % splits, rest = t / splits;
+                const int n0 = (rest % tiles_n) * BN, m0 = (rest / tiles_n) * BM;
+                const int kbeg = split * k_per_split;
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const int s = g % STAGES;
+                    if (g >= STAGES && !mbar_wait(&empty[s], (uint32_t)(((g / STAGES) - 1) & 1), abort)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+                    tma_load_2d(sA + s * A_BYTES, &ta, kbeg + kb * BK, m0, &full[s]);
+                    tma_load_2d(sB + s * B_BYTES, &tb, kbeg + kb * BK, n0, &full[s]);
+                    *issued = g + 1;
+                }
+            }
+            if (!ok) {
+                *abort = 1;
+                atomicExch(err, 1);
             }
         }
-        umma_commit(done);
-        if (!ok) {
-            // drain the copies still in flight before the CTA's shared memory goes away
-            for (int kb = consumed; kb < issued; ++kb) mbar_wait(&full[kb % STAGES], (uint32_t)((kb / STAGES) & 1));
-            atomicExch(err, 1);
+    } else if (warp == 1) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(BM, BN);
+            int g = 0, tl = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++tl) {
+                const int b = tl & 1;
+                if (tl >= 2 && !mbar_wait(&tempty[b], (uint32_t)(((tl >> 1) - 1) & 1), abort)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * BN);
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const int s = g % STAGES;
+                    if (!mbar_wait(&full[s], (uint32_t)((g / STAGES) & 1), abort)) {
+                        ok = false;
+                        break;
+                    }
+                    *consumed = g + 1;
+                    tc_fence_after();
+                    const uint64_t da = sdesc_k_sw128(smem_u32(sA + s * A_BYTES));
+                    const uint64_t db = sdesc_k_sw128(smem_u32(sB + s * B_BYTES));
+#pragma unroll
+                    for (int k = 0; k < BK / 16; ++k)   // 32 bytes along K per instruction
+                        umma_bf16(d, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), idesc, (kb | k) != 0);
+                    umma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                umma_commit(&tfull[b]);
+            }
+            umma_commit(done);
+            if (!ok) {
+                *abort = 1;
+                atomicExch(err, 2);
+            }
         }
-        s_ok = ok ? 1 : 0;
+    } else {
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 and column quarter (w - 2) / 4
+        const int q = warp & 3, part = (warp - 2) >> 2;
+        constexpr int COLS = BN / (EPI_WARPS / 4);
+        int tl = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x, ++tl) {
+            const int b = tl & 1;
+            const int split = t % splits, rest = t / splits;
+            const int n0 = (rest % tiles_n) * BN, m0 = (rest / tiles_n) * BM;
+            if (!mbar_wait(&tfull[b], (uint32_t)((tl >> 1) & 1), abort)) {
+                if (lane == 0) {
+                    *abort = 1;
+                    atomicExch(err, 3);
+                }
+                break;
+            }
+            tc_fence_after();
+            const int row = m0 + q * 32 + lane;
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN);
+#pragma unroll 1
+            for (int c0 = part * COLS; c0 < (part + 1) * COLS; c0 += 16) {
+                float v[16];
+                tmem_ld16(taddr + (uint32_t)c0, v);
+                epilogue16(ep, v, row, n0 + c0, split);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+        }
     }
     __syncthreads();
-    const bool fin = mbar_wait(done, 0);
-    tc_fence_after();
-    if (!fin) atomicExch(err, 2);
-    if (fin && s_ok) {
-        const int row = m0 + warp * 32 + lane;
-        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            float v[16];
-            tmem_ld16(trow + (uint32_t)c0, v);
-            const int col = n0 + c0;
-            if (ep.mode == NPX_EPI_F32) {
-                float *o = ep.outf + (size_t)blockIdx.z * ep.split_stride + (size_t)row * ep.ldf + col;
-#pragma unroll
-                for (int i = 0; i < 16; i += 4) *reinterpret_cast<float4 *>(o + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-                continue;
-            }
-            if (ep.bias) {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] += ep.bias[col + i];
-            }
-            if (ep.mode == NPX_EPI_BIAS_GELU) {
-                if (ep.zsave) {
-                    __nv_bfloat16 *z = static_cast<__nv_bfloat16 *>(ep.zsave) + (size_t)row * ep.ldz + col;
-#pragma unroll
-                    for (int i = 0; i < 16; i += 2) *reinterpret_cast<__nv_bfloat162 *>(z + i) = __floats2bfloat162_rn(v[i], v[i + 1]);
-                }
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] = gelu(v[i]);
-            } else if (ep.mode == NPX_EPI_DGELU) {
-                const __nv_bfloat16 *z = static_cast<const __nv_bfloat16 *>(ep.zin) + (size_t)row * ep.ldzi + col;
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] *= gelu_grad(__bfloat162float(z[i]));
-            }
-            if (ep.outf) {
-                float *o = ep.outf + (size_t)row * ep.ldf + col;
-#pragma unroll
-                for (int i = 0; i < 16; i += 4) *reinterpret_cast<float4 *>(o + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-            }
-            if (ep.out) {
-                __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(ep.out) + (size_t)row * ep.ldo + col;
-#pragma unroll
-                for (int i = 0; i < 16; i += 2) *reinterpret_cast<__nv_bfloat162 *>(o + i) = __floats2bfloat162_rn(v[i], v[i + 1]);
-            }
-            if (ep.outT) {
-#pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    static_cast<__nv_bfloat16 *>(ep.outT)[(size_t)(col + i) * ep.ldt + row] = __float2bfloat16_rn(v[i]);
-            }
-        }
+    if (threadIdx.x == 0) {
+        // after a failure: let the copies still in flight land before the shared memory goes away
+        for (int g = *consumed; g < *issued; ++g) mbar_wait(&full[g % STAGES], (uint32_t)((g / STAGES) & 1));
+        // every MMA issued by this CTA has completed before its tensor memory is freed
+        if (!mbar_wait(done, 0)) atomicExch(err, 4);
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN)) : "memory");
     }
 }
 
@@ -293,7 +401,18 @@ static bool make_map(CUtensorMap *m, const void *ptr, int rows, int cols, int bo
 
 template <int BN>
 static size_t smem_bytes() {
-    return 1024 + (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + (2 * STAGES + 1) * 8 + 16;
+    return 1024 + (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + (2 * STAGES + 5) * 8 + 16;
+}
+
+static int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+            n = 1;
+    }
+    return n;
 }
 
 template <int BN>
@@ -302,8 +421,9 @@ static cudaError_t launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, i
     const size_t smem = smem_bytes<BN>();
     cudaError_t e = cudaFuncSetAttribute(gemm_tn_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid(M / BM, N / BN, splits);
-    gemm_tn_kernel<BN><<<grid, THREADS, smem, st>>>(ta, tb, M, N, K / splits, ep, err);
+    const int tiles = (M / BM) * (N / BN) * splits;
+    const int grid = tiles < sm_count() ? tiles : sm_count();
+    gemm_tn_kernel<BN><<<grid, THREADS, smem, st>>>(ta, tb, M, N, K / splits, splits, ep, err);
     return cudaGetLastError();
 }
 
@@ -325,6 +445,15 @@ extern "C" int npx_gemm_bf16(const void *A, const void *B, int M, int N, int K, 
     if (ep->mode == NPX_EPI_F32 ? !ep->outf : (!ep->out && !ep->outT && !ep->outf))
         return npx::set_last_error(NPX_EINVAL, "npx_gemm_bf16: no output");
     if (ep->mode == NPX_EPI_DGELU && !ep->zin) return npx::set_last_error(NPX_EINVAL, "npx_gemm_bf16: DGELU needs zin");
+    // the epilogue stores 16-byte vectors: 16-byte aligned rows of the row-major outputs
+    auto rows16 = [](const void *p, long long ld, int elem) {
+        return !p || ((reinterpret_cast<uintptr_t>(p) & 15) == 0 && (ld * elem) % 16 == 0);
+    };
+    if (!rows16(ep->bias, 0, 4) || !rows16(ep->out, ep->ldo, 2) || !rows16(ep->zsave, ep->ldz, 2) ||
+        !rows16(ep->zin, ep->ldzi, 2) || !rows16(ep->outf, ep->ldf, 4) ||
+        (ep->outf && splits > 1 && (ep->split_stride * 4) % 16 != 0) ||
+        (ep->outT && (reinterpret_cast<uintptr_t>(ep->outT) & 1)))
+        return npx::set_last_error(NPX_EINVAL, "npx_gemm_bf16: outputs, bias and zin need 16-byte aligned rows");
     if (splits > 1 && ep->mode != NPX_EPI_F32) return npx::set_last_error(NPX_EINVAL, "npx_gemm_bf16: split K needs the F32 epilogue");
     CUtensorMap ta, tb;
     if (!make_map(&ta, A, M, K, BM) || !make_map(&tb, B, N, K, BN))

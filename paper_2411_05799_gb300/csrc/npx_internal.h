@@ -1,6 +1,7 @@
 // npx_internal.h -- device data layout shared by the host library (npx_world.cpp) and the
 // kernels (npx_step.cu).  Not part of the public C-ABI.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -67,17 +68,41 @@ cudaError_t launch_advance(long long *d_step, int n, cudaStream_t st);
 cudaError_t launch_init(const WorldDev &W, const float *d_origin, const float *d_quat,
                         const float *d_vel, const float *d_omega, cudaStream_t st);
 cudaError_t launch_refresh(const WorldDev &W, cudaStream_t st);
-cudaError_t launch_features(const WorldDev &W, int nf, int nt, int nl, int ns, float *X, float *Xraw,
-                            float *cxy_out, const float *cxy_ref, const float *prev, float *T,
-                            const float *x_mu, const float *x_isd, const float *t_mu,
-                            const float *t_sd, cudaStream_t st);
-cudaError_t launch_surrogate_apply(const WorldDev &W, const float *Y, const float *t_mu,
-                                   const float *t_sd, const float *F0, int nf, int nt,
-                                   const float *cxy0, cudaStream_t st);
-cudaError_t launch_contact_probe(const WorldDev &W, int *list, int *count, cudaStream_t st);
-cudaError_t launch_restore(const WorldDev &W, const int *list, const int *count, const float *st_b,
-                           const float *theta_b, const uint8_t *kappa_b, const uint32_t *sens_b,
-                           const uint32_t *status_b, cudaStream_t st);
+// ---- learned surrogate
+// Per-scene posed shape (a function of the joint angles), rebuilt whenever they change.
+struct SurCache {
+    float4 *lk;       // [S * nl * 2]: per link, its orientation quaternion (w, x, y, z) in the body
+                      //   frame, then its CoG offset from the robot CoG in the body frame (w = 0)
+    float *inert;     // [12 * S]: body-frame inertia (xx yy zz xy xz yz), then its inverse
+    float4 *spt;      // [S * nsp]: points of contact-sensor links, offset from the robot CoG in
+                      //   the body frame; w = the sensor bit
+    int *nsp_s;       // [S] sensor points of each scene
+    int nsp, nl;      // capacity per scene; links per scene
+};
+
+struct SurrogateIO {
+    int nf, nt, nl, ns;      // features, targets, links, sensor bits
+    float *X;                // [S x nf] features (standardised when x_mu is set) or NULL
+    void *Xb;                // [S x ldb] BF16 standardised features, zero-padded, or NULL
+    int ldb;
+    float *Xraw;             // [S x nf] raw features or NULL
+    float *cxy_out;          // [S x 2] robot CoG (x, y) or NULL
+    const float *cxy_ref;    // [S x 2] horizontal reference or NULL (the robot CoG)
+    const float *prev;       // [S x nf] raw features of the previous state (delta target) or NULL
+    float *T;                // [S x nt] delta target (standardised when t_mu is set) or NULL
+    const float *x_mu, *x_isd, *t_mu, *t_sd;
+};
+
+cudaError_t launch_sensor_points(const WorldDev &W, int *count, int *max_count, cudaStream_t st);
+cudaError_t launch_shape_cache(const WorldDev &W, const SurCache &C, cudaStream_t st);
+cudaError_t launch_features(const WorldDev &W, const SurCache &C, const SurrogateIO &io, cudaStream_t st);
+// the surrogate's next state from the network output Y [S x ldy] (standardised deltas), kept
+// where the contact sensors do not change; the other scenes go to list / count.  nx [16 * S],
+// applied [S] and sens_new [S] are scratch.
+cudaError_t launch_surrogate_update(const WorldDev &W, const SurCache &C, const float *Y, int ldy,
+                                    const float *t_mu, const float *t_sd, float *nx, uint8_t *applied,
+                                    uint32_t *sens_new, int *list, int *count, cudaStream_t st);
+cudaError_t launch_kappa_refresh(const WorldDev &W, const int *list, const int *count, cudaStream_t st);
 cudaError_t launch_accumulate(long long *total, int *count, cudaStream_t st);
 // records msg as the thread's npx_last_error() text and returns code
 int set_last_error(int code, const char *msg);
@@ -91,4 +116,9 @@ namespace npx {
 cudaStream_t mlp_stream(const npx_mlp *net);
 int mlp_max_batch(const npx_mlp *net);
 void mlp_dims(const npx_mlp *net, int *n_in, int *n_out);
+// the network's packed BF16 input rows [max_batch x ld] (zero-padded columns), a forward pass of
+// M rows from them, and the FP32 output rows [M x ld] it leaves (padded columns)
+__nv_bfloat16 *mlp_input(npx_mlp *net, int *ld);
+int mlp_forward_packed(npx_mlp *net, int M);
+const float *mlp_output(const npx_mlp *net, int *ld);
 }  // namespace npx

@@ -25,39 +25,81 @@ namespace {
 
 int pad_to(int n, int m) { return (n + m - 1) / m * m; }
 
-__global__ void pack_input_kernel(const float *__restrict__ x, int M, int n_in, int in_p, bf16 *X,
-                                  bf16 *XT) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)M * in_p) return;
-    const int m = (int)(i / in_p), k = (int)(i % in_p);
-    const bf16 v = __float2bfloat16_rn(k < n_in ? x[(size_t)m * n_in + k] : 0.f);
-    X[i] = v;
-    if (XT) XT[(size_t)k * M + m] = v;
-}
+// Tiles of 32 x 32 elements go through shared memory so that both the row-major output and its
+// transpose are written in full lines: block (32, 8), grid (cols / 32, rows / 32).
 
-// dY = 2 (y - t) / M on real outputs, 0 on the padding; loss += sum (y - t)^2 / M
-__global__ void loss_grad_kernel(const float *__restrict__ Y, const float *__restrict__ T, int M,
-                                 int n_out, int out_p, bf16 *dY, bf16 *dYT, float *loss) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    float sq = 0.f;
-    if (i < (long long)M * out_p) {
-        const int m = (int)(i / out_p), j = (int)(i % out_p);
-        const float d = j < n_out ? Y[i] - T[(size_t)m * n_out + j] : 0.f;
-        sq = d * d / (float)M;
-        const bf16 g = __float2bfloat16_rn(2.f * d / (float)M);
-        dY[i] = g;
-        dYT[(size_t)j * M + m] = g;
+// X = bf16(x) zero-padded to in_p columns, and optionally X^T [in_p x M]
+__global__ void __launch_bounds__(256) pack_input_kernel(const float *__restrict__ x, int M, int n_in, int in_p,
+                                                         bf16 *X, bf16 *XT) {
+    __shared__ bf16 tile[32][33];
+    const int k0 = blockIdx.x * 32, m0 = blockIdx.y * 32, tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + ty + 8 * i, k = k0 + tx;
+        const bf16 v = __float2bfloat16_rn(k < n_in ? x[(size_t)m * n_in + k] : 0.f);
+        X[(size_t)m * in_p + k] = v;
+        tile[ty + 8 * i][tx] = v;
     }
-    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-    if ((threadIdx.x & 31) == 0 && sq != 0.f) atomicAdd(loss, sq);
+    if (!XT) return;   // block-uniform
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) XT[(size_t)(k0 + ty + 8 * i) * M + m0 + tx] = tile[tx][ty + 8 * i];
 }
 
-__global__ void colsum_kernel(const bf16 *__restrict__ G, int M, int N, float *out) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
+// dY = 2 (y - t) / M on real outputs, 0 on the padding, and dY^T; loss += sum (y - t)^2 / M
+__global__ void __launch_bounds__(256) loss_grad_kernel(const float *__restrict__ Y, const float *__restrict__ T,
+                                                        int M, int n_out, int out_p, bf16 *dY, bf16 *dYT,
+                                                        float *loss) {
+    __shared__ bf16 tile[32][33];
+    __shared__ float red[8];
+    const int j0 = blockIdx.x * 32, m0 = blockIdx.y * 32, tx = threadIdx.x, ty = threadIdx.y;
+    const float inv = 1.f / (float)M;
+    float sq = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + ty + 8 * i, j = j0 + tx;
+        const float d = j < n_out ? Y[(size_t)m * out_p + j] - T[(size_t)m * n_out + j] : 0.f;
+        sq += d * d * inv;
+        const bf16 g = __float2bfloat16_rn(2.f * d * inv);
+        dY[(size_t)m * out_p + j] = g;
+        tile[ty + 8 * i][tx] = g;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) dYT[(size_t)(j0 + ty + 8 * i) * M + m0 + tx] = tile[tx][ty + 8 * i];
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if (tx == 0) red[ty] = sq;
+    __syncthreads();
+    if (ty == 0 && tx == 0) {
+        float t = 0.f;
+        for (int i = 0; i < 8; ++i) t += red[i];
+        if (t != 0.f) atomicAdd(loss, t);
+    }
+}
+
+// out[n] = sum over the M entries of row n of GT [N x M] (the bias gradient: column sums of the
+// layer's output gradient, read from its transpose so that every load is a full line)
+__global__ void __launch_bounds__(256) rowsum_kernel(const bf16 *__restrict__ GT, int M, float *out) {
+    __shared__ float red[8];
+    const bf16 *row = GT + (size_t)blockIdx.x * M;
     float s = 0.f;
-    for (int m = 0; m < M; ++m) s += __bfloat162float(G[(size_t)m * N + n]);
-    out[n] = s;
+    for (int m = threadIdx.x * 8; m < M; m += 256 * 8) {
+        const uint4 u = *reinterpret_cast<const uint4 *>(row + m);
+        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 f = __bfloat1622float2(h[k]);
+            s += f.x + f.y;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int i = 0; i < 8; ++i) t += red[i];
+        out[blockIdx.x] = t;
+    }
 }
 
 __global__ void splitk_reduce_kernel(const float *__restrict__ part, int splits, long long n, float *out) {
@@ -169,11 +211,8 @@ int check(npx_mlp *n, int M) {
         if (r_) return r_;          \
     } while (0)
 
-int forward_impl(npx_mlp *n, const float *x, int M, bool train) {
-    const int in_p = n->din[0];
-    pack_input_kernel<<<blocks_for((long long)M * in_p), 256, 0, n->stream>>>(x, M, n->d.n_in, in_p, n->X0,
-                                                                            train ? n->X0T : nullptr);
-    CU(cudaGetLastError());
+// the layers, from the packed BF16 input X0
+int forward_layers(npx_mlp *n, int M, bool train) {
     const bf16 *A = n->X0;
     for (int l = 0; l < n->L - 1; ++l) {
         npx_gemm_epilogue e = epi(NPX_EPI_BIAS_GELU);
@@ -198,6 +237,14 @@ int forward_impl(npx_mlp *n, const float *x, int M, bool train) {
     return NPX_OK;
 }
 
+int forward_impl(npx_mlp *n, const float *x, int M, bool train) {
+    const int in_p = n->din[0];
+    pack_input_kernel<<<dim3(in_p / 32, M / 32), dim3(32, 8), 0, n->stream>>>(x, M, n->d.n_in, in_p, n->X0,
+                                                                             train ? n->X0T : nullptr);
+    CU(cudaGetLastError());
+    return forward_layers(n, M, train);
+}
+
 }  // namespace
 
 cudaStream_t npx::mlp_stream(const npx_mlp *n) { return n->stream; }
@@ -205,6 +252,18 @@ int npx::mlp_max_batch(const npx_mlp *n) { return n->d.max_batch; }
 void npx::mlp_dims(const npx_mlp *n, int *n_in, int *n_out) {
     *n_in = n->d.n_in;
     *n_out = n->d.n_out;
+}
+__nv_bfloat16 *npx::mlp_input(npx_mlp *n, int *ld) {
+    *ld = n->din[0];
+    return n->X0;
+}
+int npx::mlp_forward_packed(npx_mlp *n, int M) {
+    RC(check(n, M));
+    return forward_layers(n, M, false);
+}
+const float *npx::mlp_output(const npx_mlp *n, int *ld) {
+    *ld = n->dout[n->L - 1];
+    return n->Y;
 }
 
 extern "C" {
@@ -347,8 +406,8 @@ int npx_mlp_backward(npx_mlp *n, const float *x, const float *t, int M, float *l
     RC(forward_impl(n, x, M, true));
     const int L = n->L, H = n->d.n_hidden, out_p = n->dout[L - 1];
     CU(cudaMemsetAsync(loss, 0, sizeof(float), n->stream));
-    loss_grad_kernel<<<blocks_for((long long)M * out_p), 256, 0, n->stream>>>(n->Y, t, M, n->d.n_out, out_p, n->dY,
-                                                                           n->dYT, loss);
+    loss_grad_kernel<<<dim3(out_p / 32, M / 32), dim3(32, 8), 0, n->stream>>>(n->Y, t, M, n->d.n_out, out_p, n->dY,
+                                                                              n->dYT, loss);
     CU(cudaGetLastError());
     const bf16 *G = n->dY, *GT = n->dYT;     // gradient of the current layer's output
     for (int l = L - 1; l >= 0; --l) {
@@ -363,7 +422,7 @@ int npx_mlp_backward(npx_mlp *n, const float *x, const float *t, int M, float *l
         RC(gemm(n, GT, XprevT, No, Ni, M, splits, e));
         splitk_reduce_kernel<<<blocks_for((long long)No * Ni), 256, 0, n->stream>>>(n->part, splits, (long long)No * Ni,
                                                                                    n->dW[l]);
-        colsum_kernel<<<blocks_for(No), 256, 0, n->stream>>>(G, M, No, n->db[l]);
+        rowsum_kernel<<<No, 256, 0, n->stream>>>(GT, M, n->db[l]);
         CU(cudaGetLastError());
         if (l > 0) {
             // dZ_prev = (G W) * gelu'(Z_prev): A = G [M x No], B = W^T [Ni x No]

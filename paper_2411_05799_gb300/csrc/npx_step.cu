@@ -24,6 +24,8 @@
 //   friction (Sec. III-C, Eqs. 1-6): least squares over the points in contact in both steps,
 //     solved in centred form (identical to the paper's 3x3 normal equations), a3 applied as a
 //     rotation by asin(a3) about the contact centroid, dynamic part capped by mu * FN * dt.
+#include <algorithm>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -831,11 +833,14 @@ __global__ void __launch_bounds__(32) points_kernel(WorldDev W, int s, float *ou
 }
 
 // ------------------------------------------------------------------------ learned surrogate
-// Scene features for the surrogate network (one warp per scene): per link, the CoG of its points
-// (horizontally relative to ref, or to the robot CoG), its orientation, the velocity of its CoG
-// and the angular velocity (13 numbers; the robot is one rigid body, so every link shares it);
+// The surrogate sees a scene through per-link features: per link, the CoG of its points
+// (horizontally relative to a reference, z absolute), its orientation, the velocity of its CoG
+// and the angular velocity (13 numbers; the robot is one rigid body, so every link shares it),
 // then the joint angles after this step's joint update and the contact-sensor bits of the last
-// step.  Optionally standardised ((x - mu) * isd), optionally also the next-step delta target.
+// step.  The link part is a function of the root state and the posed shape; the shape depends on
+// the joint angles only, which change on joint-update steps (always taken by the plain step), so
+// it is computed once per change into a per-scene cache (shape_cache_kernel) and the per-step
+// kernels do no forward kinematics.
 
 // unit quaternion of a rotation matrix (row-major), sign chosen with w >= 0
 __device__ __forceinline__ void quat_from_mat(const float *Q, float *q) {
@@ -868,18 +873,62 @@ __device__ __forceinline__ float angle_after(const WorldDev &W, int l0, int j0, 
     return th[j];
 }
 
-struct SurrogateIO {
-    int nf, nt, nl, ns;
-    float *X;            // [S x nf] features (standardised when x_mu is set)
-    float *Xraw;         // [S x nf] raw features or NULL
-    float *cxy_out;      // [S x 2] robot CoG (x, y) or NULL
-    const float *cxy_ref;// [S x 2] horizontal reference or NULL (the robot CoG)
-    const float *prev;   // [S x nf] raw features of the previous state (delta target) or NULL
-    float *T;            // [S x nt] delta target (standardised when t_mu is set)
-    const float *x_mu, *x_isd, *t_mu, *t_sd;
+__device__ __forceinline__ Sym cached_sym(const float *a, int S, int s) {
+    return Sym{a[0 * S + s], a[1 * S + s], a[2 * S + s], a[3 * S + s], a[4 * S + s], a[5 * S + s]};
+}
+
+struct RootState {
+    float c[3], q[4], v[3], L[3];
 };
 
-__global__ void __launch_bounds__(128) features_kernel(WorldDev W, SurrogateIO io, int sbytes) {
+__device__ __forceinline__ RootState load_root(const WorldDev &W, int s) {
+    const int S = W.S;
+    RootState r;
+    r.c[0] = W.st[ST_CX * S + s]; r.c[1] = W.st[ST_CY * S + s]; r.c[2] = W.st[ST_CZ * S + s];
+    r.q[0] = W.st[ST_QW * S + s]; r.q[1] = W.st[ST_QX * S + s]; r.q[2] = W.st[ST_QY * S + s];
+    r.q[3] = W.st[ST_QZ * S + s];
+    r.v[0] = W.st[ST_VX * S + s]; r.v[1] = W.st[ST_VY * S + s]; r.v[2] = W.st[ST_VZ * S + s];
+    r.L[0] = W.st[ST_LX * S + s]; r.L[1] = W.st[ST_LY * S + s]; r.L[2] = W.st[ST_LZ * S + s];
+    return r;
+}
+
+// The 13 features of one link: lq = link orientation in the body frame, lp = link CoG offset from
+// the robot CoG in the body frame; R = root rotation, om = angular velocity.
+__device__ __forceinline__ void link_features(const RootState &x, const float R[9], const float om[3],
+                                              float4 lq, float4 lp, float rx, float ry, float f[13]) {
+    const float ps[3] = {lp.x, lp.y, lp.z};
+    const float ql[4] = {lq.x, lq.y, lq.z, lq.w};
+    float r[3], qq[4];
+    mat_vec(R, ps, r);
+    quat_mul(x.q, ql, qq);
+    f[0] = x.c[0] + r[0] - rx; f[1] = x.c[1] + r[1] - ry; f[2] = x.c[2] + r[2];
+    f[3] = qq[0]; f[4] = qq[1]; f[5] = qq[2]; f[6] = qq[3];
+    f[7] = x.v[0] + om[1] * r[2] - om[2] * r[1];
+    f[8] = x.v[1] + om[2] * r[0] - om[0] * r[2];
+    f[9] = x.v[2] + om[0] * r[1] - om[1] * r[0];
+    f[10] = om[0]; f[11] = om[1]; f[12] = om[2];
+}
+
+// Number of points on contact-sensor links, per scene, and the largest (one warp per scene).
+__global__ void __launch_bounds__(128) sensor_points_kernel(WorldDev W, int *count, int *max_count) {
+    const int lane = threadIdx.x & 31;
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (s >= W.S) return;   // warp-uniform
+    const int p0 = W.point_off[s], np = W.point_off[s + 1] - p0, l0 = W.link_off[s];
+    int c = 0;
+    for (int i = lane; i < np; i += 32) {
+        const int sid = W.links[l0 + W.plink[p0 + i]].sensor;
+        c += (sid >= 0 && sid < 32) ? 1 : 0;
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL_MASK, c, o);
+    if (lane == 0) {
+        count[s] = c;
+        atomicMax(max_count, c);
+    }
+}
+
+// The posed shape of every scene at its current joint angles, into the cache (one warp per scene).
+__global__ void __launch_bounds__(128) shape_cache_kernel(WorldDev W, SurCache C, int sbytes) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int s = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -894,165 +943,263 @@ __global__ void __launch_bounds__(128) features_kernel(WorldDev W, SurrogateIO i
     __syncwarp();
     Shape sh;
     shape_update<32>(W, s, p0, np, l0, nl, th, fr, pts, lane, sh);
-    const int S = W.S;
-    const float c[3] = {W.st[ST_CX * S + s], W.st[ST_CY * S + s], W.st[ST_CZ * S + s]};
-    const float q[4] = {W.st[ST_QW * S + s], W.st[ST_QX * S + s], W.st[ST_QY * S + s], W.st[ST_QZ * S + s]};
-    const float v[3] = {W.st[ST_VX * S + s], W.st[ST_VY * S + s], W.st[ST_VZ * S + s]};
-    const float L[3] = {W.st[ST_LX * S + s], W.st[ST_LY * S + s], W.st[ST_LZ * S + s]};
-    float R[9], om[3];
-    quat_mat(q, R);
-    world_sym(R, sh.Ii, L, om);
-    const float rx = io.cxy_ref ? io.cxy_ref[2 * s] : c[0], ry = io.cxy_ref ? io.cxy_ref[2 * s + 1] : c[1];
-    const long long n = *W.step;
-    auto emit = [&](int i, float raw) {
-        const size_t o = (size_t)s * io.nf + i;
-        if (io.Xraw) io.Xraw[o] = raw;
-        if (io.X) io.X[o] = io.x_mu ? (raw - io.x_mu[i]) * io.x_isd[i] : raw;
-        if (io.T && i < io.nt) {
-            const float d = raw - io.prev[o];
-            io.T[(size_t)s * io.nt + i] = io.t_mu ? (d - io.t_mu[i]) / io.t_sd[i] : d;
-        }
-    };
-    for (int l = lane; l < io.nl; l += 32) {
-        float f[13];
+    for (int l = lane; l < C.nl; l += 32) {
+        float4 lq = make_float4(1.f, 0.f, 0.f, 0.f), lp = make_float4(0.f, 0.f, 0.f, 0.f);
         if (l < nl) {
             const float *F = fr + 12 * l;
             const float pc[3] = {W.link_cog[3 * (l0 + l)], W.link_cog[3 * (l0 + l) + 1], W.link_cog[3 * (l0 + l) + 2]};
-            float ps[3], r[3], ql[4], qq[4];
-            ps[0] = F[0] * pc[0] + F[1] * pc[1] + F[2] * pc[2] + F[9] - sh.g[0];
-            ps[1] = F[3] * pc[0] + F[4] * pc[1] + F[5] * pc[2] + F[10] - sh.g[1];
-            ps[2] = F[6] * pc[0] + F[7] * pc[1] + F[8] * pc[2] + F[11] - sh.g[2];
-            mat_vec(R, ps, r);
+            float ql[4];
             quat_from_mat(F, ql);
-            quat_mul(q, ql, qq);
-            f[0] = c[0] + r[0] - rx; f[1] = c[1] + r[1] - ry; f[2] = c[2] + r[2];
-            f[3] = qq[0]; f[4] = qq[1]; f[5] = qq[2]; f[6] = qq[3];
-            f[7] = v[0] + om[1] * r[2] - om[2] * r[1];
-            f[8] = v[1] + om[2] * r[0] - om[0] * r[2];
-            f[9] = v[2] + om[0] * r[1] - om[1] * r[0];
-            f[10] = om[0]; f[11] = om[1]; f[12] = om[2];
-        } else {
-            for (int i = 0; i < 13; ++i) f[i] = 0.f;
+            lq = make_float4(ql[0], ql[1], ql[2], ql[3]);
+            lp.x = F[0] * pc[0] + F[1] * pc[1] + F[2] * pc[2] + F[9] - sh.g[0];
+            lp.y = F[3] * pc[0] + F[4] * pc[1] + F[5] * pc[2] + F[10] - sh.g[1];
+            lp.z = F[6] * pc[0] + F[7] * pc[1] + F[8] * pc[2] + F[11] - sh.g[2];
         }
-        for (int i = 0; i < 13; ++i) emit(13 * l + i, f[i]);
+        C.lk[((size_t)s * C.nl + l) * 2] = lq;
+        C.lk[((size_t)s * C.nl + l) * 2 + 1] = lp;
     }
-    for (int j = lane; j < io.nl - 1; j += 32) emit(13 * io.nl + j, j < nl - 1 ? angle_after(W, l0, j0, j, th, n) : 0.f);
-    const uint32_t sens = W.sensors[s];
-    for (int k = lane; k < io.ns; k += 32) emit(13 * io.nl + io.nl - 1 + k, (float)((sens >> k) & 1u));
-    if (lane == 0 && io.cxy_out) { io.cxy_out[2 * s] = c[0]; io.cxy_out[2 * s + 1] = c[1]; }
+    if (lane == 0) {
+        const int S = W.S;
+        const float v[12] = {sh.Ib.xx, sh.Ib.yy, sh.Ib.zz, sh.Ib.xy, sh.Ib.xz, sh.Ib.yz,
+                             sh.Ii.xx, sh.Ii.yy, sh.Ii.zz, sh.Ii.xy, sh.Ii.xz, sh.Ii.yz};
+        for (int k = 0; k < 12; ++k) C.inert[k * S + s] = v[k];
+    }
+    // the points of sensor links, compacted in stored order
+    int base = 0;
+    for (int i0 = 0; i0 < np; i0 += 32) {
+        const int i = i0 + lane;
+        int sid = -1;
+        if (i < np) sid = W.links[l0 + W.plink[p0 + i]].sensor;
+        const bool is = sid >= 0 && sid < 32;
+        const unsigned m = __ballot_sync(FULL_MASK, is);
+        if (is) {
+            const int k = base + __popc(m & ((1u << lane) - 1u));
+            const float4 r = pts[i];
+            if (k < C.nsp) C.spt[(size_t)s * C.nsp + k] = make_float4(r.x, r.y, r.z, (float)sid);
+        }
+        base += __popc(m);
+    }
 }
 
-// Surrogate update of one scene: joint angles of this step's update, then the root state from
-// the torso's predicted next state (position, orientation, CoG velocity, angular velocity).
-__global__ void __launch_bounds__(128) surrogate_apply_kernel(WorldDev W, const float *Y, const float *t_mu,
-                                                              const float *t_sd, const float *F0, int nf, int nt,
-                                                              const float *cxy0, int sbytes) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int s = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (s >= W.S) return;   // warp-uniform
-    unsigned char *slot = smem + (size_t)warp * sbytes;
-    float4 *pts = reinterpret_cast<float4 *>(slot);
-    float *fr = reinterpret_cast<float *>(slot + 16 * W.max_points);
-    float *th = fr + 12 * W.max_links;
-    const int p0 = W.point_off[s], np = W.point_off[s + 1] - p0;
-    const int l0 = W.link_off[s], nl = W.link_off[s + 1] - l0, j0 = l0 - s;
-    const long long n = *W.step;
+// Features of every scene, one thread per (scene, link): the link's 13 features, the angle of the
+// joint that drives the link and the sensor bits k = link (mod links).  Outputs: FP32 (standardised
+// when x_mu is set), raw, BF16 standardised into the network's input rows (whose padding columns
+// are zero and are not written), and the delta target against the raw features of the previous
+// state.
+__global__ void __launch_bounds__(256) features_kernel(WorldDev W, SurCache C, SurrogateIO io, int spb) {
+    extern __shared__ float rows[];   // [spb x nf] raw features of the block's scenes
+    const int tid = threadIdx.x, S = W.S;
+    const int s0 = blockIdx.x * spb, ns = min(spb, S - s0);
+    if (tid < ns * io.nl) {
+        const int sl = tid / io.nl, l = tid % io.nl, s = s0 + sl;
+        float *row = rows + (size_t)sl * io.nf;
+        const RootState x = load_root(W, s);
+        float R[9], om[3];
+        quat_mat(x.q, R);
+        world_sym(R, cached_sym(C.inert + 6 * S, S, s), x.L, om);
+        const float rx = io.cxy_ref ? io.cxy_ref[2 * s] : x.c[0], ry = io.cxy_ref ? io.cxy_ref[2 * s + 1] : x.c[1];
+        const int l0 = W.link_off[s], nl = W.link_off[s + 1] - l0, j0 = l0 - s;
+        float f[13];
+        if (l < nl) {
+            link_features(x, R, om, C.lk[((size_t)s * C.nl + l) * 2], C.lk[((size_t)s * C.nl + l) * 2 + 1], rx, ry, f);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 13; ++k) f[k] = 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 13; ++k) row[13 * l + k] = f[k];
+        if (l >= 1) {   // joint l - 1 drives link l
+            const int j = l - 1;
+            row[13 * io.nl + j] = j < nl - 1 ? angle_after(W, l0, j0, j, W.theta + j0, *W.step) : 0.f;
+        }
+        const uint32_t sens = W.sensors[s];
+        for (int k = l; k < io.ns; k += io.nl) row[14 * io.nl - 1 + k] = (float)((sens >> k) & 1u);
+        if (l == 0 && io.cxy_out) { io.cxy_out[2 * s] = x.c[0]; io.cxy_out[2 * s + 1] = x.c[1]; }
+    }
+    __syncthreads();
+    // the block's rows are contiguous in every output: write them out in full lines
+    if (io.X || io.Xraw || io.T) {
+        for (int e = tid; e < ns * io.nf; e += blockDim.x) {
+            const int sl = e / io.nf, col = e - sl * io.nf, s = s0 + sl;
+            const float raw = rows[e];
+            const size_t o = (size_t)s * io.nf + col;
+            if (io.Xraw) io.Xraw[o] = raw;
+            if (io.X) io.X[o] = io.x_mu ? (raw - io.x_mu[col]) * io.x_isd[col] : raw;
+            if (io.T && col < io.nt) {
+                const float d = raw - io.prev[o];
+                io.T[(size_t)s * io.nt + col] = io.t_mu ? (d - io.t_mu[col]) / io.t_sd[col] : d;
+            }
+        }
+    }
+    if (io.Xb) {   // 8 BF16 (16 bytes) per store; the columns past nf are padding and stay zero
+        const int chunks = (io.nf + 7) >> 3;
+        for (int e = tid; e < ns * chunks; e += blockDim.x) {
+            const int sl = e / chunks, c0 = (e - sl * chunks) * 8;
+            uint32_t w[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float v[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int col = c0 + 2 * k + h;
+                    const float raw = col < io.nf ? rows[(size_t)sl * io.nf + col] : 0.f;
+                    v[h] = col < io.nf && io.x_mu ? (raw - io.x_mu[col]) * io.x_isd[col] : raw;
+                }
+                const __nv_bfloat162 hv = __floats2bfloat162_rn(v[0], v[1]);
+                w[k] = *reinterpret_cast<const uint32_t *>(&hv);
+            }
+            *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(io.Xb) + (size_t)(s0 + sl) * io.ldb + c0) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+// Surrogate update, one thread per scene: the root state from the torso's predicted next state
+// (position, orientation, CoG velocity, angular velocity) into the candidate buffer nx
+// [NX_N * S]; applied[s] says whether scene s has a candidate (frozen scenes and non-finite
+// predictions have none; the latter freeze the scene).
+enum { NX_CX = 0, NX_CY, NX_CZ, NX_QW, NX_QX, NX_QY, NX_QZ, NX_VX, NX_VY, NX_VZ, NX_LX, NX_LY, NX_LZ,
+       NX_WX, NX_WY, NX_WZ, NX_N };
+
+__global__ void __launch_bounds__(256) surrogate_apply_kernel(WorldDev W, SurCache C, const float *Y, int ldy,
+                                                              const float *t_mu, const float *t_sd, float *nx,
+                                                              uint8_t *applied) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= W.S) return;
+    const int S = W.S;
     const uint32_t status = W.status[s];
-    for (int j = lane; j < nl - 1; j += 32) th[j] = W.theta[j0 + j];
-    __syncwarp();
-    for (int j = lane; j < nl - 1; j += 32) {
-        const float a = status ? th[j] : angle_after(W, l0, j0, j, th, n);
-        th[j] = a;
-        W.theta[j0 + j] = a;
-    }
-    __syncwarp();
-    Shape sh;
-    shape_update<32>(W, s, p0, np, l0, nl, th, fr, pts, lane, sh);
-    if (lane != 0 || status) return;
+    if (status) { applied[s] = 0; return; }
+    const RootState x = load_root(W, s);
+    float R[9], om[3];
+    quat_mat(x.q, R);
+    world_sym(R, cached_sym(C.inert + 6 * S, S, s), x.L, om);
+    const float4 lq = C.lk[(size_t)s * C.nl * 2], lp = C.lk[(size_t)s * C.nl * 2 + 1];
     float f[13];
-    for (int i = 0; i < 13; ++i) f[i] = F0[(size_t)s * nf + i] + Y[(size_t)s * nt + i] * t_sd[i] + t_mu[i];
-    float qn[4] = {f[3], f[4], f[5], f[6]};
-    const float inv = rsqrtf(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
-    qn[0] *= inv; qn[1] *= inv; qn[2] *= inv; qn[3] *= inv;
-    float R[9];
-    quat_mat(qn, R);
-    // root link frame = shape frame: torso CoG offset from the robot CoG is link_cog - g
-    const float ps[3] = {W.link_cog[3 * l0] - sh.g[0], W.link_cog[3 * l0 + 1] - sh.g[1], W.link_cog[3 * l0 + 2] - sh.g[2]};
+    link_features(x, R, om, lq, lp, x.c[0], x.c[1], f);
+    const float *y = Y + (size_t)s * ldy;
+#pragma unroll
+    for (int i = 0; i < 13; ++i) f[i] += y[i] * t_sd[i] + t_mu[i];
+    // torso orientation -> root orientation (the torso frame relative to the body frame is lq)
+    float qt[4] = {f[3], f[4], f[5], f[6]};
+    const float inv = rsqrtf(qt[0] * qt[0] + qt[1] * qt[1] + qt[2] * qt[2] + qt[3] * qt[3]);
+    qt[0] *= inv; qt[1] *= inv; qt[2] *= inv; qt[3] *= inv;
+    const float lqc[4] = {lq.x, -lq.y, -lq.z, -lq.w};
+    float qn[4], Rn[9];
+    quat_mul(qt, lqc, qn);
+    quat_mat(qn, Rn);
+    const float ps[3] = {lp.x, lp.y, lp.z};
     float d[3], L[3];
-    mat_vec(R, ps, d);
-    const float om[3] = {f[10], f[11], f[12]};
-    const float c[3] = {cxy0[2 * s] + f[0] - d[0], cxy0[2 * s + 1] + f[1] - d[1], f[2] - d[2]};
-    const float v[3] = {f[7] - (om[1] * d[2] - om[2] * d[1]), f[8] - (om[2] * d[0] - om[0] * d[2]),
-                        f[9] - (om[0] * d[1] - om[1] * d[0])};
-    world_sym(R, sh.Ib, om, L);
+    mat_vec(Rn, ps, d);
+    const float w[3] = {f[10], f[11], f[12]};
+    const float c[3] = {x.c[0] + f[0] - d[0], x.c[1] + f[1] - d[1], f[2] - d[2]};
+    const float v[3] = {f[7] - (w[1] * d[2] - w[2] * d[1]), f[8] - (w[2] * d[0] - w[0] * d[2]),
+                        f[9] - (w[0] * d[1] - w[1] * d[0])};
+    world_sym(Rn, cached_sym(C.inert, S, s), w, L);
     const float chk = c[0] + c[1] + c[2] + v[0] + v[1] + v[2] + L[0] + L[1] + L[2] + qn[0] + qn[1] + qn[2] + qn[3];
-    if (!isfinite(chk)) { W.status[s] = status | 1u; return; }
-    const int S = W.S;
-    W.st[ST_CX * S + s] = c[0]; W.st[ST_CY * S + s] = c[1]; W.st[ST_CZ * S + s] = c[2];
-    W.st[ST_QW * S + s] = qn[0]; W.st[ST_QX * S + s] = qn[1]; W.st[ST_QY * S + s] = qn[2]; W.st[ST_QZ * S + s] = qn[3];
-    W.st[ST_VX * S + s] = v[0]; W.st[ST_VY * S + s] = v[1]; W.st[ST_VZ * S + s] = v[2];
-    W.st[ST_LX * S + s] = L[0]; W.st[ST_LY * S + s] = L[1]; W.st[ST_LZ * S + s] = L[2];
-    W.omega[s] = om[0]; W.omega[S + s] = om[1]; W.omega[2 * S + s] = om[2];
+    if (!isfinite(chk)) {
+        W.status[s] = status | 1u;
+        applied[s] = 0;
+        return;
+    }
+    const float o[NX_N] = {c[0], c[1], c[2], qn[0], qn[1], qn[2], qn[3], v[0], v[1], v[2], L[0], L[1], L[2],
+                           w[0], w[1], w[2]};
+#pragma unroll
+    for (int k = 0; k < NX_N; ++k) nx[(size_t)k * S + s] = o[k];
+    applied[s] = 1;
 }
 
-// Contacts of every point at the current state; scenes whose contact sensors changed are
-// appended to list (the plain step redoes them), the others keep the new contacts.
+// Contact sensors at the candidate state, one warp per scene over its sensor points (the cached
+// body-frame offsets of the points of contact-sensor links).
 template <bool FLAT>
-__global__ void __launch_bounds__(128) contact_probe_kernel(WorldDev W, int *list, int *count, int sbytes) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int s = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (s >= W.S) return;   // warp-uniform
-    unsigned char *slot = smem + (size_t)warp * sbytes;
-    float4 *pts = reinterpret_cast<float4 *>(slot);
-    float *fr = reinterpret_cast<float *>(slot + 16 * W.max_points);
-    float *th = fr + 12 * W.max_links;
-    const int p0 = W.point_off[s], np = W.point_off[s + 1] - p0;
-    const int l0 = W.link_off[s], nl = W.link_off[s + 1] - l0, j0 = l0 - s;
-    for (int j = lane; j < nl - 1; j += 32) th[j] = W.theta[j0 + j];
-    __syncwarp();
-    Shape sh;
-    shape_update<32>(W, s, p0, np, l0, nl, th, fr, pts, lane, sh);
+__global__ void __launch_bounds__(256) sensor_probe_kernel(WorldDev W, SurCache C, const float *nx,
+                                                           const uint8_t *applied, uint32_t *sens_new) {
+    const int lane = threadIdx.x & 31;
+    const int s = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (s >= W.S || !applied[s]) return;   // warp-uniform
     const int S = W.S;
-    const float c[3] = {W.st[ST_CX * S + s], W.st[ST_CY * S + s], W.st[ST_CZ * S + s]};
-    const float q[4] = {W.st[ST_QW * S + s], W.st[ST_QX * S + s], W.st[ST_QY * S + s], W.st[ST_QZ * S + s]};
+    const float q[4] = {nx[NX_QW * S + s], nx[NX_QX * S + s], nx[NX_QY * S + s], nx[NX_QZ * S + s]};
+    const float c[3] = {nx[NX_CX * S + s], nx[NX_CY * S + s], nx[NX_CZ * S + s]};
+    const int n = C.nsp_s[s], hm = FLAT ? -1 : W.hmap[s];
     float R[9];
     quat_mat(q, R);
-    const int hm = FLAT ? -1 : W.hmap[s];
-    uint32_t sens = 0;
-    for (int i = lane; i < np; i += 32) {
-        const float4 r = pts[i];
-        const float x = c[0] + R[0] * r.x + R[1] * r.y + R[2] * r.z;
-        const float y = c[1] + R[3] * r.x + R[4] * r.y + R[5] * r.z;
-        const float z = c[2] + R[6] * r.x + R[7] * r.y + R[8] * r.z;
-        const bool k = z < ground<FLAT>(W, hm, x, y);
-        W.kappa[p0 + i] = k ? 1 : 0;
-        if (k) {
-            const int sid = W.links[l0 + W.plink[p0 + i]].sensor;
-            if (sid >= 0 && sid < 32) sens |= 1u << sid;
-        }
+    uint32_t bits = 0u;
+    for (int k = lane; k < n; k += 32) {
+        const float4 r = C.spt[(size_t)s * C.nsp + k];
+        const float px = c[0] + R[0] * r.x + R[1] * r.y + R[2] * r.z;
+        const float py = c[1] + R[3] * r.x + R[4] * r.y + R[5] * r.z;
+        const float pz = c[2] + R[6] * r.x + R[7] * r.y + R[8] * r.z;
+        if (pz < ground<FLAT>(W, hm, px, py)) bits |= 1u << (int)r.w;
     }
-    sens = gor<32>(sens);
-    if (lane == 0) {
-        if (sens != W.sensors[s] && W.status[s] == 0u) list[atomicAdd(count, 1)] = s;
-        W.sensors[s] = sens;
-    }
+    bits = gor<32>(bits);
+    if (lane == 0) sens_new[s] = bits;
 }
 
-// Put the listed scenes back to their state before the surrogate step.
-__global__ void restore_kernel(WorldDev W, const int *list, const int *count, const float *st, const float *theta,
-                               const uint8_t *kappa, const uint32_t *sensors, const uint32_t *status) {
-    const int i = blockIdx.x;
-    if (i >= *count) return;
-    const int s = list[i];
+// One thread per scene: keep the candidate state if the contact sensors did not change, otherwise
+// leave the scene at its state and append it to the fallback list (the plain step takes it).
+__global__ void __launch_bounds__(256) surrogate_commit_kernel(WorldDev W, const float *nx, const uint8_t *applied,
+                                                               const uint32_t *sens_new, int *list, int *count) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool app = s < W.S && applied[s];
+    const bool fall = app && sens_new[s] != W.sensors[s];
+    // warp-aggregated append
+    const unsigned m = __ballot_sync(FULL_MASK, fall);
+    int base = 0;
+    const int lane = threadIdx.x & 31;
+    if (m) {
+        if (lane == __ffs(m) - 1) base = atomicAdd(count, __popc(m));
+        base = __shfl_sync(FULL_MASK, base, __ffs(m) - 1);
+    }
+    if (fall) list[base + __popc(m & ((1u << lane) - 1u))] = s;
+    if (!app || fall) return;
     const int S = W.S;
-    const int p0 = W.point_off[s], np = W.point_off[s + 1] - p0;
-    const int l0 = W.link_off[s], nj = W.link_off[s + 1] - l0 - 1, j0 = l0 - s;
-    for (int k = threadIdx.x; k < ST_N; k += blockDim.x) W.st[k * S + s] = st[k * S + s];
-    for (int j = threadIdx.x; j < nj; j += blockDim.x) W.theta[j0 + j] = theta[j0 + j];
-    for (int p = threadIdx.x; p < np; p += blockDim.x) W.kappa[p0 + p] = kappa[p0 + p];
-    if (threadIdx.x == 0) { W.sensors[s] = sensors[s]; W.status[s] = status[s]; }
+#pragma unroll
+    for (int k = 0; k < ST_N; ++k) W.st[(size_t)k * S + s] = nx[(size_t)k * S + s];
+    W.omega[s] = nx[NX_WX * S + s];
+    W.omega[S + s] = nx[NX_WY * S + s];
+    W.omega[2 * S + s] = nx[NX_WZ * S + s];
+}
+
+// Contact flags of every point and the contact sensors at the current state, for the listed scenes
+// (list NULL: every scene) -- the previous-step contacts a plain step needs after surrogate steps.
+template <bool FLAT>
+__global__ void __launch_bounds__(128) kappa_refresh_kernel(WorldDev W, const int *list, const int *count,
+                                                            int sbytes) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    unsigned char *slot = smem + (size_t)warp * sbytes;
+    float4 *pts = reinterpret_cast<float4 *>(slot);
+    float *fr = reinterpret_cast<float *>(slot + 16 * W.max_points);
+    float *th = fr + 12 * W.max_links;
+    const int n = list ? *count : W.S;
+    for (int i = blockIdx.x * wpb + warp; i < n; i += gridDim.x * wpb) {   // warp-uniform
+        const int s = list ? list[i] : i;
+        const int p0 = W.point_off[s], np = W.point_off[s + 1] - p0;
+        const int l0 = W.link_off[s], nl = W.link_off[s + 1] - l0, j0 = l0 - s;
+        for (int j = lane; j < nl - 1; j += 32) th[j] = W.theta[j0 + j];
+        __syncwarp();
+        Shape sh;
+        shape_update<32>(W, s, p0, np, l0, nl, th, fr, pts, lane, sh);
+        const RootState x = load_root(W, s);
+        float R[9];
+        quat_mat(x.q, R);
+        const int hm = FLAT ? -1 : W.hmap[s];
+        uint32_t sens = 0;
+        for (int k = lane; k < np; k += 32) {
+            const float4 r = pts[k];
+            const float px = x.c[0] + R[0] * r.x + R[1] * r.y + R[2] * r.z;
+            const float py = x.c[1] + R[3] * r.x + R[4] * r.y + R[5] * r.z;
+            const float pz = x.c[2] + R[6] * r.x + R[7] * r.y + R[8] * r.z;
+            const bool kap = pz < ground<FLAT>(W, hm, px, py);
+            W.kappa[p0 + k] = kap ? 1 : 0;
+            if (kap) {
+                const int sid = W.links[l0 + W.plink[p0 + k]].sensor;
+                if (sid >= 0 && sid < 32) sens |= 1u << sid;
+            }
+        }
+        sens = gor<32>(sens);
+        if (lane == 0) W.sensors[s] = sens;
+        __syncwarp();
+    }
 }
 
 __global__ void accumulate_kernel(long long *total, int *count) {
@@ -1065,42 +1212,68 @@ cudaError_t launch_accumulate(long long *total, int *count, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_features(const WorldDev &W, int nf, int nt, int nl, int ns, float *X, float *Xraw, float *cxy_out,
-                            const float *cxy_ref, const float *prev, float *T, const float *x_mu, const float *x_isd,
-                            const float *t_mu, const float *t_sd, cudaStream_t st) {
-    const int wpb = 4, sb = slot_bytes(W.max_points, W.max_links, 32);
-    cudaError_t e = cudaFuncSetAttribute((void *)features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, wpb * sb);
-    if (e != cudaSuccess) return e;
-    SurrogateIO io{nf, nt, nl, ns, X, Xraw, cxy_out, cxy_ref, prev, T, x_mu, x_isd, t_mu, t_sd};
-    features_kernel<<<(W.S + wpb - 1) / wpb, wpb * 32, wpb * sb, st>>>(W, io, sb);
+namespace {
+constexpr int SUR_WPB = 4;   // warps (scenes) per block of the surrogate kernels
+unsigned sur_blocks(int S) { return (unsigned)((S + SUR_WPB - 1) / SUR_WPB); }
+}  // namespace
+
+cudaError_t launch_sensor_points(const WorldDev &W, int *count, int *max_count, cudaStream_t st) {
+    sensor_points_kernel<<<sur_blocks(W.S), SUR_WPB * 32, 0, st>>>(W, count, max_count);
     return cudaGetLastError();
 }
 
-cudaError_t launch_surrogate_apply(const WorldDev &W, const float *Y, const float *t_mu, const float *t_sd,
-                                   const float *F0, int nf, int nt, const float *cxy0, cudaStream_t st) {
-    const int wpb = 4, sb = slot_bytes(W.max_points, W.max_links, 32);
-    cudaError_t e = cudaFuncSetAttribute((void *)surrogate_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, wpb * sb);
+cudaError_t launch_shape_cache(const WorldDev &W, const SurCache &C, cudaStream_t st) {
+    const int sb = (int)slot_bytes(W.max_points, W.max_links, 32);
+    cudaError_t e = cudaFuncSetAttribute((void *)shape_cache_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SUR_WPB * sb);
     if (e != cudaSuccess) return e;
-    surrogate_apply_kernel<<<(W.S + wpb - 1) / wpb, wpb * 32, wpb * sb, st>>>(W, Y, t_mu, t_sd, F0, nf, nt, cxy0, sb);
+    shape_cache_kernel<<<sur_blocks(W.S), SUR_WPB * 32, SUR_WPB * sb, st>>>(W, C, sb);
     return cudaGetLastError();
 }
 
-cudaError_t launch_contact_probe(const WorldDev &W, int *list, int *count, cudaStream_t st) {
-    const int wpb = 4, sb = slot_bytes(W.max_points, W.max_links, 32);
-    void *fn = W.hm ? (void *)contact_probe_kernel<false> : (void *)contact_probe_kernel<true>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, wpb * sb);
+cudaError_t launch_features(const WorldDev &W, const SurCache &C, const SurrogateIO &io, cudaStream_t st) {
+    const int spb = io.nl >= 256 ? 1 : 256 / io.nl;             // scenes per block
+    const int threads = std::max(256, (io.nl + 31) / 32 * 32);
+    const size_t sm = (size_t)spb * io.nf * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute((void *)features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
+    features_kernel<<<(unsigned)((W.S + spb - 1) / spb), threads, sm, st>>>(W, C, io, spb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_surrogate_update(const WorldDev &W, const SurCache &C, const float *Y, int ldy, const float *t_mu,
+                                    const float *t_sd, float *nx, uint8_t *applied, uint32_t *sens_new, int *list,
+                                    int *count, cudaStream_t st) {
+    const unsigned bs = (unsigned)((W.S + 255) / 256);
+    surrogate_apply_kernel<<<bs, 256, 0, st>>>(W, C, Y, ldy, t_mu, t_sd, nx, applied);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const unsigned bp = (unsigned)(((long long)W.S * 32 + 255) / 256);
+    if (W.hm)
+        sensor_probe_kernel<false><<<bp, 256, 0, st>>>(W, C, nx, applied, sens_new);
+    else
+        sensor_probe_kernel<true><<<bp, 256, 0, st>>>(W, C, nx, applied, sens_new);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    surrogate_commit_kernel<<<bs, 256, 0, st>>>(W, nx, applied, sens_new, list, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kappa_refresh(const WorldDev &W, const int *list, const int *count, cudaStream_t st) {
+    const int sb = (int)slot_bytes(W.max_points, W.max_links, 32);
+    void *fn = W.hm ? (void *)kappa_refresh_kernel<false> : (void *)kappa_refresh_kernel<true>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SUR_WPB * sb);
+    if (e != cudaSuccess) return e;
+    // a grid-stride loop over the scenes (or the listed ones), at most a few blocks per SM
+    int dev = 0, nsm = 1;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const unsigned blocks = std::min(sur_blocks(W.S), (unsigned)(8 * nsm));
     WorldDev w = W;
+    const int *l = list, *c = count;
     int sbv = sb;
-    void *args[] = {&w, &list, &count, &sbv};
-    return cudaLaunchKernel(fn, dim3((W.S + wpb - 1) / wpb), dim3(wpb * 32), args, wpb * sb, st);
-}
-
-cudaError_t launch_restore(const WorldDev &W, const int *list, const int *count, const float *st_b,
-                           const float *theta_b, const uint8_t *kappa_b, const uint32_t *sens_b,
-                           const uint32_t *status_b, cudaStream_t st) {
-    restore_kernel<<<W.S, 128, 0, st>>>(W, list, count, st_b, theta_b, kappa_b, sens_b, status_b);
-    return cudaGetLastError();
+    void *args[] = {&w, &l, &c, &sbv};
+    return cudaLaunchKernel(fn, dim3(blocks), dim3(SUR_WPB * 32), args, SUR_WPB * sb, st);
 }
 
 // ------------------------------------------------------------------------ host-side launchers
@@ -1126,8 +1299,21 @@ int step_blocks_per_sm(const WorldDev &W, int lps, int wpb, cudaError_t *err) {
     *err = cudaSuccess;
     if (!fn) { *err = cudaErrorInvalidValue; return 0; }
     const size_t smem = step_smem_bytes(W, lps, wpb);
-    *err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (*err != cudaSuccess) return 0;
+    // a shape over the per-block limit does not fit: report 0 blocks without a failing call (a
+    // failed runtime call would leave an error behind for the next launch check to pick up)
+    int dev = 0, optin = 0;
+    if ((*err = cudaGetDevice(&dev)) != cudaSuccess) return 0;
+    if ((*err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return 0;
+    if (smem > (size_t)optin) return 0;
+    // the attribute is an upper limit: raise it, never lower it, so that a shape set up earlier
+    // (another world, or the fallback shape of this one) stays launchable
+    cudaFuncAttributes fa{};
+    *err = cudaFuncGetAttributes(&fa, fn);
+    if (*err != cudaSuccess) { cudaGetLastError(); return 0; }
+    if ((size_t)fa.maxDynamicSharedSizeBytes < smem) {
+        *err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (*err != cudaSuccess) { cudaGetLastError(); return 0; }
+    }
     int nb = 0;
     *err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, wpb * 32, smem);
     return nb;

@@ -113,10 +113,12 @@ struct npx_world {
     int sensor_bits = 0;                // highest contact-sensor bit + 1
     // surrogate-step buffers, allocated on first use
     struct {
-        float *X = nullptr, *F0 = nullptr, *F1 = nullptr, *C0 = nullptr, *Y = nullptr;
-        float *st = nullptr, *theta = nullptr;
-        uint8_t *kappa = nullptr;
-        uint32_t *sens = nullptr, *status = nullptr;
+        bool ready = false;
+        float *F0 = nullptr, *C0 = nullptr;   // raw features and CoG (x, y) before a collected step
+        npx::SurCache cache{};
+        float *nx = nullptr;                  // candidate next states [16 * S]
+        uint8_t *applied = nullptr;           // [S]
+        uint32_t *sens_new = nullptr;         // [S]
         int *list = nullptr, *count = nullptr;
         long long *total = nullptr;
         cudaEvent_t ev_w = nullptr, ev_n = nullptr;
@@ -322,24 +324,32 @@ int surrogate_dims(npx_world *w, int *nf, int *nt) {
 }
 
 int surrogate_buffers(npx_world *w) {
-    if (w->sg.X) return NPX_OK;
+    if (w->sg.ready) return NPX_OK;
     int nf, nt;
     if (int rc = surrogate_dims(w, &nf, &nt)) return rc;
     const int rows = (w->S + 127) / 128 * 128;
-    int rc;
-    if ((rc = dev_alloc(w, &w->sg.X, (size_t)rows * nf)) || (rc = dev_alloc(w, &w->sg.F0, (size_t)w->S * nf)) ||
-        (rc = dev_alloc(w, &w->sg.F1, (size_t)w->S * nf)) || (rc = dev_alloc(w, &w->sg.C0, 2 * (size_t)w->S)) ||
-        (rc = dev_alloc(w, &w->sg.Y, (size_t)rows * nt)) || (rc = dev_alloc(w, &w->sg.st, (size_t)npx::ST_N * w->S)) ||
-        (rc = dev_alloc(w, &w->sg.theta, std::max(w->J, 1))) || (rc = dev_alloc(w, &w->sg.kappa, w->P)) ||
-        (rc = dev_alloc(w, &w->sg.sens, w->S)) || (rc = dev_alloc(w, &w->sg.status, w->S)) ||
+    npx::SurCache &C = w->sg.cache;
+    int rc, *d_max = nullptr;
+    if ((rc = dev_alloc(w, &w->sg.F0, (size_t)w->S * nf)) || (rc = dev_alloc(w, &w->sg.C0, 2 * (size_t)w->S)) ||
         (rc = dev_alloc(w, &w->sg.list, w->S)) || (rc = dev_alloc(w, &w->sg.count, 1)) ||
-        (rc = dev_alloc(w, &w->sg.total, 1)))
+        (rc = dev_alloc(w, &w->sg.total, 1)) || (rc = dev_alloc(w, &C.lk, 2 * (size_t)w->S * w->max_links)) ||
+        (rc = dev_alloc(w, &C.inert, 12 * (size_t)w->S)) || (rc = dev_alloc(w, &C.nsp_s, w->S)) ||
+        (rc = dev_alloc(w, &d_max, 1)) || (rc = dev_alloc(w, &w->sg.nx, 16 * (size_t)w->S)) ||
+        (rc = dev_alloc(w, &w->sg.applied, w->S)) || (rc = dev_alloc(w, &w->sg.sens_new, w->S)))
         return rc;
-    CUDA_TRY(cudaMemset(w->sg.X, 0, sizeof(float) * (size_t)rows * nf));
-    CUDA_TRY(cudaMemset(w->sg.count, 0, sizeof(int)));
+    CUDA_TRY(cudaMemsetAsync(w->sg.count, 0, sizeof(int), w->stream));
+    CUDA_TRY(cudaMemsetAsync(d_max, 0, sizeof(int), w->stream));
+    CUDA_TRY(npx::launch_sensor_points(w->W, C.nsp_s, d_max, w->stream));
+    int nsp = 0;
+    CUDA_TRY(cudaMemcpyAsync(&nsp, d_max, sizeof(int), cudaMemcpyDeviceToHost, w->stream));
+    CUDA_TRY(cudaStreamSynchronize(w->stream));
+    if ((rc = dev_alloc(w, &C.spt, (size_t)w->S * std::max(nsp, 1)))) return rc;
+    C.nsp = std::max(nsp, 1);
+    C.nl = w->max_links;
     CUDA_TRY(cudaEventCreateWithFlags(&w->sg.ev_w, cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreateWithFlags(&w->sg.ev_n, cudaEventDisableTiming));
     w->sg.rows = rows;
+    w->sg.ready = true;
     return NPX_OK;
 }
 
@@ -976,25 +986,32 @@ int npx_surrogate_collect(npx_world *w, const npx_surrogate_norm *nrm, int n_ste
     if (int rc = surrogate_buffers(w)) return rc;
     int nf, nt;
     surrogate_dims(w, &nf, &nt);
-    const float *xm = nrm ? nrm->x_mu : nullptr, *xi = nrm ? nrm->x_isd : nullptr;
-    const float *tm = nrm ? nrm->t_mu : nullptr, *ts = nrm ? nrm->t_sd : nullptr;
-    const int NL = w->max_links;
+    const npx::SurCache &C = w->sg.cache;
     const bool actuated = w->act_mode != NPX_ACT_HOLD;
+    npx::SurrogateIO pre{nf, nt, w->max_links, w->sensor_bits};
+    pre.Xraw = w->sg.F0;
+    pre.cxy_out = w->sg.C0;
+    if (nrm) { pre.x_mu = nrm->x_mu; pre.x_isd = nrm->x_isd; }
+    npx::SurrogateIO post{nf, nt, w->max_links, w->sensor_bits};
+    post.cxy_ref = w->sg.C0;
+    post.prev = w->sg.F0;
+    if (nrm) { post.t_mu = nrm->t_mu; post.t_sd = nrm->t_sd; }
+    CUDA_TRY(npx::launch_shape_cache(w->W, C, w->stream));
     for (int k = 0; k < n_steps;) {
         if (actuated && w->step % w->desc.joint_update_steps == 0) {   // joint updates stay plain
             CUDA_TRY(npx::launch_step(w->W, w->cfg, 1, w->stream));
             CUDA_TRY(npx::launch_advance(w->d_step, 1, w->stream));
+            CUDA_TRY(npx::launch_shape_cache(w->W, C, w->stream));
             w->step += 1;
             w->launches += 1;
             continue;
         }
-        float *Xk = X + (size_t)k * w->S * nf, *Tk = T + (size_t)k * w->S * nt;
-        CUDA_TRY(npx::launch_features(w->W, nf, nt, NL, w->sensor_bits, Xk, w->sg.F0, w->sg.C0, nullptr, nullptr,
-                                      nullptr, xm, xi, nullptr, nullptr, w->stream));
+        pre.X = X + (size_t)k * w->S * nf;
+        post.T = T + (size_t)k * w->S * nt;
+        CUDA_TRY(npx::launch_features(w->W, C, pre, w->stream));
         CUDA_TRY(npx::launch_step(w->W, w->cfg, 1, w->stream));
         CUDA_TRY(npx::launch_advance(w->d_step, 1, w->stream));
-        CUDA_TRY(npx::launch_features(w->W, nf, nt, NL, w->sensor_bits, nullptr, w->sg.F1, nullptr, w->sg.C0,
-                                      w->sg.F0, Tk, nullptr, nullptr, tm, ts, w->stream));
+        CUDA_TRY(npx::launch_features(w->W, C, post, w->stream));
         w->step += 1;
         w->launches += 1;
         ++k;
@@ -1017,43 +1034,58 @@ int npx_world_step_surrogate(npx_world *w, npx_mlp *net, const npx_surrogate_nor
     if (npx::mlp_max_batch(net) < w->sg.rows) return fail(NPX_ERANGE, "network batch capacity below %d rows", w->sg.rows);
     CUDA_TRY(cudaMemsetAsync(w->sg.total, 0, sizeof(long long), w->stream));
     cudaStream_t ns = npx::mlp_stream(net);
+    int ldx = 0, ldy = 0;
+    __nv_bfloat16 *Xb = npx::mlp_input(net, &ldx);
+    const float *Y = npx::mlp_output(net, &ldy);
+    const npx::SurCache &C = w->sg.cache;
+    npx::SurrogateIO io{nf, nt, w->max_links, w->sensor_bits};
+    io.Xb = Xb;
+    io.ldb = ldx;
+    io.x_mu = nrm->x_mu;
+    io.x_isd = nrm->x_isd;
     npx::WorldDev Wsub = w->W;            // the plain step on the fallback list only
     Wsub.order = w->sg.list;
     Wsub.sched_count = w->sg.count;
-    const size_t S = w->S;
+    // the fallback list is short: one scene per warp (32 lanes) gives it the least latency
+    int rc_cfg = 0;
+    npx::LaunchCfg fcfg = w->cfg;
+    if (w->max_points <= 64 * 32) {
+        fcfg = clamp_cfg(w, {32, 4, 0}, &rc_cfg);
+        if (rc_cfg) return rc_cfg;
+    }
     const bool actuated = w->act_mode != NPX_ACT_HOLD;
+    CUDA_TRY(npx::launch_shape_cache(w->W, C, w->stream));
     for (int k = 0; k < n_steps; ++k) {
         if (actuated && (w->step + k) % w->desc.joint_update_steps == 0) {
-            // joint-update steps (Sec. III-B) are taken by the plain step for every scene
+            // joint-update steps (Sec. III-B) are taken by the plain step for every scene, from
+            // the contacts at the current state
+            CUDA_TRY(npx::launch_kappa_refresh(w->W, nullptr, nullptr, w->stream));
             CUDA_TRY(npx::launch_step(w->W, w->cfg, 1, w->stream));
             CUDA_TRY(npx::launch_advance(w->d_step, 1, w->stream));
+            CUDA_TRY(npx::launch_shape_cache(w->W, C, w->stream));
             continue;
         }
-        CUDA_TRY(npx::launch_features(w->W, nf, nt, w->max_links, w->sensor_bits, w->sg.X, w->sg.F0, w->sg.C0, nullptr,
-                                      nullptr, nullptr, nrm->x_mu, nrm->x_isd, nullptr, nullptr, w->stream));
+        CUDA_TRY(npx::launch_features(w->W, C, io, w->stream));
         if (ns != w->stream) {
             CUDA_TRY(cudaEventRecord(w->sg.ev_w, w->stream));
             CUDA_TRY(cudaStreamWaitEvent(ns, w->sg.ev_w, 0));
         }
-        if (int rc = npx_mlp_forward(net, w->sg.X, w->sg.Y, w->sg.rows)) return rc;
+        if (int rc = npx::mlp_forward_packed(net, w->sg.rows)) return rc;
         if (ns != w->stream) {
             CUDA_TRY(cudaEventRecord(w->sg.ev_n, ns));
             CUDA_TRY(cudaStreamWaitEvent(w->stream, w->sg.ev_n, 0));
         }
-        // keep the state before the step for the scenes that fall back
-        CUDA_TRY(cudaMemcpyAsync(w->sg.st, w->W.st, sizeof(float) * npx::ST_N * S, cudaMemcpyDeviceToDevice, w->stream));
-        if (w->J) CUDA_TRY(cudaMemcpyAsync(w->sg.theta, w->W.theta, sizeof(float) * w->J, cudaMemcpyDeviceToDevice, w->stream));
-        CUDA_TRY(cudaMemcpyAsync(w->sg.kappa, w->W.kappa, w->P, cudaMemcpyDeviceToDevice, w->stream));
-        CUDA_TRY(cudaMemcpyAsync(w->sg.sens, w->W.sensors, sizeof(uint32_t) * S, cudaMemcpyDeviceToDevice, w->stream));
-        CUDA_TRY(cudaMemcpyAsync(w->sg.status, w->W.status, sizeof(uint32_t) * S, cudaMemcpyDeviceToDevice, w->stream));
-        CUDA_TRY(npx::launch_surrogate_apply(w->W, w->sg.Y, nrm->t_mu, nrm->t_sd, w->sg.F0, nf, nt, w->sg.C0, w->stream));
-        CUDA_TRY(npx::launch_contact_probe(w->W, w->sg.list, w->sg.count, w->stream));
-        CUDA_TRY(npx::launch_restore(w->W, w->sg.list, w->sg.count, w->sg.st, w->sg.theta, w->sg.kappa, w->sg.sens,
-                                     w->sg.status, w->stream));
-        CUDA_TRY(npx::launch_step(Wsub, w->cfg, 1, w->stream));
+        CUDA_TRY(npx::launch_surrogate_update(w->W, C, Y, ldy, nrm->t_mu, nrm->t_sd, w->sg.nx, w->sg.applied,
+                                              w->sg.sens_new, w->sg.list, w->sg.count, w->stream));
+        // the fallback: listed scenes kept their state; the plain step takes them from the
+        // contacts at that state
+        CUDA_TRY(npx::launch_kappa_refresh(w->W, w->sg.list, w->sg.count, w->stream));
+        CUDA_TRY(npx::launch_step(Wsub, fcfg, 1, w->stream));
         CUDA_TRY(npx::launch_accumulate(w->sg.total, w->sg.count, w->stream));
         CUDA_TRY(npx::launch_advance(w->d_step, 1, w->stream));
     }
+    // contact flags consistent with the final state for whatever reads or steps the world next
+    CUDA_TRY(npx::launch_kappa_refresh(w->W, nullptr, nullptr, w->stream));
     w->step += n_steps;
     w->launches += n_steps;
     if (fallbacks) {
