@@ -148,6 +148,120 @@ def other_workloads(World, scenes, stream, device) -> dict:
     return out
 
 
+def _measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def surrogate_leg(World, scenes, stream, device, n_transitions: int) -> dict:
+    """The learned surrogate: trained on n_transitions transitions of the 4,096-hexapod workload,
+    then stepping 65,536 hexapods (joint-update steps and scenes whose foot contacts change are
+    taken by the plain step); its throughput beside the plain step's on the same scenes, its
+    50-step error against the FP64 oracle on 256 held-out scenes, and its network's forward
+    pass against the bf16 tensor peak."""
+    import torch
+    from oracle.oracle import Oracle
+    from paper_2411_05799_gb300 import npx, surrogate
+    S, PERIOD = 65536, 80
+    res = surrogate.train(scenes.hexapod_batch(4096, seed_key=40), n_transitions=n_transitions,
+                          passes=2, lr=1e-3, max_batch=S)
+    sur = res["surrogate"]
+    big = scenes.hexapod_batch(S, seed_key=5)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+    out = {"workload": f"hexapod_18dof_{S}_scenes_flat_dt1ms_K80", "unit": UNIT}
+
+    def timed(fn, reps):
+        ms = 0.0
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            torch.cuda.synchronize(device)
+            ms += e0.elapsed_time(e1)
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+        return ms, r
+
+    # plain step on the same scenes (1,000-step chunks)
+    w = World.from_batch(big, stream=stream.cuda_stream, device=device.index or 0)
+    w.autotune(100)
+    w.configure(chunk_steps=CHUNK)
+    w.step(CHUNK)
+    ms, _ = timed(lambda: w.step(CHUNK), 2)
+    out["plain_value"] = S * 2 * CHUNK / (ms / 1e3)
+    # surrogate steps: whole joint-update periods, after one warm-up period
+    npx.world_step_surrogate(w, sur.net, sur.norm, PERIOD)
+    fb_total, reps = 0, 4
+    ms, _ = 0.0, None
+    for _ in range(reps):
+        m, fb = timed(lambda: npx.world_step_surrogate(w, sur.net, sur.norm, PERIOD), 1)
+        ms += m
+        fb_total += fb
+    out["value"] = S * PERIOD * reps / (ms / 1e3)
+    out["ms_per_step"] = ms / (PERIOD * reps)
+    out["fallback_fraction"] = fb_total / (S * PERIOD * reps)
+    out["frozen_scenes"] = int((w.read()["status"] != 0).sum())
+    w.close()
+    # the network's forward pass over all scenes: five BF16 GEMMs with fused epilogues
+    x = torch.zeros(S, sur.n_in, device=device)
+    y = torch.empty(S, sur.n_out, device=device)
+    net_stream = torch.cuda.ExternalStream(sur.stream, device=device)
+    sur.net.forward(x.data_ptr(), y.data_ptr(), S)
+    torch.cuda.synchronize(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record(net_stream)
+    for _ in range(reps):
+        sur.net.forward(x.data_ptr(), y.data_ptr(), S)
+    e1.record(net_stream)
+    torch.cuda.synchronize(device)
+    fwd_ms = e0.elapsed_time(e1) / reps
+    n_in, H, n_out = sur.n_in, surrogate.N_HIDDEN, sur.n_out
+    flops = 2.0 * S * (n_in * H + (surrogate.N_LAYERS - 1) * H * H + H * n_out)
+    peak = _measured_peaks().get("bf16_tflops")
+    achieved = flops / (fwd_ms / 1e3) / 1e12
+    out["roofline"] = {"bound": "tensor", "kernel": "gemm_tn_kernel (network forward, 5 launches)",
+                       "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                       "frac": achieved / peak if peak else None, "traffic": None,
+                       "flops_per_scene_step": flops / S,
+                       "peak_note": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
+    out["forward_ms"] = fwd_ms
+    # 50-step error against the FP64 oracle, from a mid-gait state of 256 held-out scenes
+    test_b = scenes.hexapod_batch(256, seed_key=41)
+    o = Oracle(test_b, threads=os.cpu_count() or 1)
+    o.step(1000)
+    ref = Oracle(test_b, threads=os.cpu_count() or 1)
+    ref.copy_state_from(o)
+    ref.step(50)
+    err = {}
+    for name, fn in (("surrogate", lambda ww: npx.world_step_surrogate(ww, sur.net, sur.norm, 50)),
+                     ("plain", lambda ww: ww.step(50))):
+        ww = World.from_batch(test_b, stream=stream.cuda_stream, device=device.index or 0)
+        ww.write_state(o.c.astype(np.float32), o.q.astype(np.float32), o.v.astype(np.float32),
+                       o.L.astype(np.float32), o.theta.astype(np.float32),
+                       o.kappa.astype(np.uint8), o.n)
+        fn(ww)
+        r = ww.read()
+        dc = np.linalg.norm(r["cog"] - ref.c, axis=1)
+        qa, qb = r["quat"].astype(np.float64), ref.q
+        ang = 2 * np.arctan2(np.linalg.norm(qa - qb, axis=1), np.linalg.norm(qa + qb, axis=1))
+        ang = np.minimum(ang, 2 * np.pi - ang)
+        err[name] = {"cog_m_median": float(np.median(dc)), "cog_m_rms": float(np.sqrt(np.mean(dc ** 2))),
+                     "cog_m_p90": float(np.percentile(dc, 90)),
+                     "angle_rad_median": float(np.median(ang)), "angle_rad_rms": float(np.sqrt(np.mean(ang ** 2)))}
+        ww.close()
+    out["error_50_steps_vs_fp64_oracle"] = err
+    u = res["unexplained"]
+    out["training"] = {"transitions": int(res["transitions"]), "adam_steps": int(res["adam_steps"]),
+                       "seconds": round(res["seconds"], 2), "scenes": 4096,
+                       "held_out_unexplained_variance": float(np.mean(u[-5:]))}
+    return out
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle on the host cores, same workload and metric."""
     ws, rank, _ = dist_env()
@@ -284,6 +398,8 @@ def run_gpu(args):
     # mix and on 16,384 hexapods walking on rough height fields (informational)
     if rank == 0 and not args.no_extra:
         line["other_workloads"] = other_workloads(World, scenes, stream, local)
+    if rank == 0 and not args.no_surrogate:
+        line["surrogate"] = surrogate_leg(World, scenes, stream, dev, args.surrogate_transitions)
 
     if rank == 0:
         # algorithmic flops per scene-step from the oracle's event counts on a sample
@@ -337,6 +453,8 @@ def main():
     ap.add_argument("--wpb", type=int, default=16)
     ap.add_argument("--chunk", type=int, default=100)
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate leg")
+    ap.add_argument("--surrogate-transitions", type=int, default=100_000_000)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
