@@ -426,29 +426,59 @@ def run_gpu(args):
 
 
 def run_profile(args):
-    """A few step-kernel launches of `--chunk` steps on the benchmark workload in a fixed launch
-    shape, for ncu captures (prints no benchmark line)."""
+    """ncu drivers (print no benchmark line).
+    step:      a few step-kernel launches of `--chunk` steps on the benchmark workload in a fixed
+               launch shape;
+    gemm:      the surrogate network's forward GEMMs over 65,536 rows (random weights), 3 passes;
+    surrogate: a briefly trained surrogate stepping 65,536 hexapods for 4 steps."""
     import torch
     from paper_2411_05799_gb300 import scenes
     from paper_2411_05799_gb300.build import build
     from paper_2411_05799_gb300.npx import World
     build()
     torch.cuda.set_device(0)
-    world = World.from_batch(scenes.hexapod_batch(N_SCENES),
-                             configure=dict(lanes_per_scene=args.lps, warps_per_block=args.wpb,
-                                            chunk_steps=args.chunk))
-    for _ in range(3):
-        world.step(args.chunk)
-    world.sync()
-    print(json.dumps({"profile": True, **world.info(),
-                      "status_nonzero": int((world.read()["status"] != 0).sum())}))
-    world.close()
+    if args.profile == "step":
+        world = World.from_batch(scenes.hexapod_batch(N_SCENES),
+                                 configure=dict(lanes_per_scene=args.lps, warps_per_block=args.wpb,
+                                                chunk_steps=args.chunk))
+        for _ in range(3):
+            world.step(args.chunk)
+        world.sync()
+        print(json.dumps({"profile": "step", **world.info(),
+                          "status_nonzero": int((world.read()["status"] != 0).sum())}))
+        world.close()
+        return 0
+    from paper_2411_05799_gb300 import npx, surrogate
+    S = 65536
+    if args.profile == "gemm":
+        stream = torch.cuda.Stream()
+        net = npx.MLP(271, 247, n_hidden=surrogate.N_HIDDEN, n_hidden_layers=surrogate.N_LAYERS,
+                      max_batch=S, stream=stream.cuda_stream)
+        with torch.cuda.stream(stream):
+            x = torch.randn(S, 271, device="cuda")
+            y = torch.empty(S, 247, device="cuda")
+            for _ in range(3):
+                net.forward(x.data_ptr(), y.data_ptr(), S)
+            stream.synchronize()
+        print(json.dumps({"profile": "gemm", "rows": S, "finite": bool(torch.isfinite(y).all())}))
+        return 0
+    res = surrogate.train(scenes.hexapod_batch(4096, seed_key=40), n_transitions=65536 * 8,
+                          passes=2, stat_periods=1, warm_steps=100, max_batch=S)
+    sur = res["surrogate"]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        w = World.from_batch(scenes.hexapod_batch(S, seed_key=5), stream=stream.cuda_stream)
+        w.step(301)
+        fb = npx.world_step_surrogate(w, sur.net, sur.norm, 4)
+        stream.synchronize()
+    print(json.dumps({"profile": "surrogate", "scenes": S, "steps": 4, "fallbacks": fb}))
     return 0
 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile", action="store_true", help="ncu driver: 3 launches, no bench line")
+    ap.add_argument("--profile", choices=["step", "gemm", "surrogate"],
+                    help="ncu driver (no bench line): step kernel, network GEMMs or surrogate step")
     ap.add_argument("--lps", type=int, default=16)
     ap.add_argument("--wpb", type=int, default=16)
     ap.add_argument("--chunk", type=int, default=100)
