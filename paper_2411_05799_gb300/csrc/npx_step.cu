@@ -36,6 +36,7 @@ namespace npx {
 #define FULL_MASK 0xffffffffu
 
 constexpr float POINT_RADIUS = 1e-3f;   // m, see shape_update
+constexpr float CULL_MARGIN = 4e-3f;    // m, height margin of the candidate tiles (run_scene)
 
 // ------------------------------------------------------------------------ group reductions
 
@@ -45,52 +46,6 @@ __device__ __forceinline__ void gsum(float (&v)[N]) {
     for (int o = LPS / 2; o > 0; o >>= 1) {
 #pragma unroll
         for (int i = 0; i < N; ++i) v[i] += __shfl_xor_sync(FULL_MASK, v[i], o);
-    }
-}
-
-// Count, mean and second central moment (symmetric 3x3: xx yy zz xy xz yz) of a point set,
-// merged across the group with Chan's pairwise formula.  The merge is written symmetrically in
-// its two operands (the partner's sign of the mean difference cancels in the outer product), so
-// every lane ends with bit-identical moments.
-struct Moments {
-    float n, m[3], M[6];
-};
-
-__device__ __forceinline__ void moments_add(Moments &a, const float x[3]) {
-    const float n1 = a.n + 1.f, f = __frcp_rn(n1), w = a.n * f;
-    const float d0 = x[0] - a.m[0], d1 = x[1] - a.m[1], d2 = x[2] - a.m[2];
-    a.m[0] += d0 * f; a.m[1] += d1 * f; a.m[2] += d2 * f;
-    a.M[0] += w * d0 * d0; a.M[1] += w * d1 * d1; a.M[2] += w * d2 * d2;
-    a.M[3] += w * d0 * d1; a.M[4] += w * d0 * d2; a.M[5] += w * d1 * d2;
-    a.n = n1;
-}
-
-template <int LPS>
-__device__ __forceinline__ void moments_reduce(Moments &a, float (&f)[3]) {
-#pragma unroll
-    for (int o = LPS / 2; o > 0; o >>= 1) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) f[i] += __shfl_xor_sync(FULL_MASK, f[i], o);
-        Moments b;
-        b.n = __shfl_xor_sync(FULL_MASK, a.n, o);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) b.m[i] = __shfl_xor_sync(FULL_MASK, a.m[i], o);
-#pragma unroll
-        for (int i = 0; i < 6; ++i) b.M[i] = __shfl_xor_sync(FULL_MASK, a.M[i], o);
-        const float n = a.n + b.n;
-        const float inv = n > 0.f ? __frcp_rn(n) : 0.f;
-        const float w = a.n * b.n * inv;
-        const float d0 = b.m[0] - a.m[0], d1 = b.m[1] - a.m[1], d2 = b.m[2] - a.m[2];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)   // no FMA contraction: keep the merge symmetric
-            a.m[i] = (__fmul_rn(a.n, a.m[i]) + __fmul_rn(b.n, b.m[i])) * inv;
-        a.M[0] = (a.M[0] + b.M[0]) + w * (d0 * d0);
-        a.M[1] = (a.M[1] + b.M[1]) + w * (d1 * d1);
-        a.M[2] = (a.M[2] + b.M[2]) + w * (d2 * d2);
-        a.M[3] = (a.M[3] + b.M[3]) + w * (d0 * d1);
-        a.M[4] = (a.M[4] + b.M[4]) + w * (d0 * d2);
-        a.M[5] = (a.M[5] + b.M[5]) + w * (d1 * d2);
-        a.n = n;
     }
 }
 
@@ -206,43 +161,59 @@ __host__ __device__ inline int slot_bytes(int max_points, int max_links, int lps
 // gathers points of similar height); tb[2t], tb[2t+1] are the min / max corners of the offsets r
 // of its points, and c_z + min over that box of (R r)_z bounds their heights from below.
 template <int LPS>
-__device__ __noinline__ void tile_bounds(const float4 *pts, int np, float4 *tb, int gl) {
+__device__ __noinline__ float tile_bounds(const float4 *pts, int np, float4 *tb, int gl) {
     __syncwarp();
     const int nt = (np + LPS - 1) / LPS;
+    float r2 = 0.f;
     for (int t = gl; t < nt; t += LPS) {
         float4 lo = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
         float4 hi = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
-        const int e = min(np, (t + 1) * LPS);
-        for (int i = t * LPS; i < e; ++i) {
-            const float4 r = pts[i];
+        const int b = t * LPS, n = min(np, b + LPS) - b;
+#pragma unroll 4
+        for (int j = 0; j < n; ++j) {
+            // in full tiles each lane starts at a different point, so the group's loads hit
+            // distinct banks
+            const float4 r = pts[b + (n == LPS ? ((j + gl) & (LPS - 1)) : j)];
             lo.x = fminf(lo.x, r.x); lo.y = fminf(lo.y, r.y); lo.z = fminf(lo.z, r.z);
             hi.x = fmaxf(hi.x, r.x); hi.y = fmaxf(hi.y, r.y); hi.z = fmaxf(hi.z, r.z);
+            r2 = fmaxf(r2, r.x * r.x + r.y * r.y + r.z * r.z);
         }
         tb[2 * t] = lo;
         tb[2 * t + 1] = hi;
     }
+#pragma unroll
+    for (int o = LPS / 2; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(FULL_MASK, r2, o));
     __syncwarp();
+    return sqrtf(r2);   // the largest |r| of the scene's points (a bound for the cull margin)
 }
 
 // Tiles that may hold a point at or below the highest ground hmax: every lane tests the boxes of
-// its tiles (t = gl, gl + LPS, ...) and a ballot gathers the group's answers into a mask.
+// its tiles (t = gl, gl + LPS, ...) and ballots gather the group's answers into a mask.  The
+// contact mask holds at most 64 tiles, so there are at most 64 / LPS rounds: all box tests are
+// issued first (independent shared-memory loads), then the ballots.
 template <int LPS>
-__device__ __forceinline__ uint64_t tiles_near_ground(const float4 *tb, int ntiles, int ntiles_warp,
-                                                      const float R[9], float cz, float hmax, int gl) {
-    uint64_t mask = 0;
+__device__ __forceinline__ uint64_t tiles_near_ground(const float4 *tb, int ntiles, const float R[9], float cz,
+                                                      float hmax, int gl) {
+    constexpr int ROUNDS = 64 / LPS;
     const int g = (threadIdx.x & 31) / LPS;
-    for (int t0 = 0; t0 < ntiles_warp; t0 += LPS) {   // warp-uniform trip count
-        const int t = t0 + gl;
-        bool near = false;
+    bool near[ROUNDS];
+#pragma unroll
+    for (int r = 0; r < ROUNDS; ++r) {
+        const int t = r * LPS + gl;
+        near[r] = false;
         if (t < ntiles) {
             const float4 lo = tb[2 * t], hi = tb[2 * t + 1];
             const float zb = cz + fminf(R[6] * lo.x, R[6] * hi.x) + fminf(R[7] * lo.y, R[7] * hi.y) +
                              fminf(R[8] * lo.z, R[8] * hi.z);
-            near = zb <= hmax;
+            near[r] = zb <= hmax;
         }
-        const uint32_t bal = __ballot_sync(FULL_MASK, near);
+    }
+    uint64_t mask = 0;
+#pragma unroll
+    for (int r = 0; r < ROUNDS; ++r) {
+        const uint32_t bal = __ballot_sync(FULL_MASK, near[r]);
         const uint64_t mine = (bal >> (g * LPS)) & (LPS == 32 ? 0xffffffffu : ((1u << LPS) - 1u));
-        mask |= mine << t0;
+        mask |= mine << (r * LPS);
     }
     return mask;
 }
@@ -423,16 +394,21 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
     __syncwarp();
     Shape sh;
     shape_update<LPS>(W, valid ? s : 0, p0, np, l0, nl, th, fr, pts, gl, sh);
-    tile_bounds<LPS>(pts, np, tb, gl);
+    float rmax = tile_bounds<LPS>(pts, np, tb, gl);
     // highest ground a point can meet (plus a margin for the rounding of the bound)
     const float hmax = (FLAT || hm < 0 ? 0.f : W.hm_max[hm]) + 1e-5f;
     const int ntiles = (np + LPS - 1) / LPS;
-    int ntiles_warp = ntiles;   // the warp's largest tile count (uniform loop bound)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ntiles_warp = max(ntiles_warp, __shfl_xor_sync(FULL_MASK, ntiles_warp, o));
 
     const float dt = W.dt, idt = 1.0f / W.dt, kw2 = W.kw2, kc = W.kc;
+    float iM = 1.0f / sh.M;
     const bool actuated = W.act_mode != 0;
+    // Candidate tiles: those whose box came within CULL_MARGIN of the highest ground at the last
+    // cull.  slack is CULL_MARGIN minus a bound on how far any point has moved down since then
+    // (integration only: the friction corrections move the robot horizontally and rotate it about
+    // the vertical); while it is >= 0 no other tile can have reached the ground, so the set stays
+    // exact and the boxes are tested again only when it runs out or the shape changes.
+    float slack = -1.f;
+    uint64_t cand = 0;
     int ph = (int)(step0 % (long long)W.K);
     for (int t = 0; t < n_steps; ++t) {
         const long long n = step0 + t;
@@ -454,61 +430,105 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             }
             __syncwarp();
             shape_update<LPS>(W, valid ? s : 0, p0, np, l0, nl, th, fr, pts, gl, sh);
-            tile_bounds<LPS>(pts, np, tb, gl);
+            rmax = tile_bounds<LPS>(pts, np, tb, gl);
+            iM = 1.0f / sh.M;
+            slack = -1.f;   // the tiles moved: cull again
         }
 
         float om[3];
         world_sym(R, sh.Ii, L, om);
 
-        // -- pass 1: collision against the ground and penalty normal forces.  For the points in
-        //    contact in both steps (the friction set C, Sec. III-C) it also sums the count, first
-        //    and second moments of rho = R r about the reference point o (last step's centroid):
-        //    every term of the dynamic least squares is a function of these (see below).
-        uint64_t know = 0;
-        float red[3] = {0.f, 0.f, 0.f};
-        Moments mc = {0.f, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}};
-        for (uint64_t tm = tiles_near_ground<LPS>(tb, ntiles, ntiles_warp, R, c[2], hmax, gl); tm;
-             tm &= tm - 1) {
-            const int k = __ffsll((long long)tm) - 1;
-            const int i = gl + k * LPS;
-            if (i >= np) continue;
-            const float4 r = pts[i];
-            const float rz = R[6] * r.x + R[7] * r.y + R[8] * r.z;
-            const float z = c[2] + rz;
-            float rx = 0.f, ry = 0.f, h = 0.f;
-            if (!FLAT) {
-                rx = R[0] * r.x + R[1] * r.y + R[2] * r.z;
-                ry = R[3] * r.x + R[4] * r.y + R[5] * r.z;
-                h = ground<FLAT>(W, hm, c[0] + rx, c[1] + ry);
-            }
-            if (z < h) {
-                know |= 1ull << k;
-                if (FLAT) {
-                    rx = R[0] * r.x + R[1] * r.y + R[2] * r.z;
-                    ry = R[3] * r.x + R[4] * r.y + R[5] * r.z;
-                }
-                const float vz = v[2] + (om[0] * ry - om[1] * rx);
-                const float F = fmaxf(0.f, r.w * (kw2 * (h - z) - kc * vz));
-                red[0] += F;
-                red[1] += ry * F;
-                red[2] -= rx * F;
-                if ((kprev >> k) & 1ull) {
-                    const float rho[3] = {rx, ry, rz};
-                    moments_add(mc, rho);
-                }
-            }
+        // -- pass 1: collision against the ground and penalty normal forces over the candidate
+        //    tiles.  For the points in contact in both steps (the friction set C, Sec. III-C) a
+        //    second loop sums the count, the first and the second moments of d = rho - o,
+        //    rho = R r, about a reference point o near them: every term of the dynamic least
+        //    squares is a function of these (see below).  All sums are independent, so the group
+        //    reduction is one butterfly and every lane ends with bit-identical values.
+        // the cull's ballots involve the whole warp: every group culls when any one needs to
+        if (__any_sync(FULL_MASK, slack < 0.f)) {
+            cand = tiles_near_ground<LPS>(tb, ntiles, R, c[2], hmax + CULL_MARGIN, gl);
+            slack = CULL_MARGIN;
         }
-        moments_reduce<LPS>(mc, red);
-        const float FN = red[0];
+        uint64_t know = 0;
+        // FN, tau_x, tau_y | n | sum d (3) | sum d d^T (xx yy zz xy xz yz)
+        float acc[13] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        // two tiles per iteration: two independent chains (a point that is absent or not in
+        // contact adds an exact zero, so the sums see the same terms in the same order)
+        for (uint64_t tm = cand; tm;) {
+            const int ka = __ffsll((long long)tm) - 1;
+            tm &= tm - 1;
+            const bool two = tm != 0;
+            const int kb = two ? __ffsll((long long)tm) - 1 : ka;
+            if (two) tm &= tm - 1;
+            const int ia = gl + ka * LPS, ib = gl + kb * LPS;
+            const bool oka = ia < np, okb = two && ib < np;
+            const float4 pa = pts[oka ? ia : 0], pb = pts[okb ? ib : 0];
+            const float rxa = R[0] * pa.x + R[1] * pa.y + R[2] * pa.z, rxb = R[0] * pb.x + R[1] * pb.y + R[2] * pb.z;
+            const float rya = R[3] * pa.x + R[4] * pa.y + R[5] * pa.z, ryb = R[3] * pb.x + R[4] * pb.y + R[5] * pb.z;
+            const float rza = R[6] * pa.x + R[7] * pa.y + R[8] * pa.z, rzb = R[6] * pb.x + R[7] * pb.y + R[8] * pb.z;
+            const float za = c[2] + rza, zb = c[2] + rzb;
+            const float ha = ground<FLAT>(W, hm, c[0] + rxa, c[1] + rya);
+            const float hb = ground<FLAT>(W, hm, c[0] + rxb, c[1] + ryb);
+            const bool ca = oka && za < ha, cb = okb && zb < hb;
+            const float vza = v[2] + (om[0] * rya - om[1] * rxa), vzb = v[2] + (om[0] * ryb - om[1] * rxb);
+            const float Fa = ca ? fmaxf(0.f, pa.w * (kw2 * (ha - za) - kc * vza)) : 0.f;
+            const float Fb = cb ? fmaxf(0.f, pb.w * (kw2 * (hb - zb) - kc * vzb)) : 0.f;
+            if (ca) know |= 1ull << ka;
+            if (cb) know |= 1ull << kb;
+            acc[0] += Fa; acc[1] += rya * Fa; acc[2] -= rxa * Fa;
+            acc[0] += Fb; acc[1] += ryb * Fb; acc[2] -= rxb * Fb;
+        }
+        // moments of the friction set C about o, the rotated centre of the first tile holding a
+        // point of C (a function of C and the state alone)
+        const uint64_t cset = kprev & know;
+        int kf = cset ? __ffsll((long long)cset) - 1 : 64;
+#pragma unroll
+        for (int ofs = LPS / 2; ofs > 0; ofs >>= 1) kf = min(kf, __shfl_xor_sync(FULL_MASK, kf, ofs));
+        float o[3] = {0.f, 0.f, 0.f};
+        if (kf < 64) {
+            const float4 lo = tb[2 * kf], hi = tb[2 * kf + 1];
+            const float mid[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
+            mat_vec(R, mid, o);
+        }
+        for (uint64_t cm = cset; cm;) {
+            const int ka = __ffsll((long long)cm) - 1;
+            cm &= cm - 1;
+            const bool two = cm != 0;
+            const int kb = two ? __ffsll((long long)cm) - 1 : ka;
+            if (two) cm &= cm - 1;
+            const float4 pa = pts[gl + ka * LPS], pb = pts[gl + kb * LPS];
+            const float wb = two ? 1.f : 0.f;
+            const float a0 = (R[0] * pa.x + R[1] * pa.y + R[2] * pa.z) - o[0];
+            const float a1 = (R[3] * pa.x + R[4] * pa.y + R[5] * pa.z) - o[1];
+            const float a2 = (R[6] * pa.x + R[7] * pa.y + R[8] * pa.z) - o[2];
+            const float b0 = wb * ((R[0] * pb.x + R[1] * pb.y + R[2] * pb.z) - o[0]);
+            const float b1 = wb * ((R[3] * pb.x + R[4] * pb.y + R[5] * pb.z) - o[1]);
+            const float b2 = wb * ((R[6] * pb.x + R[7] * pb.y + R[8] * pb.z) - o[2]);
+            acc[3] += 1.f; acc[3] += wb;
+            acc[4] += a0; acc[5] += a1; acc[6] += a2;
+            acc[4] += b0; acc[5] += b1; acc[6] += b2;
+            acc[7] += a0 * a0; acc[8] += a1 * a1; acc[9] += a2 * a2;
+            acc[10] += a0 * a1; acc[11] += a0 * a2; acc[12] += a1 * a2;
+            acc[7] += b0 * b0; acc[8] += b1 * b1; acc[9] += b2 * b2;
+            acc[10] += b0 * b1; acc[11] += b0 * b2; acc[12] += b1 * b2;
+        }
+        gsum<LPS, 13>(acc);
+        const float FN = acc[0];
+        // friction set: count, centroid of rho and second central moments sum (rho - gb)(rho - gb)^T
+        const float nC = acc[3];
+        const float in = nC > 0.f ? __fdividef(1.f, nC) : 0.f;
+        const float e0 = acc[4] * in, e1 = acc[5] * in, e2 = acc[6] * in;   // centroid - o
+        const float gb[3] = {o[0] + e0, o[1] + e1, o[2] + e2};
+        const Sym M2 = {acc[7] - nC * (e0 * e0), acc[8] - nC * (e1 * e1), acc[9] - nC * (e2 * e2),
+                        acc[10] - nC * (e0 * e1), acc[11] - nC * (e0 * e2), acc[12] - nC * (e1 * e2)};
 
         // -- semi-implicit Euler
         float vs[3], Ls[3], cs[3], qs[4], oms[3];
-        const float iM = 1.0f / sh.M;
         vs[0] = v[0] + dt * W.gx;
         vs[1] = v[1] + dt * W.gy;
         vs[2] = v[2] + dt * (W.gz + FN * iM);
-        Ls[0] = L[0] + dt * red[1];
-        Ls[1] = L[1] + dt * red[2];
+        Ls[0] = L[0] + dt * acc[1];
+        Ls[1] = L[1] + dt * acc[2];
         Ls[2] = L[2];
         world_sym(R, sh.Ii, Ls, oms);
         cs[0] = c[0] + dt * vs[0]; cs[1] = c[1] + dt * vs[1]; cs[2] = c[2] + dt * vs[2];
@@ -519,13 +539,14 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         {
             const float px = dt * oms[0], py = dt * oms[1], pz = dt * oms[2];
             const float a2 = px * px + py * py + pz * pz;
-            const float a = sqrtf(a2);
+            const float ra = a2 > 0.f ? rsqrtf(a2) : 0.f;   // 1 / |u|
+            const float a = a2 * ra;
             float dq[4] = {1.f, 0.f, 0.f, 0.f};
             float fa = 1.f, fb = 0.5f;
             if (a > 0.f) {
                 float sn, cn;
                 sincos_small(0.5f * a, &sn, &cn);
-                const float f = sn / a;
+                const float f = sn * ra;
                 dq[0] = cn; dq[1] = f * px; dq[2] = f * py; dq[3] = f * pz;
                 fa = 2.f * f * cn;
                 fb = 2.f * f * f;
@@ -536,6 +557,9 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             quat_mul(dq, q, qs);
             const float inv = rsqrtf(qs[0] * qs[0] + qs[1] * qs[1] + qs[2] * qs[2] + qs[3] * qs[3]);
             qs[0] *= inv; qs[1] *= inv; qs[2] *= inv; qs[3] *= inv;
+            // largest downward move of any point this step: dt max(0, -v*_z) from the CoG plus
+            // |(dR - 1) R r| <= |u| |r| from the rotation (with a small factor for rounding)
+            slack -= fmaxf(0.f, -dt * vs[2]) + 1.0001f * a * rmax;
         }
 
         // -- friction (Sec. III-C, Eqs. 1-6) over C.  With d_i = rho_i - centroid and
@@ -544,9 +568,6 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         //      S2 = a_x^T M2 a_x + a_y^T M2 a_y,  sum s~ x e = -(a_x^T M2 b_y - a_y^T M2 b_x),
         //      mean e = -dt v*_xy - [D centroid]_xy
         //    with a_x, a_y the x, y rows of (1 + D) and b_x, b_y those of D.
-        const float nC = mc.n;
-        const float in = nC > 0.f ? 1.0f / nC : 0.f;
-        const float gb[3] = {mc.m[0], mc.m[1], mc.m[2]};   // centroid of rho over C
         float cn[3] = {cs[0], cs[1], cs[2]}, vn[3] = {vs[0], vs[1], vs[2]};
         float Ln[3] = {Ls[0], Ls[1], Ls[2]}, qn[4] = {qs[0], qs[1], qs[2], qs[3]};
         // kinematic least squares (joint-update steps): a second pass over C about the exact
@@ -574,7 +595,6 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             gsum<LPS, 6>(f6);
         }
         if (nC >= 1.f) {
-            const Sym M2 = {mc.M[0], mc.M[1], mc.M[2], mc.M[3], mc.M[4], mc.M[5]};
             const float ax[3] = {1.f + Dm[0], Dm[1], Dm[2]}, ay[3] = {Dm[3], 1.f + Dm[4], Dm[5]};
             const float bx[3] = {Dm[0], Dm[1], Dm[2]}, by[3] = {Dm[3], Dm[4], Dm[5]};
             float Max[3], May[3];
@@ -590,15 +610,17 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             const float tDy = -dt * vs[1] - (by[0] * gb[0] + by[1] * gb[1] + by[2] * gb[2]);
             float a3 = (nC >= 2.f && S2 > 1e-12f) ? __fdividef(X, S2) : 0.f;
             a3 = fminf(fmaxf(a3, -1.f), 1.f);
-            const float cD = sqrtf(fmaxf(0.f, 1.f - a3 * a3));
-            const float cm1 = -a3 * a3 / (1.f + cD);                  // cos(alpha_D) - 1
+            const float t1 = fmaxf(0.f, 1.f - a3 * a3);
+            const float cD = t1 > 0.f ? t1 * rsqrtf(t1) : 0.f;       // cos(alpha_D)
+            const float r1 = __fdividef(1.f, 1.f + cD);
+            const float cm1 = -a3 * a3 * r1;                          // cos(alpha_D) - 1
             const float dDx = -sbx, dDy = -sby;                       // CoG minus centroid
             const float DDx = tDx + cm1 * dDx - a3 * dDy;             // uncapped CoG shift
             const float DDy = tDy + a3 * dDx + cm1 * dDy;
             // maximum static friction (Coulomb cap on the impulse that undoes the slip)
-            const float sh2 = a3 * a3 / (2.f * (1.f + cD));            // sin^2(alpha_D / 2)
+            const float sh2 = 0.5f * a3 * a3 * r1;                    // sin^2(alpha_D / 2)
             const float u2 = tDx * tDx + tDy * tDy + 4.f * sh2 * S2 * in;
-            const float Jreq = sh.M * sqrtf(u2) * idt;
+            const float Jreq = sh.M * (u2 > 0.f ? u2 * rsqrtf(u2) : 0.f) * idt;
             const float Jmax = mu * dt * FN;
             const float sc = (Jreq <= Jmax) ? 1.f : __fdividef(Jmax, Jreq);
             const float aD = asin_small(a3);
@@ -613,7 +635,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
                 const float S2K = f6[2] - nC * (kbx * kbx + kby * kby);
                 const float tKx = f6[3] * in, tKy = f6[4] * in;
                 const float XK = f6[5] - (kbx * f6[4] - kby * f6[3]);
-                float a3K = (nC >= 2.f && S2K > 1e-12f) ? XK / S2K : 0.f;
+                float a3K = (nC >= 2.f && S2K > 1e-12f) ? __fdividef(XK, S2K) : 0.f;
                 a3K = fminf(fmaxf(a3K, -1.f), 1.f);
                 const float aK = asin_small(a3K);
                 float s2, c2;
