@@ -274,6 +274,14 @@ __device__ __noinline__ void link_frames(const WorldDev &W, int l0, int nl, cons
     }
 }
 
+// 16-byte asynchronous copy global -> shared (cp.async, completes at cp_async_wait_all)
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+                 "l"(gmem_src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ void fk_point(const float *fr, float4 a, int l, float p[3]) {
     const float *F = fr + 12 * l;
     p[0] = F[0] * a.x + F[1] * a.y + F[2] * a.z + F[9];
@@ -296,14 +304,25 @@ template <int LPS>
 __device__ __noinline__ void shape_update(const WorldDev &W, int s, int p0, int np, int l0, int nl,
                                           const float *th, float *fr, float4 *pts, int gl,
                                           Shape &sh) {
+    // the construction positions and masses go straight into the offsets array (asynchronous
+    // copies, all in flight at once) and the points' links into the tile-box area (rebuilt after
+    // every shape update) while the link frames are built
+    uint8_t *lk = reinterpret_cast<uint8_t *>(pts) + tiles_offset(W.max_points, W.max_links);
+#pragma unroll 8
+    for (int i = gl; i < np; i += LPS) {
+        cp_async16(pts + i, W.p0m + p0 + i);
+        lk[i] = W.plink[p0 + i];
+    }
     link_frames<LPS>(W, l0, nl, th, fr, gl);
+    cp_async_wait_all();
+    __syncwarp();
     const float gref[3] = {W.gref[3 * s], W.gref[3 * s + 1], W.gref[3 * s + 2]};
     float a[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll 4
     for (int i = gl; i < np; i += LPS) {
-        const float4 q = W.p0m[p0 + i];
+        const float4 q = pts[i];
         float p[3];
-        fk_point(fr, q, W.plink[p0 + i], p);
+        fk_point(fr, q, lk[i], p);
         const float dx = p[0] - gref[0], dy = p[1] - gref[1], dz = p[2] - gref[2], m = q.w;
         pts[i] = make_float4(dx, dy, dz, m);
         a[0] += m;
@@ -389,6 +408,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
     }
     for (int j = gl; j < nj; j += LPS) th[j] = W.theta[j0 + j];
     uint64_t kprev = 0;
+#pragma unroll 8
     for (int k = 0, i = gl; i < np; ++k, i += LPS)
         if (W.kappa[p0 + i]) kprev |= 1ull << k;
     __syncwarp();
@@ -449,35 +469,40 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             cand = tiles_near_ground<LPS>(tb, ntiles, R, c[2], hmax + CULL_MARGIN, gl);
             slack = CULL_MARGIN;
         }
-        uint64_t know = 0;
         // FN, tau_x, tau_y | n | sum d (3) | sum d d^T (xx yy zz xy xz yz)
         float acc[13] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        // two tiles per iteration: two independent chains (a point that is absent or not in
-        // contact adds an exact zero, so the sums see the same terms in the same order)
-        for (uint64_t tm = cand; tm;) {
-            const int ka = __ffsll((long long)tm) - 1;
-            tm &= tm - 1;
-            const bool two = tm != 0;
-            const int kb = two ? __ffsll((long long)tm) - 1 : ka;
-            if (two) tm &= tm - 1;
-            const int ia = gl + ka * LPS, ib = gl + kb * LPS;
-            const bool oka = ia < np, okb = two && ib < np;
-            const float4 pa = pts[oka ? ia : 0], pb = pts[okb ? ib : 0];
-            const float rxa = R[0] * pa.x + R[1] * pa.y + R[2] * pa.z, rxb = R[0] * pb.x + R[1] * pb.y + R[2] * pb.z;
-            const float rya = R[3] * pa.x + R[4] * pa.y + R[5] * pa.z, ryb = R[3] * pb.x + R[4] * pb.y + R[5] * pb.z;
-            const float rza = R[6] * pa.x + R[7] * pa.y + R[8] * pa.z, rzb = R[6] * pb.x + R[7] * pb.y + R[8] * pb.z;
-            const float za = c[2] + rza, zb = c[2] + rzb;
-            const float ha = ground<FLAT>(W, hm, c[0] + rxa, c[1] + rya);
-            const float hb = ground<FLAT>(W, hm, c[0] + rxb, c[1] + ryb);
-            const bool ca = oka && za < ha, cb = okb && zb < hb;
-            const float vza = v[2] + (om[0] * rya - om[1] * rxa), vzb = v[2] + (om[0] * ryb - om[1] * rxb);
-            const float Fa = ca ? fmaxf(0.f, pa.w * (kw2 * (ha - za) - kc * vza)) : 0.f;
-            const float Fb = cb ? fmaxf(0.f, pb.w * (kw2 * (hb - zb) - kc * vzb)) : 0.f;
-            if (ca) know |= 1ull << ka;
-            if (cb) know |= 1ull << kb;
-            acc[0] += Fa; acc[1] += rya * Fa; acc[2] -= rxa * Fa;
-            acc[0] += Fb; acc[1] += ryb * Fb; acc[2] -= rxb * Fb;
+        // The 64-bit tile masks are walked as two 32-bit words (hexapod candidates sit in the low
+        // word: points are stored by construction height).  Two tiles per iteration: two
+        // independent chains; a point that is absent or not in contact adds an exact zero, so the
+        // sums see the same terms in the same order.
+        uint32_t knw[2] = {0u, 0u};
+#pragma unroll
+        for (int hw = 0; hw < 2; ++hw) {
+            for (uint32_t tm = (uint32_t)(cand >> (32 * hw)); tm;) {
+                const int ja = __ffs(tm) - 1;
+                tm &= tm - 1;
+                const bool two = tm != 0;
+                const int jb = two ? __ffs(tm) - 1 : ja;
+                if (two) tm &= tm - 1;
+                const int ia = gl + (ja + 32 * hw) * LPS, ib = gl + (jb + 32 * hw) * LPS;
+                const bool oka = ia < np, okb = two && ib < np;
+                const float4 pa = pts[oka ? ia : 0], pb = pts[okb ? ib : 0];
+                const float rxa = R[0] * pa.x + R[1] * pa.y + R[2] * pa.z, rxb = R[0] * pb.x + R[1] * pb.y + R[2] * pb.z;
+                const float rya = R[3] * pa.x + R[4] * pa.y + R[5] * pa.z, ryb = R[3] * pb.x + R[4] * pb.y + R[5] * pb.z;
+                const float rza = R[6] * pa.x + R[7] * pa.y + R[8] * pa.z, rzb = R[6] * pb.x + R[7] * pb.y + R[8] * pb.z;
+                const float za = c[2] + rza, zb = c[2] + rzb;
+                const float ha = ground<FLAT>(W, hm, c[0] + rxa, c[1] + rya);
+                const float hb = ground<FLAT>(W, hm, c[0] + rxb, c[1] + ryb);
+                const bool ca = oka && za < ha, cb = okb && zb < hb;
+                const float vza = v[2] + (om[0] * rya - om[1] * rxa), vzb = v[2] + (om[0] * ryb - om[1] * rxb);
+                const float Fa = ca ? fmaxf(0.f, pa.w * (kw2 * (ha - za) - kc * vza)) : 0.f;
+                const float Fb = cb ? fmaxf(0.f, pb.w * (kw2 * (hb - zb) - kc * vzb)) : 0.f;
+                knw[hw] |= (ca ? 1u << ja : 0u) | (cb ? 1u << jb : 0u);
+                acc[0] += Fa; acc[1] += rya * Fa; acc[2] -= rxa * Fa;
+                acc[0] += Fb; acc[1] += ryb * Fb; acc[2] -= rxb * Fb;
+            }
         }
+        const uint64_t know = (uint64_t)knw[0] | ((uint64_t)knw[1] << 32);
         // moments of the friction set C about o, the rotated centre of the first tile holding a
         // point of C (a function of C and the state alone)
         const uint64_t cset = kprev & know;
@@ -490,27 +515,30 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             const float mid[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
             mat_vec(R, mid, o);
         }
-        for (uint64_t cm = cset; cm;) {
-            const int ka = __ffsll((long long)cm) - 1;
-            cm &= cm - 1;
-            const bool two = cm != 0;
-            const int kb = two ? __ffsll((long long)cm) - 1 : ka;
-            if (two) cm &= cm - 1;
-            const float4 pa = pts[gl + ka * LPS], pb = pts[gl + kb * LPS];
-            const float wb = two ? 1.f : 0.f;
-            const float a0 = (R[0] * pa.x + R[1] * pa.y + R[2] * pa.z) - o[0];
-            const float a1 = (R[3] * pa.x + R[4] * pa.y + R[5] * pa.z) - o[1];
-            const float a2 = (R[6] * pa.x + R[7] * pa.y + R[8] * pa.z) - o[2];
-            const float b0 = wb * ((R[0] * pb.x + R[1] * pb.y + R[2] * pb.z) - o[0]);
-            const float b1 = wb * ((R[3] * pb.x + R[4] * pb.y + R[5] * pb.z) - o[1]);
-            const float b2 = wb * ((R[6] * pb.x + R[7] * pb.y + R[8] * pb.z) - o[2]);
-            acc[3] += 1.f; acc[3] += wb;
-            acc[4] += a0; acc[5] += a1; acc[6] += a2;
-            acc[4] += b0; acc[5] += b1; acc[6] += b2;
-            acc[7] += a0 * a0; acc[8] += a1 * a1; acc[9] += a2 * a2;
-            acc[10] += a0 * a1; acc[11] += a0 * a2; acc[12] += a1 * a2;
-            acc[7] += b0 * b0; acc[8] += b1 * b1; acc[9] += b2 * b2;
-            acc[10] += b0 * b1; acc[11] += b0 * b2; acc[12] += b1 * b2;
+#pragma unroll
+        for (int hw = 0; hw < 2; ++hw) {
+            for (uint32_t cm = (uint32_t)(cset >> (32 * hw)); cm;) {
+                const int ja = __ffs(cm) - 1;
+                cm &= cm - 1;
+                const bool two = cm != 0;
+                const int jb = two ? __ffs(cm) - 1 : ja;
+                if (two) cm &= cm - 1;
+                const float4 pa = pts[gl + (ja + 32 * hw) * LPS], pb = pts[gl + (jb + 32 * hw) * LPS];
+                const float wb = two ? 1.f : 0.f;
+                const float a0 = (R[0] * pa.x + R[1] * pa.y + R[2] * pa.z) - o[0];
+                const float a1 = (R[3] * pa.x + R[4] * pa.y + R[5] * pa.z) - o[1];
+                const float a2 = (R[6] * pa.x + R[7] * pa.y + R[8] * pa.z) - o[2];
+                const float b0 = wb * ((R[0] * pb.x + R[1] * pb.y + R[2] * pb.z) - o[0]);
+                const float b1 = wb * ((R[3] * pb.x + R[4] * pb.y + R[5] * pb.z) - o[1]);
+                const float b2 = wb * ((R[6] * pb.x + R[7] * pb.y + R[8] * pb.z) - o[2]);
+                acc[3] += 1.f; acc[3] += wb;
+                acc[4] += a0; acc[5] += a1; acc[6] += a2;
+                acc[4] += b0; acc[5] += b1; acc[6] += b2;
+                acc[7] += a0 * a0; acc[8] += a1 * a1; acc[9] += a2 * a2;
+                acc[10] += a0 * a1; acc[11] += a0 * a2; acc[12] += a1 * a2;
+                acc[7] += b0 * b0; acc[8] += b1 * b1; acc[9] += b2 * b2;
+                acc[10] += b0 * b1; acc[11] += b0 * b2; acc[12] += b1 * b2;
+            }
         }
         gsum<LPS, 13>(acc);
         const float FN = acc[0];
@@ -557,9 +585,11 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             quat_mul(dq, q, qs);
             const float inv = rsqrtf(qs[0] * qs[0] + qs[1] * qs[1] + qs[2] * qs[2] + qs[3] * qs[3]);
             qs[0] *= inv; qs[1] *= inv; qs[2] *= inv; qs[3] *= inv;
-            // largest downward move of any point this step: dt max(0, -v*_z) from the CoG plus
-            // |(dR - 1) R r| <= |u| |r| from the rotation (with a small factor for rounding)
-            slack -= fmaxf(0.f, -dt * vs[2]) + 1.0001f * a * rmax;
+            // largest downward move of any point this step: dt max(0, -v*_z) from the CoG plus the
+            // rotation's: for x = R r, ((dR - 1) x)_z = sin|u| (n x x)_z + (1 - cos|u|) (n (n.x) - x)_z
+            // with n = u / |u|, so |dz| <= (|u_xy| + |u|^2 / 2) |x| (yaw moves no point up or
+            // down; |u_xy| <= |u_x| + |u_y|); a small factor covers rounding
+            slack -= fmaxf(0.f, -dt * vs[2]) + 1.0001f * (fabsf(px) + fabsf(py) + 0.5f * a2) * rmax;
         }
 
         // -- friction (Sec. III-C, Eqs. 1-6) over C.  With d_i = rho_i - centroid and
