@@ -124,7 +124,12 @@ __device__ __forceinline__ void quat_mul(const float a[4], const float b[4], flo
 // exact to single precision (first omitted terms x^7/5040, x^8/40320 and 35 x^9/1152 are below
 // 1e-12); outside it the library functions are used.  Per-step rotation increments and friction
 // corrections are almost always tiny, so this removes the range reduction from the hot path.
-__device__ __noinline__ void sincos_large(float x, float *s, float *c) { sincosf(x, s, c); }
+// (returned by value: a pointer into the caller would force its results into local memory)
+__device__ __noinline__ float2 sincos_large(float x) {
+    float s, c;
+    sincosf(x, &s, &c);
+    return make_float2(s, c);
+}
 __device__ __noinline__ float asin_large(float x) { return asinf(x); }
 
 __device__ __forceinline__ void sincos_small(float x, float *s, float *c) {
@@ -133,7 +138,9 @@ __device__ __forceinline__ void sincos_small(float x, float *s, float *c) {
         *s = x * fmaf(x2, fmaf(x2, 1.f / 120.f, -1.f / 6.f), 1.f);
         *c = fmaf(x2, fmaf(x2, fmaf(x2, -1.f / 720.f, 1.f / 24.f), -0.5f), 1.f);
     } else {
-        sincos_large(x, s, c);
+        const float2 sc = sincos_large(x);
+        *s = sc.x;
+        *c = sc.y;
     }
 }
 
@@ -415,12 +422,15 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
     Shape sh;
     shape_update<LPS>(W, valid ? s : 0, p0, np, l0, nl, th, fr, pts, gl, sh);
     float rmax = tile_bounds<LPS>(pts, np, tb, gl);
+    // sh is written by the (out-of-line) shape update through a reference, so it lives in local
+    // memory; the step loop reads this register copy
+    Shape shr = sh;
     // highest ground a point can meet (plus a margin for the rounding of the bound)
     const float hmax = (FLAT || hm < 0 ? 0.f : W.hm_max[hm]) + 1e-5f;
     const int ntiles = (np + LPS - 1) / LPS;
 
     const float dt = W.dt, idt = 1.0f / W.dt, kw2 = W.kw2, kc = W.kc;
-    float iM = 1.0f / sh.M;
+    float iM = 1.0f / shr.M;
     const bool actuated = W.act_mode != 0;
     // Candidate tiles: those whose box came within CULL_MARGIN of the highest ground at the last
     // cull.  slack is CULL_MARGIN minus a bound on how far any point has moved down since then
@@ -439,8 +449,9 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
 
         // -- joint-angle determination: new angles, frames, mass properties and offsets; the
         //    old angles and CoG are kept for the kinematic slip of the contact points
-        float gold[3] = {sh.g[0], sh.g[1], sh.g[2]};
+        float gold[3] = {0.f, 0.f, 0.f};
         if (tick) {
+            gold[0] = shr.g[0]; gold[1] = shr.g[1]; gold[2] = shr.g[2];
             for (int j = gl; j < nj; j += LPS) {
                 th_old[j] = th[j];
                 if (status == 0u) {   // a frozen scene keeps its angles
@@ -451,12 +462,13 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             __syncwarp();
             shape_update<LPS>(W, valid ? s : 0, p0, np, l0, nl, th, fr, pts, gl, sh);
             rmax = tile_bounds<LPS>(pts, np, tb, gl);
-            iM = 1.0f / sh.M;
+            shr = sh;
+            iM = 1.0f / shr.M;
             slack = -1.f;   // the tiles moved: cull again
         }
 
         float om[3];
-        world_sym(R, sh.Ii, L, om);
+        world_sym(R, shr.Ii, L, om);
 
         // -- pass 1: collision against the ground and penalty normal forces over the candidate
         //    tiles.  For the points in contact in both steps (the friction set C, Sec. III-C) a
@@ -558,7 +570,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         Ls[0] = L[0] + dt * acc[1];
         Ls[1] = L[1] + dt * acc[2];
         Ls[2] = L[2];
-        world_sym(R, sh.Ii, Ls, oms);
+        world_sym(R, shr.Ii, Ls, oms);
         cs[0] = c[0] + dt * vs[0]; cs[1] = c[1] + dt * vs[1]; cs[2] = c[2] + dt * vs[2];
         // rotation increment dR = exp([u]x), u = dt w*: q* = dq (x) q and R* = dR R, so a point's
         // offset moves from rho to (1 + D) rho with D = dR - 1 = a [u]x + b [u]x^2
@@ -650,7 +662,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             // maximum static friction (Coulomb cap on the impulse that undoes the slip)
             const float sh2 = 0.5f * a3 * a3 * r1;                    // sin^2(alpha_D / 2)
             const float u2 = tDx * tDx + tDy * tDy + 4.f * sh2 * S2 * in;
-            const float Jreq = sh.M * (u2 > 0.f ? u2 * rsqrtf(u2) : 0.f) * idt;
+            const float Jreq = shr.M * (u2 > 0.f ? u2 * rsqrtf(u2) : 0.f) * idt;
             const float Jmax = mu * dt * FN;
             const float sc = (Jreq <= Jmax) ? 1.f : __fdividef(Jmax, Jreq);
             const float aD = asin_small(a3);
@@ -687,7 +699,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             quat_mat(qs, Rs);
             const float ez[3] = {0.f, 0.f, 1.f};
             float Iz[3];
-            world_sym(Rs, sh.Ib, ez, Iz);
+            world_sym(Rs, shr.Ib, ez, Iz);
             const float w = sc * aD * idt;
             Ln[0] = Ls[0] + w * Iz[0]; Ln[1] = Ls[1] + w * Iz[1]; Ln[2] = Ls[2] + w * Iz[2];
             float sa, ca;
@@ -739,7 +751,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         W.st[ST_LX * S + s] = L[0]; W.st[ST_LY * S + s] = L[1]; W.st[ST_LZ * S + s] = L[2];
         float R[9], om[3];
         quat_mat(q, R);
-        world_sym(R, sh.Ii, L, om);
+        world_sym(R, shr.Ii, L, om);
         W.omega[s] = om[0]; W.omega[S + s] = om[1]; W.omega[2 * S + s] = om[2];
         W.sensors[s] = sens;
         W.status[s] = status;
@@ -748,7 +760,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
 }
 
 template <int LPS, bool FLAT>
-__global__ void __launch_bounds__(512) step_kernel(WorldDev W, int n_steps, int sbytes) {
+__global__ void __launch_bounds__(512) step_kernel(const __grid_constant__ WorldDev W, int n_steps, int sbytes) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int G = 32 / LPS;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -779,7 +791,7 @@ __global__ void advance_kernel(long long *step, int n) { *step += n; }
 
 // One warp per scene: joint angles already in W.theta; origin/quat/vel/omega are the caller's
 // arrays (AoS, [S*3] / [S*4]).  CoG = origin + R g, L = R Ib R^T omega, contact history cleared.
-__global__ void __launch_bounds__(128) init_kernel(WorldDev W, const float *origin, const float *quat,
+__global__ void __launch_bounds__(128) init_kernel(const __grid_constant__ WorldDev W, const float *origin, const float *quat,
                                                    const float *vel, const float *omega, int sbytes) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -821,7 +833,7 @@ __global__ void __launch_bounds__(128) init_kernel(WorldDev W, const float *orig
 }
 
 // Angular velocity of every scene from its state (one warp per scene), after a raw state write.
-__global__ void __launch_bounds__(128) refresh_kernel(WorldDev W, int sbytes) {
+__global__ void __launch_bounds__(128) refresh_kernel(const __grid_constant__ WorldDev W, int sbytes) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int s = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -857,7 +869,7 @@ __global__ void __launch_bounds__(128) refresh_kernel(WorldDev W, int sbytes) {
 }
 
 // World positions x_i = c + R r_i of one scene's points (one warp).
-__global__ void __launch_bounds__(32) points_kernel(WorldDev W, int s, float *out, int sbytes) {
+__global__ void __launch_bounds__(32) points_kernel(const __grid_constant__ WorldDev W, int s, float *out, int sbytes) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x;
     float4 *pts = reinterpret_cast<float4 *>(smem);
@@ -962,7 +974,7 @@ __device__ __forceinline__ void link_features(const RootState &x, const float R[
 }
 
 // Number of points on contact-sensor links, per scene, and the largest (one warp per scene).
-__global__ void __launch_bounds__(128) sensor_points_kernel(WorldDev W, int *count, int *max_count) {
+__global__ void __launch_bounds__(128) sensor_points_kernel(const __grid_constant__ WorldDev W, int *count, int *max_count) {
     const int lane = threadIdx.x & 31;
     const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (s >= W.S) return;   // warp-uniform
@@ -980,7 +992,7 @@ __global__ void __launch_bounds__(128) sensor_points_kernel(WorldDev W, int *cou
 }
 
 // The posed shape of every scene at its current joint angles, into the cache (one warp per scene).
-__global__ void __launch_bounds__(128) shape_cache_kernel(WorldDev W, SurCache C, int sbytes) {
+__global__ void __launch_bounds__(128) shape_cache_kernel(const __grid_constant__ WorldDev W, SurCache C, int sbytes) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int s = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -1038,7 +1050,7 @@ __global__ void __launch_bounds__(128) shape_cache_kernel(WorldDev W, SurCache C
 // when x_mu is set), raw, BF16 standardised into the network's input rows (whose padding columns
 // are zero and are not written), and the delta target against the raw features of the previous
 // state.
-__global__ void __launch_bounds__(256) features_kernel(WorldDev W, SurCache C, SurrogateIO io, int spb) {
+__global__ void __launch_bounds__(256) features_kernel(const __grid_constant__ WorldDev W, SurCache C, SurrogateIO io, int spb) {
     extern __shared__ float rows[];   // [spb x nf] raw features of the block's scenes
     const int tid = threadIdx.x, S = W.S;
     const int s0 = blockIdx.x * spb, ns = min(spb, S - s0);
@@ -1113,7 +1125,7 @@ __global__ void __launch_bounds__(256) features_kernel(WorldDev W, SurCache C, S
 enum { NX_CX = 0, NX_CY, NX_CZ, NX_QW, NX_QX, NX_QY, NX_QZ, NX_VX, NX_VY, NX_VZ, NX_LX, NX_LY, NX_LZ,
        NX_WX, NX_WY, NX_WZ, NX_N };
 
-__global__ void __launch_bounds__(256) surrogate_apply_kernel(WorldDev W, SurCache C, const float *Y, int ldy,
+__global__ void __launch_bounds__(256) surrogate_apply_kernel(const __grid_constant__ WorldDev W, SurCache C, const float *Y, int ldy,
                                                               const float *t_mu, const float *t_sd, float *nx,
                                                               uint8_t *applied) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1163,7 +1175,7 @@ __global__ void __launch_bounds__(256) surrogate_apply_kernel(WorldDev W, SurCac
 // Contact sensors at the candidate state, one warp per scene over its sensor points (the cached
 // body-frame offsets of the points of contact-sensor links).
 template <bool FLAT>
-__global__ void __launch_bounds__(256) sensor_probe_kernel(WorldDev W, SurCache C, const float *nx,
+__global__ void __launch_bounds__(256) sensor_probe_kernel(const __grid_constant__ WorldDev W, SurCache C, const float *nx,
                                                            const uint8_t *applied, uint32_t *sens_new) {
     const int lane = threadIdx.x & 31;
     const int s = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -1188,7 +1200,7 @@ __global__ void __launch_bounds__(256) sensor_probe_kernel(WorldDev W, SurCache 
 
 // One thread per scene: keep the candidate state if the contact sensors did not change, otherwise
 // leave the scene at its state and append it to the fallback list (the plain step takes it).
-__global__ void __launch_bounds__(256) surrogate_commit_kernel(WorldDev W, const float *nx, const uint8_t *applied,
+__global__ void __launch_bounds__(256) surrogate_commit_kernel(const __grid_constant__ WorldDev W, const float *nx, const uint8_t *applied,
                                                                const uint32_t *sens_new, int *list, int *count) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const bool app = s < W.S && applied[s];
@@ -1214,7 +1226,7 @@ __global__ void __launch_bounds__(256) surrogate_commit_kernel(WorldDev W, const
 // Contact flags of every point and the contact sensors at the current state, for the listed scenes
 // (list NULL: every scene) -- the previous-step contacts a plain step needs after surrogate steps.
 template <bool FLAT>
-__global__ void __launch_bounds__(128) kappa_refresh_kernel(WorldDev W, const int *list, const int *count,
+__global__ void __launch_bounds__(128) kappa_refresh_kernel(const __grid_constant__ WorldDev W, const int *list, const int *count,
                                                             int sbytes) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
