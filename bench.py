@@ -55,6 +55,20 @@ def algorithmic_flops(counts: dict) -> float:
     return float(sum(FLOPS_PER[k] * counts[k] for k in FLOPS_PER))
 
 
+def job_throughput(units_per_rank: float, rank_ms: float, dist=None, device="cpu"):
+    """Whole-job throughput of N replicas: each rank processed units_per_rank in rank_ms; the job
+    lasts as long as its slowest rank (max over ranks), so value = N * units_per_rank / max time.
+    Returns (value per second, max time in ms)."""
+    import torch
+    ws = dist.get_world_size() if dist else 1
+    t = float(rank_ms)
+    if dist:
+        x = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return ws * units_per_rank / (t / 1e3), t
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
@@ -354,10 +368,8 @@ def run_gpu(args):
     per_step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = float(sum(per_step_ms))
     launches = world.info()["kernel_launches"] - launches0
+    value, total_ms = job_throughput(N_SCENES * CHUNK * args.steps, total_ms, dist, dev)
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     status = world.read()["status"]
 
@@ -377,9 +389,8 @@ def run_gpu(args):
         last = world.read()
     e2e_s = time.perf_counter() - t0
     d2h = sum(v.nbytes for v in last.values() if isinstance(v, np.ndarray)) + 8
-    e2e_val = ws * N_SCENES * CHUNK * e2e_steps / e2e_s
+    e2e_val, _ = job_throughput(N_SCENES * CHUNK * e2e_steps, e2e_s * 1e3, dist, dev)
 
-    value = ws * N_SCENES * CHUNK * args.steps / (total_ms / 1e3)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
