@@ -62,6 +62,7 @@ struct LaunchCfg {
 };
 
 size_t step_smem_bytes(const WorldDev &W, int lps, int wpb);
+int step_slot_bytes(const WorldDev &W, int lps);
 int step_blocks_per_sm(const WorldDev &W, int lps, int wpb, cudaError_t *err);
 cudaError_t launch_step(const WorldDev &W, const LaunchCfg &cfg, int n_steps, cudaStream_t st);
 cudaError_t launch_advance(long long *d_step, int n, cudaStream_t st);

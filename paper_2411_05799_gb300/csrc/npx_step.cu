@@ -37,6 +37,9 @@ namespace npx {
 
 constexpr float POINT_RADIUS = 1e-3f;   // m, see shape_update
 constexpr float CULL_MARGIN = 4e-3f;    // m, height margin of the candidate tiles (run_scene)
+// height-map window kept in shared memory per scene (run_scene): HM_WIN x HM_WIN cells around the
+// CoG, moved when the CoG's cell drifts more than HM_DRIFT cells from the window's centre
+constexpr int HM_WIN = 16, HM_DRIFT = 2;
 
 // ------------------------------------------------------------------------ group reductions
 
@@ -373,6 +376,23 @@ __device__ __forceinline__ float ground(const WorldDev &W, int hm, float x, floa
     return __ldg(W.hm + ((size_t)hm * W.hm_ny + iy) * W.hm_nx + ix);
 }
 
+// The same lookup through a window of the scene's map in shared memory: cells [wx0, wx0 + HM_WIN)
+// x [wy0, wy0 + HM_WIN) come from the window, others from global memory (the same value either
+// way).
+template <bool FLAT>
+__device__ __forceinline__ float ground_win(const WorldDev &W, int hm, const float *win, int wx0, int wy0, float x,
+                                            float y) {
+    if (FLAT || hm < 0) return 0.f;
+    const float fx = __fmul_rn(__fsub_rn(x, W.hm_ox), W.hm_scale);
+    const float fy = __fmul_rn(__fsub_rn(y, W.hm_oy), W.hm_scale);
+    int ix = __float2int_rd(fx), iy = __float2int_rd(fy);
+    ix = min(max(ix, 0), W.hm_nx - 1);
+    iy = min(max(iy, 0), W.hm_ny - 1);
+    const unsigned ux = (unsigned)(ix - wx0), uy = (unsigned)(iy - wy0);
+    if (ux < (unsigned)HM_WIN && uy < (unsigned)HM_WIN) return win[uy * HM_WIN + ux];
+    return __ldg(W.hm + ((size_t)hm * W.hm_ny + iy) * W.hm_nx + ix);
+}
+
 // ------------------------------------------------------------------------ actuators (Sec. III-B)
 
 __device__ __forceinline__ float joint_target(const WorldDev &W, int j, long long n) {
@@ -427,6 +447,10 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
     Shape shr = sh;
     // highest ground a point can meet (plus a margin for the rounding of the bound)
     const float hmax = (FLAT || hm < 0 ? 0.f : W.hm_max[hm]) + 1e-5f;
+    // height-map window (after the slot); its origin is invalid until the first refresh
+    float *win = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(pts) +
+                                           slot_bytes(W.max_points, W.max_links, LPS));
+    int wx0 = -(1 << 24), wy0 = -(1 << 24);
     const int ntiles = (np + LPS - 1) / LPS;
 
     const float dt = W.dt, idt = 1.0f / W.dt, kw2 = W.kw2, kc = W.kc;
@@ -476,6 +500,26 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         //    rho = R r, about a reference point o near them: every term of the dynamic least
         //    squares is a function of these (see below).  All sums are independent, so the group
         //    reduction is one butterfly and every lane ends with bit-identical values.
+        if (!FLAT) {
+            // move the height-map window when the CoG's cell has drifted from its centre (the
+            // groups of the warp refresh together; each loads only its own window)
+            const int cx = __float2int_rd(__fmul_rn(__fsub_rn(c[0], W.hm_ox), W.hm_scale));
+            const int cy = __float2int_rd(__fmul_rn(__fsub_rn(c[1], W.hm_oy), W.hm_scale));
+            const bool need = hm >= 0 && (abs(cx - (wx0 + HM_WIN / 2)) > HM_DRIFT ||
+                                          abs(cy - (wy0 + HM_WIN / 2)) > HM_DRIFT);
+            if (__any_sync(FULL_MASK, need)) {
+                if (need) {
+                    wx0 = min(max(cx - HM_WIN / 2, 0), max(W.hm_nx - HM_WIN, 0));
+                    wy0 = min(max(cy - HM_WIN / 2, 0), max(W.hm_ny - HM_WIN, 0));
+                    const float *map = W.hm + (size_t)hm * W.hm_ny * W.hm_nx;
+                    for (int e = gl; e < HM_WIN * HM_WIN; e += LPS) {
+                        const int iy = wy0 + e / HM_WIN, ix = wx0 + e % HM_WIN;
+                        win[e] = (iy < W.hm_ny && ix < W.hm_nx) ? __ldg(map + (size_t)iy * W.hm_nx + ix) : 0.f;
+                    }
+                }
+                __syncwarp();
+            }
+        }
         // the cull's ballots involve the whole warp: every group culls when any one needs to
         if (__any_sync(FULL_MASK, slack < 0.f)) {
             cand = tiles_near_ground<LPS>(tb, ntiles, R, c[2], hmax + CULL_MARGIN, gl);
@@ -503,8 +547,8 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
                 const float rya = R[3] * pa.x + R[4] * pa.y + R[5] * pa.z, ryb = R[3] * pb.x + R[4] * pb.y + R[5] * pb.z;
                 const float rza = R[6] * pa.x + R[7] * pa.y + R[8] * pa.z, rzb = R[6] * pb.x + R[7] * pb.y + R[8] * pb.z;
                 const float za = c[2] + rza, zb = c[2] + rzb;
-                const float ha = ground<FLAT>(W, hm, c[0] + rxa, c[1] + rya);
-                const float hb = ground<FLAT>(W, hm, c[0] + rxb, c[1] + ryb);
+                const float ha = ground_win<FLAT>(W, hm, win, wx0, wy0, c[0] + rxa, c[1] + rya);
+                const float hb = ground_win<FLAT>(W, hm, win, wx0, wy0, c[0] + rxb, c[1] + ryb);
                 const bool ca = oka && za < ha, cb = okb && zb < hb;
                 const float vza = v[2] + (om[0] * rya - om[1] * rxa), vzb = v[2] + (om[0] * ryb - om[1] * rxb);
                 const float Fa = ca ? fmaxf(0.f, pa.w * (kw2 * (ha - za) - kc * vza)) : 0.f;
@@ -1342,8 +1386,13 @@ cudaError_t launch_kappa_refresh(const WorldDev &W, const int *list, const int *
 
 // ------------------------------------------------------------------------ host-side launchers
 
+// per-scene shared memory of the step kernel: the slot, plus the height-map window on maps
+int step_slot_bytes(const WorldDev &W, int lps) {
+    return slot_bytes(W.max_points, W.max_links, lps) + (W.hm ? HM_WIN * HM_WIN * (int)sizeof(float) : 0);
+}
+
 size_t step_smem_bytes(const WorldDev &W, int lps, int wpb) {
-    return (size_t)wpb * (32 / lps) * slot_bytes(W.max_points, W.max_links, lps);
+    return (size_t)wpb * (32 / lps) * step_slot_bytes(W, lps);
 }
 
 template <int LPS, bool FLAT>
@@ -1390,7 +1439,7 @@ cudaError_t launch_step(const WorldDev &W, const LaunchCfg &cfg, int n_steps, cu
     const size_t smem = step_smem_bytes(W, cfg.lps, cfg.wpb);
     cudaError_t e = cudaMemsetAsync(W.queue, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    int sb = slot_bytes(W.max_points, W.max_links, cfg.lps);
+    int sb = step_slot_bytes(W, cfg.lps);
     WorldDev w = W;
     void *args[] = {&w, &n_steps, &sb};
     return cudaLaunchKernel(fn, dim3(cfg.blocks), dim3(cfg.wpb * 32), args, smem, st);
