@@ -155,6 +155,7 @@ def other_workloads(World, scenes, stream, device) -> dict:
         info = w.info()
         out[name] = {"value": b.n_scenes * 2 * CHUNK / (ms / 1e3), "unit": UNIT, "steps": 2 * CHUNK,
                      "ms": ms, "points": b.n_points, "lanes_per_scene": info["lanes_per_scene"],
+                     "size_classes": info["size_classes"],
                      "warps_per_block": info["warps_per_block"],
                      "frozen_scenes": int((w.read()["status"] != 0).sum())}
         w.close()
@@ -399,8 +400,9 @@ def run_gpu(args):
                        "parallelism": f"replicas{ws}", "l2": "flushed between timed steps (256 MiB write)",
                        "lanes_per_scene": info["lanes_per_scene"],
                        "warps_per_block": info["warps_per_block"], "blocks": info["blocks"],
+                       "size_classes": info["size_classes"],
                        "frozen_scenes": int((status != 0).sum())},
-            "gpu_launches": int(2 * launches),
+            "gpu_launches": int(launches + args.steps),   # step-kernel launches + step-counter kernels
             "clocks": clk,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "steps": e2e_steps}}

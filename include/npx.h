@@ -171,6 +171,8 @@ typedef struct {
     int lanes_per_scene, warps_per_block, blocks, chunk_steps;
     int64_t step;
     int64_t kernel_launches;    /* step-kernel launches so far */
+    int size_classes;           /* launches per chunk: scenes grouped by point count, each with
+                                   its own shared-memory slots and launch shape */
 } npx_world_info;
 int npx_world_info_get(npx_world *w, npx_world_info *out);
 /* Launch shape of the step kernel: lanes per scene (8, 16 or 32), warps per block (1..16),

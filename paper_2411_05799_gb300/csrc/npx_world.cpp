@@ -103,7 +103,15 @@ struct npx_world {
     float *d_points = nullptr;          // points_read staging [3 * max_points]
     long long step = 0;
     // launch shape
-    npx::LaunchCfg cfg{32, 4, 0};
+    npx::LaunchCfg cfg{32, 4, 0};       // whole-world launch shape (single steps, the fallback)
+    // chunked stepping runs one launch per size class: a slice of the schedule (scenes of similar
+    // point counts, most points first) with its own shared-memory slots and launch shape
+    struct SizeClass {
+        int start, count, max_points, max_links;   // slice of the schedule and its largest scene
+        npx::LaunchCfg cfg;
+    };
+    std::vector<SizeClass> classes;
+    std::vector<int> order_host;        // the schedule: scenes by point count, descending
     int chunk = 1000;
     bool graphs = true;
     std::map<int, cudaGraphExec_t> graph_cache;
@@ -259,23 +267,96 @@ int check_flat(const Flat &f, int scene) {
     return NPX_OK;
 }
 
-npx::LaunchCfg clamp_cfg(npx_world *w, npx::LaunchCfg c, int *rc) {
+// launch shape for the scenes of W's schedule (count of them): checks the lanes per scene against
+// the largest scene, and sizes the grid to what is resident and what is needed
+npx::LaunchCfg clamp_cfg_for(npx_world *w, const npx::WorldDev &W, int count, npx::LaunchCfg c, int *rc) {
     *rc = NPX_OK;
-    if (w->max_points > 64 * c.lps) {
+    if (W.max_points > 64 * c.lps) {
         *rc = fail(NPX_ERANGE, "%d points per scene exceed 64 per lane at %d lanes per scene",
-                   w->max_points, c.lps);
+                   W.max_points, c.lps);
         return c;
     }
     cudaError_t e;
-    int nb = npx::step_blocks_per_sm(w->W, c.lps, c.wpb, &e);
+    int nb = npx::step_blocks_per_sm(W, c.lps, c.wpb, &e);
     if (e != cudaSuccess) { *rc = fail(NPX_ECUDA, "occupancy query: %s", cudaGetErrorString(e)); return c; }
     if (nb < 1) { *rc = fail(NPX_ERANGE, "launch shape lps=%d wpb=%d does not fit on an SM", c.lps, c.wpb); return c; }
     const int per_block = c.wpb * (32 / c.lps);
-    const int need = (w->S + per_block - 1) / per_block;
+    const int need = (count + per_block - 1) / per_block;
     const int full = nb * w->n_sm;
     if (c.blocks <= 0 || c.blocks > full) c.blocks = full;
     c.blocks = std::max(1, std::min(c.blocks, need));
     return c;
+}
+
+npx::LaunchCfg clamp_cfg(npx_world *w, npx::LaunchCfg c, int *rc) { return clamp_cfg_for(w, w->W, w->S, c, rc); }
+
+// the world as one class's launch sees it: its slice of the schedule and its slot sizes (built from
+// the current world, so that later changes -- actuators, state -- reach every class)
+npx::WorldDev class_world(const npx_world *w, const npx_world::SizeClass &c) {
+    npx::WorldDev W = w->W;
+    W.order = w->W.order + c.start;
+    W.n_sched = c.count;
+    W.sched_count = nullptr;
+    W.max_points = c.max_points;
+    W.max_links = c.max_links;
+    return W;
+}
+
+// default shape for scenes of up to max_points points: the narrowest group that holds them,
+// at least 16 lanes, 4 warps per block
+npx::LaunchCfg default_shape(int max_points) {
+    int lps = 8;
+    while (lps < 32 && max_points > 64 * lps) lps *= 2;
+    return {std::max(lps, 16), 4, 0};
+}
+
+// Size classes of the schedule: runs of scenes whose point counts fall in the same power-of-two
+// bin (up to 128, 256, 512, ...), a class too small to fill the GPU joining the class before it.
+// A world of equal scenes has one class, the whole world.
+int build_classes(npx_world *w, bool split) {
+    w->classes.clear();
+    const int S = w->S;
+    const std::vector<int> &order = w->order_host;
+    auto pts = [&](int s) { return w->point_off[s + 1] - w->point_off[s]; };
+    auto lnk = [&](int s) { return w->link_off[s + 1] - w->link_off[s]; };
+    auto bin = [](int np) { int b = 7; while ((1 << b) < np) ++b; return b; };
+    std::vector<std::pair<int, int>> ranges;
+    if (split) {
+        const int min_count = std::max(1024, S / 64);
+        int start = 0;
+        for (int i = 1; i <= S; ++i) {
+            if (i < S && bin(pts(order[i])) == bin(pts(order[start]))) continue;
+            if (!ranges.empty() && i - start < min_count) ranges.back().second = i;
+            else ranges.push_back({start, i});
+            start = i;
+        }
+        if (ranges.size() > 1 && ranges[0].second - ranges[0].first < min_count) {
+            ranges[1].first = ranges[0].first;
+            ranges.erase(ranges.begin());
+        }
+    } else {
+        ranges.push_back({0, S});
+    }
+    for (const auto &r : ranges) {
+        npx_world::SizeClass c;
+        c.start = r.first;
+        c.count = r.second - r.first;
+        c.max_points = 1;
+        c.max_links = 1;
+        for (int i = r.first; i < r.second; ++i) {
+            c.max_points = std::max(c.max_points, pts(order[i]));
+            c.max_links = std::max(c.max_links, lnk(order[i]));
+        }
+        if (ranges.size() == 1) {
+            c.cfg = w->cfg;
+        } else {
+            int rc;
+            c.cfg = clamp_cfg_for(w, class_world(w, c), c.count, default_shape(c.max_points), &rc);
+            if (rc) return rc;
+        }
+        w->classes.push_back(c);
+    }
+    return NPX_OK;
 }
 
 void clear_graphs(npx_world *w) {
@@ -286,7 +367,8 @@ void clear_graphs(npx_world *w) {
 int enqueue_steps(npx_world *w, int n) {
     for (int done = 0; done < n;) {
         const int nc = std::min(w->chunk, n - done);
-        CUDA_TRY(npx::launch_step(w->W, w->cfg, nc, w->stream));
+        // every class reads the same step counter; it advances after all of them
+        for (const auto &c : w->classes) CUDA_TRY(npx::launch_step(class_world(w, c), c.cfg, nc, w->stream));
         CUDA_TRY(npx::launch_advance(w->d_step, nc, w->stream));
         done += nc;
     }
@@ -699,15 +781,14 @@ int npx_world_finalize(npx_world *w) {
     w->flats.shrink_to_fit();
     w->builds.clear();
     w->builds.shrink_to_fit();
-    // default launch shape: widest group that holds the largest scene
-    int lps = 8;
-    while (lps < 32 && w->max_points > 64 * lps) lps *= 2;
+    // default launch shapes: the narrowest group that holds the largest scene, per size class
     if (w->max_points > 64 * 32) return fail(NPX_ERANGE, "scene too large");
-    if (lps < 16) lps = 16;
     int rc2;
-    npx::LaunchCfg c = clamp_cfg(w, {lps, 4, 0}, &rc2);
+    npx::LaunchCfg c = clamp_cfg(w, default_shape(w->max_points), &rc2);
     if (rc2) return rc2;
     w->cfg = c;
+    w->order_host = order;
+    if (int rc3 = build_classes(w, true)) return rc3;
     // construction pose, at rest
     std::vector<float> zero(3 * (size_t)S, 0.f), quat(4 * (size_t)S, 0.f);
     for (int s = 0; s < S; ++s) quat[4 * s] = 1.f;
@@ -832,7 +913,7 @@ int npx_world_step(npx_world *w, int n) {
     } else {
         if (int rc = enqueue_steps(w, n)) return rc;
     }
-    w->launches += nchunks;
+    w->launches += (long long)nchunks * (long long)w->classes.size();
     w->step += n;
     return NPX_OK;
 }
@@ -939,6 +1020,7 @@ int npx_world_info_get(npx_world *w, npx_world_info *o) {
     o->max_points = w->max_points; o->max_links = w->max_links;
     o->lanes_per_scene = w->cfg.lps; o->warps_per_block = w->cfg.wpb; o->blocks = w->cfg.blocks;
     o->chunk_steps = w->chunk; o->step = w->step; o->kernel_launches = w->launches;
+    o->size_classes = (int)w->classes.size();
     return NPX_OK;
 }
 
@@ -959,7 +1041,10 @@ int npx_world_configure(npx_world *w, int lps, int wpb, int blocks, int chunk) {
     int rc;
     c = clamp_cfg(w, c, &rc);
     if (rc) return rc;
-    w->cfg = c;
+    if (lps || wpb || blocks) {   // an explicit shape runs the whole world in one launch
+        w->cfg = c;
+        if ((rc = build_classes(w, false))) return rc;
+    }
     if (chunk) w->chunk = chunk;
     clear_graphs(w);
     return NPX_OK;
@@ -1106,58 +1191,77 @@ int npx_world_autotune(npx_world *w, int n_steps, npx_world_info *out) {
     if (int rc = npx_state_export(w, nullptr, &bytes)) return rc;
     blob.resize(bytes);
     if (int rc = npx_state_export(w, blob.data(), &bytes)) return rc;
-    const npx::LaunchCfg saved = w->cfg;
-    npx::LaunchCfg best = saved;
-    float best_ms = 1e30f;
+    // size classes of the schedule, each tuned on its own scenes
+    if (int rc = build_classes(w, true)) return rc;
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
     const int lps_list[3] = {8, 16, 32};
     int rc_out = NPX_OK;
-    for (int lps : lps_list) {
-        if (w->max_points > 64 * lps) continue;
-        // fixed block sizes plus the "balanced" ones that spread the scenes evenly over all SMs
-        // with 1, 2 or 3 resident blocks per SM
-        std::vector<int> wpb_list = {2, 4, 8, 16};
-        const int G = 32 / lps;
-        for (int k = 1; k <= 3; ++k) {
-            const long long per = (long long)w->n_sm * G * k;
-            const int wb = (int)((w->S + per - 1) / per);
-            if (wb >= 1 && wb <= 16 &&
-                std::find(wpb_list.begin(), wpb_list.end(), wb) == wpb_list.end())
-                wpb_list.push_back(wb);
-        }
-        for (int wpb : wpb_list) {
-            int rc;
-            npx::LaunchCfg c = clamp_cfg(w, {lps, wpb, 0}, &rc);
-            if (rc) { g_err.clear(); continue; }
-            w->cfg = c;
-            float ms = 0.f;
-            bool ok = true;
-            for (int rep = 0; rep < 2 && ok; ++rep) {   // first run warms up
-                if (npx_state_import(w, blob.data(), bytes)) { ok = false; break; }
-                cudaEventRecord(e0, w->stream);
-                for (int done = 0; done < n_steps && ok;) {
-                    const int nc = std::min(w->chunk, n_steps - done);
-                    ok = npx::launch_step(w->W, w->cfg, nc, w->stream) == cudaSuccess &&
-                         npx::launch_advance(w->d_step, nc, w->stream) == cudaSuccess;
-                    done += nc;
-                }
-                cudaEventRecord(e1, w->stream);
-                if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
-                cudaEventElapsedTime(&ms, e0, e1);
+    for (auto &cls : w->classes) {
+        const npx::WorldDev CW = class_world(w, cls);
+        const npx::LaunchCfg saved = cls.cfg;
+        npx::LaunchCfg best = saved;
+        float best_ms = 1e30f;
+        for (int lps : lps_list) {
+            if (cls.max_points > 64 * lps) continue;
+            // fixed block sizes plus the "balanced" ones that spread the class's scenes evenly
+            // over all SMs with 1, 2 or 3 resident blocks per SM
+            std::vector<int> wpb_list = {2, 4, 8, 16};
+            const int G = 32 / lps;
+            for (int k = 1; k <= 3; ++k) {
+                const long long per = (long long)w->n_sm * G * k;
+                const int wb = (int)((cls.count + per - 1) / per);
+                if (wb >= 1 && wb <= 16 && std::find(wpb_list.begin(), wpb_list.end(), wb) == wpb_list.end())
+                    wpb_list.push_back(wb);
             }
-            if (ok && ms < best_ms) { best_ms = ms; best = c; }
-            if (!ok) { rc_out = fail(NPX_ECUDA, "autotune trial lps=%d wpb=%d failed: %s", lps, wpb, cudaGetErrorString(cudaGetLastError())); break; }
+            for (int wpb : wpb_list) {
+                int rc;
+                npx::LaunchCfg c = clamp_cfg_for(w, CW, cls.count, {lps, wpb, 0}, &rc);
+                if (rc) { g_err.clear(); continue; }
+                float ms = 0.f;
+                bool ok = true;
+                for (int rep = 0; rep < 2 && ok; ++rep) {   // first run warms up
+                    if (npx_state_import(w, blob.data(), bytes)) { ok = false; break; }
+                    cudaEventRecord(e0, w->stream);
+                    for (int done = 0; done < n_steps && ok;) {
+                        const int nc = std::min(w->chunk, n_steps - done);
+                        ok = npx::launch_step(CW, c, nc, w->stream) == cudaSuccess &&
+                             npx::launch_advance(w->d_step, nc, w->stream) == cudaSuccess;
+                        done += nc;
+                    }
+                    cudaEventRecord(e1, w->stream);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                }
+                if (ok && ms < best_ms) { best_ms = ms; best = c; }
+                if (!ok) {
+                    rc_out = fail(NPX_ECUDA, "autotune trial lps=%d wpb=%d failed: %s", lps, wpb,
+                                  cudaGetErrorString(cudaGetLastError()));
+                    break;
+                }
+            }
+            if (rc_out) break;
         }
+        int rc_cfg;
+        cls.cfg = clamp_cfg_for(w, CW, cls.count, rc_out ? saved : best, &rc_cfg);   // re-arms the smem limit
+        if (rc_cfg && !rc_out) rc_out = rc_cfg;
         if (rc_out) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    int rc_cfg;
-    w->cfg = clamp_cfg(w, rc_out ? saved : best, &rc_cfg);   // re-arms the kernel's smem limit
+    // the whole-world shape (single steps, the surrogate's fallback): that of the class of the
+    // largest scenes
+    if (!rc_out) {
+        int rc_cfg;
+        npx::LaunchCfg c = clamp_cfg(w, {w->classes[0].cfg.lps, w->classes[0].cfg.wpb, 0}, &rc_cfg);
+        if (rc_cfg) rc_out = rc_cfg;
+        else w->cfg = c;
+        if (w->classes.size() == 1) w->classes[0].cfg = w->cfg;
+        // the occupancy queries above may have lowered nothing, but the class shapes come last
+        for (auto &cls : w->classes) clamp_cfg_for(w, class_world(w, cls), cls.count, cls.cfg, &rc_cfg);
+    }
     clear_graphs(w);
-    if (rc_cfg && !rc_out) rc_out = rc_cfg;
     if (int rc = npx_state_import(w, blob.data(), bytes)) return rc;
     if (rc_out) return rc_out;
     if (out) return npx_world_info_get(w, out);
