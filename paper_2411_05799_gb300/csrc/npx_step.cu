@@ -495,11 +495,11 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         world_sym(R, shr.Ii, L, om);
 
         // -- pass 1: collision against the ground and penalty normal forces over the candidate
-        //    tiles.  For the points in contact in both steps (the friction set C, Sec. III-C) a
-        //    second loop sums the count, the first and the second moments of d = rho - o,
-        //    rho = R r, about a reference point o near them: every term of the dynamic least
-        //    squares is a function of these (see below).  All sums are independent, so the group
-        //    reduction is one butterfly and every lane ends with bit-identical values.
+        //    tiles.  For the points in contact in both steps (the friction set C, Sec. III-C) it
+        //    also sums the count, the first and the second moments of d = rho - o, rho = R r,
+        //    about a reference point o near them: every term of the dynamic least squares is a
+        //    function of these (see below).  All sums are independent, so the group reduction is
+        //    one butterfly and every lane ends with bit-identical values.
         if (!FLAT) {
             // move the height-map window when the CoG's cell has drifted from its centre (the
             // groups of the warp refresh together; each loads only its own window)
@@ -525,15 +525,27 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             cand = tiles_near_ground<LPS>(tb, ntiles, R, c[2], hmax + CULL_MARGIN, gl);
             slack = CULL_MARGIN;
         }
+        // reference o of the friction-set moments: the rotated centre of the first tile holding a
+        // point that was in contact last step (C is a subset of those; o depends on the state alone)
+        int kf = kprev ? __ffsll((long long)kprev) - 1 : 64;
+#pragma unroll
+        for (int ofs = LPS / 2; ofs > 0; ofs >>= 1) kf = min(kf, __shfl_xor_sync(FULL_MASK, kf, ofs));
+        float o[3] = {0.f, 0.f, 0.f};
+        if (kf < 64) {
+            const float4 lo = tb[2 * kf], hi = tb[2 * kf + 1];
+            const float mid[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
+            mat_vec(R, mid, o);
+        }
         // FN, tau_x, tau_y | n | sum d (3) | sum d d^T (xx yy zz xy xz yz)
         float acc[13] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         // The 64-bit tile masks are walked as two 32-bit words (hexapod candidates sit in the low
         // word: points are stored by construction height).  Two tiles per iteration: two
-        // independent chains; a point that is absent or not in contact adds an exact zero, so the
-        // sums see the same terms in the same order.
+        // independent chains; a point that is absent, not in contact or not in C adds an exact
+        // zero, so the sums see the same terms in the same order.
         uint32_t knw[2] = {0u, 0u};
 #pragma unroll
         for (int hw = 0; hw < 2; ++hw) {
+            const uint32_t kp = (uint32_t)(kprev >> (32 * hw));
             for (uint32_t tm = (uint32_t)(cand >> (32 * hw)); tm;) {
                 const int ja = __ffs(tm) - 1;
                 tm &= tm - 1;
@@ -556,38 +568,11 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
                 knw[hw] |= (ca ? 1u << ja : 0u) | (cb ? 1u << jb : 0u);
                 acc[0] += Fa; acc[1] += rya * Fa; acc[2] -= rxa * Fa;
                 acc[0] += Fb; acc[1] += ryb * Fb; acc[2] -= rxb * Fb;
-            }
-        }
-        const uint64_t know = (uint64_t)knw[0] | ((uint64_t)knw[1] << 32);
-        // moments of the friction set C about o, the rotated centre of the first tile holding a
-        // point of C (a function of C and the state alone)
-        const uint64_t cset = kprev & know;
-        int kf = cset ? __ffsll((long long)cset) - 1 : 64;
-#pragma unroll
-        for (int ofs = LPS / 2; ofs > 0; ofs >>= 1) kf = min(kf, __shfl_xor_sync(FULL_MASK, kf, ofs));
-        float o[3] = {0.f, 0.f, 0.f};
-        if (kf < 64) {
-            const float4 lo = tb[2 * kf], hi = tb[2 * kf + 1];
-            const float mid[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
-            mat_vec(R, mid, o);
-        }
-#pragma unroll
-        for (int hw = 0; hw < 2; ++hw) {
-            for (uint32_t cm = (uint32_t)(cset >> (32 * hw)); cm;) {
-                const int ja = __ffs(cm) - 1;
-                cm &= cm - 1;
-                const bool two = cm != 0;
-                const int jb = two ? __ffs(cm) - 1 : ja;
-                if (two) cm &= cm - 1;
-                const float4 pa = pts[gl + (ja + 32 * hw) * LPS], pb = pts[gl + (jb + 32 * hw) * LPS];
-                const float wb = two ? 1.f : 0.f;
-                const float a0 = (R[0] * pa.x + R[1] * pa.y + R[2] * pa.z) - o[0];
-                const float a1 = (R[3] * pa.x + R[4] * pa.y + R[5] * pa.z) - o[1];
-                const float a2 = (R[6] * pa.x + R[7] * pa.y + R[8] * pa.z) - o[2];
-                const float b0 = wb * ((R[0] * pb.x + R[1] * pb.y + R[2] * pb.z) - o[0]);
-                const float b1 = wb * ((R[3] * pb.x + R[4] * pb.y + R[5] * pb.z) - o[1]);
-                const float b2 = wb * ((R[6] * pb.x + R[7] * pb.y + R[8] * pb.z) - o[2]);
-                acc[3] += 1.f; acc[3] += wb;
+                // friction set C: in contact now and last step
+                const float wa = (ca && ((kp >> ja) & 1u)) ? 1.f : 0.f, wb = (cb && ((kp >> jb) & 1u)) ? 1.f : 0.f;
+                const float a0 = wa * (rxa - o[0]), a1 = wa * (rya - o[1]), a2 = wa * (rza - o[2]);
+                const float b0 = wb * (rxb - o[0]), b1 = wb * (ryb - o[1]), b2 = wb * (rzb - o[2]);
+                acc[3] += wa; acc[3] += wb;
                 acc[4] += a0; acc[5] += a1; acc[6] += a2;
                 acc[4] += b0; acc[5] += b1; acc[6] += b2;
                 acc[7] += a0 * a0; acc[8] += a1 * a1; acc[9] += a2 * a2;
@@ -596,6 +581,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
                 acc[10] += b0 * b1; acc[11] += b0 * b2; acc[12] += b1 * b2;
             }
         }
+        const uint64_t know = (uint64_t)knw[0] | ((uint64_t)knw[1] << 32);
         gsum<LPS, 13>(acc);
         const float FN = acc[0];
         // friction set: count, centroid of rho and second central moments sum (rho - gb)(rho - gb)^T
