@@ -201,12 +201,15 @@ __device__ __noinline__ float tile_bounds(const float4 *pts, int np, float4 *tb,
 // its tiles (t = gl, gl + LPS, ...) and ballots gather the group's answers into a mask.  The
 // contact mask holds at most 64 tiles, so there are at most 64 / LPS rounds: all box tests are
 // issued first (independent shared-memory loads), then the ballots.
+// zfar receives the lowest box bottom among the tiles left out (+inf if none), the same for every
+// lane of the group.
 template <int LPS>
 __device__ __forceinline__ uint64_t tiles_near_ground(const float4 *tb, int ntiles, const float R[9], float cz,
-                                                      float hmax, int gl) {
+                                                      float hmax, int gl, float &zfar) {
     constexpr int ROUNDS = 64 / LPS;
     const int g = (threadIdx.x & 31) / LPS;
     bool near[ROUNDS];
+    zfar = INFINITY;
 #pragma unroll
     for (int r = 0; r < ROUNDS; ++r) {
         const int t = r * LPS + gl;
@@ -216,8 +219,11 @@ __device__ __forceinline__ uint64_t tiles_near_ground(const float4 *tb, int ntil
             const float zb = cz + fminf(R[6] * lo.x, R[6] * hi.x) + fminf(R[7] * lo.y, R[7] * hi.y) +
                              fminf(R[8] * lo.z, R[8] * hi.z);
             near[r] = zb <= hmax;
+            if (!near[r]) zfar = fminf(zfar, zb);
         }
     }
+#pragma unroll
+    for (int o = LPS / 2; o > 0; o >>= 1) zfar = fminf(zfar, __shfl_xor_sync(FULL_MASK, zfar, o));
     uint64_t mask = 0;
 #pragma unroll
     for (int r = 0; r < ROUNDS; ++r) {
@@ -457,7 +463,8 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
     float iM = 1.0f / shr.M;
     const bool actuated = W.act_mode != 0;
     // Candidate tiles: those whose box came within CULL_MARGIN of the highest ground at the last
-    // cull.  slack is CULL_MARGIN minus a bound on how far any point has moved down since then
+    // cull.  slack is the height above the highest ground of the lowest box left out then, minus
+    // a bound on how far any point has moved down since
     // (integration only: the friction corrections move the robot horizontally and rotate it about
     // the vertical); while it is >= 0 no other tile can have reached the ground, so the set stays
     // exact and the boxes are tested again only when it runs out or the shape changes.
@@ -522,8 +529,11 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         }
         // the cull's ballots involve the whole warp: every group culls when any one needs to
         if (__any_sync(FULL_MASK, slack < 0.f)) {
-            cand = tiles_near_ground<LPS>(tb, ntiles, R, c[2], hmax + CULL_MARGIN, gl);
-            slack = CULL_MARGIN;
+            // the slack is the height of the lowest tile left out above the highest ground (at
+            // least CULL_MARGIN; unbounded when no tile is left out)
+            float zfar;
+            cand = tiles_near_ground<LPS>(tb, ntiles, R, c[2], hmax + CULL_MARGIN, gl, zfar);
+            slack = fminf(zfar - hmax, 1e30f);
         }
         // reference o of the friction-set moments: the rotated centre of the first tile holding a
         // point that was in contact last step (C is a subset of those; o depends on the state alone)
