@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstring>
+
 #include "../../include/npx_mlp.h"
 #include "npx_internal.h"
 
@@ -81,6 +83,23 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// TMA store of a box from shared memory (bulk group), its commit and waits
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, const void *src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
+                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, int x, int y, int z, const void *src) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"
+                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // UMMA shared-memory descriptor of a K-major operand tile in the 128-byte swizzled layout:
 // rows of 128 bytes (64 BF16 along K), 8-row groups 1024 bytes apart (stride byte offset),
 // descriptor version 1, swizzle mode 2 (128 B).  The leading byte offset is unused here.
@@ -117,18 +136,17 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
+// 16 consecutive accumulator columns of this thread's TMEM lane; the values are valid after
+// tmem_wait_ld
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr)
         : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Standard normal CDF Phi(z) = (1 + erf(z / sqrt 2)) / 2, with erf from the rational
 // approximation of Abramowitz & Stegun, Handbook of Mathematical Functions, formula 7.1.26
@@ -165,9 +183,31 @@ __device__ __forceinline__ void store_bf16x16(__nv_bfloat16 *o, const float (&v)
     reinterpret_cast<uint4 *>(o)[1] = u[1];
 }
 
-// the epilogue of 16 accumulator values of one row: v = acc[row, col .. col + 15]
-__device__ __forceinline__ void epilogue16(const npx_gemm_epilogue &ep, float (&v)[16], int row, int col, int split) {
+// The epilogue of 16 accumulator values of one row: v = acc[row, col .. col + 15].  With a store
+// mode the row-major output goes to this thread's row of the warp's staging box (st: 16 BF16 or
+// 16 FP32 values) instead of global memory; the warp then stores the box with TMA.
+__device__ __forceinline__ void stage16(void *st, const float (&v)[16], bool f32) {
+    if (f32) {
+        float4 *o = reinterpret_cast<float4 *>(st);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    } else {
+        uint32_t w[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+            w[i] = *reinterpret_cast<const uint32_t *>(&h);
+        }
+        uint4 *o = reinterpret_cast<uint4 *>(st);
+        o[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        o[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+}
+
+__device__ __forceinline__ void epilogue16(const npx_gemm_epilogue &ep, float (&v)[16], int row, int col, int split,
+                                           int store_mode, void *st) {
     if (ep.mode == NPX_EPI_F32) {
+        if (store_mode == 2) { stage16(st, v, true); return; }
         float4 *o = reinterpret_cast<float4 *>(ep.outf + (size_t)split * ep.split_stride + (size_t)row * ep.ldf + col);
 #pragma unroll
         for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
@@ -197,11 +237,18 @@ __device__ __forceinline__ void epilogue16(const npx_gemm_epilogue &ep, float (&
         }
     }
     if (ep.outf) {
-        float4 *o = reinterpret_cast<float4 *>(ep.outf + (size_t)row * ep.ldf + col);
+        if (store_mode == 2) {
+            stage16(st, v, true);
+        } else {
+            float4 *o = reinterpret_cast<float4 *>(ep.outf + (size_t)row * ep.ldf + col);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        }
     }
-    if (ep.out) store_bf16x16(static_cast<__nv_bfloat16 *>(ep.out) + (size_t)row * ep.ldo + col, v);
+    if (ep.out) {
+        if (store_mode == 1) stage16(st, v, false);
+        else store_bf16x16(static_cast<__nv_bfloat16 *>(ep.out) + (size_t)row * ep.ldo + col, v);
+    }
     if (ep.outT) {
         // lanes hold consecutive rows: each store instruction writes 64 contiguous bytes
         __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(ep.outT) + (size_t)col * ep.ldt + row;
@@ -210,10 +257,14 @@ __device__ __forceinline__ void epilogue16(const npx_gemm_epilogue &ep, float (&
     }
 }
 
-template <int BN>
+// STORE = 2: the FP32 row-major output (outf) leaves through per-warp shared-memory boxes and TMA
+// stores (tout); STORE = 0: every output is stored directly.
+template <int BN, int STORE>
 __global__ void __launch_bounds__(THREADS, 1)
-gemm_tn_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int M, int N,
-               int k_per_split, int splits, npx_gemm_epilogue ep, int *err) {
+gemm_tn_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+               const __grid_constant__ CUtensorMap tout, int M, int N, int k_per_split, int splits,
+               npx_gemm_epilogue ep, int *err) {
+    constexpr int store_mode = STORE;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
@@ -228,6 +279,9 @@ gemm_tn_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ C
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
     int *issued = reinterpret_cast<int *>(tmem_slot + 2);      // k-blocks whose copies were started
     int *consumed = reinterpret_cast<int *>(tmem_slot + 3);    // k-blocks whose copies were waited for
+    // per epilogue warp, a 2 KB staging area for the TMA store of the row-major output: two
+    // 32 x 16 BF16 boxes (double-buffered) or one 32 x 16 FP32 box
+    uint8_t *stage_base = sB + STAGES * B_BYTES + 1024;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_m = M / BM, tiles_n = N / BN, total = tiles_m * tiles_n * splits;
@@ -327,6 +381,9 @@ gemm_tn_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ C
         // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 and column quarter (w - 2) / 4
         const int q = warp & 3, part = (warp - 2) >> 2;
         constexpr int COLS = BN / (EPI_WARPS / 4);
+        uint8_t *stage = stage_base + (warp - 2) * 2048;
+        const bool f32 = store_mode == 2;
+        int nstore = 0;   // TMA stores issued by this warp
         int tl = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x, ++tl) {
             const int b = tl & 1;
@@ -344,14 +401,42 @@ gemm_tn_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ C
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN);
 #pragma unroll 1
             for (int c0 = part * COLS; c0 < (part + 1) * COLS; c0 += 16) {
+                uint32_t r[16];
+                tmem_ld16_issue(taddr + (uint32_t)c0, r);
+                tmem_wait_ld();
                 float v[16];
-                tmem_ld16(taddr + (uint32_t)c0, v);
-                epilogue16(ep, v, row, n0 + c0, split);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+                uint8_t *box = nullptr;
+                if (store_mode) {
+                    // the staging box is free once the store that last read it has read it
+                    box = stage + (f32 ? 0 : (nstore & 1) * 1024);
+                    if (f32 ? nstore >= 1 : nstore >= 2) {
+                        if (lane == 0) {
+                            if (f32) bulk_wait_read<0>();
+                            else bulk_wait_read<1>();
+                        }
+                        __syncwarp();
+                    }
+                }
+                epilogue16(ep, v, row, n0 + c0, split, store_mode, box + lane * (f32 ? 64 : 32));
+                if (store_mode) {
+                    fence_async_shared();
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (f32) tma_store_3d(&tout, n0 + c0, m0 + q * 32, split, box);
+                        else tma_store_2d(&tout, n0 + c0, m0 + q * 32, box);
+                        bulk_commit();
+                    }
+                    ++nstore;
+                }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[b]);
         }
+        if (store_mode && lane == 0) bulk_wait_all();   // the stores have landed before the CTA ends
+        __syncwarp();
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -399,9 +484,26 @@ static bool make_map(CUtensorMap *m, const void *ptr, int rows, int cols, int bo
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN>
+// map of the row-major output written by the epilogue's TMA stores, in boxes of 32 rows x 16
+// columns: BF16 [rows x cols] with row stride ld (2-D), or FP32 split partials
+// [splits][rows x cols] with row stride ld and split stride split_stride (3-D)
+static bool make_out_map(CUtensorMap *m, void *ptr, bool f32, int rows, int cols, long long ld, int splits,
+                         long long split_stride) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t es = f32 ? 4 : 2;
+    const cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)splits};
+    const cuuint64_t strides[2] = {(cuuint64_t)ld * es, (cuuint64_t)(splits > 1 ? split_stride : ld * rows) * es};
+    const cuuint32_t box[3] = {16, 32, 1};
+    const cuuint32_t el[3] = {1, 1, 1};
+    return fn(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, f32 ? 3 : 2, ptr, dims,
+              strides, box, el, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, int STORE>
 static size_t smem_bytes() {
-    return 1024 + (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + (2 * STAGES + 5) * 8 + 16;
+    return 1024 + (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 1024 + (STORE ? (size_t)EPI_WARPS * 2048 : 0);
 }
 
 static int sm_count() {
@@ -415,15 +517,15 @@ static int sm_count() {
     return n;
 }
 
-template <int BN>
-static cudaError_t launch(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int K, int splits,
-                          const npx_gemm_epilogue &ep, int *err, cudaStream_t st) {
-    const size_t smem = smem_bytes<BN>();
-    cudaError_t e = cudaFuncSetAttribute(gemm_tn_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int BN, int STORE>
+static cudaError_t launch(const CUtensorMap &ta, const CUtensorMap &tb, const CUtensorMap &tout, int M, int N, int K,
+                          int splits, const npx_gemm_epilogue &ep, int *err, cudaStream_t st) {
+    const size_t smem = smem_bytes<BN, STORE>();
+    cudaError_t e = cudaFuncSetAttribute(gemm_tn_kernel<BN, STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int tiles = (M / BM) * (N / BN) * splits;
     const int grid = tiles < sm_count() ? tiles : sm_count();
-    gemm_tn_kernel<BN><<<grid, THREADS, smem, st>>>(ta, tb, M, N, K / splits, splits, ep, err);
+    gemm_tn_kernel<BN, STORE><<<grid, THREADS, smem, st>>>(ta, tb, tout, M, N, K / splits, splits, ep, err);
     return cudaGetLastError();
 }
 
@@ -455,12 +557,26 @@ extern "C" int npx_gemm_bf16(const void *A, const void *B, int M, int N, int K, 
         (ep->outT && (reinterpret_cast<uintptr_t>(ep->outT) & 1)))
         return npx::set_last_error(NPX_EINVAL, "npx_gemm_bf16: outputs, bias and zin need 16-byte aligned rows");
     if (splits > 1 && ep->mode != NPX_EPI_F32) return npx::set_last_error(NPX_EINVAL, "npx_gemm_bf16: split K needs the F32 epilogue");
-    CUtensorMap ta, tb;
+    CUtensorMap ta, tb, tout;
     if (!make_map(&ta, A, M, K, BM) || !make_map(&tb, B, N, K, BN))
         return npx::set_last_error(NPX_ECUDA, "npx_gemm_bf16: tensor-map encoding failed");
+    // FP32 row-major output leaves through TMA stores (BF16 outputs are stored directly: those
+    // epilogues are bound by the GELU arithmetic, and staging them measured slower)
+    memset(&tout, 0, sizeof tout);
+    int store_mode = 0;
+    if (ep->outf && !(ep->out && ep->mode != NPX_EPI_F32)) {
+        if (!make_out_map(&tout, ep->outf, true, M, N, ep->ldf, ep->mode == NPX_EPI_F32 ? splits : 1, ep->split_stride))
+            return npx::set_last_error(NPX_ECUDA, "npx_gemm_bf16: output tensor-map encoding failed");
+        store_mode = 2;
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = BN == 256 ? launch<256>(ta, tb, M, N, K, splits, *ep, err, st)
-                              : launch<128>(ta, tb, M, N, K, splits, *ep, err, st);
+    cudaError_t e;
+    if (store_mode)
+        e = BN == 256 ? launch<256, 2>(ta, tb, tout, M, N, K, splits, *ep, err, st)
+                      : launch<128, 2>(ta, tb, tout, M, N, K, splits, *ep, err, st);
+    else
+        e = BN == 256 ? launch<256, 0>(ta, tb, tout, M, N, K, splits, *ep, err, st)
+                      : launch<128, 0>(ta, tb, tout, M, N, K, splits, *ep, err, st);
     if (e != cudaSuccess) return npx::set_last_error(NPX_ECUDA, cudaGetErrorString(e));
     return NPX_OK;
 }
