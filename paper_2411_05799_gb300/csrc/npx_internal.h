@@ -69,6 +69,12 @@ cudaError_t launch_advance(long long *d_step, int n, cudaStream_t st);
 cudaError_t launch_init(const WorldDev &W, const float *d_origin, const float *d_quat,
                         const float *d_vel, const float *d_omega, cudaStream_t st);
 cudaError_t launch_refresh(const WorldDev &W, cudaStream_t st);
+// state exchange with the caller's layouts: AoS blocks <-> SoA state, contact flags between the
+// caller's point order and the stored one (perm[i] = caller index of stored point i)
+cudaError_t launch_scatter_state(const WorldDev &W, const float *aos, cudaStream_t st);
+cudaError_t launch_gather_state(const WorldDev &W, float *aos, cudaStream_t st);
+cudaError_t launch_permute_kappa(uint8_t *dst, const uint8_t *src, const int *perm, int P, bool to_stored,
+                                 cudaStream_t st);
 // ---- learned surrogate
 // Per-scene posed shape (a function of the joint angles), rebuilt whenever they change.
 struct SurCache {

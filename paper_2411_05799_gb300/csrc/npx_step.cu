@@ -1380,6 +1380,68 @@ cudaError_t launch_kappa_refresh(const WorldDev &W, const int *list, const int *
     return cudaLaunchKernel(fn, dim3(blocks), dim3(SUR_WPB * 32), args, SUR_WPB * sb, st);
 }
 
+// ------------------------------------------------------------------------ state in and out
+// The caller's arrays are per scene (AoS: cog[3S], quat[4S], vel[3S], angmom[3S], omega[3S]) and its
+// points in its own order; the device keeps SoA state and points by construction height (perm[i] =
+// the caller's index of stored point i).  These kernels do the transposes and permutations next to
+// the data, so a state exchange is one copy each way.
+
+// staged AoS state (cog | quat | vel | angmom blocks) -> SoA state
+__global__ void scatter_state_kernel(WorldDev W, const float *aos) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= W.S) return;
+    const int S = W.S;
+    const float *cog = aos, *quat = aos + 3 * S, *vel = aos + 7 * S, *L = aos + 10 * S;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        W.st[(ST_CX + k) * S + s] = cog[3 * s + k];
+        W.st[(ST_VX + k) * S + s] = vel[3 * s + k];
+        W.st[(ST_LX + k) * S + s] = L[3 * s + k];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) W.st[(ST_QW + k) * S + s] = quat[4 * s + k];
+}
+
+// SoA state and angular velocity -> AoS blocks cog | quat | vel | omega | angmom
+__global__ void gather_state_kernel(WorldDev W, float *aos) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= W.S) return;
+    const int S = W.S;
+    float *cog = aos, *quat = aos + 3 * S, *vel = aos + 7 * S, *om = aos + 10 * S, *L = aos + 13 * S;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        cog[3 * s + k] = W.st[(ST_CX + k) * S + s];
+        vel[3 * s + k] = W.st[(ST_VX + k) * S + s];
+        om[3 * s + k] = W.omega[k * S + s];
+        L[3 * s + k] = W.st[(ST_LX + k) * S + s];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) quat[4 * s + k] = W.st[(ST_QW + k) * S + s];
+}
+
+// contact flags: caller order -> stored order (to_stored) or back
+__global__ void permute_kappa_kernel(uint8_t *dst, const uint8_t *src, const int *perm, int P, int to_stored) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    if (to_stored) dst[i] = src[perm[i]] ? 1 : 0;
+    else dst[perm[i]] = src[i];
+}
+
+cudaError_t launch_scatter_state(const WorldDev &W, const float *aos, cudaStream_t st) {
+    scatter_state_kernel<<<(W.S + 255) / 256, 256, 0, st>>>(W, aos);
+    return cudaGetLastError();
+}
+cudaError_t launch_gather_state(const WorldDev &W, float *aos, cudaStream_t st) {
+    gather_state_kernel<<<(W.S + 255) / 256, 256, 0, st>>>(W, aos);
+    return cudaGetLastError();
+}
+cudaError_t launch_permute_kappa(uint8_t *dst, const uint8_t *src, const int *perm, int P, bool to_stored,
+                                 cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    permute_kappa_kernel<<<(P + 255) / 256, 256, 0, st>>>(dst, src, perm, P, to_stored ? 1 : 0);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------ host-side launchers
 
 // per-scene shared memory of the step kernel: the slot, plus the height-map window on maps

@@ -99,7 +99,9 @@ struct npx_world {
     std::vector<DevBuf> bufs;
     npx::WorldDev W{};
     long long *d_step = nullptr;
-    float *d_stage = nullptr;           // state_set staging [13 * S]
+    float *d_stage = nullptr;           // state staging, AoS blocks [16 * S]
+    uint8_t *d_kstage = nullptr;        // contact-flag staging in the caller's order [P]
+    int *d_perm = nullptr;              // [P] caller index of each stored point
     float *d_points = nullptr;          // points_read staging [3 * max_points]
     long long step = 0;
     // launch shape
@@ -741,7 +743,8 @@ int npx_world_finalize(npx_world *w) {
         (rc = dev_alloc(w, &d_lcog, 3 * (size_t)w->L)) ||
         (rc = dev_alloc(w, &d_omega, 3 * (size_t)S)) || (rc = dev_alloc(w, &d_sens, S)) ||
         (rc = dev_alloc(w, &d_status, S)) || (rc = dev_alloc(w, &d_queue, 1)) ||
-        (rc = dev_alloc(w, &w->d_step, 1)) || (rc = dev_alloc(w, &w->d_stage, 13 * (size_t)S)) ||
+        (rc = dev_alloc(w, &w->d_step, 1)) || (rc = dev_alloc(w, &w->d_stage, 16 * (size_t)S)) ||
+        (rc = dev_alloc(w, &w->d_kstage, w->P)) || (rc = dev_alloc(w, &w->d_perm, w->P)) ||
         (rc = dev_alloc(w, &w->d_points, 3 * (size_t)w->max_points)))
         return rc;
     CUDA_TRY(cudaMemcpy(d_lo, w->link_off.data(), sizeof(int) * (S + 1), cudaMemcpyHostToDevice));
@@ -754,6 +757,7 @@ int npx_world_finalize(npx_world *w) {
     CUDA_TRY(cudaMemcpy(d_mu, w->mu.data(), sizeof(float) * S, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(d_gref, gref.data(), sizeof(float) * 3 * S, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(d_lcog, lcog.data(), sizeof(float) * 3 * w->L, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(w->d_perm, w->perm.data(), sizeof(int) * w->P, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemset(d_act, 0, sizeof(float4) * std::max(w->J, 1)));
     CUDA_TRY(cudaMemset(d_nu, 0, sizeof(uint32_t) * std::max(w->J, 1)));
     CUDA_TRY(cudaMemset(d_theta, 0, sizeof(float) * std::max(w->J, 1)));
@@ -821,23 +825,19 @@ int npx_state_write(npx_world *w, const float *cog, const float *quat, const flo
     if (step < 0) return fail(NPX_EINVAL, "step must be >= 0");
     CUDA_TRY(cudaSetDevice(w->device));
     const size_t S = w->S;
-    std::vector<float> st((size_t)npx::ST_N * S);
-    for (size_t s = 0; s < S; ++s) {
-        for (int k = 0; k < 3; ++k) {
-            st[(npx::ST_CX + k) * S + s] = cog[3 * s + k];
-            st[(npx::ST_VX + k) * S + s] = vel[3 * s + k];
-            st[(npx::ST_LX + k) * S + s] = angmom[3 * s + k];
-        }
-        for (int k = 0; k < 4; ++k) st[(npx::ST_QW + k) * S + s] = quat[4 * s + k];
-    }
-    CUDA_TRY(cudaMemcpyAsync(w->W.st, st.data(), st.size() * sizeof(float), cudaMemcpyHostToDevice, w->stream));
+    // the caller's arrays go to the device as they are (one copy each); kernels transpose and
+    // permute them there
+    float *d = w->d_stage;
+    CUDA_TRY(cudaMemcpyAsync(d, cog, 3 * S * sizeof(float), cudaMemcpyHostToDevice, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(d + 3 * S, quat, 4 * S * sizeof(float), cudaMemcpyHostToDevice, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(d + 7 * S, vel, 3 * S * sizeof(float), cudaMemcpyHostToDevice, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(d + 10 * S, angmom, 3 * S * sizeof(float), cudaMemcpyHostToDevice, w->stream));
+    CUDA_TRY(npx::launch_scatter_state(w->W, d, w->stream));
     if (theta && w->J > 0)
         CUDA_TRY(cudaMemcpyAsync(w->W.theta, theta, w->J * sizeof(float), cudaMemcpyHostToDevice, w->stream));
-    std::vector<uint8_t> kap;
     if (contact_prev) {
-        kap.resize(w->P);
-        for (int i = 0; i < w->P; ++i) kap[i] = contact_prev[w->perm[i]] ? 1 : 0;
-        CUDA_TRY(cudaMemcpyAsync(w->W.kappa, kap.data(), w->P, cudaMemcpyHostToDevice, w->stream));
+        CUDA_TRY(cudaMemcpyAsync(w->d_kstage, contact_prev, w->P, cudaMemcpyHostToDevice, w->stream));
+        CUDA_TRY(npx::launch_permute_kappa(w->W.kappa, w->d_kstage, w->d_perm, w->P, true, w->stream));
     } else {
         CUDA_TRY(cudaMemsetAsync(w->W.kappa, 0, w->P, w->stream));
     }
@@ -845,7 +845,7 @@ int npx_state_write(npx_world *w, const float *cog, const float *quat, const flo
     const long long st64 = step;
     CUDA_TRY(cudaMemcpyAsync(w->d_step, &st64, sizeof st64, cudaMemcpyHostToDevice, w->stream));
     CUDA_TRY(npx::launch_refresh(w->W, w->stream));
-    CUDA_TRY(cudaStreamSynchronize(w->stream));
+    CUDA_TRY(cudaStreamSynchronize(w->stream));   // the caller's arrays have been read
     w->step = step;
     return NPX_OK;
 }
@@ -854,10 +854,9 @@ int npx_contacts_read(npx_world *w, uint8_t *contact, size_t n) {
     if (int rc = check_ready(w)) return rc;
     if (!contact || n < (size_t)w->P) return fail(NPX_EINVAL, "buffer holds %zu flags, world has %d points", n, w->P);
     CUDA_TRY(cudaSetDevice(w->device));
-    std::vector<uint8_t> kap(w->P);
-    CUDA_TRY(cudaMemcpyAsync(kap.data(), w->W.kappa, w->P, cudaMemcpyDeviceToHost, w->stream));
+    CUDA_TRY(npx::launch_permute_kappa(w->d_kstage, w->W.kappa, w->d_perm, w->P, false, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(contact, w->d_kstage, w->P, cudaMemcpyDeviceToHost, w->stream));
     CUDA_TRY(cudaStreamSynchronize(w->stream));
-    for (int i = 0; i < w->P; ++i) contact[w->perm[i]] = kap[i];
     return NPX_OK;
 }
 
@@ -930,20 +929,18 @@ int npx_sensors_read(npx_world *w, npx_sensors *o) {
     if (!o) return fail(NPX_EINVAL, "null sensors");
     CUDA_TRY(cudaSetDevice(w->device));
     const size_t S = w->S;
-    std::vector<float> st((size_t)npx::ST_N * S), om(3 * S);
-    CUDA_TRY(cudaMemcpyAsync(st.data(), w->W.st, st.size() * sizeof(float), cudaMemcpyDeviceToHost, w->stream));
-    if (o->omega) CUDA_TRY(cudaMemcpyAsync(om.data(), w->W.omega, om.size() * sizeof(float), cudaMemcpyDeviceToHost, w->stream));
+    // per-scene (AoS) blocks assembled on the device, then one copy into each caller array
+    float *d = w->d_stage;
+    CUDA_TRY(npx::launch_gather_state(w->W, d, w->stream));
+    const struct { float *dst; size_t off, n; } parts[5] = {
+        {o->cog, 0, 3 * S}, {o->quat, 3 * S, 4 * S}, {o->vel, 7 * S, 3 * S}, {o->omega, 10 * S, 3 * S},
+        {o->angmom, 13 * S, 3 * S}};
+    for (const auto &p : parts)
+        if (p.dst) CUDA_TRY(cudaMemcpyAsync(p.dst, d + p.off, p.n * sizeof(float), cudaMemcpyDeviceToHost, w->stream));
     if (o->theta && w->J > 0) CUDA_TRY(cudaMemcpyAsync(o->theta, w->W.theta, w->J * sizeof(float), cudaMemcpyDeviceToHost, w->stream));
     if (o->contacts) CUDA_TRY(cudaMemcpyAsync(o->contacts, w->W.sensors, S * sizeof(uint32_t), cudaMemcpyDeviceToHost, w->stream));
     if (o->status) CUDA_TRY(cudaMemcpyAsync(o->status, w->W.status, S * sizeof(uint32_t), cudaMemcpyDeviceToHost, w->stream));
     CUDA_TRY(cudaStreamSynchronize(w->stream));
-    for (size_t s = 0; s < S; ++s) {
-        if (o->cog) for (int k = 0; k < 3; ++k) o->cog[3 * s + k] = st[(npx::ST_CX + k) * S + s];
-        if (o->quat) for (int k = 0; k < 4; ++k) o->quat[4 * s + k] = st[(npx::ST_QW + k) * S + s];
-        if (o->vel) for (int k = 0; k < 3; ++k) o->vel[3 * s + k] = st[(npx::ST_VX + k) * S + s];
-        if (o->angmom) for (int k = 0; k < 3; ++k) o->angmom[3 * s + k] = st[(npx::ST_LX + k) * S + s];
-        if (o->omega) for (int k = 0; k < 3; ++k) o->omega[3 * s + k] = om[k * S + s];
-    }
     if (o->step) *o->step = w->step;
     return NPX_OK;
 }

@@ -309,8 +309,11 @@ class World:
         _check(_lib.npx_state_write(self._h, _p(c), _p(q), _p(v), _p(L), _p(th), _p(k),
                                     int(step)))
 
-    def contacts(self) -> np.ndarray:
-        out = np.zeros(self._info["n_points"], np.uint8)
+    def contacts(self, out: np.ndarray | None = None) -> np.ndarray:
+        """Per-point contact flags of the last step, in the caller's point order (npx_contacts_read),
+        into a new array or into out (uint8, n_points)."""
+        if out is None:
+            out = np.zeros(self._info["n_points"], np.uint8)
         _check(_lib.npx_contacts_read(self._h, _p(out), out.size))
         return out
 
@@ -324,13 +327,24 @@ class World:
     def sync(self):
         _check(_lib.npx_world_sync(self._h))
 
-    def read(self) -> dict:
+    def read_buffers(self) -> dict:
+        """Arrays for read(out=...): allocate them once (pinned memory makes the copies DMA)."""
         S, J = self.n_scenes, self._info["n_joints"]
-        out = {"cog": np.zeros((S, 3), np.float32), "quat": np.zeros((S, 4), np.float32),
-               "vel": np.zeros((S, 3), np.float32), "omega": np.zeros((S, 3), np.float32),
-               "angmom": np.zeros((S, 3), np.float32), "theta": np.zeros(J, np.float32),
-               "contacts": np.zeros(S, np.uint32), "status": np.zeros(S, np.uint32),
-               "step": np.zeros(1, np.int64)}
+        return {"cog": np.zeros((S, 3), np.float32), "quat": np.zeros((S, 4), np.float32),
+                "vel": np.zeros((S, 3), np.float32), "omega": np.zeros((S, 3), np.float32),
+                "angmom": np.zeros((S, 3), np.float32), "theta": np.zeros(J, np.float32),
+                "contacts": np.zeros(S, np.uint32), "status": np.zeros(S, np.uint32),
+                "step": np.zeros(1, np.int64)}
+
+    def read(self, out: dict | None = None) -> dict:
+        """State and sensors (npx_sensors_read) into new arrays, or into out's arrays (same
+        shapes and dtypes as read_buffers(); returned with "step" as an int)."""
+        if out is None:
+            out = self.read_buffers()
+        else:
+            out = dict(out)
+            if not isinstance(out.get("step"), np.ndarray):
+                out["step"] = np.zeros(1, np.int64)
         s = Sensors(*[_p(out[k]) for k in ("cog", "quat", "vel", "omega", "angmom", "theta",
                                            "contacts", "status", "step")])
         _check(_lib.npx_sensors_read(self._h, C.byref(s)))
