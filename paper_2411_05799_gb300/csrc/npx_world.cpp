@@ -637,6 +637,9 @@ int npx_world_finalize(npx_world *w) {
     }
     w->L = w->link_off[S];
     w->P = w->point_off[S];
+    if (w->max_points > 64 * 32)
+        return fail(NPX_ERANGE, "a scene has %d points; at most 2048 (64 per lane at 32 lanes per scene)",
+                    w->max_points);
     for (int s = 0; s < S; ++s) {
         if (w->link_off[s + 1] - w->link_off[s] != w->max_links) w->uniform_links = false;
         for (int sid : w->flats[s].sensor) w->sensor_bits = std::max(w->sensor_bits, sid + 1);

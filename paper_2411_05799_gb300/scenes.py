@@ -432,6 +432,22 @@ def tilted_gravity(batch: SceneBatch, theta: float, g: float = 9.81) -> SceneBat
                                 float(np.float32(-g * math.cos(theta)))))
 
 
+def ragged_bodies(counts, seed_key: int = 0, mu: float = 0.6) -> SceneBatch:
+    """Single-link bodies with the given point counts (uniform in a 0.2 x 0.1 x 0.05 m box, 1 kg),
+    random orientation, dropped from 0.3 m with random linear and angular velocity onto flat
+    ground: ragged batches from one point up to the largest scene a world holds."""
+    rng = _rng(7, seed_key)
+    S = len(counts)
+    robots = []
+    for n in counts:
+        pts = box_uniform(rng, (0.2, 0.1, 0.05), (0.0, 0.0, 0.0), int(n))
+        robots.append(([((0.2, 0.1, 0.05), (0, 0, 0), 1.0, -1, None, None, -1)], [pts]))
+    origin = np.column_stack([rng.uniform(-1, 1, S), rng.uniform(-1, 1, S), np.full(S, 0.3)])
+    return _assemble(robots, mu=np.full(S, mu), origin=origin, quat=random_unit_quat(rng, S),
+                     vel=rng.normal(0.0, 0.5, (S, 3)), omega=rng.normal(0.0, 2.0, (S, 3)),
+                     act_params=None, name="ragged_bodies", act_mode=ACT_HOLD)
+
+
 def block_batch(n_scenes=1, mu=0.5, extent=(0.2, 0.2, 0.1), counts=(3, 3, 2), mass=1.0,
                 z_gap=0.0, vel=(0.0, 0.0, 0.0), omega=(0.0, 0.0, 0.0), name="block") -> SceneBatch:
     """A single-link lattice block resting (bottom face at z = z_gap) on flat ground."""

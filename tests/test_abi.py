@@ -127,3 +127,24 @@ def test_batched_construction_validates(lib):
     sb3 = npx.SceneBatchC(1, 2, *[a.ctypes.data for a in keep])
     assert lib.npx_scenes_add(h, C.byref(sb3)) == -1          # scenes 1..2 exceed n_scenes
     lib.npx_world_destroy(h)
+
+
+def test_scene_size_limit_is_checked_on_the_host(lib):
+    from paper_2411_05799_gb300 import scenes
+    b = scenes.ragged_bodies([2049])
+    rc, h = _create(lib, n_scenes=1)
+    keep = [npx._i32(b.link_off), npx._i32(b.point_off), npx._i32(b.parent), npx._f32(b.anchor),
+            npx._f32(b.axis), npx._f32(b.lo), npx._f32(b.hi), npx._i32(b.sensor),
+            npx._f32(b.p0), npx._f32(b.m), npx._i32(b.plink), npx._f32(b.mu), npx._i32(b.hmap)]
+    sb = npx.SceneBatchC(0, 1, *[a.ctypes.data for a in keep])
+    assert lib.npx_scenes_add(h, C.byref(sb)) == npx_build_codes("ERANGE")   # at most 2048 points
+    lib.npx_world_destroy(h)
+    # the largest scene is accepted
+    b = scenes.ragged_bodies([2048])
+    rc, h = _create(lib, n_scenes=1)
+    keep = [npx._i32(b.link_off), npx._i32(b.point_off), npx._i32(b.parent), npx._f32(b.anchor),
+            npx._f32(b.axis), npx._f32(b.lo), npx._f32(b.hi), npx._i32(b.sensor),
+            npx._f32(b.p0), npx._f32(b.m), npx._i32(b.plink), npx._f32(b.mu), npx._i32(b.hmap)]
+    sb = npx.SceneBatchC(0, 1, *[a.ctypes.data for a in keep])
+    assert lib.npx_scenes_add(h, C.byref(sb)) == 0
+    lib.npx_world_destroy(h)

@@ -369,3 +369,38 @@ def test_runtime_argument_errors():
         w.add_scenes(b)                   # after finalize
     with pytest.raises(NpxError):
         w.import_state(b"\0" * 16)
+
+
+def test_ragged_extremes_per_step():
+    """One world from a single point up to the largest scene (2,048 points, 64 per lane at 32
+    lanes per scene), tumbling onto the ground, step by step against the oracle.  (Two-point rods
+    are left out: their inertia about the rod axis is only the point-sphere term, a condition
+    number near 1e4, which puts FP32 angular velocities beyond 1e-5 per step; the oracle's rod pin
+    covers them.)"""
+    counts = [2048, 1, 4, 3, 31, 32, 33, 63, 64, 65, 511, 1024, 1500, 7]
+    b = scenes.ragged_bodies(counts, seed_key=5)
+    w = World.from_batch(b)
+    assert w.info()["max_points"] == 2048 and w.info()["lanes_per_scene"] == 32
+    _assert_step_parity(w, Oracle(b, threads=THREADS), [0, 1, 100, 200, 260, 300, 400, 700],
+                        max_near_frac=0.3)
+
+
+def test_size_classes_match_the_oracle():
+    """A world that splits into two size classes (small and large scenes, one launch each) gives
+    the same 200-step results as the oracle."""
+    counts = [8] * 1100 + [600] * 1100
+    b = scenes.ragged_bodies(counts, seed_key=6)
+    w = World.from_batch(b)
+    assert w.info()["size_classes"] == 2
+    dc, da, r, o = _window_world(b, w, 200)
+    assert ((dc <= 1e-3) & (da <= 1e-3)).mean() >= 0.95
+    assert np.median(dc) < 1e-5
+
+
+def _window_world(b, w, horizon):
+    o = Oracle(b, threads=THREADS)
+    to_gpu(w, o)
+    o.step(horizon, threads=THREADS)
+    w.step(horizon)
+    r = w.read()
+    return np.linalg.norm(r["cog"] - o.c, axis=1), quat_angle(r["quat"], o.q), r, o
