@@ -325,9 +325,22 @@ __device__ __noinline__ void shape_update(const WorldDev &W, int s, int p0, int 
     // every shape update) while the link frames are built
     uint8_t *lk = reinterpret_cast<uint8_t *>(pts) + tiles_offset(W.max_points, W.max_links);
 #pragma unroll 8
-    for (int i = gl; i < np; i += LPS) {
-        cp_async16(pts + i, W.p0m + p0 + i);
-        lk[i] = W.plink[p0 + i];
+    for (int i = gl; i < np; i += LPS) cp_async16(pts + i, W.p0m + p0 + i);
+    {
+        // the link bytes as whole aligned words (a quarter of the loads), the unaligned head and
+        // tail byte by byte; every read stays inside the scene's bytes
+        const uint8_t *src = W.plink + p0;
+        const int h = min((int)((4u - ((uint32_t)(uintptr_t)src & 3u)) & 3u), np);
+        const int nw = (np - h) >> 2;
+        const uint32_t *ws = reinterpret_cast<const uint32_t *>(src + h);
+        for (int i = gl; i < h; i += LPS) lk[i] = src[i];
+#pragma unroll 4
+        for (int k = gl; k < nw; k += LPS) {
+            const uint32_t v = ws[k];
+            uint8_t *d = lk + h + 4 * k;
+            d[0] = (uint8_t)v; d[1] = (uint8_t)(v >> 8); d[2] = (uint8_t)(v >> 16); d[3] = (uint8_t)(v >> 24);
+        }
+        for (int i = h + 4 * nw + gl; i < np; i += LPS) lk[i] = src[i];
     }
     link_frames<LPS>(W, l0, nl, th, fr, gl);
     cp_async_wait_all();
