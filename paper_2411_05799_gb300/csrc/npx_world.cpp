@@ -1207,7 +1207,7 @@ int npx_world_autotune(npx_world *w, int n_steps, npx_world_info *out) {
             if (cls.max_points > 64 * lps) continue;
             // fixed block sizes plus the "balanced" ones that spread the class's scenes evenly
             // over all SMs with 1, 2 or 3 resident blocks per SM
-            std::vector<int> wpb_list = {2, 4, 8, 16};
+            std::vector<int> wpb_list = {1, 2, 4, 8, 16};
             const int G = 32 / lps;
             for (int k = 1; k <= 3; ++k) {
                 const long long per = (long long)w->n_sm * G * k;
