@@ -51,6 +51,12 @@ FLOPS_PER = {"points": 7, "contacts": 27, "friction_pts": 42, "tick_points": 115
              "scene_steps": 320}
 
 
+# DRAM bytes (read + write) of one 1,000-step step-kernel launch on this workload, by launch shape
+# (lanes per scene, warps per block, blocks), from ncu (profiles/step_kernel_hexapod4096x1000_dram.md);
+# reported only for a captured shape, and to be re-taken whenever the kernel changes
+STEP_TRAFFIC = {(8, 7, 147): 31872768}
+
+
 def algorithmic_flops(counts: dict) -> float:
     return float(sum(FLOPS_PER[k] * counts[k] for k in FLOPS_PER))
 
@@ -419,9 +425,11 @@ def run_gpu(args):
         flops_per_ss = algorithmic_flops(r["counts"]) / r["counts"]["scene_steps"]
         launch_ms = total_ms / max(1, launches)
         achieved = flops_per_ss * N_SCENES * CHUNK / (launch_ms / 1e3) / 1e12
+        shape = (info["lanes_per_scene"], info["warps_per_block"], info["blocks"])
         line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                             "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                            "traffic": None, "kernel": "step_kernel",
+                            "traffic": STEP_TRAFFIC.get(shape) if CHUNK == 1000 else None,
+                            "kernel": "step_kernel",
                             "flops_per_scene_step": flops_per_ss,
                             "peak_note": "FP32 FMA peak from unit counts and max SM clock"}
         line["cpu_baseline"] = {"value": r["scene_steps_per_s"], "unit": UNIT, "cores": threads,
