@@ -141,11 +141,13 @@ int npx_state_set(npx_world *w, const float *origin, const float *quat, const fl
  * angular momentum about the CoG [S*3], joint angles [J], contact flags of the previous step per
  * mass point [P] (NULL clears them; 1 = in contact), and the global step counter n (which fixes
  * the joint-update phase n % K and the actuator phase).  Status words are cleared; the contact
- * sensors are recomputed from contact_prev. */
+ * sensors are recomputed from contact_prev.  The arrays are read before the call returns (each is
+ * copied to the device once; pinned host memory makes that a DMA transfer). */
 int npx_state_write(npx_world *w, const float *cog, const float *quat, const float *vel,
                     const float *angmom, const float *theta, const uint8_t *contact_prev,
                     int64_t step);
-/* Per mass point contact flag of the last step [P] (1 = in contact), scene-major. */
+/* Per mass point contact flag of the last step [P] (1 = in contact), scene-major, in the order the
+ * points were given; returns when the array is filled. */
 int npx_contacts_read(npx_world *w, uint8_t *contact, size_t n);
 /* Actuators: NPX_ACT_HOLD (params ignored) or NPX_ACT_SINUSOID with params [J*4] =
  * (amplitude rad, frequency Hz, phase rad, bias rad) per joint.  The phase advances by
@@ -155,6 +157,8 @@ int npx_actuator_set(npx_world *w, int mode, const float *params);
 int npx_world_step(npx_world *w, int n);
 /* Wait for queued work; reports a latched error of an earlier asynchronous call. */
 int npx_world_sync(npx_world *w);
+/* Fill the caller's arrays of npx_sensors (after the queued steps); returns when they are filled.
+ * Each array is one copy from the device (pinned host memory makes it a DMA transfer). */
 int npx_sensors_read(npx_world *w, npx_sensors *out);
 /* World positions of one scene's mass points [n*3] (n = its point count) */
 int npx_points_read(npx_world *w, int scene, float *xyz, int n);
