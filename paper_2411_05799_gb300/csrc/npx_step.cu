@@ -395,9 +395,10 @@ __device__ __forceinline__ float ground(const WorldDev &W, int hm, float x, floa
     return __ldg(W.hm + ((size_t)hm * W.hm_ny + iy) * W.hm_nx + ix);
 }
 
-// The same lookup through a window of the scene's map in shared memory: cells [wx0, wx0 + HM_WIN)
-// x [wy0, wy0 + HM_WIN) come from the window, others from global memory (the same value either
-// way).
+// The same lookup through a window of the scene's map in shared memory.  The window (origin
+// wx0, wy0 >= 0) holds the height at the clamped index of each of its cells, so an unclamped index
+// inside it already reads the clamped cell's height; others are clamped and read from global
+// memory (the same value either way).
 template <bool FLAT>
 __device__ __forceinline__ float ground_win(const WorldDev &W, int hm, const float *win, int wx0, int wy0, float x,
                                             float y) {
@@ -405,10 +406,10 @@ __device__ __forceinline__ float ground_win(const WorldDev &W, int hm, const flo
     const float fx = __fmul_rn(__fsub_rn(x, W.hm_ox), W.hm_scale);
     const float fy = __fmul_rn(__fsub_rn(y, W.hm_oy), W.hm_scale);
     int ix = __float2int_rd(fx), iy = __float2int_rd(fy);
+    const unsigned ux = (unsigned)ix - (unsigned)wx0, uy = (unsigned)iy - (unsigned)wy0;
+    if (ux < (unsigned)HM_WIN && uy < (unsigned)HM_WIN) return win[uy * HM_WIN + ux];
     ix = min(max(ix, 0), W.hm_nx - 1);
     iy = min(max(iy, 0), W.hm_ny - 1);
-    const unsigned ux = (unsigned)(ix - wx0), uy = (unsigned)(iy - wy0);
-    if (ux < (unsigned)HM_WIN && uy < (unsigned)HM_WIN) return win[uy * HM_WIN + ux];
     return __ldg(W.hm + ((size_t)hm * W.hm_ny + iy) * W.hm_nx + ix);
 }
 
@@ -466,7 +467,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
     Shape shr = sh;
     // highest ground a point can meet (plus a margin for the rounding of the bound)
     const float hmax = (FLAT || hm < 0 ? 0.f : W.hm_max[hm]) + 1e-5f;
-    // height-map window (after the slot); its origin is invalid until the first refresh
+    // height-map window (after the slot); its origin is negative until the first refresh
     float *win = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(pts) +
                                            slot_bytes(W.max_points, W.max_links, LPS));
     int wx0 = -(1 << 24), wy0 = -(1 << 24);
@@ -525,7 +526,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             // groups of the warp refresh together; each loads only its own window)
             const int cx = __float2int_rd(__fmul_rn(__fsub_rn(c[0], W.hm_ox), W.hm_scale));
             const int cy = __float2int_rd(__fmul_rn(__fsub_rn(c[1], W.hm_oy), W.hm_scale));
-            const bool need = hm >= 0 && (abs(cx - (wx0 + HM_WIN / 2)) > HM_DRIFT ||
+            const bool need = hm >= 0 && (wx0 < 0 || abs(cx - (wx0 + HM_WIN / 2)) > HM_DRIFT ||
                                           abs(cy - (wy0 + HM_WIN / 2)) > HM_DRIFT);
             if (__any_sync(FULL_MASK, need)) {
                 if (need) {
@@ -534,7 +535,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
                     const float *map = W.hm + (size_t)hm * W.hm_ny * W.hm_nx;
                     for (int e = gl; e < HM_WIN * HM_WIN; e += LPS) {
                         const int iy = wy0 + e / HM_WIN, ix = wx0 + e % HM_WIN;
-                        win[e] = (iy < W.hm_ny && ix < W.hm_nx) ? __ldg(map + (size_t)iy * W.hm_nx + ix) : 0.f;
+                        win[e] = __ldg(map + (size_t)min(iy, W.hm_ny - 1) * W.hm_nx + min(ix, W.hm_nx - 1));
                     }
                 }
                 __syncwarp();

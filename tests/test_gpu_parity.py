@@ -220,21 +220,25 @@ def test_gpu_points_match_oracle_kinematics():
     np.testing.assert_allclose(r["omega"], o.omega(), rtol=1e-4, atol=1e-6)
 
 
-def test_gpu_heightmap_cells():
-    """Random clouds over a random height map: the first step's contact bits agree point for
-    point with the oracle's (same single-precision cell and contact decisions)."""
+@pytest.mark.parametrize("ny, nx, spread", [(16, 16, 0.4), (8, 12, 0.4), (40, 48, 1.8)])
+def test_gpu_heightmap_cells(ny, nx, spread):
+    """Random clouds over random height maps: the first step's contact bits agree point for
+    point with the oracle's (same single-precision cell and contact decisions).  The maps are the
+    size of the kernel's cached window, smaller than it (cells past the map's edge read the
+    clamped edge) and larger (points outside the window, windows clamped at the map's edges);
+    every cloud also reaches off the map."""
     rng = np.random.default_rng(21)
-    maps = rng.uniform(-0.05, 0.05, (2, 16, 16)).astype(np.float32)
+    maps = rng.uniform(-0.05, 0.05, (2, ny, nx)).astype(np.float32)
     S, n = 8, 200
     robots = []
     for _ in range(S):
         pts = scenes.box_uniform(rng, (1.6, 1.6, 0.12), (0, 0, 0), n)
         robots.append(([((1.6, 1.6, 0.12), (0, 0, 0), 1.0, -1, None, None, 0)], [pts]))
-    b = scenes._assemble(robots, mu=np.full(S, 0.5), origin=rng.uniform(-0.4, 0.4, (S, 3)) * [1, 1, 0],
+    b = scenes._assemble(robots, mu=np.full(S, 0.5), origin=rng.uniform(-spread, spread, (S, 3)) * [1, 1, 0],
                          quat=scenes.random_unit_quat(rng, S), vel=np.zeros((S, 3)),
                          omega=np.zeros((S, 3)), act_params=None, name="lut",
                          hmap=rng.integers(0, 2, S), heightmaps=maps, hm_scale=10.0,
-                         hm_origin=(-0.8, -0.8), act_mode=scenes.ACT_HOLD)
+                         hm_origin=(-nx / 20, -ny / 20), act_mode=scenes.ACT_HOLD)
     w = World.from_batch(b)
     o = Oracle(b)
     o.step(1)
