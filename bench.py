@@ -177,22 +177,22 @@ def _measured_peaks() -> dict:
         return {}
 
 
-def surrogate_leg(World, scenes, stream, device, n_transitions: int) -> dict:
-    """The learned surrogate: trained on n_transitions transitions of the 4,096-hexapod workload,
-    then stepping 65,536 hexapods (joint-update steps and scenes whose foot contacts change are
-    taken by the plain step); its throughput beside the plain step's on the same scenes, its
-    50-step error against the FP64 oracle on 256 held-out scenes, and its network's forward
-    pass against the bf16 tensor peak."""
+def surrogate_leg(World, scenes, stream, device, n_transitions: int, stride: int = 1) -> dict:
+    """The learned surrogate: trained on n_transitions transitions (windows of `stride` steps) of
+    the 4,096-hexapod workload, then stepping 65,536 hexapods (joint-update steps, the steps left
+    before them and scenes whose foot contacts change over a window are taken by the plain step);
+    its throughput beside the plain step's on the same scenes, its 50-step error against the FP64
+    oracle on 256 held-out scenes, and its network's forward pass against the bf16 tensor peak."""
     import torch
     from oracle.oracle import Oracle
     from paper_2411_05799_gb300 import npx, surrogate
     S, PERIOD = 65536, 80
     res = surrogate.train(scenes.hexapod_batch(4096, seed_key=40), n_transitions=n_transitions,
-                          passes=2, lr=1e-3, max_batch=S)
+                          passes=2, lr=1e-3, max_batch=S, stride=stride)
     sur = res["surrogate"]
     big = scenes.hexapod_batch(S, seed_key=5)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
-    out = {"workload": f"hexapod_18dof_{S}_scenes_flat_dt1ms_K80", "unit": UNIT}
+    out = {"workload": f"hexapod_18dof_{S}_scenes_flat_dt1ms_K80", "unit": UNIT, "stride": stride}
 
     def timed(fn, reps):
         ms = 0.0
@@ -215,11 +215,11 @@ def surrogate_leg(World, scenes, stream, device, n_transitions: int) -> dict:
     ms, _ = timed(lambda: w.step(CHUNK), 2)
     out["plain_value"] = S * 2 * CHUNK / (ms / 1e3)
     # surrogate steps: whole joint-update periods, after one warm-up period
-    npx.world_step_surrogate(w, sur.net, sur.norm, PERIOD)
+    sur.step(w, PERIOD)
     fb_total, reps = 0, 4
     ms, _ = 0.0, None
     for _ in range(reps):
-        m, fb = timed(lambda: npx.world_step_surrogate(w, sur.net, sur.norm, PERIOD), 1)
+        m, fb = timed(lambda: sur.step(w, PERIOD), 1)
         ms += m
         fb_total += fb
     out["value"] = S * PERIOD * reps / (ms / 1e3)
@@ -259,13 +259,13 @@ def surrogate_leg(World, scenes, stream, device, n_transitions: int) -> dict:
     ref.copy_state_from(o)
     ref.step(50)
     err = {}
-    for name, fn in (("surrogate", lambda ww: npx.world_step_surrogate(ww, sur.net, sur.norm, 50)),
+    for name, fn in (("surrogate", lambda ww: sur.step(ww, 50)),
                      ("plain", lambda ww: ww.step(50))):
         ww = World.from_batch(test_b, stream=stream.cuda_stream, device=device.index or 0)
         ww.write_state(o.c.astype(np.float32), o.q.astype(np.float32), o.v.astype(np.float32),
                        o.L.astype(np.float32), o.theta.astype(np.float32),
                        o.kappa.astype(np.uint8), o.n)
-        fn(ww)
+        fb = fn(ww)
         r = ww.read()
         dc = np.linalg.norm(r["cog"] - ref.c, axis=1)
         qa, qb = r["quat"].astype(np.float64), ref.q
@@ -274,6 +274,8 @@ def surrogate_leg(World, scenes, stream, device, n_transitions: int) -> dict:
         err[name] = {"cog_m_median": float(np.median(dc)), "cog_m_rms": float(np.sqrt(np.mean(dc ** 2))),
                      "cog_m_p90": float(np.percentile(dc, 90)),
                      "angle_rad_median": float(np.median(ang)), "angle_rad_rms": float(np.sqrt(np.mean(ang ** 2)))}
+        if name == "surrogate":   # scene-steps of the 50 that the plain step took (fallbacks)
+            err[name]["fallback_fraction"] = fb / (test_b.n_scenes * 50)
         ww.close()
     out["error_50_steps_vs_fp64_oracle"] = err
     u = res["unexplained"]
@@ -415,7 +417,8 @@ def run_gpu(args):
     if rank == 0 and not args.no_extra:
         line["other_workloads"] = other_workloads(World, scenes, stream, local)
     if rank == 0 and not args.no_surrogate:
-        line["surrogate"] = surrogate_leg(World, scenes, stream, dev, args.surrogate_transitions)
+        line["surrogate"] = surrogate_leg(World, scenes, stream, dev, args.surrogate_transitions,
+                                          args.surrogate_stride)
 
     if rank == 0:
         # algorithmic flops per scene-step from the oracle's event counts on a sample
@@ -480,16 +483,18 @@ def run_profile(args):
             stream.synchronize()
         print(json.dumps({"profile": "gemm", "rows": S, "finite": bool(torch.isfinite(y).all())}))
         return 0
+    stride = args.surrogate_stride
     res = surrogate.train(scenes.hexapod_batch(4096, seed_key=40), n_transitions=65536 * 8,
-                          passes=2, stat_periods=1, warm_steps=100, max_batch=S)
+                          passes=2, stat_periods=1, warm_steps=100, max_batch=S, stride=stride)
     sur = res["surrogate"]
     stream = torch.cuda.Stream()
+    n = 4 if stride == 1 else 80      # stride 1: four steps; else one joint-update period
     with torch.cuda.stream(stream):
         w = World.from_batch(scenes.hexapod_batch(S, seed_key=5), stream=stream.cuda_stream)
-        w.step(301)
-        fb = npx.world_step_surrogate(w, sur.net, sur.norm, 4)
+        w.step(321)
+        fb = sur.step(w, n)
         stream.synchronize()
-    print(json.dumps({"profile": "surrogate", "scenes": S, "steps": 4, "fallbacks": fb}))
+    print(json.dumps({"profile": "surrogate", "scenes": S, "steps": n, "stride": stride, "fallbacks": fb}))
     return 0
 
 
@@ -503,6 +508,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate leg")
     ap.add_argument("--surrogate-transitions", type=int, default=100_000_000)
+    ap.add_argument("--surrogate-stride", type=int, default=26,
+                    help="steps per surrogate prediction (window between joint updates)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)

@@ -98,7 +98,10 @@ int npx_mlp_set_lr(npx_mlp *net, float lr);
  * and the angular velocity (13 numbers), then the NL - 1 joint angles after the current step's
  * joint update and the NS contact bits of the last step: n_features = 14 NL - 1 + NS (271 for
  * the 18-DoF six-sensor hexapod).  The target of a transition is the change of the link part
- * over one step (n_targets = 13 NL), positions taken relative to the first state's CoG.
+ * over one window of `stride` steps (n_targets = 13 NL), positions taken relative to the first
+ * state's CoG.  A window never holds a joint-update step (n % K == 0): on actuated worlds a
+ * window starts at a step n with 1 <= n % K and n % K + stride <= K, so joint-update steps and
+ * the (K - 1) mod stride steps left over before them are plain steps.
  * Standardisation (all DEVICE arrays, NULL = raw values): features (x - x_mu) * x_isd, targets
  * (d - t_mu) / t_sd. */
 typedef struct {
@@ -106,18 +109,20 @@ typedef struct {
 } npx_surrogate_norm;
 
 int npx_surrogate_dims(npx_world *w, int *n_features, int *n_targets);
-/* Advance the world with the plain step until n_steps steps have been recorded, writing each
- * recorded step's features X and targets T (DEVICE, rows = step * n_scenes + scene, standardised
- * when norm is given).  Joint-update steps (n % K == 0) are stepped but not recorded: the
- * surrogate never takes them. */
-int npx_surrogate_collect(npx_world *w, const npx_surrogate_norm *norm, int n_steps, float *X,
-                          float *T);
-/* Advance the world n_steps steps with the surrogate: the network predicts every scene's next
- * state from its features; scenes whose contact sensors change during a step redo that step with
- * the plain step (the fallback), and joint-update steps (n % K == 0) are plain for every scene.  *fallbacks (host, may be NULL) receives the number of scene-steps that
- * fell back.  The network must take n_features inputs, give n_targets outputs, and hold at least
- * n_scenes rounded up to 128 rows. */
-int npx_world_step_surrogate(npx_world *w, npx_mlp *net, const npx_surrogate_norm *norm,
+/* Advance the world with the plain step until n_windows windows of `stride` steps (1 <= stride
+ * < K on actuated worlds) have been recorded, writing each window's features X (at its first
+ * step) and targets T (DEVICE, rows = window * n_scenes + scene, standardised when norm is
+ * given).  Steps outside windows are stepped but not recorded. */
+int npx_surrogate_collect(npx_world *w, const npx_surrogate_norm *norm, int stride, int n_windows,
+                          float *X, float *T);
+/* Advance the world n_steps steps with the surrogate: at each window start the network predicts
+ * every scene's state `stride` steps later from its features; scenes whose contact sensors at
+ * the predicted state differ from those at the window's start redo the window with the plain step
+ * (the fallback); steps outside windows, and a last window that does not fit in n_steps, are
+ * plain for every scene.  *fallbacks (host, may be NULL) receives the number of scene-steps that
+ * fell back.  The network must have been trained on windows of the same stride, take n_features
+ * inputs, give n_targets outputs, and hold at least n_scenes rounded up to 128 rows. */
+int npx_world_step_surrogate(npx_world *w, npx_mlp *net, const npx_surrogate_norm *norm, int stride,
                              int n_steps, long long *fallbacks);
 
 #ifdef __cplusplus

@@ -53,6 +53,9 @@ struct WorldDev {
     int max_points, max_links;
     const long long *step;                // device step counter n
     unsigned int *queue;                  // work-queue counter (reset before each launch)
+    // 1: the launch takes the previous-step contacts from a detection at the current state
+    // instead of kappa (after surrogate steps, which move scenes without detecting contacts)
+    int reseed;
 };
 
 struct LaunchCfg {
@@ -110,7 +113,8 @@ cudaError_t launch_surrogate_update(const WorldDev &W, const SurCache &C, const 
                                     const float *t_mu, const float *t_sd, float *nx, uint8_t *applied,
                                     uint32_t *sens_new, int *list, int *count, cudaStream_t st);
 cudaError_t launch_kappa_refresh(const WorldDev &W, const int *list, const int *count, cudaStream_t st);
-cudaError_t launch_accumulate(long long *total, int *count, cudaStream_t st);
+// *total += *count * mult, then *count = 0
+cudaError_t launch_accumulate(long long *total, int *count, int mult, cudaStream_t st);
 // records msg as the thread's npx_last_error() text and returns code
 int set_last_error(int code, const char *msg);
 cudaError_t launch_points(const WorldDev &W, int scene, float *d_out, cudaStream_t st);

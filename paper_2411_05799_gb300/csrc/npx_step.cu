@@ -455,13 +455,28 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
     }
     for (int j = gl; j < nj; j += LPS) th[j] = W.theta[j0 + j];
     uint64_t kprev = 0;
+    if (!W.reseed) {
 #pragma unroll 8
-    for (int k = 0, i = gl; i < np; ++k, i += LPS)
-        if (W.kappa[p0 + i]) kprev |= 1ull << k;
+        for (int k = 0, i = gl; i < np; ++k, i += LPS)
+            if (W.kappa[p0 + i]) kprev |= 1ull << k;
+    }
     __syncwarp();
     Shape sh;
     shape_update<LPS>(W, valid ? s : 0, p0, np, l0, nl, th, fr, pts, gl, sh);
     float rmax = tile_bounds<LPS>(pts, np, tb, gl);
+    if (W.reseed) {
+        // the previous-step contacts from a detection at the current state (same test as the
+        // step's own: z below the ground at the point's cell)
+        float R0[9];
+        quat_mat(q, R0);
+        for (int k = 0, i = gl; i < np; ++k, i += LPS) {
+            const float4 r = pts[i];
+            const float x = c[0] + (R0[0] * r.x + R0[1] * r.y + R0[2] * r.z);
+            const float y = c[1] + (R0[3] * r.x + R0[4] * r.y + R0[5] * r.z);
+            const float z = c[2] + (R0[6] * r.x + R0[7] * r.y + R0[8] * r.z);
+            if (z < ground<FLAT>(W, hm, x, y)) kprev |= 1ull << k;
+        }
+    }
     // sh is written by the (out-of-line) shape update through a reference, so it lives in local
     // memory; the step loop reads this register copy
     Shape shr = sh;
@@ -1320,13 +1335,13 @@ __global__ void __launch_bounds__(128) kappa_refresh_kernel(const __grid_constan
     }
 }
 
-__global__ void accumulate_kernel(long long *total, int *count) {
-    *total += *count;
+__global__ void accumulate_kernel(long long *total, int *count, int mult) {
+    *total += (long long)*count * mult;
     *count = 0;
 }
 
-cudaError_t launch_accumulate(long long *total, int *count, cudaStream_t st) {
-    accumulate_kernel<<<1, 1, 0, st>>>(total, count);
+cudaError_t launch_accumulate(long long *total, int *count, int mult, cudaStream_t st) {
+    accumulate_kernel<<<1, 1, 0, st>>>(total, count, mult);
     return cudaGetLastError();
 }
 

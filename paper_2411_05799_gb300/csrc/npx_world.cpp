@@ -133,7 +133,11 @@ struct npx_world {
         long long *total = nullptr;
         cudaEvent_t ev_w = nullptr, ev_n = nullptr;
         int rows = 0;
+        // the shape cache holds the shapes of step cache_at under state generation cache_gen
+        long long cache_at = -1;
+        unsigned long long cache_gen = ~0ull;
     } sg;
+    unsigned long long state_gen = 0;   // counts the caller's state writes
 };
 
 namespace {
@@ -804,6 +808,7 @@ int npx_world_finalize(npx_world *w) {
 
 int npx_state_set(npx_world *w, const float *origin, const float *quat, const float *vel,
                   const float *omega, const float *theta) {
+    if (w) ++w->state_gen;
     if (int rc = check_ready(w)) return rc;
     if (!origin || !quat || !vel || !omega) return fail(NPX_EINVAL, "null state array");
     CUDA_TRY(cudaSetDevice(w->device));
@@ -823,6 +828,7 @@ int npx_state_set(npx_world *w, const float *origin, const float *quat, const fl
 int npx_state_write(npx_world *w, const float *cog, const float *quat, const float *vel,
                     const float *angmom, const float *theta, const uint8_t *contact_prev,
                     int64_t step) {
+    if (w) ++w->state_gen;
     if (int rc = check_ready(w)) return rc;
     if (!cog || !quat || !vel || !angmom) return fail(NPX_EINVAL, "null state array");
     if (step < 0) return fail(NPX_EINVAL, "step must be >= 0");
@@ -990,6 +996,7 @@ int npx_state_export(npx_world *w, void *blob, size_t *size) {
 }
 
 int npx_state_import(npx_world *w, const void *blob, size_t size) {
+    if (w) ++w->state_gen;
     if (int rc = check_ready(w)) return rc;
     const BlobLayout b = blob_layout(w);
     if (!blob || size < b.end) return fail(NPX_EINVAL, "blob too small (%zu < %zu)", size, b.end);
@@ -1063,16 +1070,63 @@ int npx_surrogate_dims(npx_world *w, int *nf, int *nt) {
     return surrogate_dims(w, nf, nt);
 }
 
-int npx_surrogate_collect(npx_world *w, const npx_surrogate_norm *nrm, int n_steps, float *X, float *T) {
+// Whether a surrogate window of `stride` steps may start at step n: it holds no joint-update step
+// (on actuated worlds 1 <= n mod K and n mod K + stride <= K).
+static bool window_fits(const npx_world *w, long long n, int stride) {
+    if (w->act_mode == NPX_ACT_HOLD) return true;
+    const long long K = w->desc.joint_update_steps, ph = n % K;
+    return ph >= 1 && ph + stride <= K;
+}
+
+static int check_stride(const npx_world *w, int stride) {
+    if (stride < 1) return fail(NPX_EINVAL, "stride must be >= 1");
+    if (w->act_mode != NPX_ACT_HOLD && stride >= w->desc.joint_update_steps)
+        return fail(NPX_EINVAL, "stride %d leaves no window between joint updates every %d steps", stride,
+                    w->desc.joint_update_steps);
+    return NPX_OK;
+}
+
+// The surrogate's shape cache (link frames, inertia, sensor points) depends on the joint angles
+// alone: it stays valid over steps without a joint update and is rebuilt after one or after the
+// caller writes the state.
+static bool cache_valid(const npx_world *w) {
+    return w->sg.cache_at == w->step && w->sg.cache_gen == w->state_gen;
+}
+static int cache_build(npx_world *w) {
+    CUDA_TRY(npx::launch_shape_cache(w->W, w->sg.cache, w->stream));
+    w->sg.cache_at = w->step;
+    w->sg.cache_gen = w->state_gen;
+    return NPX_OK;
+}
+
+// Plain steps for every scene from the current step (reseed: their previous-step contacts from a
+// detection at the current state); the shape cache follows any joint update among them.
+static int plain_run(npx_world *w, int m, bool reseed) {
+    const bool was_valid = cache_valid(w);
+    npx::WorldDev W = w->W;
+    W.reseed = reseed ? 1 : 0;
+    CUDA_TRY(npx::launch_step(W, w->cfg, m, w->stream));
+    CUDA_TRY(npx::launch_advance(w->d_step, m, w->stream));
+    const long long K = w->desc.joint_update_steps;
+    const bool tick = w->act_mode != NPX_ACT_HOLD && (w->step + K - 1) / K * K < w->step + m;   // (step >= 0)
+    w->step += m;
+    w->launches += 1;
+    if (tick) return cache_build(w);
+    if (was_valid) w->sg.cache_at = w->step;
+    return NPX_OK;
+}
+
+int npx_surrogate_collect(npx_world *w, const npx_surrogate_norm *nrm, int stride, int n_windows, float *X,
+                          float *T) {
     if (int rc = check_ready(w)) return rc;
-    if (n_steps < 1 || !X || !T) return fail(NPX_EINVAL, "need n_steps >= 1 and X, T");
+    if (n_windows < 1 || !X || !T) return fail(NPX_EINVAL, "need n_windows >= 1 and X, T");
+    if (int rc = check_stride(w, stride)) return rc;
     if (nrm && (!nrm->x_mu || !nrm->x_isd || !nrm->t_mu || !nrm->t_sd)) return fail(NPX_EINVAL, "incomplete norm");
     CUDA_TRY(cudaSetDevice(w->device));
     if (int rc = surrogate_buffers(w)) return rc;
     int nf, nt;
     surrogate_dims(w, &nf, &nt);
     const npx::SurCache &C = w->sg.cache;
-    const bool actuated = w->act_mode != NPX_ACT_HOLD;
     npx::SurrogateIO pre{nf, nt, w->max_links, w->sensor_bits};
     pre.Xraw = w->sg.F0;
     pre.cxy_out = w->sg.C0;
@@ -1081,35 +1135,34 @@ int npx_surrogate_collect(npx_world *w, const npx_surrogate_norm *nrm, int n_ste
     post.cxy_ref = w->sg.C0;
     post.prev = w->sg.F0;
     if (nrm) { post.t_mu = nrm->t_mu; post.t_sd = nrm->t_sd; }
-    CUDA_TRY(npx::launch_shape_cache(w->W, C, w->stream));
-    for (int k = 0; k < n_steps;) {
-        if (actuated && w->step % w->desc.joint_update_steps == 0) {   // joint updates stay plain
-            CUDA_TRY(npx::launch_step(w->W, w->cfg, 1, w->stream));
-            CUDA_TRY(npx::launch_advance(w->d_step, 1, w->stream));
-            CUDA_TRY(npx::launch_shape_cache(w->W, C, w->stream));
-            w->step += 1;
-            w->launches += 1;
+    if (!cache_valid(w))
+        if (int rc = cache_build(w)) return rc;
+    for (int k = 0; k < n_windows;) {
+        if (!window_fits(w, w->step, stride)) {   // joint updates and what is left before them
+            if (int rc = plain_run(w, 1, false)) return rc;
             continue;
         }
         pre.X = X + (size_t)k * w->S * nf;
         post.T = T + (size_t)k * w->S * nt;
         CUDA_TRY(npx::launch_features(w->W, C, pre, w->stream));
-        CUDA_TRY(npx::launch_step(w->W, w->cfg, 1, w->stream));
-        CUDA_TRY(npx::launch_advance(w->d_step, 1, w->stream));
+        CUDA_TRY(npx::launch_step(w->W, w->cfg, stride, w->stream));
+        CUDA_TRY(npx::launch_advance(w->d_step, stride, w->stream));
         CUDA_TRY(npx::launch_features(w->W, C, post, w->stream));
-        w->step += 1;
+        w->step += stride;
+        w->sg.cache_at = w->step;   // no joint update inside a window
         w->launches += 1;
         ++k;
     }
     return NPX_OK;
 }
 
-int npx_world_step_surrogate(npx_world *w, npx_mlp *net, const npx_surrogate_norm *nrm, int n_steps,
+int npx_world_step_surrogate(npx_world *w, npx_mlp *net, const npx_surrogate_norm *nrm, int stride, int n_steps,
                              long long *fallbacks) {
     if (int rc = check_ready(w)) return rc;
     if (!net || !nrm || !nrm->x_mu || !nrm->x_isd || !nrm->t_mu || !nrm->t_sd)
         return fail(NPX_EINVAL, "need a network and its standardisation");
     if (n_steps < 0) return fail(NPX_EINVAL, "n_steps must be >= 0");
+    if (int rc = check_stride(w, stride)) return rc;
     CUDA_TRY(cudaSetDevice(w->device));
     if (int rc = surrogate_buffers(w)) return rc;
     int nf, nt, nin, nout;
@@ -1128,26 +1181,32 @@ int npx_world_step_surrogate(npx_world *w, npx_mlp *net, const npx_surrogate_nor
     io.ldb = ldx;
     io.x_mu = nrm->x_mu;
     io.x_isd = nrm->x_isd;
-    npx::WorldDev Wsub = w->W;            // the plain step on the fallback list only
+    // the plain step on the fallback list only, from contacts detected at the window's start
+    npx::WorldDev Wsub = w->W;
     Wsub.order = w->sg.list;
     Wsub.sched_count = w->sg.count;
-    // the fallback list is short: one scene per warp (32 lanes) gives it the least latency
+    Wsub.reseed = 1;
+    // a one-step fallback list is short: one scene per warp (32 lanes) gives it the least
+    // latency; longer windows take the world's own shape
     int rc_cfg = 0;
     npx::LaunchCfg fcfg = w->cfg;
-    if (w->max_points <= 64 * 32) {
+    if (stride == 1 && w->max_points <= 64 * 32) {
         fcfg = clamp_cfg(w, {32, 4, 0}, &rc_cfg);
         if (rc_cfg) return rc_cfg;
     }
-    const bool actuated = w->act_mode != NPX_ACT_HOLD;
-    CUDA_TRY(npx::launch_shape_cache(w->W, C, w->stream));
-    for (int k = 0; k < n_steps; ++k) {
-        if (actuated && (w->step + k) % w->desc.joint_update_steps == 0) {
-            // joint-update steps (Sec. III-B) are taken by the plain step for every scene, from
-            // the contacts at the current state
-            CUDA_TRY(npx::launch_kappa_refresh(w->W, nullptr, nullptr, w->stream));
-            CUDA_TRY(npx::launch_step(w->W, w->cfg, 1, w->stream));
-            CUDA_TRY(npx::launch_advance(w->d_step, 1, w->stream));
-            CUDA_TRY(npx::launch_shape_cache(w->W, C, w->stream));
+    if (!cache_valid(w))
+        if (int rc = cache_build(w)) return rc;
+    // contact flags are stale after a window (the surrogate moves scenes without detecting
+    // contacts): plain steps of every scene start from the contacts at the current state
+    bool stale = false;
+    for (int k = 0; k < n_steps;) {
+        if (stride > n_steps - k || !window_fits(w, w->step, stride)) {
+            // plain steps up to the next window start (or the end)
+            int m = 1;
+            while (k + m < n_steps && !(stride <= n_steps - k - m && window_fits(w, w->step + m, stride))) ++m;
+            if (int rc = plain_run(w, m, stale)) return rc;
+            stale = false;
+            k += m;
             continue;
         }
         CUDA_TRY(npx::launch_features(w->W, C, io, w->stream));
@@ -1162,17 +1221,19 @@ int npx_world_step_surrogate(npx_world *w, npx_mlp *net, const npx_surrogate_nor
         }
         CUDA_TRY(npx::launch_surrogate_update(w->W, C, Y, ldy, nrm->t_mu, nrm->t_sd, w->sg.nx, w->sg.applied,
                                               w->sg.sens_new, w->sg.list, w->sg.count, w->stream));
-        // the fallback: listed scenes kept their state; the plain step takes them from the
-        // contacts at that state
-        CUDA_TRY(npx::launch_kappa_refresh(w->W, w->sg.list, w->sg.count, w->stream));
-        CUDA_TRY(npx::launch_step(Wsub, fcfg, 1, w->stream));
-        CUDA_TRY(npx::launch_accumulate(w->sg.total, w->sg.count, w->stream));
-        CUDA_TRY(npx::launch_advance(w->d_step, 1, w->stream));
+        // the fallback: listed scenes kept their state; the plain step takes them through the
+        // window from the contacts at that state
+        CUDA_TRY(npx::launch_step(Wsub, fcfg, stride, w->stream));
+        CUDA_TRY(npx::launch_accumulate(w->sg.total, w->sg.count, stride, w->stream));
+        CUDA_TRY(npx::launch_advance(w->d_step, stride, w->stream));
+        w->step += stride;
+        w->sg.cache_at = w->step;   // no joint update inside a window
+        w->launches += 1;
+        stale = true;
+        k += stride;
     }
     // contact flags consistent with the final state for whatever reads or steps the world next
-    CUDA_TRY(npx::launch_kappa_refresh(w->W, nullptr, nullptr, w->stream));
-    w->step += n_steps;
-    w->launches += n_steps;
+    if (stale) CUDA_TRY(npx::launch_kappa_refresh(w->W, nullptr, nullptr, w->stream));
     if (fallbacks) {
         CUDA_TRY(cudaMemcpyAsync(fallbacks, w->sg.total, sizeof(long long), cudaMemcpyDeviceToHost, w->stream));
         CUDA_TRY(cudaStreamSynchronize(w->stream));

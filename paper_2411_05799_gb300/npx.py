@@ -142,8 +142,8 @@ _SIGS = {
     "npx_mlp_adam_step": [P],
     "npx_mlp_set_lr": [P, F],
     "npx_surrogate_dims": [P, P, P],
-    "npx_surrogate_collect": [P, P, I, P, P],
-    "npx_world_step_surrogate": [P, P, P, I, P],
+    "npx_surrogate_collect": [P, P, I, I, P, P],
+    "npx_world_step_surrogate": [P, P, P, I, I, P],
 }
 
 _lib = None
@@ -473,13 +473,13 @@ def surrogate_dims(world: "World"):
     return nf.value, nt.value
 
 
-def surrogate_collect(world: "World", n_steps, X_ptr, T_ptr, norm: SurrogateNorm = None):
-    _check(_lib.npx_surrogate_collect(world._h, C.byref(norm) if norm else None, int(n_steps),
-                                      X_ptr, T_ptr))
+def surrogate_collect(world: "World", n_windows, X_ptr, T_ptr, norm: SurrogateNorm = None, stride: int = 1):
+    _check(_lib.npx_surrogate_collect(world._h, C.byref(norm) if norm else None, int(stride),
+                                      int(n_windows), X_ptr, T_ptr))
 
 
-def world_step_surrogate(world: "World", net: "MLP", norm: SurrogateNorm, n_steps) -> int:
+def world_step_surrogate(world: "World", net: "MLP", norm: SurrogateNorm, n_steps, stride: int = 1) -> int:
     fb = C.c_longlong()
-    _check(_lib.npx_world_step_surrogate(world._h, net._h, C.byref(norm), int(n_steps),
+    _check(_lib.npx_world_step_surrogate(world._h, net._h, C.byref(norm), int(stride), int(n_steps),
                                          C.byref(fb)))
     return fb.value
