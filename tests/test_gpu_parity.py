@@ -401,6 +401,22 @@ def test_size_classes_match_the_oracle():
     assert np.median(dc) < 1e-5
 
 
+@pytest.mark.parametrize("graphs", [True, False])
+def test_many_size_classes_run_concurrently(graphs):
+    """Six size classes: their launches go round-robin to the world's stream and three side
+    streams (forked and joined with events, inside a captured graph or not), each with its own
+    work-queue counter; 200 steps agree with the oracle."""
+    counts = [c for c in (8, 20, 50, 120, 300, 700) for _ in range(300)]
+    b = scenes.ragged_bodies(counts, seed_key=8)
+    w = World.from_batch(b)
+    w.use_graphs(graphs)
+    assert w.info()["size_classes"] == 6
+    dc, da, r, o = _window_world(b, w, 200)
+    assert (r["status"] == 0).all()
+    assert ((dc <= 1e-3) & (da <= 1e-3)).mean() >= 0.95
+    assert np.median(dc) < 1e-5
+
+
 def _window_world(b, w, horizon):
     o = Oracle(b, threads=THREADS)
     to_gpu(w, o)
