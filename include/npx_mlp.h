@@ -53,6 +53,12 @@ typedef struct {
 int npx_gemm_bf16(const void *A, const void *B, int M, int N, int K, int splits,
                   const npx_gemm_epilogue *epilogue, int *err, void *stream);
 
+/* The GEMM's bounded barrier wait on its own, for tests of its failure path: one thread waits on
+ * a barrier that nothing completes, until the two-second limit (use_abort = 0) or until a second
+ * warp raises the abort flag after 1 ms (use_abort = 1).  Synchronous: *timed_out (host) = 1 if
+ * the wait gave up, *elapsed_us (host) = how long it waited; the context stays usable. */
+int npx_gemm_wait_selftest(int use_abort, int *timed_out, int *elapsed_us, void *stream);
+
 /* --- the surrogate network --------------------------------------------------------------
  * y = W_L gelu(... gelu(W_1 x + b_1) ...) + b_L with n_hidden_layers GELU layers of width
  * n_hidden (exact GELU, z Phi(z)), trained on the mean over the batch of the squared error summed

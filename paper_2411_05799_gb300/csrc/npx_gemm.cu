@@ -529,8 +529,53 @@ static cudaError_t launch(const CUtensorMap &ta, const CUtensorMap &tb, const CU
     return cudaGetLastError();
 }
 
+// The bounded barrier wait on its own: thread 0 waits on a barrier that nothing completes; with
+// use_abort, warp 1 raises the abort flag after ABORT_NS.  out[0] = 1 if the wait gave up (0 if
+// the phase completed), out[1] = the wait in microseconds.
+constexpr unsigned long long ABORT_NS = 1000000ull;   // 1 ms
+__global__ void __launch_bounds__(64) wait_selftest_kernel(int use_abort, int *out) {
+    __shared__ uint64_t bar;
+    __shared__ volatile int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (use_abort && threadIdx.x == 32) {
+        const unsigned long long t0 = global_ns();
+        while (global_ns() - t0 < ABORT_NS) {
+        }
+        abort_flag = 1;
+    }
+    if (threadIdx.x == 0) {
+        const unsigned long long t0 = global_ns();
+        const bool ok = mbar_wait(&bar, 0, use_abort ? &abort_flag : nullptr);
+        out[0] = ok ? 0 : 1;
+        out[1] = (int)((global_ns() - t0) / 1000ull);
+    }
+}
+
 }  // namespace gemm
 }  // namespace npx
+
+extern "C" int npx_gemm_wait_selftest(int use_abort, int *timed_out, int *elapsed_us, void *stream) {
+    if (!timed_out || !elapsed_us) return npx::set_last_error(NPX_EINVAL, "npx_gemm_wait_selftest: null argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, 2 * sizeof(int));
+    if (e != cudaSuccess) return npx::set_last_error(NPX_ENOMEM, cudaGetErrorString(e));
+    int h[2] = {-1, -1};
+    npx::gemm::wait_selftest_kernel<<<1, 64, 0, st>>>(use_abort ? 1 : 0, d);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    if (e != cudaSuccess) return npx::set_last_error(NPX_ECUDA, cudaGetErrorString(e));
+    *timed_out = h[0];
+    *elapsed_us = h[1];
+    return NPX_OK;
+}
 
 extern "C" int npx_gemm_bf16(const void *A, const void *B, int M, int N, int K, int splits,
                              const npx_gemm_epilogue *ep, int *err, void *stream) {

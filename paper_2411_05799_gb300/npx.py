@@ -95,6 +95,16 @@ class GemmEpilogue(C.Structure):
                 ("zin", C.c_void_p), ("ldzi", C.c_int)]
 
 
+def gemm_wait_selftest(use_abort: bool, stream=None):
+    """The GEMM's bounded barrier wait on a barrier that nothing completes: (gave_up, microseconds)
+    after the two-second limit, or after a second warp raises the abort flag (use_abort)."""
+    load()
+    t, us = C.c_int(), C.c_int()
+    _check(_lib.npx_gemm_wait_selftest(1 if use_abort else 0, C.byref(t), C.byref(us),
+                                       C.c_void_p(stream or 0)))
+    return t.value, us.value
+
+
 def gemm_bf16(A, B, M, N, K, epilogue: GemmEpilogue, err, splits=1, stream=None):
     """npx_gemm_bf16: C = A B^T on the tensor cores (device pointers as integers)."""
     load()
@@ -132,6 +142,7 @@ _SIGS = {
     "npx_world_use_graphs": [P, I],
     "npx_step_noalloc": [P, I, P],
     "npx_gemm_bf16": [P, P, I, I, I, I, P, P, P],
+    "npx_gemm_wait_selftest": [I, P, P, P],
     "npx_mlp_create": [P, P],
     "npx_mlp_destroy": [P],
     "npx_mlp_params_set": [P, P, C.c_size_t],

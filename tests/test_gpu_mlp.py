@@ -42,6 +42,18 @@ def _setup(M=256, seed=0):
     return net, Ws, bs, x, t
 
 
+def test_bounded_wait_gives_up_and_the_context_survives():
+    """Every barrier wait of the GEMM is bounded: on a barrier that nothing completes it gives up
+    after its two-second limit, or as soon as another warp raises the abort flag, and reports it;
+    the context then still runs the network correctly."""
+    st = torch.cuda.current_stream().cuda_stream
+    gave_up, us = npx.gemm_wait_selftest(False, st)
+    assert gave_up == 1 and 1.9e6 <= us <= 6e6, us
+    gave_up, us = npx.gemm_wait_selftest(True, st)
+    assert gave_up == 1 and 900 <= us <= 5e5, us
+    test_forward_matches_fp64_oracle()
+
+
 def test_params_round_trip():
     net, Ws, bs, x, t = _setup()
     W2, b2 = net.get_params()
