@@ -144,6 +144,10 @@ struct npx_world {
         unsigned long long cache_gen = ~0ull;
     } sg;
     unsigned long long state_gen = 0;   // counts the caller's state writes
+    // angular velocity and contact sensors are derived from the state: after a state write they
+    // are recomputed when first needed (a step recomputes them anyway)
+    bool derived_stale = false;
+    cudaEvent_t ev_copied = nullptr;    // a state write's host arrays have been read
 };
 
 namespace {
@@ -408,6 +412,14 @@ void clear_graphs(npx_world *w) {
     w->graph_cache.clear();
 }
 
+// angular velocity and contact sensors consistent with the state (after a state write)
+int ensure_derived(npx_world *w) {
+    if (!w->derived_stale) return NPX_OK;
+    CUDA_TRY(npx::launch_refresh(w->W, w->stream));
+    w->derived_stale = false;
+    return NPX_OK;
+}
+
 int enqueue_steps(npx_world *w, int n) {
     const int nk = (int)w->classes.size();
     const int na = std::min(nk - 1, (int)w->aux.size());   // side streams in use
@@ -547,6 +559,7 @@ int npx_world_destroy(npx_world *w) {
     if (w->sg.ev_w) cudaEventDestroy(w->sg.ev_w);
     if (w->sg.ev_n) cudaEventDestroy(w->sg.ev_n);
     for (cudaStream_t st : w->aux) cudaStreamDestroy(st);
+    if (w->ev_copied) cudaEventDestroy(w->ev_copied);
     for (cudaEvent_t ev : w->ev_join) cudaEventDestroy(ev);
     if (w->ev_fork) cudaEventDestroy(w->ev_fork);
     if (w->own_stream) cudaStreamDestroy(w->own_stream);
@@ -878,6 +891,7 @@ int npx_state_set(npx_world *w, const float *origin, const float *quat, const fl
         CUDA_TRY(cudaMemcpyAsync(w->W.theta, theta, w->J * sizeof(float), cudaMemcpyHostToDevice, w->stream));
     CUDA_TRY(npx::launch_init(w->W, d, d + 3 * S, d + 7 * S, d + 10 * S, w->stream));
     CUDA_TRY(cudaStreamSynchronize(w->stream));
+    w->derived_stale = false;   // the set-up writes them
     return NPX_OK;
 }
 
@@ -890,27 +904,30 @@ int npx_state_write(npx_world *w, const float *cog, const float *quat, const flo
     if (step < 0) return fail(NPX_EINVAL, "step must be >= 0");
     CUDA_TRY(cudaSetDevice(w->device));
     const size_t S = w->S;
-    // the caller's arrays go to the device as they are (one copy each); kernels transpose and
-    // permute them there
+    // the caller's arrays go to the device as they are (one copy each, all copies first); kernels
+    // transpose and permute them there.  The call returns once the copies are done (the caller's
+    // arrays have been read); the kernels run on, and the angular velocity and sensors are
+    // recomputed when first needed.
     float *d = w->d_stage;
+    const long long st64 = step;
     CUDA_TRY(cudaMemcpyAsync(d, cog, 3 * S * sizeof(float), cudaMemcpyHostToDevice, w->stream));
     CUDA_TRY(cudaMemcpyAsync(d + 3 * S, quat, 4 * S * sizeof(float), cudaMemcpyHostToDevice, w->stream));
     CUDA_TRY(cudaMemcpyAsync(d + 7 * S, vel, 3 * S * sizeof(float), cudaMemcpyHostToDevice, w->stream));
     CUDA_TRY(cudaMemcpyAsync(d + 10 * S, angmom, 3 * S * sizeof(float), cudaMemcpyHostToDevice, w->stream));
-    CUDA_TRY(npx::launch_scatter_state(w->W, d, w->stream));
     if (theta && w->J > 0)
         CUDA_TRY(cudaMemcpyAsync(w->W.theta, theta, w->J * sizeof(float), cudaMemcpyHostToDevice, w->stream));
-    if (contact_prev) {
-        CUDA_TRY(cudaMemcpyAsync(w->d_kstage, contact_prev, w->P, cudaMemcpyHostToDevice, w->stream));
-        CUDA_TRY(npx::launch_permute_kappa(w->W.kappa, w->d_kstage, w->d_perm, w->P, true, w->stream));
-    } else {
-        CUDA_TRY(cudaMemsetAsync(w->W.kappa, 0, w->P, w->stream));
-    }
-    CUDA_TRY(cudaMemsetAsync(w->W.status, 0, S * sizeof(uint32_t), w->stream));
-    const long long st64 = step;
+    if (contact_prev) CUDA_TRY(cudaMemcpyAsync(w->d_kstage, contact_prev, w->P, cudaMemcpyHostToDevice, w->stream));
     CUDA_TRY(cudaMemcpyAsync(w->d_step, &st64, sizeof st64, cudaMemcpyHostToDevice, w->stream));
-    CUDA_TRY(npx::launch_refresh(w->W, w->stream));
-    CUDA_TRY(cudaStreamSynchronize(w->stream));   // the caller's arrays have been read
+    if (!w->ev_copied) CUDA_TRY(cudaEventCreateWithFlags(&w->ev_copied, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventRecord(w->ev_copied, w->stream));
+    CUDA_TRY(npx::launch_scatter_state(w->W, d, w->stream));
+    if (contact_prev)
+        CUDA_TRY(npx::launch_permute_kappa(w->W.kappa, w->d_kstage, w->d_perm, w->P, true, w->stream));
+    else
+        CUDA_TRY(cudaMemsetAsync(w->W.kappa, 0, w->P, w->stream));
+    CUDA_TRY(cudaMemsetAsync(w->W.status, 0, S * sizeof(uint32_t), w->stream));
+    w->derived_stale = true;
+    CUDA_TRY(cudaEventSynchronize(w->ev_copied));
     w->step = step;
     return NPX_OK;
 }
@@ -979,6 +996,7 @@ int npx_world_step(npx_world *w, int n) {
     }
     w->launches += (long long)nchunks * (long long)w->classes.size();
     w->step += n;
+    w->derived_stale = false;   // every scene's write-back rewrote them
     return NPX_OK;
 }
 
@@ -993,6 +1011,7 @@ int npx_sensors_read(npx_world *w, npx_sensors *o) {
     if (int rc = check_ready(w)) return rc;
     if (!o) return fail(NPX_EINVAL, "null sensors");
     CUDA_TRY(cudaSetDevice(w->device));
+    if (int rc = ensure_derived(w)) return rc;
     const size_t S = w->S;
     // per-scene (AoS) blocks assembled on the device, then one copy into each caller array
     float *d = w->d_stage;
@@ -1035,6 +1054,7 @@ int npx_state_export(npx_world *w, void *blob, size_t *size) {
     if (!blob) { *size = b.end; return NPX_OK; }
     if (*size < b.end) return fail(NPX_EINVAL, "blob needs %zu bytes", b.end);
     CUDA_TRY(cudaSetDevice(w->device));
+    if (int rc = ensure_derived(w)) return rc;
     char *p = static_cast<char *>(blob);
     const uint64_t hdr[8] = {kBlobMagic, (uint64_t)w->S, (uint64_t)w->P, (uint64_t)w->J,
                              (uint64_t)w->step, 0, 0, 0};
@@ -1073,6 +1093,7 @@ int npx_state_import(npx_world *w, const void *blob, size_t size) {
     CUDA_TRY(cudaMemcpyAsync(w->d_step, &st, sizeof st, cudaMemcpyHostToDevice, w->stream));
     CUDA_TRY(cudaStreamSynchronize(w->stream));
     w->step = st;
+    w->derived_stale = false;   // the blob's own
     return NPX_OK;
 }
 
@@ -1191,6 +1212,7 @@ int npx_surrogate_collect(npx_world *w, const npx_surrogate_norm *nrm, int strid
     post.cxy_ref = w->sg.C0;
     post.prev = w->sg.F0;
     if (nrm) { post.t_mu = nrm->t_mu; post.t_sd = nrm->t_sd; }
+    if (int rc = ensure_derived(w)) return rc;
     if (!cache_valid(w))
         if (int rc = cache_build(w)) return rc;
     for (int k = 0; k < n_windows;) {
@@ -1250,6 +1272,7 @@ int npx_world_step_surrogate(npx_world *w, npx_mlp *net, const npx_surrogate_nor
         fcfg = clamp_cfg(w, {32, 4, 0}, &rc_cfg);
         if (rc_cfg) return rc_cfg;
     }
+    if (int rc = ensure_derived(w)) return rc;
     if (!cache_valid(w))
         if (int rc = cache_build(w)) return rc;
     // contact flags are stale after a window (the surrogate moves scenes without detecting
