@@ -141,29 +141,40 @@ def cpu_oracle_sample(batch, n_scenes: int, n_steps: int, threads: int) -> dict:
 
 
 def other_workloads(World, scenes, stream, device) -> dict:
-    """Scene-steps/s of 1,000-step launches on the uneven mixed batch and the rough-terrain
-    batch (state resident in HBM, CUDA events, one warm-up launch each)."""
+    """Scene-steps/s of 1,000-step launches on the uneven mixed batch (2 s simulated after a
+    warm-up second) and the evolution-scale rollout on rough terrain (the whole 60 s simulated from
+    the initial state, after a warm-up second and a reset; its fitness is the horizontal distance
+    each robot's CoG moved), state resident in HBM, CUDA events."""
     import torch
     out = {}
-    for name, make in (("uneven_mix_65536_scenes", lambda: scenes.uneven_batch(65536)),
-                       ("hexapod_rough_terrain_16384_scenes", lambda: scenes.cpg_batch(16384))):
+    for name, make, secs in (("uneven_mix_65536_scenes", lambda: scenes.uneven_batch(65536), 2),
+                             ("hexapod_rough_terrain_16384_scenes", lambda: scenes.cpg_batch(16384), 60)):
         b = make()
         w = World.from_batch(b, stream=stream.cuda_stream, device=device)
         w.autotune(100)
         w.configure(chunk_steps=CHUNK)
+        start = w.export_state()
+        c0 = w.read()["cog"]
         w.step(CHUNK)
+        w.import_state(start)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        w.step(2 * CHUNK)
+        w.step(secs * CHUNK)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         info = w.info()
-        out[name] = {"value": b.n_scenes * 2 * CHUNK / (ms / 1e3), "unit": UNIT, "steps": 2 * CHUNK,
+        r = w.read()
+        out[name] = {"value": b.n_scenes * secs * CHUNK / (ms / 1e3), "unit": UNIT, "steps": secs * CHUNK,
                      "ms": ms, "points": b.n_points, "lanes_per_scene": info["lanes_per_scene"],
                      "size_classes": info["size_classes"],
                      "warps_per_block": info["warps_per_block"],
-                     "frozen_scenes": int((w.read()["status"] != 0).sum())}
+                     "frozen_scenes": int((r["status"] != 0).sum())}
+        if secs == 60:
+            d = np.linalg.norm(r["cog"][:, :2] - c0[:, :2], axis=1)
+            out[name]["fitness_m"] = {"what": "horizontal distance of the robot CoG from its start after 60 s",
+                                      "median": float(np.median(d)), "p90": float(np.percentile(d, 90)),
+                                      "max": float(d.max())}
         w.close()
         del b
     return out
@@ -435,9 +446,12 @@ def run_gpu(args):
                             "kernel": "step_kernel",
                             "flops_per_scene_step": flops_per_ss,
                             "peak_note": "FP32 FMA peak from unit counts and max SM clock"}
+        r1 = cpu_oracle_sample(batch, 64, 1000, 1)     # the paper's setting: one CPU thread
         line["cpu_baseline"] = {"value": r["scene_steps_per_s"], "unit": UNIT, "cores": threads,
                                 "kind": "oracle",
-                                "sample": f"{n_sc} of {N_SCENES} hexapods x {n_st} steps (FP64)"}
+                                "sample": f"{n_sc} of {N_SCENES} hexapods x {n_st} steps (FP64)",
+                                "single_thread": {"value": r1["scene_steps_per_s"], "unit": UNIT,
+                                                  "sample": f"64 of {N_SCENES} hexapods x 1000 steps"}}
         print(json.dumps(line), flush=True)
     world.close()
     if dist:
