@@ -29,6 +29,13 @@
  *    (the maximum static friction).  The CoG takes the scaled dynamic map, then the kinematic
  *    map; its velocity changes by the scaled dynamic displacement over dt, and the angular
  *    momentum by the yaw rate of the scaled dynamic rotation.
+ *  - Two options (model fric_mode, off by default) follow the refinements the paper names after
+ *    Eq. 6 without defining them: bit 0 weights every least-squares row by its point's normal
+ *    force this step (the centroid becomes the centre of pressure; the Coulomb cap uses the
+ *    force-weighted mean slip); bit 1 applies the dynamic correction's friction impulse
+ *    J = M (v_new - v*) at the contact centroid, so that its torque about the CoG also turns the
+ *    body about the horizontal axes (the x and y components of (centroid - CoG) x J; the vertical
+ *    component stays the yaw of the least-squares rotation).
  */
 #include "npxo.h"
 
@@ -135,6 +142,8 @@ typedef struct {
     double *r;             /* [np*3] point offsets from the CoG in the shape frame */
     double *x0, *xp, *xs;  /* [np*3] world positions: step start, after joint update, after integration */
     unsigned char *kap;    /* [np] contact this step */
+    double *F;             /* [np] normal force this step (0 out of contact) */
+    double *wls;           /* [np] weights of the friction least-squares rows */
     double *Q, *T;         /* [nl*9], [nl*3] link frames (construction -> shape frame) */
     double Mtot, g[3], Ib[9], Ibinv[9];
 } scene_ws;
@@ -145,13 +154,16 @@ static int ws_alloc(scene_ws *w, int np, int nl) {
     w->xp = malloc(sizeof(double) * 3 * (size_t)np);
     w->xs = malloc(sizeof(double) * 3 * (size_t)np);
     w->kap = malloc((size_t)np);
+    w->F = malloc(sizeof(double) * (size_t)np);
+    w->wls = malloc(sizeof(double) * (size_t)np);
     w->Q = malloc(sizeof(double) * 9 * (size_t)nl);
     w->T = malloc(sizeof(double) * 3 * (size_t)nl);
-    return w->r && w->x0 && w->xp && w->xs && w->kap && w->Q && w->T;
+    return w->r && w->x0 && w->xp && w->xs && w->kap && w->F && w->wls && w->Q && w->T;
 }
 
 static void ws_free(scene_ws *w) {
-    free(w->r); free(w->x0); free(w->xp); free(w->xs); free(w->kap); free(w->Q); free(w->T);
+    free(w->r); free(w->x0); free(w->xp); free(w->xs); free(w->kap); free(w->F); free(w->wls);
+    free(w->Q); free(w->T);
 }
 
 static void ws_bind(const npxo_model *M, int s, scene_ws *w) {
@@ -291,15 +303,49 @@ int npxo_friction_ls(int n, const double *s, const double *e, double *t, double 
     return 0;
 }
 
-/* centroid of n horizontal points and their spread sum |s - centroid|^2 */
-static void centroid_spread(int n, const double *s, double *sb, double *S2) {
+/* The same least squares with row weights w_i >= 0 (the refinement the paper suggests after
+ * Eq. 6: each term weighted by the force pressing its point against the ground): the weighted
+ * centroid, t = the weighted mean residual, a3 = sum w (s~ x e) / sum w |s~|^2.  No weight: t = 0,
+ * a3 = 0.  The rotation is solved when the weighted mean of |s~|^2 exceeds 1e-13 m^2 (points
+ * closer than that, or all weight on one point, give a translation only). */
+int npxo_friction_ls_w(int n, const double *s, const double *e, const double *w, double *t, double *a3) {
+    double W = 0.0, sb[2] = {0, 0}, eb[2] = {0, 0};
+    t[0] = t[1] = 0.0;
+    *a3 = 0.0;
+    for (int i = 0; i < n; ++i) {
+        W += w[i];
+        sb[0] += w[i] * s[2 * i]; sb[1] += w[i] * s[2 * i + 1];
+        eb[0] += w[i] * e[2 * i]; eb[1] += w[i] * e[2 * i + 1];
+    }
+    if (!(W > 0.0)) return 0;
+    sb[0] /= W; sb[1] /= W; eb[0] /= W; eb[1] /= W;
+    double S2 = 0.0, X = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double sx = s[2 * i] - sb[0], sy = s[2 * i + 1] - sb[1];
+        S2 += w[i] * (sx * sx + sy * sy);
+        X += w[i] * (sx * e[2 * i + 1] - sy * e[2 * i]);
+    }
+    t[0] = eb[0]; t[1] = eb[1];
+    if (S2 > 1e-13 * W) *a3 = X / S2;
+    return 0;
+}
+
+/* weighted centroid of n horizontal points (w NULL: equal weights), the total weight and the
+ * weighted spread sum w |s - centroid|^2 */
+static void centroid_spread(int n, const double *s, const double *w, double *sb, double *W, double *S2) {
     sb[0] = sb[1] = 0.0;
-    for (int i = 0; i < n; ++i) { sb[0] += s[2 * i]; sb[1] += s[2 * i + 1]; }
-    sb[0] /= n; sb[1] /= n;
+    *W = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double wi = w ? w[i] : 1.0;
+        *W += wi;
+        sb[0] += wi * s[2 * i]; sb[1] += wi * s[2 * i + 1];
+    }
     *S2 = 0.0;
+    if (!(*W > 0.0)) return;
+    sb[0] /= *W; sb[1] /= *W;
     for (int i = 0; i < n; ++i) {
         double dx = s[2 * i] - sb[0], dy = s[2 * i + 1] - sb[1];
-        *S2 += dx * dx + dy * dy;
+        *S2 += (w ? w[i] : 1.0) * (dx * dx + dy * dy);
     }
 }
 
@@ -367,12 +413,14 @@ static void scene_step(const npxo_model *M, npxo_state *st, int s, scene_ws *w, 
         const double *x = w->xp + 3 * i;
         float h = lut_height(M, s, x[0], x[1]);
         w->kap[i] = ((float)x[2] < h);
+        w->F[i] = 0.0;
         if (!w->kap[i]) continue;
         double rho[3] = {x[0] - c[0], x[1] - c[1], x[2] - c[2]};
         double vz = v[2] + (om[0] * rho[1] - om[1] * rho[0]);
         double d = (double)h - x[2];
         double F = M->m[w->p0 + i] * (kw2 * d - kc * vz);
         if (F < 0.0) F = 0.0;
+        w->F[i] = F;
         FN += F;
         tau[0] += rho[1] * F;
         tau[1] -= rho[0] * F;
@@ -396,13 +444,19 @@ static void scene_step(const npxo_model *M, npxo_state *st, int s, scene_ws *w, 
     /* Sec. III-C: friction over the contacts present in both steps */
     double cn[3] = {cs[0], cs[1], cs[2]}, vn[3] = {vs[0], vs[1], vs[2]}, Ln[3] = {Ls[0], Ls[1], Ls[2]};
     double qn[4] = {qs[0], qs[1], qs[2], qs[3]};
+    /* friction model options: the least-squares rows weighted by their points' normal forces
+     * (bit 0), and the friction impulse's torque about the horizontal axes (bit 1) -- the two
+     * refinements the paper suggests after Eq. 6; 0 = Eqs. 1-6 as written */
+    const int weighted = M->fric_mode & 1, tilt = M->fric_mode & 2;
     int nC = 0;
-    for (int i = 0; i < np; ++i) nC += st->kappa[w->p0 + i] && w->kap[i];
-    if (nC >= 1) {
+    double WC = 0.0;
+    for (int i = 0; i < np; ++i)
+        if (st->kappa[w->p0 + i] && w->kap[i]) { nC += 1; WC += weighted ? w->F[i] : 1.0; }
+    if (nC >= 1 && WC > 0.0) {
         cnt->friction_pts += (unsigned long long)nC;
         /* dynamic slip: the map taking the integrated positions back onto the positions before
          * integration */
-        double tD[2], a3D, sD[2], S2D;
+        double tD[2], a3D, sD[2], S2D, WD, zbar = 0.0;
         int k = 0;
         for (int i = 0; i < np; ++i) {
             if (!(st->kappa[w->p0 + i] && w->kap[i])) continue;
@@ -412,13 +466,17 @@ static void scene_step(const npxo_model *M, npxo_state *st, int s, scene_ws *w, 
             ls_s[2 * k + 1] = cs[1] + rw[1];
             ls_e[2 * k] = w->xp[3 * i] - ls_s[2 * k];
             ls_e[2 * k + 1] = w->xp[3 * i + 1] - ls_s[2 * k + 1];
+            w->wls[k] = weighted ? w->F[i] : 1.0;
+            zbar += w->wls[k] * (cs[2] + rw[2]);
             k++;
         }
-        npxo_friction_ls(nC, ls_s, ls_e, tD, &a3D);
-        centroid_spread(nC, ls_s, sD, &S2D);
+        if (weighted) npxo_friction_ls_w(nC, ls_s, ls_e, w->wls, tD, &a3D);
+        else npxo_friction_ls(nC, ls_s, ls_e, tD, &a3D);
+        centroid_spread(nC, ls_s, weighted ? w->wls : NULL, sD, &WD, &S2D);
+        zbar /= WD;
         /* kinematic slip (joint-update steps): the map taking the points moved by the joints
          * back onto their step-start positions */
-        double tK[2] = {0, 0}, a3K = 0.0, sK[2] = {0, 0}, S2K = 0.0;
+        double tK[2] = {0, 0}, a3K = 0.0, sK[2] = {0, 0}, S2K = 0.0, WK = 0.0;
         if (tick) {
             k = 0;
             for (int i = 0; i < np; ++i) {
@@ -429,15 +487,16 @@ static void scene_step(const npxo_model *M, npxo_state *st, int s, scene_ws *w, 
                 ls_e[2 * k + 1] = w->x0[3 * i + 1] - w->xp[3 * i + 1];
                 k++;
             }
-            npxo_friction_ls(nC, ls_s, ls_e, tK, &a3K);
-            centroid_spread(nC, ls_s, sK, &S2K);
+            if (weighted) npxo_friction_ls_w(nC, ls_s, ls_e, w->wls, tK, &a3K);
+            else npxo_friction_ls(nC, ls_s, ls_e, tK, &a3K);
+            centroid_spread(nC, ls_s, weighted ? w->wls : NULL, sK, &WK, &S2K);
         }
         double aD = asin(a3D < -1 ? -1 : (a3D > 1 ? 1 : a3D));
         double aK = asin(a3K < -1 ? -1 : (a3K > 1 ? 1 : a3K));
         /* maximum static friction: the impulse that undoes the dynamic slip is at most
          * mu * FN * dt; beyond that the dynamic correction is scaled down */
         double sh = sin(0.5 * aD);
-        double u2 = tD[0] * tD[0] + tD[1] * tD[1] + 4.0 * sh * sh * S2D / nC;
+        double u2 = tD[0] * tD[0] + tD[1] * tD[1] + 4.0 * sh * sh * S2D / WD;
         double Jreq = w->Mtot * sqrt(u2) / dt;
         double Jmax = (double)M->mu[s] * dt * FN;
         double sc = (Jreq <= Jmax) ? 1.0 : Jmax / Jreq;
@@ -457,6 +516,14 @@ static void scene_step(const npxo_model *M, npxo_state *st, int s, scene_ws *w, 
         mat_mul(tmp, Rst, Iw);
         mat_vec(Iw, ez, Iz);
         for (int k2 = 0; k2 < 3; ++k2) Ln[k2] = Ls[k2] + (sc * aD / dt) * Iz[k2];
+        if (tilt) {
+            /* the friction impulse J = M (v_new - v*) acts at the contact centroid (sD, zbar),
+             * below the CoG: its torque about the CoG turns the body about the horizontal axes */
+            const double Jx = w->Mtot * (vn[0] - vs[0]), Jy = w->Mtot * (vn[1] - vs[1]);
+            const double rz = zbar - cs[2];
+            Ln[0] += -rz * Jy;
+            Ln[1] += rz * Jx;
+        }
         double A = aK + sc * aD;
         double qz[4] = {cos(0.5 * A), 0.0, 0.0, sin(0.5 * A)};
         quat_mul(qz, qs, qn);

@@ -26,6 +26,8 @@ typedef struct {
     const float *mu; const int *hmap;                     /* [S] */
     const float *heightmaps; int hm_nx, hm_ny; double hm_scale, hm_origin[2];
     int act_mode; const float *act_params;                /* [J*4]: A, f, phi, bias */
+    int fric_mode;         /* bit 0: least-squares rows weighted by the normal forces; bit 1: the
+                              friction impulse's torque about the horizontal axes (0 = Eqs. 1-6) */
 } npxo_model;
 
 typedef struct {
@@ -54,6 +56,8 @@ int  npxo_link_frames(const npxo_model *M, const npxo_state *st, int s, double *
 double npxo_target(const npxo_model *M, int scene, int joint_local, long long n);
 int  npxo_lut(const npxo_model *M, int scene, double x, double y, double *h);
 int  npxo_friction_ls(int n, const double *src_xy, const double *e_xy, double *t2, double *a3);
+int  npxo_friction_ls_w(int n, const double *src_xy, const double *e_xy, const double *w, double *t2,
+                        double *a3);
 
 #ifdef __cplusplus
 }

@@ -44,6 +44,7 @@ class _Model(C.Structure):
         ("heightmaps", C.c_void_p), ("hm_nx", C.c_int), ("hm_ny", C.c_int),
         ("hm_scale", C.c_double), ("hm_origin", C.c_double * 2),
         ("act_mode", C.c_int), ("act_params", C.c_void_p),
+        ("fric_mode", C.c_int),
     ]
 
 
@@ -80,6 +81,7 @@ def lib():
         _lib.npxo_target.restype = C.c_double
         _lib.npxo_lut.argtypes = [P, C.c_int, C.c_double, C.c_double, P]
         _lib.npxo_friction_ls.argtypes = [C.c_int, P, P, P, P]
+        _lib.npxo_friction_ls_w.argtypes = [C.c_int, P, P, P, P, P]
     return _lib
 
 
@@ -97,12 +99,30 @@ def friction_ls(src_xy: np.ndarray, e_xy: np.ndarray):
     return t, float(a3[0])
 
 
+def friction_ls_w(src_xy: np.ndarray, e_xy: np.ndarray, w: np.ndarray):
+    """The oracle's weighted least squares (rows weighted by w >= 0): (t, a3) of the problem
+    centred on the weighted centroid."""
+    s = np.ascontiguousarray(src_xy, np.float64)
+    e = np.ascontiguousarray(e_xy, np.float64)
+    ww = np.ascontiguousarray(w, np.float64)
+    t = np.zeros(2)
+    a3 = np.zeros(1)
+    lib().npxo_friction_ls_w(len(s), _ptr(s), _ptr(e), _ptr(ww), _ptr(t), _ptr(a3))
+    return t, float(a3[0])
+
+
+# friction-model options (bits of fric_mode): least-squares rows weighted by the points' normal
+# forces; the friction impulse's torque about the horizontal axes.  0 = Eqs. 1-6 as written.
+FRIC_WEIGHTED, FRIC_TILT = 1, 2
+
+
 class Oracle:
     """FP64 state of every scene of a SceneBatch, advanced by the C oracle."""
 
-    def __init__(self, batch, threads: int = 1):
+    def __init__(self, batch, threads: int = 1, fric_mode: int = 0):
         self.batch = b = batch
         self.threads = threads
+        self.fric_mode = int(fric_mode)
         S, P, J = b.n_scenes, b.n_points, b.n_joints
         self._keep = [np.ascontiguousarray(a) for a in
                       (b.link_off, b.point_off, b.p0, b.m, b.plink, b.parent, b.anchor, b.axis,
@@ -120,7 +140,7 @@ class Oracle:
             sensor=_ptr(sen), mu=_ptr(mu), hmap=_ptr(hm), heightmaps=_ptr(maps),
             hm_nx=0 if maps is None else maps.shape[2], hm_ny=0 if maps is None else maps.shape[1],
             hm_scale=b.hm_scale, hm_origin=(C.c_double * 2)(*b.hm_origin),
-            act_mode=b.act_mode, act_params=_ptr(act))
+            act_mode=b.act_mode, act_params=_ptr(act), fric_mode=int(fric_mode))
         self.c = np.zeros((S, 3))
         self.q = np.zeros((S, 4))
         self.v = np.zeros((S, 3))
