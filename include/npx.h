@@ -41,6 +41,12 @@ extern "C" {
 #define NPX_ACT_HOLD 0     /* joints keep their angles; no joint updates */
 #define NPX_ACT_SINUSOID 1 /* target = bias + A sin(2 pi f t + phi), set every K steps */
 
+/* Friction-model options (bits; 0 = the least squares of Sec. III-C, Eqs. 1-6, as written).  The
+ * two refinements the paper names after Eq. 6: */
+#define NPX_FRIC_WEIGHTED 1 /* every least-squares row weighted by its point's normal force */
+#define NPX_FRIC_TILT 2     /* the friction impulse, applied at the contact centroid, also turns
+                               the body about the horizontal axes */
+
 #define NPX_MAX_LINKS 64         /* links per scene */
 #define NPX_MAX_POINTS 2048      /* mass points per scene */
 #define NPX_MAX_SENSORS 32       /* contact sensors per scene (one bit each) */
@@ -153,6 +159,13 @@ int npx_contacts_read(npx_world *w, uint8_t *contact, size_t n);
  * (amplitude rad, frequency Hz, phase rad, bias rad) per joint.  The phase advances by
  * round(f dt 2^32) / 2^32 turns per step (exact over any horizon). */
 int npx_actuator_set(npx_world *w, int mode, const float *params);
+/* Friction model of the following steps: a combination of NPX_FRIC_* bits (0 by default).
+ * NPX_FRIC_WEIGHTED: the least-squares centroid, moments and slip are weighted by the points'
+ * normal forces of the step (the centroid becomes the centre of pressure); a rotation is solved
+ * when the weighted mean squared spread about it exceeds 1e-6 m^2.  NPX_FRIC_TILT: the angular momentum
+ * also changes by the x and y components of r x J, J = M dv the dynamic correction's impulse and r
+ * the contact centroid relative to the CoG.  Unknown bits: NPX_EINVAL. */
+int npx_world_set_friction_model(npx_world *w, int flags);
 /* Advance all scenes n >= 0 steps (asynchronous on the world's stream). */
 int npx_world_step(npx_world *w, int n);
 /* Wait for queued work; reports a latched error of an earlier asynchronous call. */

@@ -306,8 +306,9 @@ int npxo_friction_ls(int n, const double *s, const double *e, double *t, double 
 /* The same least squares with row weights w_i >= 0 (the refinement the paper suggests after
  * Eq. 6: each term weighted by the force pressing its point against the ground): the weighted
  * centroid, t = the weighted mean residual, a3 = sum w (s~ x e) / sum w |s~|^2.  No weight: t = 0,
- * a3 = 0.  The rotation is solved when the weighted mean of |s~|^2 exceeds 1e-13 m^2 (points
- * closer than that, or all weight on one point, give a translation only). */
+ * a3 = 0.  The rotation is solved when the weighted mean of |s~|^2 exceeds 1e-6 m^2 (a centre of
+ * pressure spread over at least a millimetre; one point, or weight gathered on one point, gives a
+ * translation only: the rotation is not determined there). */
 int npxo_friction_ls_w(int n, const double *s, const double *e, const double *w, double *t, double *a3) {
     double W = 0.0, sb[2] = {0, 0}, eb[2] = {0, 0};
     t[0] = t[1] = 0.0;
@@ -326,7 +327,7 @@ int npxo_friction_ls_w(int n, const double *s, const double *e, const double *w,
         X += w[i] * (sx * e[2 * i + 1] - sy * e[2 * i]);
     }
     t[0] = eb[0]; t[1] = eb[1];
-    if (S2 > 1e-13 * W) *a3 = X / S2;
+    if (S2 > 1e-6 * W) *a3 = X / S2;
     return 0;
 }
 

@@ -56,6 +56,9 @@ struct WorldDev {
     // 1: the launch takes the previous-step contacts from a detection at the current state
     // instead of kappa (after surrogate steps, which move scenes without detecting contacts)
     int reseed;
+    // friction-model options: bit 0 rows weighted by the normal forces, bit 1 the friction
+    // impulse's torque about the horizontal axes (0: Eqs. 1-6 as written)
+    int fric_mode;
 };
 
 struct LaunchCfg {

@@ -424,7 +424,9 @@ __device__ __forceinline__ float joint_target(const WorldDev &W, int j, long lon
 
 // ------------------------------------------------------------------------ one scene, n steps
 
-template <int LPS, bool FLAT>
+// OPT: the friction-model options (W.fric_mode) are compiled in; without them the step is the
+// least squares of Eqs. 1-6 as written, with no test of the options in the step loop
+template <int LPS, bool FLAT, bool OPT>
 __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *fr, float *th,
                           float *th_old, float4 *tb, int n_steps, long long step0) {
     const bool valid = s >= 0;
@@ -489,6 +491,9 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
     const int ntiles = (np + LPS - 1) / LPS;
 
     const float dt = W.dt, idt = 1.0f / W.dt, kw2 = W.kw2, kc = W.kc;
+    // friction-model options (Sec. III-C, the refinements named after Eq. 6): rows weighted by
+    // the normal forces; the friction impulse's torque about the horizontal axes
+    const bool weighted = OPT && (W.fric_mode & 1) != 0, tilt = OPT && (W.fric_mode & 2) != 0;
     float iM = 1.0f / shr.M;
     const bool actuated = W.act_mode != 0;
     // Candidate tiles: those whose box came within CULL_MARGIN of the highest ground at the last
@@ -607,17 +612,21 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
                 knw[hw] |= (ca ? 1u << ja : 0u) | (cb ? 1u << jb : 0u);
                 acc[0] += Fa; acc[1] += rya * Fa; acc[2] -= rxa * Fa;
                 acc[0] += Fb; acc[1] += ryb * Fb; acc[2] -= rxb * Fb;
-                // friction set C: in contact now and last step
-                const float wa = (ca && ((kp >> ja) & 1u)) ? 1.f : 0.f, wb = (cb && ((kp >> jb) & 1u)) ? 1.f : 0.f;
-                const float a0 = wa * (rxa - o[0]), a1 = wa * (rya - o[1]), a2 = wa * (rza - o[2]);
-                const float b0 = wb * (rxb - o[0]), b1 = wb * (ryb - o[1]), b2 = wb * (rzb - o[2]);
+                // friction set C: in contact now and last step; a row's weight is 1, or its normal
+                // force with force-weighted friction.  Sums: weight, weight x d, weight x d d^T
+                const float wa = (ca && ((kp >> ja) & 1u)) ? (weighted ? Fa : 1.f) : 0.f;
+                const float wb = (cb && ((kp >> jb) & 1u)) ? (weighted ? Fb : 1.f) : 0.f;
+                const float da0 = rxa - o[0], da1 = rya - o[1], da2 = rza - o[2];
+                const float db0 = rxb - o[0], db1 = ryb - o[1], db2 = rzb - o[2];
+                const float a0 = wa * da0, a1 = wa * da1, a2 = wa * da2;
+                const float b0 = wb * db0, b1 = wb * db1, b2 = wb * db2;
                 acc[3] += wa; acc[3] += wb;
                 acc[4] += a0; acc[5] += a1; acc[6] += a2;
                 acc[4] += b0; acc[5] += b1; acc[6] += b2;
-                acc[7] += a0 * a0; acc[8] += a1 * a1; acc[9] += a2 * a2;
-                acc[10] += a0 * a1; acc[11] += a0 * a2; acc[12] += a1 * a2;
-                acc[7] += b0 * b0; acc[8] += b1 * b1; acc[9] += b2 * b2;
-                acc[10] += b0 * b1; acc[11] += b0 * b2; acc[12] += b1 * b2;
+                acc[7] += a0 * da0; acc[8] += a1 * da1; acc[9] += a2 * da2;
+                acc[10] += a0 * da1; acc[11] += a0 * da2; acc[12] += a1 * da2;
+                acc[7] += b0 * db0; acc[8] += b1 * db1; acc[9] += b2 * db2;
+                acc[10] += b0 * db1; acc[11] += b0 * db2; acc[12] += b1 * db2;
             }
         }
         const uint64_t know = (uint64_t)knw[0] | ((uint64_t)knw[1] << 32);
@@ -645,6 +654,8 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         // offset moves from rho to (1 + D) rho with D = dR - 1 = a [u]x + b [u]x^2
         // (a = sin|u| / |u|, b = (1 - cos|u|) / |u|^2), free of the cancellation in R* r - R r
         float Dm[6];   // rows 0 and 1 of D (only horizontal displacements are needed)
+        float rzc = 0.f;   // (with the horizontal-axis friction torque) height of the integrated
+                           // friction-set centroid above the integrated CoG: [(1 + D) gb]_z
         {
             const float px = dt * oms[0], py = dt * oms[1], pz = dt * oms[2];
             const float a2 = px * px + py * py + pz * pz;
@@ -660,6 +671,9 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
                 fa = 2.f * f * cn;
                 fb = 2.f * f * f;
             }
+            if (tilt)
+                rzc = gb[2] + (-fa * py + fb * pz * px) * gb[0] + (fa * px + fb * pz * py) * gb[1] +
+                      fb * (pz * pz - a2) * gb[2];
             // [u]x^2 = u u^T - |u|^2 1
             Dm[0] = fb * (px * px - a2); Dm[1] = -fa * pz + fb * px * py; Dm[2] = fa * py + fb * px * pz;
             Dm[3] = fa * pz + fb * py * px; Dm[4] = fb * (py * py - a2); Dm[5] = -fa * px + fb * py * pz;
@@ -695,17 +709,28 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
                 float po[3];
                 fk_point(fr, a0, W.plink[p0 + i], po);
                 const float4 ro = make_float4(po[0] - gold[0], po[1] - gold[1], po[2] - gold[2], 0.f);
-                const float ux = (R[0] * r.x + R[1] * r.y + R[2] * r.z) - gb[0];
-                const float uy = (R[3] * r.x + R[4] * r.y + R[5] * r.z) - gb[1];
+                const float rx = R[0] * r.x + R[1] * r.y + R[2] * r.z;
+                const float ry = R[3] * r.x + R[4] * r.y + R[5] * r.z;
+                const float ux = rx - gb[0];
+                const float uy = ry - gb[1];
                 const float d[3] = {ro.x - r.x, ro.y - r.y, ro.z - r.z};
                 const float kx = R[0] * d[0] + R[1] * d[1] + R[2] * d[2];
                 const float ky = R[3] * d[0] + R[4] * d[1] + R[5] * d[2];
-                f6[0] += ux; f6[1] += uy; f6[2] += ux * ux + uy * uy;
-                f6[3] += kx; f6[4] += ky; f6[5] += ux * ky - uy * kx;
+                float wk = 1.f;   // the row's weight: its normal force this step (as in pass 1)
+                if (weighted) {
+                    const float rz = R[6] * r.x + R[7] * r.y + R[8] * r.z;
+                    const float z = c[2] + rz;
+                    const float h = ground_win<FLAT>(W, hm, win, wx0, wy0, c[0] + rx, c[1] + ry);
+                    const float vz = v[2] + (om[0] * ry - om[1] * rx);
+                    wk = fmaxf(0.f, r.w * (kw2 * (h - z) - kc * vz));
+                }
+                const float wux = wk * ux, wuy = wk * uy;
+                f6[0] += wux; f6[1] += wuy; f6[2] += wux * ux + wuy * uy;
+                f6[3] += wk * kx; f6[4] += wk * ky; f6[5] += wux * ky - wuy * kx;
             }
             gsum<LPS, 6>(f6);
         }
-        if (nC >= 1.f) {
+        if (nC > 0.f) {
             const float ax[3] = {1.f + Dm[0], Dm[1], Dm[2]}, ay[3] = {Dm[3], 1.f + Dm[4], Dm[5]};
             const float bx[3] = {Dm[0], Dm[1], Dm[2]}, by[3] = {Dm[3], Dm[4], Dm[5]};
             float Max[3], May[3];
@@ -719,7 +744,10 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             const float sby = ay[0] * gb[0] + ay[1] * gb[1] + ay[2] * gb[2];
             const float tDx = -dt * vs[0] - (bx[0] * gb[0] + bx[1] * gb[1] + bx[2] * gb[2]);
             const float tDy = -dt * vs[1] - (by[0] * gb[0] + by[1] * gb[1] + by[2] * gb[2]);
-            float a3 = (nC >= 2.f && S2 > 1e-12f) ? __fdividef(X, S2) : 0.f;
+            // a rotation needs two distinct points (force-weighted: a weighted mean spread about
+            // the centre of pressure above 1e-6 m^2, far above the rounding left by the moments'
+            // cancellation when the weight sits on one point)
+            float a3 = (weighted ? S2 > 1e-6f * nC : (nC >= 2.f && S2 > 1e-12f)) ? __fdividef(X, S2) : 0.f;
             a3 = fminf(fmaxf(a3, -1.f), 1.f);
             const float t1 = fmaxf(0.f, 1.f - a3 * a3);
             const float cD = t1 > 0.f ? t1 * rsqrtf(t1) : 0.f;       // cos(alpha_D)
@@ -746,7 +774,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
                 const float S2K = f6[2] - nC * (kbx * kbx + kby * kby);
                 const float tKx = f6[3] * in, tKy = f6[4] * in;
                 const float XK = f6[5] - (kbx * f6[4] - kby * f6[3]);
-                float a3K = (nC >= 2.f && S2K > 1e-12f) ? __fdividef(XK, S2K) : 0.f;
+                float a3K = (weighted ? S2K > 1e-6f * nC : (nC >= 2.f && S2K > 1e-12f)) ? __fdividef(XK, S2K) : 0.f;
                 a3K = fminf(fmaxf(a3K, -1.f), 1.f);
                 const float aK = asin_small(a3K);
                 float s2, c2;
@@ -771,6 +799,13 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             world_sym(Rs, shr.Ib, ez, Iz);
             const float w = sc * aD * idt;
             Ln[0] = Ls[0] + w * Iz[0]; Ln[1] = Ls[1] + w * Iz[1]; Ln[2] = Ls[2] + w * Iz[2];
+            if (tilt) {
+                // the friction impulse J = M (v_new - v*) acts at the friction-set centroid,
+                // rzc below the CoG: the x and y components of its moment r x J
+                const float Jx = shr.M * (vn[0] - vs[0]), Jy = shr.M * (vn[1] - vs[1]);
+                Ln[0] -= rzc * Jy;
+                Ln[1] += rzc * Jx;
+            }
             float sa, ca;
             sincos_small(0.5f * A, &sa, &ca);
             const float qz[4] = {ca, 0.f, 0.f, sa};
@@ -828,8 +863,8 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
     __syncwarp();
 }
 
-template <int LPS, bool FLAT>
-__global__ void __launch_bounds__(512) step_kernel(const __grid_constant__ WorldDev W, int n_steps, int sbytes) {
+template <int LPS, bool FLAT, bool OPT>
+__device__ __forceinline__ void step_body(const WorldDev &W, int n_steps, int sbytes) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int G = 32 / LPS;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -850,8 +885,21 @@ __global__ void __launch_bounds__(512) step_kernel(const __grid_constant__ World
         if (item >= n_items) break;
         const int idx = item * G + g;
         const int s = idx < n_sched ? W.order[idx] : -1;
-        run_scene<LPS, FLAT>(W, s, gl, pts, fr, th, th_old, tb, n_steps, step0);
+        run_scene<LPS, FLAT, OPT>(W, s, gl, pts, fr, th, th_old, tb, n_steps, step0);
     }
+}
+
+// Flat ground: up to 16 warps per block, 128 registers a thread.
+template <int LPS, bool OPT>
+__global__ void __launch_bounds__(512) step_kernel(const __grid_constant__ WorldDev W, int n_steps, int sbytes) {
+    step_body<LPS, true, OPT>(W, n_steps, sbytes);
+}
+
+// Height maps keep more state (the map window and its origin): 168 registers a thread, up to 12
+// warps per block; their larger slots leave no more warps resident at 16 lanes per scene anyway.
+template <int LPS, bool OPT>
+__global__ void __maxnreg__(168) step_kernel_hm(const __grid_constant__ WorldDev W, int n_steps, int sbytes) {
+    step_body<LPS, false, OPT>(W, n_steps, sbytes);
 }
 
 __global__ void advance_kernel(long long *step, int n) { *step += n; }
@@ -1482,20 +1530,27 @@ size_t step_smem_bytes(const WorldDev &W, int lps, int wpb) {
     return (size_t)wpb * (32 / lps) * step_slot_bytes(W, lps);
 }
 
-template <int LPS, bool FLAT>
-static void *step_fn() { return (void *)step_kernel<LPS, FLAT>; }
+template <int LPS, bool FLAT, bool OPT>
+static void *step_fn() { return FLAT ? (void *)step_kernel<LPS, OPT> : (void *)step_kernel_hm<LPS, OPT>; }
 
-static void *pick_step(int lps, bool flat) {
+template <bool OPT>
+static void *pick_step_opt(int lps, bool flat) {
     switch (lps) {
-        case 8: return flat ? step_fn<8, true>() : step_fn<8, false>();
-        case 16: return flat ? step_fn<16, true>() : step_fn<16, false>();
-        case 32: return flat ? step_fn<32, true>() : step_fn<32, false>();
+        case 8: return flat ? step_fn<8, true, OPT>() : step_fn<8, false, OPT>();
+        case 16: return flat ? step_fn<16, true, OPT>() : step_fn<16, false, OPT>();
+        case 32: return flat ? step_fn<32, true, OPT>() : step_fn<32, false, OPT>();
         default: return nullptr;
     }
 }
 
+// the kernel for a world: flat or height maps, friction options compiled in only when used
+static void *pick_step(const WorldDev &W, int lps) {
+    const bool flat = W.hm == nullptr;
+    return W.fric_mode ? pick_step_opt<true>(lps, flat) : pick_step_opt<false>(lps, flat);
+}
+
 int step_blocks_per_sm(const WorldDev &W, int lps, int wpb, cudaError_t *err) {
-    void *fn = pick_step(lps, W.hm == nullptr);
+    void *fn = pick_step(W, lps);
     *err = cudaSuccess;
     if (!fn) { *err = cudaErrorInvalidValue; return 0; }
     const size_t smem = step_smem_bytes(W, lps, wpb);
@@ -1510,6 +1565,7 @@ int step_blocks_per_sm(const WorldDev &W, int lps, int wpb, cudaError_t *err) {
     cudaFuncAttributes fa{};
     *err = cudaFuncGetAttributes(&fa, fn);
     if (*err != cudaSuccess) { cudaGetLastError(); return 0; }
+    if (wpb * 32 > fa.maxThreadsPerBlock) return 0;
     if ((size_t)fa.maxDynamicSharedSizeBytes < smem) {
         *err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (*err != cudaSuccess) { cudaGetLastError(); return 0; }
@@ -1520,7 +1576,7 @@ int step_blocks_per_sm(const WorldDev &W, int lps, int wpb, cudaError_t *err) {
 }
 
 cudaError_t launch_step(const WorldDev &W, const LaunchCfg &cfg, int n_steps, cudaStream_t st) {
-    void *fn = pick_step(cfg.lps, W.hm == nullptr);
+    void *fn = pick_step(W, cfg.lps);
     if (!fn || cfg.wpb < 1 || cfg.wpb > 16 || cfg.blocks < 1) return cudaErrorInvalidValue;
     // the kernel's shared-memory limit was raised by step_blocks_per_sm for this shape
     const size_t smem = step_smem_bytes(W, cfg.lps, cfg.wpb);

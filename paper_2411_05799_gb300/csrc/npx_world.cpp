@@ -968,6 +968,26 @@ int npx_actuator_set(npx_world *w, int mode, const float *params) {
     return NPX_OK;
 }
 
+int npx_world_set_friction_model(npx_world *w, int flags) {
+    if (int rc = check_world(w)) return rc;
+    if (flags & ~(NPX_FRIC_WEIGHTED | NPX_FRIC_TILT)) return fail(NPX_EINVAL, "unknown friction flags %d", flags);
+    w->W.fric_mode = flags;
+    clear_graphs(w);    // kernel arguments changed
+    if (w->finalized) {
+        // the options select another build of the step kernel: size its launches (and raise its
+        // shared-memory limit) as the current shapes' were
+        CUDA_TRY(cudaSetDevice(w->device));
+        int rc;
+        for (auto &cls : w->classes) {
+            cls.cfg = clamp_cfg_for(w, class_world(w, cls), cls.count, cls.cfg, &rc);
+            if (rc) return rc;
+        }
+        w->cfg = clamp_cfg(w, w->cfg, &rc);
+        if (rc) return rc;
+    }
+    return NPX_OK;
+}
+
 int npx_world_step(npx_world *w, int n) {
     if (int rc = check_ready(w)) return rc;
     if (n < 0) return fail(NPX_EINVAL, "n must be >= 0");

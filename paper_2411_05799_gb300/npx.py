@@ -21,6 +21,8 @@ NPX_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ESTATE", -4: "ECUDA", -5: "ETIMEOUT", -6: "ERANGE"}
 ACT_HOLD = 0
 ACT_SINUSOID = 1
+FRIC_WEIGHTED = 1     # friction rows weighted by the normal forces (npx_world_set_friction_model)
+FRIC_TILT = 2         # the friction impulse also turns the body about the horizontal axes
 
 
 class NpxError(RuntimeError):
@@ -143,6 +145,7 @@ _SIGS = {
     "npx_step_noalloc": [P, I, P],
     "npx_gemm_bf16": [P, P, I, I, I, I, P, P, P],
     "npx_gemm_wait_selftest": [I, P, P, P],
+    "npx_world_set_friction_model": [P, I],
     "npx_mlp_create": [P, P],
     "npx_mlp_destroy": [P],
     "npx_mlp_params_set": [P, P, C.c_size_t],
@@ -327,6 +330,10 @@ class World:
             out = np.zeros(self._info["n_points"], np.uint8)
         _check(_lib.npx_contacts_read(self._h, _p(out), out.size))
         return out
+
+    def set_friction_model(self, flags: int):
+        """FRIC_WEIGHTED | FRIC_TILT (0: Eqs. 1-6 as written)."""
+        _check(_lib.npx_world_set_friction_model(self._h, int(flags)))
 
     def set_actuators(self, mode, params=None):
         p = None if params is None else _f32(params)

@@ -63,6 +63,15 @@ def test_weighted_ls_special_cases():
     assert a == 0.0
     t, a = friction_ls_w(s, e, np.zeros(9))
     assert a == 0.0 and np.all(t == 0.0)
+    # the rotation needs a centre of pressure spread over more than a millimetre (mean squared
+    # spread above 1e-6 m^2): two points 0.5 mm apart, or 5 cm apart with the weight nearly all on
+    # one, give a translation only; 5 cm apart with equal weights, a rotation
+    two = np.array([[0.0, 0.0], [5e-4, 0.0]])
+    e2 = np.array([[0.0, -1e-5], [0.0, 1e-5]])
+    assert friction_ls_w(two, e2, np.ones(2))[1] == 0.0
+    two = np.array([[0.0, 0.0], [0.05, 0.0]])
+    assert friction_ls_w(two, e2, np.array([1.0, 1e-4]))[1] == 0.0
+    assert friction_ls_w(two, e2, np.ones(2))[1] == pytest.approx(2e-5 / 0.05)
     # a rigid motion in the model's family is recovered exactly whatever the weights
     a, a3 = np.array([0.01, -0.02]), 0.003
     e = a + a3 * np.stack([-s[:, 1], s[:, 0]], 1)
