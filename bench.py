@@ -142,15 +142,22 @@ def cpu_oracle_sample(batch, n_scenes: int, n_steps: int, threads: int) -> dict:
 
 def other_workloads(World, scenes, stream, device) -> dict:
     """Scene-steps/s of 1,000-step launches on the uneven mixed batch (2 s simulated after a
-    warm-up second) and the evolution-scale rollout on rough terrain (the whole 60 s simulated from
+    warm-up second), the evolution-scale rollout on rough terrain (the whole 60 s simulated from
     the initial state, after a warm-up second and a reset; its fitness is the horizontal distance
-    each robot's CoG moved), state resident in HBM, CUDA events."""
+    each robot's CoG moved) and the benchmark's hexapods with both friction refinements on (2 s),
+    state resident in HBM, CUDA events."""
     import torch
     out = {}
-    for name, make, secs in (("uneven_mix_65536_scenes", lambda: scenes.uneven_batch(65536), 2),
-                             ("hexapod_rough_terrain_16384_scenes", lambda: scenes.cpg_batch(16384), 60)):
+    from paper_2411_05799_gb300.npx import FRIC_TILT, FRIC_WEIGHTED
+    for name, make, secs, fric in (
+            ("uneven_mix_65536_scenes", lambda: scenes.uneven_batch(65536), 2, 0),
+            ("hexapod_rough_terrain_16384_scenes", lambda: scenes.cpg_batch(16384), 60, 0),
+            ("hexapod_4096_scenes_friction_weighted_tilt", lambda: scenes.hexapod_batch(N_SCENES), 2,
+             FRIC_WEIGHTED | FRIC_TILT)):
         b = make()
         w = World.from_batch(b, stream=stream.cuda_stream, device=device)
+        if fric:
+            w.set_friction_model(fric)
         w.autotune(100)
         w.configure(chunk_steps=CHUNK)
         start = w.export_state()
