@@ -46,6 +46,10 @@
 #include <string.h>
 
 #define NPXO_ACT_HOLD 0
+#define NPXO_ACT_GP 2
+#define NPXO_GP_LEN 32          /* program bytes (the 5-bit jump address reaches 32) */
+#define NPXO_GP_PER_UPDATE 32   /* instructions executed per joint update */
+#define NPXO_GP_KMAX 36         /* joint targets saturate at +-36 steps (+-180 degrees) */
 #define NPXO_PI 3.14159265358979323846
 #define NPXO_POINT_RADIUS 1e-3
 
@@ -198,6 +202,35 @@ double npxo_target(const npxo_model *M, int scene, int jl, long long n) {
     uint32_t u = (uint32_t)((uint64_t)nu * (uint64_t)n);
     double turns = (double)u / 4294967296.0;
     return b + A * sin(2.0 * NPXO_PI * turns + phi);
+}
+
+/* ------------------------------------------------------------------ Sec. IV: GP controller */
+
+/* Table I: an 8-bit opcode is a 3-bit command and a 5-bit value x.  000 move motor x left and 001
+ * right (its target by -/+ one 5-degree step, saturating at +-NPXO_GP_KMAX steps; a motor the
+ * scene lacks is ignored), 010 read sensor x (acc = foot-contact bit x of the last step), 011 load
+ * x (acc = x), 100 jump to address x if acc != 0, 101 not (acc = ~acc), 110 inc, 111 dec.  The
+ * accumulator is 8 bits wide (it wraps); the program counter wraps after the last address. */
+void npxo_gp_run(const unsigned char *prog, unsigned char *pc, unsigned char *acc, signed char *k,
+                 int nj, unsigned int sensors, int n_instr) {
+    unsigned int p = *pc % NPXO_GP_LEN, a = *acc;
+    for (int it = 0; it < n_instr; ++it) {
+        const unsigned int op = prog[p] >> 5, x = prog[p] & 31u;
+        unsigned int next = (p + 1) % NPXO_GP_LEN;
+        switch (op) {
+            case 0: if ((int)x < nj && k[x] > -NPXO_GP_KMAX) k[x] -= 1; break;
+            case 1: if ((int)x < nj && k[x] < NPXO_GP_KMAX) k[x] += 1; break;
+            case 2: a = (sensors >> x) & 1u; break;
+            case 3: a = x; break;
+            case 4: if (a != 0) next = x; break;
+            case 5: a = ~a & 255u; break;
+            case 6: a = (a + 1) & 255u; break;
+            default: a = (a + 255u) & 255u; break;
+        }
+        p = next;
+    }
+    *pc = (unsigned char)p;
+    *acc = (unsigned char)a;
 }
 
 /* Forward kinematics over the link tree, then the mass properties of the whole robot
@@ -381,8 +414,14 @@ static void scene_step(const npxo_model *M, npxo_state *st, int s, scene_ws *w, 
     int tick = (M->act_mode != NPXO_ACT_HOLD) && (n % M->K == 0);
     if (tick) {
         int nj = w->nl - 1;
+        /* the machine-code controller (Sec. IV): its instructions run, reading the foot contacts
+         * of the last step, and set the targets in 5-degree steps */
+        if (M->act_mode == NPXO_ACT_GP)
+            npxo_gp_run(M->gp_prog + NPXO_GP_LEN * (size_t)s, st->gp_pc + s, st->gp_acc + s,
+                        st->gp_k + w->j0, nj, st->sensors[s], NPXO_GP_PER_UPDATE);
         for (int j = 0; j < nj; ++j) {
-            double th = npxo_target(M, s, j, n);
+            double th = M->act_mode == NPXO_ACT_GP ? st->gp_k[w->j0 + j] * (NPXO_PI / 36.0)
+                                                   : npxo_target(M, s, j, n);
             double lo = M->lo[w->l0 + j + 1], hi = M->hi[w->l0 + j + 1];
             if (th < lo) th = lo;
             if (th > hi) th = hi;
@@ -557,6 +596,7 @@ static void scene_step(const npxo_model *M, npxo_state *st, int s, scene_ws *w, 
 
 static int check_model(const npxo_model *M) {
     if (M->n_scenes < 0 || M->K < 1 || !(M->dt > 0.0)) return -1;
+    if (M->act_mode == NPXO_ACT_GP && !M->gp_prog) return -1;
     for (int s = 0; s < M->n_scenes; ++s) {
         int l0 = M->link_off[s], nl = M->link_off[s + 1] - l0;
         int p0 = M->point_off[s], np = M->point_off[s + 1] - p0;
@@ -599,6 +639,9 @@ int npxo_init(const npxo_model *M, const float *origin, const float *quat, const
         for (int i = 0; i < w.np; ++i) st->kappa[w.p0 + i] = 0;
         st->sensors[s] = 0;
         st->status[s] = 0;
+        if (st->gp_pc) { st->gp_pc[s] = 0; st->gp_acc[s] = 0; }
+        if (st->gp_k)
+            for (int j = 0; j < w.nl - 1; ++j) st->gp_k[w.j0 + j] = 0;
     }
     ws_free(&w);
     return 0;

@@ -28,6 +28,7 @@ typedef struct {
     int act_mode; const float *act_params;                /* [J*4]: A, f, phi, bias */
     int fric_mode;         /* bit 0: least-squares rows weighted by the normal forces; bit 1: the
                               friction impulse's torque about the horizontal axes (0 = Eqs. 1-6) */
+    const unsigned char *gp_prog;  /* [S*32] machine-code programs (act_mode 2, Sec. IV, Table I) */
 } npxo_model;
 
 typedef struct {
@@ -36,6 +37,8 @@ typedef struct {
     unsigned char *kappa;        /* [P] contact flag of the previous step */
     unsigned int *sensors;       /* [S] foot-contact bits of the last step */
     unsigned int *status;        /* [S] 0 = ok, bit 0 non-finite, bit 1 out of bounds */
+    unsigned char *gp_pc, *gp_acc;  /* [S] program counter and accumulator (act_mode 2) */
+    signed char *gp_k;           /* [J] joint targets in 5-degree steps (act_mode 2) */
 } npxo_state;
 
 /* event counts: the numerators of the algorithmic-flop model */
@@ -58,6 +61,10 @@ int  npxo_lut(const npxo_model *M, int scene, double x, double y, double *h);
 int  npxo_friction_ls(int n, const double *src_xy, const double *e_xy, double *t2, double *a3);
 int  npxo_friction_ls_w(int n, const double *src_xy, const double *e_xy, const double *w, double *t2,
                         double *a3);
+/* The machine-code controller (Table I): n_instr instructions of prog from *pc, with accumulator
+ * *acc, the scene's foot-contact bits `sensors` and the nj joint targets k (5-degree steps). */
+void npxo_gp_run(const unsigned char *prog, unsigned char *pc, unsigned char *acc, signed char *k,
+                 int nj, unsigned int sensors, int n_instr);
 
 #ifdef __cplusplus
 }

@@ -45,13 +45,15 @@ class _Model(C.Structure):
         ("hm_scale", C.c_double), ("hm_origin", C.c_double * 2),
         ("act_mode", C.c_int), ("act_params", C.c_void_p),
         ("fric_mode", C.c_int),
+        ("gp_prog", C.c_void_p),
     ]
 
 
 class _State(C.Structure):
     _fields_ = [("c", C.c_void_p), ("q", C.c_void_p), ("v", C.c_void_p), ("L", C.c_void_p),
                 ("theta", C.c_void_p), ("kappa", C.c_void_p), ("sensors", C.c_void_p),
-                ("status", C.c_void_p)]
+                ("status", C.c_void_p), ("gp_pc", C.c_void_p), ("gp_acc", C.c_void_p),
+                ("gp_k", C.c_void_p)]
 
 
 class Counts(C.Structure):
@@ -82,6 +84,8 @@ def lib():
         _lib.npxo_lut.argtypes = [P, C.c_int, C.c_double, C.c_double, P]
         _lib.npxo_friction_ls.argtypes = [C.c_int, P, P, P, P]
         _lib.npxo_friction_ls_w.argtypes = [C.c_int, P, P, P, P, P]
+        _lib.npxo_gp_run.argtypes = [P, P, P, P, C.c_int, C.c_uint, C.c_int]
+        _lib.npxo_gp_run.restype = None
     return _lib
 
 
@@ -111,6 +115,20 @@ def friction_ls_w(src_xy: np.ndarray, e_xy: np.ndarray, w: np.ndarray):
     return t, float(a3[0])
 
 
+ACT_GP = 2                # actuator mode of the machine-code controller (Sec. IV, Table I)
+GP_LEN, GP_PER_UPDATE = 32, 32
+
+
+def gp_run(prog, pc: int, acc: int, k, sensors: int, n_instr: int = GP_PER_UPDATE):
+    """The oracle's interpreter on one program: returns (pc, acc, k) after n_instr instructions."""
+    p = np.ascontiguousarray(prog, np.uint8)
+    pcs = np.array([pc], np.uint8)
+    accs = np.array([acc], np.uint8)
+    kk = np.ascontiguousarray(np.array(k, np.int8))
+    lib().npxo_gp_run(_ptr(p), _ptr(pcs), _ptr(accs), _ptr(kk), len(kk), int(sensors), int(n_instr))
+    return int(pcs[0]), int(accs[0]), kk
+
+
 # friction-model options (bits of fric_mode): least-squares rows weighted by the points' normal
 # forces; the friction impulse's torque about the horizontal axes.  0 = Eqs. 1-6 as written.
 FRIC_WEIGHTED, FRIC_TILT = 1, 2
@@ -119,7 +137,7 @@ FRIC_WEIGHTED, FRIC_TILT = 1, 2
 class Oracle:
     """FP64 state of every scene of a SceneBatch, advanced by the C oracle."""
 
-    def __init__(self, batch, threads: int = 1, fric_mode: int = 0):
+    def __init__(self, batch, threads: int = 1, fric_mode: int = 0, gp_programs=None):
         self.batch = b = batch
         self.threads = threads
         self.fric_mode = int(fric_mode)
@@ -131,6 +149,8 @@ class Oracle:
         maps = None if b.heightmaps is None else np.ascontiguousarray(b.heightmaps, np.float32)
         act = np.ascontiguousarray(b.act_params if b.act_params is not None
                                    else np.zeros((J, 4), np.float32), np.float32)
+        # the machine-code controller replaces the batch's actuators when programs are given
+        self.gp_prog = None if gp_programs is None else np.ascontiguousarray(gp_programs, np.uint8).reshape(S, GP_LEN)
         self._keep += [maps, act]
         self.model = _Model(
             n_scenes=S, dt=b.dt, gravity=(C.c_double * 3)(*b.gravity), K=b.joint_update_steps,
@@ -140,7 +160,8 @@ class Oracle:
             sensor=_ptr(sen), mu=_ptr(mu), hmap=_ptr(hm), heightmaps=_ptr(maps),
             hm_nx=0 if maps is None else maps.shape[2], hm_ny=0 if maps is None else maps.shape[1],
             hm_scale=b.hm_scale, hm_origin=(C.c_double * 2)(*b.hm_origin),
-            act_mode=b.act_mode, act_params=_ptr(act), fric_mode=int(fric_mode))
+            act_mode=ACT_GP if self.gp_prog is not None else b.act_mode, act_params=_ptr(act),
+            fric_mode=int(fric_mode), gp_prog=_ptr(self.gp_prog) if self.gp_prog is not None else None)
         self.c = np.zeros((S, 3))
         self.q = np.zeros((S, 4))
         self.v = np.zeros((S, 3))
@@ -149,8 +170,12 @@ class Oracle:
         self.kappa = np.zeros(P, np.uint8)
         self.sensors = np.zeros(S, np.uint32)
         self.status = np.zeros(S, np.uint32)
+        self.gp_pc = np.zeros(S, np.uint8)
+        self.gp_acc = np.zeros(S, np.uint8)
+        self.gp_k = np.zeros(J, np.int8)
         self.state = _State(*[_ptr(a) for a in (self.c, self.q, self.v, self.L, self.theta,
-                                                 self.kappa, self.sensors, self.status)])
+                                                 self.kappa, self.sensors, self.status,
+                                                 self.gp_pc, self.gp_acc, self.gp_k)])
         self.n = 0
         rc = lib().npxo_init(C.byref(self.model), _ptr(b.origin), _ptr(b.quat), _ptr(b.vel),
                              _ptr(b.omega), _ptr(np.ascontiguousarray(b.theta0, np.float32)),
@@ -214,7 +239,8 @@ class Oracle:
     def copy_state_from(self, other: "Oracle"):
         for a, b_ in ((self.c, other.c), (self.q, other.q), (self.v, other.v), (self.L, other.L),
                       (self.theta, other.theta), (self.kappa, other.kappa),
-                      (self.sensors, other.sensors), (self.status, other.status)):
+                      (self.sensors, other.sensors), (self.status, other.status),
+                      (self.gp_pc, other.gp_pc), (self.gp_acc, other.gp_acc), (self.gp_k, other.gp_k)):
             a[...] = b_
         self.n = other.n
 

@@ -17,7 +17,7 @@ def to_gpu(world, o: Oracle):
 
 
 def clone(o: Oracle) -> Oracle:
-    c = Oracle(o.batch, threads=o.threads, fric_mode=o.fric_mode)
+    c = Oracle(o.batch, threads=o.threads, fric_mode=o.fric_mode, gp_programs=o.gp_prog)
     c.copy_state_from(o)
     return c
 
