@@ -187,6 +187,26 @@ def other_workloads(World, scenes, stream, device) -> dict:
     return out
 
 
+def gp_evolution_leg(scenes, stream, n_groups: int = 160, generations: int = 3) -> dict:
+    """The paper's own workload (Sec. IV): machine-code controllers of the hexapod evolved by
+    mutation, best 50 of 100 kept, two-minute evaluations; here n_groups populations side by side
+    in one world.  Scene-steps/s over the evaluations and the best fitness per generation."""
+    from paper_2411_05799_gb300 import evolution
+    t0 = time.perf_counter()
+    res = evolution.evolve(n_groups=n_groups, pop=100, keep=50, generations=generations,
+                           eval_seconds=120.0, seed=11, stream=stream.cuda_stream)
+    wall = time.perf_counter() - t0
+    best = res["best_fitness"]
+    out = {"workload": f"gp_hexapod_{n_groups}x100_robots_2min_evaluations", "unit": UNIT,
+           "value": res["scene_steps"] / res["step_seconds"], "generations": generations,
+           "populations": n_groups, "robots": n_groups * 100,
+           "seconds_per_generation": res["step_seconds"] / generations, "wall_seconds": round(wall, 2),
+           "best_fitness_m": {"median_over_populations": [float(np.median(b)) for b in best],
+                              "max": [float(b.max()) for b in best]}}
+    res["world"].close()
+    return out
+
+
 def _measured_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -437,6 +457,8 @@ def run_gpu(args):
     if rank == 0 and not args.no_surrogate:
         line["surrogate"] = surrogate_leg(World, scenes, stream, dev, args.surrogate_transitions,
                                           args.surrogate_stride)
+    if not args.no_extra and rank == 0:
+        line["gp_evolution"] = gp_evolution_leg(scenes, stream)
 
     if rank == 0:
         # algorithmic flops per scene-step from the oracle's event counts on a sample

@@ -40,6 +40,7 @@ extern "C" {
 
 #define NPX_ACT_HOLD 0     /* joints keep their angles; no joint updates */
 #define NPX_ACT_SINUSOID 1 /* target = bias + A sin(2 pi f t + phi), set every K steps */
+#define NPX_ACT_GP 2       /* targets set by each scene's machine-code program (npx_gp_programs_set) */
 
 /* Friction-model options (bits; 0 = the least squares of Sec. III-C, Eqs. 1-6, as written).  The
  * two refinements the paper names after Eq. 6: */
@@ -159,6 +160,21 @@ int npx_contacts_read(npx_world *w, uint8_t *contact, size_t n);
  * (amplitude rad, frequency Hz, phase rad, bias rad) per joint.  The phase advances by
  * round(f dt 2^32) / 2^32 turns per step (exact over any horizon). */
 int npx_actuator_set(npx_world *w, int mode, const float *params);
+/* The machine-code controller of Sec. IV (Table I) drives every scene's joints: programs [S*32]
+ * (host), one 32-byte program per scene, each byte an opcode (upper 3 bits) and value x (lower 5):
+ * 000 / 001 move motor x left / right (its target by -/+ 5 degrees, saturating at +-36 steps;
+ * motors the scene lacks are ignored), 010 accumulator = foot-contact bit x of the last step,
+ * 011 accumulator = x, 100 jump to address x if the accumulator is non-zero, 101 not, 110 inc,
+ * 111 dec (8-bit accumulator; the program counter wraps after address 31).  At every joint
+ * update (n % K == 0) each scene executes 32 instructions from its saved program counter, then
+ * its joints take the clamped targets.  The call resets the program counters, accumulators and
+ * targets (5-degree steps, 0 = the rest pose) and switches the world to NPX_ACT_GP; the state
+ * blob carries the controller state; npx_actuator_set switches back. */
+int npx_gp_programs_set(npx_world *w, const uint8_t *programs);
+/* Controller state (host arrays, NULL to skip): program counters and accumulators [S], joint
+ * targets in 5-degree steps [J] (write: each within +-36). */
+int npx_gp_state_read(npx_world *w, uint8_t *pc, uint8_t *acc, int8_t *k);
+int npx_gp_state_write(npx_world *w, const uint8_t *pc, const uint8_t *acc, const int8_t *k);
 /* Friction model of the following steps: a combination of NPX_FRIC_* bits (0 by default).
  * NPX_FRIC_WEIGHTED: the least-squares centroid, moments and slip are weighted by the points'
  * normal forces of the step (the centroid becomes the centre of pressure); a rotation is solved

@@ -59,6 +59,11 @@ struct WorldDev {
     // friction-model options: bit 0 rows weighted by the normal forces, bit 1 the friction
     // impulse's torque about the horizontal axes (0: Eqs. 1-6 as written)
     int fric_mode;
+    // machine-code controller (act_mode 2, Sec. IV Table I): programs [32 * S], program counter
+    // and accumulator [S], joint targets in 5-degree steps [J]
+    const uint8_t *gp_prog;
+    uint8_t *gp_pc, *gp_acc;
+    int8_t *gp_k;
 };
 
 struct LaunchCfg {

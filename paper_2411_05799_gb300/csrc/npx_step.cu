@@ -422,6 +422,40 @@ __device__ __forceinline__ float joint_target(const WorldDev &W, int j, long lon
     return a.w + a.x * sinf(fmaf(6.2831853071795865f, turns, a.z));
 }
 
+// ------------------------------------------------------------------------ machine-code controller
+
+constexpr int GP_LEN = 32, GP_PER_UPDATE = 32, GP_KMAX = 36;
+constexpr float GP_STEP = 0.087266462599716478846f;   // 5 degrees
+
+// The controller of Sec. IV at a joint update, run by lane 0 of the scene's group: GP_PER_UPDATE
+// instructions of Table I from the saved program counter.  8-bit opcode = 3-bit command + 5-bit
+// value x: 000 / 001 move motor x left / right (its target by -/+ one 5-degree step, saturating at
+// +-GP_KMAX; motors the scene lacks are ignored), 010 acc = foot-contact bit x of the last step,
+// 011 acc = x, 100 jump to x if acc != 0, 101 acc = ~acc, 110 inc, 111 dec (8-bit accumulator,
+// the program counter wraps after address 31).
+__device__ __noinline__ void gp_run(const WorldDev &W, int s, int j0, int nj, uint32_t sensors) {
+    const uint8_t *prog = W.gp_prog + (size_t)GP_LEN * s;
+    int8_t *k = W.gp_k + j0;
+    uint32_t p = W.gp_pc[s] & (GP_LEN - 1), a = W.gp_acc[s];
+    for (int it = 0; it < GP_PER_UPDATE; ++it) {
+        const uint32_t ins = prog[p], op = ins >> 5, x = ins & 31u;
+        uint32_t next = (p + 1) & (GP_LEN - 1);
+        switch (op) {
+            case 0: if ((int)x < nj && k[x] > -GP_KMAX) k[x] = (int8_t)(k[x] - 1); break;
+            case 1: if ((int)x < nj && k[x] < GP_KMAX) k[x] = (int8_t)(k[x] + 1); break;
+            case 2: a = (sensors >> x) & 1u; break;
+            case 3: a = x; break;
+            case 4: if (a != 0u) next = x; break;
+            case 5: a = ~a & 255u; break;
+            case 6: a = (a + 1u) & 255u; break;
+            default: a = (a + 255u) & 255u; break;
+        }
+        p = next;
+    }
+    W.gp_pc[s] = (uint8_t)p;
+    W.gp_acc[s] = (uint8_t)a;
+}
+
 // ------------------------------------------------------------------------ one scene, n steps
 
 // OPT: the friction-model options (W.fric_mode) are compiled in; without them the step is the
@@ -517,11 +551,25 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         float gold[3] = {0.f, 0.f, 0.f};
         if (tick) {
             gold[0] = shr.g[0]; gold[1] = shr.g[1]; gold[2] = shr.g[2];
+            const bool gp = W.act_mode == 2;
+            if (gp) {
+                // the controller reads the foot contacts of the last step and sets the targets
+                uint32_t sens = 0;
+                for (int k = 0, i = gl; i < np; ++k, i += LPS)
+                    if ((kprev >> k) & 1ull) {
+                        const int sid = W.links[l0 + W.plink[p0 + i]].sensor;
+                        if (sid >= 0 && sid < 32) sens |= 1u << sid;
+                    }
+                sens = gor<LPS>(sens);
+                if (gl == 0 && valid && status == 0u) gp_run(W, s, j0, nj, sens);
+                __syncwarp();
+            }
             for (int j = gl; j < nj; j += LPS) {
                 th_old[j] = th[j];
                 if (status == 0u) {   // a frozen scene keeps its angles
                     const LinkDev lk = W.links[l0 + j + 1];
-                    th[j] = fminf(fmaxf(joint_target(W, j0 + j, n), lk.lo), lk.hi);
+                    const float tgt = gp ? (float)W.gp_k[j0 + j] * GP_STEP : joint_target(W, j0 + j, n);
+                    th[j] = fminf(fmaxf(tgt, lk.lo), lk.hi);
                 }
             }
             __syncwarp();

@@ -447,7 +447,7 @@ int enqueue_steps(npx_world *w, int n) {
 }
 
 struct BlobLayout {
-    size_t st, theta, omega, kappa, sensors, status, end;
+    size_t st, theta, omega, kappa, sensors, status, gp_pc, gp_acc, gp_k, end;
 };
 
 BlobLayout blob_layout(const npx_world *w) {
@@ -458,7 +458,10 @@ BlobLayout blob_layout(const npx_world *w) {
     b.sensors = b.omega + sizeof(float) * 3 * (size_t)w->S;
     b.status = b.sensors + sizeof(uint32_t) * (size_t)w->S;
     b.kappa = b.status + sizeof(uint32_t) * (size_t)w->S;
-    b.end = b.kappa + (size_t)w->P;
+    b.gp_pc = b.kappa + (size_t)w->P;        // the machine-code controller's state
+    b.gp_acc = b.gp_pc + (size_t)w->S;
+    b.gp_k = b.gp_acc + (size_t)w->S;
+    b.end = b.gp_k + (size_t)w->J;
     return b;
 }
 
@@ -808,6 +811,8 @@ int npx_world_finalize(npx_world *w) {
     float *d_mu, *d_st, *d_theta, *d_omega;
     uint32_t *d_nu, *d_sens, *d_status;
     unsigned int *d_queue;
+    uint8_t *d_gp_prog, *d_gp_pc, *d_gp_acc;
+    int8_t *d_gp_k;
     int rc = 0;
     if ((rc = dev_alloc(w, &d_lo, S + 1)) || (rc = dev_alloc(w, &d_po, S + 1)) ||
         (rc = dev_alloc(w, &d_hmap, S)) || (rc = dev_alloc(w, &d_order, S)) ||
@@ -821,8 +826,14 @@ int npx_world_finalize(npx_world *w) {
         (rc = dev_alloc(w, &d_status, S)) || (rc = dev_alloc(w, &d_queue, kMaxClasses)) ||
         (rc = dev_alloc(w, &w->d_step, 1)) || (rc = dev_alloc(w, &w->d_stage, 16 * (size_t)S)) ||
         (rc = dev_alloc(w, &w->d_kstage, w->P)) || (rc = dev_alloc(w, &w->d_perm, w->P)) ||
-        (rc = dev_alloc(w, &w->d_points, 3 * (size_t)w->max_points)))
+        (rc = dev_alloc(w, &w->d_points, 3 * (size_t)w->max_points)) ||
+        (rc = dev_alloc(w, &d_gp_prog, 32 * (size_t)S)) || (rc = dev_alloc(w, &d_gp_pc, S)) ||
+        (rc = dev_alloc(w, &d_gp_acc, S)) || (rc = dev_alloc(w, &d_gp_k, w->J)))
         return rc;
+    CUDA_TRY(cudaMemset(d_gp_prog, 0, 32 * (size_t)S));
+    CUDA_TRY(cudaMemset(d_gp_pc, 0, S));
+    CUDA_TRY(cudaMemset(d_gp_acc, 0, S));
+    CUDA_TRY(cudaMemset(d_gp_k, 0, std::max(w->J, 1)));
     CUDA_TRY(cudaMemcpy(d_lo, w->link_off.data(), sizeof(int) * (S + 1), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(d_po, w->point_off.data(), sizeof(int) * (S + 1), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(d_hmap, w->hmap.data(), sizeof(int) * S, cudaMemcpyHostToDevice));
@@ -856,6 +867,7 @@ int npx_world_finalize(npx_world *w) {
     W.order = d_order; W.n_sched = S; W.sched_count = nullptr;
     W.max_points = w->max_points; W.max_links = w->max_links;
     W.step = w->d_step; W.queue = d_queue;
+    W.gp_prog = d_gp_prog; W.gp_pc = d_gp_pc; W.gp_acc = d_gp_acc; W.gp_k = d_gp_k;
     w->finalized = true;
     w->flats.clear();
     w->flats.shrink_to_fit();
@@ -965,6 +977,45 @@ int npx_actuator_set(npx_world *w, int mode, const float *params) {
     w->act_mode = mode;
     w->W.act_mode = mode;
     clear_graphs(w);    // kernel arguments changed
+    return NPX_OK;
+}
+
+int npx_gp_programs_set(npx_world *w, const uint8_t *programs) {
+    if (int rc = check_ready(w)) return rc;
+    if (!programs) return fail(NPX_EINVAL, "null programs");
+    CUDA_TRY(cudaSetDevice(w->device));
+    const size_t S = w->S;
+    CUDA_TRY(cudaMemcpyAsync((void *)w->W.gp_prog, programs, 32 * S, cudaMemcpyHostToDevice, w->stream));
+    CUDA_TRY(cudaMemsetAsync(w->W.gp_pc, 0, S, w->stream));
+    CUDA_TRY(cudaMemsetAsync(w->W.gp_acc, 0, S, w->stream));
+    CUDA_TRY(cudaMemsetAsync(w->W.gp_k, 0, std::max(w->J, 1), w->stream));
+    CUDA_TRY(cudaStreamSynchronize(w->stream));
+    w->act_mode = NPX_ACT_GP;
+    w->W.act_mode = NPX_ACT_GP;
+    clear_graphs(w);    // kernel arguments changed
+    return NPX_OK;
+}
+
+int npx_gp_state_read(npx_world *w, uint8_t *pc, uint8_t *acc, int8_t *k) {
+    if (int rc = check_ready(w)) return rc;
+    CUDA_TRY(cudaSetDevice(w->device));
+    if (pc) CUDA_TRY(cudaMemcpyAsync(pc, w->W.gp_pc, w->S, cudaMemcpyDeviceToHost, w->stream));
+    if (acc) CUDA_TRY(cudaMemcpyAsync(acc, w->W.gp_acc, w->S, cudaMemcpyDeviceToHost, w->stream));
+    if (k && w->J) CUDA_TRY(cudaMemcpyAsync(k, w->W.gp_k, w->J, cudaMemcpyDeviceToHost, w->stream));
+    CUDA_TRY(cudaStreamSynchronize(w->stream));
+    return NPX_OK;
+}
+
+int npx_gp_state_write(npx_world *w, const uint8_t *pc, const uint8_t *acc, const int8_t *k) {
+    if (int rc = check_ready(w)) return rc;
+    if (!pc || !acc || (!k && w->J)) return fail(NPX_EINVAL, "null controller state");
+    for (int j = 0; j < w->J; ++j)
+        if (k[j] < -36 || k[j] > 36) return fail(NPX_EINVAL, "joint %d: target step %d outside +-36", j, k[j]);
+    CUDA_TRY(cudaSetDevice(w->device));
+    CUDA_TRY(cudaMemcpyAsync(w->W.gp_pc, pc, w->S, cudaMemcpyHostToDevice, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(w->W.gp_acc, acc, w->S, cudaMemcpyHostToDevice, w->stream));
+    if (w->J) CUDA_TRY(cudaMemcpyAsync(w->W.gp_k, k, w->J, cudaMemcpyHostToDevice, w->stream));
+    CUDA_TRY(cudaStreamSynchronize(w->stream));
     return NPX_OK;
 }
 
@@ -1086,6 +1137,9 @@ int npx_state_export(npx_world *w, void *blob, size_t *size) {
     CUDA_TRY(cudaMemcpyAsync(p + b.sensors, w->W.sensors, sizeof(uint32_t) * S, cudaMemcpyDeviceToHost, w->stream));
     CUDA_TRY(cudaMemcpyAsync(p + b.status, w->W.status, sizeof(uint32_t) * S, cudaMemcpyDeviceToHost, w->stream));
     CUDA_TRY(cudaMemcpyAsync(p + b.kappa, w->W.kappa, w->P, cudaMemcpyDeviceToHost, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(p + b.gp_pc, w->W.gp_pc, S, cudaMemcpyDeviceToHost, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(p + b.gp_acc, w->W.gp_acc, S, cudaMemcpyDeviceToHost, w->stream));
+    if (w->J) CUDA_TRY(cudaMemcpyAsync(p + b.gp_k, w->W.gp_k, w->J, cudaMemcpyDeviceToHost, w->stream));
     CUDA_TRY(cudaStreamSynchronize(w->stream));
     *size = b.end;
     return NPX_OK;
@@ -1109,6 +1163,9 @@ int npx_state_import(npx_world *w, const void *blob, size_t size) {
     CUDA_TRY(cudaMemcpyAsync(w->W.sensors, p + b.sensors, sizeof(uint32_t) * S, cudaMemcpyHostToDevice, w->stream));
     CUDA_TRY(cudaMemcpyAsync(w->W.status, p + b.status, sizeof(uint32_t) * S, cudaMemcpyHostToDevice, w->stream));
     CUDA_TRY(cudaMemcpyAsync(w->W.kappa, p + b.kappa, w->P, cudaMemcpyHostToDevice, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(w->W.gp_pc, p + b.gp_pc, S, cudaMemcpyHostToDevice, w->stream));
+    CUDA_TRY(cudaMemcpyAsync(w->W.gp_acc, p + b.gp_acc, S, cudaMemcpyHostToDevice, w->stream));
+    if (w->J) CUDA_TRY(cudaMemcpyAsync(w->W.gp_k, p + b.gp_k, w->J, cudaMemcpyHostToDevice, w->stream));
     const long long st = (long long)hdr[4];
     CUDA_TRY(cudaMemcpyAsync(w->d_step, &st, sizeof st, cudaMemcpyHostToDevice, w->stream));
     CUDA_TRY(cudaStreamSynchronize(w->stream));

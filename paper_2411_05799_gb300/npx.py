@@ -21,6 +21,7 @@ NPX_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ESTATE", -4: "ECUDA", -5: "ETIMEOUT", -6: "ERANGE"}
 ACT_HOLD = 0
 ACT_SINUSOID = 1
+ACT_GP = 2            # targets from each scene's machine-code program (World.set_gp_programs)
 FRIC_WEIGHTED = 1     # friction rows weighted by the normal forces (npx_world_set_friction_model)
 FRIC_TILT = 2         # the friction impulse also turns the body about the horizontal axes
 
@@ -146,6 +147,9 @@ _SIGS = {
     "npx_gemm_bf16": [P, P, I, I, I, I, P, P, P],
     "npx_gemm_wait_selftest": [I, P, P, P],
     "npx_world_set_friction_model": [P, I],
+    "npx_gp_programs_set": [P, P],
+    "npx_gp_state_read": [P, P, P, P],
+    "npx_gp_state_write": [P, P, P, P],
     "npx_mlp_create": [P, P],
     "npx_mlp_destroy": [P],
     "npx_mlp_params_set": [P, P, C.c_size_t],
@@ -230,6 +234,7 @@ class World:
                       device=device)
         _check(lib.npx_world_create(C.byref(d), C.byref(self._h)))
         self.n_scenes = n_scenes
+        self.dt = float(np.float32(dt))
         self._info = None
 
     @classmethod
@@ -330,6 +335,29 @@ class World:
             out = np.zeros(self._info["n_points"], np.uint8)
         _check(_lib.npx_contacts_read(self._h, _p(out), out.size))
         return out
+
+    def set_gp_programs(self, programs):
+        """One 32-byte machine-code program per scene (uint8 [S, 32]); resets the controllers."""
+        p = np.ascontiguousarray(programs, np.uint8)
+        if p.shape != (self.n_scenes, 32):
+            raise ValueError(f"programs must be uint8 [{self.n_scenes}, 32]")
+        _check(_lib.npx_gp_programs_set(self._h, p.ctypes.data))
+
+    def gp_state(self) -> dict:
+        """Controller state: program counters and accumulators [S], joint targets in 5-degree
+        steps [J]."""
+        info = self.info()
+        pc = np.zeros(self.n_scenes, np.uint8)
+        acc = np.zeros(self.n_scenes, np.uint8)
+        k = np.zeros(max(info["n_joints"], 1), np.int8)
+        _check(_lib.npx_gp_state_read(self._h, pc.ctypes.data, acc.ctypes.data, k.ctypes.data))
+        return {"pc": pc, "acc": acc, "k": k[:info["n_joints"]]}
+
+    def write_gp_state(self, pc, acc, k):
+        pc = np.ascontiguousarray(pc, np.uint8)
+        acc = np.ascontiguousarray(acc, np.uint8)
+        k = np.ascontiguousarray(k, np.int8)
+        _check(_lib.npx_gp_state_write(self._h, pc.ctypes.data, acc.ctypes.data, k.ctypes.data))
 
     def set_friction_model(self, flags: int):
         """FRIC_WEIGHTED | FRIC_TILT (0: Eqs. 1-6 as written)."""
