@@ -187,6 +187,38 @@ def other_workloads(World, scenes, stream, device) -> dict:
     return out
 
 
+def simplify_leg(World, stream, device) -> dict:
+    """simplifyMode (Sec. III-D): the hexapod built from a torso box and 18 cylinder segments,
+    4,096 copies with seeded sinusoid targets, in each simplify mode; scene-steps/s of 1,000-step
+    launches (2 s simulated after a warm-up second), points per scene beside it."""
+    import torch
+    from paper_2411_05799_gb300 import construct
+    out = {}
+    for mode in (0, 1, 2, 3):
+        rb = construct.cylinder_hexapod(mode)
+        z0 = -float(rb.batch(1).p0[:, 2].min()) + 0.01
+        rng = np.random.default_rng(50)
+        J = 18 * N_SCENES
+        act = np.stack([rng.uniform(0, 0.5, J), rng.uniform(0.5, 2.0, J), rng.uniform(0, 2 * np.pi, J),
+                        np.zeros(J)], 1)
+        b = rb.batch(N_SCENES, origin=(0.0, 0.0, z0), act_params=act)
+        w = World.from_batch(b, stream=stream.cuda_stream, device=device)
+        w.autotune(100)
+        w.configure(chunk_steps=CHUNK)
+        w.step(CHUNK)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        w.step(2 * CHUNK)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[f"mode_{mode}"] = {"value": N_SCENES * 2 * CHUNK / (ms / 1e3), "unit": UNIT,
+                               "points_per_scene": b.n_points // N_SCENES,
+                               "frozen_scenes": int((w.read()["status"] != 0).sum())}
+        w.close()
+    return out
+
+
 def gp_evolution_leg(scenes, stream, n_groups: int = 160, generations: int = 3) -> dict:
     """The paper's own workload (Sec. IV): machine-code controllers of the hexapod evolved by
     mutation, best 50 of 100 kept, two-minute evaluations; here n_groups populations side by side
@@ -459,6 +491,7 @@ def run_gpu(args):
                                           args.surrogate_stride)
     if not args.no_extra and rank == 0:
         line["gp_evolution"] = gp_evolution_leg(scenes, stream)
+        line["simplify_modes"] = simplify_leg(World, stream, local)
 
     if rank == 0:
         # algorithmic flops per scene-step from the oracle's event counts on a sample
