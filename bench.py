@@ -54,7 +54,7 @@ FLOPS_PER = {"points": 7, "contacts": 27, "friction_pts": 42, "tick_points": 115
 # DRAM bytes (read + write) of one 1,000-step step-kernel launch on this workload, by launch shape
 # (lanes per scene, warps per block, blocks), from ncu (profiles/step_kernel_hexapod4096x1000_dram.md);
 # reported only for a captured shape, and to be re-taken whenever the kernel changes
-STEP_TRAFFIC = {(8, 7, 147): 31876352}
+STEP_TRAFFIC = {(8, 7, 147): 31880448}
 
 
 def algorithmic_flops(counts: dict) -> float:
