@@ -150,6 +150,9 @@ typedef struct {
     double *wls;           /* [np] weights of the friction least-squares rows */
     double *Q, *T;         /* [nl*9], [nl*3] link frames (construction -> shape frame) */
     double Mtot, g[3], Ib[9], Ibinv[9];
+    /* carried from the first half of a step to the second */
+    double R[9], Iw_inv[9], om[3];
+    int tick;
 } scene_ws;
 
 static int ws_alloc(scene_ws *w, int np, int nl) {
@@ -394,12 +397,13 @@ static void rigid_map_2d(const double centre[2], double tx, double ty, double al
 
 /* ------------------------------------------------------------------ one step of one scene */
 
-static void scene_step(const npxo_model *M, npxo_state *st, int s, scene_ws *w, long long n,
-                       double *ls_s, double *ls_e, npxo_counts *cnt) {
-    double *c = st->c + 3 * s, *q = st->q + 4 * s, *v = st->v + 3 * s, *L = st->L + 3 * s;
-    const double dt = M->dt;
+/* First half of a step: step-start positions, the joint update, the positions after it and the
+ * angular velocity (everything robot-robot contact reads). */
+static void scene_pre(const npxo_model *M, npxo_state *st, int s, scene_ws *w, long long n,
+                      npxo_counts *cnt) {
+    double *c = st->c + 3 * s, *q = st->q + 4 * s, *L = st->L + 3 * s;
     const int np = w->np;
-    double R[9], Rt[9], Iw_inv[9], tmp[9];
+    double *R = w->R, *Iw_inv = w->Iw_inv, Rt[9], tmp[9];
 
     /* start-of-step world positions x = c + R r */
     quat_to_mat(q, R);
@@ -412,6 +416,7 @@ static void scene_step(const npxo_model *M, npxo_state *st, int s, scene_ws *w, 
     /* Sec. III-B: every K steps the joints jump to their clamped targets; the robot stays one
      * rigid body whose CoG, orientation and angular momentum are kept */
     int tick = (M->act_mode != NPXO_ACT_HOLD) && (n % M->K == 0);
+    w->tick = tick;
     if (tick) {
         int nj = w->nl - 1;
         /* the machine-code controller (Sec. IV): its instructions run, reading the foot contacts
@@ -443,8 +448,20 @@ static void scene_step(const npxo_model *M, npxo_state *st, int s, scene_ws *w, 
     mat_transpose(R, Rt);
     mat_mul(R, w->Ibinv, tmp);
     mat_mul(tmp, Rt, Iw_inv);
-    double om[3];
-    mat_vec(Iw_inv, L, om);
+    mat_vec(Iw_inv, L, w->om);
+}
+
+/* Second half: ground contact, integration with the external wrench fext (force, torque about the
+ * CoG; NULL = none), friction, commit. */
+static void scene_post(const npxo_model *M, npxo_state *st, int s, scene_ws *w, long long n,
+                       double *ls_s, double *ls_e, npxo_counts *cnt, const double *fext) {
+    double *c = st->c + 3 * s, *q = st->q + 4 * s, *v = st->v + 3 * s, *L = st->L + 3 * s;
+    const double dt = M->dt;
+    const int np = w->np;
+    const int tick = w->tick;
+    const double *Iw_inv = w->Iw_inv, *om = w->om;
+    double tmp[9];
+    (void)n;
 
     /* Sec. III-A: every mass point looks up the ground height under it; penalty normal force */
     const double kw2 = M->omega_c * M->omega_c, kc = 2.0 * M->zeta * M->omega_c;
@@ -473,6 +490,11 @@ static void scene_step(const npxo_model *M, npxo_state *st, int s, scene_ws *w, 
     for (int k = 0; k < 3; ++k) vs[k] = v[k] + dt * M->gravity[k];
     vs[2] += dt * FN / w->Mtot;
     for (int k = 0; k < 3; ++k) Ls[k] = L[k] + dt * tau[k];
+    if (fext)
+        for (int k = 0; k < 3; ++k) {
+            vs[k] += dt * fext[k] / w->Mtot;
+            Ls[k] += dt * fext[3 + k];
+        }
     mat_vec(Iw_inv, Ls, oms);
     for (int k = 0; k < 3; ++k) cs[k] = c[k] + dt * vs[k];
     for (int k = 0; k < 3; ++k) phi[k] = dt * oms[k];
@@ -592,11 +614,73 @@ static void scene_step(const npxo_model *M, npxo_state *st, int s, scene_ws *w, 
     cnt->scene_steps += 1;
 }
 
+static void scene_step(const npxo_model *M, npxo_state *st, int s, scene_ws *w, long long n,
+                       double *ls_s, double *ls_e, npxo_counts *cnt) {
+    scene_pre(M, st, s, w, n, cnt);
+    scene_post(M, st, s, w, n, ls_s, ls_e, cnt, NULL);
+}
+
+/* ------------------------------------------------------------------ robot-robot contact */
+
+/* Robot-robot collision, named as future work after the API section: here every mass point is a
+ * sphere of the given radius, and two points of different robots whose centres are closer than
+ * two radii push each other apart along the line through their centres with the penalty law of
+ * the ground contact (Sec. III-A's spring-damper, reading R4) written for the pair: stiffness
+ * mu omega_c^2 and damping 2 zeta mu omega_c with mu = m_a m_b / (m_a + m_b) the pair's reduced
+ * mass (so the pair's relative motion is a spring-damper of natural frequency omega_c), force
+ * max(0, mu (omega_c^2 (2 r - d) - 2 zeta omega_c v_n)) with v_n the rate of change of d.  No
+ * friction acts between robots.  Every pair is visited: no culling. */
+void npxo_arena_forces(int n_robots, const int *np, const double *const *x, const float *const *m,
+                       const double *c, const double *v, const double *om, const int *active,
+                       double radius, double omega_c, double zeta, double *fext) {
+    const double reach = 2.0 * radius, kw2 = omega_c * omega_c, kc = 2.0 * zeta * omega_c;
+    for (int i = 0; i < 6 * n_robots; ++i) fext[i] = 0.0;
+    for (int a = 0; a < n_robots; ++a) {
+        if (!active[a]) continue;
+        for (int b = 0; b < n_robots; ++b) {
+            if (b == a || !active[b]) continue;
+            for (int i = 0; i < np[a]; ++i) {
+                const double *xi = x[a] + 3 * i;
+                const double ri[3] = {xi[0] - c[3 * a], xi[1] - c[3 * a + 1], xi[2] - c[3 * a + 2]};
+                /* velocity of the point: v + omega x r */
+                const double *wa = om + 3 * a;
+                const double vi[3] = {v[3 * a] + wa[1] * ri[2] - wa[2] * ri[1],
+                                      v[3 * a + 1] + wa[2] * ri[0] - wa[0] * ri[2],
+                                      v[3 * a + 2] + wa[0] * ri[1] - wa[1] * ri[0]};
+                for (int j = 0; j < np[b]; ++j) {
+                    const double *xj = x[b] + 3 * j;
+                    const double d[3] = {xi[0] - xj[0], xi[1] - xj[1], xi[2] - xj[2]};
+                    const double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                    if (!(dist < reach) || dist == 0.0) continue;
+                    const double nrm[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
+                    const double rj[3] = {xj[0] - c[3 * b], xj[1] - c[3 * b + 1], xj[2] - c[3 * b + 2]};
+                    const double *wb = om + 3 * b;
+                    const double vj[3] = {v[3 * b] + wb[1] * rj[2] - wb[2] * rj[1],
+                                          v[3 * b + 1] + wb[2] * rj[0] - wb[0] * rj[2],
+                                          v[3 * b + 2] + wb[0] * rj[1] - wb[1] * rj[0]};
+                    const double vn = (vi[0] - vj[0]) * nrm[0] + (vi[1] - vj[1]) * nrm[1] + (vi[2] - vj[2]) * nrm[2];
+                    const double ma = m[a][i], mb = m[b][j], mr = ma * mb / (ma + mb);
+                    double f = mr * (kw2 * (reach - dist) - kc * vn);
+                    if (f < 0.0) f = 0.0;
+                    const double F[3] = {f * nrm[0], f * nrm[1], f * nrm[2]};
+                    double *o = fext + 6 * a;
+                    o[0] += F[0]; o[1] += F[1]; o[2] += F[2];
+                    o[3] += ri[1] * F[2] - ri[2] * F[1];
+                    o[4] += ri[2] * F[0] - ri[0] * F[2];
+                    o[5] += ri[0] * F[1] - ri[1] * F[0];
+                }
+            }
+        }
+    }
+}
+
 /* ------------------------------------------------------------------ public entry points */
 
 static int check_model(const npxo_model *M) {
     if (M->n_scenes < 0 || M->K < 1 || !(M->dt > 0.0)) return -1;
     if (M->act_mode == NPXO_ACT_GP && !M->gp_prog) return -1;
+    if (M->arena > 1 && (M->n_scenes % M->arena != 0 || !(M->arena_radius > 0.0) || !isfinite(M->arena_radius)))
+        return -1;
     for (int s = 0; s < M->n_scenes; ++s) {
         int l0 = M->link_off[s], nl = M->link_off[s + 1] - l0;
         int p0 = M->point_off[s], np = M->point_off[s + 1] - p0;
@@ -647,8 +731,57 @@ int npxo_init(const npxo_model *M, const float *origin, const float *quat, const
     return 0;
 }
 
+/* Arenas: the robots of an arena advance in lock step, each step in two halves around their
+ * contact forces, which all read the same step-start states.  A frozen robot takes no part. */
+static int step_arenas(const npxo_model *M, npxo_state *st, int s0, int s1, int n_steps, long long step0,
+                       npxo_counts *cnt) {
+    const int A = M->arena;
+    int npm, nlm;
+    if (max_scene_sizes(M, &npm, &nlm)) return -1;
+    if (s0 % A || s1 % A) return -1;
+    scene_ws *ws = calloc((size_t)A, sizeof *ws);
+    int *active = calloc((size_t)A, sizeof(int)), *np = calloc((size_t)A, sizeof(int));
+    const double **x = calloc((size_t)A, sizeof *x);
+    const float **m = calloc((size_t)A, sizeof *m);
+    double *om = calloc(3 * (size_t)A, sizeof(double)), *fext = calloc(6 * (size_t)A, sizeof(double));
+    double *ls_s = malloc(sizeof(double) * 2 * (size_t)npm);
+    double *ls_e = malloc(sizeof(double) * 2 * (size_t)npm);
+    int ok = ws && active && np && x && m && om && fext && ls_s && ls_e, nalloc = 0;
+    for (; ok && nalloc < A; ++nalloc) ok = ws_alloc(&ws[nalloc], npm, nlm);
+    if (ok) {
+        for (int a0 = s0; a0 < s1; a0 += A) {
+            for (int k = 0; k < A; ++k) {
+                ws_bind(M, a0 + k, &ws[k]);
+                shape_update(M, st, &ws[k]);
+            }
+            for (int t = 0; t < n_steps; ++t) {
+                int any = 0;
+                for (int k = 0; k < A; ++k) any |= (active[k] = st->status[a0 + k] == 0);
+                if (!any) break;
+                for (int k = 0; k < A; ++k) {
+                    if (!active[k]) continue;
+                    scene_pre(M, st, a0 + k, &ws[k], step0 + t, cnt);
+                    np[k] = ws[k].np;
+                    x[k] = ws[k].xp;
+                    m[k] = M->m + ws[k].p0;
+                    memcpy(om + 3 * k, ws[k].om, sizeof ws[k].om);
+                }
+                npxo_arena_forces(A, np, x, m, st->c + 3 * (size_t)a0, st->v + 3 * (size_t)a0, om, active,
+                                  M->arena_radius, M->omega_c, M->zeta, fext);
+                for (int k = 0; k < A; ++k)
+                    if (active[k]) scene_post(M, st, a0 + k, &ws[k], step0 + t, ls_s, ls_e, cnt, fext + 6 * k);
+            }
+        }
+    }
+    if (ws)
+        for (int k = 0; k < nalloc; ++k) ws_free(&ws[k]);
+    free(ws); free(active); free(np); free(x); free(m); free(om); free(fext); free(ls_s); free(ls_e);
+    return ok ? 0 : -2;
+}
+
 int npxo_step(const npxo_model *M, npxo_state *st, int s0, int s1, int n_steps, long long step0,
               npxo_counts *cnt) {
+    if (M->arena > 1) return step_arenas(M, st, s0, s1, n_steps, step0, cnt);
     int npm, nlm;
     if (max_scene_sizes(M, &npm, &nlm)) return -1;
     scene_ws w;
@@ -682,15 +815,17 @@ static void *npxo_worker(void *arg) {
 
 int npxo_step_mt(const npxo_model *M, npxo_state *st, int n_steps, long long step0, int n_threads,
                  npxo_counts *cnt) {
+    /* threads take whole arenas */
+    const int A = M->arena > 1 ? M->arena : 1, units = M->n_scenes / A;
     if (n_threads < 1) n_threads = 1;
-    if (n_threads > M->n_scenes) n_threads = M->n_scenes > 0 ? M->n_scenes : 1;
+    if (n_threads > units) n_threads = units > 0 ? units : 1;
     npxo_job *jobs = calloc((size_t)n_threads, sizeof *jobs);
     pthread_t *th = calloc((size_t)n_threads, sizeof *th);
     if (!jobs || !th) { free(jobs); free(th); return -2; }
     int rc = 0;
     for (int t = 0; t < n_threads; ++t) {
-        jobs[t] = (npxo_job){M, st, (int)((long long)M->n_scenes * t / n_threads),
-                             (int)((long long)M->n_scenes * (t + 1) / n_threads), n_steps, step0,
+        jobs[t] = (npxo_job){M, st, A * (int)((long long)units * t / n_threads),
+                             A * (int)((long long)units * (t + 1) / n_threads), n_steps, step0,
                              {0}, 0};
         if (pthread_create(&th[t], NULL, npxo_worker, &jobs[t])) { rc = -3; n_threads = t; break; }
     }

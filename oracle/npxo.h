@@ -29,6 +29,9 @@ typedef struct {
     int fric_mode;         /* bit 0: least-squares rows weighted by the normal forces; bit 1: the
                               friction impulse's torque about the horizontal axes (0 = Eqs. 1-6) */
     const unsigned char *gp_prog;  /* [S*32] machine-code programs (act_mode 2, Sec. IV, Table I) */
+    int arena;             /* robots per arena (consecutive scenes sharing one ground and colliding
+                              with one another; <= 1: every robot alone) */
+    double arena_radius;   /* radius of the sphere around every mass point for robot-robot contact */
 } npxo_model;
 
 typedef struct {
@@ -61,6 +64,13 @@ int  npxo_lut(const npxo_model *M, int scene, double x, double y, double *h);
 int  npxo_friction_ls(int n, const double *src_xy, const double *e_xy, double *t2, double *a3);
 int  npxo_friction_ls_w(int n, const double *src_xy, const double *e_xy, const double *w, double *t2,
                         double *a3);
+/* Robot-robot contact forces at the given world positions (the future-work extension): robots
+ * n_robots, robot k with np[k] points at x[k] ([np*3]), masses m[k], CoG c[k*3], velocity v[k*3],
+ * angular velocity om[k*3]; active[k] = 0 leaves a robot out.  Writes the force and the torque
+ * about the CoG on every robot to fext[k*6]. */
+void npxo_arena_forces(int n_robots, const int *np, const double *const *x, const float *const *m,
+                       const double *c, const double *v, const double *om, const int *active,
+                       double radius, double omega_c, double zeta, double *fext);
 /* The machine-code controller (Table I): n_instr instructions of prog from *pc, with accumulator
  * *acc, the scene's foot-contact bits `sensors` and the nj joint targets k (5-degree steps). */
 void npxo_gp_run(const unsigned char *prog, unsigned char *pc, unsigned char *acc, signed char *k,

@@ -46,6 +46,7 @@ class _Model(C.Structure):
         ("act_mode", C.c_int), ("act_params", C.c_void_p),
         ("fric_mode", C.c_int),
         ("gp_prog", C.c_void_p),
+        ("arena", C.c_int), ("arena_radius", C.c_double),
     ]
 
 
@@ -86,6 +87,9 @@ def lib():
         _lib.npxo_friction_ls_w.argtypes = [C.c_int, P, P, P, P, P]
         _lib.npxo_gp_run.argtypes = [P, P, P, P, C.c_int, C.c_uint, C.c_int]
         _lib.npxo_gp_run.restype = None
+        _lib.npxo_arena_forces.argtypes = [C.c_int, P, P, P, P, P, P, P, C.c_double, C.c_double,
+                                           C.c_double, P]
+        _lib.npxo_arena_forces.restype = None
     return _lib
 
 
@@ -129,6 +133,24 @@ def gp_run(prog, pc: int, acc: int, k, sensors: int, n_instr: int = GP_PER_UPDAT
     return int(pcs[0]), int(accs[0]), kk
 
 
+def arena_forces(x, m, c, v, om, active, radius: float, omega_c: float, zeta: float) -> np.ndarray:
+    """The oracle's robot-robot contact wrenches: x[k] ([n_k, 3] world points) and m[k] ([n_k]
+    masses) of robot k, with its CoG c[k], velocity v[k] and angular velocity om[k]; returns
+    [n_robots, 6] force and torque about each CoG."""
+    n = len(x)
+    xs = [np.ascontiguousarray(a, np.float64) for a in x]
+    ms = [np.ascontiguousarray(a, np.float32) for a in m]
+    npts = np.array([len(a) for a in xs], np.int32)
+    xp = (C.c_void_p * n)(*[a.ctypes.data for a in xs])
+    mp = (C.c_void_p * n)(*[a.ctypes.data for a in ms])
+    cc, vv, ww = (np.ascontiguousarray(a, np.float64).reshape(n, 3) for a in (c, v, om))
+    act = np.ascontiguousarray(active, np.int32)
+    out = np.zeros((n, 6))
+    lib().npxo_arena_forces(n, _ptr(npts), C.cast(xp, C.c_void_p), C.cast(mp, C.c_void_p), _ptr(cc), _ptr(vv),
+                            _ptr(ww), _ptr(act), radius, omega_c, zeta, _ptr(out))
+    return out
+
+
 # friction-model options (bits of fric_mode): least-squares rows weighted by the points' normal
 # forces; the friction impulse's torque about the horizontal axes.  0 = Eqs. 1-6 as written.
 FRIC_WEIGHTED, FRIC_TILT = 1, 2
@@ -137,10 +159,13 @@ FRIC_WEIGHTED, FRIC_TILT = 1, 2
 class Oracle:
     """FP64 state of every scene of a SceneBatch, advanced by the C oracle."""
 
-    def __init__(self, batch, threads: int = 1, fric_mode: int = 0, gp_programs=None):
+    def __init__(self, batch, threads: int = 1, fric_mode: int = 0, gp_programs=None, arena: int = 1,
+                 arena_radius: float = 0.0):
         self.batch = b = batch
         self.threads = threads
         self.fric_mode = int(fric_mode)
+        # robots per arena (consecutive scenes colliding with one another) and the point radius
+        self.arena, self.arena_radius = int(arena), float(arena_radius)
         S, P, J = b.n_scenes, b.n_points, b.n_joints
         self._keep = [np.ascontiguousarray(a) for a in
                       (b.link_off, b.point_off, b.p0, b.m, b.plink, b.parent, b.anchor, b.axis,
@@ -161,7 +186,8 @@ class Oracle:
             hm_nx=0 if maps is None else maps.shape[2], hm_ny=0 if maps is None else maps.shape[1],
             hm_scale=b.hm_scale, hm_origin=(C.c_double * 2)(*b.hm_origin),
             act_mode=ACT_GP if self.gp_prog is not None else b.act_mode, act_params=_ptr(act),
-            fric_mode=int(fric_mode), gp_prog=_ptr(self.gp_prog) if self.gp_prog is not None else None)
+            fric_mode=int(fric_mode), gp_prog=_ptr(self.gp_prog) if self.gp_prog is not None else None,
+            arena=self.arena, arena_radius=self.arena_radius)
         self.c = np.zeros((S, 3))
         self.q = np.zeros((S, 4))
         self.v = np.zeros((S, 3))

@@ -459,3 +459,44 @@ def block_batch(n_scenes=1, mu=0.5, extent=(0.2, 0.2, 0.1), counts=(3, 3, 2), ma
                      quat=np.tile([1.0, 0, 0, 0], (S, 1)), vel=np.tile(vel, (S, 1)),
                      omega=np.tile(omega, (S, 1)), act_params=None, name=name,
                      act_mode=ACT_HOLD)
+
+
+def concat(batches) -> SceneBatch:
+    """The scenes of several batches (same step, gravity, contact law, actuator mode; flat ground)
+    as one batch, in order."""
+    b0 = batches[0]
+    for b in batches[1:]:
+        if (b.dt, b.gravity, b.joint_update_steps, b.contact_omega, b.contact_zeta, b.act_mode) != \
+                (b0.dt, b0.gravity, b0.joint_update_steps, b0.contact_omega, b0.contact_zeta, b0.act_mode):
+            raise ValueError("batches differ in their world parameters")
+    if any(b.heightmaps is not None for b in batches):
+        raise ValueError("concat takes flat-ground batches")
+    offs = lambda key: np.concatenate([[0]] + [getattr(b, key)[1:] + sum(int(getattr(c, key)[-1])
+                                                                         for c in batches[:i])
+                                               for i, b in enumerate(batches)]).astype(np.int32)
+    cat = lambda key: np.ascontiguousarray(np.concatenate([getattr(b, key) for b in batches]))
+    return b0.with_(link_off=offs("link_off"), point_off=offs("point_off"),
+                    **{k: cat(k) for k in ("p0", "m", "plink", "parent", "anchor", "axis", "lo", "hi",
+                                           "sensor", "mu", "hmap", "origin", "quat", "vel", "omega",
+                                           "theta0", "act_params")},
+                    name="+".join(b.name for b in batches), meta={})
+
+
+# Arena layouts (robot-robot collision): hexapod k of an arena is placed at ARENA_XY[size][k].
+# Side by side along y, 0.44 m apart, the legs of the two rows overlap by 4 cm and are staggered
+# by 6 cm along x, so that swinging coxae drive legs into each other's; in the 2 x 2 layout the
+# torsos of a row are 4 cm apart.
+ARENA_XY = {2: ((0.0, -0.22), (0.06, 0.22)),
+            4: ((-0.17, -0.22), (0.17, -0.22), (-0.11, 0.22), (0.23, 0.22))}
+
+
+def arena_batch(n_arenas: int, size: int = 4, seed_key: int = 0) -> SceneBatch:
+    """n_arenas arenas of `size` hexapods (scenes a*size .. a*size + size - 1), each robot with its
+    own seeded sinusoid gaits, laid out by ARENA_XY (every arena at the same place: arenas do not
+    interact)."""
+    base = hexapod_batch(n_arenas * size, seed_key=seed_key)
+    xy = np.tile(np.asarray(ARENA_XY[size], np.float64), (n_arenas, 1))
+    origin = base.origin.astype(np.float64).copy()
+    origin[:, :2] = xy
+    return base.with_(origin=origin.astype(np.float32), name=f"hexapod_arenas_{n_arenas}x{size}",
+                      meta={"arena": size})

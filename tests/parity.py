@@ -17,7 +17,8 @@ def to_gpu(world, o: Oracle):
 
 
 def clone(o: Oracle) -> Oracle:
-    c = Oracle(o.batch, threads=o.threads, fric_mode=o.fric_mode, gp_programs=o.gp_prog)
+    c = Oracle(o.batch, threads=o.threads, fric_mode=o.fric_mode, gp_programs=o.gp_prog, arena=o.arena,
+               arena_radius=o.arena_radius)
     c.copy_state_from(o)
     return c
 
