@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 
 N_SCENES = 4096
 CHUNK = 1000
+ARENA_RADIUS = 0.01      # m, the sphere around every mass point for robot-robot contact
 WORKLOAD = "hexapod_18dof_4096_scenes_flat_dt1ms_K80"
 METRIC = "hexapod scene-steps/s on 1 GB300 (plain vs surrogate at stated error) + % roofline"
 UNIT = "scene-steps/s"
@@ -144,20 +145,27 @@ def other_workloads(World, scenes, stream, device) -> dict:
     """Scene-steps/s of 1,000-step launches on the uneven mixed batch (2 s simulated after a
     warm-up second), the evolution-scale rollout on rough terrain (the whole 60 s simulated from
     the initial state, after a warm-up second and a reset; its fitness is the horizontal distance
-    each robot's CoG moved) and the benchmark's hexapods with both friction refinements on (2 s),
-    state resident in HBM, CUDA events."""
+    each robot's CoG moved), the benchmark's hexapods with both friction refinements on (2 s) and
+    the same number of hexapods colliding in arenas of four (2 s; with the same robots stepped
+    alone beside it, and how far the collisions moved them), state resident in HBM, CUDA
+    events."""
     import torch
     out = {}
     from paper_2411_05799_gb300.npx import FRIC_TILT, FRIC_WEIGHTED
-    for name, make, secs, fric in (
-            ("uneven_mix_65536_scenes", lambda: scenes.uneven_batch(65536), 2, 0),
-            ("hexapod_rough_terrain_16384_scenes", lambda: scenes.cpg_batch(16384), 60, 0),
+    alone = {}
+    for name, make, secs, fric, arena in (
+            ("uneven_mix_65536_scenes", lambda: scenes.uneven_batch(65536), 2, 0, 1),
+            ("hexapod_rough_terrain_16384_scenes", lambda: scenes.cpg_batch(16384), 60, 0, 1),
             ("hexapod_4096_scenes_friction_weighted_tilt", lambda: scenes.hexapod_batch(N_SCENES), 2,
-             FRIC_WEIGHTED | FRIC_TILT)):
+             FRIC_WEIGHTED | FRIC_TILT, 1),
+            ("hexapod_arenas_1024x4_scenes_alone", lambda: scenes.arena_batch(N_SCENES // 4, 4), 2, 0, 1),
+            ("hexapod_arenas_1024x4_scenes", lambda: scenes.arena_batch(N_SCENES // 4, 4), 2, 0, 4)):
         b = make()
         w = World.from_batch(b, stream=stream.cuda_stream, device=device)
         if fric:
             w.set_friction_model(fric)
+        if arena > 1:
+            w.set_arenas(arena, ARENA_RADIUS)
         w.autotune(100)
         w.configure(chunk_steps=CHUNK)
         start = w.export_state()
@@ -177,6 +185,17 @@ def other_workloads(World, scenes, stream, device) -> dict:
                      "size_classes": info["size_classes"],
                      "warps_per_block": info["warps_per_block"],
                      "frozen_scenes": int((r["status"] != 0).sum())}
+        if name.endswith("_alone"):
+            alone = {"cog": r["cog"].copy(), "value": out[name]["value"]}
+            del out[name]
+        elif arena > 1:
+            d = np.linalg.norm(r["cog"][:, :2] - alone["cog"][:, :2], axis=1)
+            out[name].update({"arena": arena, "contact_radius_m": ARENA_RADIUS,
+                              "alone_value": alone["value"],
+                              "cog_shift_by_collisions_m": {"what": "horizontal distance between each robot's CoG "
+                                                                    "and its CoG stepped alone, after 2 s",
+                                                            "median": float(np.median(d)),
+                                                            "p90": float(np.percentile(d, 90))}})
         if secs == 60:
             d = np.linalg.norm(r["cog"][:, :2] - c0[:, :2], axis=1)
             out[name]["fitness_m"] = {"what": "horizontal distance of the robot CoG from its start after 60 s",

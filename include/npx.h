@@ -182,6 +182,20 @@ int npx_gp_state_write(npx_world *w, const uint8_t *pc, const uint8_t *acc, cons
  * also changes by the x and y components of r x J, J = M dv the dynamic correction's impulse and r
  * the contact centroid relative to the CoG.  Unknown bits: NPX_EINVAL. */
 int npx_world_set_friction_model(npx_world *w, int flags);
+/* Robot-robot collision (the extension the paper names as future work, after its API section).
+ * Scenes [a*size, (a+1)*size) form arena a: its robots share the ground and collide.  Every mass
+ * point is a sphere of `radius` metres; two points of different robots of an arena whose centres
+ * are closer than 2 radius push apart along the line through them with the ground contact's
+ * penalty law for the pair (stiffness m_r w_c^2 and damping 2 zeta m_r w_c of the world's w_c and
+ * zeta, m_r = m_a m_b / (m_a + m_b)); no friction acts between robots and the foot sensors report
+ * ground contact only.  The forces are taken at the step's start (after the joint update) and
+ * enter the integration with the ground forces; a frozen robot takes no part.
+ * size: 1 (off, the default), 2 or 4, dividing the scene count; each arena runs in one warp, so
+ * at most 32 / size lanes per scene (the call narrows the launch shape if needed; NPX_ERANGE when
+ * the largest scene holds more than 64 * 32 / size points).  The learned surrogate refuses
+ * worlds with arenas (NPX_EINVAL).  Errors: NPX_EINVAL for another size, a size that does not
+ * divide the scene count, or radius <= 0 or not finite. */
+int npx_world_set_arenas(npx_world *w, int size, float radius);
 /* Advance all scenes n >= 0 steps (asynchronous on the world's stream). */
 int npx_world_step(npx_world *w, int n);
 /* Wait for queued work; reports a latched error of an earlier asynchronous call. */

@@ -64,6 +64,13 @@ struct WorldDev {
     const uint8_t *gp_prog;
     uint8_t *gp_pc, *gp_acc;
     int8_t *gp_k;
+    // arenas: robots per arena (consecutive entries of the schedule, one warp; <= 1 = none) and
+    // the radius of the sphere around every mass point for robot-robot contact
+    int arena;
+    float rc;
+    const float4 *lbox;                   // [2 L] each link's construction-frame box: centre, half extent
+    const int *lpo;                       // [L + 1] each link's entries in lpt
+    const uint16_t *lpt;                  // [P] scene-local stored point indices, grouped by link
 };
 
 struct LaunchCfg {

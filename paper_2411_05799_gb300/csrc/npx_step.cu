@@ -197,6 +197,32 @@ __device__ __noinline__ float tile_bounds(const float4 *pts, int np, float4 *tb,
     return sqrtf(r2);   // the largest |r| of the scene's points (a bound for the cull margin)
 }
 
+// Body-frame box of a scene's posed points (the union of its tile boxes) as centre and half
+// extent, the same on every lane of the group; a scene without points gets an empty box at 0.
+template <int LPS>
+__device__ __forceinline__ void robot_box(const float4 *tb, int ntiles, int gl, float (&bc)[3], float (&bh)[3]) {
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int t = gl; t < ntiles; t += LPS) {
+        const float4 a = tb[2 * t], b = tb[2 * t + 1];
+        lo[0] = fminf(lo[0], a.x); lo[1] = fminf(lo[1], a.y); lo[2] = fminf(lo[2], a.z);
+        hi[0] = fmaxf(hi[0], b.x); hi[1] = fmaxf(hi[1], b.y); hi[2] = fmaxf(hi[2], b.z);
+    }
+#pragma unroll
+    for (int o = LPS / 2; o > 0; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            lo[i] = fminf(lo[i], __shfl_xor_sync(FULL_MASK, lo[i], o));
+            hi[i] = fmaxf(hi[i], __shfl_xor_sync(FULL_MASK, hi[i], o));
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const bool e = !(lo[i] <= hi[i]);
+        bc[i] = e ? 0.f : 0.5f * (lo[i] + hi[i]);
+        bh[i] = e ? 0.f : 0.5f * (hi[i] - lo[i]);
+    }
+}
+
 // Tiles that may hold a point at or below the highest ground hmax: every lane tests the boxes of
 // its tiles (t = gl, gl + LPS, ...) and ballots gather the group's answers into a mask.  The
 // contact mask holds at most 64 tiles, so there are at most 64 / LPS rounds: all box tests are
@@ -456,13 +482,237 @@ __device__ __noinline__ void gp_run(const WorldDev &W, int s, int j0, int nj, ui
     W.gp_acc[s] = (uint8_t)a;
 }
 
+// ------------------------------------------------------------------------ robot-robot contact
+
+// Arenas (robot-robot collision, the extension named as future work): the W.arena robots of an
+// arena are consecutive groups of one warp.  Every mass point is a sphere of radius W.rc; two
+// points of different robots closer than 2 rc push apart along the line through them with the
+// ground contact's penalty law written for the pair (stiffness m_r w_c^2, damping 2 zeta m_r w_c,
+// m_r the pair's reduced mass), no adhesion, no friction between robots.
+//
+// Broad phase by links.  At every shape update each robot turns its links' construction-frame
+// boxes (W.lbox) into body-frame boxes with the new link frames.  Each step, after the joint
+// update, it publishes in its exchange area (after all slots of the block) its CoG, rotation,
+// velocity, angular velocity, point and link ranges, the world box of all its points and the world
+// boxes of its links.  Then the whole warp takes the robot pairs (i < j) of its arenas one at a
+// time, so that its lanes follow one control flow: if the pair's world boxes come within 2 rc, the
+// lanes mark for each link of i the links of j whose boxes come within 2 rc of it (a 64-bit mask
+// in shared memory), then spread over i's points; a point of a marked link goes into j's body
+// frame once, is tested against each marked link's body-frame box and then against the link's
+// stored offsets (the per-link lists W.lpo / W.lpt).  Each pair force acts on both robots
+// (F on i, -F on j); the warp sums the pair's wrenches and adds them to the two robots' totals in
+// shared memory, pair after pair in a fixed order.  All culls are conservative (a margin covers
+// the rounding of the boxes), so the forces are those of all pairs within reach.
+constexpr float ARENA_MARGIN = 1e-4f;   // m, added to every cull distance
+enum { XC_C = 0, XC_R = 3, XC_V = 12, XC_W = 15, XC_BC = 18, XC_BH = 21, XC_ACTIVE = 24, XC_L0 = 25,
+       XC_NL = 26, XC_P0 = 27, XC_NP = 28, XC_RF = 32, XC_N = 48 };
+
+// Exchange area of a scene: XC_N floats of state and wrench totals | world link boxes [max_links]
+// (2 float4) | body link boxes [max_links] (2 float4) | near masks [max_links] (uint64)
+__host__ __device__ inline int xch_bytes(int max_links) { return (4 * XC_N + 72 * max_links + 15) & ~15; }
+
+// body-frame boxes of the scene's links from the current link frames (centre Q c + T - g, half
+// extent |Q| h; g the posed CoG in the shape frame)
+template <int LPS>
+__device__ __forceinline__ void link_boxes_body(const WorldDev &W, int l0, int nl, const float *fr, const float g[3],
+                                                float4 *LB, int gl) {
+    for (int l = gl; l < nl; l += LPS) {
+        const float4 cc = W.lbox[2 * (l0 + l)], hh = W.lbox[2 * (l0 + l) + 1];
+        const float *F = fr + 12 * l;
+        float4 cb, hb;
+        cb.x = F[0] * cc.x + F[1] * cc.y + F[2] * cc.z + F[9] - g[0];
+        cb.y = F[3] * cc.x + F[4] * cc.y + F[5] * cc.z + F[10] - g[1];
+        cb.z = F[6] * cc.x + F[7] * cc.y + F[8] * cc.z + F[11] - g[2];
+        hb.x = fabsf(F[0]) * hh.x + fabsf(F[1]) * hh.y + fabsf(F[2]) * hh.z;
+        hb.y = fabsf(F[3]) * hh.x + fabsf(F[4]) * hh.y + fabsf(F[5]) * hh.z;
+        hb.z = fabsf(F[6]) * hh.x + fabsf(F[7]) * hh.y + fabsf(F[8]) * hh.z;
+        cb.w = hb.w = 0.f;
+        LB[2 * l] = cb;
+        LB[2 * l + 1] = hb;
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ bool boxes_meet(float4 ca, float4 ha, float4 cb, float4 hb, float cull) {
+    return fabsf(ca.x - cb.x) <= ha.x + hb.x + cull && fabsf(ca.y - cb.y) <= ha.y + hb.y + cull &&
+           fabsf(ca.z - cb.z) <= ha.z + hb.z + cull;
+}
+
+template <int LPS>
+__device__ __forceinline__ void arena_wrench(const WorldDev &W, unsigned char *xch, int sbytes, const float4 *pts,
+                                             int l0, int nl, int p0, int np, const float c[3], const float R[9],
+                                             const float v[3], const float om[3], const float bbc[3],
+                                             const float bbh[3], bool active, int gl, float (&rf)[6]) {
+    constexpr int G = 32 / LPS;
+    const int lane = threadIdx.x & 31, g = lane / LPS, A = W.arena, XB = xch_bytes(W.max_links);
+    float *X = reinterpret_cast<float *>(xch);
+    float4 *LW = reinterpret_cast<float4 *>(xch + 4 * XC_N);
+    const float4 *LB = LW + 2 * W.max_links;
+    // world boxes: all points (the body box turned by R) and each link
+    float wc[3], wh[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        wc[i] = c[i] + (R[3 * i] * bbc[0] + R[3 * i + 1] * bbc[1] + R[3 * i + 2] * bbc[2]);
+        wh[i] = fabsf(R[3 * i]) * bbh[0] + fabsf(R[3 * i + 1]) * bbh[1] + fabsf(R[3 * i + 2]) * bbh[2];
+    }
+    for (int l = gl; l < nl; l += LPS) {
+        const float4 cb = LB[2 * l], hb = LB[2 * l + 1];
+        LW[2 * l] = make_float4(c[0] + (R[0] * cb.x + R[1] * cb.y + R[2] * cb.z),
+                                c[1] + (R[3] * cb.x + R[4] * cb.y + R[5] * cb.z),
+                                c[2] + (R[6] * cb.x + R[7] * cb.y + R[8] * cb.z), 0.f);
+        LW[2 * l + 1] = make_float4(fabsf(R[0]) * hb.x + fabsf(R[1]) * hb.y + fabsf(R[2]) * hb.z,
+                                    fabsf(R[3]) * hb.x + fabsf(R[4]) * hb.y + fabsf(R[5]) * hb.z,
+                                    fabsf(R[6]) * hb.x + fabsf(R[7]) * hb.y + fabsf(R[8]) * hb.z, 0.f);
+    }
+    if (gl == 0) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            X[XC_C + i] = c[i]; X[XC_V + i] = v[i]; X[XC_W + i] = om[i];
+            X[XC_BC + i] = wc[i]; X[XC_BH + i] = wh[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) X[XC_R + i] = R[i];
+        X[XC_ACTIVE] = active ? 1.f : 0.f;
+        X[XC_L0] = __int_as_float(l0);
+        X[XC_NL] = __int_as_float(nl);
+        X[XC_P0] = __int_as_float(p0);
+        X[XC_NP] = __int_as_float(np);
+    }
+    if (gl < 6) X[XC_RF + gl] = 0.f;
+    __syncwarp();
+    const float reach = 2.f * W.rc, reach2 = reach * reach, cull = reach + ARENA_MARGIN;
+    const float kw2 = W.kw2, kc = W.kc;
+    unsigned char *xw = xch - g * XB;                                     // the warp's first area
+    const unsigned char *pw = reinterpret_cast<const unsigned char *>(pts) - (ptrdiff_t)g * sbytes;  // first slot
+    const int per_arena = A * (A - 1) / 2;
+    for (int pr = 0; pr < (G / A) * per_arena; ++pr) {   // the same pairs, in the same order, on every lane
+        int i = 0, t = pr % per_arena;
+        while (t >= A - 1 - i) { t -= A - 1 - i; ++i; }
+        const int gi = (pr / per_arena) * A + i, gj = gi + 1 + t;
+        float *Xi = reinterpret_cast<float *>(xw + gi * XB);
+        float *Xj = reinterpret_cast<float *>(xw + gj * XB);
+        bool ov = Xi[XC_ACTIVE] != 0.f && Xj[XC_ACTIVE] != 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) ov = ov && fabsf(Xi[XC_BC + k] - Xj[XC_BC + k]) <= Xi[XC_BH + k] + Xj[XC_BH + k] + cull;
+        if (!ov) continue;   // read from shared memory: the same on every lane
+        const float4 *LWi = reinterpret_cast<const float4 *>(xw + gi * XB + 4 * XC_N);
+        const float4 *LWj = reinterpret_cast<const float4 *>(xw + gj * XB + 4 * XC_N);
+        const float4 *LBj = LWj + 2 * W.max_links;
+        uint64_t *NMi = reinterpret_cast<uint64_t *>(xw + gi * XB + 4 * XC_N + 64 * W.max_links);
+        const int nli = __float_as_int(Xi[XC_NL]), nlj = __float_as_int(Xj[XC_NL]);
+        const int p0i = __float_as_int(Xi[XC_P0]), npi = __float_as_int(Xi[XC_NP]);
+        const int l0j = __float_as_int(Xj[XC_L0]);
+        // links of j near each link of i (only links of i inside j's world box)
+        const float4 bcj = make_float4(Xj[XC_BC], Xj[XC_BC + 1], Xj[XC_BC + 2], 0.f);
+        const float4 bhj = make_float4(Xj[XC_BH], Xj[XC_BH + 1], Xj[XC_BH + 2], 0.f);
+        for (int l = lane; l < nli; l += 32) {
+            uint64_t nm = 0;
+            const float4 ca = LWi[2 * l], ha = LWi[2 * l + 1];
+            if (boxes_meet(ca, ha, bcj, bhj, cull))
+                for (int lb = 0; lb < nlj; ++lb)
+                    if (boxes_meet(ca, ha, LWj[2 * lb], LWj[2 * lb + 1], cull)) nm |= 1ull << lb;
+            NMi[l] = nm;
+        }
+        __syncwarp();
+        float ci[3], Ri[9], vi[3], wi[3], cj[3], Rj[9], vj[3], wj[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            ci[k] = Xi[XC_C + k]; vi[k] = Xi[XC_V + k]; wi[k] = Xi[XC_W + k];
+            cj[k] = Xj[XC_C + k]; vj[k] = Xj[XC_V + k]; wj[k] = Xj[XC_W + k];
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) { Ri[k] = Xi[XC_R + k]; Rj[k] = Xj[XC_R + k]; }
+        const float4 *pti = reinterpret_cast<const float4 *>(pw + (ptrdiff_t)gi * sbytes);
+        const float4 *ptj = reinterpret_cast<const float4 *>(pw + (ptrdiff_t)gj * sbytes);
+        float fi[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, fj[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int ia = lane; ia < npi; ia += 32) {
+            const uint64_t nm = NMi[W.plink[p0i + ia]];
+            if (!nm) continue;
+            const float4 pa = pti[ia];
+            float ra[3], e[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                ra[k] = Ri[3 * k] * pa.x + Ri[3 * k + 1] * pa.y + Ri[3 * k + 2] * pa.z;
+                e[k] = (ci[k] + ra[k]) - cj[k];
+            }
+            // the point in j's body frame, Rj^T (x_a - c_j): distances to j's points are then
+            // differences of stored offsets
+            const float ah0 = Rj[0] * e[0] + Rj[3] * e[1] + Rj[6] * e[2];
+            const float ah1 = Rj[1] * e[0] + Rj[4] * e[1] + Rj[7] * e[2];
+            const float ah2 = Rj[2] * e[0] + Rj[5] * e[1] + Rj[8] * e[2];
+            for (uint64_t bm = nm; bm; bm &= bm - 1) {
+                const int lb = __ffsll((long long)bm) - 1;
+                // skip the link unless the point is within reach of its body-frame box
+                const float4 cbh = LBj[2 * lb], hbh = LBj[2 * lb + 1];
+                if (fabsf(ah0 - cbh.x) > hbh.x + cull || fabsf(ah1 - cbh.y) > hbh.y + cull ||
+                    fabsf(ah2 - cbh.z) > hbh.z + cull)
+                    continue;
+                const int b1 = W.lpo[l0j + lb + 1];
+#pragma unroll 4
+                for (int ib = W.lpo[l0j + lb]; ib < b1; ++ib) {
+                    const float4 pb = ptj[__ldg(W.lpt + ib)];
+                    const float d0 = ah0 - pb.x, d1 = ah1 - pb.y, d2 = ah2 - pb.z;
+                    const float dd = d0 * d0 + d1 * d1 + d2 * d2;
+                    if (dd < reach2 && dd > 0.f) {
+                        const float dist = sqrtf(dd), inv = 1.f / dist;
+                        const float hn[3] = {d0 * inv, d1 * inv, d2 * inv};
+                        float n[3], rb[3];
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            n[k] = Rj[3 * k] * hn[0] + Rj[3 * k + 1] * hn[1] + Rj[3 * k + 2] * hn[2];
+                            rb[k] = Rj[3 * k] * pb.x + Rj[3 * k + 1] * pb.y + Rj[3 * k + 2] * pb.z;
+                        }
+                        const float va[3] = {vi[0] + (wi[1] * ra[2] - wi[2] * ra[1]),
+                                             vi[1] + (wi[2] * ra[0] - wi[0] * ra[2]),
+                                             vi[2] + (wi[0] * ra[1] - wi[1] * ra[0])};
+                        const float vb[3] = {vj[0] + (wj[1] * rb[2] - wj[2] * rb[1]),
+                                             vj[1] + (wj[2] * rb[0] - wj[0] * rb[2]),
+                                             vj[2] + (wj[0] * rb[1] - wj[1] * rb[0])};
+                        const float vn = (va[0] - vb[0]) * n[0] + (va[1] - vb[1]) * n[1] + (va[2] - vb[2]) * n[2];
+                        const float mr = pa.w * pb.w / (pa.w + pb.w);
+                        const float f = fmaxf(0.f, mr * (kw2 * (reach - dist) - kc * vn));
+                        const float F[3] = {f * n[0], f * n[1], f * n[2]};
+                        // F on i at its point, -F on j at its point
+                        fi[0] += F[0]; fi[1] += F[1]; fi[2] += F[2];
+                        fi[3] += ra[1] * F[2] - ra[2] * F[1];
+                        fi[4] += ra[2] * F[0] - ra[0] * F[2];
+                        fi[5] += ra[0] * F[1] - ra[1] * F[0];
+                        fj[0] -= F[0]; fj[1] -= F[1]; fj[2] -= F[2];
+                        fj[3] -= rb[1] * F[2] - rb[2] * F[1];
+                        fj[4] -= rb[2] * F[0] - rb[0] * F[2];
+                        fj[5] -= rb[0] * F[1] - rb[1] * F[0];
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                fi[k] += __shfl_xor_sync(FULL_MASK, fi[k], o);
+                fj[k] += __shfl_xor_sync(FULL_MASK, fj[k], o);
+            }
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) { Xi[XC_RF + k] += fi[k]; Xj[XC_RF + k] += fj[k]; }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) rf[k] = X[XC_RF + k];
+    __syncwarp();   // the exchange area is written again next step
+}
+
 // ------------------------------------------------------------------------ one scene, n steps
 
 // OPT: the friction-model options (W.fric_mode) are compiled in; without them the step is the
-// least squares of Eqs. 1-6 as written, with no test of the options in the step loop
-template <int LPS, bool FLAT, bool OPT>
+// least squares of Eqs. 1-6 as written, with no test of the options in the step loop; ARENA:
+// robot-robot contact within arenas (below)
+template <int LPS, bool FLAT, bool OPT, bool ARENA>
 __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *fr, float *th,
-                          float *th_old, float4 *tb, int n_steps, long long step0) {
+                          float *th_old, float4 *tb, int n_steps, long long step0, unsigned char *xch,
+                          int sbytes) {
     const bool valid = s >= 0;
     int p0 = 0, np = 0, l0 = 0, nl = 1;
     if (valid) {
@@ -500,6 +750,13 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
     Shape sh;
     shape_update<LPS>(W, valid ? s : 0, p0, np, l0, nl, th, fr, pts, gl, sh);
     float rmax = tile_bounds<LPS>(pts, np, tb, gl);
+    // (arenas) body-frame box of the posed points
+    float bbc[3] = {0.f, 0.f, 0.f}, bbh[3] = {0.f, 0.f, 0.f};
+    float4 *lbb = reinterpret_cast<float4 *>(xch + 4 * XC_N) + 2 * W.max_links;   // body link boxes
+    if (ARENA) {
+        robot_box<LPS>(tb, (np + LPS - 1) / LPS, gl, bbc, bbh);
+        link_boxes_body<LPS>(W, l0, nl, fr, sh.g, lbb, gl);
+    }
     if (W.reseed) {
         // the previous-step contacts from a detection at the current state (same test as the
         // step's own: z below the ground at the point's cell)
@@ -576,12 +833,20 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             shape_update<LPS>(W, valid ? s : 0, p0, np, l0, nl, th, fr, pts, gl, sh);
             rmax = tile_bounds<LPS>(pts, np, tb, gl);
             shr = sh;
+            if (ARENA) {
+                robot_box<LPS>(tb, ntiles, gl, bbc, bbh);
+                link_boxes_body<LPS>(W, l0, nl, fr, shr.g, lbb, gl);
+            }
             iM = 1.0f / shr.M;
             slack = -1.f;   // the tiles moved: cull again
         }
 
         float om[3];
         world_sym(R, shr.Ii, L, om);
+
+        // -- (arenas) contact forces and their torques about the CoG from the other robots
+        float rf[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (ARENA) arena_wrench<LPS>(W, xch, sbytes, pts, l0, nl, p0, np, c, R, v, om, bbc, bbh, valid && status == 0u, gl, rf);
 
         // -- pass 1: collision against the ground and penalty normal forces over the candidate
         //    tiles.  For the points in contact in both steps (the friction set C, Sec. III-C) it
@@ -696,6 +961,10 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         Ls[0] = L[0] + dt * acc[1];
         Ls[1] = L[1] + dt * acc[2];
         Ls[2] = L[2];
+        if (ARENA) {
+            vs[0] += dt * (rf[0] * iM); vs[1] += dt * (rf[1] * iM); vs[2] += dt * (rf[2] * iM);
+            Ls[0] += dt * rf[3]; Ls[1] += dt * rf[4]; Ls[2] += dt * rf[5];
+        }
         world_sym(R, shr.Ii, Ls, oms);
         cs[0] = c[0] + dt * vs[0]; cs[1] = c[1] + dt * vs[1]; cs[2] = c[2] + dt * vs[2];
         // rotation increment dR = exp([u]x), u = dt w*: q* = dq (x) q and R* = dR R, so a point's
@@ -911,7 +1180,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
     __syncwarp();
 }
 
-template <int LPS, bool FLAT, bool OPT>
+template <int LPS, bool FLAT, bool OPT, bool ARENA>
 __device__ __forceinline__ void step_body(const WorldDev &W, int n_steps, int sbytes) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int G = 32 / LPS;
@@ -923,6 +1192,8 @@ __device__ __forceinline__ void step_body(const WorldDev &W, int n_steps, int sb
     float *th = fr + 12 * W.max_links;
     float *th_old = th + W.max_links;
     float4 *tb = reinterpret_cast<float4 *>(slot + tiles_offset(W.max_points, W.max_links));
+    // (arenas) the scene's exchange area, after all slots of the block
+    unsigned char *xch = smem + (size_t)(blockDim.x / 32) * G * sbytes + (size_t)(warp * G + g) * xch_bytes(W.max_links);
     const long long step0 = *W.step;
     const int n_sched = W.sched_count ? *W.sched_count : W.n_sched;
     const int n_items = (n_sched + G - 1) / G;
@@ -933,21 +1204,28 @@ __device__ __forceinline__ void step_body(const WorldDev &W, int n_steps, int sb
         if (item >= n_items) break;
         const int idx = item * G + g;
         const int s = idx < n_sched ? W.order[idx] : -1;
-        run_scene<LPS, FLAT, OPT>(W, s, gl, pts, fr, th, th_old, tb, n_steps, step0);
+        run_scene<LPS, FLAT, OPT, ARENA>(W, s, gl, pts, fr, th, th_old, tb, n_steps, step0, xch, sbytes);
     }
 }
 
 // Flat ground: up to 16 warps per block, 128 registers a thread.
 template <int LPS, bool OPT>
 __global__ void __launch_bounds__(512) step_kernel(const __grid_constant__ WorldDev W, int n_steps, int sbytes) {
-    step_body<LPS, true, OPT>(W, n_steps, sbytes);
+    step_body<LPS, true, OPT, false>(W, n_steps, sbytes);
 }
 
 // Height maps keep more state (the map window and its origin): 168 registers a thread, up to 12
 // warps per block; their larger slots leave no more warps resident at 16 lanes per scene anyway.
 template <int LPS, bool OPT>
 __global__ void __maxnreg__(168) step_kernel_hm(const __grid_constant__ WorldDev W, int n_steps, int sbytes) {
-    step_body<LPS, false, OPT>(W, n_steps, sbytes);
+    step_body<LPS, false, OPT, false>(W, n_steps, sbytes);
+}
+
+// Arenas (robots colliding with one another, 8 or 16 lanes per scene), with the friction options
+// compiled in: 168 registers a thread.
+template <int LPS, bool FLAT>
+__global__ void __maxnreg__(168) step_kernel_arena(const __grid_constant__ WorldDev W, int n_steps, int sbytes) {
+    step_body<LPS, FLAT, true, true>(W, n_steps, sbytes);
 }
 
 __global__ void advance_kernel(long long *step, int n) { *step += n; }
@@ -1575,7 +1853,7 @@ int step_slot_bytes(const WorldDev &W, int lps) {
 }
 
 size_t step_smem_bytes(const WorldDev &W, int lps, int wpb) {
-    return (size_t)wpb * (32 / lps) * step_slot_bytes(W, lps);
+    return (size_t)wpb * (32 / lps) * (step_slot_bytes(W, lps) + (W.arena > 1 ? xch_bytes(W.max_links) : 0));
 }
 
 template <int LPS, bool FLAT, bool OPT>
@@ -1591,9 +1869,15 @@ static void *pick_step_opt(int lps, bool flat) {
     }
 }
 
-// the kernel for a world: flat or height maps, friction options compiled in only when used
+// the kernel for a world: flat or height maps, friction options compiled in only when used,
+// arenas (8 or 16 lanes per scene) in their own build
 static void *pick_step(const WorldDev &W, int lps) {
     const bool flat = W.hm == nullptr;
+    if (W.arena > 1) {
+        if (lps == 8) return flat ? (void *)step_kernel_arena<8, true> : (void *)step_kernel_arena<8, false>;
+        if (lps == 16) return flat ? (void *)step_kernel_arena<16, true> : (void *)step_kernel_arena<16, false>;
+        return nullptr;
+    }
     return W.fric_mode ? pick_step_opt<true>(lps, flat) : pick_step_opt<false>(lps, flat);
 }
 

@@ -287,6 +287,10 @@ int check_flat(const Flat &f, int scene) {
 // the largest scene, and sizes the grid to what is resident and what is needed
 npx::LaunchCfg clamp_cfg_for(npx_world *w, const npx::WorldDev &W, int count, npx::LaunchCfg c, int *rc) {
     *rc = NPX_OK;
+    if (W.arena > 1 && c.lps * W.arena > 32) {
+        *rc = fail(NPX_ERANGE, "an arena of %d robots is one warp: at most %d lanes per scene", W.arena, 32 / W.arena);
+        return c;
+    }
     if (W.max_points > 64 * c.lps) {
         *rc = fail(NPX_ERANGE, "%d points per scene exceed 64 per lane at %d lanes per scene",
                    W.max_points, c.lps);
@@ -341,6 +345,7 @@ constexpr int kAuxStreams = 3;
 
 int build_classes(npx_world *w, bool split) {
     w->classes.clear();
+    if (w->W.arena > 1) split = false;   // an arena's robots run in one warp of one launch
     const int S = w->S;
     const std::vector<int> &order = w->order_host;
     auto pts = [&](int s) { return w->point_off[s + 1] - w->point_off[s]; };
@@ -1039,6 +1044,111 @@ int npx_world_set_friction_model(npx_world *w, int flags) {
     return NPX_OK;
 }
 
+namespace {
+// Per-link data of the robot-robot broad phase, built once from the stored points: each link's
+// construction-frame box (centre, half extent; a link without points gets a negative extent,
+// which meets nothing) and its points' scene-local stored indices, grouped by link.
+int arena_tables(npx_world *w) {
+    if (w->W.lbox) return NPX_OK;
+    const int P = w->P, L = w->L;
+    std::vector<float4> p0m(P), lbox(2 * (size_t)L);
+    std::vector<uint8_t> plink(P);
+    std::vector<int> lpo(L + 1, 0);
+    std::vector<uint16_t> lpt(P);
+    CUDA_TRY(cudaMemcpy(p0m.data(), w->W.p0m, sizeof(float4) * (size_t)P, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(plink.data(), w->W.plink, (size_t)P, cudaMemcpyDeviceToHost));
+    for (int s = 0; s < w->S; ++s) {
+        const int l0 = w->link_off[s], nl = w->link_off[s + 1] - l0, p0 = w->point_off[s];
+        const int np = w->point_off[s + 1] - p0;
+        std::vector<int> cnt(nl, 0);
+        std::vector<float> lo(3 * (size_t)nl, INFINITY), hi(3 * (size_t)nl, -INFINITY);
+        for (int i = 0; i < np; ++i) {
+            const int l = plink[p0 + i];
+            const float4 q = p0m[p0 + i];
+            const float x[3] = {q.x, q.y, q.z};
+            cnt[l] += 1;
+            for (int a = 0; a < 3; ++a) {
+                lo[3 * l + a] = std::min(lo[3 * l + a], x[a]);
+                hi[3 * l + a] = std::max(hi[3 * l + a], x[a]);
+            }
+        }
+        int at = p0;
+        std::vector<int> fill(nl);
+        for (int l = 0; l < nl; ++l) {
+            lpo[l0 + l] = at;
+            fill[l] = at;
+            at += cnt[l];
+            const bool e = cnt[l] == 0;
+            lbox[2 * (size_t)(l0 + l)] = e ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                           : make_float4(0.5f * (lo[3 * l] + hi[3 * l]), 0.5f * (lo[3 * l + 1] + hi[3 * l + 1]),
+                                                         0.5f * (lo[3 * l + 2] + hi[3 * l + 2]), 0.f);
+            lbox[2 * (size_t)(l0 + l) + 1] = e ? make_float4(-1e30f, -1e30f, -1e30f, 0.f)
+                                               : make_float4(0.5f * (hi[3 * l] - lo[3 * l]), 0.5f * (hi[3 * l + 1] - lo[3 * l + 1]),
+                                                             0.5f * (hi[3 * l + 2] - lo[3 * l + 2]), 0.f);
+        }
+        for (int i = 0; i < np; ++i) lpt[fill[plink[p0 + i]]++] = (uint16_t)i;
+    }
+    lpo[L] = P;
+    float4 *d_lbox;
+    int *d_lpo;
+    uint16_t *d_lpt;
+    int rc;
+    if ((rc = dev_alloc(w, &d_lbox, 2 * (size_t)L)) || (rc = dev_alloc(w, &d_lpo, (size_t)L + 1)) ||
+        (rc = dev_alloc(w, &d_lpt, (size_t)P)))
+        return rc;
+    CUDA_TRY(cudaMemcpy(d_lbox, lbox.data(), sizeof(float4) * lbox.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_lpo, lpo.data(), sizeof(int) * lpo.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_lpt, lpt.data(), sizeof(uint16_t) * lpt.size(), cudaMemcpyHostToDevice));
+    w->W.lbox = d_lbox;
+    w->W.lpo = d_lpo;
+    w->W.lpt = d_lpt;
+    return NPX_OK;
+}
+}  // namespace
+
+int npx_world_set_arenas(npx_world *w, int size, float radius) {
+    if (int rc = check_ready(w)) return rc;
+    const int S = w->S;
+    if (size != 1 && size != 2 && size != 4) return fail(NPX_EINVAL, "arena size must be 1, 2 or 4 (got %d)", size);
+    if (size > 1 && S % size) return fail(NPX_EINVAL, "%d scenes do not split into arenas of %d", S, size);
+    if (size > 1 && !(radius > 0.f && std::isfinite(radius))) return fail(NPX_EINVAL, "contact radius must be > 0");
+    if (size > 1 && w->max_points > 64 * (32 / size))
+        return fail(NPX_ERANGE, "%d points per scene exceed the %d an arena of %d holds", w->max_points,
+                    64 * (32 / size), size);
+    CUDA_TRY(cudaSetDevice(w->device));
+    CUDA_TRY(cudaStreamSynchronize(w->stream));   // launches in flight read the schedule
+    if (size > 1)
+        if (int rc = arena_tables(w)) return rc;
+    auto pts = [&](int s) { return w->point_off[s + 1] - w->point_off[s]; };
+    std::vector<int> order(S);
+    if (size > 1) {
+        // arenas whole and aligned (so that each is one warp), the one with the largest robot first
+        const int na = S / size;
+        std::vector<int> top(na, 0), ar(na);
+        for (int a = 0; a < na; ++a)
+            for (int k = 0; k < size; ++k) top[a] = std::max(top[a], pts(a * size + k));
+        std::iota(ar.begin(), ar.end(), 0);
+        std::stable_sort(ar.begin(), ar.end(), [&](int a, int b) { return top[a] > top[b]; });
+        for (int i = 0; i < na; ++i)
+            for (int k = 0; k < size; ++k) order[i * size + k] = ar[i] * size + k;
+    } else {
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pts(a) > pts(b); });
+    }
+    CUDA_TRY(cudaMemcpy(const_cast<int *>(w->W.order), order.data(), sizeof(int) * (size_t)S, cudaMemcpyHostToDevice));
+    w->order_host = order;
+    w->W.arena = size;
+    w->W.rc = size > 1 ? radius : 0.f;
+    clear_graphs(w);
+    npx::LaunchCfg c = w->cfg;
+    if (size > 1 && c.lps * size > 32) { c.lps = 32 / size; c.blocks = 0; }
+    int rc;
+    c = clamp_cfg(w, c, &rc);   // also raises the shared-memory limit of the kernel it selects
+    if (rc) return rc;
+    w->cfg = c;
+    return build_classes(w, size == 1);
+}
+
 int npx_world_step(npx_world *w, int n) {
     if (int rc = check_ready(w)) return rc;
     if (n < 0) return fail(NPX_EINVAL, "n must be >= 0");
@@ -1273,6 +1383,7 @@ static int plain_run(npx_world *w, int m, bool reseed) {
 int npx_surrogate_collect(npx_world *w, const npx_surrogate_norm *nrm, int stride, int n_windows, float *X,
                           float *T) {
     if (int rc = check_ready(w)) return rc;
+    if (w->W.arena > 1) return fail(NPX_EINVAL, "the surrogate models robots alone: not available with arenas");
     if (n_windows < 1 || !X || !T) return fail(NPX_EINVAL, "need n_windows >= 1 and X, T");
     if (int rc = check_stride(w, stride)) return rc;
     if (nrm && (!nrm->x_mu || !nrm->x_isd || !nrm->t_mu || !nrm->t_sd)) return fail(NPX_EINVAL, "incomplete norm");
@@ -1314,6 +1425,7 @@ int npx_surrogate_collect(npx_world *w, const npx_surrogate_norm *nrm, int strid
 int npx_world_step_surrogate(npx_world *w, npx_mlp *net, const npx_surrogate_norm *nrm, int stride, int n_steps,
                              long long *fallbacks) {
     if (int rc = check_ready(w)) return rc;
+    if (w->W.arena > 1) return fail(NPX_EINVAL, "the surrogate models robots alone: not available with arenas");
     if (!net || !nrm || !nrm->x_mu || !nrm->x_isd || !nrm->t_mu || !nrm->t_sd)
         return fail(NPX_EINVAL, "need a network and its standardisation");
     if (n_steps < 0) return fail(NPX_EINVAL, "n_steps must be >= 0");
@@ -1422,6 +1534,7 @@ int npx_world_autotune(npx_world *w, int n_steps, npx_world_info *out) {
         float best_ms = 1e30f;
         for (int lps : lps_list) {
             if (cls.max_points > 64 * lps) continue;
+            if (w->W.arena > 1 && lps * w->W.arena > 32) continue;
             // fixed block sizes plus the "balanced" ones that spread the class's scenes evenly
             // over all SMs with 1, 2 or 3 resident blocks per SM
             std::vector<int> wpb_list = {1, 2, 4, 8, 16};

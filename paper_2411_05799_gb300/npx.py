@@ -147,6 +147,7 @@ _SIGS = {
     "npx_gemm_bf16": [P, P, I, I, I, I, P, P, P],
     "npx_gemm_wait_selftest": [I, P, P, P],
     "npx_world_set_friction_model": [P, I],
+    "npx_world_set_arenas": [P, I, C.c_float],
     "npx_gp_programs_set": [P, P],
     "npx_gp_state_read": [P, P, P, P],
     "npx_gp_state_write": [P, P, P, P],
@@ -362,6 +363,11 @@ class World:
     def set_friction_model(self, flags: int):
         """FRIC_WEIGHTED | FRIC_TILT (0: Eqs. 1-6 as written)."""
         _check(_lib.npx_world_set_friction_model(self._h, int(flags)))
+
+    def set_arenas(self, size: int, radius: float = 0.01):
+        """Robot-robot collision within arenas of `size` consecutive scenes (1 = off, 2 or 4);
+        every mass point is a sphere of `radius` metres."""
+        _check(_lib.npx_world_set_arenas(self._h, int(size), float(radius)))
 
     def set_actuators(self, mode, params=None):
         p = None if params is None else _f32(params)

@@ -1,0 +1,162 @@
+"""Robot-robot collision (arenas) on the CUDA step against the FP64 oracle: per step from the
+oracle's state while legs of neighbouring hexapods collide, over 200-step windows, the elastic
+collision and the resting stack against their closed forms, robots apart against the plain
+kernel, and the call's argument checks."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2411_05799_gb300 import construct, scenes
+from paper_2411_05799_gb300.npx import NpxError, World
+from tests.parity import STEP_RTOL, clone, per_step_compare, quat_angle, to_gpu
+
+pytestmark = pytest.mark.gpu
+
+THREADS = 8
+RADIUS = 0.01
+# a pair this close to the reach 2 r decides its force (whose damping term jumps there) by
+# rounding: FP32 positions of points within a metre of the origin carry ~3e-8 m
+NEAR_PAIR = 1e-6
+
+
+def pairs_in_reach(o: Oracle, size: int, theta=None):
+    """Per arena: the point pairs of different robots closer than 2 r, and the smallest
+    |distance - 2 r| (how close a pair is to switching), at the oracle's state (with joint
+    angles theta if given)."""
+    if theta is not None:
+        o = clone(o)
+        o.theta[:] = theta
+    S = o.batch.n_scenes
+    x = [o.points_world(s) for s in range(S)]
+    n_in = np.zeros(S // size, np.int64)
+    gap = np.full(S // size, np.inf)
+    for a in range(S // size):
+        for i in range(size):
+            for j in range(i + 1, size):
+                d = np.linalg.norm(x[a * size + i][:, None, :] - x[a * size + j][None, :, :], axis=2)
+                n_in[a] += int((d < 2 * RADIUS).sum())
+                gap[a] = min(gap[a], float(np.abs(d - 2 * RADIUS).min()))
+    return n_in, gap
+
+
+def _arena_step_parity(w, o, size, checkpoints):
+    touched = 0
+    n_near = n_tot = 0
+    for n in checkpoints:
+        o.step(n - o.n, threads=THREADS)
+        err, near, o2, _ = per_step_compare(w, o, THREADS)
+        n_in, gap = pairs_in_reach(o, size, o2.theta)
+        _, gap2 = pairs_in_reach(o2, size)
+        near_pair = np.repeat((gap < NEAR_PAIR) | (gap2 < NEAR_PAIR), size)
+        touched += int(n_in.sum())
+        ok = ~(near | near_pair)
+        n_near += int((~ok).sum())
+        n_tot += len(ok)
+        for k in ("cog", "quat", "vel", "angmom", "theta"):
+            worst = err[k][ok].max(initial=0.0)
+            assert worst <= STEP_RTOL, f"step {n}: {k} rel err {worst:.3g}"
+        assert err["contacts"][ok].max(initial=0) == 0, f"step {n}: contact bits differ"
+    assert n_near <= 0.2 * n_tot, f"{n_near}/{n_tot} near-threshold exclusions"
+    return touched
+
+
+@pytest.mark.parametrize("size,lps", [(4, 8), (2, 8), (2, 16)])
+def test_arena_hexapods_per_step(size, lps):
+    b = scenes.arena_batch(32 // size, size, seed_key=11)
+    w = World.from_batch(b, configure=dict(lanes_per_scene=lps))
+    w.set_arenas(size, RADIUS)
+    assert w.info()["lanes_per_scene"] == lps
+    o = Oracle(b, threads=THREADS, arena=size, arena_radius=RADIUS)
+    touched = _arena_step_parity(w, o, size, [0, 1, 80, 81, 300, 480, 801, 1200, 1600])
+    assert touched > 100          # legs were in contact at the checkpoints
+
+
+@pytest.mark.parametrize("size", [2, 4])
+def test_arena_200_step_window(size):
+    """200 steps from the oracle's state after 0.6 s of walking into each other: CoG within 1e-3 m
+    and orientation within 1e-3 rad for 95% of the robots."""
+    b = scenes.arena_batch(64 // size, size, seed_key=12)
+    o = Oracle(b, threads=THREADS, arena=size, arena_radius=RADIUS)
+    o.step(600, threads=THREADS)
+    w = World.from_batch(b)
+    w.set_arenas(size, RADIUS)
+    to_gpu(w, o)
+    o.step(200, threads=THREADS)
+    w.step(200)
+    r = w.read()
+    dc = np.linalg.norm(r["cog"] - o.c, axis=1)
+    da = quat_angle(r["quat"], o.q)
+    ok = (dc <= 1e-3) & (da <= 1e-3)
+    assert ok.mean() >= 0.95, f"{(~ok).sum()} robots outside; median {np.median(dc):.3g} m {np.median(da):.3g} rad"
+    assert np.median(dc) < 1e-4 and np.median(da) < 1e-4, (np.median(dc), np.median(da))
+    assert (r["status"] == 0).all()
+
+
+def _point_robot(m, x, v, dt, zeta):
+    r = construct.Robot()
+    r.create_point(0.0, 0.0, 0.0, m)
+    return r.batch(1, origin=x, dt=dt).with_(vel=np.float32([v]), gravity=(0.0, 0.0, 0.0), contact_zeta=zeta)
+
+
+def test_elastic_collision_closed_form():
+    """Undamped points of 1 and 3 kg meeting at +-1 m/s in free space leave at -2 and 0 m/s, after
+    a contact of pi / w_c; the GPU agrees with the textbook result and with the oracle."""
+    dt = 1e-5
+    b = scenes.concat([_point_robot(1.0, (-0.05, 0.0, 1.0), (1.0, 0.0, 0.0), dt, 0.0),
+                       _point_robot(3.0, (0.05, 0.0, 1.0), (-1.0, 0.0, 0.0), dt, 0.0)])
+    w = World.from_batch(b)
+    w.set_arenas(2, RADIUS)
+    w.step(12000)
+    v = w.read()["vel"]
+    np.testing.assert_allclose(v[:, 0], [-2.0, 0.0], atol=5e-3)
+    o = Oracle(b, arena=2, arena_radius=RADIUS)
+    o.step(12000)
+    np.testing.assert_allclose(v, o.v, atol=1e-4)
+
+
+def test_box_resting_on_a_box():
+    """The top box's corners settle 2 r - M_top g / (4 m_r w_c^2) above the bottom box's."""
+    def box(m, z):
+        r = construct.Robot()
+        r.create_box(0.1, 0.1, 0.05, 0.0, 0.0, 0.0, m)
+        return r.batch(1, origin=(0.0, 0.0, z))
+    b = scenes.concat([box(2.0, 0.025), box(1.0, 0.095)])
+    w = World.from_batch(b)
+    w.set_arenas(2, RADIUS)
+    w.step(4000)
+    xb, xt = w.points(0), w.points(1)
+    gap = np.sort(xt[:, 2])[:4].mean() - np.sort(xb[:, 2])[-4:].mean()
+    m_r = (1.0 / 8) * (2.0 / 8) / (3.0 / 8)
+    assert gap == pytest.approx(2 * RADIUS - abs(b.gravity[2]) / (4 * m_r * 300.0 ** 2), rel=1e-4)
+
+
+def test_robots_apart_match_the_plain_kernel():
+    """Arenas whose robots stay 2 m apart step as the world without arenas (the arena kernel adds
+    exact zeros)."""
+    b = scenes.arena_batch(16, 2, seed_key=13)
+    b = b.with_(origin=b.origin + np.float32([[0, -1, 0], [0, 1, 0]] * 16))
+    a = World.from_batch(b, configure=dict(lanes_per_scene=8))
+    a.set_arenas(2, RADIUS)
+    p = World.from_batch(b, configure=dict(lanes_per_scene=8))
+    a.step(100)
+    p.step(100)
+    ra, rp = a.read(), p.read()
+    for k in ("cog", "vel", "angmom", "quat"):
+        np.testing.assert_allclose(ra[k], rp[k], rtol=1e-5, atol=1e-6)
+
+
+def test_arena_arguments():
+    b = scenes.arena_batch(3, 2, seed_key=14)          # 6 scenes
+    w = World.from_batch(b)
+    for size, radius in ((3, RADIUS), (4, RADIUS), (2, 0.0), (2, math.inf)):
+        with pytest.raises(NpxError):
+            w.set_arenas(size, radius)
+    w.set_arenas(2, RADIUS)
+    with pytest.raises(NpxError):
+        w.configure(lanes_per_scene=32)
+    w.step(10)
+    w.set_arenas(1)                                    # off again: every scene alone
+    w.step(10)
+    assert (w.read()["status"] == 0).all()
