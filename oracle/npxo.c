@@ -628,8 +628,9 @@ static void scene_step(const npxo_model *M, npxo_state *st, int s, scene_ws *w, 
  * the ground contact (Sec. III-A's spring-damper, reading R4) written for the pair: stiffness
  * mu omega_c^2 and damping 2 zeta mu omega_c with mu = m_a m_b / (m_a + m_b) the pair's reduced
  * mass (so the pair's relative motion is a spring-damper of natural frequency omega_c), force
- * max(0, mu (omega_c^2 (2 r - d) - 2 zeta omega_c v_n)) with v_n the rate of change of d.  No
- * friction acts between robots.  Every pair is visited: no culling. */
+ * max(0, mu (omega_c^2 (2 r - d) - 2 zeta omega_c v_n)) with v_n the rate of change of d (a
+ * force that is not a number counts as 0).  No friction acts between robots.  Every pair is
+ * visited: no culling. */
 void npxo_arena_forces(int n_robots, const int *np, const double *const *x, const float *const *m,
                        const double *c, const double *v, const double *om, const int *active,
                        double radius, double omega_c, double zeta, double *fext) {
@@ -660,8 +661,9 @@ void npxo_arena_forces(int n_robots, const int *np, const double *const *x, cons
                                           v[3 * b + 2] + wb[0] * rj[1] - wb[1] * rj[0]};
                     const double vn = (vi[0] - vj[0]) * nrm[0] + (vi[1] - vj[1]) * nrm[1] + (vi[2] - vj[2]) * nrm[2];
                     const double ma = m[a][i], mb = m[b][j], mr = ma * mb / (ma + mb);
-                    double f = mr * (kw2 * (reach - dist) - kc * vn);
-                    if (f < 0.0) f = 0.0;
+                    const double f = mr * (kw2 * (reach - dist) - kc * vn);
+                    if (!(f > 0.0)) continue;   /* no adhesion; a force that is not a number (a robot
+                                                   whose state went non-finite) exerts nothing */
                     const double F[3] = {f * nrm[0], f * nrm[1], f * nrm[2]};
                     double *o = fext + 6 * a;
                     o[0] += F[0]; o[1] += F[1]; o[2] += F[2];

@@ -1,5 +1,6 @@
 """Robot-robot collision (arenas) on the CUDA step against the FP64 oracle: per step from the
-oracle's state while legs of neighbouring hexapods collide, over 200-step windows, the elastic
+oracle's state while legs of neighbouring hexapods collide (flat ground and a shared rough height
+map), over 200-step windows, the elastic
 collision and the resting stack against their closed forms, robots apart against the plain
 kernel, and the call's argument checks."""
 import math
@@ -71,6 +72,29 @@ def test_arena_hexapods_per_step(size, lps):
     o = Oracle(b, threads=THREADS, arena=size, arena_radius=RADIUS)
     touched = _arena_step_parity(w, o, size, [0, 1, 80, 81, 300, 480, 801, 1200, 1600])
     assert touched > 100          # legs were in contact at the checkpoints
+
+
+def rough_arena_batch(n_arenas, size, seed_key):
+    """CPG hexapods on rough terrain in arenas: the members of an arena share the first member's
+    height map and stand at the arena layout's places, above its highest cell."""
+    b = scenes.cpg_batch(n_arenas * size, seed_key=seed_key)
+    S = b.n_scenes
+    hmap = (np.arange(S) // size * size).astype(np.int32)
+    origin = np.zeros((S, 3), np.float32)
+    origin[:, :2] = np.tile(np.asarray(scenes.ARENA_XY[size], np.float32), (n_arenas, 1))
+    origin[:, 2] = b.heightmaps[hmap].max(axis=(1, 2)) - scenes.FOOT_Z + 0.01
+    return b.with_(hmap=hmap, origin=origin)
+
+
+@pytest.mark.parametrize("size,lps", [(4, 8), (2, 16)])
+def test_arena_rough_terrain_per_step(size, lps):
+    """The height-map build of the arena kernel: robots sharing a rough height map collide."""
+    b = rough_arena_batch(32 // size, size, seed_key=15)
+    w = World.from_batch(b, configure=dict(lanes_per_scene=lps))
+    w.set_arenas(size, RADIUS)
+    o = Oracle(b, threads=THREADS, arena=size, arena_radius=RADIUS)
+    touched = _arena_step_parity(w, o, size, [0, 1, 80, 81, 300, 481, 800, 1201])
+    assert touched > 20
 
 
 @pytest.mark.parametrize("size", [2, 4])
@@ -145,6 +169,24 @@ def test_robots_apart_match_the_plain_kernel():
     ra, rp = a.read(), p.read()
     for k in ("cog", "vel", "angmom", "quat"):
         np.testing.assert_allclose(ra[k], rp[k], rtol=1e-5, atol=1e-6)
+
+
+def test_non_finite_neighbour_exerts_nothing():
+    """A robot written with a velocity that is not a number freezes in its first step; its
+    neighbour, legs in reach, feels nothing from it and follows the oracle."""
+    b = scenes.arena_batch(1, 2, seed_key=8)
+    o = Oracle(b, arena=2, arena_radius=RADIUS)
+    o.step(600)
+    o.v[1] = np.nan
+    w = World.from_batch(b)
+    w.set_arenas(2, RADIUS)
+    to_gpu(w, o)
+    o.step(100)
+    w.step(100)
+    r = w.read()
+    assert r["status"][1] != 0 and o.status[1] != 0 and r["status"][0] == 0
+    np.testing.assert_allclose(r["cog"][0], o.c[0], atol=1e-4)
+    np.testing.assert_allclose(r["vel"][0], o.v[0], atol=1e-3)
 
 
 def test_arena_arguments():

@@ -175,6 +175,26 @@ def test_robots_apart_or_frozen_do_not_interact():
     np.testing.assert_array_equal(o.q[0], alone.q[0])
 
 
+def test_non_finite_neighbour_exerts_nothing():
+    """A robot whose velocity is not a number freezes in its first step and its neighbour, in
+    reach, steps exactly as alone (its pair forces are not numbers and count as 0)."""
+    b = scenes.arena_batch(1, 2, seed_key=8)
+    o, alone = Oracle(b, arena=2, arena_radius=RADIUS), Oracle(b)
+    o.step(600)
+    alone.copy_state_from(o)
+    x = [o.points_world(0), o.points_world(1)]
+    m = [b.m[:b.point_off[1]], b.m[b.point_off[1]:]]
+    assert (np.linalg.norm(x[0][:, None] - x[1][None], axis=2) < 2 * RADIUS).sum() > 0   # legs in reach
+    assert np.abs(arena_forces(x, m, o.c, o.v, np.zeros((2, 3)), [1, 1], RADIUS, W_C, 1.0)[0]).max() > 0
+    o.v[1] = np.nan
+    assert (arena_forces(x, m, o.c, o.v, np.zeros((2, 3)), [1, 1], RADIUS, W_C, 1.0)[0] == 0).all()
+    o.step(300)
+    alone.status[1] = 1
+    alone.step(300)
+    assert o.status[1] != 0
+    np.testing.assert_array_equal(o.c[0], alone.c[0])
+
+
 def test_threads_take_whole_arenas():
     """Stepping arenas on several threads gives the single-thread result exactly; a scene count
     that is not a multiple of the arena size is refused."""
