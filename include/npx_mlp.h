@@ -118,7 +118,8 @@ int npx_surrogate_dims(npx_world *w, int *n_features, int *n_targets);
 /* Advance the world with the plain step until n_windows windows of `stride` steps (1 <= stride
  * < K on actuated worlds) have been recorded, writing each window's features X (at its first
  * step) and targets T (DEVICE, rows = window * n_scenes + scene, standardised when norm is
- * given).  Steps outside windows are stepped but not recorded. */
+ * given).  Steps outside windows are stepped but not recorded.  Worlds with arenas
+ * (npx_world_set_arenas) are refused with NPX_EINVAL: the features describe robots alone. */
 int npx_surrogate_collect(npx_world *w, const npx_surrogate_norm *norm, int stride, int n_windows,
                           float *X, float *T);
 /* Advance the world n_steps steps with the surrogate: at each window start the network predicts
@@ -127,7 +128,8 @@ int npx_surrogate_collect(npx_world *w, const npx_surrogate_norm *norm, int stri
  * (the fallback); steps outside windows, and a last window that does not fit in n_steps, are
  * plain for every scene.  *fallbacks (host, may be NULL) receives the number of scene-steps that
  * fell back.  The network must have been trained on windows of the same stride, take n_features
- * inputs, give n_targets outputs, and hold at least n_scenes rounded up to 128 rows. */
+ * inputs, give n_targets outputs, and hold at least n_scenes rounded up to 128 rows.  Worlds
+ * with arenas are refused (NPX_EINVAL). */
 int npx_world_step_surrogate(npx_world *w, npx_mlp *net, const npx_surrogate_norm *norm, int stride,
                              int n_steps, long long *fallbacks);
 

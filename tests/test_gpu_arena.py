@@ -10,7 +10,7 @@ import pytest
 
 from oracle.oracle import Oracle
 from paper_2411_05799_gb300 import construct, scenes
-from paper_2411_05799_gb300.npx import NpxError, World
+from paper_2411_05799_gb300.npx import NpxError, World, surrogate_collect
 from tests.parity import STEP_RTOL, clone, per_step_compare, quat_angle, to_gpu
 
 pytestmark = pytest.mark.gpu
@@ -198,6 +198,8 @@ def test_arena_arguments():
     w.set_arenas(2, RADIUS)
     with pytest.raises(NpxError):
         w.configure(lanes_per_scene=32)
+    with pytest.raises(NpxError, match="arenas"):      # the surrogate describes robots alone
+        surrogate_collect(w, 1, None, None)
     w.step(10)
     w.set_arenas(1)                                    # off again: every scene alone
     w.step(10)
