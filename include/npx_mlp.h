@@ -1,8 +1,8 @@
 /* npx_mlp.h -- tensor-core kernels of the learned surrogate (part of libnpx.so).
  *
  * The surrogate is a multilayer perceptron that predicts a scene's next state from its current
- * state, actuator targets and contact flags.  The paper has no counterpart (it is the batched
- * extension the task asks for beside the plain step).  Its building block is a BF16 GEMM on the
+ * state, actuator targets and contact flags.  The paper has no counterpart: it is a learned
+ * stand-in for the plain step over windows of steps.  Its building block is a BF16 GEMM on the
  * 5th-generation tensor cores with FP32 accumulation:
  *
  *     C[M x N] = A[M x K] . B[N x K]^T        (A, B row-major, K contiguous: "both K-major")

@@ -4,7 +4,7 @@ Per step (from the oracle's exact state): every component within 1e-5 relative, 
 and sensors exact, except scenes with a point within 1e-5 m of the ground, whose contact bits
 rounding decides (counted, and required to be rare).  Over 200-step windows: CoG within 1e-3 m
 and orientation within 1e-3 rad for at least 95% of scenes (contacts are chaotic, so the
-agreement is judged statistically).  The full-size hexapod workload is checked in the launch
+agreement is checked statistically).  The full-size hexapod workload is checked in the launch
 configuration the benchmark uses."""
 import math
 
