@@ -142,24 +142,32 @@ def cpu_oracle_sample(batch, n_scenes: int, n_steps: int, threads: int) -> dict:
 
 
 def other_workloads(World, scenes, stream, device) -> dict:
-    """Scene-steps/s of 1,000-step launches on the uneven mixed batch (2 s simulated after a
-    warm-up second), the evolution-scale rollout on rough terrain (the whole 60 s simulated from
-    the initial state, after a warm-up second and a reset; its fitness is the horizontal distance
-    each robot's CoG moved), the benchmark's hexapods with both friction refinements on (2 s) and
-    the same number of hexapods colliding in arenas of four (2 s; with the same robots stepped
-    alone beside it, and how far the collisions moved them), state resident in HBM, CUDA
-    events."""
+    """Scene-steps/s of 1,000-step launches, state resident in HBM, CUDA events, on:
+    - one single body for 10 s (the step's latency, us_per_step);
+    - the uneven mixed batch (2 s simulated after a warm-up second);
+    - the evolution-scale rollout on rough terrain (the whole 60 s from the initial state, after a
+      warm-up second and a reset; its fitness is the horizontal distance each robot's CoG moved);
+    - the benchmark's hexapods with a joint update at every step (K = 1, the worst case; 2 s);
+    - the benchmark's hexapods with both friction refinements on (2 s);
+    - the same number of hexapods colliding in arenas of four (2 s), with the same robots stepped
+      alone beside it and how far the collisions moved them.
+    Where given, the FP64 oracle is timed beside the line on a bounded sample of its workload."""
     import torch
     out = {}
     from paper_2411_05799_gb300.npx import FRIC_TILT, FRIC_WEIGHTED
     alone = {}
-    for name, make, secs, fric, arena in (
-            ("uneven_mix_65536_scenes", lambda: scenes.uneven_batch(65536), 2, 0, 1),
-            ("hexapod_rough_terrain_16384_scenes", lambda: scenes.cpg_batch(16384), 60, 0, 1),
+    threads = os.cpu_count() or 1
+    # (name, batch, seconds simulated, friction options, arena size, oracle sample (scenes, steps))
+    for name, make, secs, fric, arena, sample in (
+            ("single_body_1_scene", lambda: scenes.single_body(), 10, 0, 1, (1, 10 * CHUNK)),
+            ("uneven_mix_65536_scenes", lambda: scenes.uneven_batch(65536), 2, 0, 1, (64, CHUNK)),
+            ("hexapod_rough_terrain_16384_scenes", lambda: scenes.cpg_batch(16384), 60, 0, 1, (16, 60 * CHUNK)),
+            ("hexapod_4096_scenes_K1_joint_update_every_step", lambda: scenes.hexapod_batch(N_SCENES, K=1), 2,
+             0, 1, (64, CHUNK)),
             ("hexapod_4096_scenes_friction_weighted_tilt", lambda: scenes.hexapod_batch(N_SCENES), 2,
-             FRIC_WEIGHTED | FRIC_TILT, 1),
-            ("hexapod_arenas_1024x4_scenes_alone", lambda: scenes.arena_batch(N_SCENES // 4, 4), 2, 0, 1),
-            ("hexapod_arenas_1024x4_scenes", lambda: scenes.arena_batch(N_SCENES // 4, 4), 2, 0, 4)):
+             FRIC_WEIGHTED | FRIC_TILT, 1, None),
+            ("hexapod_arenas_1024x4_scenes_alone", lambda: scenes.arena_batch(N_SCENES // 4, 4), 2, 0, 1, None),
+            ("hexapod_arenas_1024x4_scenes", lambda: scenes.arena_batch(N_SCENES // 4, 4), 2, 0, 4, None)):
         b = make()
         w = World.from_batch(b, stream=stream.cuda_stream, device=device)
         if fric:
@@ -185,6 +193,15 @@ def other_workloads(World, scenes, stream, device) -> dict:
                      "size_classes": info["size_classes"],
                      "warps_per_block": info["warps_per_block"],
                      "frozen_scenes": int((r["status"] != 0).sum())}
+        if b.n_scenes == 1:
+            out[name]["us_per_step"] = ms * 1e3 / (secs * CHUNK)     # latency of one scene's step
+        if sample is not None:
+            n_sc, n_st = sample
+            th = min(threads, n_sc)
+            r_o = cpu_oracle_sample(b, n_sc, n_st, th)
+            out[name]["cpu_baseline"] = {"value": r_o["scene_steps_per_s"], "unit": UNIT, "cores": th,
+                                         "kind": "oracle",
+                                         "sample": f"{n_sc} scenes x {n_st} steps of this workload (FP64)"}
         if name.endswith("_alone"):
             alone = {"cog": r["cog"].copy(), "value": out[name]["value"]}
             del out[name]
