@@ -11,7 +11,7 @@ import pytest
 from oracle.oracle import Oracle
 from paper_2411_05799_gb300 import construct, scenes
 from paper_2411_05799_gb300.npx import NpxError, World, surrogate_collect
-from tests.parity import STEP_RTOL, clone, per_step_compare, quat_angle, to_gpu
+from tests.parity import STEP_RTOL, clone, near_threshold, per_step_compare, quat_angle, rel, to_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -187,6 +187,43 @@ def test_non_finite_neighbour_exerts_nothing():
     assert r["status"][1] != 0 and o.status[1] != 0 and r["status"][0] == 0
     np.testing.assert_allclose(r["cog"][0], o.c[0], atol=1e-4)
     np.testing.assert_allclose(r["vel"][0], o.v[0], atol=1e-3)
+
+
+def test_full_size_arenas_sampled():
+    """The benchmark's arena workload at full size (4,096 hexapods in arenas of four, autotuned
+    launch shape): after 0.6 s of walking into each other, one step from the GPU's own state
+    agrees per step with the oracle on sampled arenas (their state copied from the GPU)."""
+    size = 4
+    b = scenes.arena_batch(1024, size)
+    w = World.from_batch(b)
+    w.set_arenas(size, RADIUS)
+    w.autotune(100)
+    w.step(600)
+    r0 = w.read()
+    kap0 = w.contacts()
+    arenas = [0, 301, 702, 1023]
+    idx = np.concatenate([np.arange(a * size, (a + 1) * size) for a in arenas])
+    sub = b.subset(idx)
+    o = Oracle(sub, threads=THREADS, arena=size, arena_radius=RADIUS)
+    jo, po = b.joint_off, b.point_off
+    o.c[:] = r0["cog"][idx]
+    o.q[:] = r0["quat"][idx]
+    o.v[:] = r0["vel"][idx]
+    o.L[:] = r0["angmom"][idx]
+    o.theta[:] = np.concatenate([r0["theta"][jo[s]:jo[s + 1]] for s in idx])
+    o.kappa[:] = np.concatenate([kap0[po[s]:po[s + 1]] for s in idx])
+    o.n = r0["step"]
+    n_in, gap = pairs_in_reach(o, size)
+    o2 = clone(o)
+    o2.step(1, threads=THREADS)
+    _, gap2 = pairs_in_reach(o2, size)
+    w.step(1)
+    r = w.read()
+    near = near_threshold(o, o2, o2.theta) | np.repeat((gap < NEAR_PAIR) | (gap2 < NEAR_PAIR), size)
+    ok = ~near
+    assert ok.sum() >= len(idx) // 2 and n_in.sum() > 0
+    for k, ref in (("cog", o2.c), ("vel", o2.v), ("angmom", o2.L)):
+        assert rel(r[k][idx], ref).max(1)[ok].max(initial=0.0) <= STEP_RTOL, k
 
 
 def test_arena_arguments():
