@@ -167,7 +167,7 @@ def other_workloads(World, scenes, stream, device) -> dict:
             ("hexapod_4096_scenes_friction_weighted_tilt", lambda: scenes.hexapod_batch(N_SCENES), 2,
              FRIC_WEIGHTED | FRIC_TILT, 1, None),
             ("hexapod_arenas_1024x4_scenes_alone", lambda: scenes.arena_batch(N_SCENES // 4, 4), 2, 0, 1, None),
-            ("hexapod_arenas_1024x4_scenes", lambda: scenes.arena_batch(N_SCENES // 4, 4), 2, 0, 4, None)):
+            ("hexapod_arenas_1024x4_scenes", lambda: scenes.arena_batch(N_SCENES // 4, 4), 2, 0, 4, (64, 200))):
         b = make()
         w = World.from_batch(b, stream=stream.cuda_stream, device=device)
         if fric:
@@ -197,11 +197,20 @@ def other_workloads(World, scenes, stream, device) -> dict:
             out[name]["us_per_step"] = ms * 1e3 / (secs * CHUNK)     # latency of one scene's step
         if sample is not None:
             n_sc, n_st = sample
-            th = min(threads, n_sc)
-            r_o = cpu_oracle_sample(b, n_sc, n_st, th)
-            out[name]["cpu_baseline"] = {"value": r_o["scene_steps_per_s"], "unit": UNIT, "cores": th,
-                                         "kind": "oracle",
-                                         "sample": f"{n_sc} scenes x {n_st} steps of this workload (FP64)"}
+            th = min(threads, n_sc // arena)
+            if arena > 1:
+                # the colliding regime: 600 untimed steps first (the robots walk into each other)
+                from oracle.oracle import Oracle
+                o = Oracle(b.subset(np.arange(n_sc)), threads=th, arena=arena, arena_radius=ARENA_RADIUS)
+                o.step(600)
+                t0 = time.perf_counter()
+                o.step(n_st)
+                v_o = n_sc * n_st / (time.perf_counter() - t0)
+                what = f"{n_sc} scenes ({n_sc // arena} arenas) x {n_st} steps after 600 untimed steps (FP64)"
+            else:
+                v_o = cpu_oracle_sample(b, n_sc, n_st, th)["scene_steps_per_s"]
+                what = f"{n_sc} scenes x {n_st} steps of this workload (FP64)"
+            out[name]["cpu_baseline"] = {"value": v_o, "unit": UNIT, "cores": th, "kind": "oracle", "sample": what}
         if name.endswith("_alone"):
             alone = {"cog": r["cog"].copy(), "value": out[name]["value"]}
             del out[name]
