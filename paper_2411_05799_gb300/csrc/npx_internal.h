@@ -68,9 +68,14 @@ struct WorldDev {
     // the radius of the sphere around every mass point for robot-robot contact
     int arena;
     float rc;
-    const float4 *lbox;                   // [2 L] each link's construction-frame box: centre, half extent
-    const int *lpo;                       // [L + 1] each link's entries in lpt
-    const uint16_t *lpt;                  // [P] scene-local stored point indices, grouped by link
+    // robot-robot broad phase: chunks of at most 16 points of one link (at most 64 per scene)
+    const float4 *cbox;                   // [2 C] each chunk's construction-frame box: centre, half extent
+    const int *cpo;                       // [C + 1] each chunk's entries in lpt
+    const uint16_t *lpt;                  // [P] scene-local stored point indices, grouped by chunk
+    const uint8_t *clink;                 // [C] scene-local link of each chunk
+    const int *coff;                      // [S + 1] first chunk of each scene
+    const uint8_t *pchunk;                // [P] scene-local chunk of each stored point
+    int max_chunks;                       // chunks of the scene with the most
 };
 
 struct LaunchCfg {

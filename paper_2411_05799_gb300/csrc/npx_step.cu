@@ -490,35 +490,37 @@ __device__ __noinline__ void gp_run(const WorldDev &W, int s, int j0, int nj, ui
 // ground contact's penalty law written for the pair (stiffness m_r w_c^2, damping 2 zeta m_r w_c,
 // m_r the pair's reduced mass), no adhesion, no friction between robots.
 //
-// Broad phase by links.  At every shape update each robot turns its links' construction-frame
-// boxes (W.lbox) into body-frame boxes with the new link frames.  Each step, after the joint
-// update, it publishes in its exchange area (after all slots of the block) its CoG, rotation,
-// velocity, angular velocity, point and link ranges, the world box of all its points and the world
-// boxes of its links.  Then the whole warp takes the robot pairs (i < j) of its arenas one at a
-// time, so that its lanes follow one control flow: if the pair's world boxes come within 2 rc, the
-// lanes mark for each link of i the links of j whose boxes come within 2 rc of it (a 64-bit mask
-// in shared memory), then spread over i's points; a point of a marked link goes into j's body
-// frame once, is tested against each marked link's body-frame box and then against the link's
-// stored offsets (the per-link lists W.lpo / W.lpt).  Each pair force acts on both robots
-// (F on i, -F on j); the warp sums the pair's wrenches and adds them to the two robots' totals in
-// shared memory, pair after pair in a fixed order.  All culls are conservative (a margin covers
-// the rounding of the boxes), so the forces are those of all pairs within reach.
+// Broad phase by chunks: each link's points are cut along the link's longest axis into chunks of
+// at most 16 points (at most 64 per robot; W.cbox, W.clink, W.cpo / W.lpt, W.pchunk).  At every
+// shape update each robot turns its chunks' construction-frame boxes into body-frame boxes with
+// the new link frames.  Each step, after the joint update, it publishes in its exchange area
+// (after all slots of the block) its CoG, rotation, velocity, angular velocity, point and chunk
+// ranges, the world box of all its points and the world boxes of its chunks.  Then the whole warp
+// takes the robot pairs (i < j) of its arenas one at a time, so that its lanes follow one control
+// flow: if the pair's world boxes come within 2 rc, the lanes mark for each chunk of i the chunks
+// of j whose boxes come within 2 rc of it (a 64-bit mask in shared memory), then spread over i's
+// points; a point of a marked chunk goes into j's body frame once, is tested against each marked
+// chunk's body-frame box and then against that chunk's stored offsets.  Each pair force acts on
+// both robots (F on i, -F on j); the warp sums the pair's wrenches and adds them to the two
+// robots' totals in shared memory, pair after pair in a fixed order.  All culls are conservative
+// (a margin covers the rounding of the boxes), so the forces are those of all pairs within reach.
 constexpr float ARENA_MARGIN = 1e-4f;   // m, added to every cull distance
-enum { XC_C = 0, XC_R = 3, XC_V = 12, XC_W = 15, XC_BC = 18, XC_BH = 21, XC_ACTIVE = 24, XC_L0 = 25,
-       XC_NL = 26, XC_P0 = 27, XC_NP = 28, XC_RF = 32, XC_N = 48 };
+enum { XC_C = 0, XC_R = 3, XC_V = 12, XC_W = 15, XC_BC = 18, XC_BH = 21, XC_ACTIVE = 24, XC_C0 = 25,
+       XC_NC = 26, XC_P0 = 27, XC_NP = 28, XC_RF = 32, XC_N = 48 };
 
-// Exchange area of a scene: XC_N floats of state and wrench totals | world link boxes [max_links]
-// (2 float4) | body link boxes [max_links] (2 float4) | near masks [max_links] (uint64)
-__host__ __device__ inline int xch_bytes(int max_links) { return (4 * XC_N + 72 * max_links + 15) & ~15; }
+// Exchange area of a scene: XC_N floats of state and wrench totals | world chunk boxes
+// [max_chunks] (2 float4) | body chunk boxes [max_chunks] (2 float4) | near masks [max_chunks]
+// (uint64)
+__host__ __device__ inline int xch_bytes(int max_chunks) { return (4 * XC_N + 72 * max_chunks + 15) & ~15; }
 
-// body-frame boxes of the scene's links from the current link frames (centre Q c + T - g, half
-// extent |Q| h; g the posed CoG in the shape frame)
+// body-frame boxes of the scene's chunks from the current frames of their links (centre Q c + T - g,
+// half extent |Q| h; g the posed CoG in the shape frame)
 template <int LPS>
-__device__ __forceinline__ void link_boxes_body(const WorldDev &W, int l0, int nl, const float *fr, const float g[3],
-                                                float4 *LB, int gl) {
-    for (int l = gl; l < nl; l += LPS) {
-        const float4 cc = W.lbox[2 * (l0 + l)], hh = W.lbox[2 * (l0 + l) + 1];
-        const float *F = fr + 12 * l;
+__device__ __forceinline__ void chunk_boxes_body(const WorldDev &W, int c0, int nc, const float *fr, const float g[3],
+                                                 float4 *LB, int gl) {
+    for (int l = gl; l < nc; l += LPS) {
+        const float4 cc = W.cbox[2 * (c0 + l)], hh = W.cbox[2 * (c0 + l) + 1];
+        const float *F = fr + 12 * W.clink[c0 + l];
         float4 cb, hb;
         cb.x = F[0] * cc.x + F[1] * cc.y + F[2] * cc.z + F[9] - g[0];
         cb.y = F[3] * cc.x + F[4] * cc.y + F[5] * cc.z + F[10] - g[1];
@@ -540,14 +542,14 @@ __device__ __forceinline__ bool boxes_meet(float4 ca, float4 ha, float4 cb, floa
 
 template <int LPS>
 __device__ __forceinline__ void arena_wrench(const WorldDev &W, unsigned char *xch, int sbytes, const float4 *pts,
-                                             int l0, int nl, int p0, int np, const float c[3], const float R[9],
+                                             int c0, int nc, int p0, int np, const float c[3], const float R[9],
                                              const float v[3], const float om[3], const float bbc[3],
                                              const float bbh[3], bool active, int gl, float (&rf)[6]) {
     constexpr int G = 32 / LPS;
-    const int lane = threadIdx.x & 31, g = lane / LPS, A = W.arena, XB = xch_bytes(W.max_links);
+    const int lane = threadIdx.x & 31, g = lane / LPS, A = W.arena, XB = xch_bytes(W.max_chunks);
     float *X = reinterpret_cast<float *>(xch);
     float4 *LW = reinterpret_cast<float4 *>(xch + 4 * XC_N);
-    const float4 *LB = LW + 2 * W.max_links;
+    const float4 *LB = LW + 2 * W.max_chunks;
     // world boxes: all points (the body box turned by R) and each link
     float wc[3], wh[3];
 #pragma unroll
@@ -555,7 +557,7 @@ __device__ __forceinline__ void arena_wrench(const WorldDev &W, unsigned char *x
         wc[i] = c[i] + (R[3 * i] * bbc[0] + R[3 * i + 1] * bbc[1] + R[3 * i + 2] * bbc[2]);
         wh[i] = fabsf(R[3 * i]) * bbh[0] + fabsf(R[3 * i + 1]) * bbh[1] + fabsf(R[3 * i + 2]) * bbh[2];
     }
-    for (int l = gl; l < nl; l += LPS) {
+    for (int l = gl; l < nc; l += LPS) {
         const float4 cb = LB[2 * l], hb = LB[2 * l + 1];
         LW[2 * l] = make_float4(c[0] + (R[0] * cb.x + R[1] * cb.y + R[2] * cb.z),
                                 c[1] + (R[3] * cb.x + R[4] * cb.y + R[5] * cb.z),
@@ -573,8 +575,8 @@ __device__ __forceinline__ void arena_wrench(const WorldDev &W, unsigned char *x
 #pragma unroll
         for (int i = 0; i < 9; ++i) X[XC_R + i] = R[i];
         X[XC_ACTIVE] = active ? 1.f : 0.f;
-        X[XC_L0] = __int_as_float(l0);
-        X[XC_NL] = __int_as_float(nl);
+        X[XC_C0] = __int_as_float(c0);
+        X[XC_NC] = __int_as_float(nc);
         X[XC_P0] = __int_as_float(p0);
         X[XC_NP] = __int_as_float(np);
     }
@@ -597,12 +599,12 @@ __device__ __forceinline__ void arena_wrench(const WorldDev &W, unsigned char *x
         if (!ov) continue;   // read from shared memory: the same on every lane
         const float4 *LWi = reinterpret_cast<const float4 *>(xw + gi * XB + 4 * XC_N);
         const float4 *LWj = reinterpret_cast<const float4 *>(xw + gj * XB + 4 * XC_N);
-        const float4 *LBj = LWj + 2 * W.max_links;
-        uint64_t *NMi = reinterpret_cast<uint64_t *>(xw + gi * XB + 4 * XC_N + 64 * W.max_links);
-        const int nli = __float_as_int(Xi[XC_NL]), nlj = __float_as_int(Xj[XC_NL]);
+        const float4 *LBj = LWj + 2 * W.max_chunks;
+        uint64_t *NMi = reinterpret_cast<uint64_t *>(xw + gi * XB + 4 * XC_N + 64 * W.max_chunks);
+        const int nli = __float_as_int(Xi[XC_NC]), nlj = __float_as_int(Xj[XC_NC]);
         const int p0i = __float_as_int(Xi[XC_P0]), npi = __float_as_int(Xi[XC_NP]);
-        const int l0j = __float_as_int(Xj[XC_L0]);
-        // links of j near each link of i (only links of i inside j's world box)
+        const int l0j = __float_as_int(Xj[XC_C0]);
+        // chunks of j near each chunk of i (only chunks of i inside j's world box)
         const float4 bcj = make_float4(Xj[XC_BC], Xj[XC_BC + 1], Xj[XC_BC + 2], 0.f);
         const float4 bhj = make_float4(Xj[XC_BH], Xj[XC_BH + 1], Xj[XC_BH + 2], 0.f);
         for (int l = lane; l < nli; l += 32) {
@@ -626,7 +628,7 @@ __device__ __forceinline__ void arena_wrench(const WorldDev &W, unsigned char *x
         const float4 *ptj = reinterpret_cast<const float4 *>(pw + (ptrdiff_t)gj * sbytes);
         float fi[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, fj[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int ia = lane; ia < npi; ia += 32) {
-            const uint64_t nm = NMi[W.plink[p0i + ia]];
+            const uint64_t nm = NMi[W.pchunk[p0i + ia]];
             if (!nm) continue;
             const float4 pa = pti[ia];
             float ra[3], e[3];
@@ -642,14 +644,14 @@ __device__ __forceinline__ void arena_wrench(const WorldDev &W, unsigned char *x
             const float ah2 = Rj[2] * e[0] + Rj[5] * e[1] + Rj[8] * e[2];
             for (uint64_t bm = nm; bm; bm &= bm - 1) {
                 const int lb = __ffsll((long long)bm) - 1;
-                // skip the link unless the point is within reach of its body-frame box
+                // skip the chunk unless the point is within reach of its body-frame box
                 const float4 cbh = LBj[2 * lb], hbh = LBj[2 * lb + 1];
                 if (fabsf(ah0 - cbh.x) > hbh.x + cull || fabsf(ah1 - cbh.y) > hbh.y + cull ||
                     fabsf(ah2 - cbh.z) > hbh.z + cull)
                     continue;
-                const int b1 = W.lpo[l0j + lb + 1];
+                const int b1 = W.cpo[l0j + lb + 1];
 #pragma unroll 4
-                for (int ib = W.lpo[l0j + lb]; ib < b1; ++ib) {
+                for (int ib = W.cpo[l0j + lb]; ib < b1; ++ib) {
                     const float4 pb = ptj[__ldg(W.lpt + ib)];
                     const float d0 = ah0 - pb.x, d1 = ah1 - pb.y, d2 = ah2 - pb.z;
                     const float dd = d0 * d0 + d1 * d1 + d2 * d2;
@@ -752,10 +754,12 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
     float rmax = tile_bounds<LPS>(pts, np, tb, gl);
     // (arenas) body-frame box of the posed points
     float bbc[3] = {0.f, 0.f, 0.f}, bbh[3] = {0.f, 0.f, 0.f};
-    float4 *lbb = reinterpret_cast<float4 *>(xch + 4 * XC_N) + 2 * W.max_links;   // body link boxes
+    float4 *lbb = reinterpret_cast<float4 *>(xch + 4 * XC_N) + 2 * W.max_chunks;   // body chunk boxes
+    int c0 = 0, nc = 0;   // (arenas) the scene's broad-phase chunks
     if (ARENA) {
+        if (valid) { c0 = W.coff[s]; nc = W.coff[s + 1] - c0; }
         robot_box<LPS>(tb, (np + LPS - 1) / LPS, gl, bbc, bbh);
-        link_boxes_body<LPS>(W, l0, nl, fr, sh.g, lbb, gl);
+        chunk_boxes_body<LPS>(W, c0, nc, fr, sh.g, lbb, gl);
     }
     if (W.reseed) {
         // the previous-step contacts from a detection at the current state (same test as the
@@ -835,7 +839,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             shr = sh;
             if (ARENA) {
                 robot_box<LPS>(tb, ntiles, gl, bbc, bbh);
-                link_boxes_body<LPS>(W, l0, nl, fr, shr.g, lbb, gl);
+                chunk_boxes_body<LPS>(W, c0, nc, fr, shr.g, lbb, gl);
             }
             iM = 1.0f / shr.M;
             slack = -1.f;   // the tiles moved: cull again
@@ -846,7 +850,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
 
         // -- (arenas) contact forces and their torques about the CoG from the other robots
         float rf[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (ARENA) arena_wrench<LPS>(W, xch, sbytes, pts, l0, nl, p0, np, c, R, v, om, bbc, bbh, valid && status == 0u, gl, rf);
+        if (ARENA) arena_wrench<LPS>(W, xch, sbytes, pts, c0, nc, p0, np, c, R, v, om, bbc, bbh, valid && status == 0u, gl, rf);
 
         // -- pass 1: collision against the ground and penalty normal forces over the candidate
         //    tiles.  For the points in contact in both steps (the friction set C, Sec. III-C) it
@@ -1193,7 +1197,7 @@ __device__ __forceinline__ void step_body(const WorldDev &W, int n_steps, int sb
     float *th_old = th + W.max_links;
     float4 *tb = reinterpret_cast<float4 *>(slot + tiles_offset(W.max_points, W.max_links));
     // (arenas) the scene's exchange area, after all slots of the block
-    unsigned char *xch = smem + (size_t)(blockDim.x / 32) * G * sbytes + (size_t)(warp * G + g) * xch_bytes(W.max_links);
+    unsigned char *xch = smem + (size_t)(blockDim.x / 32) * G * sbytes + (size_t)(warp * G + g) * xch_bytes(W.max_chunks);
     const long long step0 = *W.step;
     const int n_sched = W.sched_count ? *W.sched_count : W.n_sched;
     const int n_items = (n_sched + G - 1) / G;
@@ -1853,7 +1857,7 @@ int step_slot_bytes(const WorldDev &W, int lps) {
 }
 
 size_t step_smem_bytes(const WorldDev &W, int lps, int wpb) {
-    return (size_t)wpb * (32 / lps) * (step_slot_bytes(W, lps) + (W.arena > 1 ? xch_bytes(W.max_links) : 0));
+    return (size_t)wpb * (32 / lps) * (step_slot_bytes(W, lps) + (W.arena > 1 ? xch_bytes(W.max_chunks) : 0));
 }
 
 template <int LPS, bool FLAT, bool OPT>

@@ -1045,63 +1045,95 @@ int npx_world_set_friction_model(npx_world *w, int flags) {
 }
 
 namespace {
-// Per-link data of the robot-robot broad phase, built once from the stored points: each link's
-// construction-frame box (centre, half extent; a link without points gets a negative extent,
-// which meets nothing) and its points' scene-local stored indices, grouped by link.
+// Chunks of the robot-robot broad phase, built once from the stored points: each link's points
+// sorted along the longest axis of their construction-frame box and cut into chunks of at most
+// `cap` points (16, doubled for a scene until it has at most 64 chunks).  Per chunk: its link,
+// its construction-frame box (centre, half extent) and its points' scene-local stored indices
+// (lpt, chunk-major); per scene its first chunk; per point its chunk.
 int arena_tables(npx_world *w) {
-    if (w->W.lbox) return NPX_OK;
-    const int P = w->P, L = w->L;
-    std::vector<float4> p0m(P), lbox(2 * (size_t)L);
-    std::vector<uint8_t> plink(P);
-    std::vector<int> lpo(L + 1, 0);
+    if (w->W.cbox) return NPX_OK;
+    const int P = w->P, S = w->S;
+    std::vector<float4> p0m(P);
+    std::vector<uint8_t> plink(P), pchunk(P), clink;
+    std::vector<float4> cbox;
+    std::vector<int> cpo, coff(S + 1, 0);
     std::vector<uint16_t> lpt(P);
     CUDA_TRY(cudaMemcpy(p0m.data(), w->W.p0m, sizeof(float4) * (size_t)P, cudaMemcpyDeviceToHost));
     CUDA_TRY(cudaMemcpy(plink.data(), w->W.plink, (size_t)P, cudaMemcpyDeviceToHost));
-    for (int s = 0; s < w->S; ++s) {
-        const int l0 = w->link_off[s], nl = w->link_off[s + 1] - l0, p0 = w->point_off[s];
+    int max_chunks = 1, at = 0;
+    for (int s = 0; s < S; ++s) {
+        const int nl = w->link_off[s + 1] - w->link_off[s], p0 = w->point_off[s];
         const int np = w->point_off[s + 1] - p0;
-        std::vector<int> cnt(nl, 0);
-        std::vector<float> lo(3 * (size_t)nl, INFINITY), hi(3 * (size_t)nl, -INFINITY);
-        for (int i = 0; i < np; ++i) {
-            const int l = plink[p0 + i];
-            const float4 q = p0m[p0 + i];
-            const float x[3] = {q.x, q.y, q.z};
-            cnt[l] += 1;
-            for (int a = 0; a < 3; ++a) {
-                lo[3 * l + a] = std::min(lo[3 * l + a], x[a]);
-                hi[3 * l + a] = std::max(hi[3 * l + a], x[a]);
+        std::vector<std::vector<int>> pts(nl);
+        for (int i = 0; i < np; ++i) pts[plink[p0 + i]].push_back(i);
+        int cap = 16, nc = 0;
+        for (;;) {
+            nc = 0;
+            for (int l = 0; l < nl; ++l) nc += ((int)pts[l].size() + cap - 1) / cap;
+            if (nc <= 64) break;
+            cap *= 2;
+        }
+        coff[s] = (int)clink.size();
+        max_chunks = std::max(max_chunks, nc);
+        for (int l = 0; l < nl; ++l) {
+            std::vector<int> &v = pts[l];
+            const int n = (int)v.size();
+            if (!n) continue;
+            float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+            for (int i : v) {
+                const float x[3] = {p0m[p0 + i].x, p0m[p0 + i].y, p0m[p0 + i].z};
+                for (int a = 0; a < 3; ++a) { lo[a] = std::min(lo[a], x[a]); hi[a] = std::max(hi[a], x[a]); }
+            }
+            int ax = 0;
+            for (int a = 1; a < 3; ++a)
+                if (hi[a] - lo[a] > hi[ax] - lo[ax]) ax = a;
+            auto coord = [&](int i) { const float4 q = p0m[p0 + i]; return ax == 0 ? q.x : ax == 1 ? q.y : q.z; };
+            std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return coord(a) < coord(b); });
+            const int k = (n + cap - 1) / cap;
+            for (int c = 0; c < k; ++c) {
+                // balanced cut: chunk c holds entries [n c / k, n (c + 1) / k)
+                const int b0 = (int)((long long)n * c / k), b1 = (int)((long long)n * (c + 1) / k);
+                float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+                const int local = (int)clink.size() - coff[s];
+                cpo.push_back(at);
+                for (int e = b0; e < b1; ++e) {
+                    const int i = v[e];
+                    const float x[3] = {p0m[p0 + i].x, p0m[p0 + i].y, p0m[p0 + i].z};
+                    for (int a = 0; a < 3; ++a) { clo[a] = std::min(clo[a], x[a]); chi[a] = std::max(chi[a], x[a]); }
+                    lpt[at++] = (uint16_t)i;
+                    pchunk[p0 + i] = (uint8_t)local;
+                }
+                clink.push_back((uint8_t)l);
+                cbox.push_back(make_float4(0.5f * (clo[0] + chi[0]), 0.5f * (clo[1] + chi[1]), 0.5f * (clo[2] + chi[2]), 0.f));
+                cbox.push_back(make_float4(0.5f * (chi[0] - clo[0]), 0.5f * (chi[1] - clo[1]), 0.5f * (chi[2] - clo[2]), 0.f));
             }
         }
-        int at = p0;
-        std::vector<int> fill(nl);
-        for (int l = 0; l < nl; ++l) {
-            lpo[l0 + l] = at;
-            fill[l] = at;
-            at += cnt[l];
-            const bool e = cnt[l] == 0;
-            lbox[2 * (size_t)(l0 + l)] = e ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                           : make_float4(0.5f * (lo[3 * l] + hi[3 * l]), 0.5f * (lo[3 * l + 1] + hi[3 * l + 1]),
-                                                         0.5f * (lo[3 * l + 2] + hi[3 * l + 2]), 0.f);
-            lbox[2 * (size_t)(l0 + l) + 1] = e ? make_float4(-1e30f, -1e30f, -1e30f, 0.f)
-                                               : make_float4(0.5f * (hi[3 * l] - lo[3 * l]), 0.5f * (hi[3 * l + 1] - lo[3 * l + 1]),
-                                                             0.5f * (hi[3 * l + 2] - lo[3 * l + 2]), 0.f);
-        }
-        for (int i = 0; i < np; ++i) lpt[fill[plink[p0 + i]]++] = (uint16_t)i;
     }
-    lpo[L] = P;
-    float4 *d_lbox;
-    int *d_lpo;
+    const int C = (int)clink.size();
+    coff[S] = C;
+    cpo.push_back(at);
+    float4 *d_cbox;
+    int *d_cpo, *d_coff;
     uint16_t *d_lpt;
+    uint8_t *d_clink, *d_pchunk;
     int rc;
-    if ((rc = dev_alloc(w, &d_lbox, 2 * (size_t)L)) || (rc = dev_alloc(w, &d_lpo, (size_t)L + 1)) ||
-        (rc = dev_alloc(w, &d_lpt, (size_t)P)))
+    if ((rc = dev_alloc(w, &d_cbox, 2 * (size_t)C)) || (rc = dev_alloc(w, &d_cpo, (size_t)C + 1)) ||
+        (rc = dev_alloc(w, &d_coff, (size_t)S + 1)) || (rc = dev_alloc(w, &d_lpt, (size_t)P)) ||
+        (rc = dev_alloc(w, &d_clink, (size_t)C)) || (rc = dev_alloc(w, &d_pchunk, (size_t)P)))
         return rc;
-    CUDA_TRY(cudaMemcpy(d_lbox, lbox.data(), sizeof(float4) * lbox.size(), cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(d_lpo, lpo.data(), sizeof(int) * lpo.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_cbox, cbox.data(), sizeof(float4) * cbox.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_cpo, cpo.data(), sizeof(int) * cpo.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_coff, coff.data(), sizeof(int) * coff.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(d_lpt, lpt.data(), sizeof(uint16_t) * lpt.size(), cudaMemcpyHostToDevice));
-    w->W.lbox = d_lbox;
-    w->W.lpo = d_lpo;
+    CUDA_TRY(cudaMemcpy(d_clink, clink.data(), clink.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_pchunk, pchunk.data(), pchunk.size(), cudaMemcpyHostToDevice));
+    w->W.cbox = d_cbox;
+    w->W.cpo = d_cpo;
+    w->W.coff = d_coff;
     w->W.lpt = d_lpt;
+    w->W.clink = d_clink;
+    w->W.pchunk = d_pchunk;
+    w->W.max_chunks = max_chunks;
     return NPX_OK;
 }
 }  // namespace
