@@ -234,10 +234,11 @@ int npx_world_use_graphs(npx_world *w, int on);
 
 /* --- stepping without any allocation ------------------------------------------------------ */
 /* The paper has no counterpart of this call; it serves callers that must not allocate device
- * memory while they run: code that records its work into a CUDA graph (cudaMalloc is not allowed
- * during stream capture), real-time loops that forbid allocation after start-up, frameworks that
- * hand out all device memory from their own pool.  They allocate the arrays below once, their own
- * way, and npx_step_noalloc steps them without allocating anything.  Its scratch memory (work-
+ * memory while they run: real-time control loops that forbid allocation after start-up
+ * (cudaMalloc and cudaFree can block on the device for an unbounded time), and frameworks that
+ * hand out all device memory from their own pool and account for every byte.  They allocate the
+ * arrays below once, their own way, and npx_step_noalloc steps them without allocating anything
+ * (no cudaMalloc, cudaFree or allocating library routine is called).  Its scratch memory (work-
  * queue counter, step counter, scene schedule) is a static device array of the library that every
  * GPU which loads the library keeps until the process exits; its size limits a call to
  * NPX_NOALLOC_MAX_SCENES scenes (larger worlds are rejected with NPX_ERANGE).  All calls share
@@ -256,10 +257,17 @@ int npx_world_use_graphs(npx_world *w, int on);
  *   state [13*S] structure of arrays (component k of scene s at k*S+s: CoG xyz, quaternion
  *   wxyz, velocity xyz, angular momentum xyz); theta [J]; contact [P] flags of the last step;
  *   omega [S*3 as 3 rows of S]; sensors, status [S].
- * step is the global step index of the first step (it fixes the joint-update phase); the caller
- * keeps the counter, the world is at step + n_steps afterwards.  The call is asynchronous on
- * stream (a cudaStream_t, NULL = legacy default stream); state, theta, contact, omega, sensors
- * and status are read and written in place. */
+ * max_points and max_links must be at least the point and link counts of the largest scene (they
+ * size the kernel's shared-memory slots; the call cannot check them without reading the device
+ * arrays), and every hmap entry must be -1 or the index of one of the maps in hm.
+ * step is the global step index of the first step (it fixes the joint-update phase and the
+ * sinusoid phase).  The call reads it from this struct on the host when it is made; the caller
+ * keeps the counter and advances it by n_steps between calls (the world is at step + n_steps
+ * afterwards).  act_mode is NPX_ACT_HOLD or NPX_ACT_SINUSOID: machine-code controllers
+ * (NPX_ACT_GP) need per-scene program state this struct does not carry and are refused with
+ * NPX_EINVAL, as are height maps with hm_nx or hm_ny < 1 or hm_scale <= 0.  The call is
+ * asynchronous on stream (a cudaStream_t, NULL = legacy default stream); state, theta, contact,
+ * omega, sensors and status are read and written in place. */
 #define NPX_NOALLOC_MAX_SCENES 65536
 typedef struct {
     int n_scenes, max_points, max_links;

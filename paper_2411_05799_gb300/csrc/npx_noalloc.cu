@@ -1,11 +1,11 @@
 // npx_noalloc.cu -- npx_step_noalloc: the scene-step kernel on caller-owned device buffers, with
 // its scratch memory in a fixed static device array instead of memory the library allocates.
 //
-// Who needs this: code that must not allocate device memory while it runs -- for example a host
-// loop that records its work into a CUDA graph (cudaMalloc is not allowed while a stream is being
-// captured), a real-time controller that forbids allocation after start-up, or a framework that
-// hands out all device memory from its own pool.  Such callers allocate their arrays once, their
-// own way, and pass them in; this entry point then adds no allocation of its own.
+// Who needs this: code that must not allocate device memory while it runs -- for example a
+// real-time controller that forbids allocation after start-up (cudaMalloc and cudaFree can block
+// on the device and take unbounded time), or a framework that hands out all device memory from
+// its own pool and counts every byte.  Such callers allocate their arrays once, their own way,
+// and pass them in; this entry point then adds no allocation of its own.
 //
 // The step kernel needs a little scratch besides its inputs and outputs: the counter of its
 // persistent work queue, the global step counter it reads, and the schedule of scenes for the
@@ -14,6 +14,7 @@
 // point accepts: NOALLOC_MAX_SCENES scenes.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdio>
 #include <string>
 
@@ -62,11 +63,21 @@ extern "C" int npx_step_noalloc(const npx_device_world *d, int n_steps, void *st
     if (d->max_points < 1 || d->max_points > 64 * lps || d->max_points > NPX_MAX_POINTS)
         return noalloc_fail(NPX_ERANGE, "npx_step_noalloc: max_points must be 1..64 * lanes_per_scene");
     if (d->max_links < 1 || d->max_links > NPX_MAX_LINKS) return noalloc_fail(NPX_ERANGE, "npx_step_noalloc: max_links out of range");
+    // the machine-code controller needs per-scene program state this call has no fields for
+    if (d->act_mode != NPX_ACT_HOLD && d->act_mode != NPX_ACT_SINUSOID)
+        return noalloc_fail(NPX_EINVAL, "npx_step_noalloc: act_mode must be NPX_ACT_HOLD or NPX_ACT_SINUSOID "
+                            "(the machine-code controller is not supported here)");
     if (!d->link_off || !d->point_off || !d->p0m || !d->plink || !d->links || !d->gref || !d->mu ||
         !d->hmap || !d->state || !d->theta || !d->contact || !d->omega || !d->sensors || !d->status ||
         (d->act_mode != NPX_ACT_HOLD && (!d->act || !d->act_nu)) ||
         (d->hm && !d->hm_max))
         return noalloc_fail(NPX_EINVAL, "npx_step_noalloc: null device array");
+    // a map lookup clamps its cell index to [0, n - 1]: empty maps or a non-positive scale would
+    // index outside the caller's array
+    if (d->hm && (d->hm_nx < 1 || d->hm_ny < 1 || !(d->hm_scale > 0.f) || !std::isfinite(d->hm_scale) ||
+                  !std::isfinite(d->hm_origin[0]) || !std::isfinite(d->hm_origin[1])))
+        return noalloc_fail(NPX_EINVAL, "npx_step_noalloc: height maps need hm_nx >= 1, hm_ny >= 1, a finite "
+                            "hm_scale > 0 and a finite origin");
     if (!(d->dt > 0.f) || d->joint_update_steps < 1 || d->step < 0)
         return noalloc_fail(NPX_EINVAL, "npx_step_noalloc: dt must be > 0, K >= 1, step >= 0");
     if (n_steps == 0) return NPX_OK;

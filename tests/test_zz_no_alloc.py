@@ -1,8 +1,10 @@
 """npx_step_noalloc: the entry point for callers that cannot allocate device memory while they run
-(code recording a CUDA graph, real-time loops, frameworks that own all device memory).  The
-caller lays out its own device arrays; the call must step them exactly like npx_world_step steps
-the same world, call after call, although its scratch lives in one static array shared by every
-call.  This file sorts last so that a stop-at-first-failure run has already run everything else."""
+(real-time control loops that forbid allocation after start-up, frameworks that hand out all
+device memory from their own pool).  The caller lays out its own device arrays; the call must step
+them exactly like npx_world_step steps the same world, call after call, although its scratch lives
+in one static array shared by every call.  Arguments it cannot serve are refused on the host,
+before anything is launched.  This file sorts last so that a stop-at-first-failure run has already
+run everything else."""
 import math
 
 import numpy as np
@@ -10,8 +12,6 @@ import pytest
 
 from paper_2411_05799_gb300 import npx, scenes
 from paper_2411_05799_gb300.npx import World
-
-pytestmark = pytest.mark.gpu
 
 LINK_DTYPE = np.dtype([("ax", "<f4"), ("ay", "<f4"), ("az", "<f4"), ("lo", "<f4"),
                        ("ux", "<f4"), ("uy", "<f4"), ("uz", "<f4"), ("hi", "<f4"),
@@ -61,27 +61,39 @@ def _rel(a, b):
     return np.abs(np.asarray(a, np.float64) - b) / np.maximum(np.abs(b), 1.0)
 
 
-def test_noalloc_steps_like_world_step_on_consecutive_calls():
+@pytest.mark.gpu
+@pytest.mark.parametrize("terrain", ["flat", "rough"])
+def test_noalloc_steps_like_world_step_on_consecutive_calls(terrain):
     torch = pytest.importorskip("torch")
-    b = scenes.hexapod_batch(96, seed_key=21)
+    if terrain == "flat":
+        b = scenes.hexapod_batch(96, seed_key=21)
+    else:   # per-scene 128 x 128 height maps: the height-map build of the step kernel
+        b = scenes.cpg_batch(24, seed_key=21)
     lps, wpb = 16, 4
     w = World.from_batch(b, configure=dict(lanes_per_scene=lps, warps_per_block=wpb))
     w.step(37)
     r = w.read()
     arr, perm = _layout(b, r, w.contacts())
+    if b.heightmaps is not None:
+        maps = np.ascontiguousarray(b.heightmaps, np.float32)
+        arr["hm"] = maps
+        arr["hm_max"] = maps.reshape(len(maps), -1).max(1)
     dev = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in arr.items()}
-    ptr = lambda k: dev[k].data_ptr()
+    ptr = lambda k: dev[k].data_ptr() if k in dev else None
     info = w.info()
+    hm_ny, hm_nx = (0, 0) if b.heightmaps is None else b.heightmaps.shape[1:]
     dw = npx.DeviceWorld(
         n_scenes=b.n_scenes, max_points=info["max_points"], max_links=info["max_links"],
         link_off=ptr("link_off"), point_off=ptr("point_off"), p0m=ptr("p0m"), plink=ptr("plink"),
-        links=ptr("links"), gref=ptr("gref"), mu=ptr("mu"), hmap=ptr("hmap"), hm=None, hm_max=None,
-        hm_nx=0, hm_ny=0, hm_scale=b.hm_scale, dt=b.dt, joint_update_steps=b.joint_update_steps,
+        links=ptr("links"), gref=ptr("gref"), mu=ptr("mu"), hmap=ptr("hmap"), hm=ptr("hm"),
+        hm_max=ptr("hm_max"), hm_nx=hm_nx, hm_ny=hm_ny, hm_scale=b.hm_scale, dt=b.dt,
+        joint_update_steps=b.joint_update_steps,
         contact_omega=b.contact_omega, contact_zeta=b.contact_zeta, act_mode=b.act_mode,
         act=ptr("act"), act_nu=ptr("act_nu"), state=ptr("state"), theta=ptr("theta"),
         contact=ptr("contact"), omega=ptr("omega"), sensors=ptr("sensors"),
         status=ptr("status"), step=r["step"], lanes_per_scene=lps, warps_per_block=wpb)
     dw.gravity[:] = b.gravity
+    dw.hm_origin[:] = b.hm_origin
     stream = torch.cuda.current_stream()
     for call in range(2):                       # two calls in a row share the static scratch
         npx.step_noalloc(dw, 150, stream.cuda_stream)
@@ -104,9 +116,43 @@ def test_noalloc_steps_like_world_step_on_consecutive_calls():
     assert ref["step"] == dw.step == 37 + 300
 
 
+def _host_world(**kw):
+    """A device-world description whose array fields hold dummy non-null addresses: every case
+    below is refused by the host-side checks, before any device memory is touched."""
+    fake = 0x1000
+    base = dict(n_scenes=8, max_points=8, max_links=1, lanes_per_scene=16, warps_per_block=4,
+                dt=1e-3, joint_update_steps=80, contact_omega=300.0, contact_zeta=1.0,
+                act_mode=npx.ACT_SINUSOID, hm_scale=20.0)
+    for k in ("link_off", "point_off", "p0m", "plink", "links", "gref", "mu", "hmap", "act",
+              "act_nu", "state", "theta", "contact", "omega", "sensors", "status"):
+        base[k] = fake
+    base.update(kw)
+    return npx.DeviceWorld(**base)
+
+
 def test_noalloc_rejects_worlds_beyond_its_scratch():
-    dw = npx.DeviceWorld(n_scenes=65537, max_points=8, max_links=1, lanes_per_scene=16,
-                         warps_per_block=4, dt=1e-3, joint_update_steps=80)
     with pytest.raises(npx.NpxError) as e:
-        npx.step_noalloc(dw, 10)
+        npx.step_noalloc(_host_world(n_scenes=65537), 10)
     assert e.value.code == -6 and "65536" in str(e.value)
+
+
+def test_noalloc_refuses_the_machine_code_controller():
+    """A world driven by machine-code programs needs per-scene program state that this entry
+    point has no fields for: it is refused before any launch."""
+    with pytest.raises(npx.NpxError) as e:
+        npx.step_noalloc(_host_world(act_mode=npx.ACT_GP), 10)
+    assert e.value.code == -1 and "act_mode" in str(e.value)
+    with pytest.raises(npx.NpxError):
+        npx.step_noalloc(_host_world(act_mode=7), 10)
+
+
+@pytest.mark.parametrize("bad", [dict(hm_nx=0, hm_ny=128), dict(hm_nx=128, hm_ny=0),
+                                 dict(hm_nx=128, hm_ny=128, hm_scale=0.0),
+                                 dict(hm_nx=128, hm_ny=128, hm_scale=-20.0),
+                                 dict(hm_nx=128, hm_ny=128, hm_scale=math.inf)])
+def test_noalloc_refuses_malformed_height_maps(bad):
+    """The map lookup clamps a cell index into [0, n - 1]; empty maps or a scale that is not
+    positive would read outside the caller's array, so such worlds are refused on the host."""
+    with pytest.raises(npx.NpxError) as e:
+        npx.step_noalloc(_host_world(hm=0x2000, hm_max=0x3000, **bad), 10)
+    assert e.value.code == -1 and "height map" in str(e.value)
