@@ -339,6 +339,60 @@ def test_incline_slips_with_coulomb_acceleration(theta_deg, mu):
     assert abs(acc - want) < 1e-3 * want
 
 
+def test_spinning_block_decelerates_at_the_rotational_coulomb_limit():
+    """Maximum static friction on a pure spin (Sec. III-C, reading R8).  A 3 x 3 x 2 lattice block
+    rests on the plane (normal force M g on its nine bottom points), then spins about the vertical
+    with no translation.  Each step the integration turns it by phi = dt w; the least squares of
+    Eqs. 4-6 recovers a3 = -sin(phi) about the contact centroid (t = 0), so the impulse that would
+    undo the slip is M u / dt with u = 2 sin(phi / 2) r_rms, r_rms^2 the mean squared horizontal
+    distance of the contact points from their centroid.  The cap mu M g dt scales the correction by
+    sc = mu g dt^2 / u, and the angular momentum changes by (sc alpha / dt) Iw z, so
+        w_(k+1) = w_k - mu g dt (phi / 2) / (sin(phi / 2) r_rms)
+    while the spin is fast enough to slip (w r_rms > mu g dt): a constant deceleration
+    mu g / r_rms up to a factor 1 + phi^2 / 24.  Once slow enough, one step stops it and it
+    sticks.  The yaw turned each step is dt w_(k+1).  A wrong factor in the rotational part of u
+    or in the angular-momentum update changes the rate."""
+    mu_in = 0.4
+    b = scenes.block_batch(extent=(0.2, 0.2, 0.1), counts=(3, 3, 2), mass=1.0, mu=mu_in)
+    o = Oracle(b)
+    o.step(1000)                                    # settle: the normal force is M g
+    mu, g, dt = float(np.float32(mu_in)), -b.gravity[2], b.dt
+    _, Ib, M = o.mass_props(0)
+    R = quat_matrix(o.q[0])
+    w0 = 3.0
+    o.L[0] = R @ Ib @ R.T @ np.array([0.0, 0.0, w0])
+    x = o.points_world(0)
+    bottom = x[np.argsort(x[:, 2])[:9], :2]
+    r_rms = math.sqrt(((bottom - bottom.mean(0)) ** 2).sum(1).mean())
+    assert r_rms == pytest.approx(0.1 * math.sqrt(4.0 / 3.0), rel=1e-6)
+
+    def yaw():
+        return Rotation.from_quat(np.roll(o.q[0], -1)).as_euler("xyz")[2]
+
+    w, yaw0, n_slip, turned = w0, yaw(), 0, 0.0
+    while w * r_rms > mu * g * dt:
+        phi = dt * w
+        want = w - mu * g * dt * (0.5 * phi) / (math.sin(0.5 * phi) * r_rms)
+        o.step(1)
+        got = o.omega()[0]
+        assert got[2] == pytest.approx(want, rel=1e-9, abs=1e-12), n_slip
+        np.testing.assert_allclose(got[:2], 0.0, atol=1e-12)
+        np.testing.assert_allclose(o.v[0], 0.0, atol=1e-12)      # no translation appears
+        turned += dt * got[2]
+        w, n_slip = got[2], n_slip + 1
+    # the closed form of a constant deceleration mu g / r_rms
+    t_stop = w0 * r_rms / (mu * g)
+    assert abs(n_slip * dt - t_stop) <= dt + 1e-3 * t_stop
+    assert w == pytest.approx(w0 - n_slip * mu * g * dt / r_rms, rel=1e-3)
+    o.step(1)                                       # slow enough: stopped in one step
+    turned += dt * o.omega()[0, 2]
+    assert abs(o.omega()[0, 2]) < 1e-12
+    assert yaw() - yaw0 == pytest.approx(turned, abs=1e-12)
+    y1 = yaw()
+    o.step(200)                                     # and it sticks
+    assert abs(o.omega()[0, 2]) < 1e-12 and abs(yaw() - y1) < 1e-12
+
+
 def _energy(o, b):
     """Kinetic (translation + rotation) + potential + penalty-spring energy per scene."""
     w2 = b.contact_omega ** 2
