@@ -37,13 +37,22 @@
  *    body about the horizontal axes (the x and y components of (centroid - CoG) x J; the vertical
  *    component stays the yaw of the least-squares rotation).
  */
-#include "npxo.h"
-
 #include <math.h>
 #include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* The operation counter (opcount.h) exists only in the C++ counting build of this file; in the
+ * plain build the region marks and the count of single-precision operations are empty. */
+#ifdef NPXO_OPCOUNT
+#include "opcount.h"
+#else
+#define NPXO_REGION(r) ((void)0)
+#define NPXO_COUNT(kind, n) ((void)0)
+#endif
+
+#include "npxo.h"
 
 #define NPXO_ACT_HOLD 0
 #define NPXO_ACT_GP 2
@@ -156,15 +165,15 @@ typedef struct {
 } scene_ws;
 
 static int ws_alloc(scene_ws *w, int np, int nl) {
-    w->r = malloc(sizeof(double) * 3 * (size_t)np);
-    w->x0 = malloc(sizeof(double) * 3 * (size_t)np);
-    w->xp = malloc(sizeof(double) * 3 * (size_t)np);
-    w->xs = malloc(sizeof(double) * 3 * (size_t)np);
-    w->kap = malloc((size_t)np);
-    w->F = malloc(sizeof(double) * (size_t)np);
-    w->wls = malloc(sizeof(double) * (size_t)np);
-    w->Q = malloc(sizeof(double) * 9 * (size_t)nl);
-    w->T = malloc(sizeof(double) * 3 * (size_t)nl);
+    w->r = (double *)malloc(sizeof(double) * 3 * (size_t)np);
+    w->x0 = (double *)malloc(sizeof(double) * 3 * (size_t)np);
+    w->xp = (double *)malloc(sizeof(double) * 3 * (size_t)np);
+    w->xs = (double *)malloc(sizeof(double) * 3 * (size_t)np);
+    w->kap = (unsigned char *)malloc((size_t)np);
+    w->F = (double *)malloc(sizeof(double) * (size_t)np);
+    w->wls = (double *)malloc(sizeof(double) * (size_t)np);
+    w->Q = (double *)malloc(sizeof(double) * 9 * (size_t)nl);
+    w->T = (double *)malloc(sizeof(double) * 3 * (size_t)nl);
     return w->r && w->x0 && w->xp && w->xs && w->kap && w->F && w->wls && w->Q && w->T;
 }
 
@@ -299,6 +308,8 @@ static float lut_height(const npxo_model *M, int scene, double x, double y) {
     if (hm < 0 || M->heightmaps == NULL) return 0.0f;
     float fx = ((float)x - (float)M->hm_origin[0]) * (float)M->hm_scale;
     float fy = ((float)y - (float)M->hm_origin[1]) * (float)M->hm_scale;
+    NPXO_COUNT(NPXO_K_ADD, 2);   /* the single-precision subtractions and multiplications above */
+    NPXO_COUNT(NPXO_K_MUL, 2);
     int ix = (int)floorf(fx), iy = (int)floorf(fy);
     if (ix < 0) ix = 0;
     if (ix > M->hm_nx - 1) ix = M->hm_nx - 1;
@@ -406,7 +417,9 @@ static void scene_pre(const npxo_model *M, npxo_state *st, int s, scene_ws *w, l
     double *R = w->R, *Iw_inv = w->Iw_inv, Rt[9], tmp[9];
 
     /* start-of-step world positions x = c + R r */
+    NPXO_REGION(NPXO_R_SCENE);
     quat_to_mat(q, R);
+    NPXO_REGION(NPXO_R_POINT);
     for (int i = 0; i < np; ++i) {
         double rw[3];
         mat_vec(R, w->r + 3 * i, rw);
@@ -417,6 +430,7 @@ static void scene_pre(const npxo_model *M, npxo_state *st, int s, scene_ws *w, l
      * rigid body whose CoG, orientation and angular momentum are kept */
     int tick = (M->act_mode != NPXO_ACT_HOLD) && (n % M->K == 0);
     w->tick = tick;
+    NPXO_REGION(NPXO_R_TICK);
     if (tick) {
         int nj = w->nl - 1;
         /* the machine-code controller (Sec. IV): its instructions run, reading the foot contacts
@@ -445,6 +459,7 @@ static void scene_pre(const npxo_model *M, npxo_state *st, int s, scene_ws *w, l
     }
 
     /* angular velocity from the angular momentum: w = R Ib^-1 R^T L */
+    NPXO_REGION(NPXO_R_SCENE);
     mat_transpose(R, Rt);
     mat_mul(R, w->Ibinv, tmp);
     mat_mul(tmp, Rt, Iw_inv);
@@ -468,10 +483,12 @@ static void scene_post(const npxo_model *M, npxo_state *st, int s, scene_ws *w, 
     double FN = 0.0, tau[3] = {0, 0, 0};
     for (int i = 0; i < np; ++i) {
         const double *x = w->xp + 3 * i;
+        NPXO_REGION(NPXO_R_POINT);
         float h = lut_height(M, s, x[0], x[1]);
         w->kap[i] = ((float)x[2] < h);
         w->F[i] = 0.0;
         if (!w->kap[i]) continue;
+        NPXO_REGION(NPXO_R_CONTACT);
         double rho[3] = {x[0] - c[0], x[1] - c[1], x[2] - c[2]};
         double vz = v[2] + (om[0] * rho[1] - om[1] * rho[0]);
         double d = (double)h - x[2];
@@ -486,6 +503,7 @@ static void scene_post(const npxo_model *M, npxo_state *st, int s, scene_ws *w, 
     cnt->points += (unsigned long long)np;
 
     /* semi-implicit Euler */
+    NPXO_REGION(NPXO_R_SCENE);
     double vs[3], Ls[3], cs[3], qs[4], oms[3], phi[3], dq[4], Rs[9];
     for (int k = 0; k < 3; ++k) vs[k] = v[k] + dt * M->gravity[k];
     vs[2] += dt * FN / w->Mtot;
@@ -512,6 +530,7 @@ static void scene_post(const npxo_model *M, npxo_state *st, int s, scene_ws *w, 
     const int weighted = M->fric_mode & 1, tilt = M->fric_mode & 2;
     int nC = 0;
     double WC = 0.0;
+    NPXO_REGION(NPXO_R_FRICTION);
     for (int i = 0; i < np; ++i)
         if (st->kappa[w->p0 + i] && w->kap[i]) { nC += 1; WC += weighted ? w->F[i] : 1.0; }
     if (nC >= 1 && WC > 0.0) {
@@ -592,6 +611,7 @@ static void scene_post(const npxo_model *M, npxo_state *st, int s, scene_ws *w, 
     }
 
     /* freeze a scene whose state is no longer finite or has left any sane range */
+    NPXO_REGION(NPXO_R_SCENE);
     int bad = 0;
     for (int k = 0; k < 3; ++k) bad |= !isfinite(cn[k]) || !isfinite(vn[k]) || !isfinite(Ln[k]);
     for (int k = 0; k < 4; ++k) bad |= !isfinite(qn[k]);
@@ -612,6 +632,7 @@ static void scene_post(const npxo_model *M, npxo_state *st, int s, scene_ws *w, 
     }
     st->sensors[s] = sens;
     cnt->scene_steps += 1;
+    NPXO_REGION(NPXO_R_OTHER);
 }
 
 static void scene_step(const npxo_model *M, npxo_state *st, int s, scene_ws *w, long long n,
@@ -741,13 +762,14 @@ static int step_arenas(const npxo_model *M, npxo_state *st, int s0, int s1, int 
     int npm, nlm;
     if (max_scene_sizes(M, &npm, &nlm)) return -1;
     if (s0 % A || s1 % A) return -1;
-    scene_ws *ws = calloc((size_t)A, sizeof *ws);
-    int *active = calloc((size_t)A, sizeof(int)), *np = calloc((size_t)A, sizeof(int));
-    const double **x = calloc((size_t)A, sizeof *x);
-    const float **m = calloc((size_t)A, sizeof *m);
-    double *om = calloc(3 * (size_t)A, sizeof(double)), *fext = calloc(6 * (size_t)A, sizeof(double));
-    double *ls_s = malloc(sizeof(double) * 2 * (size_t)npm);
-    double *ls_e = malloc(sizeof(double) * 2 * (size_t)npm);
+    scene_ws *ws = (scene_ws *)calloc((size_t)A, sizeof *ws);
+    int *active = (int *)calloc((size_t)A, sizeof(int)), *np = (int *)calloc((size_t)A, sizeof(int));
+    const double **x = (const double **)calloc((size_t)A, sizeof *x);
+    const float **m = (const float **)calloc((size_t)A, sizeof *m);
+    double *om = (double *)calloc(3 * (size_t)A, sizeof(double));
+    double *fext = (double *)calloc(6 * (size_t)A, sizeof(double));
+    double *ls_s = (double *)malloc(sizeof(double) * 2 * (size_t)npm);
+    double *ls_e = (double *)malloc(sizeof(double) * 2 * (size_t)npm);
     int ok = ws && active && np && x && m && om && fext && ls_s && ls_e, nalloc = 0;
     for (; ok && nalloc < A; ++nalloc) ok = ws_alloc(&ws[nalloc], npm, nlm);
     if (ok) {
@@ -787,12 +809,14 @@ int npxo_step(const npxo_model *M, npxo_state *st, int s0, int s1, int n_steps, 
     int npm, nlm;
     if (max_scene_sizes(M, &npm, &nlm)) return -1;
     scene_ws w;
-    double *ls_s = malloc(sizeof(double) * 2 * (size_t)npm);
-    double *ls_e = malloc(sizeof(double) * 2 * (size_t)npm);
+    double *ls_s = (double *)malloc(sizeof(double) * 2 * (size_t)npm);
+    double *ls_e = (double *)malloc(sizeof(double) * 2 * (size_t)npm);
     if (!ws_alloc(&w, npm, nlm) || !ls_s || !ls_e) { ws_free(&w); free(ls_s); free(ls_e); return -2; }
     for (int s = s0; s < s1; ++s) {
         ws_bind(M, s, &w);
+        NPXO_REGION(NPXO_R_TICK);
         shape_update(M, st, &w);
+        NPXO_REGION(NPXO_R_OTHER);
         for (int k = 0; k < n_steps; ++k) {
             if (st->status[s]) break;
             scene_step(M, st, s, &w, step0 + k, ls_s, ls_e, cnt);
@@ -821,14 +845,18 @@ int npxo_step_mt(const npxo_model *M, npxo_state *st, int n_steps, long long ste
     const int A = M->arena > 1 ? M->arena : 1, units = M->n_scenes / A;
     if (n_threads < 1) n_threads = 1;
     if (n_threads > units) n_threads = units > 0 ? units : 1;
-    npxo_job *jobs = calloc((size_t)n_threads, sizeof *jobs);
-    pthread_t *th = calloc((size_t)n_threads, sizeof *th);
+    npxo_job *jobs = (npxo_job *)calloc((size_t)n_threads, sizeof *jobs);
+    pthread_t *th = (pthread_t *)calloc((size_t)n_threads, sizeof *th);
     if (!jobs || !th) { free(jobs); free(th); return -2; }
     int rc = 0;
     for (int t = 0; t < n_threads; ++t) {
-        jobs[t] = (npxo_job){M, st, A * (int)((long long)units * t / n_threads),
-                             A * (int)((long long)units * (t + 1) / n_threads), n_steps, step0,
-                             {0}, 0};
+        memset(&jobs[t], 0, sizeof jobs[t]);
+        jobs[t].M = M;
+        jobs[t].st = st;
+        jobs[t].s0 = A * (int)((long long)units * t / n_threads);
+        jobs[t].s1 = A * (int)((long long)units * (t + 1) / n_threads);
+        jobs[t].n_steps = n_steps;
+        jobs[t].step0 = step0;
         if (pthread_create(&th[t], NULL, npxo_worker, &jobs[t])) { rc = -3; n_threads = t; break; }
     }
     for (int t = 0; t < n_threads; ++t) {
@@ -893,3 +921,17 @@ int npxo_link_frames(const npxo_model *M, const npxo_state *st, int s, double *o
     ws_free(&w);
     return 0;
 }
+
+#ifdef NPXO_OPCOUNT
+/* ------------------------------------------------------------------ the counting build's counters */
+unsigned long long npxo_ops[NPXO_R_N][NPXO_K_N];
+int npxo_region = NPXO_R_OTHER;
+
+extern "C" void npxo_opcount_reset(void) {
+    memset(npxo_ops, 0, sizeof npxo_ops);
+    npxo_region = NPXO_R_OTHER;
+}
+
+/* out[r * NPXO_K_N + k]: operations of kind k counted in region r since the last reset */
+extern "C" void npxo_opcount_get(unsigned long long *out) { memcpy(out, npxo_ops, sizeof npxo_ops); }
+#endif

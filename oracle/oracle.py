@@ -16,20 +16,28 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnpxo.so")
+COUNT_LIB_PATH = os.path.join(HERE, "libnpxo_count.so")
 SOURCES = [os.path.join(HERE, "npxo.c")]
+HEADERS = [os.path.join(HERE, "npxo.h"), os.path.join(HERE, "opcount.h")]
+
+
+def _compile(out: str, cmd_head: list, force: bool) -> str:
+    newest = max(os.path.getmtime(p) for p in SOURCES + HEADERS)
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= newest:
+        return out
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.run([*cmd_head, "-o", tmp, *SOURCES, "-lm", "-lpthread"], check=True)
+    os.replace(tmp, out)
+    return out
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C11, no FMA contraction so that x86 and Arm agree)."""
-    newest = max(os.path.getmtime(p) for p in SOURCES + [os.path.join(HERE, "npxo.h")])
-    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
-        return LIB_PATH
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fPIC", "-shared",
-           "-o", tmp, *SOURCES, "-lm", "-lpthread"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    """Compile the oracle with gcc (plain C11, no FMA contraction so that x86 and Arm agree), and
+    its counting build (the same source as C++ with every double counting its operations)."""
+    _compile(COUNT_LIB_PATH, ["g++", "-O2", "-std=c++17", "-x", "c++", "-DNPXO_OPCOUNT", "-D_GNU_SOURCE",
+                              "-ffp-contract=off", "-fPIC", "-shared"], force)
+    return _compile(LIB_PATH, ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fPIC",
+                               "-shared"], force)
 
 
 class _Model(C.Structure):
@@ -67,30 +75,55 @@ class Counts(C.Structure):
 
 
 _lib = None
+_count_lib = None
+
+
+def _declare(L):
+    P = C.c_void_p
+    L.npxo_init.argtypes = [P, P, P, P, P, P, P]
+    L.npxo_step.argtypes = [P, P, C.c_int, C.c_int, C.c_int, C.c_longlong, P]
+    L.npxo_step_mt.argtypes = [P, P, C.c_int, C.c_longlong, C.c_int, P]
+    L.npxo_points_world.argtypes = [P, P, C.c_int, P]
+    L.npxo_mass_props.argtypes = [P, P, C.c_int, P, P, P]
+    L.npxo_link_frames.argtypes = [P, P, C.c_int, P]
+    L.npxo_target.argtypes = [P, C.c_int, C.c_int, C.c_longlong]
+    L.npxo_target.restype = C.c_double
+    L.npxo_lut.argtypes = [P, C.c_int, C.c_double, C.c_double, P]
+    L.npxo_friction_ls.argtypes = [C.c_int, P, P, P, P]
+    L.npxo_friction_ls_w.argtypes = [C.c_int, P, P, P, P, P]
+    L.npxo_gp_run.argtypes = [P, P, P, P, C.c_int, C.c_uint, C.c_int]
+    L.npxo_gp_run.restype = None
+    L.npxo_arena_forces.argtypes = [C.c_int, P, P, P, P, P, P, P, C.c_double, C.c_double,
+                                    C.c_double, P]
+    L.npxo_arena_forces.restype = None
+    return L
 
 
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
-        P = C.c_void_p
-        _lib.npxo_init.argtypes = [P, P, P, P, P, P, P]
-        _lib.npxo_step.argtypes = [P, P, C.c_int, C.c_int, C.c_int, C.c_longlong, P]
-        _lib.npxo_step_mt.argtypes = [P, P, C.c_int, C.c_longlong, C.c_int, P]
-        _lib.npxo_points_world.argtypes = [P, P, C.c_int, P]
-        _lib.npxo_mass_props.argtypes = [P, P, C.c_int, P, P, P]
-        _lib.npxo_link_frames.argtypes = [P, P, C.c_int, P]
-        _lib.npxo_target.argtypes = [P, C.c_int, C.c_int, C.c_longlong]
-        _lib.npxo_target.restype = C.c_double
-        _lib.npxo_lut.argtypes = [P, C.c_int, C.c_double, C.c_double, P]
-        _lib.npxo_friction_ls.argtypes = [C.c_int, P, P, P, P]
-        _lib.npxo_friction_ls_w.argtypes = [C.c_int, P, P, P, P, P]
-        _lib.npxo_gp_run.argtypes = [P, P, P, P, C.c_int, C.c_uint, C.c_int]
-        _lib.npxo_gp_run.restype = None
-        _lib.npxo_arena_forces.argtypes = [C.c_int, P, P, P, P, P, P, P, C.c_double, C.c_double,
-                                           C.c_double, P]
-        _lib.npxo_arena_forces.restype = None
+        _lib = _declare(C.CDLL(build()))
     return _lib
+
+
+def count_lib():
+    """The counting build of the oracle (opcount.h): same results, operations counted."""
+    global _count_lib
+    if _count_lib is None:
+        build()
+        L = _declare(C.CDLL(COUNT_LIB_PATH))
+        L.npxo_opcount_reset.argtypes = []
+        L.npxo_opcount_reset.restype = None
+        L.npxo_opcount_get.argtypes = [C.c_void_p]
+        L.npxo_opcount_get.restype = None
+        _count_lib = L
+    return _count_lib
+
+
+# the counting build's regions of a step and kinds of operation (opcount.h)
+OP_REGIONS = ("other", "scene", "point", "contact", "friction", "tick")
+OP_KINDS = ("add", "mul", "div", "sqrt", "transc", "cmp")
+FLOP_KINDS = ("add", "mul", "div", "sqrt", "transc")    # comparisons are not floating-point work
 
 
 def _ptr(a):
@@ -160,9 +193,14 @@ class Oracle:
     """FP64 state of every scene of a SceneBatch, advanced by the C oracle."""
 
     def __init__(self, batch, threads: int = 1, fric_mode: int = 0, gp_programs=None, arena: int = 1,
-                 arena_radius: float = 0.0):
+                 arena_radius: float = 0.0, counting: bool = False):
         self.batch = b = batch
         self.threads = threads
+        # the counting build steps identically and counts every operation (one thread only)
+        self.counting = bool(counting)
+        if self.counting and threads != 1:
+            raise ValueError("the counting build of the oracle runs on one thread")
+        self._L = count_lib() if self.counting else lib()
         self.fric_mode = int(fric_mode)
         # robots per arena (consecutive scenes colliding with one another) and the point radius
         self.arena, self.arena_radius = int(arena), float(arena_radius)
@@ -203,7 +241,7 @@ class Oracle:
                                                  self.kappa, self.sensors, self.status,
                                                  self.gp_pc, self.gp_acc, self.gp_k)])
         self.n = 0
-        rc = lib().npxo_init(C.byref(self.model), _ptr(b.origin), _ptr(b.quat), _ptr(b.vel),
+        rc = self._L.npxo_init(C.byref(self.model), _ptr(b.origin), _ptr(b.quat), _ptr(b.vel),
                              _ptr(b.omega), _ptr(np.ascontiguousarray(b.theta0, np.float32)),
                              C.byref(self.state))
         if rc:
@@ -212,12 +250,12 @@ class Oracle:
     def step(self, n_steps: int, threads: int | None = None) -> dict:
         cnt = Counts()
         th = self.threads if threads is None else threads
-        if th > 1:
-            rc = lib().npxo_step_mt(C.byref(self.model), C.byref(self.state), n_steps, self.n, th,
-                                    C.byref(cnt))
+        if th > 1 and not self.counting:
+            rc = self._L.npxo_step_mt(C.byref(self.model), C.byref(self.state), n_steps, self.n, th,
+                                      C.byref(cnt))
         else:
-            rc = lib().npxo_step(C.byref(self.model), C.byref(self.state), 0, self.batch.n_scenes,
-                                 n_steps, self.n, C.byref(cnt))
+            rc = self._L.npxo_step(C.byref(self.model), C.byref(self.state), 0, self.batch.n_scenes,
+                                   n_steps, self.n, C.byref(cnt))
         if rc:
             raise RuntimeError(f"oracle step failed (rc={rc})")
         self.n += n_steps
@@ -269,6 +307,25 @@ class Oracle:
                       (self.gp_pc, other.gp_pc), (self.gp_acc, other.gp_acc), (self.gp_k, other.gp_k)):
             a[...] = b_
         self.n = other.n
+
+
+def count_ops(batch, n_steps: int, warm_steps: int = 0) -> dict:
+    """Floating-point operations of the oracle's step, counted by its counting build: every scene
+    of `batch` advanced by warm_steps (not counted), then n_steps counted.  Returns the event
+    counts of the counted steps, the operations per region and kind ({region: {kind: n}}), and
+    flops = additions, multiplications, divisions, square roots and transcendental calls."""
+    o = Oracle(batch, counting=True)
+    if warm_steps:
+        o.step(warm_steps)
+    L = count_lib()
+    L.npxo_opcount_reset()
+    events = o.step(n_steps)
+    raw = np.zeros(len(OP_REGIONS) * len(OP_KINDS), np.uint64)
+    L.npxo_opcount_get(raw.ctypes.data)
+    raw = raw.reshape(len(OP_REGIONS), len(OP_KINDS))
+    ops = {r: {k: int(raw[i, j]) for j, k in enumerate(OP_KINDS)} for i, r in enumerate(OP_REGIONS)}
+    flops = sum(ops[r][k] for r in OP_REGIONS for k in FLOP_KINDS)
+    return {"events": events, "ops": ops, "flops": flops, "oracle": o}
 
 
 def quat_matrix(q) -> np.ndarray:
