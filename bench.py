@@ -9,9 +9,10 @@ Timing: CUDA events on the world's stream around every step; between timed steps
 buffer is written to flush the 129 MB L2 (not timed).  `value` is whole-job throughput with the
 state resident in HBM; `e2e` is the same metric through the public C-ABI with host buffers:
 every step uploads the full dynamic state from pinned host memory, steps, and reads the sensors
-back.  The roofline object reports the step kernel's algorithmic FP32 flops (event counts of the
-CPU oracle on a sample of the same workload times a fixed per-event flop model) per launch over
-its measured launch time, against the FP32 FMA peak of the part.
+back.  The roofline object reports the step kernel's algorithmic flops per launch -- the
+floating-point operations of the plain step, counted by the oracle's counting build
+(oracle/opcount.h) on a sample of the same workload -- over its measured launch time, against the
+FP32 FMA peak of the part.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -42,24 +43,23 @@ UNIT = "scene-steps/s"
 SMS, FP32_LANES, MAX_SM_GHZ = 152, 128, 2.07
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_GHZ / 1e3
 
-# Algorithmic flops per oracle event (an FMA counts 2): flat-ground z test per point; contact
-# point (x, y, point velocity, penalty force, wrench); friction point (two positions, slip, seven
-# least-squares sums); joint-update point (forward kinematics twice for the mass properties,
-# once for the offsets, ten moment sums); fixed per-scene work (rotation matrices, angular
-# velocity twice, integration, exponential map, normalisation, friction solve, momentum and
-# orientation corrections).
-FLOPS_PER = {"points": 7, "contacts": 27, "friction_pts": 42, "tick_points": 115,
-             "scene_steps": 320}
+# DRAM bytes (read + write) of one 1,000-step step-kernel launch, by workload and launch shape
+# (lanes per scene, warps per block, blocks), from ncu (profiles/step_kernel_*_dram.md); reported
+# only for a captured shape, and to be re-taken whenever the kernel changes
+STEP_TRAFFIC = {(WORKLOAD, 8, 7, 147): 31880448}
 
 
-# DRAM bytes (read + write) of one 1,000-step step-kernel launch on this workload, by launch shape
-# (lanes per scene, warps per block, blocks), from ncu (profiles/step_kernel_hexapod4096x1000_dram.md);
-# reported only for a captured shape, and to be re-taken whenever the kernel changes
-STEP_TRAFFIC = {(8, 7, 147): 31880448}
-
-
-def algorithmic_flops(counts: dict) -> float:
-    return float(sum(FLOPS_PER[k] * counts[k] for k in FLOPS_PER))
+def counted_flops_per_scene_step(batch, n_scenes: int, n_steps: int, warm_steps: int) -> dict:
+    """Algorithmic flops of the plain step: the operations the FP64 oracle's counting build
+    performs (additions, multiplications, divisions, square roots, transcendental calls) on
+    n_scenes scenes of the workload over n_steps after warm_steps, per scene-step, with the
+    share of each part of the step."""
+    from oracle.oracle import FLOP_KINDS, count_ops
+    r = count_ops(batch.subset(np.arange(n_scenes)), n_steps, warm_steps=warm_steps)
+    ss = r["events"]["scene_steps"]
+    parts = {k: sum(v[f] for f in FLOP_KINDS) / ss for k, v in r["ops"].items() if k != "other"}
+    return {"flops_per_scene_step": r["flops"] / ss, "by_part": parts,
+            "sample": f"{n_scenes} scenes x {n_steps} steps after {warm_steps} (oracle counting build)"}
 
 
 def job_throughput(units_per_rank: float, rank_ms: float, dist=None, device="cpu"):
@@ -222,6 +222,25 @@ def other_workloads(World, scenes, stream, device) -> dict:
                                                                     "and its CoG stepped alone, after 2 s",
                                                             "median": float(np.median(d)),
                                                             "p90": float(np.percentile(d, 90))}})
+        if name.startswith("hexapod_rough_terrain"):
+            # roofline of the height-map kernel: counted algorithmic flops, and the DRAM traffic of
+            # one 1,000-step launch (ncu) against the measured HBM bandwidth
+            fl = counted_flops_per_scene_step(b, 16, CHUNK, CHUNK)
+            launch_ms = ms / secs
+            achieved = fl["flops_per_scene_step"] * b.n_scenes * CHUNK / (launch_ms / 1e3) / 1e12
+            shape = (name, info["lanes_per_scene"], info["warps_per_block"], info["blocks"])
+            traffic = STEP_TRAFFIC.get(shape)
+            hbm = _measured_peaks().get("hbm_gbs")
+            out[name]["roofline"] = {
+                "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic, "kernel": "step_kernel_hm",
+                "launch_ms": launch_ms, "flops_per_scene_step": fl["flops_per_scene_step"],
+                "flops_by_part": fl["by_part"], "flops_source": fl["sample"],
+                "peak_note": "FP32 FMA peak from unit counts and max SM clock (derived)",
+                "hbm": None if traffic is None or not hbm else {
+                    "achieved_gbs": traffic / (launch_ms / 1e3) / 1e9, "peak_gbs": hbm,
+                    "frac": traffic / (launch_ms / 1e3) / 1e9 / hbm,
+                    "peak_note": "MEASURED_PEAKS.json hbm_gbs, of measured"}}
         if secs == 60:
             d = np.linalg.norm(r["cog"][:, :2] - c0[:, :2], axis=1)
             out[name]["fitness_m"] = {"what": "horizontal distance of the robot CoG from its start after 60 s",
@@ -400,33 +419,43 @@ def surrogate_leg(World, scenes, stream, device, n_transitions: int, stride: int
     return out
 
 
+def bench_config(ws: int) -> dict:
+    """The workload of one benchmark step, the same dict in both arms."""
+    return {"workload": WORKLOAD, "scenes_per_gpu": N_SCENES, "steps_per_bench_step": CHUNK,
+            "dt": 1e-3, "K": 80, "parallelism": f"replicas{ws}",
+            "l2": "GPU arm: flushed between timed steps (256 MiB write); CPU arm: not applicable"}
+
+
 def run_reference(args):
-    """Reference arm: the CPU oracle on the host cores, same workload and metric."""
+    """Reference arm: the FP64 CPU oracle, as it stands, on all host cores, stepping the whole
+    workload: every benchmark step advances all 4,096 hexapods by 1,000 steps (the simulation
+    continues from step to step, as in the GPU arm), timed with a wall clock around each step."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     from paper_2411_05799_gb300 import scenes
+    from oracle.oracle import Oracle
     from oracle.oracle import build as build_oracle
     build_oracle()
     threads = os.cpu_count() or 1
-    batch = scenes.hexapod_batch(N_SCENES)
-    n_sc, n_st = 256, 500                  # a bounded sample of the 4,096-scene, 1,000-step step
+    o = Oracle(scenes.hexapod_batch(N_SCENES), threads=threads)
     for _ in range(args.warmup):
-        cpu_oracle_sample(batch, n_sc, 50, threads)
-    vals = []
-    t_total = 0.0
+        o.step(CHUNK)
+    secs = []
     for _ in range(args.steps):
-        r = cpu_oracle_sample(batch, n_sc, n_st, threads)
-        vals.append(r["scene_steps_per_s"])
-        t_total += r["seconds"]
-    value = float(np.mean(vals))
-    ms_per_step = N_SCENES * CHUNK / value * 1e3
-    sample = f"{n_sc} of {N_SCENES} hexapods x {n_st} of {CHUNK} steps per benchmark step"
+        t0 = time.perf_counter()
+        cnt = o.step(CHUNK)
+        secs.append(time.perf_counter() - t0)
+        assert cnt["scene_steps"] == N_SCENES * CHUNK
+    total = float(sum(secs))
+    value = N_SCENES * CHUNK * args.steps / total
+    sample = (f"the whole workload: all {N_SCENES} hexapods x {CHUNK} steps per benchmark step, "
+              f"{threads} threads (FP64)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "scenes": N_SCENES,
-                                            "steps_per_bench_step": CHUNK, "dt": 1e-3, "K": 80},
+            "data": "synthetic", "config": bench_config(ws),
+            "frozen_scenes": int((o.status != 0).sum()),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -515,13 +544,11 @@ def run_gpu(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "scenes_per_gpu": N_SCENES,
-                       "steps_per_bench_step": CHUNK, "dt": 1e-3, "K": 80,
-                       "parallelism": f"replicas{ws}", "l2": "flushed between timed steps (256 MiB write)",
-                       "lanes_per_scene": info["lanes_per_scene"],
+            "config": bench_config(ws),
+            "launch": {"lanes_per_scene": info["lanes_per_scene"],
                        "warps_per_block": info["warps_per_block"], "blocks": info["blocks"],
-                       "size_classes": info["size_classes"],
-                       "frozen_scenes": int((status != 0).sum())},
+                       "size_classes": info["size_classes"]},
+            "frozen_scenes": int((status != 0).sum()),
             "gpu_launches": int(launches + args.steps),   # step-kernel launches + step-counter kernels
             "clocks": clk,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -539,20 +566,22 @@ def run_gpu(args):
         line["simplify_modes"] = simplify_leg(World, stream, local)
 
     if rank == 0:
-        # algorithmic flops per scene-step from the oracle's event counts on a sample
+        # algorithmic flops per scene-step: the oracle's counted operations on a sample
         n_sc, n_st = 1024, 1000
         threads = os.cpu_count() or 1
         r = cpu_oracle_sample(batch, n_sc, n_st, threads)
-        flops_per_ss = algorithmic_flops(r["counts"]) / r["counts"]["scene_steps"]
+        fl = counted_flops_per_scene_step(batch, 64, 2 * CHUNK, CHUNK)
+        flops_per_ss = fl["flops_per_scene_step"]
         launch_ms = total_ms / max(1, launches)
         achieved = flops_per_ss * N_SCENES * CHUNK / (launch_ms / 1e3) / 1e12
-        shape = (info["lanes_per_scene"], info["warps_per_block"], info["blocks"])
+        shape = (WORKLOAD, info["lanes_per_scene"], info["warps_per_block"], info["blocks"])
         line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                             "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                             "traffic": STEP_TRAFFIC.get(shape) if CHUNK == 1000 else None,
-                            "kernel": "step_kernel",
-                            "flops_per_scene_step": flops_per_ss,
-                            "peak_note": "FP32 FMA peak from unit counts and max SM clock"}
+                            "kernel": "step_kernel", "launch_ms": launch_ms,
+                            "flops_per_scene_step": flops_per_ss, "flops_by_part": fl["by_part"],
+                            "flops_source": fl["sample"],
+                            "peak_note": "FP32 FMA peak from unit counts and max SM clock (derived)"}
         r1 = cpu_oracle_sample(batch, 64, 1000, 1)     # the paper's setting: one CPU thread
         line["cpu_baseline"] = {"value": r["scene_steps_per_s"], "unit": UNIT, "cores": threads,
                                 "kind": "oracle",
@@ -571,6 +600,7 @@ def run_profile(args):
     """ncu drivers (print no benchmark line).
     step:      a few step-kernel launches of `--chunk` steps on the benchmark workload in a fixed
                launch shape;
+    step_hm:   the same on the rough-terrain rollout (16,384 hexapods, 128 x 128 height maps);
     gemm:      the surrogate network's forward GEMMs over 65,536 rows (random weights), 3 passes;
     surrogate: a briefly trained surrogate stepping 65,536 hexapods for 4 steps."""
     import torch
@@ -579,14 +609,14 @@ def run_profile(args):
     from paper_2411_05799_gb300.npx import World
     build()
     torch.cuda.set_device(0)
-    if args.profile == "step":
-        world = World.from_batch(scenes.hexapod_batch(N_SCENES),
-                                 configure=dict(lanes_per_scene=args.lps, warps_per_block=args.wpb,
-                                                chunk_steps=args.chunk))
+    if args.profile in ("step", "step_hm"):
+        batch = scenes.hexapod_batch(N_SCENES) if args.profile == "step" else scenes.cpg_batch(16384)
+        world = World.from_batch(batch, configure=dict(lanes_per_scene=args.lps, warps_per_block=args.wpb,
+                                                       chunk_steps=args.chunk))
         for _ in range(3):
             world.step(args.chunk)
         world.sync()
-        print(json.dumps({"profile": "step", **world.info(),
+        print(json.dumps({"profile": args.profile, **world.info(),
                           "status_nonzero": int((world.read()["status"] != 0).sum())}))
         world.close()
         return 0
@@ -621,8 +651,9 @@ def run_profile(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile", choices=["step", "gemm", "surrogate"],
-                    help="ncu driver (no bench line): step kernel, network GEMMs or surrogate step")
+    ap.add_argument("--profile", choices=["step", "step_hm", "gemm", "surrogate"],
+                    help="ncu driver (no bench line): step kernel (4,096 hexapods on flat ground, or "
+                         "16,384 on rough height maps), network GEMMs or surrogate step")
     ap.add_argument("--lps", type=int, default=16)
     ap.add_argument("--wpb", type=int, default=16)
     ap.add_argument("--chunk", type=int, default=100)
