@@ -1,11 +1,13 @@
 """The surrogate network on the tensor cores (BF16 operands, FP32 accumulation) against the FP64
-oracle of oracle/mlp.py: forward outputs, loss and every layer's gradients within BF16 bounds,
-Adam's first step, and training that actually fits."""
+oracle of oracle/mlp.py: every forward output and every element of every layer's weight and bias
+gradients within its per-element BF16 bound (tests/bf16_bounds.py), the loss, Adam's first step,
+and training that actually fits."""
 import numpy as np
 import pytest
 
 from oracle import mlp as ref
 from paper_2411_05799_gb300 import npx
+from tests import bf16_bounds as B
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -21,11 +23,6 @@ def _own_stream():
     s.synchronize()
 
 SIZES = [271, 512, 512, 512, 512, 247]
-
-
-def _rel(a, b):
-    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
-    return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
 def _setup(M=256, seed=0):
@@ -68,8 +65,9 @@ def test_forward_matches_fp64_oracle():
     yd = torch.zeros(M, SIZES[-1], device="cuda")
     net.forward(xd.data_ptr(), yd.data_ptr(), M)
     torch.cuda.synchronize()
-    y_ref, _ = ref.forward(Ws, bs, x.astype(np.float64))
-    assert _rel(yd.cpu().numpy(), y_ref) < 2e-2
+    r = B.reference(Ws, bs, x, np.zeros((M, SIZES[-1])))
+    worst = B.worst_ratio(yd.cpu().numpy(), r["y"], r["ey"])
+    assert worst <= 1.0, f"an output is {worst:.3g} x its BF16 bound from the FP64 oracle"
 
 
 def test_gradients_match_fp64_oracle():
@@ -79,14 +77,13 @@ def test_gradients_match_fp64_oracle():
     loss = torch.zeros(1, device="cuda")
     net.backward(xd.data_ptr(), td.data_ptr(), M, loss.data_ptr())
     dW, db = net.get_grads()
-    y, cache = ref.forward(Ws, bs, x.astype(np.float64))
-    rW, rb = ref.backward(Ws, bs, cache, y, t.astype(np.float64))
-    assert abs(float(loss.item()) - ref.mse(y, t)) < 2e-2 * ref.mse(y, t)
-    for l in range(len(rW)):
-        assert _rel(dW[l], rW[l]) < 5e-2, (l, _rel(dW[l], rW[l]))
-        assert _rel(db[l], rb[l]) < 5e-2, (l, _rel(db[l], rb[l]))
-        cos = np.sum(dW[l] * rW[l]) / (np.linalg.norm(dW[l]) * np.linalg.norm(rW[l]))
-        assert cos > 0.998, (l, cos)
+    r = B.reference(Ws, bs, x, t)
+    assert abs(float(loss.item()) - r["loss"]) < 1e-2 * r["loss"]
+    for l in range(len(dW)):
+        worst = B.worst_ratio(dW[l], r["dW"][l], r["edW"][l])
+        assert worst <= 1.0, f"layer {l}: a weight gradient is {worst:.3g} x its BF16 bound"
+        worst = B.worst_ratio(db[l], r["db"][l], r["edb"][l])
+        assert worst <= 1.0, f"layer {l}: a bias gradient is {worst:.3g} x its BF16 bound"
 
 
 def test_adam_first_step_moves_each_weight_by_the_learning_rate():
