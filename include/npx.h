@@ -222,8 +222,10 @@ typedef struct {
                                    its own shared-memory slots and launch shape */
 } npx_world_info;
 int npx_world_info_get(npx_world *w, npx_world_info *out);
-/* Launch shape of the step kernel: lanes per scene (8, 16 or 32), warps per block (1..16),
- * resident blocks (0 = as many as fit), steps per kernel launch (chunk).  0 keeps a value. */
+/* Launch shape of the step kernel: lanes per scene (4, 8, 16 or 32; a scene holds at most 64
+ * points per lane), warps per block (1..16; shapes whose registers do not fit on an SM are refused
+ * with NPX_ERANGE), resident blocks (0 = as many as fit), steps per kernel launch (chunk).  0 keeps
+ * a value. */
 int npx_world_configure(npx_world *w, int lanes_per_scene, int warps_per_block, int blocks,
                         int chunk_steps);
 /* Time the step kernel over the feasible launch shapes on a copy of the state (n_steps each)

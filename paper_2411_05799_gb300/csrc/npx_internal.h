@@ -79,7 +79,7 @@ struct WorldDev {
 };
 
 struct LaunchCfg {
-    int lps;      // lanes per scene: 8, 16 or 32
+    int lps;      // lanes per scene: 4, 8, 16 or 32
     int wpb;      // warps per block
     int blocks;   // grid size
 };
@@ -127,11 +127,11 @@ cudaError_t launch_sensor_points(const WorldDev &W, int *count, int *max_count, 
 cudaError_t launch_shape_cache(const WorldDev &W, const SurCache &C, cudaStream_t st);
 cudaError_t launch_features(const WorldDev &W, const SurCache &C, const SurrogateIO &io, cudaStream_t st);
 // the surrogate's next state from the network output Y [S x ldy] (standardised deltas), kept
-// where the contact sensors do not change; the other scenes go to list / count.  nx [16 * S],
-// applied [S] and sens_new [S] are scratch.
+// where the contact sensors do not change; the other scenes go to list / count, and their
+// fallback counters fb [S] grow by one.  nx [16 * S], applied [S] and sens_new [S] are scratch.
 cudaError_t launch_surrogate_update(const WorldDev &W, const SurCache &C, const float *Y, int ldy,
                                     const float *t_mu, const float *t_sd, float *nx, uint8_t *applied,
-                                    uint32_t *sens_new, int *list, int *count, cudaStream_t st);
+                                    uint32_t *sens_new, int *list, int *count, int *fb, cudaStream_t st);
 cudaError_t launch_kappa_refresh(const WorldDev &W, const int *list, const int *count, cudaStream_t st);
 // *total += *count * mult, then *count = 0
 cudaError_t launch_accumulate(long long *total, int *count, int mult, cudaStream_t st);

@@ -58,7 +58,8 @@ extern "C" int npx_step_noalloc(const npx_device_world *d, int n_steps, void *st
         return noalloc_fail(NPX_ERANGE, buf);
     }
     const int lps = d->lanes_per_scene, wpb = d->warps_per_block;
-    if (lps != 8 && lps != 16 && lps != 32) return noalloc_fail(NPX_EINVAL, "npx_step_noalloc: lanes_per_scene must be 8, 16 or 32");
+    if (lps != 4 && lps != 8 && lps != 16 && lps != 32)
+        return noalloc_fail(NPX_EINVAL, "npx_step_noalloc: lanes_per_scene must be 4, 8, 16 or 32");
     if (wpb < 1 || wpb > 16) return noalloc_fail(NPX_EINVAL, "npx_step_noalloc: warps_per_block must be 1..16");
     if (d->max_points < 1 || d->max_points > 64 * lps || d->max_points > NPX_MAX_POINTS)
         return noalloc_fail(NPX_ERANGE, "npx_step_noalloc: max_points must be 1..64 * lanes_per_scene");

@@ -1,6 +1,6 @@
 // npx_step.cu -- the fused NeoPhysIx scene-step kernel for GB300 (sm_103a) and its helpers.
 //
-// Execution model.  A group of LPS lanes (8, 16 or 32) of one warp owns one scene; a warp owns
+// Execution model.  A group of LPS lanes (4, 8, 16 or 32) of one warp owns one scene; a warp owns
 // 32/LPS scenes.  Warps are persistent: each takes the next group of scenes from a global work
 // counter (scenes ordered by decreasing point count), runs them through all n steps of the
 // launch with their state in registers, writes them back and takes the next group.  Every
@@ -115,6 +115,25 @@ __device__ __forceinline__ void world_sym(const float R[9], const Sym &S, const 
     mat_vec(R, b, y);
 }
 
+// world-frame tensor R S R^T of a symmetric S (rows of R S dotted with rows of R)
+__device__ __forceinline__ Sym world_tensor(const float R[9], const Sym &S) {
+    float T[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        T[3 * i] = R[3 * i] * S.xx + R[3 * i + 1] * S.xy + R[3 * i + 2] * S.xz;
+        T[3 * i + 1] = R[3 * i] * S.xy + R[3 * i + 1] * S.yy + R[3 * i + 2] * S.yz;
+        T[3 * i + 2] = R[3 * i] * S.xz + R[3 * i + 1] * S.yz + R[3 * i + 2] * S.zz;
+    }
+    Sym w;
+    w.xx = T[0] * R[0] + T[1] * R[1] + T[2] * R[2];
+    w.yy = T[3] * R[3] + T[4] * R[4] + T[5] * R[5];
+    w.zz = T[6] * R[6] + T[7] * R[7] + T[8] * R[8];
+    w.xy = T[0] * R[3] + T[1] * R[4] + T[2] * R[5];
+    w.xz = T[0] * R[6] + T[1] * R[7] + T[2] * R[8];
+    w.yz = T[3] * R[6] + T[4] * R[7] + T[5] * R[8];
+    return w;
+}
+
 __device__ __forceinline__ void quat_mul(const float a[4], const float b[4], float c[4]) {
     float t0 = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
     float t1 = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
@@ -145,6 +164,15 @@ __device__ __forceinline__ void sincos_small(float x, float *s, float *c) {
         *s = sc.x;
         *c = sc.y;
     }
+}
+
+// sin(a) / a and (1 - cos a) / a^2 as series in x = a^2, for x <= 1/64 (|a| <= 1/8): the first
+// omitted terms, x^4 / 362880 and x^4 / 3628800, are below 2e-13
+__device__ __forceinline__ float sinc_sq(float x) {
+    return fmaf(x, fmaf(x, fmaf(x, -1.f / 5040.f, 1.f / 120.f), -1.f / 6.f), 1.f);
+}
+__device__ __forceinline__ float cosc_sq(float x) {
+    return fmaf(x, fmaf(x, fmaf(x, -1.f / 40320.f, 1.f / 720.f), -1.f / 24.f), 0.5f);
 }
 
 __device__ __forceinline__ float asin_small(float x) {
@@ -258,6 +286,16 @@ __device__ __forceinline__ uint64_t tiles_near_ground(const float4 *tb, int ntil
         mask |= mine << (r * LPS);
     }
     return mask;
+}
+
+// The lowest tile set in any lane's 64-bit tile mask of the group (64 if none), the same on every
+// lane of the group.
+template <int LPS>
+__device__ __forceinline__ int group_first_tile(uint64_t m) {
+    int k = m ? __ffsll((long long)m) - 1 : 64;
+#pragma unroll
+    for (int o = LPS / 2; o > 0; o >>= 1) k = min(k, __shfl_xor_sync(FULL_MASK, k, o));
+    return k;
 }
 
 // ------------------------------------------------------------------------ kinematics (Sec. III-B)
@@ -410,15 +448,25 @@ __device__ __noinline__ void shape_update(const WorldDev &W, int s, int p0, int 
 
 // ------------------------------------------------------------------------ ground (Sec. III-A)
 
+// The height maps' parameters, copied from the world into registers by the step loop.
+struct HmView {
+    const float *hm;
+    int nx, ny;
+    float ox, oy, scale;
+};
+__device__ __forceinline__ HmView hm_view(const WorldDev &W) {
+    return HmView{W.hm, W.hm_nx, W.hm_ny, W.hm_ox, W.hm_oy, W.hm_scale};
+}
+
 template <bool FLAT>
-__device__ __forceinline__ float ground(const WorldDev &W, int hm, float x, float y) {
+__device__ __forceinline__ float ground(const HmView &H, int hm, float x, float y) {
     if (FLAT || hm < 0) return 0.f;
-    const float fx = __fmul_rn(__fsub_rn(x, W.hm_ox), W.hm_scale);
-    const float fy = __fmul_rn(__fsub_rn(y, W.hm_oy), W.hm_scale);
+    const float fx = __fmul_rn(__fsub_rn(x, H.ox), H.scale);
+    const float fy = __fmul_rn(__fsub_rn(y, H.oy), H.scale);
     int ix = __float2int_rd(fx), iy = __float2int_rd(fy);
-    ix = min(max(ix, 0), W.hm_nx - 1);
-    iy = min(max(iy, 0), W.hm_ny - 1);
-    return __ldg(W.hm + ((size_t)hm * W.hm_ny + iy) * W.hm_nx + ix);
+    ix = min(max(ix, 0), H.nx - 1);
+    iy = min(max(iy, 0), H.ny - 1);
+    return __ldg(H.hm + ((size_t)hm * H.ny + iy) * H.nx + ix);
 }
 
 // The same lookup through a window of the scene's map in shared memory.  The window (origin
@@ -426,17 +474,17 @@ __device__ __forceinline__ float ground(const WorldDev &W, int hm, float x, floa
 // inside it already reads the clamped cell's height; others are clamped and read from global
 // memory (the same value either way).
 template <bool FLAT>
-__device__ __forceinline__ float ground_win(const WorldDev &W, int hm, const float *win, int wx0, int wy0, float x,
+__device__ __forceinline__ float ground_win(const HmView &H, int hm, const float *win, int wx0, int wy0, float x,
                                             float y) {
     if (FLAT || hm < 0) return 0.f;
-    const float fx = __fmul_rn(__fsub_rn(x, W.hm_ox), W.hm_scale);
-    const float fy = __fmul_rn(__fsub_rn(y, W.hm_oy), W.hm_scale);
+    const float fx = __fmul_rn(__fsub_rn(x, H.ox), H.scale);
+    const float fy = __fmul_rn(__fsub_rn(y, H.oy), H.scale);
     int ix = __float2int_rd(fx), iy = __float2int_rd(fy);
     const unsigned ux = (unsigned)ix - (unsigned)wx0, uy = (unsigned)iy - (unsigned)wy0;
     if (ux < (unsigned)HM_WIN && uy < (unsigned)HM_WIN) return win[uy * HM_WIN + ux];
-    ix = min(max(ix, 0), W.hm_nx - 1);
-    iy = min(max(iy, 0), W.hm_ny - 1);
-    return __ldg(W.hm + ((size_t)hm * W.hm_ny + iy) * W.hm_nx + ix);
+    ix = min(max(ix, 0), H.nx - 1);
+    iy = min(max(iy, 0), H.ny - 1);
+    return __ldg(H.hm + ((size_t)hm * H.ny + iy) * H.nx + ix);
 }
 
 // ------------------------------------------------------------------------ actuators (Sec. III-B)
@@ -712,7 +760,7 @@ __device__ __forceinline__ void arena_wrench(const WorldDev &W, unsigned char *x
 // least squares of Eqs. 1-6 as written, with no test of the options in the step loop; ARENA:
 // robot-robot contact within arenas (below)
 template <int LPS, bool FLAT, bool OPT, bool ARENA>
-__device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *fr, float *th,
+__device__ __forceinline__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *fr, float *th,
                           float *th_old, float4 *tb, int n_steps, long long step0, unsigned char *xch,
                           int sbytes) {
     const bool valid = s >= 0;
@@ -771,7 +819,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             const float x = c[0] + (R0[0] * r.x + R0[1] * r.y + R0[2] * r.z);
             const float y = c[1] + (R0[3] * r.x + R0[4] * r.y + R0[5] * r.z);
             const float z = c[2] + (R0[6] * r.x + R0[7] * r.y + R0[8] * r.z);
-            if (z < ground<FLAT>(W, hm, x, y)) kprev |= 1ull << k;
+            if (z < ground<FLAT>(hm_view(W), hm, x, y)) kprev |= 1ull << k;
         }
     }
     // sh is written by the (out-of-line) shape update through a reference, so it lives in local
@@ -785,12 +833,16 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
     int wx0 = -(1 << 24), wy0 = -(1 << 24);
     const int ntiles = (np + LPS - 1) / LPS;
 
+    // the world's parameters the step loop reads, in registers
     const float dt = W.dt, idt = 1.0f / W.dt, kw2 = W.kw2, kc = W.kc;
+    const float gx = W.gx, gy = W.gy, gz = W.gz;
+    const int K = W.K, act_mode = W.act_mode;
+    const HmView H = hm_view(W);
     // friction-model options (Sec. III-C, the refinements named after Eq. 6): rows weighted by
     // the normal forces; the friction impulse's torque about the horizontal axes
     const bool weighted = OPT && (W.fric_mode & 1) != 0, tilt = OPT && (W.fric_mode & 2) != 0;
     float iM = 1.0f / shr.M;
-    const bool actuated = W.act_mode != 0;
+    const bool actuated = act_mode != 0;
     // Candidate tiles: those whose box came within CULL_MARGIN of the highest ground at the last
     // cull.  slack is the height above the highest ground of the lowest box left out then, minus
     // a bound on how far any point has moved down since
@@ -799,11 +851,26 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
     // exact and the boxes are tested again only when it runs out or the shape changes.
     float slack = -1.f;
     uint64_t cand = 0;
-    int ph = (int)(step0 % (long long)W.K);
+    // The first NSLOT candidate tiles live in registers: slot s holds this lane's point of the s-th
+    // candidate tile (its offset r and mass) and that tile's bit in the contact masks (0: no
+    // point).  The contact pass runs over the slots unrolled, with no loads and no data-dependent
+    // branch; candidate tiles beyond the slots (rare) go through a loop over shared memory.  Slots
+    // and overflow together visit the candidate tiles in ascending order, as a single loop would, so
+    // the sums see the same terms in the same order whatever the slots hold.
+    constexpr int NSLOT = ARENA ? 1 : (LPS == 4 ? 4 : (LPS == 8 ? 3 : 2));
+    float4 sp[NSLOT];
+    uint64_t sbit[NSLOT];
+#pragma unroll
+    for (int s = 0; s < NSLOT; ++s) { sp[s] = make_float4(0.f, 0.f, 0.f, 0.f); sbit[s] = 0ull; }
+    uint64_t over = 0;
+    // reference of the friction-set moments: the first tile holding a point in contact last step
+    // (a function of the state alone); the same on every lane of the group
+    int kf = group_first_tile<LPS>(kprev);
+    int ph = (int)(step0 % (long long)K);
     for (int t = 0; t < n_steps; ++t) {
         const long long n = step0 + t;
         const bool tick = actuated && ph == 0;
-        ph = (ph + 1 == W.K) ? 0 : ph + 1;
+        ph = (ph + 1 == K) ? 0 : ph + 1;
         float R[9];
         quat_mat(q, R);
 
@@ -812,7 +879,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         float gold[3] = {0.f, 0.f, 0.f};
         if (tick) {
             gold[0] = shr.g[0]; gold[1] = shr.g[1]; gold[2] = shr.g[2];
-            const bool gp = W.act_mode == 2;
+            const bool gp = act_mode == 2;
             if (gp) {
                 // the controller reads the foot contacts of the last step and sets the targets
                 uint32_t sens = 0;
@@ -842,11 +909,13 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
                 chunk_boxes_body<LPS>(W, c0, nc, fr, shr.g, lbb, gl);
             }
             iM = 1.0f / shr.M;
-            slack = -1.f;   // the tiles moved: cull again
+            slack = -1.f;   // the tiles moved: cull again (and reload the slots)
         }
 
+        // world-frame inverse inertia R Ib^-1 R^T: angular velocity now and after integration
+        const Sym Wi = world_tensor(R, shr.Ii);
         float om[3];
-        world_sym(R, shr.Ii, L, om);
+        sym_mul(Wi, L, om);
 
         // -- (arenas) contact forces and their torques about the CoG from the other robots
         float rf[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -861,18 +930,18 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         if (!FLAT) {
             // move the height-map window when the CoG's cell has drifted from its centre (the
             // groups of the warp refresh together; each loads only its own window)
-            const int cx = __float2int_rd(__fmul_rn(__fsub_rn(c[0], W.hm_ox), W.hm_scale));
-            const int cy = __float2int_rd(__fmul_rn(__fsub_rn(c[1], W.hm_oy), W.hm_scale));
+            const int cx = __float2int_rd(__fmul_rn(__fsub_rn(c[0], H.ox), H.scale));
+            const int cy = __float2int_rd(__fmul_rn(__fsub_rn(c[1], H.oy), H.scale));
             const bool need = hm >= 0 && (wx0 < 0 || abs(cx - (wx0 + HM_WIN / 2)) > HM_DRIFT ||
                                           abs(cy - (wy0 + HM_WIN / 2)) > HM_DRIFT);
             if (__any_sync(FULL_MASK, need)) {
                 if (need) {
-                    wx0 = min(max(cx - HM_WIN / 2, 0), max(W.hm_nx - HM_WIN, 0));
-                    wy0 = min(max(cy - HM_WIN / 2, 0), max(W.hm_ny - HM_WIN, 0));
-                    const float *map = W.hm + (size_t)hm * W.hm_ny * W.hm_nx;
+                    wx0 = min(max(cx - HM_WIN / 2, 0), max(H.nx - HM_WIN, 0));
+                    wy0 = min(max(cy - HM_WIN / 2, 0), max(H.ny - HM_WIN, 0));
+                    const float *map = H.hm + (size_t)hm * H.ny * H.nx;
                     for (int e = gl; e < HM_WIN * HM_WIN; e += LPS) {
                         const int iy = wy0 + e / HM_WIN, ix = wx0 + e % HM_WIN;
-                        win[e] = __ldg(map + (size_t)min(iy, W.hm_ny - 1) * W.hm_nx + min(ix, W.hm_nx - 1));
+                        win[e] = __ldg(map + (size_t)min(iy, H.ny - 1) * H.nx + min(ix, H.nx - 1));
                     }
                 }
                 __syncwarp();
@@ -885,12 +954,20 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             float zfar;
             cand = tiles_near_ground<LPS>(tb, ntiles, R, c[2], hmax + CULL_MARGIN, gl, zfar);
             slack = fminf(zfar - hmax, 1e30f);
-        }
-        // reference o of the friction-set moments: the rotated centre of the first tile holding a
-        // point that was in contact last step (C is a subset of those; o depends on the state alone)
-        int kf = kprev ? __ffsll((long long)kprev) - 1 : 64;
+            // the lowest NSLOT candidate tiles into the slots, the rest to the overflow loop
+            uint64_t rest = cand;
 #pragma unroll
-        for (int ofs = LPS / 2; ofs > 0; ofs >>= 1) kf = min(kf, __shfl_xor_sync(FULL_MASK, kf, ofs));
+            for (int sl = 0; sl < NSLOT; ++sl) {
+                const int tl = rest ? __ffsll((long long)rest) - 1 : 0;
+                const int i = tl * LPS + gl;
+                const bool ok = rest != 0ull && i < np;
+                const float4 pv = pts[ok ? i : 0];
+                sp[sl] = ok ? pv : make_float4(0.f, 0.f, 0.f, 0.f);
+                sbit[sl] = ok ? 1ull << tl : 0ull;
+                rest &= rest - 1;
+            }
+            over = rest;
+        }
         float o[3] = {0.f, 0.f, 0.f};
         if (kf < 64) {
             const float4 lo = tb[2 * kf], hi = tb[2 * kf + 1];
@@ -899,54 +976,39 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         }
         // FN, tau_x, tau_y | n | sum d (3) | sum d d^T (xx yy zz xy xz yz)
         float acc[13] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        // The 64-bit tile masks are walked as two 32-bit words (hexapod candidates sit in the low
-        // word: points are stored by construction height).  Two tiles per iteration: two
-        // independent chains; a point that is absent, not in contact or not in C adds an exact
-        // zero, so the sums see the same terms in the same order.
-        uint32_t knw[2] = {0u, 0u};
+        uint64_t know = 0;
+        // a point that is absent, not in contact or not in C adds an exact zero
+        auto contact_point = [&](const float4 p, uint64_t bit) {
+            const float rx = R[0] * p.x + R[1] * p.y + R[2] * p.z;
+            const float ry = R[3] * p.x + R[4] * p.y + R[5] * p.z;
+            const float rz = R[6] * p.x + R[7] * p.y + R[8] * p.z;
+            const float z = c[2] + rz;
+            const float h = ground_win<FLAT>(H, hm, win, wx0, wy0, c[0] + rx, c[1] + ry);
+            const bool in = bit != 0ull && z < h;
+            const float vz = v[2] + (om[0] * ry - om[1] * rx);
+            const float F = in ? fmaxf(0.f, p.w * (kw2 * (h - z) - kc * vz)) : 0.f;
+            know |= in ? bit : 0ull;
+            acc[0] += F; acc[1] += ry * F; acc[2] -= rx * F;
+            // friction set C: in contact now and last step; a row's weight is 1, or its normal
+            // force with force-weighted friction.  Sums: weight, weight x d, weight x d d^T
+            const float w = (in && (kprev & bit)) ? (weighted ? F : 1.f) : 0.f;
+            const float d0 = rx - o[0], d1 = ry - o[1], d2 = rz - o[2];
+            const float a0 = w * d0, a1 = w * d1, a2 = w * d2;
+            acc[3] += w;
+            acc[4] += a0; acc[5] += a1; acc[6] += a2;
+            acc[7] += a0 * d0; acc[8] += a1 * d1; acc[9] += a2 * d2;
+            acc[10] += a0 * d1; acc[11] += a0 * d2; acc[12] += a1 * d2;
+        };
 #pragma unroll
-        for (int hw = 0; hw < 2; ++hw) {
-            const uint32_t kp = (uint32_t)(kprev >> (32 * hw));
-            for (uint32_t tm = (uint32_t)(cand >> (32 * hw)); tm;) {
-                const int ja = __ffs(tm) - 1;
-                tm &= tm - 1;
-                const bool two = tm != 0;
-                const int jb = two ? __ffs(tm) - 1 : ja;
-                if (two) tm &= tm - 1;
-                const int ia = gl + (ja + 32 * hw) * LPS, ib = gl + (jb + 32 * hw) * LPS;
-                const bool oka = ia < np, okb = two && ib < np;
-                const float4 pa = pts[oka ? ia : 0], pb = pts[okb ? ib : 0];
-                const float rxa = R[0] * pa.x + R[1] * pa.y + R[2] * pa.z, rxb = R[0] * pb.x + R[1] * pb.y + R[2] * pb.z;
-                const float rya = R[3] * pa.x + R[4] * pa.y + R[5] * pa.z, ryb = R[3] * pb.x + R[4] * pb.y + R[5] * pb.z;
-                const float rza = R[6] * pa.x + R[7] * pa.y + R[8] * pa.z, rzb = R[6] * pb.x + R[7] * pb.y + R[8] * pb.z;
-                const float za = c[2] + rza, zb = c[2] + rzb;
-                const float ha = ground_win<FLAT>(W, hm, win, wx0, wy0, c[0] + rxa, c[1] + rya);
-                const float hb = ground_win<FLAT>(W, hm, win, wx0, wy0, c[0] + rxb, c[1] + ryb);
-                const bool ca = oka && za < ha, cb = okb && zb < hb;
-                const float vza = v[2] + (om[0] * rya - om[1] * rxa), vzb = v[2] + (om[0] * ryb - om[1] * rxb);
-                const float Fa = ca ? fmaxf(0.f, pa.w * (kw2 * (ha - za) - kc * vza)) : 0.f;
-                const float Fb = cb ? fmaxf(0.f, pb.w * (kw2 * (hb - zb) - kc * vzb)) : 0.f;
-                knw[hw] |= (ca ? 1u << ja : 0u) | (cb ? 1u << jb : 0u);
-                acc[0] += Fa; acc[1] += rya * Fa; acc[2] -= rxa * Fa;
-                acc[0] += Fb; acc[1] += ryb * Fb; acc[2] -= rxb * Fb;
-                // friction set C: in contact now and last step; a row's weight is 1, or its normal
-                // force with force-weighted friction.  Sums: weight, weight x d, weight x d d^T
-                const float wa = (ca && ((kp >> ja) & 1u)) ? (weighted ? Fa : 1.f) : 0.f;
-                const float wb = (cb && ((kp >> jb) & 1u)) ? (weighted ? Fb : 1.f) : 0.f;
-                const float da0 = rxa - o[0], da1 = rya - o[1], da2 = rza - o[2];
-                const float db0 = rxb - o[0], db1 = ryb - o[1], db2 = rzb - o[2];
-                const float a0 = wa * da0, a1 = wa * da1, a2 = wa * da2;
-                const float b0 = wb * db0, b1 = wb * db1, b2 = wb * db2;
-                acc[3] += wa; acc[3] += wb;
-                acc[4] += a0; acc[5] += a1; acc[6] += a2;
-                acc[4] += b0; acc[5] += b1; acc[6] += b2;
-                acc[7] += a0 * da0; acc[8] += a1 * da1; acc[9] += a2 * da2;
-                acc[10] += a0 * da1; acc[11] += a0 * da2; acc[12] += a1 * da2;
-                acc[7] += b0 * db0; acc[8] += b1 * db1; acc[9] += b2 * db2;
-                acc[10] += b0 * db1; acc[11] += b0 * db2; acc[12] += b1 * db2;
-            }
+        for (int sl = 0; sl < NSLOT; ++sl) contact_point(sp[sl], sbit[sl]);
+        for (uint64_t tm = over; tm; tm &= tm - 1) {   // candidate tiles beyond the slots
+            const int tl = __ffsll((long long)tm) - 1;
+            const int i = tl * LPS + gl;
+            const bool ok = i < np;
+            contact_point(pts[ok ? i : 0], ok ? 1ull << tl : 0ull);
         }
-        const uint64_t know = (uint64_t)knw[0] | ((uint64_t)knw[1] << 32);
+        // the reference tile of the next step, if this step commits (overlaps the reduction)
+        const int kf_next = group_first_tile<LPS>(know);
         gsum<LPS, 13>(acc);
         const float FN = acc[0];
         // friction set: count, centroid of rho and second central moments sum (rho - gb)(rho - gb)^T
@@ -959,9 +1021,9 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
 
         // -- semi-implicit Euler
         float vs[3], Ls[3], cs[3], qs[4], oms[3];
-        vs[0] = v[0] + dt * W.gx;
-        vs[1] = v[1] + dt * W.gy;
-        vs[2] = v[2] + dt * (W.gz + FN * iM);
+        vs[0] = v[0] + dt * gx;
+        vs[1] = v[1] + dt * gy;
+        vs[2] = v[2] + dt * (gz + FN * iM);
         Ls[0] = L[0] + dt * acc[1];
         Ls[1] = L[1] + dt * acc[2];
         Ls[2] = L[2];
@@ -969,7 +1031,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             vs[0] += dt * (rf[0] * iM); vs[1] += dt * (rf[1] * iM); vs[2] += dt * (rf[2] * iM);
             Ls[0] += dt * rf[3]; Ls[1] += dt * rf[4]; Ls[2] += dt * rf[5];
         }
-        world_sym(R, shr.Ii, Ls, oms);
+        sym_mul(Wi, Ls, oms);
         cs[0] = c[0] + dt * vs[0]; cs[1] = c[1] + dt * vs[1]; cs[2] = c[2] + dt * vs[2];
         // rotation increment dR = exp([u]x), u = dt w*: q* = dq (x) q and R* = dR R, so a point's
         // offset moves from rho to (1 + D) rho with D = dR - 1 = a [u]x + b [u]x^2
@@ -977,35 +1039,51 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
         float Dm[6];   // rows 0 and 1 of D (only horizontal displacements are needed)
         float rzc = 0.f;   // (with the horizontal-axis friction torque) height of the integrated
                            // friction-set centroid above the integrated CoG: [(1 + D) gb]_z
+        float Iz[3];   // R* Ib R*^T z: the angular momentum of a unit yaw rate after integration
         {
             const float px = dt * oms[0], py = dt * oms[1], pz = dt * oms[2];
             const float a2 = px * px + py * py + pz * pz;
-            const float ra = a2 > 0.f ? rsqrtf(a2) : 0.f;   // 1 / |u|
-            const float a = a2 * ra;
-            float dq[4] = {1.f, 0.f, 0.f, 0.f};
-            float fa = 1.f, fb = 0.5f;
-            if (a > 0.f) {
-                float sn, cn;
-                sincos_small(0.5f * a, &sn, &cn);
-                const float f = sn * ra;
-                dq[0] = cn; dq[1] = f * px; dq[2] = f * py; dq[3] = f * pz;
-                fa = 2.f * f * cn;
+            float dq[4], fa, fb;
+            if (a2 <= 1.f / 64.f) {
+                // |u| <= 1/8: the series of sin|u|/|u|, (1 - cos|u|)/|u|^2 and of the half angle
+                // in |u|^2, exact to single precision (no square root, no range reduction)
+                fa = sinc_sq(a2);
+                fb = cosc_sq(a2);
+                const float h2 = 0.25f * a2, f = 0.5f * sinc_sq(h2);
+                dq[0] = 1.f - h2 * cosc_sq(h2);
+                dq[1] = f * px; dq[2] = f * py; dq[3] = f * pz;
+            } else {
+                const float ra = rsqrtf(a2), a = a2 * ra;
+                const float2 sc2 = sincos_large(0.5f * a);
+                const float f = sc2.x * ra;
+                dq[0] = sc2.y; dq[1] = f * px; dq[2] = f * py; dq[3] = f * pz;
+                fa = 2.f * f * sc2.y;
                 fb = 2.f * f * f;
             }
-            if (tilt)
-                rzc = gb[2] + (-fa * py + fb * pz * px) * gb[0] + (fa * px + fb * pz * py) * gb[1] +
-                      fb * (pz * pz - a2) * gb[2];
             // [u]x^2 = u u^T - |u|^2 1
             Dm[0] = fb * (px * px - a2); Dm[1] = -fa * pz + fb * px * py; Dm[2] = fa * py + fb * px * pz;
             Dm[3] = fa * pz + fb * py * px; Dm[4] = fb * (py * py - a2); Dm[5] = -fa * px + fb * py * pz;
+            if (tilt)
+                rzc = gb[2] + (-fa * py + fb * pz * px) * gb[0] + (fa * px + fb * pz * py) * gb[1] +
+                      fb * (pz * pz - a2) * gb[2];
             quat_mul(dq, q, qs);
-            const float inv = rsqrtf(qs[0] * qs[0] + qs[1] * qs[1] + qs[2] * qs[2] + qs[3] * qs[3]);
+            // renormalise: |q*|^2 = 1 + eps with eps a few roundings, and 1 / sqrt(1 + eps) =
+            // 1 - eps / 2 to within 3 eps^2 / 8; larger deviations take the square root
+            const float n2 = qs[0] * qs[0] + qs[1] * qs[1] + qs[2] * qs[2] + qs[3] * qs[3];
+            const float inv = fabsf(n2 - 1.f) < 1e-4f ? fmaf(-0.5f, n2, 1.5f) : rsqrtf(n2);
             qs[0] *= inv; qs[1] *= inv; qs[2] *= inv; qs[3] *= inv;
             // largest downward move of any point this step: dt max(0, -v*_z) from the CoG plus the
             // rotation's: for x = R r, ((dR - 1) x)_z = sin|u| (n x x)_z + (1 - cos|u|) (n (n.x) - x)_z
             // with n = u / |u|, so |dz| <= (|u_xy| + |u|^2 / 2) |x| (yaw moves no point up or
             // down; |u_xy| <= |u_x| + |u_y|); a small factor covers rounding
             slack -= fmaxf(0.f, -dt * vs[2]) + 1.0001f * (fabsf(px) + fabsf(py) + 0.5f * a2) * rmax;
+            // independent of the friction solve: R* Ib R*^T z = R* (Ib (R*^T z))
+            float Rs[9];
+            quat_mat(qs, Rs);
+            const float rz3[3] = {Rs[6], Rs[7], Rs[8]};
+            float t3[3];
+            sym_mul(shr.Ib, rz3, t3);
+            mat_vec(Rs, t3, Iz);
         }
 
         // -- friction (Sec. III-C, Eqs. 1-6) over C.  With d_i = rho_i - centroid and
@@ -1041,7 +1119,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
                 if (weighted) {
                     const float rz = R[6] * r.x + R[7] * r.y + R[8] * r.z;
                     const float z = c[2] + rz;
-                    const float h = ground_win<FLAT>(W, hm, win, wx0, wy0, c[0] + rx, c[1] + ry);
+                    const float h = ground_win<FLAT>(H, hm, win, wx0, wy0, c[0] + rx, c[1] + ry);
                     const float vz = v[2] + (om[0] * ry - om[1] * rx);
                     wk = fmaxf(0.f, r.w * (kw2 * (h - z) - kc * vz));
                 }
@@ -1070,26 +1148,46 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             // cancellation when the weight sits on one point)
             float a3 = (weighted ? S2 > 1e-6f * nC : (nC >= 2.f && S2 > 1e-12f)) ? __fdividef(X, S2) : 0.f;
             a3 = fminf(fmaxf(a3, -1.f), 1.f);
-            const float t1 = fmaxf(0.f, 1.f - a3 * a3);
-            const float cD = t1 > 0.f ? t1 * rsqrtf(t1) : 0.f;       // cos(alpha_D)
-            const float r1 = __fdividef(1.f, 1.f + cD);
-            const float cm1 = -a3 * a3 * r1;                          // cos(alpha_D) - 1
+            const float x3 = a3 * a3;
+            // r1 = 1 / (1 + cos alpha_D) and alpha_D = asin(a3): series in a3^2 for |a3| <= 1/16
+            // (exact to single precision), the library otherwise
+            float r1, aD;
+            if (x3 <= 1.f / 256.f) {
+                r1 = fmaf(x3, fmaf(x3, fmaf(x3, 5.f / 128.f, 1.f / 16.f), 1.f / 8.f), 0.5f);
+                aD = a3 * fmaf(x3, fmaf(x3, fmaf(x3, 5.f / 112.f, 3.f / 40.f), 1.f / 6.f), 1.f);
+            } else {
+                const float t1 = fmaxf(0.f, 1.f - x3);
+                const float cD = t1 > 0.f ? t1 * rsqrtf(t1) : 0.f;       // cos(alpha_D)
+                r1 = __fdividef(1.f, 1.f + cD);
+                aD = asin_large(a3);
+            }
+            const float cm1 = -x3 * r1;                               // cos(alpha_D) - 1
             const float dDx = -sbx, dDy = -sby;                       // CoG minus centroid
             const float DDx = tDx + cm1 * dDx - a3 * dDy;             // uncapped CoG shift
             const float DDy = tDy + a3 * dDx + cm1 * dDy;
-            // maximum static friction (Coulomb cap on the impulse that undoes the slip)
-            const float sh2 = 0.5f * a3 * a3 * r1;                    // sin^2(alpha_D / 2)
+            // maximum static friction (Coulomb cap on the impulse that undoes the slip):
+            // J_req = M u / dt with u^2 the mean squared corrective displacement, compared as
+            // squares; a capped correction is scaled by J_max / J_req
+            const float sh2 = 0.5f * x3 * r1;                         // sin^2(alpha_D / 2)
             const float u2 = tDx * tDx + tDy * tDy + 4.f * sh2 * S2 * in;
-            const float Jreq = shr.M * (u2 > 0.f ? u2 * rsqrtf(u2) : 0.f) * idt;
             const float Jmax = mu * dt * FN;
-            const float sc = (Jreq <= Jmax) ? 1.f : __fdividef(Jmax, Jreq);
-            const float aD = asin_small(a3);
-            float s1, c1;
-            sincos_small(0.5f * sc * aD, &s1, &c1);
-            const float sin1 = 2.f * s1 * c1, cm1s = -2.f * s1 * s1;
+            const float Mi = shr.M * idt;
+            const float sc = (Mi * Mi * u2 <= Jmax * Jmax) ? 1.f : Jmax * rsqrtf(u2) * (dt * iM);
+            const float AD = sc * aD;
+            float sin1, cm1s;   // sin(sc alpha_D), cos(sc alpha_D) - 1
+            const float y1 = AD * AD;
+            if (y1 <= 1.f / 64.f) {
+                sin1 = AD * sinc_sq(y1);
+                cm1s = -y1 * cosc_sq(y1);
+            } else {
+                float s1, c1;
+                sincos_small(0.5f * AD, &s1, &c1);
+                sin1 = 2.f * s1 * c1;
+                cm1s = -2.f * s1 * s1;
+            }
             float dx1 = sc * tDx + cm1s * dDx - sin1 * dDy;
             float dy1 = sc * tDy + sin1 * dDx + cm1s * dDy;
-            float A = sc * aD;
+            float A = AD;
             if (tick) {
                 const float kbx = f6[0] * in, kby = f6[1] * in;
                 const float S2K = f6[2] - nC * (kbx * kbx + kby * kby);
@@ -1113,12 +1211,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             vn[0] = vs[0] + sc * DDx * idt;
             vn[1] = vs[1] + sc * DDy * idt;
             // angular momentum of the yaw correction: (sc alpha_D / dt) R* Ib R*^T z
-            float Rs[9];
-            quat_mat(qs, Rs);
-            const float ez[3] = {0.f, 0.f, 1.f};
-            float Iz[3];
-            world_sym(Rs, shr.Ib, ez, Iz);
-            const float w = sc * aD * idt;
+            const float w = AD * idt;
             Ln[0] = Ls[0] + w * Iz[0]; Ln[1] = Ls[1] + w * Iz[1]; Ln[2] = Ls[2] + w * Iz[2];
             if (tilt) {
                 // the friction impulse J = M (v_new - v*) acts at the friction-set centroid,
@@ -1127,23 +1220,32 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
                 Ln[0] -= rzc * Jy;
                 Ln[1] += rzc * Jx;
             }
+            // yaw by A: q = (cos A/2, 0, 0, sin A/2) (x) q*
             float sa, ca;
-            sincos_small(0.5f * A, &sa, &ca);
-            const float qz[4] = {ca, 0.f, 0.f, sa};
-            quat_mul(qz, qs, qn);
+            const float y2 = 0.25f * A * A;
+            if (y2 <= 1.f / 64.f) {
+                sa = 0.5f * A * sinc_sq(y2);
+                ca = 1.f - y2 * cosc_sq(y2);
+            } else {
+                sincos_small(0.5f * A, &sa, &ca);
+            }
+            qn[0] = ca * qs[0] - sa * qs[3];
+            qn[1] = ca * qs[1] - sa * qs[2];
+            qn[2] = ca * qs[2] + sa * qs[1];
+            qn[3] = ca * qs[3] + sa * qs[0];
         }
 
         // -- freeze a scene whose state is no longer finite or has left any sane range
         if (status == 0u) {
             // any NaN or infinity makes the sum non-finite (all terms are bounded below 1e6
             // in magnitude when finite, so the sum itself cannot overflow)
-            const float chk = cn[0] + cn[1] + cn[2] + vn[0] + vn[1] + vn[2] + Ln[0] + Ln[1] +
-                              Ln[2] + qn[0] + qn[1] + qn[2] + qn[3];
-            const bool fin = isfinite(chk);
-            if (!fin) {
+            const float chk = (((cn[0] + cn[1]) + (cn[2] + vn[0])) + ((vn[1] + vn[2]) + (Ln[0] + Ln[1]))) +
+                              (((Ln[2] + qn[0]) + (qn[1] + qn[2])) + qn[3]);
+            const float vmax = fmaxf(fmaxf(fabsf(vn[0]), fabsf(vn[1])), fabsf(vn[2]));
+            const float cmax = fmaxf(fmaxf(fabsf(cn[0]), fabsf(cn[1])), fabsf(cn[2]));
+            if (!isfinite(chk)) {
                 status |= 1u;
-            } else if (fabsf(vn[0]) > 1e3f || fabsf(vn[1]) > 1e3f || fabsf(vn[2]) > 1e3f ||
-                       fabsf(cn[0]) > 1e6f || fabsf(cn[1]) > 1e6f || fabsf(cn[2]) > 1e6f) {
+            } else if (vmax > 1e3f || cmax > 1e6f) {
                 status |= 2u;
             } else {
 #pragma unroll
@@ -1151,6 +1253,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
 #pragma unroll
                 for (int i = 0; i < 4; ++i) q[i] = qn[i];
                 kprev = know;
+                kf = kf_next;
             }
         }
     }
@@ -1212,9 +1315,9 @@ __device__ __forceinline__ void step_body(const WorldDev &W, int n_steps, int sb
     }
 }
 
-// Flat ground: up to 16 warps per block, 128 registers a thread.
+// Flat ground: 168 registers a thread (the contact slots live in registers), up to 12 warps per block.
 template <int LPS, bool OPT>
-__global__ void __launch_bounds__(512) step_kernel(const __grid_constant__ WorldDev W, int n_steps, int sbytes) {
+__global__ void __maxnreg__(168) step_kernel(const __grid_constant__ WorldDev W, int n_steps, int sbytes) {
     step_body<LPS, true, OPT, false>(W, n_steps, sbytes);
 }
 
@@ -1639,7 +1742,7 @@ __global__ void __launch_bounds__(256) sensor_probe_kernel(const __grid_constant
         const float px = c[0] + R[0] * r.x + R[1] * r.y + R[2] * r.z;
         const float py = c[1] + R[3] * r.x + R[4] * r.y + R[5] * r.z;
         const float pz = c[2] + R[6] * r.x + R[7] * r.y + R[8] * r.z;
-        if (pz < ground<FLAT>(W, hm, px, py)) bits |= 1u << (int)r.w;
+        if (pz < ground<FLAT>(hm_view(W), hm, px, py)) bits |= 1u << (int)r.w;
     }
     bits = gor<32>(bits);
     if (lane == 0) sens_new[s] = bits;
@@ -1648,7 +1751,7 @@ __global__ void __launch_bounds__(256) sensor_probe_kernel(const __grid_constant
 // One thread per scene: keep the candidate state if the contact sensors did not change, otherwise
 // leave the scene at its state and append it to the fallback list (the plain step takes it).
 __global__ void __launch_bounds__(256) surrogate_commit_kernel(const __grid_constant__ WorldDev W, const float *nx, const uint8_t *applied,
-                                                               const uint32_t *sens_new, int *list, int *count) {
+                                                               const uint32_t *sens_new, int *list, int *count, int *fb) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const bool app = s < W.S && applied[s];
     const bool fall = app && sens_new[s] != W.sensors[s];
@@ -1660,7 +1763,10 @@ __global__ void __launch_bounds__(256) surrogate_commit_kernel(const __grid_cons
         if (lane == __ffs(m) - 1) base = atomicAdd(count, __popc(m));
         base = __shfl_sync(FULL_MASK, base, __ffs(m) - 1);
     }
-    if (fall) list[base + __popc(m & ((1u << lane) - 1u))] = s;
+    if (fall) {
+        list[base + __popc(m & ((1u << lane) - 1u))] = s;
+        fb[s] += 1;   // one thread per scene
+    }
     if (!app || fall) return;
     const int S = W.S;
 #pragma unroll
@@ -1700,7 +1806,7 @@ __global__ void __launch_bounds__(128) kappa_refresh_kernel(const __grid_constan
             const float px = x.c[0] + R[0] * r.x + R[1] * r.y + R[2] * r.z;
             const float py = x.c[1] + R[3] * r.x + R[4] * r.y + R[5] * r.z;
             const float pz = x.c[2] + R[6] * r.x + R[7] * r.y + R[8] * r.z;
-            const bool kap = pz < ground<FLAT>(W, hm, px, py);
+            const bool kap = pz < ground<FLAT>(hm_view(W), hm, px, py);
             W.kappa[p0 + k] = kap ? 1 : 0;
             if (kap) {
                 const int sid = W.links[l0 + W.plink[p0 + k]].sensor;
@@ -1754,7 +1860,7 @@ cudaError_t launch_features(const WorldDev &W, const SurCache &C, const Surrogat
 
 cudaError_t launch_surrogate_update(const WorldDev &W, const SurCache &C, const float *Y, int ldy, const float *t_mu,
                                     const float *t_sd, float *nx, uint8_t *applied, uint32_t *sens_new, int *list,
-                                    int *count, cudaStream_t st) {
+                                    int *count, int *fb, cudaStream_t st) {
     const unsigned bs = (unsigned)((W.S + 255) / 256);
     surrogate_apply_kernel<<<bs, 256, 0, st>>>(W, C, Y, ldy, t_mu, t_sd, nx, applied);
     cudaError_t e = cudaGetLastError();
@@ -1766,7 +1872,7 @@ cudaError_t launch_surrogate_update(const WorldDev &W, const SurCache &C, const 
         sensor_probe_kernel<true><<<bp, 256, 0, st>>>(W, C, nx, applied, sens_new);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    surrogate_commit_kernel<<<bs, 256, 0, st>>>(W, nx, applied, sens_new, list, count);
+    surrogate_commit_kernel<<<bs, 256, 0, st>>>(W, nx, applied, sens_new, list, count, fb);
     return cudaGetLastError();
 }
 
@@ -1866,6 +1972,7 @@ static void *step_fn() { return FLAT ? (void *)step_kernel<LPS, OPT> : (void *)s
 template <bool OPT>
 static void *pick_step_opt(int lps, bool flat) {
     switch (lps) {
+        case 4: return flat ? step_fn<4, true, OPT>() : step_fn<4, false, OPT>();
         case 8: return flat ? step_fn<8, true, OPT>() : step_fn<8, false, OPT>();
         case 16: return flat ? step_fn<16, true, OPT>() : step_fn<16, false, OPT>();
         case 32: return flat ? step_fn<32, true, OPT>() : step_fn<32, false, OPT>();

@@ -136,6 +136,7 @@ struct npx_world {
         uint8_t *applied = nullptr;           // [S]
         uint32_t *sens_new = nullptr;         // [S]
         int *list = nullptr, *count = nullptr;
+        int *fb = nullptr;                    // [S] windows of each scene that fell back
         long long *total = nullptr;
         cudaEvent_t ev_w = nullptr, ev_n = nullptr;
         int rows = 0;
@@ -496,9 +497,11 @@ int surrogate_buffers(npx_world *w) {
         (rc = dev_alloc(w, &w->sg.total, 1)) || (rc = dev_alloc(w, &C.lk, 2 * (size_t)w->S * w->max_links)) ||
         (rc = dev_alloc(w, &C.inert, 12 * (size_t)w->S)) || (rc = dev_alloc(w, &C.nsp_s, w->S)) ||
         (rc = dev_alloc(w, &d_max, 1)) || (rc = dev_alloc(w, &w->sg.nx, 16 * (size_t)w->S)) ||
-        (rc = dev_alloc(w, &w->sg.applied, w->S)) || (rc = dev_alloc(w, &w->sg.sens_new, w->S)))
+        (rc = dev_alloc(w, &w->sg.applied, w->S)) || (rc = dev_alloc(w, &w->sg.sens_new, w->S)) ||
+        (rc = dev_alloc(w, &w->sg.fb, w->S)))
         return rc;
     CUDA_TRY(cudaMemsetAsync(w->sg.count, 0, sizeof(int), w->stream));
+    CUDA_TRY(cudaMemsetAsync(w->sg.fb, 0, sizeof(int) * (size_t)w->S, w->stream));
     CUDA_TRY(cudaMemsetAsync(d_max, 0, sizeof(int), w->stream));
     CUDA_TRY(npx::launch_sensor_points(w->W, C.nsp_s, d_max, w->stream));
     int nsp = 0;
@@ -1332,7 +1335,7 @@ int npx_world_configure(npx_world *w, int lps, int wpb, int blocks, int chunk) {
     CUDA_TRY(cudaSetDevice(w->device));
     npx::LaunchCfg c = w->cfg;
     if (lps) {
-        if (lps != 8 && lps != 16 && lps != 32) return fail(NPX_EINVAL, "lanes per scene must be 8, 16 or 32");
+        if (lps != 4 && lps != 8 && lps != 16 && lps != 32) return fail(NPX_EINVAL, "lanes per scene must be 4, 8, 16 or 32");
         c.lps = lps;
     }
     if (wpb) {
@@ -1520,7 +1523,7 @@ int npx_world_step_surrogate(npx_world *w, npx_mlp *net, const npx_surrogate_nor
             CUDA_TRY(cudaStreamWaitEvent(w->stream, w->sg.ev_n, 0));
         }
         CUDA_TRY(npx::launch_surrogate_update(w->W, C, Y, ldy, nrm->t_mu, nrm->t_sd, w->sg.nx, w->sg.applied,
-                                              w->sg.sens_new, w->sg.list, w->sg.count, w->stream));
+                                              w->sg.sens_new, w->sg.list, w->sg.count, w->sg.fb, w->stream));
         // the fallback: listed scenes kept their state; the plain step takes them through the
         // window from the contacts at that state
         CUDA_TRY(npx::launch_step(Wsub, fcfg, stride, w->stream));
@@ -1541,6 +1544,17 @@ int npx_world_step_surrogate(npx_world *w, npx_mlp *net, const npx_surrogate_nor
     return NPX_OK;
 }
 
+int npx_surrogate_fallback_counts(npx_world *w, int *counts) {
+    if (int rc = check_ready(w)) return rc;
+    if (!counts) return fail(NPX_EINVAL, "null counts");
+    CUDA_TRY(cudaSetDevice(w->device));
+    if (int rc = surrogate_buffers(w)) return rc;
+    CUDA_TRY(cudaMemcpyAsync(counts, w->sg.fb, sizeof(int) * (size_t)w->S, cudaMemcpyDeviceToHost, w->stream));
+    CUDA_TRY(cudaMemsetAsync(w->sg.fb, 0, sizeof(int) * (size_t)w->S, w->stream));
+    CUDA_TRY(cudaStreamSynchronize(w->stream));
+    return NPX_OK;
+}
+
 int npx_world_autotune(npx_world *w, int n_steps, npx_world_info *out) {
     if (int rc = check_ready(w)) return rc;
     if (n_steps < 1) return fail(NPX_EINVAL, "n_steps must be >= 1");
@@ -1557,7 +1571,7 @@ int npx_world_autotune(npx_world *w, int n_steps, npx_world_info *out) {
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
-    const int lps_list[3] = {8, 16, 32};
+    const int lps_list[4] = {4, 8, 16, 32};
     int rc_out = NPX_OK;
     for (auto &cls : w->classes) {
         const npx::WorldDev CW = class_world(w, cls);

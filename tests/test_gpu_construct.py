@@ -43,3 +43,21 @@ def test_constructed_hexapod_200_step_window(mode):
     da = quat_angle(r["quat"], o.q)
     assert ((dc <= 1e-3) & (da <= 1e-3)).mean() >= 0.95
     assert (r["status"] == 0).all()
+
+
+@pytest.mark.parametrize("mode", [1, 3])
+def test_four_lanes_per_scene_per_step_and_window(mode):
+    """Robots of at most 256 points can run with 4 lanes per scene (8 scenes per warp): per-step
+    parity with the oracle, and a 200-step window against 8 lanes per scene."""
+    b = _batch(mode, 64)
+    w = World.from_batch(b, configure=dict(lanes_per_scene=4, warps_per_block=2))
+    assert w.info()["lanes_per_scene"] == 4
+    _assert_step_parity(w, Oracle(b, threads=THREADS), [0, 1, 80, 81, 400], max_near_frac=0.2)
+    w8 = World.from_batch(b, configure=dict(lanes_per_scene=8, warps_per_block=2))
+    w4 = World.from_batch(b, configure=dict(lanes_per_scene=4, warps_per_block=2))
+    w8.step(200)
+    w4.step(200)
+    r8, r4 = w8.read(), w4.read()
+    dc = np.linalg.norm(r4["cog"] - r8["cog"], axis=1)
+    assert ((dc <= 1e-3) & (quat_angle(r4["quat"], r8["quat"]) <= 1e-3)).mean() >= 0.95
+    assert (r4["status"] == 0).all()
