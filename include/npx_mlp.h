@@ -132,6 +132,19 @@ int npx_surrogate_collect(npx_world *w, const npx_surrogate_norm *norm, int stri
  * with arenas are refused (NPX_EINVAL). */
 int npx_world_step_surrogate(npx_world *w, npx_mlp *net, const npx_surrogate_norm *norm, int stride,
                              int n_steps, long long *fallbacks);
+/* Per-scene fallback windows: counts[s] (HOST, n_scenes ints) receives how many of scene s's
+ * surrogate windows fell back to the plain step since the previous call (or since the world's
+ * first surrogate call), and the counters restart at zero.  Synchronises the world's stream.
+ * This is how a caller tells the scenes that stayed on the network from those the plain step
+ * took over, e.g. to state the network's own error apart from the plain step's. */
+int npx_surrogate_fallback_counts(npx_world *w, int *counts);
+
+/* FP64 column statistics of FP32 rows: for X [rows x cols] (DEVICE, row-major), adds the sum and
+ * the sum of squares of every column to sum[cols] and sumsq[cols] (DEVICE, FP64; the caller
+ * zeroes them first).  Each column is summed in a fixed order, so results repeat bit for bit.
+ * Asynchronous on stream (a cudaStream_t).  The surrogate's standardisation statistics and the
+ * zero-predictor loss of training rows use it. */
+int npx_column_moments(const float *X, long long rows, int cols, double *sum, double *sumsq, void *stream);
 
 #ifdef __cplusplus
 }

@@ -146,6 +146,34 @@ __global__ void unpad_kernel(const float *__restrict__ Y, int M, int out_p, int 
 
 inline unsigned blocks_for(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// Column sums and sums of squares in FP64: block x covers 32 columns; thread (tx, ty) sums column
+// 32 x + tx over rows ty, ty + 32, ... (in that order), then thread ty = 0 adds the 32 partial sums
+// in ty order.  Every column is summed in a fixed order by one block: deterministic, no atomics.
+__global__ void __launch_bounds__(1024) column_moments_kernel(const float *__restrict__ X, long long rows, int cols,
+                                                              double *sum, double *sumsq) {
+    __shared__ double red[2][32][33];
+    const int tx = threadIdx.x, ty = threadIdx.y, c = blockIdx.x * 32 + tx;
+    double s = 0.0, q = 0.0;
+    if (c < cols)
+        for (long long r = ty; r < rows; r += 32) {
+            const double v = (double)X[r * cols + c];
+            s += v;
+            q += v * v;
+        }
+    red[0][ty][tx] = s;
+    red[1][ty][tx] = q;
+    __syncthreads();
+    if (ty == 0 && c < cols) {
+        double ts = 0.0, tq = 0.0;
+        for (int k = 0; k < 32; ++k) {
+            ts += red[0][k][tx];
+            tq += red[1][k][tx];
+        }
+        sum[c] += ts;
+        sumsq[c] += tq;
+    }
+}
+
 }  // namespace
 
 struct npx_mlp {
@@ -438,6 +466,15 @@ int npx_mlp_backward(npx_mlp *n, const float *x, const float *t, int M, float *l
             GT = n->dZT[l - 1];
         }
     }
+    return NPX_OK;
+}
+
+int npx_column_moments(const float *X, long long rows, int cols, double *sum, double *sumsq, void *stream) {
+    if (!X || !sum || !sumsq || rows < 0 || cols < 1) return npx::set_last_error(NPX_EINVAL, "npx_column_moments: bad arguments");
+    if (rows == 0) return NPX_OK;
+    column_moments_kernel<<<(cols + 31) / 32, dim3(32, 32), 0, static_cast<cudaStream_t>(stream)>>>(X, rows, cols, sum,
+                                                                                                  sumsq);
+    CU(cudaGetLastError());
     return NPX_OK;
 }
 

@@ -163,6 +163,8 @@ _SIGS = {
     "npx_surrogate_dims": [P, P, P],
     "npx_surrogate_collect": [P, P, I, I, P, P],
     "npx_world_step_surrogate": [P, P, P, I, I, P],
+    "npx_surrogate_fallback_counts": [P, P],
+    "npx_column_moments": [P, C.c_longlong, I, P, P, P],
 }
 
 _lib = None
@@ -535,3 +537,17 @@ def world_step_surrogate(world: "World", net: "MLP", norm: SurrogateNorm, n_step
     _check(_lib.npx_world_step_surrogate(world._h, net._h, C.byref(norm), int(stride), int(n_steps),
                                          C.byref(fb)))
     return fb.value
+
+
+def surrogate_fallback_counts(world: "World") -> np.ndarray:
+    """npx_surrogate_fallback_counts: windows of each scene that fell back since the last call."""
+    out = np.zeros(world.n_scenes, np.int32)
+    _check(_lib.npx_surrogate_fallback_counts(world._h, _p(out)))
+    return out
+
+
+def column_moments(X_ptr, rows: int, cols: int, sum_ptr, sumsq_ptr, stream=None):
+    """npx_column_moments: adds the FP64 column sums and sums of squares of X [rows x cols] (device
+    FP32) to sum / sumsq (device FP64 [cols])."""
+    load()
+    _check(_lib.npx_column_moments(X_ptr, int(rows), int(cols), sum_ptr, sumsq_ptr, stream))
