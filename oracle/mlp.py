@@ -2,31 +2,33 @@
 
 The surrogate is a plain multilayer perceptron: input x (the scene features), hidden layers
 h_l = gelu(W_l h_{l-1} + b_l), linear output y = W_L h_{L-1} + b_L, trained on the mean squared
-error against target deltas with Adam.  GELU is the exact one, gelu(z) = z Phi(z) =
-z (1 + erf(z / sqrt 2)) / 2.  Everything here is written directly from those definitions in
-float64; only the tests and the benchmark's CPU leg use it.
+error against target deltas with Adam.  GELU is its tanh form (Hendrycks and Gimpel give it beside
+the exact z Phi(z), from which it differs by less than 5e-4):
+gelu(z) = z (1 + tanh(sqrt(2 / pi) (z + 0.044715 z^3))) / 2.  Everything here is written directly
+from those definitions in float64; only the tests and the benchmark's CPU leg use it.
 
 Parity pins (tests/test_mlp_oracle.py): gradients against central finite differences, the
-one-layer case against the closed form of linear least squares, GELU against scipy's normal CDF,
-Adam's first step against its closed form (every parameter moves by -lr sign(g)).
+one-layer case against the closed form of linear least squares, GELU against the exact z Phi(z) of
+scipy's normal CDF (within the tanh form's 5e-4), its symmetry gelu(z) - gelu(-z) = z and its
+limits, Adam's first step against its closed form (every parameter moves by -lr sign(g)).
 """
 from __future__ import annotations
 
 import math
 
 import numpy as np
-from scipy.special import erf
 
-SQRT2 = math.sqrt(2.0)
+GELU_K, GELU_C = math.sqrt(2.0 / math.pi), 0.044715
 
 
 def gelu(z):
-    return 0.5 * z * (1.0 + erf(z / SQRT2))
+    return 0.5 * z * (1.0 + np.tanh(GELU_K * (z + GELU_C * z ** 3)))
 
 
 def gelu_grad(z):
-    """d gelu / dz = Phi(z) + z phi(z)."""
-    return 0.5 * (1.0 + erf(z / SQRT2)) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
+    """d gelu / dz = (1 + t) / 2 + z (1 - t^2) k (1 + 3 c z^2) / 2, t = tanh(k (z + c z^3))."""
+    t = np.tanh(GELU_K * (z + GELU_C * z ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * GELU_K * (1.0 + 3.0 * GELU_C * z * z)
 
 
 def init_params(sizes, seed=0):

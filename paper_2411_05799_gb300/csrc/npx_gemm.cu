@@ -148,27 +148,27 @@ __device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[16
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Standard normal CDF Phi(z) = (1 + erf(z / sqrt 2)) / 2, with erf from the rational
-// approximation of Abramowitz & Stegun, Handbook of Mathematical Functions, formula 7.1.26
-// (|error| <= 1.5e-7, far below the BF16 rounding of the outputs).  e = exp(-z^2 / 2), which the
-// approximation needs anyway, is also the Gaussian factor of GELU'.
-__device__ __forceinline__ float norm_cdf(float z, float &e) {
-    const float x = fabsf(z) * 0.70710678118654752f;
-    const float t = __fdividef(1.f, fmaf(0.3275911f, x, 1.f));
-    e = __expf(-x * x);
-    const float p = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
-                             0.254829592f);
-    const float tail = 0.5f * p * e;   // (1 - erf(x)) / 2
-    return z >= 0.f ? 1.f - tail : tail;
+// GELU in its tanh form, gelu(z) = z (1 + tanh(u)) / 2 with u = k (z + c z^3), k = sqrt(2 / pi),
+// c = 0.044715, and its derivative (1 + t) / 2 + z (1 - t^2) k (1 + 3 c z^2) / 2, t = tanh(u).
+// tanh comes from the special-function unit (PTX tanh.approx.f32, relative error about 2^-11):
+// one special-function operation and a few FMAs per element, where the epilogue's element rate
+// bounds the hidden layers' GEMMs.  The error it leaves is of the order of the BF16 rounding of the
+// stored activations.
+__device__ __forceinline__ float tanh_approx(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 __device__ __forceinline__ float gelu(float z) {
-    float e;
-    return z * norm_cdf(z, e);
+    const float t = tanh_approx(z * fmaf(0.035677408136300125f, z * z, 0.7978845608028654f));
+    const float h = 0.5f * z;
+    return fmaf(h, t, h);
 }
-__device__ __forceinline__ float gelu_grad(float z) {   // Phi(z) + z phi(z)
-    float e;
-    const float c = norm_cdf(z, e);
-    return fmaf(z * 0.3989422804014327f, e, c);
+__device__ __forceinline__ float gelu_grad(float z) {
+    const float z2 = z * z;
+    const float t = tanh_approx(z * fmaf(0.035677408136300125f, z2, 0.7978845608028654f));
+    const float du = fmaf(0.10703222440890038f, z2, 0.7978845608028654f);   // k (1 + 3 c z^2)
+    return fmaf(0.5f * z * du, fmaf(-t, t, 1.f), fmaf(0.5f, t, 0.5f));
 }
 
 __device__ __forceinline__ void store_bf16x16(__nv_bfloat16 *o, const float (&v)[16]) {

@@ -8,9 +8,19 @@ from scipy.stats import norm
 from oracle import mlp
 
 
-def test_gelu_is_z_times_normal_cdf():
-    z = np.linspace(-6, 6, 101)
-    np.testing.assert_allclose(mlp.gelu(z), z * norm.cdf(z), rtol=1e-13, atol=1e-15)
+def test_gelu_tanh_form():
+    """The tanh form of GELU stays within 5e-4 of the exact z Phi(z) (scipy's normal CDF) and
+    meets it at the origin and in both tails; gelu(z) - gelu(-z) = z (1 + tanh is odd about 0);
+    gelu'(0) = 1/2; the derivative matches central differences."""
+    z = np.linspace(-8, 8, 1601)
+    exact = z * norm.cdf(z)
+    assert np.abs(mlp.gelu(z) - exact).max() < 5e-4
+    assert np.abs(mlp.gelu(z) - exact).max() > 1e-4          # it is the tanh form, not the erf one
+    assert abs(mlp.gelu(np.array(0.0))) == 0.0
+    np.testing.assert_allclose(mlp.gelu(z[-100:]), z[-100:], rtol=1e-12)
+    np.testing.assert_allclose(mlp.gelu(z[:100]), 0.0, atol=1e-12)
+    np.testing.assert_allclose(mlp.gelu(z) - mlp.gelu(-z), z, rtol=1e-13, atol=1e-14)
+    assert mlp.gelu_grad(np.array(0.0)) == pytest.approx(0.5, abs=1e-15)
     h = 1e-6
     np.testing.assert_allclose(mlp.gelu_grad(z), (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h),
                                rtol=1e-7, atol=1e-9)
