@@ -76,6 +76,13 @@ struct WorldDev {
     const int *coff;                      // [S + 1] first chunk of each scene
     const uint8_t *pchunk;                // [P] scene-local chunk of each stored point
     int max_chunks;                       // chunks of the scene with the most
+    // posed-shape cache (worlds stepped by the surrogate, whose plain launches are short): per
+    // scene scache_mp + 2 scache_mt + 5 float4 -- the posed offsets of its points, the tile boxes
+    // of the lanes per scene that wrote them, the mass properties (4 float4) and
+    // (rmax, lanes per scene, 0, 0).  Mode 0: unused; 1: written at every shape update; 2: also
+    // read at launch entry instead of rebuilding the shape (every scene's entry is current)
+    float4 *scache;
+    int scache_mp, scache_mt, scache_mode;
 };
 
 struct LaunchCfg {

@@ -446,6 +446,55 @@ __device__ __noinline__ void shape_update(const WorldDev &W, int s, int p0, int 
     __syncwarp();
 }
 
+// ------------------------------------------------------------------------ posed-shape cache
+
+__host__ __device__ inline long long scache_stride(int mp, int mt) { return (long long)mp + 2 * mt + 5; }
+
+// Writes the scene's posed shape (pts, tile boxes, mass properties) to its cache entry; stores only.
+template <int LPS>
+__device__ __forceinline__ void scache_store(const WorldDev &W, int s, int np, const float4 *pts, const float4 *tb,
+                                             const Shape &sh, float rmax, int gl) {
+    float4 *e = W.scache + (size_t)s * scache_stride(W.scache_mp, W.scache_mt);
+    const int nt = (np + LPS - 1) / LPS;
+    for (int i = gl; i < np; i += LPS) e[i] = pts[i];
+    for (int i = gl; i < 2 * nt; i += LPS) e[W.scache_mp + i] = tb[i];
+    if (gl == 0) {
+        float4 *m = e + W.scache_mp + 2 * W.scache_mt;
+        m[0] = make_float4(sh.M, sh.g[0], sh.g[1], sh.g[2]);
+        m[1] = make_float4(sh.Ib.xx, sh.Ib.yy, sh.Ib.zz, sh.Ib.xy);
+        m[2] = make_float4(sh.Ib.xz, sh.Ib.yz, sh.Ii.xx, sh.Ii.yy);
+        m[3] = make_float4(sh.Ii.zz, sh.Ii.xy, sh.Ii.xz, sh.Ii.yz);
+        m[4] = make_float4(rmax, __int_as_float(LPS), 0.f, 0.f);
+    }
+}
+
+// Reads the posed shape of scene s (-1: no scene) from its cache entry into the slot: the offsets,
+// the mass properties and, when they were written with this many lanes per scene on every scene
+// of the warp, the tile boxes (else they are rebuilt from the offsets).  Returns rmax.
+template <int LPS>
+__device__ __forceinline__ float scache_load(const WorldDev &W, int s, int np, float4 *pts, float4 *tb, Shape &sh,
+                                             int gl) {
+    const float4 *e = W.scache + (size_t)(s < 0 ? 0 : s) * scache_stride(W.scache_mp, W.scache_mt);
+    const int nt = (np + LPS - 1) / LPS;
+    const float4 *m = e + W.scache_mp + 2 * W.scache_mt;
+    float4 m0 = make_float4(1.f, 0.f, 0.f, 0.f), m1 = make_float4(1.f, 1.f, 1.f, 0.f);
+    float4 m2 = make_float4(0.f, 0.f, 1.f, 1.f), m3 = make_float4(1.f, 0.f, 0.f, 0.f);
+    float4 m4 = make_float4(0.f, __int_as_float(LPS), 0.f, 0.f);
+    if (s >= 0) { m0 = m[0]; m1 = m[1]; m2 = m[2]; m3 = m[3]; m4 = m[4]; }
+    const bool tb_ok = __all_sync(FULL_MASK, __float_as_int(m4.y) == LPS);
+#pragma unroll 4
+    for (int i = gl; i < np; i += LPS) cp_async16(pts + i, e + i);
+    if (tb_ok)
+        for (int i = gl; i < 2 * nt; i += LPS) cp_async16(tb + i, e + W.scache_mp + i);
+    cp_async_wait_all();
+    __syncwarp();
+    sh.M = m0.x; sh.g[0] = m0.y; sh.g[1] = m0.z; sh.g[2] = m0.w;
+    sh.Ib = Sym{m1.x, m1.y, m1.z, m1.w, m2.x, m2.y};
+    sh.Ii = Sym{m2.z, m2.w, m3.x, m3.y, m3.z, m3.w};
+    if (tb_ok) return m4.x;
+    return tile_bounds<LPS>(pts, np, tb, gl);   // every lane of the warp takes this branch
+}
+
 // ------------------------------------------------------------------------ ground (Sec. III-A)
 
 // The height maps' parameters, copied from the world into registers by the step loop.
@@ -798,8 +847,16 @@ __device__ __forceinline__ void run_scene(const WorldDev &W, int s, int gl, floa
     }
     __syncwarp();
     Shape sh;
-    shape_update<LPS>(W, valid ? s : 0, p0, np, l0, nl, th, fr, pts, gl, sh);
-    float rmax = tile_bounds<LPS>(pts, np, tb, gl);
+    float rmax;
+    // the posed shape of the current joint angles: read from the posed-shape cache when the
+    // launch says every entry is current, else rebuilt (and written to the cache when there is one)
+    if (!ARENA && W.scache_mode == 2) {
+        rmax = scache_load<LPS>(W, valid ? s : -1, np, pts, tb, sh, gl);
+    } else {
+        shape_update<LPS>(W, valid ? s : 0, p0, np, l0, nl, th, fr, pts, gl, sh);
+        rmax = tile_bounds<LPS>(pts, np, tb, gl);
+        if (!ARENA && W.scache_mode != 0 && valid) scache_store<LPS>(W, s, np, pts, tb, sh, rmax, gl);
+    }
     // (arenas) body-frame box of the posed points
     float bbc[3] = {0.f, 0.f, 0.f}, bbh[3] = {0.f, 0.f, 0.f};
     float4 *lbb = reinterpret_cast<float4 *>(xch + 4 * XC_N) + 2 * W.max_chunks;   // body chunk boxes
@@ -903,6 +960,7 @@ __device__ __forceinline__ void run_scene(const WorldDev &W, int s, int gl, floa
             __syncwarp();
             shape_update<LPS>(W, valid ? s : 0, p0, np, l0, nl, th, fr, pts, gl, sh);
             rmax = tile_bounds<LPS>(pts, np, tb, gl);
+            if (!ARENA && W.scache_mode != 0 && valid) scache_store<LPS>(W, s, np, pts, tb, sh, rmax, gl);
             shr = sh;
             if (ARENA) {
                 robot_box<LPS>(tb, ntiles, gl, bbc, bbh);
@@ -1556,7 +1614,22 @@ __global__ void __launch_bounds__(128) shape_cache_kernel(const __grid_constant_
     for (int j = lane; j < nl - 1; j += 32) th[j] = W.theta[j0 + j];
     __syncwarp();
     Shape sh;
-    shape_update<32>(W, s, p0, np, l0, nl, th, fr, pts, lane, sh);
+    if (W.scache_mode == 2) {
+        // the posed offsets and mass properties from the posed-shape cache; only the link frames
+        // are built here
+        const float4 *e = W.scache + (size_t)s * scache_stride(W.scache_mp, W.scache_mt);
+        for (int i = lane; i < np; i += 32) cp_async16(pts + i, e + i);
+        const float4 *m = e + W.scache_mp + 2 * W.scache_mt;
+        const float4 m0 = m[0], m1 = m[1], m2 = m[2], m3 = m[3];
+        sh.M = m0.x; sh.g[0] = m0.y; sh.g[1] = m0.z; sh.g[2] = m0.w;
+        sh.Ib = Sym{m1.x, m1.y, m1.z, m1.w, m2.x, m2.y};
+        sh.Ii = Sym{m2.z, m2.w, m3.x, m3.y, m3.z, m3.w};
+        link_frames<32>(W, l0, nl, th, fr, lane);
+        cp_async_wait_all();
+        __syncwarp();
+    } else {
+        shape_update<32>(W, s, p0, np, l0, nl, th, fr, pts, lane, sh);
+    }
     for (int l = lane; l < C.nl; l += 32) {
         float4 lq = make_float4(1.f, 0.f, 0.f, 0.f), lp = make_float4(0.f, 0.f, 0.f, 0.f);
         if (l < nl) {

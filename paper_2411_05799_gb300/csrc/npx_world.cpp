@@ -137,6 +137,12 @@ struct npx_world {
         uint32_t *sens_new = nullptr;         // [S]
         int *list = nullptr, *count = nullptr;
         int *fb = nullptr;                    // [S] windows of each scene that fell back
+        // posed-shape cache of every scene (read at the entry of the surrogate's plain launches);
+        // current when scache_ok: written by a launch over all scenes since the last change of
+        // joint angles from outside the surrogate's own launches
+        float4 *scache = nullptr;
+        int scache_mp = 0, scache_mt = 0;
+        bool scache_ok = false;
         long long *total = nullptr;
         cudaEvent_t ev_w = nullptr, ev_n = nullptr;
         int rows = 0;
@@ -500,6 +506,11 @@ int surrogate_buffers(npx_world *w) {
         (rc = dev_alloc(w, &w->sg.applied, w->S)) || (rc = dev_alloc(w, &w->sg.sens_new, w->S)) ||
         (rc = dev_alloc(w, &w->sg.fb, w->S)))
         return rc;
+    w->sg.scache_mp = w->max_points;
+    w->sg.scache_mt = (w->max_points + 3) / 4;   // tiles at the fewest lanes per scene (4)
+    if ((rc = dev_alloc(w, &w->sg.scache, (size_t)w->S * (w->sg.scache_mp + 2 * w->sg.scache_mt + 5))))
+        return rc;
+    w->sg.scache_ok = false;
     CUDA_TRY(cudaMemsetAsync(w->sg.count, 0, sizeof(int), w->stream));
     CUDA_TRY(cudaMemsetAsync(w->sg.fb, 0, sizeof(int) * (size_t)w->S, w->stream));
     CUDA_TRY(cudaMemsetAsync(d_max, 0, sizeof(int), w->stream));
@@ -897,7 +908,7 @@ int npx_world_finalize(npx_world *w) {
 
 int npx_state_set(npx_world *w, const float *origin, const float *quat, const float *vel,
                   const float *omega, const float *theta) {
-    if (w) ++w->state_gen;
+    if (w) { ++w->state_gen; w->sg.scache_ok = false; }
     if (int rc = check_ready(w)) return rc;
     if (!origin || !quat || !vel || !omega) return fail(NPX_EINVAL, "null state array");
     CUDA_TRY(cudaSetDevice(w->device));
@@ -918,7 +929,7 @@ int npx_state_set(npx_world *w, const float *origin, const float *quat, const fl
 int npx_state_write(npx_world *w, const float *cog, const float *quat, const float *vel,
                     const float *angmom, const float *theta, const uint8_t *contact_prev,
                     int64_t step) {
-    if (w) ++w->state_gen;
+    if (w) { ++w->state_gen; w->sg.scache_ok = false; }
     if (int rc = check_ready(w)) return rc;
     if (!cog || !quat || !vel || !angmom) return fail(NPX_EINVAL, "null state array");
     if (step < 0) return fail(NPX_EINVAL, "step must be >= 0");
@@ -1188,6 +1199,7 @@ int npx_world_step(npx_world *w, int n) {
     if (int rc = check_ready(w)) return rc;
     if (n < 0) return fail(NPX_EINVAL, "n must be >= 0");
     if (n == 0) return NPX_OK;
+    w->sg.scache_ok = false;   // these launches do not keep the posed-shape cache
     CUDA_TRY(cudaSetDevice(w->device));
     const int nchunks = (n + w->chunk - 1) / w->chunk;
     if (w->graphs) {
@@ -1291,7 +1303,7 @@ int npx_state_export(npx_world *w, void *blob, size_t *size) {
 }
 
 int npx_state_import(npx_world *w, const void *blob, size_t size) {
-    if (w) ++w->state_gen;
+    if (w) { ++w->state_gen; w->sg.scache_ok = false; }
     if (int rc = check_ready(w)) return rc;
     const BlobLayout b = blob_layout(w);
     if (!blob || size < b.end) return fail(NPX_EINVAL, "blob too small (%zu < %zu)", size, b.end);
@@ -1391,10 +1403,34 @@ static int check_stride(const npx_world *w, int stride) {
 static bool cache_valid(const npx_world *w) {
     return w->sg.cache_at == w->step && w->sg.cache_gen == w->state_gen;
 }
+static npx::WorldDev scache_world(const npx_world *w);
+
 static int cache_build(npx_world *w) {
-    CUDA_TRY(npx::launch_shape_cache(w->W, w->sg.cache, w->stream));
+    CUDA_TRY(npx::launch_shape_cache(scache_world(w), w->sg.cache, w->stream));
     w->sg.cache_at = w->step;
     w->sg.cache_gen = w->state_gen;
+    return NPX_OK;
+}
+
+// The world as the surrogate's plain launches see it: with the posed-shape cache, read at entry
+// when it is current (mode 2), else written (mode 1).
+static npx::WorldDev scache_world(const npx_world *w) {
+    npx::WorldDev W = w->W;
+    W.scache = w->sg.scache;
+    W.scache_mp = w->sg.scache_mp;
+    W.scache_mt = w->sg.scache_mt;
+    W.scache_mode = w->sg.scache_ok ? 2 : 1;
+    return W;
+}
+
+// Makes the posed-shape cache current: a launch of zero steps over every scene rebuilds each
+// shape and writes it (the state is read and written back unchanged).
+static int scache_fill(npx_world *w) {
+    if (w->sg.scache_ok || w->W.arena > 1) return NPX_OK;
+    npx::WorldDev W = scache_world(w);
+    CUDA_TRY(npx::launch_step(W, w->cfg, 0, w->stream));
+    w->sg.scache_ok = true;
+    w->launches += 1;
     return NPX_OK;
 }
 
@@ -1402,9 +1438,10 @@ static int cache_build(npx_world *w) {
 // detection at the current state); the shape cache follows any joint update among them.
 static int plain_run(npx_world *w, int m, bool reseed) {
     const bool was_valid = cache_valid(w);
-    npx::WorldDev W = w->W;
+    npx::WorldDev W = scache_world(w);
     W.reseed = reseed ? 1 : 0;
     CUDA_TRY(npx::launch_step(W, w->cfg, m, w->stream));
+    w->sg.scache_ok = true;   // every scene's entry written or current
     CUDA_TRY(npx::launch_advance(w->d_step, m, w->stream));
     const long long K = w->desc.joint_update_steps;
     const bool tick = w->act_mode != NPX_ACT_HOLD && (w->step + K - 1) / K * K < w->step + m;   // (step >= 0)
@@ -1438,6 +1475,7 @@ int npx_surrogate_collect(npx_world *w, const npx_surrogate_norm *nrm, int strid
     if (int rc = ensure_derived(w)) return rc;
     if (!cache_valid(w))
         if (int rc = cache_build(w)) return rc;
+    if (int rc = scache_fill(w)) return rc;
     for (int k = 0; k < n_windows;) {
         if (!window_fits(w, w->step, stride)) {   // joint updates and what is left before them
             if (int rc = plain_run(w, 1, false)) return rc;
@@ -1446,7 +1484,7 @@ int npx_surrogate_collect(npx_world *w, const npx_surrogate_norm *nrm, int strid
         pre.X = X + (size_t)k * w->S * nf;
         post.T = T + (size_t)k * w->S * nt;
         CUDA_TRY(npx::launch_features(w->W, C, pre, w->stream));
-        CUDA_TRY(npx::launch_step(w->W, w->cfg, stride, w->stream));
+        CUDA_TRY(npx::launch_step(scache_world(w), w->cfg, stride, w->stream));
         CUDA_TRY(npx::launch_advance(w->d_step, stride, w->stream));
         CUDA_TRY(npx::launch_features(w->W, C, post, w->stream));
         w->step += stride;
@@ -1483,8 +1521,10 @@ int npx_world_step_surrogate(npx_world *w, npx_mlp *net, const npx_surrogate_nor
     io.ldb = ldx;
     io.x_mu = nrm->x_mu;
     io.x_isd = nrm->x_isd;
-    // the plain step on the fallback list only, from contacts detected at the window's start
-    npx::WorldDev Wsub = w->W;
+    // the plain step on the fallback list only, from contacts detected at the window's start, its
+    // scenes' posed shapes read from the cache (made current below, before the first window)
+    npx::WorldDev Wsub = scache_world(w);
+    Wsub.scache_mode = 2;
     Wsub.order = w->sg.list;
     Wsub.sched_count = w->sg.count;
     Wsub.reseed = 1;
@@ -1499,6 +1539,7 @@ int npx_world_step_surrogate(npx_world *w, npx_mlp *net, const npx_surrogate_nor
     if (int rc = ensure_derived(w)) return rc;
     if (!cache_valid(w))
         if (int rc = cache_build(w)) return rc;
+    if (int rc = scache_fill(w)) return rc;
     // contact flags are stale after a window (the surrogate moves scenes without detecting
     // contacts): plain steps of every scene start from the contacts at the current state
     bool stale = false;

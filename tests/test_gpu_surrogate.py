@@ -126,3 +126,32 @@ def test_training_and_50_step_rollout(stride):
     assert np.median(dc) < 0.2 * np.median(dcu), (np.median(dc), np.median(dcu))
     assert np.median(dc) < 5e-3, np.median(dc)
     assert np.median(da) < 0.2 * np.median(dau), (np.median(da), np.median(dau))
+
+
+def test_posed_shape_cache_steps_bit_identically():
+    """The surrogate's plain launches read each scene's posed shape from a cache instead of
+    rebuilding it at entry.  Two worlds stepped alike, one whose cache is invalidated (a state
+    write of its own state) before every call so that every entry is rebuilt, stay bit-identical
+    over surrogate periods with fallbacks, joint updates and a one-step stride."""
+    from paper_2411_05799_gb300 import surrogate
+    b = scenes.hexapod_batch(256, seed_key=44)
+    res = surrogate.train(scenes.hexapod_batch(512, seed_key=45), n_transitions=512 * 16 * 8,
+                          minibatch=1024, steps_per_chunk=16, passes=1, stat_periods=1, warm_steps=100,
+                          max_batch=256, stride=10)
+    sur = res["surrogate"]
+    stream = torch.cuda.current_stream().cuda_stream
+    wa = npx.World.from_batch(b, stream=stream)
+    wb = npx.World.from_batch(b, stream=stream)
+    wa.step(41)
+    wb.step(41)
+    fa = fb = 0
+    for n in (80, 37, 80, 3):
+        fa += sur.step(wa, n)
+        r = wb.read()
+        wb.write_state(r["cog"], r["quat"], r["vel"], r["angmom"], r["theta"], wb.contacts(), r["step"])
+        fb += sur.step(wb, n)
+        ra, rb = wa.read(), wb.read()
+        for k in ("cog", "quat", "vel", "angmom", "theta", "contacts", "status"):
+            assert np.array_equal(ra[k], rb[k]), (n, k)
+        assert np.array_equal(wa.contacts(), wb.contacts()), n
+    assert fa == fb and fa > 0
