@@ -1473,9 +1473,10 @@ int npx_surrogate_collect(npx_world *w, const npx_surrogate_norm *nrm, int strid
     post.prev = w->sg.F0;
     if (nrm) { post.t_mu = nrm->t_mu; post.t_sd = nrm->t_sd; }
     if (int rc = ensure_derived(w)) return rc;
+    // the posed-shape cache first: the network's shape cache is built from it
+    if (int rc = scache_fill(w)) return rc;
     if (!cache_valid(w))
         if (int rc = cache_build(w)) return rc;
-    if (int rc = scache_fill(w)) return rc;
     for (int k = 0; k < n_windows;) {
         if (!window_fits(w, w->step, stride)) {   // joint updates and what is left before them
             if (int rc = plain_run(w, 1, false)) return rc;
@@ -1537,9 +1538,10 @@ int npx_world_step_surrogate(npx_world *w, npx_mlp *net, const npx_surrogate_nor
         if (rc_cfg) return rc_cfg;
     }
     if (int rc = ensure_derived(w)) return rc;
+    // the posed-shape cache first: the network's shape cache is built from it
+    if (int rc = scache_fill(w)) return rc;
     if (!cache_valid(w))
         if (int rc = cache_build(w)) return rc;
-    if (int rc = scache_fill(w)) return rc;
     // contact flags are stale after a window (the surrogate moves scenes without detecting
     // contacts): plain steps of every scene start from the contacts at the current state
     bool stale = false;
