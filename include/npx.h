@@ -220,6 +220,9 @@ typedef struct {
     int64_t kernel_launches;    /* step-kernel launches so far */
     int size_classes;           /* launches per chunk: scenes grouped by point count, each with
                                    its own shared-memory slots and launch shape */
+    int hm_window_tma;          /* 1: each scene's 16 x 16-cell height-map window is loaded by
+                                   one TMA box copy; 0: by plain loads (no maps, maps narrower or
+                                   shorter than 16 cells, or rows not a multiple of 16 bytes) */
 } npx_world_info;
 int npx_world_info_get(npx_world *w, npx_world_info *out);
 /* Launch shape of the step kernel: lanes per scene (4, 8, 16 or 32; a scene holds at most 64

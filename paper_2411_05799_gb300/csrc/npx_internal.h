@@ -1,6 +1,7 @@
 // npx_internal.h -- device data layout shared by the host library (npx_world.cpp) and the
 // kernels (npx_step.cu).  Not part of the public C-ABI.
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -83,6 +84,11 @@ struct WorldDev {
     // read at launch entry instead of rebuilding the shape (every scene's entry is current)
     float4 *scache;
     int scache_mp, scache_mt, scache_mode;
+    // TMA map of the height maps [H][ny][nx] (FP32) in boxes of HM_BOX x HM_WIN x 1 cells for the
+    // window loads, held on the host (hm_tmap_h) and passed to the step kernels as a parameter of
+    // their own; hm_tma = 0 when the maps do not allow it (window loads by plain gathers)
+    int hm_tma;
+    const CUtensorMap *hm_tmap_h;
 };
 
 struct LaunchCfg {
@@ -145,6 +151,10 @@ cudaError_t launch_accumulate(long long *total, int *count, int mult, cudaStream
 // records msg as the thread's npx_last_error() text and returns code
 int set_last_error(int code, const char *msg);
 cudaError_t launch_points(const WorldDev &W, int scene, float *d_out, cudaStream_t st);
+// Encodes *out for maps of at least 16 x 16 cells whose rows are a multiple of 16 bytes and sets
+// W.hm_tma (1) and W.hm_tmap_h (out) on success; leaves hm_tma 0 otherwise (or when the encoder is
+// unavailable).  out must outlive every launch of the world.
+void encode_hm_tmap(WorldDev &W, int n_maps, CUtensorMap *out);
 
 }  // namespace npx
 

@@ -101,6 +101,8 @@ extern "C" int npx_step_noalloc(const npx_device_world *d, int n_steps, void *st
     unsigned int *scratch = g_scratch_ptr[dev];
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
+    // (W{} leaves hm_tma 0: the descriptor carries no map count to bound a TMA map, so height-map
+    // windows load by plain gathers here)
     npx::WorldDev W{};
     W.S = d->n_scenes;
     W.link_off = d->link_off; W.point_off = d->point_off;

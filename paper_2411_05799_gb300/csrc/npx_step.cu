@@ -25,6 +25,7 @@
 //     solved in centred form (identical to the paper's 3x3 normal equations), a3 applied as a
 //     rotation by asin(a3) about the contact centroid, dynamic part capped by mu * FN * dt.
 #include <algorithm>
+#include <cstring>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -38,8 +39,13 @@ namespace npx {
 constexpr float POINT_RADIUS = 1e-3f;   // m, see shape_update
 constexpr float CULL_MARGIN = 4e-3f;    // m, height margin of the candidate tiles (run_scene)
 // height-map window kept in shared memory per scene (run_scene): HM_WIN x HM_WIN cells around the
-// CoG, moved when the CoG's cell drifts more than HM_DRIFT cells from the window's centre
+// CoG (clamped to the map), moved when its centred origin drifts more than HM_DRIFT cells
 constexpr int HM_WIN = 16, HM_DRIFT = 2;
+// The window is stored as HM_WIN rows of HM_BOX cells: a TMA box starts on a 16-byte boundary, so
+// its first column is the window's rounded down to a multiple of 4 and the window starts wsh
+// (0..3) cells into each row; an mbarrier follows the window (HM_AREA bytes in all).
+constexpr int HM_BOX = 20, HM_AREA = 1408;
+constexpr unsigned long long HM_WAIT_NS = 1000000000ull;   // 1 s bound on a window load
 
 // ------------------------------------------------------------------------ group reductions
 
@@ -115,25 +121,6 @@ __device__ __forceinline__ void world_sym(const float R[9], const Sym &S, const 
     mat_vec(R, b, y);
 }
 
-// world-frame tensor R S R^T of a symmetric S (rows of R S dotted with rows of R)
-__device__ __forceinline__ Sym world_tensor(const float R[9], const Sym &S) {
-    float T[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        T[3 * i] = R[3 * i] * S.xx + R[3 * i + 1] * S.xy + R[3 * i + 2] * S.xz;
-        T[3 * i + 1] = R[3 * i] * S.xy + R[3 * i + 1] * S.yy + R[3 * i + 2] * S.yz;
-        T[3 * i + 2] = R[3 * i] * S.xz + R[3 * i + 1] * S.yz + R[3 * i + 2] * S.zz;
-    }
-    Sym w;
-    w.xx = T[0] * R[0] + T[1] * R[1] + T[2] * R[2];
-    w.yy = T[3] * R[3] + T[4] * R[4] + T[5] * R[5];
-    w.zz = T[6] * R[6] + T[7] * R[7] + T[8] * R[8];
-    w.xy = T[0] * R[3] + T[1] * R[4] + T[2] * R[5];
-    w.xz = T[0] * R[6] + T[1] * R[7] + T[2] * R[8];
-    w.yz = T[3] * R[6] + T[4] * R[7] + T[5] * R[8];
-    return w;
-}
-
 __device__ __forceinline__ void quat_mul(const float a[4], const float b[4], float c[4]) {
     float t0 = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
     float t1 = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
@@ -166,15 +153,6 @@ __device__ __forceinline__ void sincos_small(float x, float *s, float *c) {
     }
 }
 
-// sin(a) / a and (1 - cos a) / a^2 as series in x = a^2, for x <= 1/64 (|a| <= 1/8): the first
-// omitted terms, x^4 / 362880 and x^4 / 3628800, are below 2e-13
-__device__ __forceinline__ float sinc_sq(float x) {
-    return fmaf(x, fmaf(x, fmaf(x, -1.f / 5040.f, 1.f / 120.f), -1.f / 6.f), 1.f);
-}
-__device__ __forceinline__ float cosc_sq(float x) {
-    return fmaf(x, fmaf(x, fmaf(x, -1.f / 40320.f, 1.f / 720.f), -1.f / 24.f), 0.5f);
-}
-
 __device__ __forceinline__ float asin_small(float x) {
     if (fabsf(x) <= 0.0625f) {
         const float x2 = x * x;
@@ -192,6 +170,10 @@ __host__ __device__ inline int tiles_offset(int max_points, int max_links) {
 }
 __host__ __device__ inline int slot_bytes(int max_points, int max_links, int lps) {
     return tiles_offset(max_points, max_links) + 32 * ((max_points + lps - 1) / lps);
+}
+// (height maps) the window and its mbarrier after the slot, 128-byte aligned for the TMA box
+__host__ __device__ inline int hm_win_offset(int max_points, int max_links, int lps) {
+    return (slot_bytes(max_points, max_links, lps) + 127) & ~127;
 }
 
 // Bounding boxes for skipping points that cannot touch the ground.  Tile t holds points
@@ -286,16 +268,6 @@ __device__ __forceinline__ uint64_t tiles_near_ground(const float4 *tb, int ntil
         mask |= mine << (r * LPS);
     }
     return mask;
-}
-
-// The lowest tile set in any lane's 64-bit tile mask of the group (64 if none), the same on every
-// lane of the group.
-template <int LPS>
-__device__ __forceinline__ int group_first_tile(uint64_t m) {
-    int k = m ? __ffsll((long long)m) - 1 : 64;
-#pragma unroll
-    for (int o = LPS / 2; o > 0; o >>= 1) k = min(k, __shfl_xor_sync(FULL_MASK, k, o));
-    return k;
 }
 
 // ------------------------------------------------------------------------ kinematics (Sec. III-B)
@@ -497,25 +469,15 @@ __device__ __forceinline__ float scache_load(const WorldDev &W, int s, int np, f
 
 // ------------------------------------------------------------------------ ground (Sec. III-A)
 
-// The height maps' parameters, copied from the world into registers by the step loop.
-struct HmView {
-    const float *hm;
-    int nx, ny;
-    float ox, oy, scale;
-};
-__device__ __forceinline__ HmView hm_view(const WorldDev &W) {
-    return HmView{W.hm, W.hm_nx, W.hm_ny, W.hm_ox, W.hm_oy, W.hm_scale};
-}
-
 template <bool FLAT>
-__device__ __forceinline__ float ground(const HmView &H, int hm, float x, float y) {
+__device__ __forceinline__ float ground(const WorldDev &W, int hm, float x, float y) {
     if (FLAT || hm < 0) return 0.f;
-    const float fx = __fmul_rn(__fsub_rn(x, H.ox), H.scale);
-    const float fy = __fmul_rn(__fsub_rn(y, H.oy), H.scale);
+    const float fx = __fmul_rn(__fsub_rn(x, W.hm_ox), W.hm_scale);
+    const float fy = __fmul_rn(__fsub_rn(y, W.hm_oy), W.hm_scale);
     int ix = __float2int_rd(fx), iy = __float2int_rd(fy);
-    ix = min(max(ix, 0), H.nx - 1);
-    iy = min(max(iy, 0), H.ny - 1);
-    return __ldg(H.hm + ((size_t)hm * H.ny + iy) * H.nx + ix);
+    ix = min(max(ix, 0), W.hm_nx - 1);
+    iy = min(max(iy, 0), W.hm_ny - 1);
+    return __ldg(W.hm + ((size_t)hm * W.hm_ny + iy) * W.hm_nx + ix);
 }
 
 // The same lookup through a window of the scene's map in shared memory.  The window (origin
@@ -523,17 +485,64 @@ __device__ __forceinline__ float ground(const HmView &H, int hm, float x, float 
 // inside it already reads the clamped cell's height; others are clamped and read from global
 // memory (the same value either way).
 template <bool FLAT>
-__device__ __forceinline__ float ground_win(const HmView &H, int hm, const float *win, int wx0, int wy0, float x,
+__device__ __forceinline__ float ground_win(const WorldDev &W, int hm, const float *win, int wx0, int wy0, float x,
                                             float y) {
     if (FLAT || hm < 0) return 0.f;
-    const float fx = __fmul_rn(__fsub_rn(x, H.ox), H.scale);
-    const float fy = __fmul_rn(__fsub_rn(y, H.oy), H.scale);
+    const float fx = __fmul_rn(__fsub_rn(x, W.hm_ox), W.hm_scale);
+    const float fy = __fmul_rn(__fsub_rn(y, W.hm_oy), W.hm_scale);
     int ix = __float2int_rd(fx), iy = __float2int_rd(fy);
     const unsigned ux = (unsigned)ix - (unsigned)wx0, uy = (unsigned)iy - (unsigned)wy0;
-    if (ux < (unsigned)HM_WIN && uy < (unsigned)HM_WIN) return win[uy * HM_WIN + ux];
-    ix = min(max(ix, 0), H.nx - 1);
-    iy = min(max(iy, 0), H.ny - 1);
-    return __ldg(H.hm + ((size_t)hm * H.ny + iy) * H.nx + ix);
+    if (ux < (unsigned)HM_WIN && uy < (unsigned)HM_WIN) return win[uy * HM_BOX + ux];
+    ix = min(max(ix, 0), W.hm_nx - 1);
+    iy = min(max(iy, 0), W.hm_ny - 1);
+    return __ldg(W.hm + ((size_t)hm * W.hm_ny + iy) * W.hm_nx + ix);
+}
+
+// Window loads with TMA: one 3-D box (HM_BOX x HM_WIN cells of map hm) into shared memory,
+// completing on the scene's mbarrier, waited for with a bound.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void win_bar_init(uint64_t *b) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(b)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void win_bar_inval(uint64_t *b) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(b)) : "memory");
+}
+__device__ __forceinline__ void win_load(float *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *b) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)),
+                 "r"((uint32_t)(HM_BOX * HM_WIN * sizeof(float)))
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(b))
+        : "memory");
+}
+// The whole warp waits for the window loads of its groups: lanes with `mine` set poll their
+// group's barrier for phase `parity` (a non-blocking test); the loop ends for all lanes at once,
+// when every lane is done or when HM_WAIT_NS have passed, so the groups leave it converged (a
+// per-group wait loop left them diverged for the rest of the launch).  Returns, per lane, whether
+// its load landed (true for lanes without one).  All 32 lanes must call it.
+__device__ __forceinline__ bool win_wait_warp(uint64_t *b, uint32_t parity, bool mine) {
+    bool done = !mine;
+    unsigned long long t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (;;) {
+        if (!done) {
+            uint32_t ok;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(ok)
+                : "r"(smem_addr(b)), "r"(parity)
+                : "memory");
+            done = ok != 0;
+        }
+        if (__all_sync(FULL_MASK, done)) return true;
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (__any_sync(FULL_MASK, t - t0 > HM_WAIT_NS)) return done;
+    }
 }
 
 // ------------------------------------------------------------------------ actuators (Sec. III-B)
@@ -809,9 +818,9 @@ __device__ __forceinline__ void arena_wrench(const WorldDev &W, unsigned char *x
 // least squares of Eqs. 1-6 as written, with no test of the options in the step loop; ARENA:
 // robot-robot contact within arenas (below)
 template <int LPS, bool FLAT, bool OPT, bool ARENA>
-__device__ __forceinline__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *fr, float *th,
+__device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *fr, float *th,
                           float *th_old, float4 *tb, int n_steps, long long step0, unsigned char *xch,
-                          int sbytes) {
+                          int sbytes, const CUtensorMap *tmap) {
     const bool valid = s >= 0;
     int p0 = 0, np = 0, l0 = 0, nl = 1;
     if (valid) {
@@ -876,7 +885,7 @@ __device__ __forceinline__ void run_scene(const WorldDev &W, int s, int gl, floa
             const float x = c[0] + (R0[0] * r.x + R0[1] * r.y + R0[2] * r.z);
             const float y = c[1] + (R0[3] * r.x + R0[4] * r.y + R0[5] * r.z);
             const float z = c[2] + (R0[6] * r.x + R0[7] * r.y + R0[8] * r.z);
-            if (z < ground<FLAT>(hm_view(W), hm, x, y)) kprev |= 1ull << k;
+            if (z < ground<FLAT>(W, hm, x, y)) kprev |= 1ull << k;
         }
     }
     // sh is written by the (out-of-line) shape update through a reference, so it lives in local
@@ -884,22 +893,27 @@ __device__ __forceinline__ void run_scene(const WorldDev &W, int s, int gl, floa
     Shape shr = sh;
     // highest ground a point can meet (plus a margin for the rounding of the bound)
     const float hmax = (FLAT || hm < 0 ? 0.f : W.hm_max[hm]) + 1e-5f;
-    // height-map window (after the slot); its origin is negative until the first refresh
+    // height-map window (after the slot); its origin is negative until the first refresh.  With
+    // TMA the window's first cell sits wsh cells into each stored row; its mbarrier follows it.
     float *win = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(pts) +
-                                           slot_bytes(W.max_points, W.max_links, LPS));
-    int wx0 = -(1 << 24), wy0 = -(1 << 24);
+                                           hm_win_offset(W.max_points, W.max_links, LPS));
+    uint64_t *wbar = reinterpret_cast<uint64_t *>(win + HM_BOX * HM_WIN);
+    int wx0 = -(1 << 24), wy0 = -(1 << 24), wsh = 0;
+    uint32_t wphase = 0;
+    bool wfail = false;
+    const bool win_tma = !FLAT && W.hm_tma != 0;
+    if (win_tma) {
+        if (gl == 0) win_bar_init(wbar);
+        __syncwarp();
+    }
     const int ntiles = (np + LPS - 1) / LPS;
 
-    // the world's parameters the step loop reads, in registers
     const float dt = W.dt, idt = 1.0f / W.dt, kw2 = W.kw2, kc = W.kc;
-    const float gx = W.gx, gy = W.gy, gz = W.gz;
-    const int K = W.K, act_mode = W.act_mode;
-    const HmView H = hm_view(W);
     // friction-model options (Sec. III-C, the refinements named after Eq. 6): rows weighted by
     // the normal forces; the friction impulse's torque about the horizontal axes
     const bool weighted = OPT && (W.fric_mode & 1) != 0, tilt = OPT && (W.fric_mode & 2) != 0;
     float iM = 1.0f / shr.M;
-    const bool actuated = act_mode != 0;
+    const bool actuated = W.act_mode != 0;
     // Candidate tiles: those whose box came within CULL_MARGIN of the highest ground at the last
     // cull.  slack is the height above the highest ground of the lowest box left out then, minus
     // a bound on how far any point has moved down since
@@ -908,26 +922,11 @@ __device__ __forceinline__ void run_scene(const WorldDev &W, int s, int gl, floa
     // exact and the boxes are tested again only when it runs out or the shape changes.
     float slack = -1.f;
     uint64_t cand = 0;
-    // The first NSLOT candidate tiles live in registers: slot s holds this lane's point of the s-th
-    // candidate tile (its offset r and mass) and that tile's bit in the contact masks (0: no
-    // point).  The contact pass runs over the slots unrolled, with no loads and no data-dependent
-    // branch; candidate tiles beyond the slots (rare) go through a loop over shared memory.  Slots
-    // and overflow together visit the candidate tiles in ascending order, as a single loop would, so
-    // the sums see the same terms in the same order whatever the slots hold.
-    constexpr int NSLOT = ARENA ? 1 : (LPS == 4 ? 4 : (LPS == 8 ? 3 : 2));
-    float4 sp[NSLOT];
-    uint64_t sbit[NSLOT];
-#pragma unroll
-    for (int s = 0; s < NSLOT; ++s) { sp[s] = make_float4(0.f, 0.f, 0.f, 0.f); sbit[s] = 0ull; }
-    uint64_t over = 0;
-    // reference of the friction-set moments: the first tile holding a point in contact last step
-    // (a function of the state alone); the same on every lane of the group
-    int kf = group_first_tile<LPS>(kprev);
-    int ph = (int)(step0 % (long long)K);
+    int ph = (int)(step0 % (long long)W.K);
     for (int t = 0; t < n_steps; ++t) {
         const long long n = step0 + t;
         const bool tick = actuated && ph == 0;
-        ph = (ph + 1 == K) ? 0 : ph + 1;
+        ph = (ph + 1 == W.K) ? 0 : ph + 1;
         float R[9];
         quat_mat(q, R);
 
@@ -936,7 +935,7 @@ __device__ __forceinline__ void run_scene(const WorldDev &W, int s, int gl, floa
         float gold[3] = {0.f, 0.f, 0.f};
         if (tick) {
             gold[0] = shr.g[0]; gold[1] = shr.g[1]; gold[2] = shr.g[2];
-            const bool gp = act_mode == 2;
+            const bool gp = W.act_mode == 2;
             if (gp) {
                 // the controller reads the foot contacts of the last step and sets the targets
                 uint32_t sens = 0;
@@ -967,13 +966,11 @@ __device__ __forceinline__ void run_scene(const WorldDev &W, int s, int gl, floa
                 chunk_boxes_body<LPS>(W, c0, nc, fr, shr.g, lbb, gl);
             }
             iM = 1.0f / shr.M;
-            slack = -1.f;   // the tiles moved: cull again (and reload the slots)
+            slack = -1.f;   // the tiles moved: cull again
         }
 
-        // world-frame inverse inertia R Ib^-1 R^T: angular velocity now and after integration
-        const Sym Wi = world_tensor(R, shr.Ii);
         float om[3];
-        sym_mul(Wi, L, om);
+        world_sym(R, shr.Ii, L, om);
 
         // -- (arenas) contact forces and their torques about the CoG from the other robots
         float rf[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -986,20 +983,42 @@ __device__ __forceinline__ void run_scene(const WorldDev &W, int s, int gl, floa
         //    function of these (see below).  All sums are independent, so the group reduction is
         //    one butterfly and every lane ends with bit-identical values.
         if (!FLAT) {
-            // move the height-map window when the CoG's cell has drifted from its centre (the
-            // groups of the warp refresh together; each loads only its own window)
-            const int cx = __float2int_rd(__fmul_rn(__fsub_rn(c[0], H.ox), H.scale));
-            const int cy = __float2int_rd(__fmul_rn(__fsub_rn(c[1], H.oy), H.scale));
-            const bool need = hm >= 0 && (wx0 < 0 || abs(cx - (wx0 + HM_WIN / 2)) > HM_DRIFT ||
-                                          abs(cy - (wy0 + HM_WIN / 2)) > HM_DRIFT);
+            // move the height-map window when the origin that would centre it on the CoG's cell
+            // (clamped to the map) has drifted from the current one by more than HM_DRIFT cells;
+            // a window held at the map's edge stays put (the groups of the warp refresh together;
+            // each loads only its own window)
+            const int cx = __float2int_rd(__fmul_rn(__fsub_rn(c[0], W.hm_ox), W.hm_scale));
+            const int cy = __float2int_rd(__fmul_rn(__fsub_rn(c[1], W.hm_oy), W.hm_scale));
+            const int tx = min(max(cx - HM_WIN / 2, 0), max(W.hm_nx - HM_WIN, 0));
+            const int ty = min(max(cy - HM_WIN / 2, 0), max(W.hm_ny - HM_WIN, 0));
+            const bool need = hm >= 0 && (wx0 < 0 || abs(tx - wx0) > HM_DRIFT || abs(ty - wy0) > HM_DRIFT);
             if (__any_sync(FULL_MASK, need)) {
+                // with TMA: one lane of each group that moves its window issues one box of the
+                // map (16 x 16 cells here: maps with TMA are at least that large, so the window
+                // lies inside the map), x rounded down to a multiple of 4 cells; columns past the
+                // map's edge, outside the window, read as zero and are never looked up.  The
+                // warp meets after the copies are issued and waits for them as one.
+                const bool tma = need && win_tma && !wfail;
                 if (need) {
-                    wx0 = min(max(cx - HM_WIN / 2, 0), max(H.nx - HM_WIN, 0));
-                    wy0 = min(max(cy - HM_WIN / 2, 0), max(H.ny - HM_WIN, 0));
-                    const float *map = H.hm + (size_t)hm * H.ny * H.nx;
+                    wx0 = tx;
+                    wy0 = ty;
+                    wsh = tma ? wx0 - (wx0 & ~3) : 0;
+                    if (tma && gl == 0) win_load(win, tmap, wx0 & ~3, wy0, hm, wbar);
+                }
+                __syncwarp();
+                const bool landed = win_wait_warp(wbar, wphase, tma);
+                if (tma) {
+                    wphase ^= 1u;
+                    if (!landed) {   // the load gave up its bounded wait: freeze the scene
+                        wfail = true;
+                        status |= 4u;
+                    }
+                } else if (need && !wfail) {
+                    const float *map = W.hm + (size_t)hm * W.hm_ny * W.hm_nx;
                     for (int e = gl; e < HM_WIN * HM_WIN; e += LPS) {
                         const int iy = wy0 + e / HM_WIN, ix = wx0 + e % HM_WIN;
-                        win[e] = __ldg(map + (size_t)min(iy, H.ny - 1) * H.nx + min(ix, H.nx - 1));
+                        win[(e / HM_WIN) * HM_BOX + e % HM_WIN] =
+                            __ldg(map + (size_t)min(iy, W.hm_ny - 1) * W.hm_nx + min(ix, W.hm_nx - 1));
                     }
                 }
                 __syncwarp();
@@ -1012,20 +1031,12 @@ __device__ __forceinline__ void run_scene(const WorldDev &W, int s, int gl, floa
             float zfar;
             cand = tiles_near_ground<LPS>(tb, ntiles, R, c[2], hmax + CULL_MARGIN, gl, zfar);
             slack = fminf(zfar - hmax, 1e30f);
-            // the lowest NSLOT candidate tiles into the slots, the rest to the overflow loop
-            uint64_t rest = cand;
-#pragma unroll
-            for (int sl = 0; sl < NSLOT; ++sl) {
-                const int tl = rest ? __ffsll((long long)rest) - 1 : 0;
-                const int i = tl * LPS + gl;
-                const bool ok = rest != 0ull && i < np;
-                const float4 pv = pts[ok ? i : 0];
-                sp[sl] = ok ? pv : make_float4(0.f, 0.f, 0.f, 0.f);
-                sbit[sl] = ok ? 1ull << tl : 0ull;
-                rest &= rest - 1;
-            }
-            over = rest;
         }
+        // reference o of the friction-set moments: the rotated centre of the first tile holding a
+        // point that was in contact last step (C is a subset of those; o depends on the state alone)
+        int kf = kprev ? __ffsll((long long)kprev) - 1 : 64;
+#pragma unroll
+        for (int ofs = LPS / 2; ofs > 0; ofs >>= 1) kf = min(kf, __shfl_xor_sync(FULL_MASK, kf, ofs));
         float o[3] = {0.f, 0.f, 0.f};
         if (kf < 64) {
             const float4 lo = tb[2 * kf], hi = tb[2 * kf + 1];
@@ -1034,39 +1045,54 @@ __device__ __forceinline__ void run_scene(const WorldDev &W, int s, int gl, floa
         }
         // FN, tau_x, tau_y | n | sum d (3) | sum d d^T (xx yy zz xy xz yz)
         float acc[13] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        uint64_t know = 0;
-        // a point that is absent, not in contact or not in C adds an exact zero
-        auto contact_point = [&](const float4 p, uint64_t bit) {
-            const float rx = R[0] * p.x + R[1] * p.y + R[2] * p.z;
-            const float ry = R[3] * p.x + R[4] * p.y + R[5] * p.z;
-            const float rz = R[6] * p.x + R[7] * p.y + R[8] * p.z;
-            const float z = c[2] + rz;
-            const float h = ground_win<FLAT>(H, hm, win, wx0, wy0, c[0] + rx, c[1] + ry);
-            const bool in = bit != 0ull && z < h;
-            const float vz = v[2] + (om[0] * ry - om[1] * rx);
-            const float F = in ? fmaxf(0.f, p.w * (kw2 * (h - z) - kc * vz)) : 0.f;
-            know |= in ? bit : 0ull;
-            acc[0] += F; acc[1] += ry * F; acc[2] -= rx * F;
-            // friction set C: in contact now and last step; a row's weight is 1, or its normal
-            // force with force-weighted friction.  Sums: weight, weight x d, weight x d d^T
-            const float w = (in && (kprev & bit)) ? (weighted ? F : 1.f) : 0.f;
-            const float d0 = rx - o[0], d1 = ry - o[1], d2 = rz - o[2];
-            const float a0 = w * d0, a1 = w * d1, a2 = w * d2;
-            acc[3] += w;
-            acc[4] += a0; acc[5] += a1; acc[6] += a2;
-            acc[7] += a0 * d0; acc[8] += a1 * d1; acc[9] += a2 * d2;
-            acc[10] += a0 * d1; acc[11] += a0 * d2; acc[12] += a1 * d2;
-        };
+        // The 64-bit tile masks are walked as two 32-bit words (hexapod candidates sit in the low
+        // word: points are stored by construction height).  Two tiles per iteration: two
+        // independent chains; a point that is absent, not in contact or not in C adds an exact
+        // zero, so the sums see the same terms in the same order.
+        uint32_t knw[2] = {0u, 0u};
 #pragma unroll
-        for (int sl = 0; sl < NSLOT; ++sl) contact_point(sp[sl], sbit[sl]);
-        for (uint64_t tm = over; tm; tm &= tm - 1) {   // candidate tiles beyond the slots
-            const int tl = __ffsll((long long)tm) - 1;
-            const int i = tl * LPS + gl;
-            const bool ok = i < np;
-            contact_point(pts[ok ? i : 0], ok ? 1ull << tl : 0ull);
+        for (int hw = 0; hw < 2; ++hw) {
+            const uint32_t kp = (uint32_t)(kprev >> (32 * hw));
+            for (uint32_t tm = (uint32_t)(cand >> (32 * hw)); tm;) {
+                const int ja = __ffs(tm) - 1;
+                tm &= tm - 1;
+                const bool two = tm != 0;
+                const int jb = two ? __ffs(tm) - 1 : ja;
+                if (two) tm &= tm - 1;
+                const int ia = gl + (ja + 32 * hw) * LPS, ib = gl + (jb + 32 * hw) * LPS;
+                const bool oka = ia < np, okb = two && ib < np;
+                const float4 pa = pts[oka ? ia : 0], pb = pts[okb ? ib : 0];
+                const float rxa = R[0] * pa.x + R[1] * pa.y + R[2] * pa.z, rxb = R[0] * pb.x + R[1] * pb.y + R[2] * pb.z;
+                const float rya = R[3] * pa.x + R[4] * pa.y + R[5] * pa.z, ryb = R[3] * pb.x + R[4] * pb.y + R[5] * pb.z;
+                const float rza = R[6] * pa.x + R[7] * pa.y + R[8] * pa.z, rzb = R[6] * pb.x + R[7] * pb.y + R[8] * pb.z;
+                const float za = c[2] + rza, zb = c[2] + rzb;
+                const float ha = ground_win<FLAT>(W, hm, win + wsh, wx0, wy0, c[0] + rxa, c[1] + rya);
+                const float hb = ground_win<FLAT>(W, hm, win + wsh, wx0, wy0, c[0] + rxb, c[1] + ryb);
+                const bool ca = oka && za < ha, cb = okb && zb < hb;
+                const float vza = v[2] + (om[0] * rya - om[1] * rxa), vzb = v[2] + (om[0] * ryb - om[1] * rxb);
+                const float Fa = ca ? fmaxf(0.f, pa.w * (kw2 * (ha - za) - kc * vza)) : 0.f;
+                const float Fb = cb ? fmaxf(0.f, pb.w * (kw2 * (hb - zb) - kc * vzb)) : 0.f;
+                knw[hw] |= (ca ? 1u << ja : 0u) | (cb ? 1u << jb : 0u);
+                acc[0] += Fa; acc[1] += rya * Fa; acc[2] -= rxa * Fa;
+                acc[0] += Fb; acc[1] += ryb * Fb; acc[2] -= rxb * Fb;
+                // friction set C: in contact now and last step; a row's weight is 1, or its normal
+                // force with force-weighted friction.  Sums: weight, weight x d, weight x d d^T
+                const float wa = (ca && ((kp >> ja) & 1u)) ? (weighted ? Fa : 1.f) : 0.f;
+                const float wb = (cb && ((kp >> jb) & 1u)) ? (weighted ? Fb : 1.f) : 0.f;
+                const float da0 = rxa - o[0], da1 = rya - o[1], da2 = rza - o[2];
+                const float db0 = rxb - o[0], db1 = ryb - o[1], db2 = rzb - o[2];
+                const float a0 = wa * da0, a1 = wa * da1, a2 = wa * da2;
+                const float b0 = wb * db0, b1 = wb * db1, b2 = wb * db2;
+                acc[3] += wa; acc[3] += wb;
+                acc[4] += a0; acc[5] += a1; acc[6] += a2;
+                acc[4] += b0; acc[5] += b1; acc[6] += b2;
+                acc[7] += a0 * da0; acc[8] += a1 * da1; acc[9] += a2 * da2;
+                acc[10] += a0 * da1; acc[11] += a0 * da2; acc[12] += a1 * da2;
+                acc[7] += b0 * db0; acc[8] += b1 * db1; acc[9] += b2 * db2;
+                acc[10] += b0 * db1; acc[11] += b0 * db2; acc[12] += b1 * db2;
+            }
         }
-        // the reference tile of the next step, if this step commits (overlaps the reduction)
-        const int kf_next = group_first_tile<LPS>(know);
+        const uint64_t know = (uint64_t)knw[0] | ((uint64_t)knw[1] << 32);
         gsum<LPS, 13>(acc);
         const float FN = acc[0];
         // friction set: count, centroid of rho and second central moments sum (rho - gb)(rho - gb)^T
@@ -1079,9 +1105,9 @@ __device__ __forceinline__ void run_scene(const WorldDev &W, int s, int gl, floa
 
         // -- semi-implicit Euler
         float vs[3], Ls[3], cs[3], qs[4], oms[3];
-        vs[0] = v[0] + dt * gx;
-        vs[1] = v[1] + dt * gy;
-        vs[2] = v[2] + dt * (gz + FN * iM);
+        vs[0] = v[0] + dt * W.gx;
+        vs[1] = v[1] + dt * W.gy;
+        vs[2] = v[2] + dt * (W.gz + FN * iM);
         Ls[0] = L[0] + dt * acc[1];
         Ls[1] = L[1] + dt * acc[2];
         Ls[2] = L[2];
@@ -1089,7 +1115,7 @@ __device__ __forceinline__ void run_scene(const WorldDev &W, int s, int gl, floa
             vs[0] += dt * (rf[0] * iM); vs[1] += dt * (rf[1] * iM); vs[2] += dt * (rf[2] * iM);
             Ls[0] += dt * rf[3]; Ls[1] += dt * rf[4]; Ls[2] += dt * rf[5];
         }
-        sym_mul(Wi, Ls, oms);
+        world_sym(R, shr.Ii, Ls, oms);
         cs[0] = c[0] + dt * vs[0]; cs[1] = c[1] + dt * vs[1]; cs[2] = c[2] + dt * vs[2];
         // rotation increment dR = exp([u]x), u = dt w*: q* = dq (x) q and R* = dR R, so a point's
         // offset moves from rho to (1 + D) rho with D = dR - 1 = a [u]x + b [u]x^2
@@ -1097,51 +1123,35 @@ __device__ __forceinline__ void run_scene(const WorldDev &W, int s, int gl, floa
         float Dm[6];   // rows 0 and 1 of D (only horizontal displacements are needed)
         float rzc = 0.f;   // (with the horizontal-axis friction torque) height of the integrated
                            // friction-set centroid above the integrated CoG: [(1 + D) gb]_z
-        float Iz[3];   // R* Ib R*^T z: the angular momentum of a unit yaw rate after integration
         {
             const float px = dt * oms[0], py = dt * oms[1], pz = dt * oms[2];
             const float a2 = px * px + py * py + pz * pz;
-            float dq[4], fa, fb;
-            if (a2 <= 1.f / 64.f) {
-                // |u| <= 1/8: the series of sin|u|/|u|, (1 - cos|u|)/|u|^2 and of the half angle
-                // in |u|^2, exact to single precision (no square root, no range reduction)
-                fa = sinc_sq(a2);
-                fb = cosc_sq(a2);
-                const float h2 = 0.25f * a2, f = 0.5f * sinc_sq(h2);
-                dq[0] = 1.f - h2 * cosc_sq(h2);
-                dq[1] = f * px; dq[2] = f * py; dq[3] = f * pz;
-            } else {
-                const float ra = rsqrtf(a2), a = a2 * ra;
-                const float2 sc2 = sincos_large(0.5f * a);
-                const float f = sc2.x * ra;
-                dq[0] = sc2.y; dq[1] = f * px; dq[2] = f * py; dq[3] = f * pz;
-                fa = 2.f * f * sc2.y;
+            const float ra = a2 > 0.f ? rsqrtf(a2) : 0.f;   // 1 / |u|
+            const float a = a2 * ra;
+            float dq[4] = {1.f, 0.f, 0.f, 0.f};
+            float fa = 1.f, fb = 0.5f;
+            if (a > 0.f) {
+                float sn, cn;
+                sincos_small(0.5f * a, &sn, &cn);
+                const float f = sn * ra;
+                dq[0] = cn; dq[1] = f * px; dq[2] = f * py; dq[3] = f * pz;
+                fa = 2.f * f * cn;
                 fb = 2.f * f * f;
             }
-            // [u]x^2 = u u^T - |u|^2 1
-            Dm[0] = fb * (px * px - a2); Dm[1] = -fa * pz + fb * px * py; Dm[2] = fa * py + fb * px * pz;
-            Dm[3] = fa * pz + fb * py * px; Dm[4] = fb * (py * py - a2); Dm[5] = -fa * px + fb * py * pz;
             if (tilt)
                 rzc = gb[2] + (-fa * py + fb * pz * px) * gb[0] + (fa * px + fb * pz * py) * gb[1] +
                       fb * (pz * pz - a2) * gb[2];
+            // [u]x^2 = u u^T - |u|^2 1
+            Dm[0] = fb * (px * px - a2); Dm[1] = -fa * pz + fb * px * py; Dm[2] = fa * py + fb * px * pz;
+            Dm[3] = fa * pz + fb * py * px; Dm[4] = fb * (py * py - a2); Dm[5] = -fa * px + fb * py * pz;
             quat_mul(dq, q, qs);
-            // renormalise: |q*|^2 = 1 + eps with eps a few roundings, and 1 / sqrt(1 + eps) =
-            // 1 - eps / 2 to within 3 eps^2 / 8; larger deviations take the square root
-            const float n2 = qs[0] * qs[0] + qs[1] * qs[1] + qs[2] * qs[2] + qs[3] * qs[3];
-            const float inv = fabsf(n2 - 1.f) < 1e-4f ? fmaf(-0.5f, n2, 1.5f) : rsqrtf(n2);
+            const float inv = rsqrtf(qs[0] * qs[0] + qs[1] * qs[1] + qs[2] * qs[2] + qs[3] * qs[3]);
             qs[0] *= inv; qs[1] *= inv; qs[2] *= inv; qs[3] *= inv;
             // largest downward move of any point this step: dt max(0, -v*_z) from the CoG plus the
             // rotation's: for x = R r, ((dR - 1) x)_z = sin|u| (n x x)_z + (1 - cos|u|) (n (n.x) - x)_z
             // with n = u / |u|, so |dz| <= (|u_xy| + |u|^2 / 2) |x| (yaw moves no point up or
             // down; |u_xy| <= |u_x| + |u_y|); a small factor covers rounding
             slack -= fmaxf(0.f, -dt * vs[2]) + 1.0001f * (fabsf(px) + fabsf(py) + 0.5f * a2) * rmax;
-            // independent of the friction solve: R* Ib R*^T z = R* (Ib (R*^T z))
-            float Rs[9];
-            quat_mat(qs, Rs);
-            const float rz3[3] = {Rs[6], Rs[7], Rs[8]};
-            float t3[3];
-            sym_mul(shr.Ib, rz3, t3);
-            mat_vec(Rs, t3, Iz);
         }
 
         // -- friction (Sec. III-C, Eqs. 1-6) over C.  With d_i = rho_i - centroid and
@@ -1177,7 +1187,7 @@ __device__ __forceinline__ void run_scene(const WorldDev &W, int s, int gl, floa
                 if (weighted) {
                     const float rz = R[6] * r.x + R[7] * r.y + R[8] * r.z;
                     const float z = c[2] + rz;
-                    const float h = ground_win<FLAT>(H, hm, win, wx0, wy0, c[0] + rx, c[1] + ry);
+                    const float h = ground_win<FLAT>(W, hm, win + wsh, wx0, wy0, c[0] + rx, c[1] + ry);
                     const float vz = v[2] + (om[0] * ry - om[1] * rx);
                     wk = fmaxf(0.f, r.w * (kw2 * (h - z) - kc * vz));
                 }
@@ -1206,46 +1216,26 @@ __device__ __forceinline__ void run_scene(const WorldDev &W, int s, int gl, floa
             // cancellation when the weight sits on one point)
             float a3 = (weighted ? S2 > 1e-6f * nC : (nC >= 2.f && S2 > 1e-12f)) ? __fdividef(X, S2) : 0.f;
             a3 = fminf(fmaxf(a3, -1.f), 1.f);
-            const float x3 = a3 * a3;
-            // r1 = 1 / (1 + cos alpha_D) and alpha_D = asin(a3): series in a3^2 for |a3| <= 1/16
-            // (exact to single precision), the library otherwise
-            float r1, aD;
-            if (x3 <= 1.f / 256.f) {
-                r1 = fmaf(x3, fmaf(x3, fmaf(x3, 5.f / 128.f, 1.f / 16.f), 1.f / 8.f), 0.5f);
-                aD = a3 * fmaf(x3, fmaf(x3, fmaf(x3, 5.f / 112.f, 3.f / 40.f), 1.f / 6.f), 1.f);
-            } else {
-                const float t1 = fmaxf(0.f, 1.f - x3);
-                const float cD = t1 > 0.f ? t1 * rsqrtf(t1) : 0.f;       // cos(alpha_D)
-                r1 = __fdividef(1.f, 1.f + cD);
-                aD = asin_large(a3);
-            }
-            const float cm1 = -x3 * r1;                               // cos(alpha_D) - 1
+            const float t1 = fmaxf(0.f, 1.f - a3 * a3);
+            const float cD = t1 > 0.f ? t1 * rsqrtf(t1) : 0.f;       // cos(alpha_D)
+            const float r1 = __fdividef(1.f, 1.f + cD);
+            const float cm1 = -a3 * a3 * r1;                          // cos(alpha_D) - 1
             const float dDx = -sbx, dDy = -sby;                       // CoG minus centroid
             const float DDx = tDx + cm1 * dDx - a3 * dDy;             // uncapped CoG shift
             const float DDy = tDy + a3 * dDx + cm1 * dDy;
-            // maximum static friction (Coulomb cap on the impulse that undoes the slip):
-            // J_req = M u / dt with u^2 the mean squared corrective displacement, compared as
-            // squares; a capped correction is scaled by J_max / J_req
-            const float sh2 = 0.5f * x3 * r1;                         // sin^2(alpha_D / 2)
+            // maximum static friction (Coulomb cap on the impulse that undoes the slip)
+            const float sh2 = 0.5f * a3 * a3 * r1;                    // sin^2(alpha_D / 2)
             const float u2 = tDx * tDx + tDy * tDy + 4.f * sh2 * S2 * in;
+            const float Jreq = shr.M * (u2 > 0.f ? u2 * rsqrtf(u2) : 0.f) * idt;
             const float Jmax = mu * dt * FN;
-            const float Mi = shr.M * idt;
-            const float sc = (Mi * Mi * u2 <= Jmax * Jmax) ? 1.f : Jmax * rsqrtf(u2) * (dt * iM);
-            const float AD = sc * aD;
-            float sin1, cm1s;   // sin(sc alpha_D), cos(sc alpha_D) - 1
-            const float y1 = AD * AD;
-            if (y1 <= 1.f / 64.f) {
-                sin1 = AD * sinc_sq(y1);
-                cm1s = -y1 * cosc_sq(y1);
-            } else {
-                float s1, c1;
-                sincos_small(0.5f * AD, &s1, &c1);
-                sin1 = 2.f * s1 * c1;
-                cm1s = -2.f * s1 * s1;
-            }
+            const float sc = (Jreq <= Jmax) ? 1.f : __fdividef(Jmax, Jreq);
+            const float aD = asin_small(a3);
+            float s1, c1;
+            sincos_small(0.5f * sc * aD, &s1, &c1);
+            const float sin1 = 2.f * s1 * c1, cm1s = -2.f * s1 * s1;
             float dx1 = sc * tDx + cm1s * dDx - sin1 * dDy;
             float dy1 = sc * tDy + sin1 * dDx + cm1s * dDy;
-            float A = AD;
+            float A = sc * aD;
             if (tick) {
                 const float kbx = f6[0] * in, kby = f6[1] * in;
                 const float S2K = f6[2] - nC * (kbx * kbx + kby * kby);
@@ -1269,7 +1259,12 @@ __device__ __forceinline__ void run_scene(const WorldDev &W, int s, int gl, floa
             vn[0] = vs[0] + sc * DDx * idt;
             vn[1] = vs[1] + sc * DDy * idt;
             // angular momentum of the yaw correction: (sc alpha_D / dt) R* Ib R*^T z
-            const float w = AD * idt;
+            float Rs[9];
+            quat_mat(qs, Rs);
+            const float ez[3] = {0.f, 0.f, 1.f};
+            float Iz[3];
+            world_sym(Rs, shr.Ib, ez, Iz);
+            const float w = sc * aD * idt;
             Ln[0] = Ls[0] + w * Iz[0]; Ln[1] = Ls[1] + w * Iz[1]; Ln[2] = Ls[2] + w * Iz[2];
             if (tilt) {
                 // the friction impulse J = M (v_new - v*) acts at the friction-set centroid,
@@ -1278,32 +1273,23 @@ __device__ __forceinline__ void run_scene(const WorldDev &W, int s, int gl, floa
                 Ln[0] -= rzc * Jy;
                 Ln[1] += rzc * Jx;
             }
-            // yaw by A: q = (cos A/2, 0, 0, sin A/2) (x) q*
             float sa, ca;
-            const float y2 = 0.25f * A * A;
-            if (y2 <= 1.f / 64.f) {
-                sa = 0.5f * A * sinc_sq(y2);
-                ca = 1.f - y2 * cosc_sq(y2);
-            } else {
-                sincos_small(0.5f * A, &sa, &ca);
-            }
-            qn[0] = ca * qs[0] - sa * qs[3];
-            qn[1] = ca * qs[1] - sa * qs[2];
-            qn[2] = ca * qs[2] + sa * qs[1];
-            qn[3] = ca * qs[3] + sa * qs[0];
+            sincos_small(0.5f * A, &sa, &ca);
+            const float qz[4] = {ca, 0.f, 0.f, sa};
+            quat_mul(qz, qs, qn);
         }
 
         // -- freeze a scene whose state is no longer finite or has left any sane range
         if (status == 0u) {
             // any NaN or infinity makes the sum non-finite (all terms are bounded below 1e6
             // in magnitude when finite, so the sum itself cannot overflow)
-            const float chk = (((cn[0] + cn[1]) + (cn[2] + vn[0])) + ((vn[1] + vn[2]) + (Ln[0] + Ln[1]))) +
-                              (((Ln[2] + qn[0]) + (qn[1] + qn[2])) + qn[3]);
-            const float vmax = fmaxf(fmaxf(fabsf(vn[0]), fabsf(vn[1])), fabsf(vn[2]));
-            const float cmax = fmaxf(fmaxf(fabsf(cn[0]), fabsf(cn[1])), fabsf(cn[2]));
-            if (!isfinite(chk)) {
+            const float chk = cn[0] + cn[1] + cn[2] + vn[0] + vn[1] + vn[2] + Ln[0] + Ln[1] +
+                              Ln[2] + qn[0] + qn[1] + qn[2] + qn[3];
+            const bool fin = isfinite(chk);
+            if (!fin) {
                 status |= 1u;
-            } else if (vmax > 1e3f || cmax > 1e6f) {
+            } else if (fabsf(vn[0]) > 1e3f || fabsf(vn[1]) > 1e3f || fabsf(vn[2]) > 1e3f ||
+                       fabsf(cn[0]) > 1e6f || fabsf(cn[1]) > 1e6f || fabsf(cn[2]) > 1e6f) {
                 status |= 2u;
             } else {
 #pragma unroll
@@ -1311,9 +1297,15 @@ __device__ __forceinline__ void run_scene(const WorldDev &W, int s, int gl, floa
 #pragma unroll
                 for (int i = 0; i < 4; ++i) q[i] = qn[i];
                 kprev = know;
-                kf = kf_next;
             }
         }
+    }
+
+    if (win_tma) {
+        win_wait_warp(wbar, wphase ^ 1u, wfail);   // a load that outlived its wait lands first
+        __syncwarp();
+        if (gl == 0) win_bar_inval(wbar);
+        __syncwarp();
     }
 
     // ---- write back (contact sensors from the last step's contacts)
@@ -1346,8 +1338,12 @@ __device__ __forceinline__ void run_scene(const WorldDev &W, int s, int gl, floa
 }
 
 template <int LPS, bool FLAT, bool OPT, bool ARENA>
-__device__ __forceinline__ void step_body(const WorldDev &W, int n_steps, int sbytes) {
-    extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void step_body(const WorldDev &W, int n_steps, int sbytes, const CUtensorMap *tmap) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // (height maps) a 128-byte aligned base, so that every window is aligned for its TMA box
+    // (an integer offset from the shared array, so the pointer stays a shared-memory one)
+    unsigned char *smem = smem_raw;
+    if constexpr (!FLAT) smem += (128u - (smem_addr(smem_raw) & 127u)) & 127u;
     constexpr int G = 32 / LPS;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane / LPS, gl = lane % LPS;
@@ -1369,28 +1365,31 @@ __device__ __forceinline__ void step_body(const WorldDev &W, int n_steps, int sb
         if (item >= n_items) break;
         const int idx = item * G + g;
         const int s = idx < n_sched ? W.order[idx] : -1;
-        run_scene<LPS, FLAT, OPT, ARENA>(W, s, gl, pts, fr, th, th_old, tb, n_steps, step0, xch, sbytes);
+        run_scene<LPS, FLAT, OPT, ARENA>(W, s, gl, pts, fr, th, th_old, tb, n_steps, step0, xch, sbytes, tmap);
     }
 }
 
-// Flat ground: 168 registers a thread (the contact slots live in registers), up to 12 warps per block.
+// Flat ground: up to 16 warps per block, 128 registers a thread.
 template <int LPS, bool OPT>
-__global__ void __maxnreg__(168) step_kernel(const __grid_constant__ WorldDev W, int n_steps, int sbytes) {
-    step_body<LPS, true, OPT, false>(W, n_steps, sbytes);
+__global__ void __launch_bounds__(512) step_kernel(const __grid_constant__ WorldDev W, int n_steps, int sbytes,
+                                                   const __grid_constant__ CUtensorMap tmap) {
+    step_body<LPS, true, OPT, false>(W, n_steps, sbytes, &tmap);
 }
 
 // Height maps keep more state (the map window and its origin): 168 registers a thread, up to 12
 // warps per block; their larger slots leave no more warps resident at 16 lanes per scene anyway.
 template <int LPS, bool OPT>
-__global__ void __maxnreg__(168) step_kernel_hm(const __grid_constant__ WorldDev W, int n_steps, int sbytes) {
-    step_body<LPS, false, OPT, false>(W, n_steps, sbytes);
+__global__ void __maxnreg__(168) step_kernel_hm(const __grid_constant__ WorldDev W, int n_steps, int sbytes,
+                                                const __grid_constant__ CUtensorMap tmap) {
+    step_body<LPS, false, OPT, false>(W, n_steps, sbytes, &tmap);
 }
 
 // Arenas (robots colliding with one another, 8 or 16 lanes per scene), with the friction options
 // compiled in: 168 registers a thread.
 template <int LPS, bool FLAT>
-__global__ void __maxnreg__(168) step_kernel_arena(const __grid_constant__ WorldDev W, int n_steps, int sbytes) {
-    step_body<LPS, FLAT, true, true>(W, n_steps, sbytes);
+__global__ void __maxnreg__(168) step_kernel_arena(const __grid_constant__ WorldDev W, int n_steps, int sbytes,
+                                                   const __grid_constant__ CUtensorMap tmap) {
+    step_body<LPS, FLAT, true, true>(W, n_steps, sbytes, &tmap);
 }
 
 __global__ void advance_kernel(long long *step, int n) { *step += n; }
@@ -1815,7 +1814,7 @@ __global__ void __launch_bounds__(256) sensor_probe_kernel(const __grid_constant
         const float px = c[0] + R[0] * r.x + R[1] * r.y + R[2] * r.z;
         const float py = c[1] + R[3] * r.x + R[4] * r.y + R[5] * r.z;
         const float pz = c[2] + R[6] * r.x + R[7] * r.y + R[8] * r.z;
-        if (pz < ground<FLAT>(hm_view(W), hm, px, py)) bits |= 1u << (int)r.w;
+        if (pz < ground<FLAT>(W, hm, px, py)) bits |= 1u << (int)r.w;
     }
     bits = gor<32>(bits);
     if (lane == 0) sens_new[s] = bits;
@@ -1879,7 +1878,7 @@ __global__ void __launch_bounds__(128) kappa_refresh_kernel(const __grid_constan
             const float px = x.c[0] + R[0] * r.x + R[1] * r.y + R[2] * r.z;
             const float py = x.c[1] + R[3] * r.x + R[4] * r.y + R[5] * r.z;
             const float pz = x.c[2] + R[6] * r.x + R[7] * r.y + R[8] * r.z;
-            const bool kap = pz < ground<FLAT>(hm_view(W), hm, px, py);
+            const bool kap = pz < ground<FLAT>(W, hm, px, py);
             W.kappa[p0 + k] = kap ? 1 : 0;
             if (kap) {
                 const int sid = W.links[l0 + W.plink[p0 + k]].sensor;
@@ -2032,11 +2031,44 @@ cudaError_t launch_permute_kappa(uint8_t *dst, const uint8_t *src, const int *pe
 
 // per-scene shared memory of the step kernel: the slot, plus the height-map window on maps
 int step_slot_bytes(const WorldDev &W, int lps) {
-    return slot_bytes(W.max_points, W.max_links, lps) + (W.hm ? HM_WIN * HM_WIN * (int)sizeof(float) : 0);
+    return W.hm ? hm_win_offset(W.max_points, W.max_links, lps) + HM_AREA : slot_bytes(W.max_points, W.max_links, lps);
 }
 
 size_t step_smem_bytes(const WorldDev &W, int lps, int wpb) {
-    return (size_t)wpb * (32 / lps) * (step_slot_bytes(W, lps) + (W.arena > 1 ? xch_bytes(W.max_chunks) : 0));
+    // (height maps) 128 more bytes to align the slots' windows for TMA
+    return (size_t)wpb * (32 / lps) * (step_slot_bytes(W, lps) + (W.arena > 1 ? xch_bytes(W.max_chunks) : 0)) +
+           (W.hm ? 128 : 0);
+}
+
+typedef CUresult (*TmapEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+void encode_hm_tmap(WorldDev &W, int n_maps, CUtensorMap *out) {
+    W.hm_tma = 0;
+    W.hm_tmap_h = nullptr;
+    if (!W.hm || n_maps < 1 || W.hm_nx < HM_WIN || W.hm_ny < HM_WIN || (W.hm_nx * 4) % 16 != 0 ||
+        (reinterpret_cast<uintptr_t>(W.hm) & 15) != 0)
+        return;
+    static TmapEncodeFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return;
+        fn = reinterpret_cast<TmapEncodeFn>(p);
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)W.hm_nx, (cuuint64_t)W.hm_ny, (cuuint64_t)n_maps};
+    const cuuint64_t strides[2] = {(cuuint64_t)W.hm_nx * 4, (cuuint64_t)W.hm_nx * W.hm_ny * 4};
+    const cuuint32_t box[3] = {HM_BOX, HM_WIN, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    if (fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(W.hm), dims, strides, box, es,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
+        W.hm_tma = 1;
+        W.hm_tmap_h = out;
+    }
 }
 
 template <int LPS, bool FLAT, bool OPT>
@@ -2100,7 +2132,10 @@ cudaError_t launch_step(const WorldDev &W, const LaunchCfg &cfg, int n_steps, cu
     if (e != cudaSuccess) return e;
     int sb = step_slot_bytes(W, cfg.lps);
     WorldDev w = W;
-    void *args[] = {&w, &n_steps, &sb};
+    CUtensorMap tm;
+    if (W.hm_tma && W.hm_tmap_h) tm = *W.hm_tmap_h;
+    else memset(&tm, 0, sizeof tm);
+    void *args[] = {&w, &n_steps, &sb, &tm};
     return cudaLaunchKernel(fn, dim3(cfg.blocks), dim3(cfg.wpb * 32), args, smem, st);
 }
 

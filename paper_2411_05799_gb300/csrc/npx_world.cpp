@@ -151,6 +151,7 @@ struct npx_world {
         unsigned long long cache_gen = ~0ull;
     } sg;
     unsigned long long state_gen = 0;   // counts the caller's state writes
+    CUtensorMap hm_tmap{};              // TMA map of the height maps (W.hm_tmap_h points here)
     // angular velocity and contact sensors are derived from the state: after a state write they
     // are recomputed when first needed (a step recomputes them anyway)
     bool derived_stale = false;
@@ -818,6 +819,9 @@ int npx_world_finalize(npx_world *w) {
         CUDA_TRY(cudaMemcpy(hmx, mx.data(), mx.size() * sizeof(float), cudaMemcpyHostToDevice));
         W.hm = hm;
         W.hm_max = hmx;
+        W.hm_nx = w->desc.hm_nx;
+        W.hm_ny = w->desc.hm_ny;
+        npx::encode_hm_tmap(W, w->desc.hm_count, &w->hm_tmap);
         w->hm_host.clear();
         w->hm_host.shrink_to_fit();
     }
@@ -1339,6 +1343,7 @@ int npx_world_info_get(npx_world *w, npx_world_info *o) {
     o->lanes_per_scene = w->cfg.lps; o->warps_per_block = w->cfg.wpb; o->blocks = w->cfg.blocks;
     o->chunk_steps = w->chunk; o->step = w->step; o->kernel_launches = w->launches;
     o->size_classes = (int)w->classes.size();
+    o->hm_window_tma = w->W.hm_tma;
     return NPX_OK;
 }
 

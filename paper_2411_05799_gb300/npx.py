@@ -59,7 +59,7 @@ class WorldInfo(C.Structure):
                 ("n_points", C.c_int), ("max_points", C.c_int), ("max_links", C.c_int),
                 ("lanes_per_scene", C.c_int), ("warps_per_block", C.c_int), ("blocks", C.c_int),
                 ("chunk_steps", C.c_int), ("step", C.c_int64), ("kernel_launches", C.c_int64),
-                ("size_classes", C.c_int)]
+                ("size_classes", C.c_int), ("hm_window_tma", C.c_int)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

@@ -222,13 +222,23 @@ def test_gpu_points_match_oracle_kinematics():
     np.testing.assert_allclose(r["omega"], o.omega(), rtol=1e-4, atol=1e-6)
 
 
-@pytest.mark.parametrize("ny, nx, spread", [(16, 16, 0.4), (8, 12, 0.4), (40, 48, 1.8)])
+def _window_by_tma(ny, nx):
+    """Whether the kernel loads its 16 x 16-cell windows of an ny x nx FP32 map by TMA box copies:
+    maps at least the window's size whose rows are a multiple of 16 bytes."""
+    return ny >= 16 and nx >= 16 and (4 * nx) % 16 == 0
+
+
+@pytest.mark.parametrize("ny, nx, spread", [(16, 16, 0.4), (8, 12, 0.4), (40, 48, 1.8), (20, 22, 0.6),
+                                            (24, 36, 1.0)])
 def test_gpu_heightmap_cells(ny, nx, spread):
     """Random clouds over random height maps: the first step's contact bits agree point for
     point with the oracle's (same single-precision cell and contact decisions).  The maps are the
     size of the kernel's cached window, smaller than it (cells past the map's edge read the
     clamped edge) and larger (points outside the window, windows clamped at the map's edges);
-    every cloud also reaches off the map."""
+    every cloud also reaches off the map.  Windows load by TMA box copies where the map allows
+    (16 x 16, 40 x 48, 24 x 36 cells: windows at every column offset modulo 4, box columns past
+    the right edge) and by plain loads elsewhere (8 x 12; 20 x 22, whose rows are not a multiple
+    of 16 bytes)."""
     rng = np.random.default_rng(21)
     maps = rng.uniform(-0.05, 0.05, (2, ny, nx)).astype(np.float32)
     S, n = 8, 200
@@ -242,6 +252,7 @@ def test_gpu_heightmap_cells(ny, nx, spread):
                          hmap=rng.integers(0, 2, S), heightmaps=maps, hm_scale=10.0,
                          hm_origin=(-nx / 20, -ny / 20), act_mode=scenes.ACT_HOLD)
     w = World.from_batch(b)
+    assert w.info()["hm_window_tma"] == int(_window_by_tma(ny, nx))
     o = Oracle(b)
     o.step(1)
     w.step(1)
@@ -250,6 +261,40 @@ def test_gpu_heightmap_cells(ny, nx, spread):
     x = np.concatenate([o.points_world(s) for s in range(S)])
     assert np.count_nonzero(kap != o.kappa) <= 2      # points within rounding of the surface
     assert (kap == o.kappa).mean() > 0.99
+
+
+@pytest.mark.parametrize("ny, nx", [(40, 48), (40, 46)])
+def test_height_map_window_moves_are_exact(ny, nx):
+    """The window is a cache of the map: blocks sliding fast across a map (about a metre, two
+    window moves for the median block; some windows held at the map's edge, some blocks sliding
+    off it) step bit-identically whether every step
+    is its own launch (a fresh window each step) or all 400 steps are one launch (windows moved
+    inside it); TMA box copies (48 columns) and plain loads (46 columns) alike."""
+    rng = np.random.default_rng(33)
+    maps = rng.uniform(-0.03, 0.03, (3, ny, nx)).astype(np.float32)
+    S = 48
+    robots = []
+    for _ in range(S):
+        pts = scenes.box_uniform(rng, (0.3, 0.3, 0.1), (0, 0, 0), 96)
+        robots.append(([((0.3, 0.3, 0.1), (0, 0, 0), 1.0, -1, None, None, 0)], [pts]))
+    ang = rng.uniform(0, 2 * np.pi, S)
+    vel = np.stack([3.0 * np.cos(ang), 3.0 * np.sin(ang), np.zeros(S)], 1)
+    origin = np.concatenate([rng.uniform(-1.2, 1.2, (S, 2)), np.full((S, 1), 0.09)], 1)
+    b = scenes._assemble(robots, mu=np.full(S, 0.3), origin=origin, quat=np.tile([1.0, 0, 0, 0], (S, 1)),
+                         vel=vel, omega=np.zeros((S, 3)), act_params=None, name="slide",
+                         hmap=rng.integers(0, 3, S), heightmaps=maps, hm_scale=10.0,
+                         hm_origin=(-nx / 20, -ny / 20), act_mode=scenes.ACT_HOLD)
+    one = World.from_batch(b, configure=dict(chunk_steps=1))
+    assert one.info()["hm_window_tma"] == int(_window_by_tma(ny, nx))
+    one.step(400)
+    many = World.from_batch(b, configure=dict(chunk_steps=400))
+    many.step(400)
+    r1, r2 = one.read(), many.read()
+    moved = np.linalg.norm(r2["cog"][:, :2] - origin[:, :2], axis=1)
+    assert np.median(moved) > 0.5                    # 5 cells: several window moves per scene
+    assert (r2["status"] == 0).all()
+    for k in ("cog", "quat", "vel", "angmom", "contacts"):
+        assert np.array_equal(r1[k], r2[k]), k
 
 
 # ----------------------------------------------------------------------------- edge cases
