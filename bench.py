@@ -46,7 +46,13 @@ FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_GHZ / 1e3
 # DRAM bytes (read + write) of one 1,000-step step-kernel launch, by workload and launch shape
 # (lanes per scene, warps per block, blocks), from ncu (profiles/step_kernel_*_dram.md); reported
 # only for a captured shape, and to be re-taken whenever the kernel changes
-STEP_TRAFFIC = {}
+STEP_TRAFFIC = {
+    (WORKLOAD, 8, 7, 147): 31_890_176,
+    (WORKLOAD, 16, 14, 147): 31_950_848,
+    ("hexapod_rough_terrain_16384_scenes", 16, 4, 456): 211_604_736,
+    ("hexapod_rough_terrain_16384_scenes", 16, 2, 912): 211_816_960,
+    ("hexapod_rough_terrain_16384_scenes", 16, 1, 1824): 212_502_528,
+}
 
 
 def counted_flops_per_scene_step(batch, n_scenes: int, n_steps: int, warm_steps: int) -> dict:
