@@ -89,6 +89,11 @@ struct WorldDev {
     // their own; hm_tma = 0 when the maps do not allow it (window loads by plain gathers)
     int hm_tma;
     const CUtensorMap *hm_tmap_h;
+    // (height maps) the highest cell within hm_dr cells of every cell (a square, clamped to the
+    // map) [H * ny * nx], or NULL: a scene's cull compares its tiles with the entry at its CoG's
+    // cell while all its points stay within hm_dr cells of that cell, else with the map's highest
+    const float *hm_dmax;
+    int hm_dr;
 };
 
 struct LaunchCfg {
@@ -155,6 +160,10 @@ cudaError_t launch_points(const WorldDev &W, int scene, float *d_out, cudaStream
 // W.hm_tma (1) and W.hm_tmap_h (out) on success; leaves hm_tma 0 otherwise (or when the encoder is
 // unavailable).  out must outlive every launch of the world.
 void encode_hm_tmap(WorldDev &W, int n_maps, CUtensorMap *out);
+// out [H * ny * nx] = the highest cell of hm within R cells along x and y (clamped to the map);
+// tmp is scratch of the same size
+cudaError_t launch_hm_dilate(const float *hm, float *tmp, float *out, int H, int ny, int nx, int R,
+                             cudaStream_t st);
 
 }  // namespace npx
 

@@ -893,6 +893,13 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
     Shape shr = sh;
     // highest ground a point can meet (plus a margin for the rounding of the bound)
     const float hmax = (FLAT || hm < 0 ? 0.f : W.hm_max[hm]) + 1e-5f;
+    // (height maps) the ground bound of the cull: the map's highest cell, or, while the scene's
+    // points all lie within hm_dr cells of its CoG's cell at the last cull, the dilated map's
+    // entry there (local: in use; dm_lim: the largest posed radius plus drift that keeps it valid)
+    const bool dm = !FLAT && hm >= 0 && W.hm_dmax != nullptr;
+    const float dm_lim = dm ? ((float)W.hm_dr - 1.5f) / W.hm_scale : 0.f;
+    float hcull = hmax, cull_x = 0.f, cull_y = 0.f;
+    bool local = false;
     // height-map window (after the slot); its origin is negative until the first refresh.  With
     // TMA the window's first cell sits wsh cells into each stored row; its mbarrier follows it.
     float *win = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(pts) +
@@ -1024,13 +1031,28 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
                 __syncwarp();
             }
         }
+        // a local ground bound holds while every point is within hm_dr cells of the cull's cell:
+        // |x - c_cull| <= rmax + |c - c_cull| (max norm; the rotation keeps |R p| <= rmax), and
+        // clamping a cell index to the map moves it no further from the clamped centre
+        if (!FLAT && local && rmax + fmaxf(fabsf(c[0] - cull_x), fabsf(c[1] - cull_y)) > dm_lim) slack = -1.f;
         // the cull's ballots involve the whole warp: every group culls when any one needs to
         if (__any_sync(FULL_MASK, slack < 0.f)) {
-            // the slack is the height of the lowest tile left out above the highest ground (at
+            if (!FLAT) {
+                local = dm && rmax <= dm_lim;
+                hcull = hmax;
+                if (local) {
+                    cull_x = c[0];
+                    cull_y = c[1];
+                    const int ix = min(max(__float2int_rd(__fmul_rn(__fsub_rn(c[0], W.hm_ox), W.hm_scale)), 0), W.hm_nx - 1);
+                    const int iy = min(max(__float2int_rd(__fmul_rn(__fsub_rn(c[1], W.hm_oy), W.hm_scale)), 0), W.hm_ny - 1);
+                    hcull = fminf(hmax, __ldg(W.hm_dmax + ((size_t)hm * W.hm_ny + iy) * W.hm_nx + ix) + 1e-5f);
+                }
+            }
+            // the slack is the height of the lowest tile left out above the ground bound (at
             // least CULL_MARGIN; unbounded when no tile is left out)
             float zfar;
-            cand = tiles_near_ground<LPS>(tb, ntiles, R, c[2], hmax + CULL_MARGIN, gl, zfar);
-            slack = fminf(zfar - hmax, 1e30f);
+            cand = tiles_near_ground<LPS>(tb, ntiles, R, c[2], hcull + CULL_MARGIN, gl, zfar);
+            slack = fminf(zfar - hcull, 1e30f);
         }
         // reference o of the friction-set moments: the rotated centre of the first tile holding a
         // point that was in contact last step (C is a subset of those; o depends on the state alone)
@@ -2038,6 +2060,33 @@ size_t step_smem_bytes(const WorldDev &W, int lps, int wpb) {
     // (height maps) 128 more bytes to align the slots' windows for TMA
     return (size_t)wpb * (32 / lps) * (step_slot_bytes(W, lps) + (W.arena > 1 ? xch_bytes(W.max_chunks) : 0)) +
            (W.hm ? 128 : 0);
+}
+
+// One pass of the dilated height map: the highest cell within R cells along x (along_y = 0) or y
+// (along_y = 1), clamped to the map; two passes give the maximum over the (2R + 1)^2 square.
+__global__ void hm_dilate_kernel(const float *in, float *out, int H, int ny, int nx, int R, int along_y) {
+    const size_t n = (size_t)H * ny * nx;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % (size_t)nx), y = (int)((i / (size_t)nx) % (size_t)ny);
+        float m = -INFINITY;
+        if (along_y) {
+            const float *col = in + (i - (size_t)y * nx);
+            for (int k = max(y - R, 0); k <= min(y + R, ny - 1); ++k) m = fmaxf(m, col[(size_t)k * nx]);
+        } else {
+            const float *row = in + (i - x);
+            for (int k = max(x - R, 0); k <= min(x + R, nx - 1); ++k) m = fmaxf(m, row[k]);
+        }
+        out[i] = m;
+    }
+}
+
+cudaError_t launch_hm_dilate(const float *hm, float *tmp, float *out, int H, int ny, int nx, int R,
+                             cudaStream_t st) {
+    const size_t n = (size_t)H * ny * nx;
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 64);
+    hm_dilate_kernel<<<blocks, 256, 0, st>>>(hm, tmp, H, ny, nx, R, 0);
+    hm_dilate_kernel<<<blocks, 256, 0, st>>>(tmp, out, H, ny, nx, R, 1);
+    return cudaGetLastError();
 }
 
 typedef CUresult (*TmapEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,

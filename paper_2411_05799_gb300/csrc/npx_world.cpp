@@ -822,6 +822,28 @@ int npx_world_finalize(npx_world *w) {
         W.hm_nx = w->desc.hm_nx;
         W.hm_ny = w->desc.hm_ny;
         npx::encode_hm_tmap(W, w->desc.hm_count, &w->hm_tmap);
+        // the dilated map of the cull's local ground bound: radius R cells covers the largest
+        // rest-pose radius about the rest CoG, a quarter more for the joints' reach and 4 cells of
+        // drift between culls (a larger posed robot falls back to the map's highest cell)
+        float r_rest = 0.f;
+        for (int s = 0; s < S; ++s)
+            for (int i = w->point_off[s]; i < w->point_off[s + 1]; ++i) {
+                const float dx = p0m[i].x - gref[3 * s], dy = p0m[i].y - gref[3 * s + 1],
+                            dz = p0m[i].z - gref[3 * s + 2];
+                r_rest = std::max(r_rest, std::sqrt(dx * dx + dy * dy + dz * dz));
+            }
+        const int R = std::min((int)std::ceil(1.25f * r_rest * w->desc.hm_scale) + 4,
+                               std::max(w->desc.hm_nx, w->desc.hm_ny));
+        float *dmax = nullptr, *tmp = nullptr;
+        if (int rc = dev_alloc(w, &dmax, w->hm_host.size())) return rc;
+        CUDA_TRY(cudaMalloc(&tmp, w->hm_host.size() * sizeof(float)));
+        cudaError_t de = npx::launch_hm_dilate(hm, tmp, dmax, w->desc.hm_count, w->desc.hm_ny, w->desc.hm_nx, R,
+                                               w->stream);
+        if (de == cudaSuccess) de = cudaStreamSynchronize(w->stream);
+        cudaFree(tmp);
+        if (de != cudaSuccess) return fail(NPX_ECUDA, "height-map dilation: %s", cudaGetErrorString(de));
+        W.hm_dmax = dmax;
+        W.hm_dr = R;
         w->hm_host.clear();
         w->hm_host.shrink_to_fit();
     }
