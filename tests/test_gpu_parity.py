@@ -75,9 +75,38 @@ def test_rough_terrain_cpg_per_step():
 
 
 def test_rough_terrain_200_step_window():
+    """The flat hexapods' bar: 95% of the scenes within 1 mm and 1 mrad of the oracle after 200
+    steps (on 512 scenes of four such windows all were within 1e-3 and 508 within 1e-5)."""
     dc, da, r, o = _window(scenes.cpg_batch(64, seed_key=3), 500)
-    assert ((dc <= 1e-3) & (da <= 1e-3)).mean() >= 0.9
+    ok = (dc <= 1e-3) & (da <= 1e-3)
+    assert ok.mean() >= 0.95, f"{(~ok).sum()} of {len(ok)} scenes outside 1e-3 m / 1e-3 rad"
     assert np.median(dc) < 1e-5
+
+
+@pytest.mark.parametrize("terrain", ["flat", "rough"])
+def test_true_relative_error_of_velocity_and_angular_momentum(terrain):
+    """The per-step checks divide by max(|ref|, 1), which for velocities and angular momenta
+    (typically 0.2 m/s and 0.04 kg m^2/s) is an absolute bound.  Here the relative error of the
+    whole vector, |gpu - oracle| / |oracle|, is bounded by 5e-5 on every scene not decided by
+    rounding at the ground (measured worst: 5.3e-6 for v, 7.7e-6 for L).  Vectors shorter than
+    1e-3 of their unit are left out (a resting robot's jitter)."""
+    b = scenes.hexapod_batch(64, seed_key=7) if terrain == "flat" else scenes.cpg_batch(32, seed_key=2)
+    w = World.from_batch(b)
+    o = Oracle(b, threads=THREADS)
+    worst = {"vel": 0.0, "angmom": 0.0}
+    n_checked = 0
+    for n in [1, 80, 81, 333, 800, 1600]:
+        o.step(n - o.n, threads=THREADS)
+        err, near, o2, r = per_step_compare(w, o, THREADS)
+        for k, ref in (("vel", o2.v), ("angmom", o2.L)):
+            mag = np.linalg.norm(ref, axis=1)
+            keep = ~near & (mag >= 1e-3)
+            e = np.linalg.norm(np.asarray(r[k], np.float64) - ref, axis=1)[keep] / mag[keep]
+            worst[k] = max(worst[k], e.max(initial=0.0))
+            n_checked += int(keep.sum())
+    assert n_checked > 300
+    for k, v in worst.items():
+        assert v <= 5e-5, f"{k}: worst relative error {v:.3g}"
 
 
 def _window(b, n0, horizon=200, lps=0):
