@@ -343,7 +343,9 @@ def surrogate_leg(World, scenes, stream, device, n_transitions: int, stride: int
     the 4,096-hexapod workload, then stepping 65,536 hexapods (joint-update steps, the steps left
     before them and scenes whose foot contacts change over a window are taken by the plain step);
     its throughput beside the plain step's on the same scenes, its 50-step error against the FP64
-    oracle on 256 held-out scenes, and its network's forward pass against the bf16 tensor peak."""
+    oracle on 256 held-out scenes, and its network's forward pass against the bf16 tensor peak.
+    Windows longer than one step are also timed and evaluated with the rule that never falls back
+    (`never_fall_back`): the throughput the network alone gives, at its own stated error."""
     import torch
     from oracle.oracle import Oracle
     from paper_2411_05799_gb300 import npx, surrogate
@@ -375,17 +377,25 @@ def surrogate_leg(World, scenes, stream, device, n_transitions: int, stride: int
     w.step(CHUNK)
     ms, _ = timed(lambda: w.step(CHUNK), 2)
     out["plain_value"] = S * 2 * CHUNK / (ms / 1e3)
-    # surrogate steps: whole joint-update periods, after one warm-up period
-    sur.step(w, PERIOD)
-    fb_total, reps = 0, 4
-    ms, _ = 0.0, None
-    for _ in range(reps):
-        m, fb = timed(lambda: sur.step(w, PERIOD), 1)
-        ms += m
-        fb_total += fb
-    out["value"] = S * PERIOD * reps / (ms / 1e3)
-    out["ms_per_step"] = ms / (PERIOD * reps)
-    out["fallback_fraction"] = fb_total / (S * PERIOD * reps)
+    # surrogate steps: whole joint-update periods from the step after a joint update (n mod K = 1:
+    # the windows, then the plain steps up to and through the next joint update), after one
+    # warm-up period; for each fallback rule
+    w.step((1 - w.info()["step"]) % PERIOD)
+
+    def time_rule(bits):
+        npx.surrogate_set_fallback(w, bits)
+        sur.step(w, PERIOD)
+        fb_total, reps, ms = 0, 4, 0.0
+        for _ in range(reps):
+            m, fb = timed(lambda: sur.step(w, PERIOD), 1)
+            ms += m
+            fb_total += fb
+        return {"value": S * PERIOD * reps / (ms / 1e3), "ms_per_step": ms / (PERIOD * reps),
+                "fallback_fraction": fb_total / (S * PERIOD * reps)}
+
+    rules = {"any_change": 0} if stride == 1 else {"any_change": 0, "never": -1}
+    timing = {name: time_rule(bits) for name, bits in rules.items()}
+    out.update(timing["any_change"])
     out["frozen_scenes"] = int((w.read()["status"] != 0).sum())
     w.close()
     # the network's forward pass over all scenes: five BF16 GEMMs with fused epilogues
@@ -428,35 +438,50 @@ def surrogate_leg(World, scenes, stream, device, n_transitions: int, stride: int
                 "angle_rad_median": float(np.median(ang)), "angle_rad_rms": float(np.sqrt(np.mean(ang ** 2))),
                 "angle_rad_p90": float(np.percentile(ang, 90))}
 
-    err = {}
-    for name, fn in (("surrogate", lambda ww: sur.step(ww, 50)),
-                     ("plain", lambda ww: ww.step(50))):
-        ww = World.from_batch(test_b, stream=stream.cuda_stream, device=device.index or 0)
-        ww.write_state(o.c.astype(np.float32), o.q.astype(np.float32), o.v.astype(np.float32),
-                       o.L.astype(np.float32), o.theta.astype(np.float32),
-                       o.kappa.astype(np.uint8), o.n)
-        if name == "surrogate":
-            npx.surrogate_fallback_counts(ww)        # counters from zero
-        fb = fn(ww)
-        r = ww.read()
-        dc = np.linalg.norm(r["cog"] - ref.c, axis=1)
-        qa, qb = r["quat"].astype(np.float64), ref.q
-        ang = 2 * np.arctan2(np.linalg.norm(qa - qb, axis=1), np.linalg.norm(qa + qb, axis=1))
-        ang = np.minimum(ang, 2 * np.pi - ang)
-        err[name] = errors(dc, ang)
-        if name == "surrogate":
-            # scene-steps of the 50 that the plain step took (fallbacks), and the error of the
-            # scenes the network carried through every window of the 50 steps apart from those
-            # whose windows (some or all) the plain step redid
-            err[name]["fallback_fraction"] = fb / (test_b.n_scenes * 50)
-            stayed = npx.surrogate_fallback_counts(ww) == 0
-            err[name]["stayed_on_network"] = errors(dc[stayed], ang[stayed])
-            err[name]["fell_back_at_least_once"] = errors(dc[~stayed], ang[~stayed])
-        ww.close()
+    def rollout_errors(bits):
+        err = {}
+        for name, fn in (("surrogate", lambda ww: sur.step(ww, 50)),
+                         ("plain", lambda ww: ww.step(50))):
+            ww = World.from_batch(test_b, stream=stream.cuda_stream, device=device.index or 0)
+            ww.write_state(o.c.astype(np.float32), o.q.astype(np.float32), o.v.astype(np.float32),
+                           o.L.astype(np.float32), o.theta.astype(np.float32),
+                           o.kappa.astype(np.uint8), o.n)
+            if name == "surrogate":
+                npx.surrogate_set_fallback(ww, bits)
+                npx.surrogate_fallback_counts(ww)        # counters from zero
+            fb = fn(ww)
+            r = ww.read()
+            dc = np.linalg.norm(r["cog"] - ref.c, axis=1)
+            qa, qb = r["quat"].astype(np.float64), ref.q
+            ang = 2 * np.arctan2(np.linalg.norm(qa - qb, axis=1), np.linalg.norm(qa + qb, axis=1))
+            ang = np.minimum(ang, 2 * np.pi - ang)
+            err[name] = errors(dc, ang)
+            if name == "surrogate":
+                # scene-steps of the 50 that the plain step took (fallbacks), and the error of the
+                # scenes the network carried through every window of the 50 steps apart from those
+                # whose windows (some or all) the plain step redid
+                err[name]["fallback_fraction"] = fb / (test_b.n_scenes * 50)
+                stayed = npx.surrogate_fallback_counts(ww) == 0
+                err[name]["stayed_on_network"] = errors(dc[stayed], ang[stayed])
+                err[name]["fell_back_at_least_once"] = errors(dc[~stayed], ang[~stayed])
+            ww.close()
+        return err
+
+    err = rollout_errors(0)
     out["error_50_steps_vs_fp64_oracle"] = err
     out["stated_error"] = {"what": "50-step CoG and orientation error against the FP64 oracle of the "
                                    "held-out scenes the network carried through every window",
                            **err["surrogate"]["stayed_on_network"]}
+    if "never" in timing:
+        # the looser rule: no window falls back, so every held-out scene is the network's
+        e2 = rollout_errors(-1)
+        out["never_fall_back"] = {
+            "what": "the same network with npx_surrogate_set_fallback(-1): every window keeps the "
+                    "network's prediction (sensors read at the predicted state)",
+            **timing["never"], "plain_value": out["plain_value"],
+            "error_50_steps_vs_fp64_oracle": e2,
+            "stated_error": {"what": "50-step CoG and orientation error against the FP64 oracle of all "
+                                     "held-out scenes (none falls back)", **e2["surrogate"]}}
     u = res["unexplained"]
     out["training"] = {"transitions": int(res["transitions"]), "adam_steps": int(res["adam_steps"]),
                        "seconds": round(res["seconds"], 2), "scenes": 4096,

@@ -124,8 +124,9 @@ int npx_surrogate_collect(npx_world *w, const npx_surrogate_norm *norm, int stri
                           float *X, float *T);
 /* Advance the world n_steps steps with the surrogate: at each window start the network predicts
  * every scene's state `stride` steps later from its features; scenes whose contact sensors at
- * the predicted state differ from those at the window's start redo the window with the plain step
- * (the fallback); steps outside windows, and a last window that does not fit in n_steps, are
+ * the predicted state differ from those at the window's start in more bits than the world's
+ * fallback threshold (npx_surrogate_set_fallback; 0 by default: any change) redo the window with
+ * the plain step (the fallback); steps outside windows, and a last window that does not fit in n_steps, are
  * plain for every scene.  *fallbacks (host, may be NULL) receives the number of scene-steps that
  * fell back.  The network must have been trained on windows of the same stride, take n_features
  * inputs, give n_targets outputs, and hold at least n_scenes rounded up to 128 rows.  Worlds
@@ -138,6 +139,13 @@ int npx_world_step_surrogate(npx_world *w, npx_mlp *net, const npx_surrogate_nor
  * This is how a caller tells the scenes that stayed on the network from those the plain step
  * took over, e.g. to state the network's own error apart from the plain step's. */
 int npx_surrogate_fallback_counts(npx_world *w, int *counts);
+/* The fallback rule of npx_world_step_surrogate: a window falls back when more than
+ * max_changed_bits of the scene's contact sensors differ between the window's start and the
+ * predicted state.  0 (the default) falls back on any change; -1 never falls back (every window
+ * keeps the network's prediction, and its sensors are those read at the predicted state).  A
+ * looser rule trades the 50-step state error for throughput; the paper has no counterpart (the
+ * surrogate is not part of it).  Values below -1 are refused with NPX_EINVAL. */
+int npx_surrogate_set_fallback(npx_world *w, int max_changed_bits);
 
 /* FP64 column statistics of FP32 rows: for X [rows x cols] (DEVICE, row-major), adds the sum and
  * the sum of squares of every column to sum[cols] and sumsq[cols] (DEVICE, FP64; the caller

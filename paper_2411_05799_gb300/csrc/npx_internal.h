@@ -78,12 +78,14 @@ struct WorldDev {
     const uint8_t *pchunk;                // [P] scene-local chunk of each stored point
     int max_chunks;                       // chunks of the scene with the most
     // posed-shape cache (worlds stepped by the surrogate, whose plain launches are short): per
-    // scene scache_mp + 2 scache_mt + 5 float4 -- the posed offsets of its points, the tile boxes
-    // of the lanes per scene that wrote them, the mass properties (4 float4) and
-    // (rmax, lanes per scene, 0, 0).  Mode 0: unused; 1: written at every shape update; 2: also
-    // read at launch entry instead of rebuilding the shape (every scene's entry is current)
+    // scene scache_mp + 2 scache_mt + 5 + 2 scache_ml float4 -- the posed offsets of its points,
+    // the tile boxes of the lanes per scene that wrote them, the mass properties (4 float4),
+    // (rmax, lanes per scene, 0, 0), and per link its orientation quaternion (w, x, y, z) and CoG
+    // offset from the robot CoG (w = 0), both in the body frame.  Mode 0: unused; 1: written at
+    // every shape update; 2: also read at launch entry instead of rebuilding the shape (every
+    // scene's entry is current)
     float4 *scache;
-    int scache_mp, scache_mt, scache_mode;
+    int scache_mp, scache_mt, scache_ml, scache_mode;
     // TMA map of the height maps [H][ny][nx] (FP32) in boxes of HM_BOX x HM_WIN x 1 cells for the
     // window loads, held on the host (hm_tmap_h) and passed to the step kernels as a parameter of
     // their own; hm_tma = 0 when the maps do not allow it (window loads by plain gathers)
@@ -125,6 +127,7 @@ struct SurCache {
     float4 *spt;      // [S * nsp]: points of contact-sensor links, offset from the robot CoG in
                       //   the body frame; w = the sensor bit
     int *nsp_s;       // [S] sensor points of each scene
+    int *sidx;        // [S * nsp]: their stored point index within the scene | sensor bit << 16
     int nsp, nl;      // capacity per scene; links per scene
 };
 
@@ -142,14 +145,18 @@ struct SurrogateIO {
 };
 
 cudaError_t launch_sensor_points(const WorldDev &W, int *count, int *max_count, cudaStream_t st);
+// C.sidx: each scene's sensor points in stored order (once: the point-to-sensor map is static)
+cudaError_t launch_sensor_index(const WorldDev &W, const SurCache &C, cudaStream_t st);
 cudaError_t launch_shape_cache(const WorldDev &W, const SurCache &C, cudaStream_t st);
 cudaError_t launch_features(const WorldDev &W, const SurCache &C, const SurrogateIO &io, cudaStream_t st);
 // the surrogate's next state from the network output Y [S x ldy] (standardised deltas), kept
-// where the contact sensors do not change; the other scenes go to list / count, and their
-// fallback counters fb [S] grow by one.  nx [16 * S], applied [S] and sens_new [S] are scratch.
+// where at most max_changed contact sensors change (with the sensors read at that state); the
+// other scenes go to list / count, and their fallback counters fb [S] grow by one.  nx [16 * S],
+// applied [S] and sens_new [S] are scratch.
 cudaError_t launch_surrogate_update(const WorldDev &W, const SurCache &C, const float *Y, int ldy,
                                     const float *t_mu, const float *t_sd, float *nx, uint8_t *applied,
-                                    uint32_t *sens_new, int *list, int *count, int *fb, cudaStream_t st);
+                                    uint32_t *sens_new, int *list, int *count, int *fb, int max_changed,
+                                    cudaStream_t st);
 cudaError_t launch_kappa_refresh(const WorldDev &W, const int *list, const int *count, cudaStream_t st);
 // *total += *count * mult, then *count = 0
 cudaError_t launch_accumulate(long long *total, int *count, int mult, cudaStream_t st);

@@ -418,18 +418,53 @@ __device__ __noinline__ void shape_update(const WorldDev &W, int s, int p0, int 
     __syncwarp();
 }
 
+// unit quaternion of a rotation matrix (row-major), sign chosen with w >= 0
+__device__ __forceinline__ void quat_from_mat(const float *Q, float *q) {
+    const float tr = Q[0] + Q[4] + Q[8];
+    float w, x, y, z;
+    if (tr > 0.f) {
+        const float s = 2.f * sqrtf(tr + 1.f);
+        w = 0.25f * s; x = (Q[7] - Q[5]) / s; y = (Q[2] - Q[6]) / s; z = (Q[3] - Q[1]) / s;
+    } else if (Q[0] > Q[4] && Q[0] > Q[8]) {
+        const float s = 2.f * sqrtf(1.f + Q[0] - Q[4] - Q[8]);
+        w = (Q[7] - Q[5]) / s; x = 0.25f * s; y = (Q[1] + Q[3]) / s; z = (Q[2] + Q[6]) / s;
+    } else if (Q[4] > Q[8]) {
+        const float s = 2.f * sqrtf(1.f + Q[4] - Q[0] - Q[8]);
+        w = (Q[2] - Q[6]) / s; x = (Q[1] + Q[3]) / s; y = 0.25f * s; z = (Q[5] + Q[7]) / s;
+    } else {
+        const float s = 2.f * sqrtf(1.f + Q[8] - Q[0] - Q[4]);
+        w = (Q[3] - Q[1]) / s; x = (Q[2] + Q[6]) / s; y = (Q[5] + Q[7]) / s; z = 0.25f * s;
+    }
+    const float sg = w < 0.f ? -1.f : 1.f;
+    q[0] = sg * w; q[1] = sg * x; q[2] = sg * y; q[3] = sg * z;
+}
+
 // ------------------------------------------------------------------------ posed-shape cache
 
-__host__ __device__ inline long long scache_stride(int mp, int mt) { return (long long)mp + 2 * mt + 5; }
+__host__ __device__ inline long long scache_stride(int mp, int mt, int ml) {
+    return (long long)mp + 2 * mt + 5 + 2 * ml;
+}
 
-// Writes the scene's posed shape (pts, tile boxes, mass properties) to its cache entry; stores only.
+// Writes the scene's posed shape (pts, tile boxes, mass properties, and each link's orientation and
+// CoG offset in the body frame from its frame in fr) to its cache entry; stores only.
 template <int LPS>
 __device__ __forceinline__ void scache_store(const WorldDev &W, int s, int np, const float4 *pts, const float4 *tb,
-                                             const Shape &sh, float rmax, int gl) {
-    float4 *e = W.scache + (size_t)s * scache_stride(W.scache_mp, W.scache_mt);
+                                             const Shape &sh, float rmax, const float *fr, int l0, int nl, int gl) {
+    float4 *e = W.scache + (size_t)s * scache_stride(W.scache_mp, W.scache_mt, W.scache_ml);
     const int nt = (np + LPS - 1) / LPS;
     for (int i = gl; i < np; i += LPS) e[i] = pts[i];
     for (int i = gl; i < 2 * nt; i += LPS) e[W.scache_mp + i] = tb[i];
+    float4 *lk = e + W.scache_mp + 2 * W.scache_mt + 5;
+    for (int l = gl; l < nl; l += LPS) {
+        const float *F = fr + 12 * l;
+        const float pc0 = W.link_cog[3 * (l0 + l)], pc1 = W.link_cog[3 * (l0 + l) + 1], pc2 = W.link_cog[3 * (l0 + l) + 2];
+        float ql[4];
+        quat_from_mat(F, ql);
+        lk[2 * l] = make_float4(ql[0], ql[1], ql[2], ql[3]);
+        lk[2 * l + 1] = make_float4(F[0] * pc0 + F[1] * pc1 + F[2] * pc2 + F[9] - sh.g[0],
+                                    F[3] * pc0 + F[4] * pc1 + F[5] * pc2 + F[10] - sh.g[1],
+                                    F[6] * pc0 + F[7] * pc1 + F[8] * pc2 + F[11] - sh.g[2], 0.f);
+    }
     if (gl == 0) {
         float4 *m = e + W.scache_mp + 2 * W.scache_mt;
         m[0] = make_float4(sh.M, sh.g[0], sh.g[1], sh.g[2]);
@@ -446,7 +481,7 @@ __device__ __forceinline__ void scache_store(const WorldDev &W, int s, int np, c
 template <int LPS>
 __device__ __forceinline__ float scache_load(const WorldDev &W, int s, int np, float4 *pts, float4 *tb, Shape &sh,
                                              int gl) {
-    const float4 *e = W.scache + (size_t)(s < 0 ? 0 : s) * scache_stride(W.scache_mp, W.scache_mt);
+    const float4 *e = W.scache + (size_t)(s < 0 ? 0 : s) * scache_stride(W.scache_mp, W.scache_mt, W.scache_ml);
     const int nt = (np + LPS - 1) / LPS;
     const float4 *m = e + W.scache_mp + 2 * W.scache_mt;
     float4 m0 = make_float4(1.f, 0.f, 0.f, 0.f), m1 = make_float4(1.f, 1.f, 1.f, 0.f);
@@ -864,7 +899,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
     } else {
         shape_update<LPS>(W, valid ? s : 0, p0, np, l0, nl, th, fr, pts, gl, sh);
         rmax = tile_bounds<LPS>(pts, np, tb, gl);
-        if (!ARENA && W.scache_mode != 0 && valid) scache_store<LPS>(W, s, np, pts, tb, sh, rmax, gl);
+        if (!ARENA && W.scache_mode != 0 && valid) scache_store<LPS>(W, s, np, pts, tb, sh, rmax, fr, l0, nl, gl);
     }
     // (arenas) body-frame box of the posed points
     float bbc[3] = {0.f, 0.f, 0.f}, bbh[3] = {0.f, 0.f, 0.f};
@@ -966,7 +1001,7 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
             __syncwarp();
             shape_update<LPS>(W, valid ? s : 0, p0, np, l0, nl, th, fr, pts, gl, sh);
             rmax = tile_bounds<LPS>(pts, np, tb, gl);
-            if (!ARENA && W.scache_mode != 0 && valid) scache_store<LPS>(W, s, np, pts, tb, sh, rmax, gl);
+            if (!ARENA && W.scache_mode != 0 && valid) scache_store<LPS>(W, s, np, pts, tb, sh, rmax, fr, l0, nl, gl);
             shr = sh;
             if (ARENA) {
                 robot_box<LPS>(tb, ntiles, gl, bbc, bbh);
@@ -1535,27 +1570,6 @@ __global__ void __launch_bounds__(32) points_kernel(const __grid_constant__ Worl
 // it is computed once per change into a per-scene cache (shape_cache_kernel) and the per-step
 // kernels do no forward kinematics.
 
-// unit quaternion of a rotation matrix (row-major), sign chosen with w >= 0
-__device__ __forceinline__ void quat_from_mat(const float *Q, float *q) {
-    const float tr = Q[0] + Q[4] + Q[8];
-    float w, x, y, z;
-    if (tr > 0.f) {
-        const float s = 2.f * sqrtf(tr + 1.f);
-        w = 0.25f * s; x = (Q[7] - Q[5]) / s; y = (Q[2] - Q[6]) / s; z = (Q[3] - Q[1]) / s;
-    } else if (Q[0] > Q[4] && Q[0] > Q[8]) {
-        const float s = 2.f * sqrtf(1.f + Q[0] - Q[4] - Q[8]);
-        w = (Q[7] - Q[5]) / s; x = 0.25f * s; y = (Q[1] + Q[3]) / s; z = (Q[2] + Q[6]) / s;
-    } else if (Q[4] > Q[8]) {
-        const float s = 2.f * sqrtf(1.f + Q[4] - Q[0] - Q[8]);
-        w = (Q[2] - Q[6]) / s; x = (Q[1] + Q[3]) / s; y = 0.25f * s; z = (Q[5] + Q[7]) / s;
-    } else {
-        const float s = 2.f * sqrtf(1.f + Q[8] - Q[0] - Q[4]);
-        w = (Q[3] - Q[1]) / s; x = (Q[2] + Q[6]) / s; y = (Q[5] + Q[7]) / s; z = 0.25f * s;
-    }
-    const float sg = w < 0.f ? -1.f : 1.f;
-    q[0] = sg * w; q[1] = sg * x; q[2] = sg * y; q[3] = sg * z;
-}
-
 // joint angles after the joint update of step n (clamped targets on update steps)
 __device__ __forceinline__ float angle_after(const WorldDev &W, int l0, int j0, int j, const float *th,
                                              long long n) {
@@ -1635,22 +1649,7 @@ __global__ void __launch_bounds__(128) shape_cache_kernel(const __grid_constant_
     for (int j = lane; j < nl - 1; j += 32) th[j] = W.theta[j0 + j];
     __syncwarp();
     Shape sh;
-    if (W.scache_mode == 2) {
-        // the posed offsets and mass properties from the posed-shape cache; only the link frames
-        // are built here
-        const float4 *e = W.scache + (size_t)s * scache_stride(W.scache_mp, W.scache_mt);
-        for (int i = lane; i < np; i += 32) cp_async16(pts + i, e + i);
-        const float4 *m = e + W.scache_mp + 2 * W.scache_mt;
-        const float4 m0 = m[0], m1 = m[1], m2 = m[2], m3 = m[3];
-        sh.M = m0.x; sh.g[0] = m0.y; sh.g[1] = m0.z; sh.g[2] = m0.w;
-        sh.Ib = Sym{m1.x, m1.y, m1.z, m1.w, m2.x, m2.y};
-        sh.Ii = Sym{m2.z, m2.w, m3.x, m3.y, m3.z, m3.w};
-        link_frames<32>(W, l0, nl, th, fr, lane);
-        cp_async_wait_all();
-        __syncwarp();
-    } else {
-        shape_update<32>(W, s, p0, np, l0, nl, th, fr, pts, lane, sh);
-    }
+    shape_update<32>(W, s, p0, np, l0, nl, th, fr, pts, lane, sh);
     for (int l = lane; l < C.nl; l += 32) {
         float4 lq = make_float4(1.f, 0.f, 0.f, 0.f), lp = make_float4(0.f, 0.f, 0.f, 0.f);
         if (l < nl) {
@@ -1686,6 +1685,60 @@ __global__ void __launch_bounds__(128) shape_cache_kernel(const __grid_constant_
             if (k < C.nsp) C.spt[(size_t)s * C.nsp + k] = make_float4(r.x, r.y, r.z, (float)sid);
         }
         base += __popc(m);
+    }
+}
+
+// The same cache copied from the posed-shape cache when every scene's entry is current (its link
+// entries were written with the shape): one warp per scene, no shape rebuilt.
+__global__ void __launch_bounds__(256) shape_cache_copy_kernel(const __grid_constant__ WorldDev W, SurCache C) {
+    const int lane = threadIdx.x & 31;
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (s >= W.S) return;   // warp-uniform
+    const int nl = W.link_off[s + 1] - W.link_off[s];
+    const float4 *e = W.scache + (size_t)s * scache_stride(W.scache_mp, W.scache_mt, W.scache_ml);
+    const float4 *m = e + W.scache_mp + 2 * W.scache_mt;
+    const float4 *lk = m + 5;
+    for (int l = lane; l < C.nl; l += 32) {
+        float4 lq = make_float4(1.f, 0.f, 0.f, 0.f), lp = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (l < nl) { lq = lk[2 * l]; lp = lk[2 * l + 1]; }
+        C.lk[((size_t)s * C.nl + l) * 2] = lq;
+        C.lk[((size_t)s * C.nl + l) * 2 + 1] = lp;
+    }
+    if (lane < 12) {
+        const float4 m1 = m[1], m2 = m[2], m3 = m[3];
+        const float v[12] = {m1.x, m1.y, m1.z, m1.w, m2.x, m2.y, m2.z, m2.w, m3.x, m3.y, m3.z, m3.w};
+        float x = v[0];
+#pragma unroll
+        for (int k = 1; k < 12; ++k) x = lane == k ? v[k] : x;
+        C.inert[lane * W.S + s] = x;
+    }
+    const int n = min(C.nsp_s[s], C.nsp);
+    for (int k = lane; k < n; k += 32) {
+        const int x = C.sidx[(size_t)s * C.nsp + k];
+        const float4 r = e[x & 0xffff];
+        C.spt[(size_t)s * C.nsp + k] = make_float4(r.x, r.y, r.z, (float)(x >> 16));
+    }
+}
+
+// Each scene's sensor points in stored order: their index within the scene and sensor bit (one
+// warp per scene; the order the shape caches write them in).
+__global__ void __launch_bounds__(128) sensor_index_kernel(const __grid_constant__ WorldDev W, SurCache C) {
+    const int lane = threadIdx.x & 31;
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (s >= W.S) return;   // warp-uniform
+    const int p0 = W.point_off[s], np = W.point_off[s + 1] - p0, l0 = W.link_off[s];
+    int base = 0;
+    for (int i0 = 0; i0 < np; i0 += 32) {
+        const int i = i0 + lane;
+        int sid = -1;
+        if (i < np) sid = W.links[l0 + W.plink[p0 + i]].sensor;
+        const bool is = sid >= 0 && sid < 32;
+        const unsigned msk = __ballot_sync(FULL_MASK, is);
+        if (is) {
+            const int k = base + __popc(msk & ((1u << lane) - 1u));
+            if (k < C.nsp) C.sidx[(size_t)s * C.nsp + k] = i | (sid << 16);
+        }
+        base += __popc(msk);
     }
 }
 
@@ -1845,10 +1898,12 @@ __global__ void __launch_bounds__(256) sensor_probe_kernel(const __grid_constant
 // One thread per scene: keep the candidate state if the contact sensors did not change, otherwise
 // leave the scene at its state and append it to the fallback list (the plain step takes it).
 __global__ void __launch_bounds__(256) surrogate_commit_kernel(const __grid_constant__ WorldDev W, const float *nx, const uint8_t *applied,
-                                                               const uint32_t *sens_new, int *list, int *count, int *fb) {
+                                                               const uint32_t *sens_new, int *list, int *count, int *fb,
+                                                               int max_changed) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const bool app = s < W.S && applied[s];
-    const bool fall = app && sens_new[s] != W.sensors[s];
+    const uint32_t sn = app ? sens_new[s] : 0u, so = app ? W.sensors[s] : 0u;
+    const bool fall = app && __popc(sn ^ so) > max_changed;
     // warp-aggregated append
     const unsigned m = __ballot_sync(FULL_MASK, fall);
     int base = 0;
@@ -1863,6 +1918,7 @@ __global__ void __launch_bounds__(256) surrogate_commit_kernel(const __grid_cons
     }
     if (!app || fall) return;
     const int S = W.S;
+    if (sn != so) W.sensors[s] = sn;   // a change the rule lets through
 #pragma unroll
     for (int k = 0; k < ST_N; ++k) W.st[(size_t)k * S + s] = nx[(size_t)k * S + s];
     W.omega[s] = nx[NX_WX * S + s];
@@ -1933,7 +1989,16 @@ cudaError_t launch_sensor_points(const WorldDev &W, int *count, int *max_count, 
     return cudaGetLastError();
 }
 
+cudaError_t launch_sensor_index(const WorldDev &W, const SurCache &C, cudaStream_t st) {
+    sensor_index_kernel<<<sur_blocks(W.S), SUR_WPB * 32, 0, st>>>(W, C);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_shape_cache(const WorldDev &W, const SurCache &C, cudaStream_t st) {
+    if (W.scache_mode == 2) {   // every scene's posed-shape entry is current: copy it
+        shape_cache_copy_kernel<<<(unsigned)((W.S + 7) / 8), 256, 0, st>>>(W, C);
+        return cudaGetLastError();
+    }
     const int sb = (int)slot_bytes(W.max_points, W.max_links, 32);
     cudaError_t e = cudaFuncSetAttribute((void *)shape_cache_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          SUR_WPB * sb);
@@ -1954,7 +2019,7 @@ cudaError_t launch_features(const WorldDev &W, const SurCache &C, const Surrogat
 
 cudaError_t launch_surrogate_update(const WorldDev &W, const SurCache &C, const float *Y, int ldy, const float *t_mu,
                                     const float *t_sd, float *nx, uint8_t *applied, uint32_t *sens_new, int *list,
-                                    int *count, int *fb, cudaStream_t st) {
+                                    int *count, int *fb, int max_changed, cudaStream_t st) {
     const unsigned bs = (unsigned)((W.S + 255) / 256);
     surrogate_apply_kernel<<<bs, 256, 0, st>>>(W, C, Y, ldy, t_mu, t_sd, nx, applied);
     cudaError_t e = cudaGetLastError();
@@ -1966,7 +2031,7 @@ cudaError_t launch_surrogate_update(const WorldDev &W, const SurCache &C, const 
         sensor_probe_kernel<true><<<bp, 256, 0, st>>>(W, C, nx, applied, sens_new);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    surrogate_commit_kernel<<<bs, 256, 0, st>>>(W, nx, applied, sens_new, list, count, fb);
+    surrogate_commit_kernel<<<bs, 256, 0, st>>>(W, nx, applied, sens_new, list, count, fb, max_changed);
     return cudaGetLastError();
 }
 

@@ -137,11 +137,12 @@ struct npx_world {
         uint32_t *sens_new = nullptr;         // [S]
         int *list = nullptr, *count = nullptr;
         int *fb = nullptr;                    // [S] windows of each scene that fell back
+        int max_changed = 0;                  // fallback when more sensor bits change (32: never)
         // posed-shape cache of every scene (read at the entry of the surrogate's plain launches);
         // current when scache_ok: written by a launch over all scenes since the last change of
         // joint angles from outside the surrogate's own launches
         float4 *scache = nullptr;
-        int scache_mp = 0, scache_mt = 0;
+        int scache_mp = 0, scache_mt = 0, scache_ml = 0;
         bool scache_ok = false;
         long long *total = nullptr;
         cudaEvent_t ev_w = nullptr, ev_n = nullptr;
@@ -509,7 +510,9 @@ int surrogate_buffers(npx_world *w) {
         return rc;
     w->sg.scache_mp = w->max_points;
     w->sg.scache_mt = (w->max_points + 3) / 4;   // tiles at the fewest lanes per scene (4)
-    if ((rc = dev_alloc(w, &w->sg.scache, (size_t)w->S * (w->sg.scache_mp + 2 * w->sg.scache_mt + 5))))
+    w->sg.scache_ml = w->max_links;
+    if ((rc = dev_alloc(w, &w->sg.scache,
+                        (size_t)w->S * (w->sg.scache_mp + 2 * w->sg.scache_mt + 5 + 2 * w->sg.scache_ml))))
         return rc;
     w->sg.scache_ok = false;
     CUDA_TRY(cudaMemsetAsync(w->sg.count, 0, sizeof(int), w->stream));
@@ -519,8 +522,11 @@ int surrogate_buffers(npx_world *w) {
     int nsp = 0;
     CUDA_TRY(cudaMemcpyAsync(&nsp, d_max, sizeof(int), cudaMemcpyDeviceToHost, w->stream));
     CUDA_TRY(cudaStreamSynchronize(w->stream));
-    if ((rc = dev_alloc(w, &C.spt, (size_t)w->S * std::max(nsp, 1)))) return rc;
+    if ((rc = dev_alloc(w, &C.spt, (size_t)w->S * std::max(nsp, 1))) ||
+        (rc = dev_alloc(w, &C.sidx, (size_t)w->S * std::max(nsp, 1))))
+        return rc;
     C.nsp = std::max(nsp, 1);
+    CUDA_TRY(npx::launch_sensor_index(w->W, C, w->stream));
     C.nl = w->max_links;
     CUDA_TRY(cudaEventCreateWithFlags(&w->sg.ev_w, cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreateWithFlags(&w->sg.ev_n, cudaEventDisableTiming));
@@ -1446,6 +1452,7 @@ static npx::WorldDev scache_world(const npx_world *w) {
     W.scache = w->sg.scache;
     W.scache_mp = w->sg.scache_mp;
     W.scache_mt = w->sg.scache_mt;
+    W.scache_ml = w->sg.scache_ml;
     W.scache_mode = w->sg.scache_ok ? 2 : 1;
     return W;
 }
@@ -1593,7 +1600,8 @@ int npx_world_step_surrogate(npx_world *w, npx_mlp *net, const npx_surrogate_nor
             CUDA_TRY(cudaStreamWaitEvent(w->stream, w->sg.ev_n, 0));
         }
         CUDA_TRY(npx::launch_surrogate_update(w->W, C, Y, ldy, nrm->t_mu, nrm->t_sd, w->sg.nx, w->sg.applied,
-                                              w->sg.sens_new, w->sg.list, w->sg.count, w->sg.fb, w->stream));
+                                              w->sg.sens_new, w->sg.list, w->sg.count, w->sg.fb, w->sg.max_changed,
+                                              w->stream));
         // the fallback: listed scenes kept their state; the plain step takes them through the
         // window from the contacts at that state
         CUDA_TRY(npx::launch_step(Wsub, fcfg, stride, w->stream));
@@ -1611,6 +1619,13 @@ int npx_world_step_surrogate(npx_world *w, npx_mlp *net, const npx_surrogate_nor
         CUDA_TRY(cudaMemcpyAsync(fallbacks, w->sg.total, sizeof(long long), cudaMemcpyDeviceToHost, w->stream));
         CUDA_TRY(cudaStreamSynchronize(w->stream));
     }
+    return NPX_OK;
+}
+
+int npx_surrogate_set_fallback(npx_world *w, int max_changed_bits) {
+    if (int rc = check_ready(w)) return rc;
+    if (max_changed_bits < -1) return fail(NPX_EINVAL, "max_changed_bits must be >= -1");
+    w->sg.max_changed = max_changed_bits < 0 ? 32 : std::min(max_changed_bits, 32);
     return NPX_OK;
 }
 

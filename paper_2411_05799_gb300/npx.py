@@ -164,6 +164,7 @@ _SIGS = {
     "npx_surrogate_collect": [P, P, I, I, P, P],
     "npx_world_step_surrogate": [P, P, P, I, I, P],
     "npx_surrogate_fallback_counts": [P, P],
+    "npx_surrogate_set_fallback": [P, I],
     "npx_column_moments": [P, C.c_longlong, I, P, P, P],
 }
 
@@ -544,6 +545,12 @@ def surrogate_fallback_counts(world: "World") -> np.ndarray:
     out = np.zeros(world.n_scenes, np.int32)
     _check(_lib.npx_surrogate_fallback_counts(world._h, _p(out)))
     return out
+
+
+def surrogate_set_fallback(world: "World", max_changed_bits: int) -> None:
+    """npx_surrogate_set_fallback: a surrogate window falls back when more than max_changed_bits
+    contact sensors change over it (0: any change, the default; -1: never)."""
+    _check(_lib.npx_surrogate_set_fallback(world._h, max_changed_bits))
 
 
 def column_moments(X_ptr, rows: int, cols: int, sum_ptr, sumsq_ptr, stream=None):

@@ -155,3 +155,41 @@ def test_posed_shape_cache_steps_bit_identically():
             assert np.array_equal(ra[k], rb[k]), (n, k)
         assert np.array_equal(wa.contacts(), wb.contacts()), n
     assert fa == fb and fa > 0
+
+
+def test_fallback_threshold():
+    """The fallback rule: 0 (the default) falls back on any change of the contact sensors over a
+    window, bit-identically to a world never told; a threshold of one bit falls back at most as
+    often; -1 never falls back, keeps every state finite and ends with the sensors a detection at
+    the final state gives (the world's own read-out after a rollout); -2 is refused."""
+    from paper_2411_05799_gb300 import surrogate
+    b = scenes.hexapod_batch(256, seed_key=46)
+    res = surrogate.train(scenes.hexapod_batch(512, seed_key=47), n_transitions=512 * 16 * 8,
+                          minibatch=1024, steps_per_chunk=16, passes=1, stat_periods=1, warm_steps=100,
+                          max_batch=256, stride=10)
+    sur = res["surrogate"]
+    stream = torch.cuda.current_stream().cuda_stream
+    worlds = {k: npx.World.from_batch(b, stream=stream) for k in ("default", 0, 1, -1)}
+    for k, w in worlds.items():
+        if k != "default":
+            npx.surrogate_set_fallback(w, k)
+        w.step(41)
+    fb = {k: sur.step(w, 160) for k, w in worlds.items()}
+    r = {k: w.read() for k, w in worlds.items()}
+    for f in ("cog", "quat", "vel", "angmom", "theta", "contacts", "status"):
+        assert np.array_equal(r["default"][f], r[0][f]), f
+    assert fb["default"] == fb[0] > 0
+    assert fb[1] <= fb[0]
+    assert fb[-1] == 0
+    for f in ("cog", "quat", "vel", "angmom"):
+        assert np.isfinite(r[-1][f]).all(), f
+    assert (r[-1]["status"] == 0).all()
+    # the sensors after the rollout are the contacts at the final state: stepping on from it with
+    # the plain step agrees with a world written that state
+    w2 = npx.World.from_batch(b, stream=stream)
+    w2.write_state(r[-1]["cog"], r[-1]["quat"], r[-1]["vel"], r[-1]["angmom"], r[-1]["theta"],
+                   worlds[-1].contacts(), r[-1]["step"])
+    assert np.array_equal(w2.read()["contacts"], r[-1]["contacts"])
+    with pytest.raises(npx.NpxError) as e:
+        npx.surrogate_set_fallback(worlds[0], -2)
+    assert e.value.code == -1                              # NPX_EINVAL
