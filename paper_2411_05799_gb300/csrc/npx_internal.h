@@ -77,6 +77,11 @@ struct WorldDev {
     const int *coff;                      // [S + 1] first chunk of each scene
     const uint8_t *pchunk;                // [P] scene-local chunk of each stored point
     int max_chunks;                       // chunks of the scene with the most
+    // robot-robot pair lists (one per group of arenas a warp steps): point pairs of two robots of
+    // an arena within reach plus a skin, alist_cap entries each, valid while the robots move less
+    // than the skin between rebuilds
+    uint32_t *alist;
+    int alist_cap;
     // posed-shape cache (worlds stepped by the surrogate, whose plain launches are short): per
     // scene scache_mp + 2 scache_mt + 5 + 2 scache_ml float4 -- the posed offsets of its points,
     // the tile boxes of the lanes per scene that wrote them, the mass properties (4 float4),

@@ -647,7 +647,18 @@ __device__ __noinline__ void gp_run(const WorldDev &W, int s, int j0, int nj, ui
 // (a margin covers the rounding of the boxes), so the forces are those of all pairs within reach.
 constexpr float ARENA_MARGIN = 1e-4f;   // m, added to every cull distance
 enum { XC_C = 0, XC_R = 3, XC_V = 12, XC_W = 15, XC_BC = 18, XC_BH = 21, XC_ACTIVE = 24, XC_C0 = 25,
-       XC_NC = 26, XC_P0 = 27, XC_NP = 28, XC_RF = 32, XC_N = 48 };
+       XC_NC = 26, XC_P0 = 27, XC_NP = 28, XC_RF = 32, XC_D = 38, XC_CREF = 39, XC_RREF = 42, XC_LH = 51,
+       XC_N = 64 };
+// Pair lists (Verlet lists): the point pairs of each robot pair of the warp's arenas closer than
+// reach + skin (skin = 2 rc) at the last rebuild.  A point of robot i has since moved at most
+// |c_i - c_i,ref| + ||R_i - R_i,ref||_2 r_max,i (the posed shape is rigid between joint updates);
+// for rotations R - R_ref has two equal singular values, so ||.||_2 = ||.||_F / sqrt(2) (up to the
+// rounding of the matrices, which a small allowance covers).  While these bounds of two robots sum
+// to less than the skin, no pair left out can be within reach.  The lists are rebuilt at a launch's first step, at joint updates and when a bound
+// runs out; entries are appended in a fixed order (ballots), so results are deterministic.  The
+// list header (in the first robot's exchange area): state (0 none, 1 valid, 2 overflowed: the
+// full pass serves until the next rebuild) and each pair's end offset.
+constexpr int AL_BITS = 11;   // bits of a point index in an entry (at most 2,048 points a robot)
 
 // Exchange area of a scene: XC_N floats of state and wrench totals | world chunk boxes
 // [max_chunks] (2 float4) | body chunk boxes [max_chunks] (2 float4) | near masks [max_chunks]
@@ -681,11 +692,207 @@ __device__ __forceinline__ bool boxes_meet(float4 ca, float4 ha, float4 cb, floa
            fabsf(ca.z - cb.z) <= ha.z + hb.z + cull;
 }
 
+// The pair force of point a of robot i and point b of robot j closer than reach (d = a - b in j's
+// body frame, dd = |d|^2 > 0; ra, and rb = Rj pb, their offsets from the robots' CoGs): F along
+// the line of centres with the contact law, F on i and -F on j, added to both wrenches.
+__device__ __forceinline__ void pair_force(float4 pa, float4 pb, const float ra[3], float d0, float d1, float d2,
+                                           float dd, const float Rj[9], const float vi[3], const float wi[3],
+                                           const float vj[3], const float wj[3], float reach, float kw2, float kc,
+                                           float (&fi)[6], float (&fj)[6]) {
+    const float dist = sqrtf(dd), inv = 1.f / dist;
+    const float hn[3] = {d0 * inv, d1 * inv, d2 * inv};
+    float n[3], rb[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        n[k] = Rj[3 * k] * hn[0] + Rj[3 * k + 1] * hn[1] + Rj[3 * k + 2] * hn[2];
+        rb[k] = Rj[3 * k] * pb.x + Rj[3 * k + 1] * pb.y + Rj[3 * k + 2] * pb.z;
+    }
+    const float va[3] = {vi[0] + (wi[1] * ra[2] - wi[2] * ra[1]),
+                         vi[1] + (wi[2] * ra[0] - wi[0] * ra[2]),
+                         vi[2] + (wi[0] * ra[1] - wi[1] * ra[0])};
+    const float vb[3] = {vj[0] + (wj[1] * rb[2] - wj[2] * rb[1]),
+                         vj[1] + (wj[2] * rb[0] - wj[0] * rb[2]),
+                         vj[2] + (wj[0] * rb[1] - wj[1] * rb[0])};
+    const float vn = (va[0] - vb[0]) * n[0] + (va[1] - vb[1]) * n[1] + (va[2] - vb[2]) * n[2];
+    const float mr = pa.w * pb.w / (pa.w + pb.w);
+    const float f = fmaxf(0.f, mr * (kw2 * (reach - dist) - kc * vn));
+    const float F[3] = {f * n[0], f * n[1], f * n[2]};
+    fi[0] += F[0]; fi[1] += F[1]; fi[2] += F[2];
+    fi[3] += ra[1] * F[2] - ra[2] * F[1];
+    fi[4] += ra[2] * F[0] - ra[0] * F[2];
+    fi[5] += ra[0] * F[1] - ra[1] * F[0];
+    fj[0] -= F[0]; fj[1] -= F[1]; fj[2] -= F[2];
+    fj[3] -= rb[1] * F[2] - rb[2] * F[1];
+    fj[4] -= rb[2] * F[0] - rb[0] * F[2];
+    fj[5] -= rb[0] * F[1] - rb[1] * F[0];
+}
+
+// The pair list of the warp's arenas from the exchange areas (see above): entries ia | ib << AL_BITS
+// per robot pair, in pair order; returns the entries written (more than cap: overflowed).
+__device__ __forceinline__ int arena_build(const WorldDev &W, unsigned char *xw, const unsigned char *pw, int sbytes,
+                                           int XB, int G, float cut, uint32_t *alist) {
+    const int lane = threadIdx.x & 31, A = W.arena, per_arena = A * (A - 1) / 2;
+    // (the margin covers the rounding of the distances, so a pair left out was farther than cut)
+    const float cull = cut + ARENA_MARGIN, cut2 = cull * cull;
+    float *X0 = reinterpret_cast<float *>(xw);
+    int total = 0;
+    for (int pr = 0; pr < (G / A) * per_arena; ++pr) {   // the same pairs, in the same order, on every lane
+        int i = 0, t = pr % per_arena;
+        while (t >= A - 1 - i) { t -= A - 1 - i; ++i; }
+        const int gi = (pr / per_arena) * A + i, gj = gi + 1 + t;
+        const float *Xi = reinterpret_cast<const float *>(xw + gi * XB);
+        const float *Xj = reinterpret_cast<const float *>(xw + gj * XB);
+        bool ov = Xi[XC_ACTIVE] != 0.f && Xj[XC_ACTIVE] != 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) ov = ov && fabsf(Xi[XC_BC + k] - Xj[XC_BC + k]) <= Xi[XC_BH + k] + Xj[XC_BH + k] + cull;
+        if (ov) {   // read from shared memory: the same on every lane
+            const float4 *LWi = reinterpret_cast<const float4 *>(xw + gi * XB + 4 * XC_N);
+            const float4 *LWj = reinterpret_cast<const float4 *>(xw + gj * XB + 4 * XC_N);
+            const float4 *LBj = LWj + 2 * W.max_chunks;
+            uint64_t *NMi = reinterpret_cast<uint64_t *>(xw + gi * XB + 4 * XC_N + 64 * W.max_chunks);
+            const int nli = __float_as_int(Xi[XC_NC]), nlj = __float_as_int(Xj[XC_NC]);
+            const int p0i = __float_as_int(Xi[XC_P0]), npi = __float_as_int(Xi[XC_NP]);
+            const int l0j = __float_as_int(Xj[XC_C0]);
+            const float4 bcj = make_float4(Xj[XC_BC], Xj[XC_BC + 1], Xj[XC_BC + 2], 0.f);
+            const float4 bhj = make_float4(Xj[XC_BH], Xj[XC_BH + 1], Xj[XC_BH + 2], 0.f);
+            for (int l = lane; l < nli; l += 32) {
+                uint64_t nm = 0;
+                const float4 ca = LWi[2 * l], ha = LWi[2 * l + 1];
+                if (boxes_meet(ca, ha, bcj, bhj, cull))
+                    for (int lb = 0; lb < nlj; ++lb)
+                        if (boxes_meet(ca, ha, LWj[2 * lb], LWj[2 * lb + 1], cull)) nm |= 1ull << lb;
+                NMi[l] = nm;
+            }
+            __syncwarp();
+            float ci[3], Ri[9], cj[3], Rj[9];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) { ci[k] = Xi[XC_C + k]; cj[k] = Xj[XC_C + k]; }
+#pragma unroll
+            for (int k = 0; k < 9; ++k) { Ri[k] = Xi[XC_R + k]; Rj[k] = Xj[XC_R + k]; }
+            const float4 *pti = reinterpret_cast<const float4 *>(pw + (ptrdiff_t)gi * sbytes);
+            const float4 *ptj = reinterpret_cast<const float4 *>(pw + (ptrdiff_t)gj * sbytes);
+            for (int ia0 = 0; ia0 < npi; ia0 += 32) {   // warp-uniform
+                const int ia = ia0 + lane;
+                uint64_t bm = ia < npi ? NMi[W.pchunk[p0i + ia]] : 0ull;
+                float ah0 = 0.f, ah1 = 0.f, ah2 = 0.f;
+                if (bm) {
+                    const float4 pa = pti[ia];
+                    float e[3];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+                        e[k] = (ci[k] + (Ri[3 * k] * pa.x + Ri[3 * k + 1] * pa.y + Ri[3 * k + 2] * pa.z)) - cj[k];
+                    ah0 = Rj[0] * e[0] + Rj[3] * e[1] + Rj[6] * e[2];
+                    ah1 = Rj[1] * e[0] + Rj[4] * e[1] + Rj[7] * e[2];
+                    ah2 = Rj[2] * e[0] + Rj[5] * e[1] + Rj[8] * e[2];
+                }
+                // each lane walks its candidates (a chunk's box test or one point test per round);
+                // the rounds are warp-wide, so the appends keep a fixed order
+                int ib = 0, b1 = 0;
+                while (__any_sync(FULL_MASK, bm != 0ull || ib < b1)) {
+                    bool cand = false;
+                    uint32_t code = 0u;
+                    if (ib < b1) {
+                        const int pbi = __ldg(W.lpt + ib);
+                        const float4 pb = ptj[pbi];
+                        const float d0 = ah0 - pb.x, d1 = ah1 - pb.y, d2 = ah2 - pb.z;
+                        cand = d0 * d0 + d1 * d1 + d2 * d2 < cut2;
+                        code = (uint32_t)ia | ((uint32_t)pbi << AL_BITS);
+                        ++ib;
+                    } else if (bm) {
+                        const int lb = __ffsll((long long)bm) - 1;
+                        bm &= bm - 1;
+                        const float4 cbh = LBj[2 * lb], hbh = LBj[2 * lb + 1];
+                        if (fabsf(ah0 - cbh.x) <= hbh.x + cull && fabsf(ah1 - cbh.y) <= hbh.y + cull &&
+                            fabsf(ah2 - cbh.z) <= hbh.z + cull) {
+                            ib = W.cpo[l0j + lb];
+                            b1 = W.cpo[l0j + lb + 1];
+                        }
+                    }
+                    const unsigned bal = __ballot_sync(FULL_MASK, cand);
+                    if (cand) {
+                        const int pos = total + __popc(bal & ((1u << lane) - 1u));
+                        if (pos < W.alist_cap) alist[pos] = code;
+                    }
+                    total += __popc(bal);
+                }
+            }
+        }
+        if (lane == 0) X0[XC_LH + 1 + pr] = __int_as_float(total);
+        __syncwarp();
+    }
+    return total;
+}
+
+// Pair forces from the list: for each robot pair of the warp, its entries spread over the lanes,
+// the pair's wrenches summed by the warp and added to the two robots' totals, pair after pair.
+__device__ __forceinline__ void arena_list_forces(const WorldDev &W, unsigned char *xw, const unsigned char *pw,
+                                                  int sbytes, int XB, int G, const uint32_t *alist) {
+    const int lane = threadIdx.x & 31, A = W.arena, per_arena = A * (A - 1) / 2;
+    const float reach = 2.f * W.rc, reach2 = reach * reach, kw2 = W.kw2, kc = W.kc;
+    const float *X0 = reinterpret_cast<const float *>(xw);
+    int start = 0;
+    for (int pr = 0; pr < (G / A) * per_arena; ++pr) {
+        const int end = __float_as_int(X0[XC_LH + 1 + pr]);
+        if (end > start) {   // read from shared memory: the same on every lane
+            int i = 0, t = pr % per_arena;
+            while (t >= A - 1 - i) { t -= A - 1 - i; ++i; }
+            const int gi = (pr / per_arena) * A + i, gj = gi + 1 + t;
+            float *Xi = reinterpret_cast<float *>(xw + gi * XB);
+            float *Xj = reinterpret_cast<float *>(xw + gj * XB);
+            if (Xi[XC_ACTIVE] != 0.f && Xj[XC_ACTIVE] != 0.f) {
+                float ci[3], Ri[9], vi[3], wi[3], cj[3], Rj[9], vj[3], wj[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    ci[k] = Xi[XC_C + k]; vi[k] = Xi[XC_V + k]; wi[k] = Xi[XC_W + k];
+                    cj[k] = Xj[XC_C + k]; vj[k] = Xj[XC_V + k]; wj[k] = Xj[XC_W + k];
+                }
+#pragma unroll
+                for (int k = 0; k < 9; ++k) { Ri[k] = Xi[XC_R + k]; Rj[k] = Xj[XC_R + k]; }
+                const float4 *pti = reinterpret_cast<const float4 *>(pw + (ptrdiff_t)gi * sbytes);
+                const float4 *ptj = reinterpret_cast<const float4 *>(pw + (ptrdiff_t)gj * sbytes);
+                float fi[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, fj[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                for (int en = start + lane; en < end; en += 32) {
+                    const uint32_t code = alist[en];
+                    const float4 pa = pti[code & ((1u << AL_BITS) - 1u)], pb = ptj[code >> AL_BITS];
+                    float ra[3], e[3];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        ra[k] = Ri[3 * k] * pa.x + Ri[3 * k + 1] * pa.y + Ri[3 * k + 2] * pa.z;
+                        e[k] = (ci[k] + ra[k]) - cj[k];
+                    }
+                    const float ah0 = Rj[0] * e[0] + Rj[3] * e[1] + Rj[6] * e[2];
+                    const float ah1 = Rj[1] * e[0] + Rj[4] * e[1] + Rj[7] * e[2];
+                    const float ah2 = Rj[2] * e[0] + Rj[5] * e[1] + Rj[8] * e[2];
+                    const float d0 = ah0 - pb.x, d1 = ah1 - pb.y, d2 = ah2 - pb.z;
+                    const float dd = d0 * d0 + d1 * d1 + d2 * d2;
+                    if (dd < reach2 && dd > 0.f)
+                        pair_force(pa, pb, ra, d0, d1, d2, dd, Rj, vi, wi, vj, wj, reach, kw2, kc, fi, fj);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) {
+                        fi[k] += __shfl_xor_sync(FULL_MASK, fi[k], o);
+                        fj[k] += __shfl_xor_sync(FULL_MASK, fj[k], o);
+                    }
+                }
+                if (lane == 0) {
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) { Xi[XC_RF + k] += fi[k]; Xj[XC_RF + k] += fj[k]; }
+                }
+                __syncwarp();
+            }
+        }
+        start = end;
+    }
+}
+
 template <int LPS>
 __device__ __forceinline__ void arena_wrench(const WorldDev &W, unsigned char *xch, int sbytes, const float4 *pts,
                                              int c0, int nc, int p0, int np, const float c[3], const float R[9],
                                              const float v[3], const float om[3], const float bbc[3],
-                                             const float bbh[3], bool active, int gl, float (&rf)[6]) {
+                                             const float bbh[3], bool active, float rmax, bool fresh,
+                                             uint32_t *alist, int gl, float (&rf)[6]) {
     constexpr int G = 32 / LPS;
     const int lane = threadIdx.x & 31, g = lane / LPS, A = W.arena, XB = xch_bytes(W.max_chunks);
     float *X = reinterpret_cast<float *>(xch);
@@ -722,12 +929,54 @@ __device__ __forceinline__ void arena_wrench(const WorldDev &W, unsigned char *x
         X[XC_NP] = __int_as_float(np);
     }
     if (gl < 6) X[XC_RF + gl] = 0.f;
+    if (gl == 0) {   // how far the robot's points may have moved since the list was built
+        float dc = 0.f, dr = 0.f;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) dc += (c[i] - X[XC_CREF + i]) * (c[i] - X[XC_CREF + i]);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) dr += (R[i] - X[XC_RREF + i]) * (R[i] - X[XC_RREF + i]);
+        X[XC_D] = 1.0001f * (sqrtf(dc) + (0.70711f * sqrtf(dr) + 1e-5f) * rmax);
+    }
     __syncwarp();
     const float reach = 2.f * W.rc, reach2 = reach * reach, cull = reach + ARENA_MARGIN;
     const float kw2 = W.kw2, kc = W.kc;
     unsigned char *xw = xch - g * XB;                                     // the warp's first area
     const unsigned char *pw = reinterpret_cast<const unsigned char *>(pts) - (ptrdiff_t)g * sbytes;  // first slot
     const int per_arena = A * (A - 1) / 2;
+    if (alist) {
+        // the pair list: rebuilt at a launch's first step, after joint updates and when two robots
+        // of a pair may together have moved a skin (2 rc) since it was built
+        float *X0 = reinterpret_cast<float *>(xw);
+        const float skin = 2.f * W.rc;
+        bool need = fresh || __float_as_int(X0[XC_LH]) == 0;
+        for (int pr = 0; pr < (G / A) * per_arena; ++pr) {
+            int i = 0, t = pr % per_arena;
+            while (t >= A - 1 - i) { t -= A - 1 - i; ++i; }
+            const int gi = (pr / per_arena) * A + i, gj = gi + 1 + t;
+            const float *Xi = reinterpret_cast<const float *>(xw + gi * XB);
+            const float *Xj = reinterpret_cast<const float *>(xw + gj * XB);
+            need = need || Xi[XC_D] + Xj[XC_D] > skin;
+        }
+        if (need) {   // the same on every lane (fresh is; the rest is read from shared memory)
+            if (gl == 0) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) X[XC_CREF + i] = c[i];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) X[XC_RREF + i] = R[i];
+            }
+            __syncwarp();
+            const int n = arena_build(W, xw, pw, sbytes, XB, G, reach + skin, alist);
+            if (lane == 0) X0[XC_LH] = __int_as_float(n <= W.alist_cap ? 1 : 2);
+            __syncwarp();
+        }
+        if (__float_as_int(X0[XC_LH]) == 1) {
+            arena_list_forces(W, xw, pw, sbytes, XB, G, alist);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) rf[k] = X[XC_RF + k];
+            __syncwarp();   // the exchange area is written again next step
+            return;
+        }
+    }
     for (int pr = 0; pr < (G / A) * per_arena; ++pr) {   // the same pairs, in the same order, on every lane
         int i = 0, t = pr % per_arena;
         while (t >= A - 1 - i) { t -= A - 1 - i; ++i; }
@@ -796,35 +1045,8 @@ __device__ __forceinline__ void arena_wrench(const WorldDev &W, unsigned char *x
                     const float4 pb = ptj[__ldg(W.lpt + ib)];
                     const float d0 = ah0 - pb.x, d1 = ah1 - pb.y, d2 = ah2 - pb.z;
                     const float dd = d0 * d0 + d1 * d1 + d2 * d2;
-                    if (dd < reach2 && dd > 0.f) {
-                        const float dist = sqrtf(dd), inv = 1.f / dist;
-                        const float hn[3] = {d0 * inv, d1 * inv, d2 * inv};
-                        float n[3], rb[3];
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            n[k] = Rj[3 * k] * hn[0] + Rj[3 * k + 1] * hn[1] + Rj[3 * k + 2] * hn[2];
-                            rb[k] = Rj[3 * k] * pb.x + Rj[3 * k + 1] * pb.y + Rj[3 * k + 2] * pb.z;
-                        }
-                        const float va[3] = {vi[0] + (wi[1] * ra[2] - wi[2] * ra[1]),
-                                             vi[1] + (wi[2] * ra[0] - wi[0] * ra[2]),
-                                             vi[2] + (wi[0] * ra[1] - wi[1] * ra[0])};
-                        const float vb[3] = {vj[0] + (wj[1] * rb[2] - wj[2] * rb[1]),
-                                             vj[1] + (wj[2] * rb[0] - wj[0] * rb[2]),
-                                             vj[2] + (wj[0] * rb[1] - wj[1] * rb[0])};
-                        const float vn = (va[0] - vb[0]) * n[0] + (va[1] - vb[1]) * n[1] + (va[2] - vb[2]) * n[2];
-                        const float mr = pa.w * pb.w / (pa.w + pb.w);
-                        const float f = fmaxf(0.f, mr * (kw2 * (reach - dist) - kc * vn));
-                        const float F[3] = {f * n[0], f * n[1], f * n[2]};
-                        // F on i at its point, -F on j at its point
-                        fi[0] += F[0]; fi[1] += F[1]; fi[2] += F[2];
-                        fi[3] += ra[1] * F[2] - ra[2] * F[1];
-                        fi[4] += ra[2] * F[0] - ra[0] * F[2];
-                        fi[5] += ra[0] * F[1] - ra[1] * F[0];
-                        fj[0] -= F[0]; fj[1] -= F[1]; fj[2] -= F[2];
-                        fj[3] -= rb[1] * F[2] - rb[2] * F[1];
-                        fj[4] -= rb[2] * F[0] - rb[0] * F[2];
-                        fj[5] -= rb[0] * F[1] - rb[1] * F[0];
-                    }
+                    if (dd < reach2 && dd > 0.f)
+                        pair_force(pa, pb, ra, d0, d1, d2, dd, Rj, vi, wi, vj, wj, reach, kw2, kc, fi, fj);
                 }
             }
         }
@@ -855,7 +1077,7 @@ __device__ __forceinline__ void arena_wrench(const WorldDev &W, unsigned char *x
 template <int LPS, bool FLAT, bool OPT, bool ARENA>
 __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *fr, float *th,
                           float *th_old, float4 *tb, int n_steps, long long step0, unsigned char *xch,
-                          int sbytes, const CUtensorMap *tmap) {
+                          int sbytes, const CUtensorMap *tmap, int item) {
     const bool valid = s >= 0;
     int p0 = 0, np = 0, l0 = 0, nl = 1;
     if (valid) {
@@ -1016,7 +1238,9 @@ __device__ void run_scene(const WorldDev &W, int s, int gl, float4 *pts, float *
 
         // -- (arenas) contact forces and their torques about the CoG from the other robots
         float rf[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (ARENA) arena_wrench<LPS>(W, xch, sbytes, pts, c0, nc, p0, np, c, R, v, om, bbc, bbh, valid && status == 0u, gl, rf);
+        if (ARENA)
+            arena_wrench<LPS>(W, xch, sbytes, pts, c0, nc, p0, np, c, R, v, om, bbc, bbh, valid && status == 0u,
+                              rmax, t == 0 || tick, W.alist ? W.alist + (size_t)item * W.alist_cap : nullptr, gl, rf);
 
         // -- pass 1: collision against the ground and penalty normal forces over the candidate
         //    tiles.  For the points in contact in both steps (the friction set C, Sec. III-C) it
@@ -1422,7 +1646,7 @@ __device__ __forceinline__ void step_body(const WorldDev &W, int n_steps, int sb
         if (item >= n_items) break;
         const int idx = item * G + g;
         const int s = idx < n_sched ? W.order[idx] : -1;
-        run_scene<LPS, FLAT, OPT, ARENA>(W, s, gl, pts, fr, th, th_old, tb, n_steps, step0, xch, sbytes, tmap);
+        run_scene<LPS, FLAT, OPT, ARENA>(W, s, gl, pts, fr, th, th_old, tb, n_steps, step0, xch, sbytes, tmap, item);
     }
 }
 

@@ -152,6 +152,7 @@ struct npx_world {
         unsigned long long cache_gen = ~0ull;
     } sg;
     unsigned long long state_gen = 0;   // counts the caller's state writes
+    size_t alist_n = 0;                 // entries allocated for the arenas' pair lists
     CUtensorMap hm_tmap{};              // TMA map of the height maps (W.hm_tmap_h points here)
     // angular velocity and contact sensors are derived from the state: after a state write they
     // are recomputed when first needed (a step recomputes them anyway)
@@ -1195,8 +1196,18 @@ int npx_world_set_arenas(npx_world *w, int size, float radius) {
                     64 * (32 / size), size);
     CUDA_TRY(cudaSetDevice(w->device));
     CUDA_TRY(cudaStreamSynchronize(w->stream));   // launches in flight read the schedule
-    if (size > 1)
+    if (size > 1) {
         if (int rc = arena_tables(w)) return rc;
+        // pair lists: one per group of arenas a warp steps (at most S / size groups)
+        const size_t cap = 4096, need = (size_t)(S / size + 1) * cap;
+        if (w->alist_n < need) {
+            uint32_t *al = nullptr;
+            if (int rc = dev_alloc(w, &al, need)) return rc;
+            w->W.alist = al;
+            w->alist_n = need;
+        }
+        w->W.alist_cap = (int)cap;
+    }
     auto pts = [&](int s) { return w->point_off[s + 1] - w->point_off[s]; };
     std::vector<int> order(S);
     if (size > 1) {

@@ -241,3 +241,29 @@ def test_arena_arguments():
     w.set_arenas(1)                                    # off again: every scene alone
     w.step(10)
     assert (w.read()["status"] == 0).all()
+
+
+def test_pair_list_overflow_takes_the_full_pass():
+    """Robots of an arena stacked almost on top of each other put more point pairs within reach
+    than a warp's pair list holds (4,096 entries): the step then takes the full pair pass.  From
+    rest the pair forces have no damping term, so they are continuous where pairs leave reach
+    (no pair decides its force by rounding), and the first step agrees with the oracle on every
+    scene."""
+    size = 4
+    b = scenes.arena_batch(2, size, seed_key=17)
+    org = b.origin.copy()
+    for a in range(2):
+        for k in range(size):
+            org[a * size + k] = org[a * size] + np.float32([0.005 * k, 0.003 * k, 0.0])
+    b = b.with_(origin=org, vel=np.zeros_like(b.vel), omega=np.zeros_like(b.omega))
+    o = Oracle(b, arena=size, arena_radius=RADIUS, threads=THREADS)
+    n_in, _ = pairs_in_reach(o, size)
+    assert n_in.min() > 4096, n_in
+    w = World.from_batch(b, configure=dict(lanes_per_scene=8))
+    w.set_arenas(size, RADIUS)
+    err, near, o2, r = per_step_compare(w, o, THREADS)
+    assert not near.any()
+    for k in ("cog", "quat", "vel", "angmom", "theta"):
+        assert err[k].max() <= STEP_RTOL, f"{k} rel err {err[k].max():.3g}"
+    assert err["contacts"].max() == 0
+    assert np.abs(r["vel"]).max() > 0.1                 # the stack pushes apart
