@@ -785,20 +785,16 @@ __device__ __forceinline__ int arena_build(const WorldDev &W, unsigned char *xw,
                     ah1 = Rj[1] * e[0] + Rj[4] * e[1] + Rj[7] * e[2];
                     ah2 = Rj[2] * e[0] + Rj[5] * e[1] + Rj[8] * e[2];
                 }
-                // each lane walks its candidates (a chunk's box test or one point test per round);
-                // the rounds are warp-wide, so the appends keep a fixed order
+                // each lane walks its candidate chunks: a round takes the lane's next chunk when
+                // its current one is done (whose body-frame box must come within reach) and tests
+                // up to 16 of the chunk's points at once; the rounds are warp-wide and the lanes'
+                // entries go out in lane order (a warp prefix sum), so the appends keep a fixed
+                // order
                 int ib = 0, b1 = 0;
                 while (__any_sync(FULL_MASK, bm != 0ull || ib < b1)) {
-                    bool cand = false;
-                    uint32_t code = 0u;
-                    if (ib < b1) {
-                        const int pbi = __ldg(W.lpt + ib);
-                        const float4 pb = ptj[pbi];
-                        const float d0 = ah0 - pb.x, d1 = ah1 - pb.y, d2 = ah2 - pb.z;
-                        cand = d0 * d0 + d1 * d1 + d2 * d2 < cut2;
-                        code = (uint32_t)ia | ((uint32_t)pbi << AL_BITS);
-                        ++ib;
-                    } else if (bm) {
+                    uint32_t hit = 0u;
+                    int ib0 = 0;   // the round's first tested point
+                    if (ib >= b1 && bm) {
                         const int lb = __ffsll((long long)bm) - 1;
                         bm &= bm - 1;
                         const float4 cbh = LBj[2 * lb], hbh = LBj[2 * lb + 1];
@@ -808,12 +804,33 @@ __device__ __forceinline__ int arena_build(const WorldDev &W, unsigned char *xw,
                             b1 = W.cpo[l0j + lb + 1];
                         }
                     }
-                    const unsigned bal = __ballot_sync(FULL_MASK, cand);
-                    if (cand) {
-                        const int pos = total + __popc(bal & ((1u << lane) - 1u));
-                        if (pos < W.alist_cap) alist[pos] = code;
+                    if (ib < b1) {
+                        ib0 = ib;
+                        const int nb = min(16, b1 - ib);
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) {
+                            if (k < nb) {
+                                const float4 pb = ptj[__ldg(W.lpt + ib + k)];
+                                const float d0 = ah0 - pb.x, d1 = ah1 - pb.y, d2 = ah2 - pb.z;
+                                if (d0 * d0 + d1 * d1 + d2 * d2 < cut2) hit |= 1u << k;
+                            }
+                        }
+                        ib += nb;
                     }
-                    total += __popc(bal);
+                    const int cnt = __popc(hit);
+                    int pre = cnt;   // inclusive prefix sum over the lanes
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(FULL_MASK, pre, o);
+                        if (lane >= o) pre += y;
+                    }
+                    int pos = total + pre - cnt;
+                    for (uint32_t h = hit; h; h &= h - 1, ++pos) {
+                        const int k = __ffs(h) - 1;
+                        if (pos < W.alist_cap)
+                            alist[pos] = (uint32_t)ia | ((uint32_t)__ldg(W.lpt + ib0 + k) << AL_BITS);
+                    }
+                    total += __shfl_sync(FULL_MASK, pre, 31);
                 }
             }
         }
