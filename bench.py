@@ -673,6 +673,8 @@ def run_profile(args):
     step:      a few step-kernel launches of `--chunk` steps on the benchmark workload in a fixed
                launch shape;
     step_hm:   the same on the rough-terrain rollout (16,384 hexapods, 128 x 128 height maps);
+    arena:     the same on 4,096 hexapods colliding in arenas of four (after 600 untimed steps of
+               walking into each other);
     gemm:      the surrogate network's forward GEMMs over 65,536 rows (random weights), 3 passes;
     surrogate: a briefly trained surrogate stepping 65,536 hexapods for 4 steps."""
     import torch
@@ -681,10 +683,15 @@ def run_profile(args):
     from paper_2411_05799_gb300.npx import World
     build()
     torch.cuda.set_device(0)
-    if args.profile in ("step", "step_hm"):
-        batch = scenes.hexapod_batch(N_SCENES) if args.profile == "step" else scenes.cpg_batch(16384)
+    if args.profile in ("step", "step_hm", "arena"):
+        batch = {"step": lambda: scenes.hexapod_batch(N_SCENES), "step_hm": lambda: scenes.cpg_batch(16384),
+                 "arena": lambda: scenes.arena_batch(N_SCENES // 4, 4)}[args.profile]()
         world = World.from_batch(batch, configure=dict(lanes_per_scene=args.lps, warps_per_block=args.wpb,
                                                        chunk_steps=args.chunk))
+        if args.profile == "arena":
+            world.set_arenas(4, ARENA_RADIUS)
+            world.configure(lanes_per_scene=args.lps, warps_per_block=args.wpb, chunk_steps=args.chunk)
+            world.step(600)
         for _ in range(3):
             world.step(args.chunk)
         world.sync()
@@ -723,7 +730,7 @@ def run_profile(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile", choices=["step", "step_hm", "gemm", "surrogate"],
+    ap.add_argument("--profile", choices=["step", "step_hm", "arena", "gemm", "surrogate"],
                     help="ncu driver (no bench line): step kernel (4,096 hexapods on flat ground, or "
                          "16,384 on rough height maps), network GEMMs or surrogate step")
     ap.add_argument("--lps", type=int, default=16)
