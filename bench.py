@@ -676,7 +676,9 @@ def run_profile(args):
     arena:     the same on 4,096 hexapods colliding in arenas of four (after 600 untimed steps of
                walking into each other);
     gemm:      the surrogate network's forward GEMMs over 65,536 rows (random weights), 3 passes;
-    surrogate: a briefly trained surrogate stepping 65,536 hexapods for 4 steps."""
+    surrogate: a briefly trained surrogate stepping 65,536 hexapods from the step after a joint
+               update for one joint-update period (4 steps at stride 1) with the fallback rule
+               --fallback-bits, inside the NVTX range "period"."""
     import torch
     from paper_2411_05799_gb300 import scenes
     from paper_2411_05799_gb300.build import build
@@ -721,10 +723,15 @@ def run_profile(args):
     n = 4 if stride == 1 else 80      # stride 1: four steps; else one joint-update period
     with torch.cuda.stream(stream):
         w = World.from_batch(scenes.hexapod_batch(S, seed_key=5), stream=stream.cuda_stream)
+        npx.surrogate_set_fallback(w, args.fallback_bits)
         w.step(321)
+        stream.synchronize()
+        torch.cuda.nvtx.range_push("period")
         fb = sur.step(w, n)
         stream.synchronize()
-    print(json.dumps({"profile": "surrogate", "scenes": S, "steps": n, "stride": stride, "fallbacks": fb}))
+        torch.cuda.nvtx.range_pop()
+    print(json.dumps({"profile": "surrogate", "scenes": S, "steps": n, "stride": stride,
+                      "fallback_bits": args.fallback_bits, "fallbacks": fb}))
     return 0
 
 
@@ -734,6 +741,8 @@ def main():
                     help="ncu driver (no bench line): step kernel (4,096 hexapods on flat ground, or "
                          "16,384 on rough height maps), network GEMMs or surrogate step")
     ap.add_argument("--lps", type=int, default=16)
+    ap.add_argument("--fallback-bits", type=int, default=0,
+                    help="surrogate profile: fallback when more contact sensors change (-1: never)")
     ap.add_argument("--wpb", type=int, default=16)
     ap.add_argument("--chunk", type=int, default=100)
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
