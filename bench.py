@@ -686,6 +686,8 @@ def run_profile(args):
     step_hm:   the same on the rough-terrain rollout (16,384 hexapods, 128 x 128 height maps);
     arena:     the same on 4,096 hexapods colliding in arenas of four (after 600 untimed steps of
                walking into each other);
+    uneven:    the uneven 65,536-scene mix in its autotuned size classes, three chunks, the last
+               inside the NVTX range "chunk";
     gemm:      the surrogate network's forward GEMMs over 65,536 rows (random weights), 3 passes;
     surrogate: a briefly trained surrogate stepping 65,536 hexapods from the step after a joint
                update for one joint-update period (4 steps at stride 1) with the fallback rule
@@ -696,6 +698,20 @@ def run_profile(args):
     from paper_2411_05799_gb300.npx import World
     build()
     torch.cuda.set_device(0)
+    if args.profile == "uneven":
+        world = World.from_batch(scenes.uneven_batch(65536))
+        world.autotune(100)
+        world.configure(chunk_steps=args.chunk)
+        world.step(2 * args.chunk)
+        world.sync()
+        torch.cuda.nvtx.range_push("chunk")
+        world.step(args.chunk)
+        world.sync()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"profile": args.profile, **world.info(),
+                          "status_nonzero": int((world.read()["status"] != 0).sum())}))
+        world.close()
+        return 0
     if args.profile in ("step", "step_hm", "arena"):
         batch = {"step": lambda: scenes.hexapod_batch(N_SCENES), "step_hm": lambda: scenes.cpg_batch(16384),
                  "arena": lambda: scenes.arena_batch(N_SCENES // 4, 4)}[args.profile]()
@@ -748,7 +764,7 @@ def run_profile(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile", choices=["step", "step_hm", "arena", "gemm", "surrogate"],
+    ap.add_argument("--profile", choices=["step", "step_hm", "arena", "uneven", "gemm", "surrogate"],
                     help="ncu driver (no bench line): step kernel (4,096 hexapods on flat ground, or "
                          "16,384 on rough height maps), network GEMMs or surrogate step")
     ap.add_argument("--lps", type=int, default=16)
