@@ -105,7 +105,8 @@ typedef struct {
     float *angmom;     /* [S*3] world angular momentum about the CoG */
     float *theta;      /* [J]   joint angles, scene-major (joint j of scene s at joint_off(s)+j) */
     uint32_t *contacts;/* [S]   contact-sensor bits of the last step */
-    uint32_t *status;  /* [S]   0 = ok; bit 0 non-finite state, bit 1 out of range (scene frozen) */
+    uint32_t *status;  /* [S]   0 = ok; bit 0 non-finite state, bit 1 out of range, bit 2 a
+                                  height-map window copy that gave up its wait (scene frozen) */
     int64_t *step;     /* [1]   global step counter n */
 } npx_sensors;
 
@@ -236,6 +237,13 @@ int npx_world_configure(npx_world *w, int lanes_per_scene, int warps_per_block, 
 int npx_world_autotune(npx_world *w, int n_steps, npx_world_info *out);
 /* Capture world_step's chunk sequence in CUDA graphs (1, default) or launch directly (0). */
 int npx_world_use_graphs(npx_world *w, int on);
+/* The step kernel's bounded wait for height-map window copies on its own, for tests of its failure
+ * path: one warp whose 8-lane groups wait on mbarriers, two armed for a copy that is never issued
+ * and two completed at once.  The wait gives up after its one-second limit; a step kernel whose
+ * window copy gave up freezes the scene with status bit 2.  Synchronous: *gave_up (host) = lanes
+ * whose wait gave up (16 expected), *completed = lanes that saw their barrier complete (16),
+ * *elapsed_us = how long the wait took; the context stays usable. */
+int npx_window_wait_selftest(int *gave_up, int *completed, int *elapsed_us, void *stream);
 
 /* --- stepping without any allocation ------------------------------------------------------ */
 /* The paper has no counterpart of this call; it serves callers that must not allocate device

@@ -30,6 +30,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/npx.h"
 #include "npx_internal.h"
 
 namespace npx {
@@ -2395,6 +2396,39 @@ cudaError_t launch_hm_dilate(const float *hm, float *tmp, float *out, int H, int
     return cudaGetLastError();
 }
 
+// The window wait on its own: one warp in groups of 8 lanes, each group with an mbarrier in shared
+// memory; groups 0 and 2 arm theirs for a copy that is never issued (an arrival that expects
+// HM_BOX x HM_WIN x 4 bytes), groups 1 and 3 complete theirs at once.  Every lane then waits with
+// win_wait_warp.  out[0] = lanes whose wait gave up, out[1] = lanes that saw their barrier
+// complete, out[2] = microseconds the wait took (lane 0).
+__global__ void __launch_bounds__(32) window_wait_selftest_kernel(int *out) {
+    __shared__ uint64_t bars[4];
+    const int lane = threadIdx.x, g = lane / 8;
+    if (lane % 8 == 0) win_bar_init(&bars[g]);
+    __syncwarp();
+    if (lane % 8 == 0) {
+        if (g % 2 == 0)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bars[g])),
+                         "r"((uint32_t)(HM_BOX * HM_WIN * sizeof(float)))
+                         : "memory");
+        else
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bars[g])) : "memory");
+    }
+    __syncwarp();
+    unsigned long long t0, t1;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    const bool landed = win_wait_warp(&bars[g], 0u, true);
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+    const unsigned up = __ballot_sync(FULL_MASK, !landed), ok = __ballot_sync(FULL_MASK, landed);
+    __syncwarp();
+    if (lane % 8 == 0) win_bar_inval(&bars[g]);
+    if (lane == 0) {
+        out[0] = __popc(up);
+        out[1] = __popc(ok);
+        out[2] = (int)((t1 - t0) / 1000ull);
+    }
+}
+
 typedef CUresult (*TmapEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -2532,3 +2566,23 @@ cudaError_t launch_points(const WorldDev &W, int scene, float *d_out, cudaStream
 }
 
 }  // namespace npx
+
+extern "C" int npx_window_wait_selftest(int *gave_up, int *completed, int *elapsed_us, void *stream) {
+    if (!gave_up || !completed || !elapsed_us)
+        return npx::set_last_error(NPX_EINVAL, "npx_window_wait_selftest: null argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, 3 * sizeof(int));
+    if (e != cudaSuccess) return npx::set_last_error(NPX_ENOMEM, cudaGetErrorString(e));
+    int h[3] = {-1, -1, -1};
+    npx::window_wait_selftest_kernel<<<1, 32, 0, st>>>(d);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    if (e != cudaSuccess) return npx::set_last_error(NPX_ECUDA, cudaGetErrorString(e));
+    *gave_up = h[0];
+    *completed = h[1];
+    *elapsed_us = h[2];
+    return NPX_OK;
+}

@@ -108,6 +108,16 @@ def gemm_wait_selftest(use_abort: bool, stream=None):
     return t.value, us.value
 
 
+def window_wait_selftest(stream=None):
+    """The step kernel's bounded window-copy wait on its own: (lanes that gave up, lanes that saw
+    their barrier complete, microseconds), two of its four 8-lane groups waiting on copies that are
+    never issued."""
+    load()
+    up, ok, us = C.c_int(), C.c_int(), C.c_int()
+    _check(_lib.npx_window_wait_selftest(C.byref(up), C.byref(ok), C.byref(us), C.c_void_p(stream or 0)))
+    return up.value, ok.value, us.value
+
+
 def gemm_bf16(A, B, M, N, K, epilogue: GemmEpilogue, err, splits=1, stream=None):
     """npx_gemm_bf16: C = A B^T on the tensor cores (device pointers as integers)."""
     load()
@@ -146,6 +156,7 @@ _SIGS = {
     "npx_step_noalloc": [P, I, P],
     "npx_gemm_bf16": [P, P, I, I, I, I, P, P, P],
     "npx_gemm_wait_selftest": [I, P, P, P],
+    "npx_window_wait_selftest": [P, P, P, P],
     "npx_world_set_friction_model": [P, I],
     "npx_world_set_arenas": [P, I, C.c_float],
     "npx_gp_programs_set": [P, P],

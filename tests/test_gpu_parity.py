@@ -13,7 +13,7 @@ import pytest
 from scipy.spatial.transform import Rotation
 
 from oracle.oracle import Oracle, quat_matrix
-from paper_2411_05799_gb300 import scenes
+from paper_2411_05799_gb300 import npx, scenes
 from paper_2411_05799_gb300.npx import World, NpxError
 from tests.parity import (STEP_RTOL, clone, per_step_compare, quat_angle, rel, to_gpu)
 
@@ -500,3 +500,16 @@ def _window_world(b, w, horizon):
     w.step(horizon)
     r = w.read()
     return np.linalg.norm(r["cog"] - o.c, axis=1), quat_angle(r["quat"], o.q), r, o
+
+
+def test_window_copy_wait_gives_up_and_the_context_survives():
+    """The height-map window's copy wait is bounded: lanes whose copy never comes give up after
+    the one-second limit (the step kernel then freezes the scene with status bit 2), lanes whose
+    barrier completed go on, the warp leaves the wait together, and the context still steps a
+    rough-terrain world correctly."""
+    torch = pytest.importorskip("torch")
+    st = torch.cuda.current_stream().cuda_stream
+    up, ok, us = npx.window_wait_selftest(st)
+    assert (up, ok) == (16, 16)
+    assert 0.9e6 <= us <= 5e6, us
+    test_rough_terrain_cpg_per_step()
