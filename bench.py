@@ -88,7 +88,9 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs: sampled
+    every 10 ms, each line stamped on arrival; the report keeps the samples that arrived inside
+    the timed region (plus the sampling interval, for the reporting lag) and says how many."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -103,7 +105,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "10"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -112,9 +114,9 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
+            self.rows.append((time.perf_counter(), [x.strip() for x in line.split(",")]))
 
-    def stop(self) -> dict:
+    def stop(self, t0: float = None, t1: float = None) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -125,7 +127,9 @@ class ClockSampler:
         self.thread.join(timeout=5)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
+        inside = [r for t, r in self.rows if t0 is not None and t0 <= t <= t1 + 0.02]
+        rows = inside if inside else [r for _, r in self.rows]
+        for r in rows:
             try:
                 sm.append(float(r[1]))
                 smax.append(float(r[2]))
@@ -136,7 +140,8 @@ class ClockSampler:
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "samples_in_timed_region": len(inside),
+                "sampling_ms": 10}
 
 
 def cpu_oracle_sample(batch, n_scenes: int, n_steps: int, threads: int) -> dict:
@@ -588,13 +593,16 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     clocks.start()
     time.sleep(0.3)
+    t_begin = time.perf_counter()
     for i in range(args.steps):
         ev[i][0].record(stream)
         world.step(CHUNK)
         ev[i][1].record(stream)
         l2_flush()
     torch.cuda.synchronize(dev)
-    clk = clocks.stop()
+    t_end = time.perf_counter()
+    time.sleep(0.03)   # the samples of the region's last moments arrive
+    clk = clocks.stop(t_begin, t_end)
     per_step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = float(sum(per_step_ms))
     launches = world.info()["kernel_launches"] - launches0
