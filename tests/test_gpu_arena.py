@@ -282,3 +282,19 @@ def test_arena_runs_are_deterministic():
         out.append(w.read())
     for k in ("cog", "quat", "vel", "angmom", "theta", "contacts", "status"):
         assert np.array_equal(out[0][k], out[1][k]), k
+
+
+def test_arena_with_friction_options_per_step():
+    """Arenas with both friction refinements on (force-weighted rows and the friction impulse's
+    horizontal-axis torque; the arena build of the step kernel compiles them in): per step from
+    the oracle's state with the same options while legs collide."""
+    from paper_2411_05799_gb300.npx import FRIC_TILT, FRIC_WEIGHTED
+    mode = FRIC_WEIGHTED | FRIC_TILT
+    size = 4
+    b = scenes.arena_batch(8, size, seed_key=12)
+    w = World.from_batch(b, configure=dict(lanes_per_scene=8))
+    w.set_arenas(size, RADIUS)
+    w.set_friction_model(mode)
+    o = Oracle(b, threads=THREADS, fric_mode=mode, arena=size, arena_radius=RADIUS)
+    touched = _arena_step_parity(w, o, size, [0, 1, 80, 81, 300, 480, 801, 1200])
+    assert touched > 50
