@@ -721,7 +721,8 @@ def run_profile(args):
         world.close()
         return 0
     if args.profile in ("step", "step_hm", "arena"):
-        batch = {"step": lambda: scenes.hexapod_batch(N_SCENES), "step_hm": lambda: scenes.cpg_batch(16384),
+        batch = {"step": lambda: scenes.hexapod_batch(args.scenes or N_SCENES),
+                 "step_hm": lambda: scenes.cpg_batch(args.scenes or 16384),
                  "arena": lambda: scenes.arena_batch(N_SCENES // 4, 4)}[args.profile]()
         world = World.from_batch(batch, configure=dict(lanes_per_scene=args.lps, warps_per_block=args.wpb,
                                                        chunk_steps=args.chunk))
@@ -776,6 +777,7 @@ def main():
                     help="ncu driver (no bench line): step kernel (4,096 hexapods on flat ground, or "
                          "16,384 on rough height maps), network GEMMs or surrogate step")
     ap.add_argument("--lps", type=int, default=16)
+    ap.add_argument("--scenes", type=int, default=0, help="step profiles: scenes (0: the workload's own)")
     ap.add_argument("--fallback-bits", type=int, default=0,
                     help="surrogate profile: fallback when more contact sensors change (-1: never)")
     ap.add_argument("--wpb", type=int, default=16)
