@@ -1812,16 +1812,6 @@ __global__ void __launch_bounds__(32) points_kernel(const __grid_constant__ Worl
 // it is computed once per change into a per-scene cache (shape_cache_kernel) and the per-step
 // kernels do no forward kinematics.
 
-// joint angles after the joint update of step n (clamped targets on update steps)
-__device__ __forceinline__ float angle_after(const WorldDev &W, int l0, int j0, int j, const float *th,
-                                             long long n) {
-    if (W.act_mode != 0 && n % W.K == 0) {
-        const LinkDev lk = W.links[l0 + j + 1];
-        return fminf(fmaxf(joint_target(W, j0 + j, n), lk.lo), lk.hi);
-    }
-    return th[j];
-}
-
 __device__ __forceinline__ Sym cached_sym(const float *a, int S, int s) {
     return Sym{a[0 * S + s], a[1 * S + s], a[2 * S + s], a[3 * S + s], a[4 * S + s], a[5 * S + s]};
 }
@@ -1989,42 +1979,97 @@ __global__ void __launch_bounds__(128) sensor_index_kernel(const __grid_constant
 // when x_mu is set), raw, BF16 standardised into the network's input rows (whose padding columns
 // are zero and are not written), and the delta target against the raw features of the previous
 // state.
+// per-scene values a features block computes once: CoG, orientation, velocity, angular velocity,
+// rotation matrix, horizontal reference and sensor word
+enum { FS_C = 0, FS_Q = 3, FS_V = 7, FS_W = 10, FS_R = 13, FS_RX = 22, FS_RY = 23, FS_SENS = 24, FS_N = 25 };
+
 __global__ void __launch_bounds__(256) features_kernel(const __grid_constant__ WorldDev W, SurCache C, SurrogateIO io, int spb) {
-    extern __shared__ float rows[];   // [spb x nf] raw features of the block's scenes
-    const int tid = threadIdx.x, S = W.S;
+    // [spb x nfp] raw features of the block's scenes (rows padded to whole float4), then
+    // [spb x FS_N] per-scene values
+    extern __shared__ __align__(16) float rows[];
+    __shared__ int tick;
+    const int tid = threadIdx.x, S = W.S, nfp = (io.nf + 3) & ~3;
     const int s0 = blockIdx.x * spb, ns = min(spb, S - s0);
-    if (tid < ns * io.nl) {
-        const int sl = tid / io.nl, l = tid % io.nl, s = s0 + sl;
-        float *row = rows + (size_t)sl * io.nf;
+    float *sv = rows + (size_t)spb * nfp;
+    const long long n = *W.step;
+    // every (scene, link) thread issues its loads first, so that they overlap the per-scene phase
+    const bool mine = tid < ns * io.nl;
+    const int sl = mine ? tid / io.nl : 0, l = mine ? tid % io.nl : 0, s = s0 + sl;
+    int l0 = 0, nl = 0;
+    float4 lq = make_float4(1.f, 0.f, 0.f, 0.f), lp = make_float4(0.f, 0.f, 0.f, 0.f);
+    float th = 0.f;
+    if (mine) {
+        l0 = W.link_off[s];
+        nl = W.link_off[s + 1] - l0;
+        if (l < nl) {
+            lq = C.lk[((size_t)s * C.nl + l) * 2];
+            lp = C.lk[((size_t)s * C.nl + l) * 2 + 1];
+        }
+        if (l >= 1 && l - 1 < nl - 1) th = W.theta[l0 - s + l - 1];
+    }
+    if (tid < ns) {   // one thread per scene: the scene's rotation and angular velocity
+        const int s = s0 + tid;
         const RootState x = load_root(W, s);
         float R[9], om[3];
         quat_mat(x.q, R);
         world_sym(R, cached_sym(C.inert + 6 * S, S, s), x.L, om);
-        const float rx = io.cxy_ref ? io.cxy_ref[2 * s] : x.c[0], ry = io.cxy_ref ? io.cxy_ref[2 * s + 1] : x.c[1];
-        const int l0 = W.link_off[s], nl = W.link_off[s + 1] - l0, j0 = l0 - s;
+        float *p = sv + (size_t)tid * FS_N;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { p[FS_C + k] = x.c[k]; p[FS_V + k] = x.v[k]; p[FS_W + k] = om[k]; }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) p[FS_Q + k] = x.q[k];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) p[FS_R + k] = R[k];
+        p[FS_RX] = io.cxy_ref ? io.cxy_ref[2 * s] : x.c[0];
+        p[FS_RY] = io.cxy_ref ? io.cxy_ref[2 * s + 1] : x.c[1];
+        p[FS_SENS] = __uint_as_float(W.sensors[s]);
+        if (io.cxy_out) { io.cxy_out[2 * s] = x.c[0]; io.cxy_out[2 * s + 1] = x.c[1]; }
+    }
+    if (tid == 0) tick = W.act_mode != 0 && n % W.K == 0;   // the step's joint update (all scenes)
+    __syncthreads();
+    if (mine) {   // one thread per (scene, link)
+        float *row = rows + (size_t)sl * nfp;
+        const float *p = sv + (size_t)sl * FS_N;
+        RootState x;
+        float R[9], om[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { x.c[k] = p[FS_C + k]; x.v[k] = p[FS_V + k]; om[k] = p[FS_W + k]; x.L[k] = 0.f; }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x.q[k] = p[FS_Q + k];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) R[k] = p[FS_R + k];
+        const int j0 = l0 - s;
         float f[13];
         if (l < nl) {
-            link_features(x, R, om, C.lk[((size_t)s * C.nl + l) * 2], C.lk[((size_t)s * C.nl + l) * 2 + 1], rx, ry, f);
+            link_features(x, R, om, lq, lp, p[FS_RX], p[FS_RY], f);
         } else {
 #pragma unroll
             for (int k = 0; k < 13; ++k) f[k] = 0.f;
         }
 #pragma unroll
         for (int k = 0; k < 13; ++k) row[13 * l + k] = f[k];
-        if (l >= 1) {   // joint l - 1 drives link l
+        if (l >= 1) {   // joint l - 1 drives link l: its angle after this step's joint update
             const int j = l - 1;
-            row[13 * io.nl + j] = j < nl - 1 ? angle_after(W, l0, j0, j, W.theta + j0, *W.step) : 0.f;
+            float a = 0.f;
+            if (j < nl - 1) {
+                if (tick) {
+                    const LinkDev lk = W.links[l0 + j + 1];
+                    a = fminf(fmaxf(joint_target(W, j0 + j, n), lk.lo), lk.hi);
+                } else {
+                    a = th;
+                }
+            }
+            row[13 * io.nl + j] = a;
         }
-        const uint32_t sens = W.sensors[s];
+        const uint32_t sens = __float_as_uint(p[FS_SENS]);
         for (int k = l; k < io.ns; k += io.nl) row[14 * io.nl - 1 + k] = (float)((sens >> k) & 1u);
-        if (l == 0 && io.cxy_out) { io.cxy_out[2 * s] = x.c[0]; io.cxy_out[2 * s + 1] = x.c[1]; }
     }
     __syncthreads();
     // the block's rows are contiguous in every output: write them out in full lines
     if (io.X || io.Xraw || io.T) {
         for (int e = tid; e < ns * io.nf; e += blockDim.x) {
             const int sl = e / io.nf, col = e - sl * io.nf, s = s0 + sl;
-            const float raw = rows[e];
+            const float raw = rows[(size_t)sl * nfp + col];
             const size_t o = (size_t)s * io.nf + col;
             if (io.Xraw) io.Xraw[o] = raw;
             if (io.X) io.X[o] = io.x_mu ? (raw - io.x_mu[col]) * io.x_isd[col] : raw;
@@ -2035,20 +2080,38 @@ __global__ void __launch_bounds__(256) features_kernel(const __grid_constant__ W
         }
     }
     if (io.Xb) {   // 8 BF16 (16 bytes) per store; the columns past nf are padding and stay zero
-        const int chunks = (io.nf + 7) >> 3;
+        // chunks wholly inside the row take whole float4 loads when the norms are 16-byte aligned
+        // (the caller's arrays; the rows are padded to float4)
+        const bool vec = ((reinterpret_cast<uintptr_t>(io.x_mu) | reinterpret_cast<uintptr_t>(io.x_isd)) & 15u) == 0;
+        const int chunks = (io.nf + 7) >> 3, full = vec ? io.nf >> 3 : 0;
         for (int e = tid; e < ns * chunks; e += blockDim.x) {
-            const int sl = e / chunks, c0 = (e - sl * chunks) * 8;
+            const int sl = e / chunks, ch = e - sl * chunks, c0 = ch * 8;
+            float v[8];
+            if (ch < full) {
+                const float4 *r4 = reinterpret_cast<const float4 *>(rows + (size_t)sl * nfp + c0);
+                const float4 ra = r4[0], rb = r4[1];
+                v[0] = ra.x; v[1] = ra.y; v[2] = ra.z; v[3] = ra.w; v[4] = rb.x; v[5] = rb.y; v[6] = rb.z; v[7] = rb.w;
+                if (io.x_mu) {
+                    const float4 *m4 = reinterpret_cast<const float4 *>(io.x_mu + c0);
+                    const float4 *i4 = reinterpret_cast<const float4 *>(io.x_isd + c0);
+                    const float4 ma = __ldg(m4), mb = __ldg(m4 + 1), ia = __ldg(i4), ib = __ldg(i4 + 1);
+                    const float mu[8] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w};
+                    const float is[8] = {ia.x, ia.y, ia.z, ia.w, ib.x, ib.y, ib.z, ib.w};
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) v[k] = (v[k] - mu[k]) * is[k];
+                }
+            } else {   // the row's last, partial chunk (or unaligned norms)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int col = c0 + k;
+                    const float raw = col < io.nf ? rows[(size_t)sl * nfp + col] : 0.f;
+                    v[k] = col < io.nf && io.x_mu ? (raw - io.x_mu[col]) * io.x_isd[col] : raw;
+                }
+            }
             uint32_t w[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                float v[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int col = c0 + 2 * k + h;
-                    const float raw = col < io.nf ? rows[(size_t)sl * io.nf + col] : 0.f;
-                    v[h] = col < io.nf && io.x_mu ? (raw - io.x_mu[col]) * io.x_isd[col] : raw;
-                }
-                const __nv_bfloat162 hv = __floats2bfloat162_rn(v[0], v[1]);
+                const __nv_bfloat162 hv = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
                 w[k] = *reinterpret_cast<const uint32_t *>(&hv);
             }
             *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(io.Xb) + (size_t)(s0 + sl) * io.ldb + c0) =
@@ -2252,7 +2315,7 @@ cudaError_t launch_shape_cache(const WorldDev &W, const SurCache &C, cudaStream_
 cudaError_t launch_features(const WorldDev &W, const SurCache &C, const SurrogateIO &io, cudaStream_t st) {
     const int spb = io.nl >= 256 ? 1 : 256 / io.nl;             // scenes per block
     const int threads = std::max(256, (io.nl + 31) / 32 * 32);
-    const size_t sm = (size_t)spb * io.nf * sizeof(float);
+    const size_t sm = (size_t)spb * (((io.nf + 3) & ~3) + FS_N) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute((void *)features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     features_kernel<<<(unsigned)((W.S + spb - 1) / spb), threads, sm, st>>>(W, C, io, spb);
