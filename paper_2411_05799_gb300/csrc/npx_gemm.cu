@@ -605,20 +605,27 @@ extern "C" int npx_gemm_bf16(const void *A, const void *B, int M, int N, int K, 
     CUtensorMap ta, tb, tout;
     if (!make_map(&ta, A, M, K, BM) || !make_map(&tb, B, N, K, BN))
         return npx::set_last_error(NPX_ECUDA, "npx_gemm_bf16: tensor-map encoding failed");
-    // FP32 row-major output leaves through TMA stores (BF16 outputs are stored directly: those
-    // epilogues are bound by the GELU arithmetic, and staging them measured slower)
+    // the row-major output leaves through per-warp staging boxes and TMA stores: FP32 (store
+    // mode 2), or BF16 when it is the only row-major output (mode 1)
     memset(&tout, 0, sizeof tout);
     int store_mode = 0;
     if (ep->outf && !(ep->out && ep->mode != NPX_EPI_F32)) {
         if (!make_out_map(&tout, ep->outf, true, M, N, ep->ldf, ep->mode == NPX_EPI_F32 ? splits : 1, ep->split_stride))
             return npx::set_last_error(NPX_ECUDA, "npx_gemm_bf16: output tensor-map encoding failed");
         store_mode = 2;
+    } else if (ep->out && !ep->outf && ep->mode != NPX_EPI_F32) {
+        if (!make_out_map(&tout, ep->out, false, M, N, ep->ldo, 1, 0))
+            return npx::set_last_error(NPX_ECUDA, "npx_gemm_bf16: output tensor-map encoding failed");
+        store_mode = 1;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
-    if (store_mode)
+    if (store_mode == 2)
         e = BN == 256 ? launch<256, 2>(ta, tb, tout, M, N, K, splits, *ep, err, st)
                       : launch<128, 2>(ta, tb, tout, M, N, K, splits, *ep, err, st);
+    else if (store_mode == 1)
+        e = BN == 256 ? launch<256, 1>(ta, tb, tout, M, N, K, splits, *ep, err, st)
+                      : launch<128, 1>(ta, tb, tout, M, N, K, splits, *ep, err, st);
     else
         e = BN == 256 ? launch<256, 0>(ta, tb, tout, M, N, K, splits, *ep, err, st)
                       : launch<128, 0>(ta, tb, tout, M, N, K, splits, *ep, err, st);
