@@ -47,11 +47,11 @@ FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_GHZ / 1e3
 # (lanes per scene, warps per block, blocks), from ncu (profiles/step_kernel_*_dram.md); reported
 # only for a captured shape, and to be re-taken whenever the kernel changes
 STEP_TRAFFIC = {
-    (WORKLOAD, 8, 7, 147): 31_890_176,
-    (WORKLOAD, 16, 14, 147): 31_950_848,
-    ("hexapod_rough_terrain_16384_scenes", 16, 4, 456): 211_604_736,
-    ("hexapod_rough_terrain_16384_scenes", 16, 2, 912): 211_816_960,
-    ("hexapod_rough_terrain_16384_scenes", 16, 1, 1824): 212_502_528,
+    (WORKLOAD, 8, 7, 147): 32_006_400,
+    (WORKLOAD, 16, 14, 147): 31_901_440,
+    ("hexapod_rough_terrain_16384_scenes", 16, 4, 456): 225_079_808,
+    ("hexapod_rough_terrain_16384_scenes", 16, 2, 912): 224_312_320,
+    ("hexapod_rough_terrain_16384_scenes", 16, 1, 1824): 225_149_696,
 }
 
 
